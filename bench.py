@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark of batched DDSG (cut-HDMR adaptive sparse grid) interpolation.
+
+Default workload: d = 100 (N = 50), m = 51 outputs, order-2 cut-HDMR with the
+anchor at the domain centre (100 1D + 4950 2D components + the empty one),
+every component adaptively refined (surplus threshold 1e-3, level 10) on the
+seeded kinked test family; 2e6 query points uniform in [0,1]^100. One step is
+one evaluation of all 2e6 points (query encoding + interpolation kernels).
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload d100|d20|sg4]
+                  [--precision f32c|f64] [--form slicefree|paper]
+                  [--impl reference]
+
+Prints one JSON line (rank 0). --impl reference times the CPU oracle (test
+infrastructure) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "interp evals/s (points·outputs) at d=100; % HBM roofline; FP32 vs FP64 error"
+
+WORKLOADS = {
+    "d100": dict(d=100, m=51, order=2, eps=1e-3, level=10, Q=2_000_000, wid=synth.W_D100,
+                 queries="uniform", precision="f32c", form="slicefree"),
+    "d20": dict(d=20, m=11, order=2, eps=1e-3, level=10, Q=440_000, wid=synth.W_D20,
+                queries="monomial", precision="f64", form="slicefree"),
+    "sg4": dict(d=4, m=3, order=4, eps=None, level=5, Q=100_000, wid=synth.W_SG4,
+                queries="uniform", precision="f64", form="paper"),
+}
+
+FP32_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (no tensor path)
+
+
+def full_order_components(d, order):
+    import itertools
+    out = []
+    for k in range(order + 1):
+        out.extend(itertools.combinations(range(d), k))
+    return out
+
+
+def comp_list(w):
+    if w["eps"] is None:
+        return [tuple(range(w["d"]))]
+    return full_order_components(w["d"], w["order"])
+
+
+def make_queries(w, rank=0):
+    seed = synth.BASE_SEED + w["wid"] + 7919 * rank
+    if w["queries"] == "monomial":
+        N = w["d"] // 2
+        return synth.monomial_shaped_queries(seed, w["Q"] // (2 * (N + 1)), N)
+    return synth.uniform_queries(seed, w["Q"], w["d"])
+
+
+def value_fn(w):
+    c = synth.family_coeffs(synth.BASE_SEED + w["wid"], w["m"], w["d"])
+    return lambda dims, X: synth.family_cut(c, dims, X)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def oracle_build(w):
+    import oracle as O
+    E = O.OracleDDSG(w["d"], w["m"])
+    if w["eps"] is None:
+        E.add_regular(tuple(range(w["d"])), w["level"])
+        E.fill_values(value_fn(w))
+        E.hierarchize()
+    else:
+        for u in comp_list(w):
+            E.add_regular(u, 2)
+        E.build_adaptive(value_fn(w), w["eps"], w["level"])
+    return E
+
+
+def oracle_rate(E, w, X, budget_s):
+    """Oracle evaluation rate (evals/s, points*outputs) on a prefix of X that
+    takes about budget_s seconds; returns (rate, n_used)."""
+    form = 1 if w["form"] == "slicefree" else 0
+    n = 1
+    used, t_used = 0, 0.0
+    while True:
+        t0 = time.perf_counter()
+        E.eval(X[used:used + n], form=form)
+        dt = time.perf_counter() - t0
+        used += n
+        t_used += dt
+        if t_used >= budget_s or used >= X.shape[0]:
+            break
+        n = max(1, min(X.shape[0] - used, int(n * 2 if dt < 0.2 * budget_s else n)))
+    return used * w["m"] / t_used, used
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    E = oracle_build(w)
+    X = make_queries(w)
+    # each step: a bounded sample sized to ~4 s of single-thread oracle work
+    _, n_probe = oracle_rate(E, w, X, 1.0)
+    per_step = max(1, int(n_probe * 4))
+    for s in range(args.warmup):
+        E.eval(X[:min(per_step, 2)], form=1 if w["form"] == "slicefree" else 0)
+    times = []
+    for s in range(args.steps):
+        lo = (s * per_step) % max(1, X.shape[0] - per_step)
+        t0 = time.perf_counter()
+        E.eval(X[lo:lo + per_step], form=1 if w["form"] == "slicefree" else 0)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    value = per_step * w["m"] / (ms * 1e-3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "d": w["d"], "m": w["m"],
+                       "queries_per_step": per_step, "form": w["form"]},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} of the {w['Q']} queries per step, single thread"},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# CUDA arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ddsg", choices=["ddsg", "reference"])
+    ap.add_argument("--workload", default="d100", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["f32c", "f64"])
+    ap.add_argument("--form", default=None, choices=["slicefree", "paper"])
+    ap.add_argument("--queries", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    w = dict(WORKLOADS[args.workload])
+    if args.precision:
+        w["precision"] = args.precision
+    if args.form:
+        w["form"] = args.form
+    if args.queries:
+        w["Q"] = args.queries
+    args.warmup = max(args.warmup, 3) if args.impl == "ddsg" else args.warmup
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import paper_2202_06555_gb300 as G
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (libddsg has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    G.load()
+    prec = G.F32C if w["precision"] == "f32c" else G.F64
+    form = G.FORM_SLICEFREE if w["form"] == "slicefree" else G.FORM_PAPER
+
+    # -- construction (not timed as a step) ---------------------------------
+    t0 = time.perf_counter()
+    h = G.HDMR(w["d"], w["m"], w["order"])
+    fn = value_fn(w)
+    if w["eps"] is None:
+        h.add_regular(list(range(w["d"])), w["level"])
+        _, _, xs = h.component_points(0)
+        h.hierarchize(torch.from_numpy(np.ascontiguousarray(fn(tuple(range(w["d"])), xs))).cuda())
+    else:
+        for u in comp_list(w):
+            h.add_regular(list(u), 2)
+        G.build_adaptive(h, fn, w["eps"], w["level"])
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    ncomp, npts = h.sizes()
+
+    X = make_queries(w, rank)
+    n = X.shape[0]
+    x = torch.from_numpy(X).cuda()
+    y = torch.empty((n, w["m"]), dtype=torch.float64, device="cuda")
+    cnt = torch.empty(n, dtype=torch.int32, device="cuda")
+    h.reserve(n)
+    stream = torch.cuda.current_stream()
+
+    # algorithmic work of one launch: active points per query (index work is exact)
+    h.eval(x, y, prec, form, None, cnt)
+    torch.cuda.synchronize()
+    active_total = float(cnt.double().sum().item())
+    k_mean = 2.0 if w["order"] >= 2 else 1.0
+    flops_per_launch = active_total * (2.0 * w["m"] + (k_mean - 1.0))
+
+    for _ in range(args.warmup):
+        h.eval(x, y, prec, form)
+    torch.cuda.synchronize()
+
+    h.profile(True)
+    h.profile_read(reset=True)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        if uuid and not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            h.eval(x, y, prec, form)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+    prof = h.profile_read(reset=True)
+    h.profile(False)
+    ms_total = e0.elapsed_time(e1)
+    if dist is not None:
+        tt = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    value = world * n * w["m"] / (ms_step * 1e-3)
+    launches = sum(v[1] for v in prof.values())
+    eval_ms, eval_n = prof.get("eval", (0.0, 0))
+    eval_avg_ms = eval_ms / max(1, eval_n)
+
+    # -- roofline of the dominant kernel (interpolation) ----------------------
+    if prec == G.F32C:
+        peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        peak_src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+    else:
+        peak = FP64_PEAK_TFLOPS
+        peak_src = "nominal GB300 FP64 1.25 TFLOP/s"
+    achieved = flops_per_launch / (eval_avg_ms * 1e-3) / 1e12
+    hbm_bytes = n * w["d"] * 8 + n * w["m"] * 8 + npts * w["m"] * (4 if prec == G.F32C else 8)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_frac = hbm_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak
+
+    # -- end to end: host buffers through the C ABI ---------------------------
+    xh = torch.from_numpy(X).pin_memory()
+    yh = torch.empty((n, w["m"]), dtype=torch.float64).pin_memory()
+    xnp, ynp = xh.numpy(), yh.numpy()
+    h.eval_host(xnp, ynp, prec, form)
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        h.eval_host(xnp, ynp, prec, form)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_times)
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    out = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if prec == G.F32C else "f64", "data": "synthetic",
+           "config": {"workload": f"ddsg_{args.workload}", "d": w["d"], "m": w["m"],
+                      "order": w["order"], "components": ncomp, "grid_points": npts,
+                      "eps_gamma": w["eps"], "max_level": w["level"], "queries_per_gpu": n,
+                      "precision": w["precision"], "form": w["form"],
+                      "active_points_per_query": active_total / n,
+                      "l2": "inputs larger than L2 (x %.2f GB, surpluses %.2f GB); no flush"
+                            % (n * w["d"] * 8 / 1e9, npts * w["m"] * (4 if prec == G.F32C else 8) / 1e9),
+                      "build_s": t_build},
+           "gpu_launches": launches,
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                        "kernel": "eval", "kernel_ms": eval_avg_ms,
+                        "flops_per_launch": flops_per_launch},
+           "hbm_roofline": {"bytes_per_step": hbm_bytes, "frac": hbm_frac, "peak_gbs": hbm_peak,
+                            "note": "compulsory bytes / step time / measured copy bandwidth"},
+           "kernels_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
+           "clocks": clk.summary(),
+           "e2e": {"value": world * n * w["m"] / e2e_s, "unit": "evals/s",
+                   "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(n * w["m"] * 8),
+                   "ms_per_step": e2e_s * 1e3}}
+
+    # -- precision: FP32-compensated vs the plain FP64 GPU form -----------------
+    if rank == 0 and not args.no_fp64 and prec == G.F32C:
+        ns = min(n, 500_000)
+        y64 = torch.empty((ns, w["m"]), dtype=torch.float64, device="cuda")
+        y32 = torch.empty((ns, w["m"]), dtype=torch.float64, device="cuda")
+        h.eval(x[:ns], y32, G.F32C, form)
+        h.eval(x[:ns], y64, G.F64, form)   # warm
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.eval(x[:ns], y64, G.F64, form)
+        b.record(stream)
+        torch.cuda.synchronize()
+        rel = ((y32 - y64).abs() / y64.abs().clamp_min(1e-300))
+        out["fp64_gpu"] = {"value": ns * w["m"] / (a.elapsed_time(b) * 1e-3), "unit": "evals/s",
+                           "queries": ns}
+        out["f32c_vs_f64_gpu"] = {"max_rel": float(rel.max().item()),
+                                  "rms_rel": float(rel.pow(2).mean().sqrt().item()),
+                                  "per_output_max_rel_max": float(rel.max(0).values.max().item()),
+                                  "queries": ns}
+
+    # -- CPU baseline: the oracle on a bounded sample (rank 0, N=1 only) --------
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        E = oracle_build(w)
+        rate, used = oracle_rate(E, w, X, 20.0)
+        # precision against the FP64 oracle on the sample (scale max(|y|, S))
+        r = E.eval(X[:min(used, 400)], form=1 if w["form"] == "slicefree" else 0, want=("y", "S"))
+        ys = y[:min(used, 400)].cpu().numpy()   # y holds the last timed step's result
+        scale = np.maximum(np.abs(r["y"]), r["S"])
+        relo = np.abs(ys - r["y"]) / scale
+        out["error_vs_oracle"] = {"queries": int(relo.shape[0]), "max_rel": float(relo.max()),
+                                  "rms_rel": float(np.sqrt(np.mean(relo ** 2))),
+                                  "per_output_max": [float(v) for v in relo.max(0)],
+                                  "scale": "max(|y|, sum of |terms|)"}
+        out["cpu_baseline"] = {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                               "sample": f"first {used} of the {n} queries, single thread "
+                                         f"(~20 s of CPU work)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,230 @@
+/*
+ * ddsg.h -- C ABI of libddsg: batched evaluation of a cut-HDMR adaptive
+ * sparse-grid ("DDSG") interpolant on one GB300 GPU (sm_103a).
+ *
+ * Method: Eftekhari & Scheidegger, "High-Dimensional Dynamic Stochastic Model
+ * Representation", arXiv 2202.06555.
+ *   - sparse grids, hat basis, surpluses, refinement:   Sec. 3.1, eq. 3.1-3.8
+ *   - cut-HDMR and its telescopic components:           Sec. 3.2, eq. ddsg2.2.5-2.2.6
+ *   - DDSG approximation:                               Sec. 3.3, eq. 3.16
+ *   - vectorized evaluation f(x) = a(x)^T b:            Sec. 4.1, eq. 4.2
+ *   - IRBC model residual (Euler equations):            Sec. 2.1, eq. model1-model2
+ *
+ * Conventions shared by every call
+ *   d        state dimension; m number of outputs (policy components).
+ *   Domain   physical box [lo_i, hi_i]; a coordinate maps to [0,1] by
+ *            (x - lo)/(hi - lo) and is clamped to [0,1] (clamps are counted).
+ *   Basis    boundary-augmented hats (Sec. 3.1, "augmenting the basis"):
+ *            level 1: constant 1 (node 1/2, index 1);
+ *            level 2: nodes 0 and 1 (index 0 and 2), phi = max(0, 1 - |2x - i|);
+ *            level l >= 3: nodes i/2^(l-1), i odd, phi = max(0, 1 - |2^(l-1)x - i|).
+ *            Level constraint of a level-L grid: sum_j (l_j - 1) <= L - 1 (eq. 3.5).
+ *   Points   a component of k dimensions stores per point k levels (uint8)
+ *            and k indices (uint32); arrays are point-major: levels[p*k + j].
+ *   Order    canonical point order is (level sum, level tuple, index tuple),
+ *            lexicographic; refinement appends new points in that order.
+ *   Memory   pointers named *_dev are device pointers the caller owns (e.g.
+ *            torch tensors); pointers named *_host are host arrays, copied
+ *            before the call returns. The handle owns every device table.
+ *   Streams  calls taking a cudaStream_t are asynchronous on that stream.
+ *   Errors   every call returns DDSG_OK (0) or a negative DDSG_ERR_* code and
+ *            stores a message readable by ddsg_last_error() (thread-local).
+ *            Kernels never trap: bad inputs become NaN outputs and counters.
+ */
+#ifndef DDSG_H
+#define DDSG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ddsg_stream_t; /* == cudaStream_t; NULL = legacy default stream */
+typedef struct hdmr hdmr_t;                /* opaque handle */
+
+enum {
+    DDSG_OK = 0,
+    DDSG_ERR_ARG = -1,     /* invalid argument (sizes, ranges, NULL)                */
+    DDSG_ERR_OOM = -2,     /* device or host allocation failed                      */
+    DDSG_ERR_CUDA = -3,    /* a CUDA runtime call failed                            */
+    DDSG_ERR_STATE = -4,   /* call out of order (e.g. eval before hierarchize)      */
+    DDSG_ERR_TABLE = -5,   /* invalid grid table (range, duplicate, level sum)      */
+    DDSG_ERR_TIMEOUT = -6, /* a bounded device wait gave up                         */
+    DDSG_ERR_NUMERIC = -7  /* non-finite values where finite ones are required      */
+};
+
+enum { DDSG_F64 = 0, DDSG_F32C = 1 };            /* arithmetic of hdmr_eval           */
+enum { DDSG_FORM_PAPER = 0, DDSG_FORM_SLICEFREE = 1 };
+
+#define DDSG_KMAX 8        /* most dimensions of one component                       */
+#define DDSG_LMAX 24       /* highest 1D level                                        */
+
+/* Last error message of the calling thread ("" if none). */
+const char *ddsg_last_error(void);
+/* Library version string. */
+const char *ddsg_version(void);
+
+/*
+ * hdmr_create -- new empty expansion (Sec. 4.2, Alg. 2 inputs: anchor, order).
+ *   d >= 1, m >= 1, 0 <= order <= DDSG_KMAX.
+ *   anchor_host, lo_host, hi_host: length d, physical units, lo < hi.
+ *   The slice-free form additionally needs the anchor at the domain centre
+ *   (canonical 1/2, the level-1 node); hdmr_eval refuses it otherwise.
+ *   Makes no CUDA call: the handle binds to the current CUDA device at its
+ *   first GPU use (hdmr_hierarchize, hdmr_reserve, hdmr_stats) and must be
+ *   used on that device afterwards.
+ */
+int hdmr_create(int d, int m, int order, const double *anchor_host, const double *lo_host,
+                const double *hi_host, hdmr_t **out);
+int hdmr_destroy(hdmr_t *h);
+
+/*
+ * hdmr_add_component -- append the grid of component u = dims (eq. ddsg2.2.6:
+ * it will interpolate the cut function f(anchor \ x_u)).
+ *   k = |u| in [0, order]; dims_host strictly ascending in [0, d); k = 0 is the
+ *   empty component (npts must be 1, levels/indices may be NULL).
+ *   levels_host/indices_host: npts*k. Checked: level in [1, DDSG_LMAX], index
+ *   valid for its level, no duplicate point, u not already present.
+ *   Returns the component id (insertion order) in *comp_id.
+ *   The b coefficients of eq. 4.2 are computed over the accepted set as given
+ *   when the tables are first uploaded (hdmr_hierarchize). A set that is not
+ *   downward closed (e.g. one full-dimensional sparse grid alone) is valid
+ *   for the paper form; the slice-free form needs closure.
+ */
+int hdmr_add_component(hdmr_t *h, int k, const int32_t *dims_host, int64_t npts,
+                       const uint8_t *levels_host, const uint32_t *indices_host, int32_t *comp_id);
+
+/* Same, with the regular level-`level` grid of eq. 3.5 generated by the library. */
+int hdmr_add_regular_component(hdmr_t *h, int k, const int32_t *dims_host, int level,
+                               int32_t *comp_id);
+
+/* Sizes: number of components and total points. */
+int hdmr_num_components(const hdmr_t *h, int32_t *ncomp, int64_t *npts_total);
+
+/*
+ * hdmr_component_info -- k, dims (DDSG_KMAX entries, unused = -1), number of
+ * points and the offset of its first point in the concatenated point order
+ * used by hdmr_hierarchize.
+ */
+int hdmr_component_info(const hdmr_t *h, int32_t comp, int32_t *k, int32_t *dims_host,
+                        int64_t *npts, int64_t *first_point);
+
+/*
+ * hdmr_component_points -- levels/indices (count*k) and physical node
+ * coordinates (count*k, on the component's dims) of points
+ * [first, first+count) of component comp. Any output may be NULL. The caller
+ * evaluates f at these nodes with the other coordinates at the anchor
+ * (the cut points of eq. ddsg2.2.6).
+ */
+int hdmr_component_points(const hdmr_t *h, int32_t comp, int64_t first, int64_t count,
+                          uint8_t *levels_host, uint32_t *indices_host, double *coords_host);
+
+/*
+ * hdmr_hierarchize -- surpluses of every point (Sec. 3.1; "surplus = value
+ * minus the coarser interpolant"), computed on the GPU in FP64:
+ *   alpha_p = v_p - sum_{q in G_u, levelsum(q) < levelsum(p)} alpha_q phi_q(x_p),
+ * layer by layer in increasing level sum, all components in one launch.
+ *   values_dev: device, npts_total*m FP64, components in id order, points in
+ *   table order (the layout hdmr_component_info's first_point describes).
+ *   Also refreshes the FP32 copy of the surpluses used by DDSG_F32C.
+ * Synchronous with respect to the host on return of the table upload only;
+ * the hierarchization itself is asynchronous on `stream`.
+ */
+int hdmr_hierarchize(hdmr_t *h, const double *values_dev, ddsg_stream_t stream);
+
+/*
+ * hdmr_refine -- one adaptive refinement sweep of every component (eq. 3.8):
+ * a point is significant if ||alpha_p||_inf > eps_gamma; each child of a
+ * significant point, in each dimension of its component, is added when its
+ * level tuple satisfies sum(l-1) <= max_level-1 and it is not yet present.
+ *   strict = 0: a child of at least one significant parent is added.
+ *   strict = 1: a child is dropped if any present parent of it is not
+ *               significant (the stricter reading of Sec. 3.1, where finer
+ *               points inside the support of a rejected point are left out).
+ * New points are appended per component in canonical order; *n_new = total.
+ * Needs hierarchized surpluses (reads them back, synchronizing `stream`).
+ * The new points need values before the next hdmr_hierarchize.
+ */
+int hdmr_refine(hdmr_t *h, double eps_gamma, int max_level, int strict, int64_t *n_new,
+                ddsg_stream_t stream);
+
+/* Copy FP64 surpluses of all points to the host (npts_total*m). Synchronous. */
+int hdmr_get_surpluses(const hdmr_t *h, double *alpha_host, ddsg_stream_t stream);
+
+/* b coefficients of eq. 4.2 (one per component, id order), computed on the
+ * host: b_v = sum over accepted u containing v of (-1)^(|u|-|v|). No CUDA call. */
+int hdmr_get_b(const hdmr_t *h, double *b_host);
+
+/*
+ * hdmr_eval -- f(x) for n query points (the vectorized DDSG interpolation of
+ * Sec. 4.1).
+ *   x_dev: device, n*d FP64, physical units, row-major.
+ *   y_dev: device, n*m FP64, row-major (written).
+ *   precision: DDSG_F64 -- FP64 basis products and sums;
+ *              DDSG_F32C -- FP32 surpluses and basis values, FP32 products,
+ *              compensated (Kahan) accumulation, result rounded to FP64.
+ *   form: DDSG_FORM_PAPER -- y = sum_v b_v s_v(x), eq. 4.2 (components with
+ *              b_v = 0 skipped);
+ *         DDSG_FORM_SLICEFREE -- y = sum_u (sum of the points of G_u whose
+ *              levels are all >= 2); equal to the paper form when the anchor
+ *              is the level-1 node and every slice {l_j = 1, j in u\w} of G_u
+ *              equals G_w (true for grids built by hdmr_refine from cut
+ *              values); it avoids the cancellation of large |b_v|.
+ *   hash_dev (nullable, n uint64) / count_dev (nullable, n int32): XOR of the
+ *   point keys / number of summed points with phi_p(x) > 0 in exact
+ *   arithmetic (the active set). Key of point (l, i) of component c:
+ *     z = c; for j < k: z = mix(z ^ (l_j << 40) ^ i_j); key = mix(z + 0x9E3779B97F4A7C15)
+ *   with mix the SplitMix64 finalizer (Steele, Lea & Flood 2014):
+ *     z ^= z>>30; z *= 0xBF58476D1CE4E5B9; z ^= z>>27; z *= 0x94D049BB133111EB; z ^= z>>31.
+ *   Non-finite coordinates give NaN rows (counted in hdmr_stats).
+ *   The slice-free form needs the anchor at the domain centre and a
+ *   downward-closed component set (DDSG_ERR_ARG otherwise).
+ *   Asynchronous on `stream`. Uses a handle-owned workspace that grows on
+ *   demand (cudaMalloc): call hdmr_reserve first to make it capture-safe.
+ */
+int hdmr_eval(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int precision, int form,
+              uint64_t *hash_dev, int32_t *count_dev, ddsg_stream_t stream);
+
+/* Pre-size the eval workspace for up to n queries (no allocation in later evals). */
+int hdmr_reserve(hdmr_t *h, int64_t n);
+
+/*
+ * hdmr_stats -- counters accumulated by hdmr_eval since the last reset:
+ *   stats[0] = clamped coordinates, stats[1] = non-finite query rows.
+ * Synchronizes `stream`. reset != 0 zeroes them afterwards.
+ */
+int hdmr_stats(hdmr_t *h, int64_t *stats_host, int reset, ddsg_stream_t stream);
+
+/*
+ * hdmr_eval_host -- hdmr_eval with HOST buffers: copies x_host (n*d) to a
+ * handle-owned device buffer on `stream`, evaluates, copies y_host (n*m) back
+ * and synchronizes `stream` before returning. Pinned host memory gives the
+ * fastest copies. The whole round trip is the end-to-end cost of one call.
+ */
+int hdmr_eval_host(hdmr_t *h, int64_t n, const double *x_host, double *y_host, int precision,
+                   int form, ddsg_stream_t stream);
+
+/*
+ * Kernel timing (tracing). While enabled, every kernel the handle launches is
+ * bracketed by CUDA events recorded on its launching stream; hdmr_profile_read
+ * waits for them and returns, per kernel kind, the summed device milliseconds
+ * and the number of launches since the last reset. Do not enable while the
+ * stream is being captured into a CUDA graph.
+ */
+enum {
+    DDSG_K_ENCODE = 0,   /* query encoding (clamp, fixed point)   */
+    DDSG_K_EVAL = 1,     /* interpolant evaluation               */
+    DDSG_K_HIER = 2,     /* hierarchization                      */
+    DDSG_K_CONVERT = 3,  /* FP64 -> FP32 surplus copy            */
+    DDSG_K_COPY = 4,     /* host<->device copies of hdmr_eval_host */
+    DDSG_NKINDS = 8
+};
+int hdmr_profile(hdmr_t *h, int enable);
+int hdmr_profile_read(hdmr_t *h, double *ms_host /* DDSG_NKINDS */,
+                      int64_t *launches_host /* DDSG_NKINDS */, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDSG_H */

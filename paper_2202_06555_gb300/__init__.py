@@ -1,0 +1,274 @@
+"""Python binding of libddsg (argument marshalling over the C ABI in include/ddsg.h).
+
+Batched evaluation of a cut-HDMR adaptive sparse-grid (DDSG) interpolant on a
+GB300 GPU -- Eftekhari & Scheidegger, arXiv 2202.06555, Sec. 3-4. Every step
+of the computation runs inside libddsg's CUDA kernels; this module only moves
+pointers, sizes and streams across the ABI. PyTorch provides device memory
+and streams. There is no CPU fallback: importing works without a GPU (for
+the ABI export checks), but every compute call needs the built library and a
+CUDA device and raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+F64 = 0
+F32C = 1
+FORM_PAPER = 0
+FORM_SLICEFREE = 1
+KMAX = 8
+
+ERRORS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_STATE",
+          -5: "ERR_TABLE", -6: "ERR_TIMEOUT", -7: "ERR_NUMERIC"}
+
+# name -> (restype, argtypes); mirrors include/ddsg.h
+_p = C.c_void_p
+_i32 = C.c_int32
+_i64 = C.c_int64
+_int = C.c_int
+_d = C.c_double
+SIGNATURES = {
+    "ddsg_last_error": (C.c_char_p, []),
+    "ddsg_version": (C.c_char_p, []),
+    "hdmr_create": (_int, [_int, _int, _int, _p, _p, _p, C.POINTER(_p)]),
+    "hdmr_destroy": (_int, [_p]),
+    "hdmr_add_component": (_int, [_p, _int, _p, _i64, _p, _p, C.POINTER(_i32)]),
+    "hdmr_add_regular_component": (_int, [_p, _int, _p, _int, C.POINTER(_i32)]),
+    "hdmr_num_components": (_int, [_p, C.POINTER(_i32), C.POINTER(_i64)]),
+    "hdmr_component_info": (_int, [_p, _i32, C.POINTER(_i32), _p, C.POINTER(_i64), C.POINTER(_i64)]),
+    "hdmr_component_points": (_int, [_p, _i32, _i64, _i64, _p, _p, _p]),
+    "hdmr_hierarchize": (_int, [_p, _p, _p]),
+    "hdmr_refine": (_int, [_p, _d, _int, _int, C.POINTER(_i64), _p]),
+    "hdmr_get_surpluses": (_int, [_p, _p, _p]),
+    "hdmr_get_b": (_int, [_p, _p]),
+    "hdmr_eval": (_int, [_p, _i64, _p, _p, _int, _int, _p, _p, _p]),
+    "hdmr_reserve": (_int, [_p, _i64]),
+    "hdmr_stats": (_int, [_p, _p, _int, _p]),
+    "hdmr_eval_host": (_int, [_p, _i64, _p, _p, _int, _int, _p]),
+    "hdmr_profile": (_int, [_p, _int]),
+    "hdmr_profile_read": (_int, [_p, _p, _p, _int]),
+}
+
+KERNEL_KINDS = ["encode", "eval", "hierarchize", "convert", "copy", "k5", "k6", "k7"]
+
+_lib = None
+
+
+class DDSGError(RuntimeError):
+    pass
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libddsg.so (building it in-tree with nvcc if it is missing/stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise DDSGError(f"libddsg is not built ({_build.LIB}); run __graft_entry__.build()")
+    lib = C.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        msg = load().ddsg_last_error().decode()
+        raise DDSGError(f"{what} failed ({ERRORS.get(rc, rc)}): {msg}")
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise DDSGError("libddsg needs CUDA tensors (no CPU path)")
+    if not t.is_contiguous():
+        raise DDSGError("libddsg needs contiguous tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class HDMR:
+    """A cut-HDMR expansion with one sparse grid per accepted component.
+
+    Thin wrapper over the hdmr_* calls; see include/ddsg.h for semantics.
+    """
+
+    def __init__(self, d: int, m: int, order: int, anchor=None, lo=None, hi=None):
+        lib = load()
+        self.d, self.m, self.order = int(d), int(m), int(order)
+        self.lo = np.zeros(d) if lo is None else np.ascontiguousarray(lo, np.float64)
+        self.hi = np.ones(d) if hi is None else np.ascontiguousarray(hi, np.float64)
+        self.anchor = (0.5 * (self.lo + self.hi) if anchor is None
+                       else np.ascontiguousarray(anchor, np.float64))
+        h = C.c_void_p()
+        _check(lib.hdmr_create(self.d, self.m, self.order, _np_ptr(self.anchor), _np_ptr(self.lo),
+                               _np_ptr(self.hi), C.byref(h)), "hdmr_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hdmr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- construction ------------------------------------------------------
+    def add_component(self, dims, levels=None, indices=None) -> int:
+        dims = np.ascontiguousarray(dims, np.int32).reshape(-1)
+        k = dims.size
+        cid = C.c_int32()
+        if k == 0:
+            _check(load().hdmr_add_component(self._h, 0, None, 1, None, None, C.byref(cid)),
+                   "hdmr_add_component")
+            return cid.value
+        lv = np.ascontiguousarray(levels, np.uint8).reshape(-1, k)
+        ix = np.ascontiguousarray(indices, np.uint32).reshape(-1, k)
+        _check(load().hdmr_add_component(self._h, k, _np_ptr(dims), lv.shape[0], _np_ptr(lv),
+                                         _np_ptr(ix), C.byref(cid)), "hdmr_add_component")
+        return cid.value
+
+    def add_regular(self, dims, level: int) -> int:
+        dims = np.ascontiguousarray(dims, np.int32).reshape(-1)
+        cid = C.c_int32()
+        _check(load().hdmr_add_regular_component(self._h, dims.size, _np_ptr(dims), int(level),
+                                                 C.byref(cid)), "hdmr_add_regular_component")
+        return cid.value
+
+    def sizes(self):
+        nc, npt = C.c_int32(), C.c_int64()
+        _check(load().hdmr_num_components(self._h, C.byref(nc), C.byref(npt)), "hdmr_num_components")
+        return nc.value, npt.value
+
+    def component_info(self, comp: int):
+        k, npts, first = C.c_int32(), C.c_int64(), C.c_int64()
+        dims = np.zeros(KMAX, np.int32)
+        _check(load().hdmr_component_info(self._h, comp, C.byref(k), _np_ptr(dims), C.byref(npts),
+                                          C.byref(first)), "hdmr_component_info")
+        return tuple(int(x) for x in dims[:k.value]), npts.value, first.value
+
+    def component_points(self, comp: int, first: int = 0, count=None):
+        dims, npts, _ = self.component_info(comp)
+        k = len(dims)
+        if count is None:
+            count = npts - first
+        lv = np.zeros((count, max(k, 1)), np.uint8)
+        ix = np.zeros((count, max(k, 1)), np.uint32)
+        xs = np.zeros((count, max(k, 1)), np.float64)
+        _check(load().hdmr_component_points(self._h, comp, first, count, _np_ptr(lv), _np_ptr(ix),
+                                            _np_ptr(xs)), "hdmr_component_points")
+        return lv[:, :k], ix[:, :k], xs[:, :k]
+
+    def hierarchize(self, values_dev, stream=None):
+        _check(load().hdmr_hierarchize(self._h, _dev_ptr(values_dev), _stream_ptr(stream)),
+               "hdmr_hierarchize")
+
+    def refine(self, eps_gamma: float, max_level: int, strict: bool = False, stream=None) -> int:
+        n = C.c_int64()
+        _check(load().hdmr_refine(self._h, float(eps_gamma), int(max_level), int(bool(strict)),
+                                  C.byref(n), _stream_ptr(stream)), "hdmr_refine")
+        return n.value
+
+    def surpluses(self, stream=None) -> np.ndarray:
+        _, P = self.sizes()
+        out = np.zeros((P, self.m))
+        _check(load().hdmr_get_surpluses(self._h, _np_ptr(out), _stream_ptr(stream)),
+               "hdmr_get_surpluses")
+        return out
+
+    def b_coeffs(self) -> np.ndarray:
+        nc, _ = self.sizes()
+        out = np.zeros(nc)
+        _check(load().hdmr_get_b(self._h, _np_ptr(out)), "hdmr_get_b")
+        return out
+
+    # -- evaluation ----------------------------------------------------------
+    def reserve(self, n: int):
+        _check(load().hdmr_reserve(self._h, int(n)), "hdmr_reserve")
+
+    def eval(self, x_dev, y_dev, precision: int = F64, form: int = FORM_PAPER, hash_dev=None,
+             count_dev=None, stream=None):
+        n = x_dev.shape[0]
+        _check(load().hdmr_eval(self._h, n, _dev_ptr(x_dev), _dev_ptr(y_dev), int(precision),
+                                int(form), _dev_ptr(hash_dev), _dev_ptr(count_dev),
+                                _stream_ptr(stream)), "hdmr_eval")
+
+    def eval_host(self, x_host: np.ndarray, y_host: np.ndarray, precision: int = F64,
+                  form: int = FORM_PAPER, stream=None):
+        """End-to-end call with host arrays (copies inside the call)."""
+        assert x_host.dtype == np.float64 and y_host.dtype == np.float64
+        assert x_host.flags.c_contiguous and y_host.flags.c_contiguous
+        n = x_host.shape[0]
+        _check(load().hdmr_eval_host(self._h, n, C.c_void_p(x_host.ctypes.data),
+                                     C.c_void_p(y_host.ctypes.data), int(precision), int(form),
+                                     _stream_ptr(stream)), "hdmr_eval_host")
+
+    def profile(self, enable: bool = True):
+        _check(load().hdmr_profile(self._h, int(bool(enable))), "hdmr_profile")
+
+    def profile_read(self, reset: bool = True):
+        ms = np.zeros(8)
+        n = np.zeros(8, np.int64)
+        _check(load().hdmr_profile_read(self._h, _np_ptr(ms), _np_ptr(n), int(bool(reset))),
+               "hdmr_profile_read")
+        return {KERNEL_KINDS[i]: (float(ms[i]), int(n[i])) for i in range(8) if n[i]}
+
+    def stats(self, reset: bool = False, stream=None):
+        out = np.zeros(2, np.int64)
+        _check(load().hdmr_stats(self._h, _np_ptr(out), int(bool(reset)), _stream_ptr(stream)),
+               "hdmr_stats")
+        return {"clamped": int(out[0]), "nonfinite_rows": int(out[1])}
+
+
+def build_adaptive(h: HDMR, value_fn, eps_gamma: float, max_level: int, strict: bool = False,
+                   max_sweeps: int = 64, stream=None):
+    """Hierarchize / refine sweeps until no point is added (eq. 3.8).
+
+    value_fn(dims, phys_coords (n, k)) -> (n, m) values of the function at the
+    cut points (coordinates outside dims at the anchor). Only the values of new
+    points are requested; the library does all grid and surplus work.
+    """
+    import torch
+    ncomp, _ = h.sizes()
+    vals = [None] * ncomp
+    for _ in range(max_sweeps):
+        for c in range(ncomp):
+            dims, npts, _ = h.component_info(c)
+            have = 0 if vals[c] is None else vals[c].shape[0]
+            if have < npts:
+                _, _, xs = h.component_points(c, have, npts - have)
+                new = np.asarray(value_fn(dims, xs), np.float64).reshape(npts - have, h.m)
+                vals[c] = new if vals[c] is None else np.concatenate([vals[c], new])
+        allv = torch.from_numpy(np.ascontiguousarray(np.concatenate(vals))).cuda()
+        h.hierarchize(allv, stream)
+        if h.refine(eps_gamma, max_level, strict, stream) == 0:
+            break
+    return np.concatenate(vals)

@@ -1,0 +1,842 @@
+// ddsg_host.cu -- host runtime of libddsg: the hdmr_t handle, grid tables,
+// validation, eq. 4.2 coefficients, refinement (eq. 3.8), upload and launches.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <functional>
+#include <map>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "ddsg_internal.h"
+
+using namespace ddsg;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(DDSG_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_),   \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+extern "C" const char *ddsg_last_error(void) { return g_err.c_str(); }
+extern "C" const char *ddsg_version(void) { return "libddsg 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+
+struct Comp {
+    int k = 0;
+    int32_t dims[KMAX];
+    std::vector<uint8_t> lv;   // npts * k
+    std::vector<uint32_t> ix;  // npts * k
+    int64_t npts() const { return k == 0 ? (int64_t)lv.size() : (int64_t)lv.size() / k; }
+};
+
+struct hdmr {
+    int d = 0, m = 0, order = 0, device = 0;
+    std::vector<double> anchor, lo, hi, span;
+    bool anchor_central = false;
+    bool closed = false;      // accepted set downward closed (set at upload)
+    std::vector<Comp> comps;
+    std::vector<int64_t> first_point;  // per comp, offset in concatenated order
+    int64_t P = 0;
+    // device state
+    DevTables dt;
+    bool uploaded = false;    // dt matches comps
+    bool have_alpha = false;  // alpha64/alpha32 valid
+    std::vector<double> b;
+    double *dlo = nullptr, *dspan = nullptr;
+    int64_t *stats = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    void *hbuf = nullptr;      // device staging for hdmr_eval_host
+    size_t hbuf_bytes = 0;
+    // tracing
+    bool prof = false;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[DDSG_NKINDS] = {0};
+    int64_t prof_n[DDSG_NKINDS] = {0};
+};
+
+// Event bracket around one launch when tracing is on.
+struct ProfScope {
+    hdmr *h;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    static cudaEvent_t take(hdmr *h) {
+        if (!h->pool.empty()) {
+            cudaEvent_t e = h->pool.back();
+            h->pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    ProfScope(hdmr *h_, int kind_, cudaStream_t st_) : h(h_), kind(kind_), st(st_) {
+        if (!h->prof) return;
+        a = take(h);
+        b = take(h);
+        if (a) cudaEventRecord(a, st);
+    }
+    ~ProfScope() {
+        if (!h->prof || !a || !b) return;
+        cudaEventRecord(b, st);
+        h->recs.push_back({kind, a, b});
+    }
+};
+
+// Keeps the caller's current device, switches to the handle's for the call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static void free_tables(DevTables &t) {
+    cudaFree(t.comps);
+    cudaFree(t.tups);
+    cudaFree(t.slots);
+    cudaFree(t.alpha64);
+    cudaFree(t.alpha32);
+    cudaFree(t.layer_pts);
+    cudaFree(t.layer_off);
+    cudaFree(t.pt_lv);
+    cudaFree(t.pt_ix);
+    t = DevTables();
+}
+
+// First GPU use: bind the handle to the current device and allocate its
+// small per-handle buffers (domain map, counters).
+static int ensure_device(hdmr *h) {
+    if (h->device >= 0) return DDSG_OK;
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    const int d = h->d;
+    CUDA_TRY(cudaMalloc(&h->dlo, sizeof(double) * d));
+    CUDA_TRY(cudaMalloc(&h->dspan, sizeof(double) * d));
+    CUDA_TRY(cudaMalloc(&h->stats, sizeof(int64_t) * 2));
+    CUDA_TRY(cudaMemcpy(h->dlo, h->lo.data(), sizeof(double) * d, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(h->dspan, h->span.data(), sizeof(double) * d, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemset(h->stats, 0, sizeof(int64_t) * 2));
+    h->device = dev;
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_create(int d, int m, int order, const double *anchor, const double *lo,
+                           const double *hi, hdmr_t **out) {
+    if (!out) return fail(DDSG_ERR_ARG, "hdmr_create: out is NULL");
+    *out = nullptr;
+    if (d < 1 || m < 1 || order < 0 || order > KMAX)
+        return fail(DDSG_ERR_ARG, "hdmr_create: need d >= 1, m >= 1, 0 <= order <= %d", KMAX);
+    if (!anchor || !lo || !hi) return fail(DDSG_ERR_ARG, "hdmr_create: NULL anchor/lo/hi");
+    hdmr *h = new (std::nothrow) hdmr();
+    if (!h) return fail(DDSG_ERR_OOM, "hdmr_create: host allocation failed");
+    h->d = d;
+    h->m = m;
+    h->order = order;
+    h->anchor.assign(anchor, anchor + d);
+    h->lo.assign(lo, lo + d);
+    h->hi.assign(hi, hi + d);
+    h->span.resize(d);
+    h->anchor_central = true;
+    for (int i = 0; i < d; ++i) {
+        if (!(lo[i] < hi[i])) {
+            delete h;
+            return fail(DDSG_ERR_ARG, "hdmr_create: lo[%d] < hi[%d] required", i, i);
+        }
+        h->span[i] = hi[i] - lo[i];
+        if ((anchor[i] - lo[i]) / h->span[i] != 0.5) h->anchor_central = false;
+    }
+    h->device = -1;  // bound to the current device at first GPU use
+    *out = h;
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_destroy(hdmr_t *h) {
+    if (!h) return DDSG_OK;
+    if (h->device < 0) {
+        delete h;
+        return DDSG_OK;
+    }
+    DeviceGuard g(h->device);
+    free_tables(h->dt);
+    cudaFree(h->dlo);
+    cudaFree(h->dspan);
+    cudaFree(h->stats);
+    cudaFree(h->ws);
+    cudaFree(h->hbuf);
+    for (auto &r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : h->pool) cudaEventDestroy(e);
+    delete h;
+    return DDSG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// components
+// ---------------------------------------------------------------------------
+
+static bool valid_index(int l, uint32_t i) {
+    if (l == 1) return i == 1;
+    if (l == 2) return i == 0 || i == 2;
+    return (i & 1u) && i < (1u << (l - 1));
+}
+
+static uint32_t cell_of_index(int l, uint32_t i) {
+    return l == 1 ? 0u : (l == 2 ? i / 2 : (i - 1) / 2);
+}
+
+static int level_sum(const uint8_t *lv, int k) {
+    int s = 0;
+    for (int j = 0; j < k; ++j) s += lv[j] - 1;
+    return s;
+}
+
+static std::string point_key(const uint8_t *lv, const uint32_t *ix, int k) {
+    std::string s;
+    s.append(reinterpret_cast<const char *>(lv), k);
+    s.append(reinterpret_cast<const char *>(ix), sizeof(uint32_t) * k);
+    return s;
+}
+
+static void rebuild_offsets(hdmr *h) {
+    h->first_point.resize(h->comps.size());
+    int64_t off = 0;
+    for (size_t c = 0; c < h->comps.size(); ++c) {
+        h->first_point[c] = off;
+        off += h->comps[c].npts();
+    }
+    h->P = off;
+}
+
+extern "C" int hdmr_add_component(hdmr_t *h, int k, const int32_t *dims, int64_t npts,
+                                  const uint8_t *levels, const uint32_t *indices,
+                                  int32_t *comp_id) {
+    if (!h) return fail(DDSG_ERR_ARG, "hdmr_add_component: NULL handle");
+    if (k < 0 || k > h->order) return fail(DDSG_ERR_ARG, "hdmr_add_component: k=%d outside [0, order=%d]", k, h->order);
+    if (npts < 1) return fail(DDSG_ERR_ARG, "hdmr_add_component: npts must be >= 1");
+    if (k == 0 && npts != 1) return fail(DDSG_ERR_ARG, "hdmr_add_component: the empty component has exactly 1 point");
+    if (k > 0 && (!dims || !levels || !indices)) return fail(DDSG_ERR_ARG, "hdmr_add_component: NULL table");
+    if (npts > (int64_t)1 << 30) return fail(DDSG_ERR_ARG, "hdmr_add_component: too many points");
+    Comp c;
+    c.k = k;
+    for (int j = 0; j < KMAX; ++j) c.dims[j] = -1;
+    for (int j = 0; j < k; ++j) {
+        if (dims[j] < 0 || dims[j] >= h->d) return fail(DDSG_ERR_ARG, "hdmr_add_component: dim %d out of range", dims[j]);
+        if (j > 0 && dims[j] <= dims[j - 1]) return fail(DDSG_ERR_ARG, "hdmr_add_component: dims must be strictly ascending");
+        c.dims[j] = dims[j];
+    }
+    for (const Comp &o : h->comps) {
+        if (o.k == k && std::equal(o.dims, o.dims + k, c.dims))
+            return fail(DDSG_ERR_ARG, "hdmr_add_component: component already present");
+    }
+    if (k == 0) {
+        c.lv.assign(1, 0);  // one point, zero dims (size 1 marker)
+        c.ix.assign(1, 0);
+    } else {
+        c.lv.assign(levels, levels + npts * k);
+        c.ix.assign(indices, indices + npts * k);
+        std::unordered_map<std::string, int64_t> seen;
+        seen.reserve((size_t)npts * 2);
+        for (int64_t p = 0; p < npts; ++p) {
+            for (int j = 0; j < k; ++j) {
+                int l = c.lv[p * k + j];
+                if (l < 1 || l > LMAX) return fail(DDSG_ERR_TABLE, "hdmr_add_component: point %lld dim %d level %d outside [1,%d]", (long long)p, j, l, LMAX);
+                if (!valid_index(l, c.ix[p * k + j])) return fail(DDSG_ERR_TABLE, "hdmr_add_component: point %lld dim %d index %u invalid for level %d", (long long)p, j, c.ix[p * k + j], l);
+            }
+            if (!seen.emplace(point_key(&c.lv[p * k], &c.ix[p * k], k), p).second)
+                return fail(DDSG_ERR_TABLE, "hdmr_add_component: duplicate point %lld", (long long)p);
+        }
+    }
+    h->comps.push_back(std::move(c));
+    rebuild_offsets(h);
+    h->uploaded = false;
+    h->have_alpha = false;
+    if (comp_id) *comp_id = (int32_t)h->comps.size() - 1;
+    return DDSG_OK;
+}
+
+// Regular grid of eq. 3.5: all level tuples with sum(l-1) <= L-1, canonical order.
+static void gen_compositions(int k, int s, std::vector<std::vector<int>> &out) {
+    // compositions of s into k non-negative parts, lexicographic
+    std::vector<int> e(k, 0);
+    std::function<void(int, int)> rec;
+    rec = [&](int j, int rest) {
+        if (j == k - 1) {
+            e[j] = rest;
+            out.push_back(e);
+            return;
+        }
+        for (int v = 0; v <= rest; ++v) {
+            e[j] = v;
+            rec(j + 1, rest - v);
+        }
+    };
+    if (k == 0) {
+        if (s == 0) out.push_back(e);
+        return;
+    }
+    rec(0, s);
+}
+
+extern "C" int hdmr_add_regular_component(hdmr_t *h, int k, const int32_t *dims, int level,
+                                          int32_t *comp_id) {
+    if (!h) return fail(DDSG_ERR_ARG, "hdmr_add_regular_component: NULL handle");
+    if (level < 1 || level > LMAX) return fail(DDSG_ERR_ARG, "hdmr_add_regular_component: level out of range");
+    if (k == 0) return hdmr_add_component(h, 0, dims, 1, nullptr, nullptr, comp_id);
+    std::vector<uint8_t> lv;
+    std::vector<uint32_t> ix;
+    for (int s = 0; s <= level - 1; ++s) {
+        std::vector<std::vector<int>> comps;
+        gen_compositions(k, s, comps);
+        for (auto &e : comps) {
+            std::vector<uint32_t> n(k);
+            uint64_t tot = 1;
+            for (int j = 0; j < k; ++j) {
+                n[j] = ncells(e[j] + 1);
+                tot *= n[j];
+            }
+            if (tot > (1ull << 28) || lv.size() / k + tot > (1ull << 30))
+                return fail(DDSG_ERR_ARG, "hdmr_add_regular_component: grid too large");
+            std::vector<uint32_t> r(k, 0);
+            for (uint64_t t = 0; t < tot; ++t) {
+                for (int j = 0; j < k; ++j) {
+                    lv.push_back((uint8_t)(e[j] + 1));
+                    ix.push_back(index_of_cell(e[j] + 1, r[j]));
+                }
+                for (int j = k - 1; j >= 0; --j) {  // last dim fastest
+                    if (++r[j] < n[j]) break;
+                    r[j] = 0;
+                }
+            }
+        }
+    }
+    return hdmr_add_component(h, k, dims, (int64_t)(lv.size() / k), lv.data(), ix.data(), comp_id);
+}
+
+extern "C" int hdmr_num_components(const hdmr_t *h, int32_t *ncomp, int64_t *npts) {
+    if (!h) return fail(DDSG_ERR_ARG, "hdmr_num_components: NULL handle");
+    if (ncomp) *ncomp = (int32_t)h->comps.size();
+    if (npts) *npts = h->P;
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_component_info(const hdmr_t *h, int32_t comp, int32_t *k, int32_t *dims,
+                                   int64_t *npts, int64_t *first_point) {
+    if (!h || comp < 0 || comp >= (int32_t)h->comps.size())
+        return fail(DDSG_ERR_ARG, "hdmr_component_info: bad handle or component");
+    const Comp &c = h->comps[comp];
+    if (k) *k = c.k;
+    if (dims) for (int j = 0; j < KMAX; ++j) dims[j] = c.dims[j];
+    if (npts) *npts = c.npts();
+    if (first_point) *first_point = h->first_point[comp];
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_component_points(const hdmr_t *h, int32_t comp, int64_t first, int64_t count,
+                                     uint8_t *levels, uint32_t *indices, double *coords) {
+    if (!h || comp < 0 || comp >= (int32_t)h->comps.size())
+        return fail(DDSG_ERR_ARG, "hdmr_component_points: bad handle or component");
+    const Comp &c = h->comps[comp];
+    if (first < 0 || count < 0 || first + count > c.npts())
+        return fail(DDSG_ERR_ARG, "hdmr_component_points: range outside the component");
+    const int k = c.k;
+    for (int64_t p = first; p < first + count; ++p) {
+        for (int j = 0; j < k; ++j) {
+            const int l = c.lv[p * k + j];
+            const uint32_t i = c.ix[p * k + j];
+            const int64_t o = (p - first) * k + j;
+            if (levels) levels[o] = (uint8_t)l;
+            if (indices) indices[o] = i;
+            if (coords) {
+                const double xc = (l == 1) ? 0.5 : ldexp((double)i, -(l - 1));
+                const int dm = c.dims[j];
+                coords[o] = h->lo[dm] + xc * h->span[dm];
+            }
+        }
+    }
+    return DDSG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// table upload: closure check, eq. 4.2 coefficients, tuple directories, layers
+// ---------------------------------------------------------------------------
+
+static std::vector<int32_t> dims_vec(const Comp &c) { return std::vector<int32_t>(c.dims, c.dims + c.k); }
+
+// eq. 4.2 over the accepted set as given: b_v = sum_{u in U, u >= v} (-1)^(|u|-|v|).
+// Also records whether U is downward closed (every subset of an accepted
+// component accepted), which the slice-free form needs.
+static int compute_b_and_check(hdmr *h) {
+    std::map<std::vector<int32_t>, int> index;
+    for (size_t c = 0; c < h->comps.size(); ++c) index[dims_vec(h->comps[c])] = (int)c;
+    h->b.assign(h->comps.size(), 0.0);
+    h->closed = true;
+    for (size_t u = 0; u < h->comps.size(); ++u) {
+        const Comp &cu = h->comps[u];
+        for (uint32_t mask = 0; mask < (1u << cu.k); ++mask) {
+            std::vector<int32_t> v;
+            for (int j = 0; j < cu.k; ++j)
+                if (mask & (1u << j)) v.push_back(cu.dims[j]);
+            auto it = index.find(v);
+            if (it == index.end()) {
+                h->closed = false;
+                continue;
+            }
+            h->b[it->second] += ((cu.k - (int)v.size()) & 1) ? -1.0 : 1.0;
+        }
+    }
+    return DDSG_OK;
+}
+
+template <typename T>
+static int dev_upload(T **dst, const std::vector<T> &src) {
+    *dst = nullptr;
+    if (src.empty()) return DDSG_OK;
+    CUDA_TRY(cudaMalloc(dst, sizeof(T) * src.size()));
+    CUDA_TRY(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+    return DDSG_OK;
+}
+
+static int upload_tables(hdmr *h) {
+    if (h->comps.empty()) return fail(DDSG_ERR_STATE, "no components");
+    int rc = compute_b_and_check(h);
+    if (rc) return rc;
+    const int C = (int)h->comps.size();
+    const int64_t P = h->P;
+    if (P >= ((int64_t)1 << 31)) return fail(DDSG_ERR_TABLE, "too many points for 32-bit ids");
+    std::vector<DevComp> dc(C);
+    std::vector<DevTup> tups;
+    std::vector<int32_t> slots;
+    std::vector<int32_t> layer_pts;
+    std::vector<int32_t> layer_off;
+    std::vector<uint8_t> pt_lv((size_t)KMAX * P, 0);
+    std::vector<uint32_t> pt_ix((size_t)KMAX * P, 0);
+    for (int c = 0; c < C; ++c) {
+        const Comp &cp = h->comps[c];
+        const int k = cp.k;
+        const int64_t np = cp.npts();
+        const int64_t base = h->first_point[c];
+        DevComp &d = dc[c];
+        memset(&d, 0, sizeof d);
+        d.k = k;
+        for (int j = 0; j < KMAX; ++j) d.dims[j] = cp.dims[j];
+        d.pt_begin = (int32_t)base;
+        d.pt_end = (int32_t)(base + np);
+        d.b = h->b[c];
+        // group points by level tuple
+        std::map<std::vector<uint8_t>, std::vector<int64_t>> bytup;
+        for (int64_t p = 0; p < np; ++p) {
+            std::vector<uint8_t> key(k);
+            for (int j = 0; j < k; ++j) {
+                key[j] = cp.lv[p * k + j];
+                pt_lv[(size_t)j * P + base + p] = cp.lv[p * k + j];
+                pt_ix[(size_t)j * P + base + p] = cp.ix[p * k + j];
+            }
+            bytup[key].push_back(p);
+        }
+        // order: (interior, level sum, lexicographic)
+        std::vector<std::vector<uint8_t>> keys;
+        for (auto &kv : bytup) keys.push_back(kv.first);
+        auto interior = [](const std::vector<uint8_t> &t) {
+            for (uint8_t l : t) if (l < 2) return 0;
+            return 1;
+        };
+        std::stable_sort(keys.begin(), keys.end(), [&](const std::vector<uint8_t> &a, const std::vector<uint8_t> &b) {
+            int ia = interior(a), ib = interior(b);
+            if (ia != ib) return ia < ib;
+            int sa = level_sum(a.data(), k), sb = level_sum(b.data(), k);
+            if (sa != sb) return sa < sb;
+            return a < b;
+        });
+        d.tup_begin = (int32_t)tups.size();
+        d.tup_int = -1;
+        for (auto &key : keys) {
+            if (d.tup_int < 0 && interior(key)) d.tup_int = (int32_t)tups.size();
+            DevTup t;
+            memset(&t, 0, sizeof t);
+            uint64_t size = 1;
+            for (int j = 0; j < k; ++j) {
+                t.lev[j] = key[j];
+                size *= ncells(key[j]);
+            }
+            if (size > (1ull << 26)) return fail(DDSG_ERR_TABLE, "component %d: level tuple too fine for a dense cell directory", c);
+            t.lsum = level_sum(key.data(), k);
+            if (slots.size() + size > ((size_t)1 << 31)) return fail(DDSG_ERR_TABLE, "cell directories exceed 2^31 entries");
+            t.slot_base = (int32_t)slots.size();
+            slots.resize(slots.size() + size, -1);
+            for (int64_t p : bytup[key]) {
+                uint64_t off = 0;
+                for (int j = 0; j < k; ++j) off = off * ncells(key[j]) + cell_of_index(key[j], cp.ix[p * k + j]);
+                slots[t.slot_base + off] = (int32_t)(base + p);
+            }
+            tups.push_back(t);
+        }
+        d.tup_end = (int32_t)tups.size();
+        if (d.tup_int < 0) d.tup_int = d.tup_end;
+        // layers by level sum
+        std::vector<int64_t> order(np);
+        for (int64_t p = 0; p < np; ++p) order[p] = p;
+        std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b2) {
+            return level_sum(&cp.lv[a * k], k) < level_sum(&cp.lv[b2 * k], k);
+        });
+        d.layer_begin = (int32_t)layer_off.size();
+        int maxs = k == 0 ? 0 : level_sum(&cp.lv[order[np - 1] * k], k);
+        d.nlayers = maxs + 1;
+        const size_t lp0 = layer_pts.size();
+        size_t pos = 0;
+        for (int s = 0; s <= maxs; ++s) {
+            layer_off.push_back((int32_t)(lp0 + pos));
+            while (pos < (size_t)np && (k == 0 ? 0 : level_sum(&cp.lv[order[pos] * k], k)) == s) {
+                layer_pts.push_back((int32_t)(base + order[pos]));
+                ++pos;
+            }
+        }
+        layer_off.push_back((int32_t)(lp0 + pos));
+    }
+    free_tables(h->dt);
+    DevTables &t = h->dt;
+    t.C = C;
+    t.T = (int32_t)tups.size();
+    t.P = P;
+    t.S = (int64_t)slots.size();
+    t.m = h->m;
+    if ((rc = dev_upload(&t.comps, dc))) return rc;
+    if ((rc = dev_upload(&t.tups, tups))) return rc;
+    if ((rc = dev_upload(&t.slots, slots))) return rc;
+    if ((rc = dev_upload(&t.layer_pts, layer_pts))) return rc;
+    if ((rc = dev_upload(&t.layer_off, layer_off))) return rc;
+    if ((rc = dev_upload(&t.pt_lv, pt_lv))) return rc;
+    if ((rc = dev_upload(&t.pt_ix, pt_ix))) return rc;
+    CUDA_TRY(cudaMalloc(&t.alpha64, sizeof(double) * (size_t)P * h->m));
+    CUDA_TRY(cudaMalloc(&t.alpha32, sizeof(float) * (size_t)P * h->m));
+    h->uploaded = true;
+    h->have_alpha = false;
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_hierarchize(hdmr_t *h, const double *values_dev, ddsg_stream_t stream) {
+    if (!h || !values_dev) return fail(DDSG_ERR_ARG, "hdmr_hierarchize: NULL argument");
+    if (int rc0 = ensure_device(h)) return rc0;
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(DDSG_ERR_CUDA, "hdmr_hierarchize: cannot select device");
+    if (!h->uploaded) {
+        int rc = upload_tables(h);
+        if (rc) return rc;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    {
+        ProfScope ps(h, DDSG_K_HIER, st);
+        CUDA_TRY(launch_hierarchize(h->dt, h->m, values_dev, st));
+    }
+    {
+        ProfScope ps(h, DDSG_K_CONVERT, st);
+        CUDA_TRY(launch_to_f32(h->dt.alpha64, h->dt.alpha32, h->P * (int64_t)h->m, st));
+    }
+    h->have_alpha = true;
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_get_surpluses(const hdmr_t *h, double *alpha_host, ddsg_stream_t stream) {
+    if (!h || !alpha_host) return fail(DDSG_ERR_ARG, "hdmr_get_surpluses: NULL argument");
+    if (!h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_get_surpluses: not hierarchized");
+    DeviceGuard g(h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemcpyAsync(alpha_host, h->dt.alpha64, sizeof(double) * (size_t)h->P * h->m,
+                             cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_get_b(const hdmr_t *h, double *b_host) {
+    if (!h || !b_host) return fail(DDSG_ERR_ARG, "hdmr_get_b: NULL argument");
+    if (!h->uploaded) {
+        int rc = compute_b_and_check(const_cast<hdmr *>(h));
+        if (rc) return rc;
+    }
+    std::copy(h->b.begin(), h->b.end(), b_host);
+    return DDSG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// refinement (eq. 3.8)
+// ---------------------------------------------------------------------------
+
+static int children1d(int l, uint32_t i, uint32_t *ci) {
+    if (l == 1) { ci[0] = 0; ci[1] = 2; return 2; }
+    if (l == 2) { ci[0] = i == 0 ? 1u : 3u; return 1; }
+    ci[0] = 2 * i - 1;
+    ci[1] = 2 * i + 1;
+    return 2;
+}
+
+static void parent1d(int l, uint32_t i, int *pl, uint32_t *pi) {
+    if (l == 2) { *pl = 1; *pi = 1; return; }
+    if (l == 3) { *pl = 2; *pi = i == 1 ? 0u : 2u; return; }
+    *pl = l - 1;
+    const uint32_t a = (i - 1) / 2, b = (i + 1) / 2;
+    *pi = (a & 1u) ? a : b;
+}
+
+extern "C" int hdmr_refine(hdmr_t *h, double eps, int max_level, int strict, int64_t *n_new,
+                           ddsg_stream_t stream) {
+    if (!h) return fail(DDSG_ERR_ARG, "hdmr_refine: NULL handle");
+    if (max_level < 1 || max_level > LMAX) return fail(DDSG_ERR_ARG, "hdmr_refine: max_level out of range");
+    if (!h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_refine: surpluses not computed");
+    const int m = h->m;
+    std::vector<double> alpha((size_t)h->P * m);
+    int rc = hdmr_get_surpluses(h, alpha.data(), stream);
+    if (rc) return rc;
+    int64_t added = 0;
+    for (size_t c = 0; c < h->comps.size(); ++c) {
+        Comp &cp = h->comps[c];
+        const int k = cp.k;
+        if (k == 0) continue;
+        const int64_t np = cp.npts();
+        const double *al = alpha.data() + (size_t)h->first_point[c] * m;
+        std::unordered_map<std::string, int64_t> present;
+        present.reserve((size_t)np * 2);
+        for (int64_t p = 0; p < np; ++p) present.emplace(point_key(&cp.lv[p * k], &cp.ix[p * k], k), p);
+        auto significant = [&](int64_t p) {
+            double g = 0.0;
+            for (int j = 0; j < m; ++j) g = std::max(g, fabs(al[p * m + j]));
+            return g > eps;
+        };
+        struct Cand { uint8_t lv[KMAX]; uint32_t ix[KMAX]; };
+        std::vector<Cand> cand;
+        std::unordered_map<std::string, int> seen;
+        for (int64_t p = 0; p < np; ++p) {
+            if (!significant(p)) continue;
+            for (int j = 0; j < k; ++j) {
+                uint32_t ci[2];
+                const int nch = children1d(cp.lv[p * k + j], cp.ix[p * k + j], ci);
+                for (int q = 0; q < nch; ++q) {
+                    Cand o;
+                    memset(&o, 0, sizeof o);
+                    for (int r = 0; r < k; ++r) {
+                        o.lv[r] = cp.lv[p * k + r];
+                        o.ix[r] = cp.ix[p * k + r];
+                    }
+                    o.lv[j] = (uint8_t)(o.lv[j] + 1);
+                    o.ix[j] = ci[q];
+                    if (o.lv[j] > LMAX || level_sum(o.lv, k) > max_level - 1) continue;
+                    const std::string key = point_key(o.lv, o.ix, k);
+                    if (present.count(key) || seen.count(key)) continue;
+                    if (strict) {
+                        bool ok = true;
+                        for (int r = 0; r < k && ok; ++r) {
+                            if (o.lv[r] < 2) continue;
+                            Cand par = o;
+                            int pl;
+                            uint32_t pi;
+                            parent1d(o.lv[r], o.ix[r], &pl, &pi);
+                            par.lv[r] = (uint8_t)pl;
+                            par.ix[r] = pi;
+                            auto it = present.find(point_key(par.lv, par.ix, k));
+                            if (it != present.end() && !significant(it->second)) ok = false;
+                        }
+                        if (!ok) continue;
+                    }
+                    seen.emplace(key, 1);
+                    cand.push_back(o);
+                }
+            }
+        }
+        std::sort(cand.begin(), cand.end(), [k](const Cand &a, const Cand &b) {
+            const int sa = level_sum(a.lv, k), sb = level_sum(b.lv, k);
+            if (sa != sb) return sa < sb;
+            for (int j = 0; j < k; ++j) if (a.lv[j] != b.lv[j]) return a.lv[j] < b.lv[j];
+            for (int j = 0; j < k; ++j) if (a.ix[j] != b.ix[j]) return a.ix[j] < b.ix[j];
+            return false;
+        });
+        for (const Cand &o : cand) {
+            cp.lv.insert(cp.lv.end(), o.lv, o.lv + k);
+            cp.ix.insert(cp.ix.end(), o.ix, o.ix + k);
+        }
+        added += (int64_t)cand.size();
+    }
+    if (added) {
+        rebuild_offsets(h);
+        h->uploaded = false;
+        h->have_alpha = false;
+    }
+    if (n_new) *n_new = added;
+    return DDSG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// evaluation
+// ---------------------------------------------------------------------------
+
+static int ensure_ws(hdmr *h, int64_t n) {
+    const size_t need = (size_t)n * h->d * sizeof(uint64_t) + (size_t)n * sizeof(int32_t) + 256;
+    if (need <= h->ws_bytes) return DDSG_OK;
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    if (cudaMalloc(&h->ws, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DDSG_ERR_OOM, "hdmr_eval: workspace of %zu bytes unavailable", need);
+    }
+    h->ws_bytes = need;
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_reserve(hdmr_t *h, int64_t n) {
+    if (!h || n < 0) return fail(DDSG_ERR_ARG, "hdmr_reserve: bad argument");
+    if (int rc0 = ensure_device(h)) return rc0;
+    DeviceGuard g(h->device);
+    return ensure_ws(h, n);
+}
+
+extern "C" int hdmr_eval(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int precision,
+                         int form, uint64_t *hash_dev, int32_t *count_dev, ddsg_stream_t stream) {
+    if (!h) return fail(DDSG_ERR_ARG, "hdmr_eval: NULL handle");
+    if (n < 0) return fail(DDSG_ERR_ARG, "hdmr_eval: n < 0");
+    if (n == 0) return DDSG_OK;
+    if (!x_dev || !y_dev) return fail(DDSG_ERR_ARG, "hdmr_eval: NULL x or y");
+    if (precision != DDSG_F64 && precision != DDSG_F32C) return fail(DDSG_ERR_ARG, "hdmr_eval: unknown precision %d", precision);
+    if (form != DDSG_FORM_PAPER && form != DDSG_FORM_SLICEFREE) return fail(DDSG_ERR_ARG, "hdmr_eval: unknown form %d", form);
+    if (!h->uploaded || !h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_eval: call hdmr_hierarchize first");
+    if (form == DDSG_FORM_SLICEFREE && !h->anchor_central)
+        return fail(DDSG_ERR_ARG, "hdmr_eval: the slice-free form needs the anchor at the domain centre");
+    if (form == DDSG_FORM_SLICEFREE && !h->closed)
+        return fail(DDSG_ERR_ARG, "hdmr_eval: the slice-free form needs a downward-closed component set");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(DDSG_ERR_CUDA, "hdmr_eval: cannot select device");
+    int rc = ensure_ws(h, n);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint64_t *X = reinterpret_cast<uint64_t *>(h->ws);
+    {
+        ProfScope ps(h, DDSG_K_ENCODE, st);
+        CUDA_TRY(launch_encode_queries(n, h->d, x_dev, h->dlo, h->dspan, X, h->stats, st));
+    }
+    EvalArgs a;
+    a.t = &h->dt;
+    a.d = h->d;
+    a.m = h->m;
+    a.n = n;
+    a.X = X;
+    a.y = y_dev;
+    a.hash = hash_dev;
+    a.count = count_dev;
+    a.form = form;
+    a.precision = precision;
+    {
+        ProfScope ps(h, DDSG_K_EVAL, st);
+        CUDA_TRY(launch_eval(a, st));
+    }
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_eval_host(hdmr_t *h, int64_t n, const double *x_host, double *y_host,
+                              int precision, int form, ddsg_stream_t stream) {
+    if (!h) return fail(DDSG_ERR_ARG, "hdmr_eval_host: NULL handle");
+    if (n < 0) return fail(DDSG_ERR_ARG, "hdmr_eval_host: n < 0");
+    if (n == 0) return DDSG_OK;
+    if (!x_host || !y_host) return fail(DDSG_ERR_ARG, "hdmr_eval_host: NULL x or y");
+    if (!h->uploaded || !h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_eval_host: call hdmr_hierarchize first");
+    DeviceGuard g(h->device);
+    const size_t xb = sizeof(double) * (size_t)n * h->d, yb = sizeof(double) * (size_t)n * h->m;
+    if (xb + yb > h->hbuf_bytes) {
+        cudaFree(h->hbuf);
+        h->hbuf = nullptr;
+        h->hbuf_bytes = 0;
+        if (cudaMalloc(&h->hbuf, xb + yb) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DDSG_ERR_OOM, "hdmr_eval_host: staging buffer of %zu bytes unavailable", xb + yb);
+        }
+        h->hbuf_bytes = xb + yb;
+    }
+    double *xd = reinterpret_cast<double *>(h->hbuf);
+    double *yd = xd + (size_t)n * h->d;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    {
+        ProfScope ps(h, DDSG_K_COPY, st);
+        CUDA_TRY(cudaMemcpyAsync(xd, x_host, xb, cudaMemcpyHostToDevice, st));
+    }
+    int rc = hdmr_eval(h, n, xd, yd, precision, form, nullptr, nullptr, stream);
+    if (rc) return rc;
+    {
+        ProfScope ps(h, DDSG_K_COPY, st);
+        CUDA_TRY(cudaMemcpyAsync(y_host, yd, yb, cudaMemcpyDeviceToHost, st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_profile(hdmr_t *h, int enable) {
+    if (!h) return fail(DDSG_ERR_ARG, "hdmr_profile: NULL handle");
+    h->prof = enable != 0;
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_profile_read(hdmr_t *h, double *ms, int64_t *launches, int reset) {
+    if (!h) return fail(DDSG_ERR_ARG, "hdmr_profile_read: NULL handle");
+    if (h->device >= 0) {
+        DeviceGuard g(h->device);
+        for (auto &r : h->recs) {
+            CUDA_TRY(cudaEventSynchronize(r.b));
+            float t = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+            h->prof_ms[r.kind] += t;
+            h->prof_n[r.kind] += 1;
+            h->pool.push_back(r.a);
+            h->pool.push_back(r.b);
+        }
+        h->recs.clear();
+    }
+    for (int k = 0; k < DDSG_NKINDS; ++k) {
+        if (ms) ms[k] = h->prof_ms[k];
+        if (launches) launches[k] = h->prof_n[k];
+        if (reset) { h->prof_ms[k] = 0; h->prof_n[k] = 0; }
+    }
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_stats(hdmr_t *h, int64_t *stats_host, int reset, ddsg_stream_t stream) {
+    if (!h || !stats_host) return fail(DDSG_ERR_ARG, "hdmr_stats: NULL argument");
+    if (int rc0 = ensure_device(h)) return rc0;
+    DeviceGuard g(h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemcpyAsync(stats_host, h->stats, sizeof(int64_t) * 2, cudaMemcpyDeviceToHost, st));
+    if (reset) CUDA_TRY(cudaMemsetAsync(h->stats, 0, sizeof(int64_t) * 2, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return DDSG_OK;
+}

@@ -1,0 +1,160 @@
+// ddsg_internal.h -- private declarations shared by the libddsg translation units.
+//
+// Device data layout (all tables owned by the handle, uploaded by hdmr_hierarchize):
+//
+//   DevComp[C]        one per HDMR component u (eq. 4.2 index set):
+//                       k, dims, b_u, tuple range [tup_begin, tup_end),
+//                       first interior tuple (all levels >= 2) tup_int,
+//                       point range [pt_begin, pt_end) and layer table offset.
+//   DevTup[T]         one per non-empty level tuple of a component, ordered
+//                       (interior flag, level sum, lexicographic): levels and the
+//                       base offset of its dense cell directory in `slots`.
+//   slots[S] int32    dense directory of a tuple: for every cell of the level
+//                       tuple (product of per-dimension cell counts, last dim
+//                       fastest) the global point id, or -1 if absent. This turns
+//                       the support test of a query into O(1) arithmetic per tuple
+//                       (the per-level-tuple alternative to a tree walk).
+//   alpha64[P*m]      FP64 surpluses, point-major (m contiguous values per point).
+//   alpha32[P*m]      FP32 copy used by the compensated FP32 form.
+//   pt_lv/pt_ix       structure-of-arrays (level, index) tables, [KMAX][P].
+//   layer_pts[P]      point ids of each component sorted by level sum, and
+//   layer_off[...]    per component, the start of each level-sum layer in it
+//                       (used by the layer-by-layer hierarchization).
+//
+// Query encoding: each canonical coordinate c in [0,1] is held as the 64-bit
+// fixed-point integer X = floor(c * 2^62), with bit 0 forced to 1 when the
+// product is not an integer (a sticky bit, so X never lands on a dyadic cell
+// boundary unless c does). Cells, support tests and hash indices are then exact
+// integer arithmetic; basis values are exact integers scaled by a power of two.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ddsg.h"
+
+namespace ddsg {
+
+constexpr int KMAX = DDSG_KMAX;
+constexpr int LMAX = DDSG_LMAX;
+constexpr uint64_t X_ONE = 1ull << 62;          // fixed-point 1.0
+constexpr uint64_t X_NAN = 0xFFFFFFFFFFFFFFFFull; // marks a non-finite coordinate
+
+struct DevComp {
+    int32_t k;
+    int32_t dims[KMAX];
+    int32_t tup_begin, tup_int, tup_end;
+    int32_t pt_begin, pt_end;
+    int32_t layer_begin;  // index into layer_off; layers of this comp: layer_off[layer_begin .. +nlayers]
+    int32_t nlayers;
+    double b;
+};
+
+struct DevTup {
+    uint8_t lev[KMAX];
+    int32_t slot_base;
+    int32_t lsum;  // sum of (l_j - 1)
+};
+
+struct DevTables {
+    int32_t C = 0, T = 0;
+    int64_t P = 0, S = 0;
+    int32_t m = 0;
+    DevComp *comps = nullptr;
+    DevTup *tups = nullptr;
+    int32_t *slots = nullptr;
+    double *alpha64 = nullptr;
+    float *alpha32 = nullptr;
+    int32_t *layer_pts = nullptr;
+    int32_t *layer_off = nullptr;
+    uint8_t *pt_lv = nullptr;     // SoA levels:  pt_lv[j*P + p], j < KMAX
+    uint32_t *pt_ix = nullptr;    // SoA indices: pt_ix[j*P + p]
+};
+
+// ---------------------------------------------------------------------------
+// 1D basis on the fixed-point coordinate (boundary-augmented hats, Sec. 3.1)
+// ---------------------------------------------------------------------------
+
+__host__ __device__ inline uint32_t ncells(int l) {
+    return l <= 1 ? 1u : (l == 2 ? 2u : (1u << (l - 2)));
+}
+
+// Cell of level l containing X, its support test (phi > 0 exactly) and the
+// basis value numerator N with phi = N * 2^(-e). Returns active flag.
+struct Basis1D {
+    uint32_t cell;
+    uint64_t N;
+    int e;
+};
+
+__host__ __device__ inline bool basis1d(uint64_t X, int l, Basis1D &o) {
+    if (l == 1) {
+        o.cell = 0;
+        o.N = 1;
+        o.e = 0;
+        return true;
+    }
+    if (l == 2) {
+        // node 0 on [0, 1/2), node 1 on (1/2, 1]; phi = |2c - 1| = |X - 2^61| / 2^61
+        const uint64_t half = 1ull << 61;
+        o.cell = X >= half ? 1u : 0u;
+        o.N = X >= half ? X - half : half - X;
+        o.e = 61;
+        return o.N != 0;
+    }
+    const int sh = 64 - l;                // cell width 2^sh in X units
+    uint64_t cell = X >> sh;
+    const uint64_t nmax = (1ull << (l - 2)) - 1;
+    if (cell > nmax) cell = nmax;         // only at c = 1
+    const uint64_t F = X - (cell << sh);  // position inside the cell, [0, 2^sh]
+    const uint64_t half = 1ull << (sh - 1);
+    const uint64_t dist = F >= half ? F - half : half - F;
+    o.cell = (uint32_t)cell;
+    o.N = half - dist;
+    o.e = sh - 1;
+    return o.N != 0;
+}
+
+__host__ __device__ inline uint32_t index_of_cell(int l, uint32_t cell) {
+    return l == 1 ? 1u : (l == 2 ? 2u * cell : 2u * cell + 1u);
+}
+
+// fixed-point coordinate of node (l, i)
+__host__ __device__ inline uint64_t node_X(int l, uint32_t i) {
+    if (l == 1) return 1ull << 61;
+    return (uint64_t)i << (63 - l);   // i / 2^(l-1) * 2^62
+}
+
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------------------
+// kernel launchers (ddsg_kernels.cu)
+// ---------------------------------------------------------------------------
+
+cudaError_t launch_encode_queries(int64_t n, int d, const double *x, const double *lo,
+                                  const double *span, uint64_t *X, int64_t *stats,
+                                  cudaStream_t st);
+
+struct EvalArgs {
+    const DevTables *t;       // host copy of the table pointers
+    int d, m;
+    int64_t n;
+    const uint64_t *X;        // n*d encoded queries
+    double *y;                // n*m
+    uint64_t *hash;           // nullable
+    int32_t *count;           // nullable
+    int form;                 // DDSG_FORM_*
+    int precision;            // DDSG_F64 / DDSG_F32C
+};
+
+cudaError_t launch_eval(const EvalArgs &a, cudaStream_t st);
+
+cudaError_t launch_hierarchize(const DevTables &t, int m, const double *values,
+                               cudaStream_t st);
+
+cudaError_t launch_to_f32(const double *a, float *b, int64_t n, cudaStream_t st);
+
+}  // namespace ddsg

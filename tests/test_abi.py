@@ -1,0 +1,118 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+symbol include/ddsg.h declares, and its host-side logic (argument and table
+validation, regular grids of eq. 3.5, b coefficients of eq. 4.2) agrees with
+the oracle. No compute call is made."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2202_06555_gb300 as G
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for fname in os.listdir(os.path.join(ROOT, "include")):
+        if not fname.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fname)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for mt in re.finditer(r"^[A-Za-z_][\w \t\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, re.M):
+            if not mt.group(0).lstrip().startswith(("typedef", "#", "return")):
+                names.append(mt.group(1))
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = G.load()
+    names = _declared_functions()
+    assert "hdmr_eval" in names and "hdmr_hierarchize" in names and len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # the binding declares exactly what the header declares
+    assert set(names) <= set(G.SIGNATURES) | {"ddsg_version", "ddsg_last_error"}
+    assert lib.ddsg_version().startswith(b"libddsg")
+
+
+def test_create_validates_arguments():
+    lib = G.load()
+    h = C.c_void_p()
+    z = np.zeros(3)
+    o = np.ones(3)
+    assert lib.hdmr_create(0, 1, 1, G._np_ptr(z), G._np_ptr(z), G._np_ptr(o), C.byref(h)) == -1
+    assert lib.hdmr_create(3, 1, 9, G._np_ptr(z), G._np_ptr(z), G._np_ptr(o), C.byref(h)) == -1
+    assert lib.hdmr_create(3, 1, 1, G._np_ptr(z), G._np_ptr(o), G._np_ptr(z), C.byref(h)) == -1
+    assert b"lo" in lib.ddsg_last_error()
+    assert lib.hdmr_create(3, 1, 1, G._np_ptr(z), G._np_ptr(z), G._np_ptr(o), C.byref(h)) == 0
+    assert lib.hdmr_destroy(h) == 0
+
+
+def test_add_component_validation():
+    h = G.HDMR(3, 2, 2)
+    h.add_component([])
+    with pytest.raises(G.DDSGError, match="ERR_ARG"):
+        h.add_component([])                              # duplicate component
+    with pytest.raises(G.DDSGError, match="ERR_ARG"):
+        h.add_component([2, 1], [[1, 1]], [[1, 1]])      # dims not ascending
+    with pytest.raises(G.DDSGError, match="ERR_ARG"):
+        h.add_component([0, 1, 2], [[1, 1, 1]], [[1, 1, 1]])  # k > order
+    with pytest.raises(G.DDSGError, match="ERR_TABLE"):
+        h.add_component([0], [[3]], [[2]])               # even index at level 3
+    with pytest.raises(G.DDSGError, match="ERR_TABLE"):
+        h.add_component([0], [[2]], [[1]])               # level 2 takes index 0 or 2
+    with pytest.raises(G.DDSGError, match="ERR_TABLE"):
+        h.add_component([0], [[1], [1]], [[1], [1]])     # duplicate point
+    with pytest.raises(G.DDSGError, match="ERR_TABLE"):
+        h.add_component([0], [[0]], [[1]])               # level 0
+    assert h.add_component([0], [[1], [2], [2]], [[1], [0], [2]]) == 1
+    h.close()
+
+
+@pytest.mark.parametrize("k,level", [(0, 4), (1, 1), (1, 10), (2, 6), (3, 5), (4, 5)])
+def test_regular_grid_matches_oracle(k, level):
+    h = G.HDMR(max(k, 1), 1, max(k, 1))
+    cid = h.add_regular(list(range(k)), level)
+    dims, npts, first = h.component_info(cid)
+    lv, ix = O.regular_grid(k, level)
+    assert npts == lv.shape[0] and first == 0
+    if k:
+        glv, gix, xs = h.component_points(cid)
+        assert np.array_equal(glv, lv[:, :k]) and np.array_equal(gix, ix[:, :k])
+        ref = np.array([[O.node1d(l, i) for l, i in zip(a, b)] for a, b in zip(lv[:, :k], ix[:, :k])])
+        assert np.array_equal(xs, ref)
+    h.close()
+
+
+def test_component_points_physical_coordinates():
+    h = G.HDMR(2, 1, 1, lo=[0.8, -2.0], hi=[1.2, 2.0])
+    h.add_component([])
+    cid = h.add_regular([1], 3)
+    _, _, xs = h.component_points(cid)
+    assert np.array_equal(np.sort(xs[:, 0]), np.array([-2.0, -1.0, 0.0, 1.0, 2.0]))
+
+
+def test_b_coefficients_match_oracle():
+    d = 6
+    comps = O.full_order_components(d, 2)
+    comps = [u for u in comps if u not in [(0, 3), (2, 5)]]   # an eta-pruned set stays closed
+    h = G.HDMR(d, 1, 2)
+    E = O.OracleDDSG(d, 1)
+    for u in comps:
+        h.add_regular(list(u), 2)
+        E.add_regular(u, 2)
+    assert np.array_equal(h.b_coeffs(), E.b_coeffs())
+
+
+def test_b_coefficients_non_closed_set_match_oracle():
+    comps = [(), (0,), (0, 1), (0, 1, 2)]     # {1}, {2}, ... missing: eq. 4.2 over U as given
+    h = G.HDMR(3, 1, 3)
+    E = O.OracleDDSG(3, 1)
+    for u in comps:
+        h.add_regular(list(u), 2)
+        E.add_regular(u, 2)
+    assert np.array_equal(h.b_coeffs(), E.b_coeffs())

@@ -1,0 +1,209 @@
+"""GPU parity of libddsg against the CPU oracle, through the C ABI.
+
+Bars (written here, derived in the design doc):
+  index work (grid point sets, active-set counts and hashes): bit-exact;
+  FP64:  |y_gpu - y_oracle| <= 1e-12 * max(|y|, S), S = sum of |terms| (oracle);
+  F32C:  |y_gpu - y_oracle| <= 1e-6  * max(|y|, S);
+  surpluses: |alpha_gpu - alpha_oracle| <= 1e-13 * max|values| (cancellation in
+  value - coarser interpolant makes a relative bar on alpha meaningless).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-6}
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2202_06555_gb300 as G
+    G.load()
+    return G
+
+
+def build_pair(G, d, m, comps, fn, eps=None, level=None, regular_level=2, strict=False,
+               lo=None, hi=None, anchor=None):
+    ref = O.OracleDDSG(d, m, lo=lo, hi=hi, anchor=anchor)
+    h = G.HDMR(d, m, max(len(u) for u in comps), anchor=anchor, lo=lo, hi=hi)
+    for u in comps:
+        ref.add_regular(u, regular_level)
+        h.add_regular(list(u), regular_level)
+    if eps is None:
+        ref.fill_values(fn)
+        ref.hierarchize()
+        vals = np.concatenate(ref.values)
+        h.hierarchize(torch.from_numpy(vals).cuda())
+    else:
+        ref.build_adaptive(fn, eps, level, strict)
+        G.build_adaptive(h, fn, eps, level, strict)
+    return ref, h
+
+
+def eval_gpu(h, X, prec, form, m):
+    n = X.shape[0]
+    xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    y = torch.full((n, m), -7.0, dtype=torch.float64, device="cuda")
+    hs = torch.zeros(n, dtype=torch.int64, device="cuda")
+    ct = torch.zeros(n, dtype=torch.int32, device="cuda")
+    h.eval(xd, y, prec, form, hs, ct)
+    torch.cuda.synchronize()
+    return y.cpu().numpy(), hs.cpu().numpy().view(np.uint64), ct.cpu().numpy()
+
+
+def check_eval(h, ref, X, forms=(0, 1), precs=(0, 1)):
+    worst = {}
+    for form in forms:
+        r = ref.eval(X, form=form, want=("y", "S", "hash", "count"))
+        scale = np.maximum(np.abs(r["y"]), r["S"])
+        for prec in precs:
+            y, hs, ct = eval_gpu(h, X, prec, form, ref.m)
+            assert np.array_equal(ct, r["count"]), (form, prec)
+            assert np.array_equal(hs, r["hash"]), (form, prec)
+            fin = np.isfinite(r["y"]).all(1)
+            assert np.array_equal(np.isnan(y).any(1), ~fin)
+            rel = np.abs(y[fin] - r["y"][fin]) / np.where(scale[fin] > 0, scale[fin], 1.0)
+            assert rel.max(initial=0.0) <= TOL[prec], (form, prec, rel.max())
+            worst[(form, prec)] = float(rel.max(initial=0.0))
+    return worst
+
+
+def check_grids(h, ref):
+    nc, P = h.sizes()
+    assert nc == len(ref.comps)
+    for c in range(nc):
+        dims, npts, first = h.component_info(c)
+        assert dims == ref.comps[c] and npts == ref.npts(c)
+        k = len(dims)
+        if k:
+            lv, ix, _ = h.component_points(c)
+            assert np.array_equal(lv, ref.lv[c][:, :k]) and np.array_equal(ix, ref.ix[c][:, :k]), c
+
+
+def check_surpluses(h, ref):
+    a = h.surpluses()
+    b = np.concatenate(ref.alpha)
+    v = np.concatenate(ref.values)
+    assert np.max(np.abs(a - b)) <= 1e-13 * max(1.0, np.max(np.abs(v)))
+
+
+# ---------------------------------------------------------------------------
+
+def test_regular_4d_single_grid(G):
+    """d=4 level-5 regular sparse grid (401 points), m=3 kinked family."""
+    d, m = 4, 3
+    c = synth.family_coeffs(synth.BASE_SEED + synth.W_SG4, m, d)
+    fn = lambda dims, X: synth.family_cut(c, dims, X)
+    ref, h = build_pair(G, d, m, [(0, 1, 2, 3)], fn, regular_level=5)
+    assert h.sizes()[1] == 401
+    check_surpluses(h, ref)
+    X = synth.uniform_queries(synth.BASE_SEED + synth.W_SG4, 3000, d)
+    check_eval(h, ref, X, forms=(0,))
+    _, _, ct = eval_gpu(h, X, 0, 0, m)
+    assert np.all(ct == 70)
+    with pytest.raises(G.DDSGError, match="downward-closed"):
+        eval_gpu(h, X, 0, 1, m)
+
+
+def test_full_expansion_regular_d3(G):
+    d, m = 3, 2
+    f = lambda X: np.stack([np.exp(-np.sum(X ** 2, 1)), np.prod(np.sin(3 * X + 1), 1)], 1)
+    def fn(dims, X):
+        P = np.full((X.shape[0], d), 0.5)
+        P[:, list(dims)] = X
+        return f(P)
+    ref, h = build_pair(G, d, m, O.full_order_components(d, 3), fn, regular_level=5)
+    assert np.array_equal(h.b_coeffs(), ref.b_coeffs())
+    X = synth.uniform_queries(31, 2000, d)
+    check_eval(h, ref, X)
+
+
+@pytest.mark.parametrize("strict", [False, True])
+def test_adaptive_d4_order2(G, strict):
+    d, m = 4, 3
+    c = synth.family_coeffs(synth.BASE_SEED + 99, m, d)
+    fn = lambda dims, X: synth.family_cut(c, dims, X)
+    ref, h = build_pair(G, d, m, O.full_order_components(d, 2), fn, eps=1e-3, level=6,
+                        strict=strict)
+    check_grids(h, ref)
+    check_surpluses(h, ref)
+    X = np.concatenate([synth.uniform_queries(32, 4000, d), ref.node_coords(5)[:, [0, 0, 0, 0]]])
+    check_eval(h, ref, X)
+
+
+def test_adaptive_d20_order2_monomial_queries(G):
+    """d=20 (N=10) order-2, eps 1e-3, level 10 on the kinked family with m=11;
+    queries shaped like the monomial-rule nodes, some leaving [0,1] (clamped)."""
+    d, m = 20, 11
+    c = synth.family_coeffs(synth.BASE_SEED + synth.W_D20, m, d)
+    fn = lambda dims, X: synth.family_cut(c, dims, X)
+    ref, h = build_pair(G, d, m, O.full_order_components(d, 2), fn, eps=1e-3, level=10)
+    check_grids(h, ref)
+    check_surpluses(h, ref)
+    X = synth.monomial_shaped_queries(synth.BASE_SEED + synth.W_D20, 60, 10, s=0.05)
+    assert (X < 0).any() or (X > 1).any()
+    h.stats(reset=True)
+    w = check_eval(h, ref, X)
+    st = h.stats()
+    assert st["clamped"] > 0 and st["nonfinite_rows"] == 0
+
+
+def test_edge_queries(G):
+    """Nodes, cell faces, domain corners, outside points, NaN/inf rows, n = 0, 1."""
+    d, m = 3, 2
+    c = synth.family_coeffs(7, m, d)
+    fn = lambda dims, X: synth.family_cut(c, dims, X)
+    ref, h = build_pair(G, d, m, O.full_order_components(d, 2), fn, eps=1e-4, level=8)
+    pts = [np.zeros(d), np.ones(d), np.full(d, 0.5), np.array([0.25, 0.75, 0.125]),
+           np.array([1 / 3, 2 / 3, 0.7]), np.array([-0.1, 1.3, 0.5]),
+           np.array([5e-324, 1 - 2 ** -53, 2 ** -60]), np.array([0.5 + 2 ** -40, 0.5 - 2 ** -40, 0.7]),
+           np.array([np.nan, 0.2, 0.3]), np.array([0.2, np.inf, 0.3]), np.array([0.2, 0.3, -np.inf])]
+    for l in range(2, 9):
+        pts.append(np.array([2.0 ** -(l - 1), 1 - 2.0 ** -(l - 1), 3 * 2.0 ** -(l - 1)]))
+    X = np.array(pts)
+    check_eval(h, ref, X)
+    check_eval(h, ref, X[:1])
+    h.stats(reset=True)
+    check_eval(h, ref, X, forms=(0,), precs=(0,))
+    assert h.stats()["nonfinite_rows"] == 3
+    y = torch.zeros((0, m), dtype=torch.float64, device="cuda")
+    h.eval(torch.zeros((0, d), dtype=torch.float64, device="cuda"), y)
+
+
+def test_physical_domain_and_anchor(G):
+    """IRBC-like box [0.8, 1.2]^4 with the anchor at its centre; a non-central
+    anchor is refused by the slice-free form but the paper form still holds."""
+    d, m = 4, 2
+    lo, hi = np.full(d, 0.8), np.full(d, 1.2)
+    f = lambda P: np.stack([np.log(P).sum(1), (P ** 0.36).prod(1)], 1)
+    def fn_at(anchor):
+        def fn(dims, X):
+            P = np.repeat(anchor[None, :], X.shape[0], 0)
+            P[:, list(dims)] = X
+            return f(P)
+        return fn
+    comps = O.full_order_components(d, 2)
+    ref, h = build_pair(G, d, m, comps, fn_at(np.full(d, 1.0)), eps=1e-5, level=7, lo=lo, hi=hi)
+    X = synth.uniform_matrix(41, 1500, d, 0.75, 1.25)
+    check_eval(h, ref, X)
+    anc = np.array([0.9, 1.0, 1.1, 1.0])
+    ref2, h2 = build_pair(G, d, m, comps, fn_at(anc), regular_level=4, lo=lo, hi=hi, anchor=anc)
+    check_eval(h2, ref2, X, forms=(0,))
+    with pytest.raises(G.DDSGError, match="slice-free"):
+        eval_gpu(h2, X, 0, 1, m)
+
+
+def test_eval_before_hierarchize_is_an_error(G):
+    h = G.HDMR(2, 1, 1)
+    h.add_component([])
+    h.add_regular([0], 3)
+    x = torch.zeros((4, 2), dtype=torch.float64, device="cuda")
+    y = torch.zeros((4, 1), dtype=torch.float64, device="cuda")
+    with pytest.raises(G.DDSGError, match="ERR_STATE"):
+        h.eval(x, y)
