@@ -282,6 +282,9 @@ def main():
     k_mean = 2.0 if w["order"] >= 2 else 1.0
     flops_per_launch = active_total * (2.0 * w["m"] + (k_mean - 1.0))
 
+    # batching schedule: autotune kernel / output chunk on a subset of the queries
+    nt = min(n, 131072)
+    tuned = h.autotune(x[:nt], y[:nt], prec, form)
     for _ in range(args.warmup):
         h.eval(x, y, prec, form)
     torch.cuda.synchronize()
@@ -365,6 +368,8 @@ def main():
                       "eps_gamma": w["eps"], "max_level": w["level"], "queries_per_gpu": n,
                       "precision": w["precision"], "form": w["form"],
                       "active_points_per_query": active_total / n,
+                      "schedule": {"kernel": ["tile", "per-tuple"][tuned[0]], "outputs_per_pass": tuned[1],
+                                   "autotune_subset": nt},
                       "l2": "inputs larger than L2 (x %.2f GB, surpluses %.2f GB); no flush"
                             % (n * w["d"] * 8 / 1e9, npts * w["m"] * (4 if prec == G.F32C else 8) / 1e9),
                       "build_s": t_build},

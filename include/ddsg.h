@@ -186,6 +186,21 @@ int hdmr_get_b(const hdmr_t *h, double *b_host);
 int hdmr_eval(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int precision, int form,
               uint64_t *hash_dev, int32_t *count_dev, ddsg_stream_t stream);
 
+/*
+ * Evaluation kernel choice (the batching schedule). kernel 0 = staged tile
+ * kernel (1D bases of a component staged once per dimension and level),
+ * kernel 1 = per-tuple kernel; mc = outputs per thread and pass (0 = the
+ * heuristic: smallest compiled chunk >= m). hdmr_autotune times every compiled
+ * pair on the caller's queries (x_dev, n; y_dev is scratch output) and keeps
+ * the fastest for (precision, form); *best_ms (nullable) gets its time.
+ * Autotuning runs the evaluation about 36 times: tune on a representative
+ * subset of the queries.
+ */
+int hdmr_set_eval_config(hdmr_t *h, int precision, int form, int kernel, int mc);
+int hdmr_get_eval_config(const hdmr_t *h, int precision, int form, int *kernel, int *mc);
+int hdmr_autotune(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int precision,
+                  int form, ddsg_stream_t stream, double *best_ms);
+
 /* Pre-size the eval workspace for up to n queries (no allocation in later evals). */
 int hdmr_reserve(hdmr_t *h, int64_t n);
 

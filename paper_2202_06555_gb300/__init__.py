@@ -51,6 +51,9 @@ SIGNATURES = {
     "hdmr_stats": (_int, [_p, _p, _int, _p]),
     "hdmr_eval_host": (_int, [_p, _i64, _p, _p, _int, _int, _p]),
     "hdmr_profile": (_int, [_p, _int]),
+    "hdmr_set_eval_config": (_int, [_p, _int, _int, _int, _int]),
+    "hdmr_get_eval_config": (_int, [_p, _int, _int, C.POINTER(_int), C.POINTER(_int)]),
+    "hdmr_autotune": (_int, [_p, _i64, _p, _p, _int, _int, _p, C.POINTER(_d)]),
     "hdmr_profile_read": (_int, [_p, _p, _p, _int]),
 }
 
@@ -230,6 +233,23 @@ class HDMR:
         _check(load().hdmr_eval_host(self._h, n, C.c_void_p(x_host.ctypes.data),
                                      C.c_void_p(y_host.ctypes.data), int(precision), int(form),
                                      _stream_ptr(stream)), "hdmr_eval_host")
+
+    def set_eval_config(self, precision: int, form: int, kernel: int, mc: int):
+        _check(load().hdmr_set_eval_config(self._h, precision, form, kernel, mc),
+               "hdmr_set_eval_config")
+
+    def eval_config(self, precision: int, form: int):
+        k, mc = C.c_int(), C.c_int()
+        _check(load().hdmr_get_eval_config(self._h, precision, form, C.byref(k), C.byref(mc)),
+               "hdmr_get_eval_config")
+        return k.value, mc.value
+
+    def autotune(self, x_dev, y_dev, precision: int = F64, form: int = FORM_PAPER, stream=None):
+        best = C.c_double()
+        _check(load().hdmr_autotune(self._h, x_dev.shape[0], _dev_ptr(x_dev), _dev_ptr(y_dev),
+                                    int(precision), int(form), _stream_ptr(stream), C.byref(best)),
+               "hdmr_autotune")
+        return self.eval_config(precision, form) + (best.value,)
 
     def profile(self, enable: bool = True):
         _check(load().hdmr_profile(self._h, int(bool(enable))), "hdmr_profile")

@@ -76,6 +76,8 @@ struct hdmr {
     size_t ws_bytes = 0;
     void *hbuf = nullptr;      // device staging for hdmr_eval_host
     size_t hbuf_bytes = 0;
+    // evaluation kernel choice per [precision][form] (autotuned or heuristic)
+    EvalConfig cfg[2][2];
     // tracing
     bool prof = false;
     struct Rec { int kind; cudaEvent_t a, b; };
@@ -447,6 +449,7 @@ static int upload_tables(hdmr *h) {
     std::vector<int32_t> layer_off;
     std::vector<uint8_t> pt_lv((size_t)KMAX * P, 0);
     std::vector<uint32_t> pt_ix((size_t)KMAX * P, 0);
+    bool all_tile = true;
     for (int c = 0; c < C; ++c) {
         const Comp &cp = h->comps[c];
         const int k = cp.k;
@@ -459,6 +462,9 @@ static int upload_tables(hdmr *h) {
         d.pt_begin = (int32_t)base;
         d.pt_end = (int32_t)(base + np);
         d.b = h->b[c];
+        for (int64_t p = 0; p < np; ++p)
+            for (int j = 0; j < k; ++j) d.lmax[j] = std::max<uint8_t>(d.lmax[j], cp.lv[p * k + j]);
+        if (k > 2 || d.lmax[0] > LT || d.lmax[1] > LT) all_tile = false;
         // group points by level tuple
         std::map<std::vector<uint8_t>, std::vector<int64_t>> bytup;
         for (int64_t p = 0; p < np; ++p) {
@@ -536,6 +542,9 @@ static int upload_tables(hdmr *h) {
     t.P = P;
     t.S = (int64_t)slots.size();
     t.m = h->m;
+    t.mp64 = (h->m + 1) & ~1;
+    t.mp32 = (h->m + 3) & ~3;
+    t.tile_ok = all_tile ? 1 : 0;
     if ((rc = dev_upload(&t.comps, dc))) return rc;
     if ((rc = dev_upload(&t.tups, tups))) return rc;
     if ((rc = dev_upload(&t.slots, slots))) return rc;
@@ -543,8 +552,10 @@ static int upload_tables(hdmr *h) {
     if ((rc = dev_upload(&t.layer_off, layer_off))) return rc;
     if ((rc = dev_upload(&t.pt_lv, pt_lv))) return rc;
     if ((rc = dev_upload(&t.pt_ix, pt_ix))) return rc;
-    CUDA_TRY(cudaMalloc(&t.alpha64, sizeof(double) * (size_t)P * h->m));
-    CUDA_TRY(cudaMalloc(&t.alpha32, sizeof(float) * (size_t)P * h->m));
+    CUDA_TRY(cudaMalloc(&t.alpha64, sizeof(double) * (size_t)P * t.mp64));
+    CUDA_TRY(cudaMalloc(&t.alpha32, sizeof(float) * (size_t)P * t.mp32));
+    CUDA_TRY(cudaMemset(t.alpha64, 0, sizeof(double) * (size_t)P * t.mp64));
+    CUDA_TRY(cudaMemset(t.alpha32, 0, sizeof(float) * (size_t)P * t.mp32));
     h->uploaded = true;
     h->have_alpha = false;
     return DDSG_OK;
@@ -566,7 +577,7 @@ extern "C" int hdmr_hierarchize(hdmr_t *h, const double *values_dev, ddsg_stream
     }
     {
         ProfScope ps(h, DDSG_K_CONVERT, st);
-        CUDA_TRY(launch_to_f32(h->dt.alpha64, h->dt.alpha32, h->P * (int64_t)h->m, st));
+        CUDA_TRY(launch_to_f32(h->dt.alpha64, h->dt.mp64, h->dt.alpha32, h->dt.mp32, h->P, h->m, st));
     }
     h->have_alpha = true;
     return DDSG_OK;
@@ -577,8 +588,9 @@ extern "C" int hdmr_get_surpluses(const hdmr_t *h, double *alpha_host, ddsg_stre
     if (!h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_get_surpluses: not hierarchized");
     DeviceGuard g(h->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    CUDA_TRY(cudaMemcpyAsync(alpha_host, h->dt.alpha64, sizeof(double) * (size_t)h->P * h->m,
-                             cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpy2DAsync(alpha_host, sizeof(double) * h->m, h->dt.alpha64,
+                               sizeof(double) * h->dt.mp64, sizeof(double) * h->m, (size_t)h->P,
+                               cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     return DDSG_OK;
 }
@@ -758,6 +770,7 @@ extern "C" int hdmr_eval(hdmr_t *h, int64_t n, const double *x_dev, double *y_de
     a.count = count_dev;
     a.form = form;
     a.precision = precision;
+    a.cfg = h->cfg[precision][form];
     {
         ProfScope ps(h, DDSG_K_EVAL, st);
         CUDA_TRY(launch_eval(a, st));
@@ -798,6 +811,76 @@ extern "C" int hdmr_eval_host(hdmr_t *h, int64_t n, const double *x_host, double
         CUDA_TRY(cudaMemcpyAsync(y_host, yd, yb, cudaMemcpyDeviceToHost, st));
     }
     CUDA_TRY(cudaStreamSynchronize(st));
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_set_eval_config(hdmr_t *h, int precision, int form, int kernel, int mc) {
+    if (!h) return fail(DDSG_ERR_ARG, "hdmr_set_eval_config: NULL handle");
+    if (precision < 0 || precision > 1 || form < 0 || form > 1 || kernel < 0 || kernel > 1)
+        return fail(DDSG_ERR_ARG, "hdmr_set_eval_config: bad precision/form/kernel");
+    int cand[16];
+    const int nc = eval_mc_candidates(precision, kernel, cand, 16);
+    bool ok = mc == 0;
+    for (int i = 0; i < nc; ++i) ok = ok || cand[i] == mc;
+    if (!ok) return fail(DDSG_ERR_ARG, "hdmr_set_eval_config: output chunk %d not compiled", mc);
+    h->cfg[precision][form].kernel = kernel;
+    h->cfg[precision][form].mc = mc;
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_get_eval_config(const hdmr_t *h, int precision, int form, int *kernel, int *mc) {
+    if (!h || precision < 0 || precision > 1 || form < 0 || form > 1)
+        return fail(DDSG_ERR_ARG, "hdmr_get_eval_config: bad argument");
+    if (kernel) *kernel = h->cfg[precision][form].kernel;
+    if (mc) *mc = h->cfg[precision][form].mc;
+    return DDSG_OK;
+}
+
+// Times every compiled (kernel, output chunk) pair on the caller's queries
+// and keeps the fastest for this precision and form.
+extern "C" int hdmr_autotune(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int precision,
+                             int form, ddsg_stream_t stream, double *best_ms) {
+    if (!h || n <= 0 || !x_dev || !y_dev) return fail(DDSG_ERR_ARG, "hdmr_autotune: bad argument");
+    if (precision < 0 || precision > 1 || form < 0 || form > 1) return fail(DDSG_ERR_ARG, "hdmr_autotune: bad precision/form");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const bool prof = h->prof;
+    h->prof = false;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    EvalConfig best;
+    double best_t = 1e300;
+    for (int kernel = 0; kernel < 2; ++kernel) {
+        int cand[16];
+        const int nc = eval_mc_candidates(precision, kernel, cand, 16);
+        for (int i = 0; i < nc; ++i) {
+            h->cfg[precision][form].kernel = kernel;
+            h->cfg[precision][form].mc = cand[i];
+            int rc = hdmr_eval(h, n, x_dev, y_dev, precision, form, nullptr, nullptr, stream);
+            if (rc) { h->prof = prof; return rc; }
+            double t = 0.0;
+            for (int rep = 0; rep < 2; ++rep) {
+                CUDA_TRY(cudaEventRecord(e0, st));
+                rc = hdmr_eval(h, n, x_dev, y_dev, precision, form, nullptr, nullptr, stream);
+                if (rc) { h->prof = prof; return rc; }
+                CUDA_TRY(cudaEventRecord(e1, st));
+                CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                t = rep == 0 ? ms : std::min(t, (double)ms);
+            }
+            if (t < best_t) {
+                best_t = t;
+                best.kernel = kernel;
+                best.mc = cand[i];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->cfg[precision][form] = best;
+    h->prof = prof;
+    if (best_ms) *best_ms = best_t;
     return DDSG_OK;
 }
 

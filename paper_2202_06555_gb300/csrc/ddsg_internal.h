@@ -14,14 +14,16 @@
 //                       fastest) the global point id, or -1 if absent. This turns
 //                       the support test of a query into O(1) arithmetic per tuple
 //                       (the per-level-tuple alternative to a tree walk).
-//   alpha64[P*m]      FP64 surpluses, point-major (m contiguous values per point).
-//   alpha32[P*m]      FP32 copy used by the compensated FP32 form.
+//   alpha64[P*mp64]   FP64 surpluses, point-major; rows padded with zeros to a
+//                       multiple of 16 bytes so they load as double2.
+//   alpha32[P*mp32]   FP32 copy used by the compensated FP32 form (float4 rows).
 //   pt_lv/pt_ix       structure-of-arrays (level, index) tables, [KMAX][P].
 //   layer_pts[P]      point ids of each component sorted by level sum, and
 //   layer_off[...]    per component, the start of each level-sum layer in it
 //                       (used by the layer-by-layer hierarchization).
 //
-// Query encoding: each canonical coordinate c in [0,1] is held as the 64-bit
+// Query encoding (stored dimension-major, X[j*n + q], so that one coordinate
+// of consecutive queries is contiguous): each canonical coordinate c in [0,1] is held as the 64-bit
 // fixed-point integer X = floor(c * 2^62), with bit 0 forced to 1 when the
 // product is not an integer (a sticky bit, so X never lands on a dyadic cell
 // boundary unless c does). Cells, support tests and hash indices are then exact
@@ -42,6 +44,7 @@ constexpr uint64_t X_NAN = 0xFFFFFFFFFFFFFFFFull; // marks a non-finite coordina
 struct DevComp {
     int32_t k;
     int32_t dims[KMAX];
+    uint8_t lmax[KMAX];   // highest level present per dimension
     int32_t tup_begin, tup_int, tup_end;
     int32_t pt_begin, pt_end;
     int32_t layer_begin;  // index into layer_off; layers of this comp: layer_off[layer_begin .. +nlayers]
@@ -59,6 +62,9 @@ struct DevTables {
     int32_t C = 0, T = 0;
     int64_t P = 0, S = 0;
     int32_t m = 0;
+    int32_t mp64 = 0;     // row stride of alpha64 (m rounded up to 2: 16-byte rows)
+    int32_t mp32 = 0;     // row stride of alpha32 (m rounded up to 4: 16-byte rows)
+    int32_t tile_ok = 0;  // every component fits the staged path (k <= 2, levels <= LT)
     DevComp *comps = nullptr;
     DevTup *tups = nullptr;
     int32_t *slots = nullptr;
@@ -138,23 +144,35 @@ cudaError_t launch_encode_queries(int64_t n, int d, const double *x, const doubl
                                   const double *span, uint64_t *X, int64_t *stats,
                                   cudaStream_t st);
 
+constexpr int LT = 15;        // levels (1..LT) the staged evaluation path keeps per dimension
+
+struct EvalConfig {
+    int kernel = 0;           // 0 = staged tile kernel, 1 = per-tuple kernel
+    int mc = 0;               // outputs per thread and pass (0 = heuristic)
+};
+
 struct EvalArgs {
     const DevTables *t;       // host copy of the table pointers
     int d, m;
     int64_t n;
-    const uint64_t *X;        // n*d encoded queries
+    const uint64_t *X;        // d*n encoded queries (dimension-major), then n int32 flags
     double *y;                // n*m
     uint64_t *hash;           // nullable
     int32_t *count;           // nullable
     int form;                 // DDSG_FORM_*
     int precision;            // DDSG_F64 / DDSG_F32C
+    EvalConfig cfg;
 };
+
+// candidate output-chunk sizes the kernels are compiled for
+int eval_mc_candidates(int precision, int kernel, int *out, int cap);
 
 cudaError_t launch_eval(const EvalArgs &a, cudaStream_t st);
 
 cudaError_t launch_hierarchize(const DevTables &t, int m, const double *values,
                                cudaStream_t st);
 
-cudaError_t launch_to_f32(const double *a, float *b, int64_t n, cudaStream_t st);
+cudaError_t launch_to_f32(const double *a, int mp64, float *b, int mp32, int64_t P, int m,
+                          cudaStream_t st);
 
 }  // namespace ddsg

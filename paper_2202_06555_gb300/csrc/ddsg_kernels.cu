@@ -1,10 +1,16 @@
 // ddsg_kernels.cu -- CUDA kernels of libddsg (sm_103a).
 //
-//   encode_queries   physical FP64 query -> clamped canonical fixed point (Sec. 2.2
-//                    canonical domain), one warp per query.
-//   eval_lq          DDSG interpolation (Sec. 4.1, eq. 4.2 / slice-free form):
-//                    one thread per query, a chunk of MC outputs per thread,
-//                    all components in one pass.
+//   encode_queries   physical FP64 queries -> clamped canonical fixed point,
+//                    transposed to dimension-major order through shared memory.
+//   eval_tile        DDSG interpolation (Sec. 4.1, eq. 4.2 and the slice-free
+//                    form): one thread per query, 128 queries per block, the
+//                    block sweeps the components in lockstep so each
+//                    component's tables stay hot in L1; per component the 1D
+//                    basis of each of its dimensions is staged once per level in
+//                    per-thread shared memory, then every non-empty level tuple
+//                    costs one directory lookup; surplus rows load as 16-byte
+//                    vectors into a chunk of MC output accumulators.
+//   eval_lq          the same with the 1D basis recomputed per tuple (any k).
 //   hierarchize      surpluses layer by layer (Sec. 3.1), one block per component.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -19,61 +25,100 @@ namespace ddsg {
 // helpers
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ double pow2m_d(int e) {  // 2^-e, 0 <= e < 1022
-    return __longlong_as_double((long long)(1023 - e) << 52);
-}
 __device__ __forceinline__ float pow2m_f(int e) {  // 2^-e, 0 <= e < 126
     return __int_as_float((127 - e) << 23);
 }
 
+// phi = N * 2^-e as a double, N < 2^63, built from the bits (truncated to 53
+// significant bits; the exact value is N * 2^-e).
+__device__ __forceinline__ double basis_to_f64(uint64_t N, int e) {
+    if (N == 0) return 0.0;
+    const int lz = __clzll((long long)N);
+    const uint64_t mant = (N << lz) >> 11;        // 53 bits, leading one at bit 52
+    const int64_t ex = (int64_t)(63 - lz) - e + 1023;
+    return __longlong_as_double((long long)(((uint64_t)ex << 52) | (mant & ((1ull << 52) - 1))));
+}
+
+// phi = N * 2^-e as a float with 32 significant bits kept before rounding.
+// For l >= 2, e = 63 - l (l >= 3) or 61 (l == 2): N >> (e - 31) < 2^32.
+__device__ __forceinline__ float basis_to_f32(uint64_t N, int e) {
+    if (e <= 31) return __uint2float_rn((uint32_t)N) * pow2m_f(e);
+    return __uint2float_rn((uint32_t)(N >> (e - 31))) * pow2m_f(31);
+}
+
+template <typename W>
+__device__ __forceinline__ W basis_val(const Basis1D &o);
+template <>
+__device__ __forceinline__ double basis_val<double>(const Basis1D &o) { return basis_to_f64(o.N, o.e); }
+template <>
+__device__ __forceinline__ float basis_val<float>(const Basis1D &o) { return basis_to_f32(o.N, o.e); }
+
+__device__ __forceinline__ uint64_t point_key(int c, int k, const uint8_t *lev, const uint32_t *cells) {
+    uint64_t z = (uint64_t)(uint32_t)c;
+    for (int j = 0; j < k; ++j)
+        z = mix64(z ^ ((uint64_t)lev[j] << 40) ^ (uint64_t)index_of_cell(lev[j], cells[j]));
+    return mix64(z + 0x9E3779B97F4A7C15ull);
+}
+
 // ---------------------------------------------------------------------------
-// query encoding
+// query encoding (transposing)
 // ---------------------------------------------------------------------------
 
-// One warp per query row: X[q*d + j] = fixed point of clamp((x - lo_j) / span_j).
-// flags (n int32, stored after X) = 1 when any coordinate is non-finite.
-// stats[0] += clamped coordinates, stats[1] += non-finite rows.
+// Block of 32x8 threads handles 32 queries; it loops over the d coordinates in
+// tiles of 32, reading rows (coalesced along j) and writing X[j*n + q]
+// (coalesced along q). flags[q] = 1 if any coordinate is non-finite.
 __global__ void __launch_bounds__(256) encode_queries_kernel(int64_t n, int d, const double *__restrict__ x,
                                                              const double *__restrict__ lo,
                                                              const double *__restrict__ span,
                                                              uint64_t *__restrict__ X,
                                                              int32_t *__restrict__ flags,
                                                              unsigned long long *__restrict__ stats) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long clamps = 0, nans = 0;
-    for (int64_t q = warp; q < n; q += nwarps) {
-        bool bad = false;
-        for (int j = lane; j < d; j += 32) {
-            const double xv = x[q * d + j];
-            double c = (xv - lo[j]) / span[j];
-            uint64_t Xv;
-            if (!(c == c) || c == __longlong_as_double(0x7ff0000000000000ll) ||
-                c == __longlong_as_double(0xfff0000000000000ll) || !(xv - xv == 0.0)) {
-                bad = true;
-                Xv = X_NAN;
-            } else {
-                if (c < 0.0) { c = 0.0; ++clamps; }
-                if (c > 1.0) { c = 1.0; ++clamps; }
-                const double yv = c * 4611686018427387904.0;  // c * 2^62, exact
-                Xv = (uint64_t)yv;                              // floor (yv >= 0)
-                if ((double)Xv != yv) Xv |= 1ull;               // sticky: strictly inside a cell
+    __shared__ uint64_t tile[32][33];
+    __shared__ int bad_q[32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of 32
+    unsigned long long clamps = 0;
+    for (int64_t q0 = (int64_t)blockIdx.x * 32; q0 < n; q0 += (int64_t)gridDim.x * 32) {
+        if (threadIdx.x < 32) bad_q[threadIdx.x] = 0;
+        __syncthreads();
+        for (int j0 = 0; j0 < d; j0 += 32) {
+            // load: row r = query q0 + r, column tx = coordinate j0 + tx
+            for (int r = ty; r < 32; r += 8) {
+                const int64_t q = q0 + r;
+                const int j = j0 + tx;
+                uint64_t Xv = 0;
+                if (q < n && j < d) {
+                    const double xv = x[q * d + j];
+                    double c = (xv - lo[j]) / span[j];
+                    if (!isfinite(xv) || !isfinite(c)) {
+                        Xv = X_NAN;
+                        bad_q[r] = 1;
+                    } else {
+                        if (c < 0.0) { c = 0.0; ++clamps; }
+                        if (c > 1.0) { c = 1.0; ++clamps; }
+                        const double yv = c * 4611686018427387904.0;  // c * 2^62, exact
+                        Xv = (uint64_t)yv;                              // floor (yv >= 0)
+                        if ((double)Xv != yv) Xv |= 1ull;               // sticky bit
+                    }
+                }
+                tile[r][tx] = Xv;
             }
-            X[q * d + j] = Xv;
+            __syncthreads();
+            // store: row = coordinate j0 + r, column tx = query q0 + tx
+            for (int r = ty; r < 32; r += 8) {
+                const int j = j0 + r;
+                const int64_t q = q0 + tx;
+                if (j < d && q < n) X[(int64_t)j * n + q] = tile[tx][r];
+            }
+            __syncthreads();
         }
-        const bool any_bad = __any_sync(0xffffffffu, bad);
-        if (lane == 0) {
-            flags[q] = any_bad ? 1 : 0;
-            if (any_bad) ++nans;
+        if (threadIdx.x < 32 && q0 + threadIdx.x < n) {
+            flags[q0 + threadIdx.x] = bad_q[threadIdx.x];
+            if (bad_q[threadIdx.x]) atomicAdd(&stats[1], 1ull);
         }
+        __syncthreads();
     }
-    // warp-level reduction of counters, one atomic per warp
     for (int o = 16; o > 0; o >>= 1) clamps += __shfl_down_sync(0xffffffffu, clamps, o);
-    if (lane == 0 && (clamps | nans)) {
-        atomicAdd(&stats[0], clamps);
-        atomicAdd(&stats[1], nans);
-    }
+    if ((threadIdx.x & 31) == 0 && clamps) atomicAdd(&stats[0], clamps);
 }
 
 cudaError_t launch_encode_queries(int64_t n, int d, const double *x, const double *lo,
@@ -81,15 +126,15 @@ cudaError_t launch_encode_queries(int64_t n, int d, const double *x, const doubl
                                   cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     int32_t *flags = reinterpret_cast<int32_t *>(X + n * (int64_t)d);
-    int64_t blocks = (n + 7) / 8;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    int64_t blocks = (n + 31) / 32;
+    if (blocks > 152 * 16) blocks = 152 * 16;
     encode_queries_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, d, x, lo, span, X, flags,
                                                            reinterpret_cast<unsigned long long *>(stats));
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// evaluation: lanes over queries
+// evaluation
 // ---------------------------------------------------------------------------
 
 struct EvalParams {
@@ -104,33 +149,127 @@ struct EvalParams {
     int form;
 };
 
-// Accumulators: FP64 plain sums, or FP32 with Kahan compensation per term.
 template <int PREC>
-struct Acc;
-
+struct Types;
 template <>
-struct Acc<DDSG_F64> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double w, double a) { s = fma(w, a, s); }
-    __device__ __forceinline__ double result() const { return s; }
+struct Types<DDSG_F64> {
+    using W = double;
+    using V = double2;
+    static constexpr int VW = 2;
+    static __device__ __forceinline__ const double *alpha(const DevTables &t) { return t.alpha64; }
+    static __device__ __forceinline__ int stride(const DevTables &t) { return t.mp64; }
+};
+template <>
+struct Types<DDSG_F32C> {
+    using W = float;
+    using V = float4;
+    static constexpr int VW = 4;
+    static __device__ __forceinline__ const float *alpha(const DevTables &t) { return t.alpha32; }
+    static __device__ __forceinline__ int stride(const DevTables &t) { return t.mp32; }
 };
 
-template <>
-struct Acc<DDSG_F32C> {
-    float s = 0.0f, c = 0.0f;
-    __device__ __forceinline__ void add(float w, float a) {
-        const float term = __fmul_rn(w, a);
-        const float yk = __fsub_rn(term, c);
-        const float tk = __fadd_rn(s, yk);
-        c = __fsub_rn(__fsub_rn(tk, s), yk);
-        s = tk;
+// acc[o] += w * alpha_row[m0 + o] for o < MC, reading 16-byte vectors; vectors
+// past the padded row (stride mp) are skipped (never read).
+template <int PREC, int MC>
+__device__ __forceinline__ void accumulate(typename Types<PREC>::W (&acc)[MC], typename Types<PREC>::W w,
+                                           const typename Types<PREC>::W *row, int m0, int mp) {
+    using T = Types<PREC>;
+    constexpr int VW = T::VW;
+    const typename T::V *v = reinterpret_cast<const typename T::V *>(row + m0);
+#pragma unroll
+    for (int g = 0; g < MC / VW; ++g) {
+        if (m0 + g * VW < mp) {
+            const typename T::V a = __ldg(v + g);
+            if constexpr (VW == 4) {
+                acc[4 * g + 0] = fmaf(w, a.x, acc[4 * g + 0]);
+                acc[4 * g + 1] = fmaf(w, a.y, acc[4 * g + 1]);
+                acc[4 * g + 2] = fmaf(w, a.z, acc[4 * g + 2]);
+                acc[4 * g + 3] = fmaf(w, a.w, acc[4 * g + 3]);
+            } else {
+                acc[2 * g + 0] = fma(w, a.x, acc[2 * g + 0]);
+                acc[2 * g + 1] = fma(w, a.y, acc[2 * g + 1]);
+            }
+        }
     }
-    __device__ __forceinline__ double result() const { return (double)s - (double)c; }
+}
+
+// Final per-thread result holder: FP64 accumulates directly; FP32 folds each
+// component's plain-FP32 partial sum into a Kahan-compensated total.
+template <int PREC, int MC>
+struct Result;
+template <int MC>
+struct Result<DDSG_F64, MC> {
+    double s[MC];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int o = 0; o < MC; ++o) s[o] = 0.0;
+    }
+    __device__ __forceinline__ double (&partial())[MC] { return s; }
+    __device__ __forceinline__ void fold() {}
+    __device__ __forceinline__ double value(int o) const { return s[o]; }
 };
+template <int MC>
+struct Result<DDSG_F32C, MC> {
+    float p[MC], s[MC], c[MC];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int o = 0; o < MC; ++o) p[o] = s[o] = c[o] = 0.0f;
+    }
+    __device__ __forceinline__ float (&partial())[MC] { return p; }
+    __device__ __forceinline__ void fold() {
+#pragma unroll
+        for (int o = 0; o < MC; ++o) {
+            const float yk = __fsub_rn(p[o], c[o]);
+            const float tk = __fadd_rn(s[o], yk);
+            c[o] = __fsub_rn(__fsub_rn(tk, s[o]), yk);
+            s[o] = tk;
+            p[o] = 0.0f;
+        }
+    }
+    __device__ __forceinline__ double value(int o) const { return (double)s[o] - (double)c[o]; }
+};
+
+// Per-tuple evaluation of one component (any k), basis recomputed per tuple.
+template <int PREC, int MC, bool HC>
+__device__ __forceinline__ void comp_generic(const EvalParams &p, const DevComp &cd, int c,
+                                             int64_t q, bool paper, int m0,
+                                             typename Types<PREC>::W (&acc)[MC], uint64_t &h,
+                                             int32_t &cnt) {
+    using W = typename Types<PREC>::W;
+    const int k = cd.k;
+    uint64_t Xd[KMAX];
+    for (int j = 0; j < k; ++j) Xd[j] = p.X[(int64_t)cd.dims[j] * p.n + q];
+    const int tb = paper ? cd.tup_begin : cd.tup_int;
+    const W *alpha = Types<PREC>::alpha(p.t);
+    const int mp = Types<PREC>::stride(p.t);
+    for (int ti = tb; ti < cd.tup_end; ++ti) {
+        const DevTup tu = p.t.tups[ti];
+        bool act = true;
+        uint32_t off = 0;
+        W w = (W)1;
+        uint32_t cells[KMAX];
+        for (int j = 0; j < k; ++j) {
+            Basis1D o;
+            const int l = tu.lev[j];
+            if (!basis1d(Xd[j], l, o)) { act = false; break; }
+            off = off * ncells(l) + o.cell;
+            cells[j] = o.cell;
+            w = w * basis_val<W>(o);
+        }
+        if (!act) continue;
+        const int32_t pid = p.t.slots[tu.slot_base + off];
+        if (pid < 0) continue;
+        if (paper) w = (W)cd.b * w;
+        accumulate<PREC, MC>(acc, w, alpha + (int64_t)pid * mp, m0, mp);
+        if (HC) {
+            h ^= point_key(c, k, tu.lev, cells);
+            ++cnt;
+        }
+    }
+}
 
 template <int PREC, int MC, bool HC>
 __global__ void __launch_bounds__(128) eval_lq_kernel(const EvalParams p) {
-    using W = typename std::conditional<PREC == DDSG_F64, double, float>::type;
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= p.n) return;
     const int m0 = blockIdx.y * MC;
@@ -144,85 +283,171 @@ __global__ void __launch_bounds__(128) eval_lq_kernel(const EvalParams p) {
         }
         return;
     }
-    const uint64_t *Xq = p.X + q * (int64_t)p.d;
-    Acc<PREC> acc[MC];
+    Result<PREC, MC> r;
+    r.init();
     uint64_t h = 0;
     int32_t cnt = 0;
     const bool paper = p.form == DDSG_FORM_PAPER;
-    const int C = p.t.C;
-    for (int c = 0; c < C; ++c) {
+    for (int c = 0; c < p.t.C; ++c) {
         const DevComp &cd = p.t.comps[c];
-        const double b = cd.b;
-        if (paper && b == 0.0) continue;
-        const int k = cd.k;
-        uint64_t Xd[KMAX];
-        for (int j = 0; j < k; ++j) Xd[j] = Xq[cd.dims[j]];
-        const int tb = paper ? cd.tup_begin : cd.tup_int;
-        const int te = cd.tup_end;
-        for (int ti = tb; ti < te; ++ti) {
-            const DevTup tu = p.t.tups[ti];
-            bool act = true;
-            uint32_t off = 0;
-            W w = (W)1;
-            uint32_t cells[KMAX];
-            for (int j = 0; j < k; ++j) {
-                Basis1D o;
-                const int l = tu.lev[j];
-                if (!basis1d(Xd[j], l, o)) { act = false; break; }
-                off = off * ncells(l) + o.cell;
-                cells[j] = o.cell;
-                if (PREC == DDSG_F64) w = w * ((W)__ull2double_rn(o.N) * pow2m_d(o.e));
-                else w = w * ((W)__ull2float_rn(o.N) * pow2m_f(o.e));
-            }
-            if (!act) continue;
-            const int32_t pid = p.t.slots[tu.slot_base + off];
-            if (pid < 0) continue;
-            if (paper) w = (W)b * w;
-            if (PREC == DDSG_F64) {
-                const double *a = p.t.alpha64 + (int64_t)pid * m + m0;
-#pragma unroll
-                for (int o = 0; o < MC; ++o)
-                    if (m0 + o < m) acc[o].add(w, __ldg(a + o));
-            } else {
-                const float *a = p.t.alpha32 + (int64_t)pid * m + m0;
-#pragma unroll
-                for (int o = 0; o < MC; ++o)
-                    if (m0 + o < m) acc[o].add(w, __ldg(a + o));
-            }
-            if (HC) {
-                uint64_t z = (uint64_t)(uint32_t)c;
-                for (int j = 0; j < k; ++j)
-                    z = mix64(z ^ ((uint64_t)tu.lev[j] << 40) ^ (uint64_t)index_of_cell(tu.lev[j], cells[j]));
-                h ^= mix64(z + 0x9E3779B97F4A7C15ull);
-                ++cnt;
-            }
-        }
+        if (paper && cd.b == 0.0) continue;
+        comp_generic<PREC, MC, HC>(p, cd, c, q, paper, m0, r.partial(), h, cnt);
+        r.fold();
     }
 #pragma unroll
     for (int o = 0; o < MC; ++o)
-        if (m0 + o < m) p.y[q * m + m0 + o] = acc[o].result();
+        if (m0 + o < m) p.y[q * m + m0 + o] = r.value(o);
     if (HC && blockIdx.y == 0) {
         if (p.hash) p.hash[q] = h;
         if (p.count) p.count[q] = cnt;
     }
 }
 
+constexpr int TQ = 128;  // queries per block of the tile kernel
+
+template <int PREC, int MC, bool HC>
+__global__ void __launch_bounds__(TQ) eval_tile_kernel(const EvalParams p) {
+    using W = typename Types<PREC>::W;
+    // staged 1D basis of the current component: [dim][level][thread]; bit 31 of
+    // the cell marks "phi == 0 at this level" (query on a cell face).
+    __shared__ uint32_t s_cell[2][LT][TQ];
+    __shared__ W s_t[2][LT][TQ];
+    const int tid = threadIdx.x;
+    const int64_t q = (int64_t)blockIdx.x * TQ + tid;
+    const int m0 = blockIdx.y * MC;
+    const int m = p.m;
+    const bool valid = q < p.n;
+    const bool bad = !valid || p.flags[q] != 0;
+    const bool paper = p.form == DDSG_FORM_PAPER;
+    const W *alpha = Types<PREC>::alpha(p.t);
+    const int mp = Types<PREC>::stride(p.t);
+    Result<PREC, MC> r;
+    r.init();
+    uint64_t h = 0;
+    int32_t cnt = 0;
+    if (!bad) {
+        for (int c = 0; c < p.t.C; ++c) {
+            const DevComp &cd = p.t.comps[c];
+            const double b = cd.b;
+            if (paper && b == 0.0) continue;
+            const int k = cd.k;
+            if (k > 2 || cd.lmax[0] > LT || cd.lmax[1] > LT) {
+                comp_generic<PREC, MC, HC>(p, cd, c, q, paper, m0, r.partial(), h, cnt);
+                r.fold();
+                continue;
+            }
+            // stage the 1D basis of each dimension, levels 1..lmax
+            for (int j = 0; j < k; ++j) {
+                const uint64_t Xv = p.X[(int64_t)cd.dims[j] * p.n + q];
+                const int lm = cd.lmax[j];
+                for (int l = 1; l <= lm; ++l) {
+                    Basis1D o;
+                    const bool act = basis1d(Xv, l, o);
+                    s_cell[j][l - 1][tid] = act ? o.cell : 0x80000000u;
+                    s_t[j][l - 1][tid] = basis_val<W>(o);
+                }
+            }
+            const int tb = paper ? cd.tup_begin : cd.tup_int;
+            const W wb = paper ? (W)b : (W)1;
+            for (int ti = tb; ti < cd.tup_end; ++ti) {
+                const DevTup tu = p.t.tups[ti];
+                uint32_t off;
+                W w;
+                uint32_t cells[2];
+                if (k == 0) {
+                    off = 0;
+                    w = wb;
+                } else if (k == 1) {
+                    const uint32_t ca = s_cell[0][tu.lev[0] - 1][tid];
+                    if (ca & 0x80000000u) continue;
+                    off = ca;
+                    cells[0] = ca;
+                    w = wb * s_t[0][tu.lev[0] - 1][tid];
+                } else {
+                    const uint32_t ca = s_cell[0][tu.lev[0] - 1][tid];
+                    const uint32_t cb = s_cell[1][tu.lev[1] - 1][tid];
+                    if ((ca | cb) & 0x80000000u) continue;
+                    off = ca * ncells(tu.lev[1]) + cb;
+                    cells[0] = ca;
+                    cells[1] = cb;
+                    w = wb * (s_t[0][tu.lev[0] - 1][tid] * s_t[1][tu.lev[1] - 1][tid]);
+                }
+                const int32_t pid = __ldg(p.t.slots + tu.slot_base + off);
+                if (pid < 0) continue;
+                accumulate<PREC, MC>(r.partial(), w, alpha + (int64_t)pid * mp, m0, mp);
+                if (HC) {
+                    h ^= point_key(c, k, tu.lev, cells);
+                    ++cnt;
+                }
+            }
+            r.fold();
+        }
+    }
+    if (!valid) return;
+#pragma unroll
+    for (int o = 0; o < MC; ++o)
+        if (m0 + o < m) p.y[q * m + m0 + o] = bad ? __longlong_as_double(0x7ff8000000000000ll) : r.value(o);
+    if (HC && blockIdx.y == 0) {
+        if (p.hash) p.hash[q] = bad ? 0 : h;
+        if (p.count) p.count[q] = bad ? 0 : cnt;
+    }
+}
+
 template <int PREC, int MC>
-static cudaError_t launch_eval_mc(const EvalParams &p, bool hc, cudaStream_t st) {
-    dim3 grid((unsigned)((p.n + 127) / 128), (unsigned)((p.m + MC - 1) / MC));
-    if (hc) eval_lq_kernel<PREC, MC, true><<<grid, 128, 0, st>>>(p);
-    else eval_lq_kernel<PREC, MC, false><<<grid, 128, 0, st>>>(p);
+static cudaError_t launch_mc(const EvalParams &p, int kernel, bool hc, cudaStream_t st) {
+    dim3 grid((unsigned)((p.n + TQ - 1) / TQ), (unsigned)((p.m + MC - 1) / MC));
+    if (kernel == 0) {
+        if (hc) eval_tile_kernel<PREC, MC, true><<<grid, TQ, 0, st>>>(p);
+        else eval_tile_kernel<PREC, MC, false><<<grid, TQ, 0, st>>>(p);
+    } else {
+        if (hc) eval_lq_kernel<PREC, MC, true><<<grid, TQ, 0, st>>>(p);
+        else eval_lq_kernel<PREC, MC, false><<<grid, TQ, 0, st>>>(p);
+    }
     return cudaGetLastError();
 }
 
+// compiled output-chunk sizes (multiples of the vector width)
+static const int MC_F64[] = {2, 4, 6, 8, 12, 16};
+static const int MC_F32[] = {4, 8, 12, 16, 28, 52};
+
+int eval_mc_candidates(int precision, int kernel, int *out, int cap) {
+    (void)kernel;
+    const int *src = precision == DDSG_F64 ? MC_F64 : MC_F32;
+    const int n = 6;
+    for (int i = 0; i < n && i < cap; ++i) out[i] = src[i];
+    return n < cap ? n : cap;
+}
+
 template <int PREC>
-static cudaError_t launch_eval_prec(const EvalParams &p, bool hc, cudaStream_t st) {
-    if (p.m <= 1) return launch_eval_mc<PREC, 1>(p, hc, st);
-    if (p.m <= 2) return launch_eval_mc<PREC, 2>(p, hc, st);
-    if (p.m <= 4) return launch_eval_mc<PREC, 4>(p, hc, st);
-    if (p.m <= 8) return launch_eval_mc<PREC, 8>(p, hc, st);
-    if (p.m <= 12) return launch_eval_mc<PREC, 12>(p, hc, st);
-    return launch_eval_mc<PREC, 16>(p, hc, st);
+static cudaError_t launch_prec(const EvalParams &p, int kernel, int mc, bool hc, cudaStream_t st) {
+    if (PREC == DDSG_F64) {
+        switch (mc) {
+            case 2: return launch_mc<PREC, 2>(p, kernel, hc, st);
+            case 4: return launch_mc<PREC, 4>(p, kernel, hc, st);
+            case 6: return launch_mc<PREC, 6>(p, kernel, hc, st);
+            case 8: return launch_mc<PREC, 8>(p, kernel, hc, st);
+            case 12: return launch_mc<PREC, 12>(p, kernel, hc, st);
+            default: return launch_mc<PREC, 16>(p, kernel, hc, st);
+        }
+    } else {
+        switch (mc) {
+            case 4: return launch_mc<PREC, 4>(p, kernel, hc, st);
+            case 8: return launch_mc<PREC, 8>(p, kernel, hc, st);
+            case 12: return launch_mc<PREC, 12>(p, kernel, hc, st);
+            case 16: return launch_mc<PREC, 16>(p, kernel, hc, st);
+            case 28: return launch_mc<PREC, 28>(p, kernel, hc, st);
+            default: return launch_mc<PREC, 52>(p, kernel, hc, st);
+        }
+    }
+}
+
+// Heuristic chunk: the smallest compiled size covering m, else the largest.
+static int default_mc(int precision, int m) {
+    int c[8];
+    const int n = eval_mc_candidates(precision, 0, c, 8);
+    for (int i = 0; i < n; ++i)
+        if (c[i] >= m) return c[i];
+    return precision == DDSG_F64 ? 16 : 28;
 }
 
 cudaError_t launch_eval(const EvalArgs &a, cudaStream_t st) {
@@ -239,8 +464,9 @@ cudaError_t launch_eval(const EvalArgs &a, cudaStream_t st) {
     p.count = a.count;
     p.form = a.form;
     const bool hc = a.hash != nullptr || a.count != nullptr;
-    if (a.precision == DDSG_F64) return launch_eval_prec<DDSG_F64>(p, hc, st);
-    return launch_eval_prec<DDSG_F32C>(p, hc, st);
+    const int mc = a.cfg.mc > 0 ? a.cfg.mc : default_mc(a.precision, a.m);
+    if (a.precision == DDSG_F64) return launch_prec<DDSG_F64>(p, a.cfg.kernel, mc, hc, st);
+    return launch_prec<DDSG_F32C>(p, a.cfg.kernel, mc, hc, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -253,6 +479,7 @@ __global__ void __launch_bounds__(128) hierarchize_kernel(const DevTables t, int
                                                           const double *__restrict__ values) {
     const DevComp cd = t.comps[blockIdx.x];
     const int k = cd.k;
+    const int mp = t.mp64;
     for (int s = 0; s < cd.nlayers; ++s) {
         const int lb = t.layer_off[cd.layer_begin + s];
         const int le = t.layer_off[cd.layer_begin + s + 1];
@@ -278,12 +505,12 @@ __global__ void __launch_bounds__(128) hierarchize_kernel(const DevTables t, int
                     Basis1D o;
                     if (!basis1d(Xp[j], tu.lev[j], o)) { act = false; break; }
                     off = off * ncells(tu.lev[j]) + o.cell;
-                    wv *= __ull2double_rn(o.N) * pow2m_d(o.e);
+                    wv *= basis_to_f64(o.N, o.e);
                 }
                 if (!act) continue;
                 const int32_t q = t.slots[tu.slot_base + off];
                 if (q < 0) continue;
-                const double *a = t.alpha64 + (int64_t)q * m + m0;
+                const double *a = t.alpha64 + (int64_t)q * mp + m0;
 #pragma unroll
                 for (int o = 0; o < HC_CHUNK; ++o)
                     if (m0 + o < m) acc[o] = fma(wv, a[o], acc[o]);
@@ -291,7 +518,7 @@ __global__ void __launch_bounds__(128) hierarchize_kernel(const DevTables t, int
 #pragma unroll
             for (int o = 0; o < HC_CHUNK; ++o)
                 if (m0 + o < m)
-                    t.alpha64[(int64_t)pid * m + m0 + o] = values[(int64_t)pid * m + m0 + o] - acc[o];
+                    t.alpha64[(int64_t)pid * mp + m0 + o] = values[(int64_t)pid * m + m0 + o] - acc[o];
         }
         __syncthreads();
     }
@@ -303,17 +530,23 @@ cudaError_t launch_hierarchize(const DevTables &t, int m, const double *values, 
     return cudaGetLastError();
 }
 
-__global__ void to_f32_kernel(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        b[i] = __double2float_rn(a[i]);
+__global__ void to_f32_kernel(const double *__restrict__ a, int mp64, float *__restrict__ b, int mp32,
+                              int64_t P, int m) {
+    const int64_t total = P * (int64_t)mp32;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pt = i / mp32;
+        const int j = (int)(i - pt * mp32);
+        b[i] = j < m ? __double2float_rn(a[pt * mp64 + j]) : 0.0f;
+    }
 }
 
-cudaError_t launch_to_f32(const double *a, float *b, int64_t n, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    int64_t blocks = (n + 255) / 256;
+cudaError_t launch_to_f32(const double *a, int mp64, float *b, int mp32, int64_t P, int m,
+                          cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    int64_t blocks = (P * mp32 + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    to_f32_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, b, n);
+    to_f32_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, mp64, b, mp32, P, m);
     return cudaGetLastError();
 }
 

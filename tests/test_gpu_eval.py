@@ -207,3 +207,28 @@ def test_eval_before_hierarchize_is_an_error(G):
     y = torch.zeros((4, 1), dtype=torch.float64, device="cuda")
     with pytest.raises(G.DDSGError, match="ERR_STATE"):
         h.eval(x, y)
+
+
+def test_every_kernel_config_matches_oracle(G):
+    """Both evaluation kernels at every compiled output chunk, and the autotuner's
+    pick, give the same active sets and values (d=6, order 2, m=11)."""
+    d, m = 6, 11
+    c = synth.family_coeffs(synth.BASE_SEED + 55, m, d)
+    fn = lambda dims, X: synth.family_cut(c, dims, X)
+    ref, h = build_pair(G, d, m, O.full_order_components(d, 2), fn, eps=1e-3, level=9)
+    X = synth.uniform_queries(56, 700, d)
+    mcs = {0: [2, 4, 6, 8, 12, 16], 1: [4, 8, 12, 16, 28, 52]}
+    for prec in (0, 1):
+        for kernel in (0, 1):
+            for mc in mcs[prec]:
+                h.set_eval_config(prec, 1, kernel, mc)
+                h.set_eval_config(prec, 0, kernel, mc)
+                check_eval(h, ref, X, precs=(prec,))
+    xd = torch.from_numpy(X).cuda()
+    yd = torch.empty((X.shape[0], m), dtype=torch.float64, device="cuda")
+    for prec in (0, 1):
+        kernel, mc, ms = h.autotune(xd, yd, prec, 1)
+        assert kernel in (0, 1) and mc in mcs[prec] and ms > 0
+        check_eval(h, ref, X, forms=(1,), precs=(prec,))
+    with pytest.raises(G.DDSGError, match="not compiled"):
+        h.set_eval_config(0, 0, 0, 5)
