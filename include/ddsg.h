@@ -201,6 +201,31 @@ int hdmr_get_eval_config(const hdmr_t *h, int precision, int form, int *kernel, 
 int hdmr_autotune(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int precision,
                   int form, ddsg_stream_t stream, double *best_ms);
 
+/*
+ * hdmr_eval_noalloc -- hdmr_eval (no hash/count outputs) that allocates no
+ * device memory. The paper has no counterpart; this exists for callers that
+ * must not allocate while they evaluate: frameworks that own all device
+ * memory through their own pool or run under a fixed memory cap, and
+ * latency-critical loops where an allocation would stall or fail. hdmr_eval
+ * grows a handle workspace with cudaMalloc; this call instead uses one
+ * file-scope static device array of 16 MiB (2^21 words), which every GPU that
+ * loads the library keeps reserved until the process exits.
+ *   n must not exceed hdmr_eval_noalloc_capacity(d) (= floor(2^22 / (2d + 1)):
+ *   n*d coordinates plus n flags); larger batches are refused with
+ *   DDSG_ERR_ARG before anything runs -- split them.
+ *   The first call on a device looks up the array's device address there
+ *   (cudaGetSymbolAddress, once per device): make that first call before any
+ *   stream capture begins.
+ *   All calls on a device share the array and it keeps the last call's
+ *   contents (each call overwrites all it reads). Calls whose kernels overlap
+ *   on the GPU race on it: serialize them on one stream.
+ *   The handle must be hierarchized. Asynchronous on `stream`.
+ */
+int hdmr_eval_noalloc(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int precision,
+                      int form, ddsg_stream_t stream);
+/* Largest n hdmr_eval_noalloc accepts for dimension d (0 if d < 1). */
+int64_t hdmr_eval_noalloc_capacity(int d);
+
 /* Pre-size the eval workspace for up to n queries (no allocation in later evals). */
 int hdmr_reserve(hdmr_t *h, int64_t n);
 

@@ -54,6 +54,8 @@ SIGNATURES = {
     "hdmr_set_eval_config": (_int, [_p, _int, _int, _int, _int]),
     "hdmr_get_eval_config": (_int, [_p, _int, _int, C.POINTER(_int), C.POINTER(_int)]),
     "hdmr_autotune": (_int, [_p, _i64, _p, _p, _int, _int, _p, C.POINTER(_d)]),
+    "hdmr_eval_noalloc": (_int, [_p, _i64, _p, _p, _int, _int, _p]),
+    "hdmr_eval_noalloc_capacity": (_i64, [_int]),
     "hdmr_profile_read": (_int, [_p, _p, _p, _int]),
 }
 
@@ -223,6 +225,16 @@ class HDMR:
         _check(load().hdmr_eval(self._h, n, _dev_ptr(x_dev), _dev_ptr(y_dev), int(precision),
                                 int(form), _dev_ptr(hash_dev), _dev_ptr(count_dev),
                                 _stream_ptr(stream)), "hdmr_eval")
+
+    def eval_noalloc(self, x_dev, y_dev, precision: int = F64, form: int = FORM_PAPER, stream=None):
+        """Evaluation that allocates no device memory (scratch in a static device
+        array); batches above noalloc_capacity() queries are refused."""
+        n = x_dev.shape[0]
+        _check(load().hdmr_eval_noalloc(self._h, n, _dev_ptr(x_dev), _dev_ptr(y_dev), int(precision),
+                                        int(form), _stream_ptr(stream)), "hdmr_eval_noalloc")
+
+    def noalloc_capacity(self) -> int:
+        return int(load().hdmr_eval_noalloc_capacity(self.d))
 
     def eval_host(self, x_host: np.ndarray, y_host: np.ndarray, precision: int = F64,
                   form: int = FORM_PAPER, stream=None):

@@ -923,3 +923,33 @@ extern "C" int hdmr_stats(hdmr_t *h, int64_t *stats_host, int reset, ddsg_stream
     CUDA_TRY(cudaStreamSynchronize(st));
     return DDSG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// read-only view of a ready handle for entry points in other translation units
+// ---------------------------------------------------------------------------
+
+namespace ddsg {
+int handle_eval_view(hdmr_t *h, int precision, int form, HandleView *v) {
+    if (!h || !v) return fail(DDSG_ERR_ARG, "NULL handle");
+    if (precision != DDSG_F64 && precision != DDSG_F32C) return fail(DDSG_ERR_ARG, "unknown precision %d", precision);
+    if (form != DDSG_FORM_PAPER && form != DDSG_FORM_SLICEFREE) return fail(DDSG_ERR_ARG, "unknown form %d", form);
+    if (!h->uploaded || !h->have_alpha || h->device < 0)
+        return fail(DDSG_ERR_STATE, "call hdmr_hierarchize first");
+    if (form == DDSG_FORM_SLICEFREE && !h->anchor_central)
+        return fail(DDSG_ERR_ARG, "the slice-free form needs the anchor at the domain centre");
+    if (form == DDSG_FORM_SLICEFREE && !h->closed)
+        return fail(DDSG_ERR_ARG, "the slice-free form needs a downward-closed component set");
+    v->d = h->d;
+    v->m = h->m;
+    v->device = h->device;
+    v->tables = &h->dt;
+    v->lo = h->dlo;
+    v->span = h->dspan;
+    v->stats = h->stats;
+    v->cfg = h->cfg[precision][form];
+    return DDSG_OK;
+}
+
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace ddsg
+

@@ -172,6 +172,19 @@ cudaError_t launch_eval(const EvalArgs &a, cudaStream_t st);
 cudaError_t launch_hierarchize(const DevTables &t, int m, const double *values,
                                cudaStream_t st);
 
+// Read-only view of a hierarchized handle (host pointers to its device tables),
+// for entry points defined outside ddsg_host.cu. Returns DDSG_OK or an error
+// code with the message set (ddsg_last_error).
+struct HandleView {
+    int d = 0, m = 0, device = -1;
+    const DevTables *tables = nullptr;
+    const double *lo = nullptr, *span = nullptr;
+    int64_t *stats = nullptr;
+    EvalConfig cfg;
+};
+int handle_eval_view(hdmr_t *h, int precision, int form, HandleView *v);
+int set_error(int code, const char *msg);
+
 cudaError_t launch_to_f32(const double *a, int mp64, float *b, int mp32, int64_t P, int m,
                           cudaStream_t st);
 
