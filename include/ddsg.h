@@ -187,9 +187,12 @@ int hdmr_eval(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int prec
               uint64_t *hash_dev, int32_t *count_dev, ddsg_stream_t stream);
 
 /*
- * Evaluation kernel choice (the batching schedule). kernel 0 = staged tile
- * kernel (1D bases of a component staged once per dimension and level),
- * kernel 1 = per-tuple kernel; mc = outputs per thread and pass (0 = the
+ * Evaluation kernel choice (the batching schedule). kernel 0 = tile kernel
+ * (1D bases of a component staged once per dimension and level), kernel 1 =
+ * per-tuple kernel, kernel 2 = tile kernel whose component surplus blocks are
+ * staged into shared memory by TMA bulk copies, double-buffered (needs every
+ * evaluated component's block to fit the staging buffer; refused otherwise);
+ * mc = outputs per thread and pass (0 = the
  * heuristic: smallest compiled chunk >= m). hdmr_autotune times every compiled
  * pair on the caller's queries (x_dev, n; y_dev is scratch output) and keeps
  * the fastest for (precision, form); *best_ms (nullable) gets its time.
@@ -231,7 +234,9 @@ int hdmr_reserve(hdmr_t *h, int64_t n);
 
 /*
  * hdmr_stats -- counters accumulated by hdmr_eval since the last reset:
- *   stats[0] = clamped coordinates, stats[1] = non-finite query rows.
+ *   stats[0] = clamped coordinates, stats[1] = non-finite query rows,
+ *   stats[2] = bounded device waits that gave up (staging copies that did not
+ *   arrive in time; the affected outputs are invalid). stats_host holds 3.
  * Synchronizes `stream`. reset != 0 zeroes them afterwards.
  */
 int hdmr_stats(hdmr_t *h, int64_t *stats_host, int reset, ddsg_stream_t stream);

@@ -274,10 +274,10 @@ class HDMR:
         return {KERNEL_KINDS[i]: (float(ms[i]), int(n[i])) for i in range(8) if n[i]}
 
     def stats(self, reset: bool = False, stream=None):
-        out = np.zeros(2, np.int64)
+        out = np.zeros(3, np.int64)
         _check(load().hdmr_stats(self._h, _np_ptr(out), int(bool(reset)), _stream_ptr(stream)),
                "hdmr_stats")
-        return {"clamped": int(out[0]), "nonfinite_rows": int(out[1])}
+        return {"clamped": int(out[0]), "nonfinite_rows": int(out[1]), "wait_timeouts": int(out[2])}
 
 
 def build_adaptive(h: HDMR, value_fn, eps_gamma: float, max_level: int, strict: bool = False,

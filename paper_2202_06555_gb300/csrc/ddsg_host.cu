@@ -70,6 +70,7 @@ struct hdmr {
     bool uploaded = false;    // dt matches comps
     bool have_alpha = false;  // alpha64/alpha32 valid
     std::vector<double> b;
+    std::vector<int32_t> dpos;  // device row of each point (host copy)
     double *dlo = nullptr, *dspan = nullptr;
     int64_t *stats = nullptr;
     void *ws = nullptr;
@@ -140,6 +141,9 @@ static void free_tables(DevTables &t) {
     cudaFree(t.layer_off);
     cudaFree(t.pt_lv);
     cudaFree(t.pt_ix);
+    cudaFree(t.pt_dpos);
+    cudaFree(t.proc[0]);
+    cudaFree(t.proc[1]);
     t = DevTables();
 }
 
@@ -152,10 +156,10 @@ static int ensure_device(hdmr *h) {
     const int d = h->d;
     CUDA_TRY(cudaMalloc(&h->dlo, sizeof(double) * d));
     CUDA_TRY(cudaMalloc(&h->dspan, sizeof(double) * d));
-    CUDA_TRY(cudaMalloc(&h->stats, sizeof(int64_t) * 2));
+    CUDA_TRY(cudaMalloc(&h->stats, sizeof(int64_t) * 4));
     CUDA_TRY(cudaMemcpy(h->dlo, h->lo.data(), sizeof(double) * d, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(h->dspan, h->span.data(), sizeof(double) * d, cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemset(h->stats, 0, sizeof(int64_t) * 2));
+    CUDA_TRY(cudaMemset(h->stats, 0, sizeof(int64_t) * 4));
     h->device = dev;
     return DDSG_OK;
 }
@@ -449,6 +453,8 @@ static int upload_tables(hdmr *h) {
     std::vector<int32_t> layer_off;
     std::vector<uint8_t> pt_lv((size_t)KMAX * P, 0);
     std::vector<uint32_t> pt_ix((size_t)KMAX * P, 0);
+    std::vector<int32_t> dpos((size_t)P, -1);
+    int64_t row = 0;
     bool all_tile = true;
     for (int c = 0; c < C; ++c) {
         const Comp &cp = h->comps[c];
@@ -503,18 +509,33 @@ static int upload_tables(hdmr *h) {
             }
             if (size > (1ull << 26)) return fail(DDSG_ERR_TABLE, "component %d: level tuple too fine for a dense cell directory", c);
             t.lsum = level_sum(key.data(), k);
-            if (slots.size() + size > ((size_t)1 << 31)) return fail(DDSG_ERR_TABLE, "cell directories exceed 2^31 entries");
-            t.slot_base = (int32_t)slots.size();
-            slots.resize(slots.size() + size, -1);
+            t.ncell = (uint32_t)size;
+            t.first = (int32_t)row;
+            // present cells of this tuple, in increasing cell index
+            std::vector<std::pair<uint64_t, int64_t>> cells;
             for (int64_t p : bytup[key]) {
                 uint64_t off = 0;
                 for (int j = 0; j < k; ++j) off = off * ncells(key[j]) + cell_of_index(key[j], cp.ix[p * k + j]);
-                slots[t.slot_base + off] = (int32_t)(base + p);
+                cells.emplace_back(off, p);
+            }
+            std::sort(cells.begin(), cells.end());
+            for (auto &cl : cells) dpos[base + cl.second] = (int32_t)row++;
+            if (size <= 64) {
+                for (auto &cl : cells) t.mask |= 1ull << cl.first;
+                t.slot_base = -1;
+            } else {
+                if (slots.size() + size > ((size_t)1 << 31)) return fail(DDSG_ERR_TABLE, "cell directories exceed 2^31 entries");
+                t.slot_base = (int32_t)slots.size();
+                slots.resize(slots.size() + size, -1);
+                for (auto &cl : cells) slots[t.slot_base + cl.first] = dpos[base + cl.second];
             }
             tups.push_back(t);
         }
         d.tup_end = (int32_t)tups.size();
         if (d.tup_int < 0) d.tup_int = d.tup_end;
+        d.row_begin = (int32_t)(row - np);
+        d.row_end = (int32_t)row;
+        d.row_int = d.tup_int < d.tup_end ? tups[d.tup_int].first : d.row_end;
         // layers by level sum
         std::vector<int64_t> order(np);
         for (int64_t p = 0; p < np; ++p) order[p] = p;
@@ -552,6 +573,24 @@ static int upload_tables(hdmr *h) {
     if ((rc = dev_upload(&t.layer_off, layer_off))) return rc;
     if ((rc = dev_upload(&t.pt_lv, pt_lv))) return rc;
     if ((rc = dev_upload(&t.pt_ix, pt_ix))) return rc;
+    if ((rc = dev_upload(&t.pt_dpos, dpos))) return rc;
+    h->dpos = dpos;
+    // per-form component lists and the largest staged surplus block
+    const int64_t mp64 = (h->m + 1) & ~1, mp32 = (h->m + 3) & ~3;
+    for (int form = 0; form < 2; ++form) {
+        std::vector<int32_t> lst;
+        int64_t rows_max = 0;
+        for (int c = 0; c < C; ++c) {
+            if (form == DDSG_FORM_PAPER && h->b[c] == 0.0) continue;
+            lst.push_back(c);
+            const int64_t r0 = form == DDSG_FORM_PAPER ? dc[c].row_begin : dc[c].row_int;
+            rows_max = std::max<int64_t>(rows_max, dc[c].row_end - r0);
+        }
+        if ((rc = dev_upload(&t.proc[form], lst))) return rc;
+        t.nproc[form] = (int32_t)lst.size();
+        t.stage_bytes[form][DDSG_F64] = rows_max * mp64 * 8;
+        t.stage_bytes[form][DDSG_F32C] = rows_max * mp32 * 4;
+    }
     CUDA_TRY(cudaMalloc(&t.alpha64, sizeof(double) * (size_t)P * t.mp64));
     CUDA_TRY(cudaMalloc(&t.alpha32, sizeof(float) * (size_t)P * t.mp32));
     CUDA_TRY(cudaMemset(t.alpha64, 0, sizeof(double) * (size_t)P * t.mp64));
@@ -588,10 +627,13 @@ extern "C" int hdmr_get_surpluses(const hdmr_t *h, double *alpha_host, ddsg_stre
     if (!h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_get_surpluses: not hierarchized");
     DeviceGuard g(h->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    CUDA_TRY(cudaMemcpy2DAsync(alpha_host, sizeof(double) * h->m, h->dt.alpha64,
-                               sizeof(double) * h->dt.mp64, sizeof(double) * h->m, (size_t)h->P,
-                               cudaMemcpyDeviceToHost, st));
+    const int mp = h->dt.mp64, m = h->m;
+    std::vector<double> tmp((size_t)h->P * mp);
+    CUDA_TRY(cudaMemcpyAsync(tmp.data(), h->dt.alpha64, sizeof(double) * tmp.size(),
+                             cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t p = 0; p < h->P; ++p)
+        std::copy(&tmp[(size_t)h->dpos[p] * mp], &tmp[(size_t)h->dpos[p] * mp] + m, alpha_host + p * m);
     return DDSG_OK;
 }
 
@@ -745,6 +787,8 @@ extern "C" int hdmr_eval(hdmr_t *h, int64_t n, const double *x_dev, double *y_de
     if (precision != DDSG_F64 && precision != DDSG_F32C) return fail(DDSG_ERR_ARG, "hdmr_eval: unknown precision %d", precision);
     if (form != DDSG_FORM_PAPER && form != DDSG_FORM_SLICEFREE) return fail(DDSG_ERR_ARG, "hdmr_eval: unknown form %d", form);
     if (!h->uploaded || !h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_eval: call hdmr_hierarchize first");
+    if (!eval_kernel_eligible(h->dt, h->cfg[precision][form].kernel, precision, form))
+        h->cfg[precision][form] = EvalConfig();
     if (form == DDSG_FORM_SLICEFREE && !h->anchor_central)
         return fail(DDSG_ERR_ARG, "hdmr_eval: the slice-free form needs the anchor at the domain centre");
     if (form == DDSG_FORM_SLICEFREE && !h->closed)
@@ -771,6 +815,7 @@ extern "C" int hdmr_eval(hdmr_t *h, int64_t n, const double *x_dev, double *y_de
     a.form = form;
     a.precision = precision;
     a.cfg = h->cfg[precision][form];
+    a.err = reinterpret_cast<unsigned long long *>(h->stats + 2);
     {
         ProfScope ps(h, DDSG_K_EVAL, st);
         CUDA_TRY(launch_eval(a, st));
@@ -816,8 +861,10 @@ extern "C" int hdmr_eval_host(hdmr_t *h, int64_t n, const double *x_host, double
 
 extern "C" int hdmr_set_eval_config(hdmr_t *h, int precision, int form, int kernel, int mc) {
     if (!h) return fail(DDSG_ERR_ARG, "hdmr_set_eval_config: NULL handle");
-    if (precision < 0 || precision > 1 || form < 0 || form > 1 || kernel < 0 || kernel > 1)
+    if (precision < 0 || precision > 1 || form < 0 || form > 1 || kernel < 0 || kernel >= NKERNELS)
         return fail(DDSG_ERR_ARG, "hdmr_set_eval_config: bad precision/form/kernel");
+    if (h->uploaded && !eval_kernel_eligible(h->dt, kernel, precision, form))
+        return fail(DDSG_ERR_ARG, "hdmr_set_eval_config: kernel %d cannot run these tables (a component's surplus block exceeds the staging buffer)", kernel);
     int cand[16];
     const int nc = eval_mc_candidates(precision, kernel, cand, 16);
     bool ok = mc == 0;
@@ -850,7 +897,8 @@ extern "C" int hdmr_autotune(hdmr_t *h, int64_t n, const double *x_dev, double *
     CUDA_TRY(cudaEventCreate(&e1));
     EvalConfig best;
     double best_t = 1e300;
-    for (int kernel = 0; kernel < 2; ++kernel) {
+    for (int kernel = 0; kernel < NKERNELS; ++kernel) {
+        if (!eval_kernel_eligible(h->dt, kernel, precision, form)) continue;
         int cand[16];
         const int nc = eval_mc_candidates(precision, kernel, cand, 16);
         for (int i = 0; i < nc; ++i) {
@@ -918,8 +966,8 @@ extern "C" int hdmr_stats(hdmr_t *h, int64_t *stats_host, int reset, ddsg_stream
     if (int rc0 = ensure_device(h)) return rc0;
     DeviceGuard g(h->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    CUDA_TRY(cudaMemcpyAsync(stats_host, h->stats, sizeof(int64_t) * 2, cudaMemcpyDeviceToHost, st));
-    if (reset) CUDA_TRY(cudaMemsetAsync(h->stats, 0, sizeof(int64_t) * 2, st));
+    CUDA_TRY(cudaMemcpyAsync(stats_host, h->stats, sizeof(int64_t) * 3, cudaMemcpyDeviceToHost, st));
+    if (reset) CUDA_TRY(cudaMemsetAsync(h->stats, 0, sizeof(int64_t) * 4, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     return DDSG_OK;
 }

@@ -9,12 +9,16 @@
 //   DevTup[T]         one per non-empty level tuple of a component, ordered
 //                       (interior flag, level sum, lexicographic): levels and the
 //                       base offset of its dense cell directory in `slots`.
-//   slots[S] int32    dense directory of a tuple: for every cell of the level
-//                       tuple (product of per-dimension cell counts, last dim
-//                       fastest) the global point id, or -1 if absent. This turns
-//                       the support test of a query into O(1) arithmetic per tuple
-//                       (the per-level-tuple alternative to a tree walk).
-//   alpha64[P*mp64]   FP64 surpluses, point-major; rows padded with zeros to a
+//   Device row order: per component, its tuples in DevTup order, and inside a
+//   tuple its present cells in increasing cell index (last dim fastest).
+//   pt_dpos[P]        device row of each point (points keep the caller's order).
+//   mask (in DevTup)  presence bit per cell for tuples of <= 64 cells: the row of
+//                       a cell is `first` + popcount of the present cells below it.
+//   slots[S] int32    for larger tuples, a dense directory: for every cell the
+//                       device row, or -1 if absent. Either way the support test
+//                       of a query costs O(1) arithmetic per tuple (the
+//                       per-level-tuple alternative to a tree walk).
+//   alpha64[P*mp64]   FP64 surpluses by device row; rows padded with zeros to a
 //                       multiple of 16 bytes so they load as double2.
 //   alpha32[P*mp32]   FP32 copy used by the compensated FP32 form (float4 rows).
 //   pt_lv/pt_ix       structure-of-arrays (level, index) tables, [KMAX][P].
@@ -49,14 +53,33 @@ struct DevComp {
     int32_t pt_begin, pt_end;
     int32_t layer_begin;  // index into layer_off; layers of this comp: layer_off[layer_begin .. +nlayers]
     int32_t nlayers;
+    int32_t row_begin, row_int, row_end;  // device rows: all / interior (levels >= 2) / end
     double b;
 };
 
 struct DevTup {
     uint8_t lev[KMAX];
-    int32_t slot_base;
-    int32_t lsum;  // sum of (l_j - 1)
+    int32_t first;      // device row of the tuple's first present point
+    int32_t slot_base;  // cell directory (only when ncell > 64)
+    int32_t lsum;       // sum of (l_j - 1)
+    uint32_t ncell;     // cells of the level tuple (product of per-dim counts)
+    uint64_t mask;      // presence bit per cell when ncell <= 64
 };
+
+// Device row of cell `off` of tuple tu, or -1 if that cell holds no point.
+// Rows of a tuple are stored in increasing cell order, so for ncell <= 64 the
+// row is first + (number of present cells below off): no memory access.
+__host__ __device__ inline int32_t tuple_row(const DevTup &tu, uint32_t off, const int32_t *slots) {
+    if (tu.ncell <= 64) {
+        if (!((tu.mask >> off) & 1ull)) return -1;
+#ifdef __CUDA_ARCH__
+        return tu.first + __popcll(tu.mask & ((2ull << off) - 1ull)) - 1;
+#else
+        return tu.first + __builtin_popcountll(tu.mask & ((2ull << off) - 1ull)) - 1;
+#endif
+    }
+    return slots[tu.slot_base + off];
+}
 
 struct DevTables {
     int32_t C = 0, T = 0;
@@ -74,6 +97,12 @@ struct DevTables {
     int32_t *layer_off = nullptr;
     uint8_t *pt_lv = nullptr;     // SoA levels:  pt_lv[j*P + p], j < KMAX
     uint32_t *pt_ix = nullptr;    // SoA indices: pt_ix[j*P + p]
+    int32_t *pt_dpos = nullptr;   // device row of point p
+    // components each form evaluates, in order (paper form skips b == 0), and
+    // the largest surplus block (bytes, FP32 and FP64) one of them stages
+    int32_t *proc[2] = {nullptr, nullptr};
+    int32_t nproc[2] = {0, 0};
+    int64_t stage_bytes[2][2] = {{0, 0}, {0, 0}};  // [form][precision]
 };
 
 // ---------------------------------------------------------------------------
@@ -147,9 +176,12 @@ cudaError_t launch_encode_queries(int64_t n, int d, const double *x, const doubl
 constexpr int LT = 15;        // levels (1..LT) the staged evaluation path keeps per dimension
 
 struct EvalConfig {
-    int kernel = 0;           // 0 = staged tile kernel, 1 = per-tuple kernel
+    int kernel = 0;           // 0 = tile kernel, 1 = per-tuple kernel, 2 = TMA-staged tile kernel
     int mc = 0;               // outputs per thread and pass (0 = heuristic)
 };
+
+constexpr int NKERNELS = 3;
+constexpr int64_t TMA_STAGE_MAX = 88 * 1024;  // largest per-component surplus block staged by TMA
 
 struct EvalArgs {
     const DevTables *t;       // host copy of the table pointers
@@ -162,7 +194,11 @@ struct EvalArgs {
     int form;                 // DDSG_FORM_*
     int precision;            // DDSG_F64 / DDSG_F32C
     EvalConfig cfg;
+    unsigned long long *err = nullptr;  // device word: bounded waits that gave up (nullable)
 };
+
+// true if kernel `kernel` can run this handle/form/precision
+bool eval_kernel_eligible(const DevTables &t, int kernel, int precision, int form);
 
 // candidate output-chunk sizes the kernels are compiled for
 int eval_mc_candidates(int precision, int kernel, int *out, int cap);

@@ -147,6 +147,7 @@ struct EvalParams {
     uint64_t *hash;
     int32_t *count;
     int form;
+    unsigned long long *err;
 };
 
 template <int PREC>
@@ -257,7 +258,7 @@ __device__ __forceinline__ void comp_generic(const EvalParams &p, const DevComp 
             w = w * basis_val<W>(o);
         }
         if (!act) continue;
-        const int32_t pid = p.t.slots[tu.slot_base + off];
+        const int32_t pid = tuple_row(tu, off, p.t.slots);
         if (pid < 0) continue;
         if (paper) w = (W)cd.b * w;
         accumulate<PREC, MC>(acc, w, alpha + (int64_t)pid * mp, m0, mp);
@@ -305,6 +306,112 @@ __global__ void __launch_bounds__(128) eval_lq_kernel(const EvalParams p) {
 
 constexpr int TQ = 128;  // queries per block of the tile kernel
 
+// Look up one level tuple for this thread's query from the staged 1D basis:
+// device row (-1 if the query's cell holds no point or the query sits on a
+// cell face) and the basis weight (0 when there is no point).
+template <int PREC, int K>
+__device__ __forceinline__ int32_t tile_probe(const DevTup &tu, const int32_t *slots, int tid,
+                                             const uint32_t (*s_cell)[LT][TQ],
+                                             const typename Types<PREC>::W (*s_t)[LT][TQ],
+                                             typename Types<PREC>::W wb,
+                                             typename Types<PREC>::W &w, uint32_t *cells) {
+    using W = typename Types<PREC>::W;
+    uint32_t off = 0;
+    W wt = wb;
+    if (K >= 1) {
+        const uint32_t ca = s_cell[0][tu.lev[0] - 1][tid];
+        cells[0] = ca;
+        if (K == 1) {
+            if (ca & 0x80000000u) { w = (W)0; return -1; }
+            off = ca;
+            wt = wb * s_t[0][tu.lev[0] - 1][tid];
+        } else {
+            const uint32_t cb = s_cell[1][tu.lev[1] - 1][tid];
+            cells[1] = cb;
+            if ((ca | cb) & 0x80000000u) { w = (W)0; return -1; }
+            off = ca * ncells(tu.lev[1]) + cb;
+            wt = wb * (s_t[0][tu.lev[0] - 1][tid] * s_t[1][tu.lev[1] - 1][tid]);
+        }
+    }
+    const int32_t row = tuple_row(tu, off, slots);
+    w = row >= 0 ? wt : (W)0;
+    return row;
+}
+
+// Load the output chunk [m0, m0+MC) of device row `row` as 16-byte vectors
+// (zeros when row < 0 or past the padded row).
+template <int PREC, int MC>
+__device__ __forceinline__ void tile_load(typename Types<PREC>::V (&v)[MC / Types<PREC>::VW],
+                                          const typename Types<PREC>::W *alpha, int32_t row, int m0,
+                                          int mp) {
+    using T = Types<PREC>;
+    const typename T::V *src = reinterpret_cast<const typename T::V *>(alpha + (int64_t)(row < 0 ? 0 : row) * mp + m0);
+#pragma unroll
+    for (int g = 0; g < MC / T::VW; ++g) {
+        if (row >= 0 && m0 + g * T::VW < mp) v[g] = __ldg(src + g);
+        else memset(&v[g], 0, sizeof(v[g]));
+    }
+}
+
+template <int PREC, int MC>
+__device__ __forceinline__ void tile_fma(typename Types<PREC>::W (&acc)[MC], typename Types<PREC>::W w,
+                                         const typename Types<PREC>::V (&v)[MC / Types<PREC>::VW]) {
+#pragma unroll
+    for (int g = 0; g < MC / Types<PREC>::VW; ++g) {
+        if constexpr (Types<PREC>::VW == 4) {
+            acc[4 * g + 0] = fmaf(w, v[g].x, acc[4 * g + 0]);
+            acc[4 * g + 1] = fmaf(w, v[g].y, acc[4 * g + 1]);
+            acc[4 * g + 2] = fmaf(w, v[g].z, acc[4 * g + 2]);
+            acc[4 * g + 3] = fmaf(w, v[g].w, acc[4 * g + 3]);
+        } else {
+            acc[2 * g + 0] = fma(w, v[g].x, acc[2 * g + 0]);
+            acc[2 * g + 1] = fma(w, v[g].y, acc[2 * g + 1]);
+        }
+    }
+}
+
+// The tuples [tb, te) of one component with K dims, two at a time so that two
+// surplus rows are in flight before their FMAs.
+template <int PREC, int MC, bool HC, int K>
+__device__ __forceinline__ void tile_tuples(const EvalParams &p, int c, int tb, int te,
+                                            typename Types<PREC>::W wb, int m0, int tid,
+                                            const uint32_t (*s_cell)[LT][TQ],
+                                            const typename Types<PREC>::W (*s_t)[LT][TQ],
+                                            typename Types<PREC>::W (&acc)[MC], uint64_t &h,
+                                            int32_t &cnt) {
+    using T = Types<PREC>;
+    using W = typename T::W;
+    const W *alpha = T::alpha(p.t);
+    const int mp = T::stride(p.t);
+    for (int ti = tb; ti < te; ti += 2) {
+        const bool two = ti + 1 < te;
+        const DevTup t0 = p.t.tups[ti];
+        const DevTup t1 = p.t.tups[two ? ti + 1 : ti];
+        W w0, w1;
+        uint32_t c0[2] = {0, 0}, c1[2] = {0, 0};
+        const int32_t r0 = tile_probe<PREC, K>(t0, p.t.slots, tid, s_cell, s_t, wb, w0, c0);
+        int32_t r1 = tile_probe<PREC, K>(t1, p.t.slots, tid, s_cell, s_t, wb, w1, c1);
+        if (!two) {
+            r1 = -1;
+            w1 = (W)0;
+        }
+        typename T::V v0[MC / T::VW], v1[MC / T::VW];
+        tile_load<PREC, MC>(v0, alpha, r0, m0, mp);
+        tile_load<PREC, MC>(v1, alpha, r1, m0, mp);
+        if constexpr (PREC == DDSG_F64) {   // FP64 issue slots are scarce: no FMAs on misses
+            if (r0 >= 0) tile_fma<PREC, MC>(acc, w0, v0);
+            if (r1 >= 0) tile_fma<PREC, MC>(acc, w1, v1);
+        } else {
+            tile_fma<PREC, MC>(acc, w0, v0);
+            tile_fma<PREC, MC>(acc, w1, v1);
+        }
+        if (HC) {
+            if (r0 >= 0) { h ^= point_key(c, K, t0.lev, c0); ++cnt; }
+            if (r1 >= 0) { h ^= point_key(c, K, t1.lev, c1); ++cnt; }
+        }
+    }
+}
+
 template <int PREC, int MC, bool HC>
 __global__ void __launch_bounds__(TQ) eval_tile_kernel(const EvalParams p) {
     using W = typename Types<PREC>::W;
@@ -349,37 +456,9 @@ __global__ void __launch_bounds__(TQ) eval_tile_kernel(const EvalParams p) {
             }
             const int tb = paper ? cd.tup_begin : cd.tup_int;
             const W wb = paper ? (W)b : (W)1;
-            for (int ti = tb; ti < cd.tup_end; ++ti) {
-                const DevTup tu = p.t.tups[ti];
-                uint32_t off;
-                W w;
-                uint32_t cells[2];
-                if (k == 0) {
-                    off = 0;
-                    w = wb;
-                } else if (k == 1) {
-                    const uint32_t ca = s_cell[0][tu.lev[0] - 1][tid];
-                    if (ca & 0x80000000u) continue;
-                    off = ca;
-                    cells[0] = ca;
-                    w = wb * s_t[0][tu.lev[0] - 1][tid];
-                } else {
-                    const uint32_t ca = s_cell[0][tu.lev[0] - 1][tid];
-                    const uint32_t cb = s_cell[1][tu.lev[1] - 1][tid];
-                    if ((ca | cb) & 0x80000000u) continue;
-                    off = ca * ncells(tu.lev[1]) + cb;
-                    cells[0] = ca;
-                    cells[1] = cb;
-                    w = wb * (s_t[0][tu.lev[0] - 1][tid] * s_t[1][tu.lev[1] - 1][tid]);
-                }
-                const int32_t pid = __ldg(p.t.slots + tu.slot_base + off);
-                if (pid < 0) continue;
-                accumulate<PREC, MC>(r.partial(), w, alpha + (int64_t)pid * mp, m0, mp);
-                if (HC) {
-                    h ^= point_key(c, k, tu.lev, cells);
-                    ++cnt;
-                }
-            }
+            if (k == 2) tile_tuples<PREC, MC, HC, 2>(p, c, tb, cd.tup_end, wb, m0, tid, s_cell, s_t, r.partial(), h, cnt);
+            else if (k == 1) tile_tuples<PREC, MC, HC, 1>(p, c, tb, cd.tup_end, wb, m0, tid, s_cell, s_t, r.partial(), h, cnt);
+            else tile_tuples<PREC, MC, HC, 0>(p, c, tb, cd.tup_end, wb, m0, tid, s_cell, s_t, r.partial(), h, cnt);
             r.fold();
         }
     }
@@ -393,8 +472,284 @@ __global__ void __launch_bounds__(TQ) eval_tile_kernel(const EvalParams p) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// TMA-staged tile kernel: 256 queries per block; the surplus rows each
+// component contributes (all rows, or the interior rows for the slice-free
+// form) are one contiguous device-row range, copied into shared memory by a
+// bulk TMA copy two components ahead (double buffer, one mbarrier each).
+// ---------------------------------------------------------------------------
+
+constexpr int TQ2 = 256;
+constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait calls before giving up
+constexpr int kSmemLimit = 232448;          // opt-in shared memory per block (227 KiB)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of `bar` with an iteration limit; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <int PREC>
+__host__ __device__ constexpr int tma_fixed_smem() {
+    return 128 + (int)sizeof(uint16_t) * 2 * LT * TQ2 +
+           (int)sizeof(typename std::conditional<PREC == DDSG_F64, double, float>::type) * 2 * LT * TQ2;
+}
+
+bool eval_kernel_eligible(const DevTables &t, int kernel, int precision, int form) {
+    if (kernel == 0 || kernel == 1) return true;
+    if (kernel != 2) return false;
+    if (!t.tile_ok) return false;   // the staged kernel handles only k <= 2, levels <= LT
+    const int64_t fixed = precision == DDSG_F64 ? tma_fixed_smem<DDSG_F64>() : tma_fixed_smem<DDSG_F32C>();
+    const int64_t bytes = t.stage_bytes[form][precision];
+    return bytes <= TMA_STAGE_MAX && fixed + 2 * ((bytes + 127) & ~127ll) <= kSmemLimit;
+}
+
+template <int PREC, int K>
+__device__ __forceinline__ int32_t tma_probe(const DevTup &tu, const int32_t *slots, int tid,
+                                            const uint16_t (*s_cell)[LT][TQ2],
+                                            const typename Types<PREC>::W (*s_t)[LT][TQ2],
+                                            typename Types<PREC>::W wb, typename Types<PREC>::W &w,
+                                            uint32_t *cells) {
+    using W = typename Types<PREC>::W;
+    uint32_t off = 0;
+    W wt = wb;
+    if (K >= 1) {
+        const uint32_t ca = s_cell[0][tu.lev[0] - 1][tid];
+        cells[0] = ca;
+        if (K == 1) {
+            if (ca & 0x8000u) { w = (W)0; return -1; }
+            off = ca;
+            wt = wb * s_t[0][tu.lev[0] - 1][tid];
+        } else {
+            const uint32_t cb = s_cell[1][tu.lev[1] - 1][tid];
+            cells[1] = cb;
+            if ((ca | cb) & 0x8000u) { w = (W)0; return -1; }
+            off = ca * ncells(tu.lev[1]) + cb;
+            wt = wb * (s_t[0][tu.lev[0] - 1][tid] * s_t[1][tu.lev[1] - 1][tid]);
+        }
+    }
+    const int32_t row = tuple_row(tu, off, slots);
+    w = row >= 0 ? wt : (W)0;
+    return row;
+}
+
+template <int PREC, int MC>
+__device__ __forceinline__ void tma_load(typename Types<PREC>::V (&v)[MC / Types<PREC>::VW],
+                                         const typename Types<PREC>::W *sbuf, int32_t srow, bool hit,
+                                         int m0, int mp) {
+    using T = Types<PREC>;
+    const typename T::V *src = reinterpret_cast<const typename T::V *>(sbuf + (int64_t)(hit ? srow : 0) * mp + m0);
+#pragma unroll
+    for (int g = 0; g < MC / T::VW; ++g) {
+        if (hit && m0 + g * T::VW < mp) v[g] = src[g];
+        else memset(&v[g], 0, sizeof(v[g]));
+    }
+}
+
+template <int PREC, int MC, bool HC, int K>
+__device__ __forceinline__ void tma_tuples(const EvalParams &p, int c, int tb, int te,
+                                           typename Types<PREC>::W wb, int m0, int tid,
+                                           const uint16_t (*s_cell)[LT][TQ2],
+                                           const typename Types<PREC>::W (*s_t)[LT][TQ2],
+                                           const typename Types<PREC>::W *sbuf, int32_t row0,
+                                           typename Types<PREC>::W (&acc)[MC], uint64_t &h, int32_t &cnt) {
+    using T = Types<PREC>;
+    using W = typename T::W;
+    const int mp = T::stride(p.t);
+    for (int ti = tb; ti < te; ti += 2) {
+        const bool two = ti + 1 < te;
+        const DevTup t0 = p.t.tups[ti];
+        const DevTup t1 = p.t.tups[two ? ti + 1 : ti];
+        W w0, w1;
+        uint32_t c0[2] = {0, 0}, c1[2] = {0, 0};
+        const int32_t r0 = tma_probe<PREC, K>(t0, p.t.slots, tid, s_cell, s_t, wb, w0, c0);
+        int32_t r1 = tma_probe<PREC, K>(t1, p.t.slots, tid, s_cell, s_t, wb, w1, c1);
+        if (!two) {
+            r1 = -1;
+            w1 = (W)0;
+        }
+        typename T::V v0[MC / T::VW], v1[MC / T::VW];
+        tma_load<PREC, MC>(v0, sbuf, r0 - row0, r0 >= 0, m0, mp);
+        tma_load<PREC, MC>(v1, sbuf, r1 - row0, r1 >= 0, m0, mp);
+        if constexpr (PREC == DDSG_F64) {
+            if (r0 >= 0) tile_fma<PREC, MC>(acc, w0, v0);
+            if (r1 >= 0) tile_fma<PREC, MC>(acc, w1, v1);
+        } else {
+            tile_fma<PREC, MC>(acc, w0, v0);
+            tile_fma<PREC, MC>(acc, w1, v1);
+        }
+        if (HC) {
+            if (r0 >= 0) { h ^= point_key(c, K, t0.lev, c0); ++cnt; }
+            if (r1 >= 0) { h ^= point_key(c, K, t1.lev, c1); ++cnt; }
+        }
+    }
+}
+
+template <int PREC, int MC, bool HC>
+__global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, int buf_bytes) {
+    using T = Types<PREC>;
+    using W = typename T::W;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    auto s_cell = reinterpret_cast<uint16_t (*)[LT][TQ2]>(smem + 128);
+    auto s_t = reinterpret_cast<W (*)[LT][TQ2]>(smem + 128 + sizeof(uint16_t) * 2 * LT * TQ2);
+    unsigned char *bufbase = smem + tma_fixed_smem<PREC>();
+    W *buf[2] = {reinterpret_cast<W *>(bufbase), reinterpret_cast<W *>(bufbase + buf_bytes)};
+
+    const int tid = threadIdx.x;
+    const int64_t q = (int64_t)blockIdx.x * TQ2 + tid;
+    const int m0 = blockIdx.y * MC;
+    const int m = p.m;
+    const bool valid = q < p.n;
+    const bool bad = !valid || p.flags[q] != 0;
+    const bool paper = p.form == DDSG_FORM_PAPER;
+    const int32_t *list = p.t.proc[p.form];
+    const int nproc = p.t.nproc[p.form];
+    const W *galpha = T::alpha(p.t);
+    const int mp = T::stride(p.t);
+
+    auto row_range = [&](int i, int32_t &r0, uint32_t &bytes) {
+        const DevComp &cd = p.t.comps[list[i]];
+        r0 = paper ? cd.row_begin : cd.row_int;
+        bytes = (uint32_t)((int64_t)(cd.row_end - r0) * mp * (int64_t)sizeof(W));
+    };
+    auto issue = [&](int i, int b) {  // thread 0 only
+        int32_t r0;
+        uint32_t bytes;
+        row_range(i, r0, bytes);
+        if (bytes) {
+            mbar_expect_tx(&bar[b], bytes);
+            tma_bulk_g2s(buf[b], galpha + (int64_t)r0 * mp, bytes, &bar[b]);
+        } else {
+            mbar_arrive(&bar[b]);
+        }
+    };
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (nproc > 0) issue(0, 0);
+        if (nproc > 1) issue(1, 1);
+    }
+
+    Result<PREC, MC> r;
+    r.init();
+    uint64_t h = 0;
+    int32_t cnt = 0;
+    bool failed = false;
+    for (int i = 0; i < nproc; ++i) {
+        const int b = i & 1;
+        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((i >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            // a staging copy did not arrive: record it, wait (bounded) for the
+            // copies this block still has in flight, then give up on the block
+            failed = true;
+            if (tid == 0 && p.err) atomicAdd(p.err, 1ull);
+            mbar_wait_bounded(&bar[b], (uint32_t)((i >> 1) & 1));
+            if (i + 1 < nproc) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((i + 1) >> 1) & 1));
+            break;
+        }
+        const int c = list[i];
+        const DevComp &cd = p.t.comps[c];
+        if (!bad) {
+            const int k = cd.k;
+            for (int j = 0; j < k; ++j) {
+                const uint64_t Xv = p.X[(int64_t)cd.dims[j] * p.n + q];
+                const int lm = cd.lmax[j];
+                for (int l = 1; l <= lm; ++l) {
+                    Basis1D o;
+                    const bool act = basis1d(Xv, l, o);
+                    s_cell[j][l - 1][tid] = act ? (uint16_t)o.cell : (uint16_t)0x8000u;
+                    s_t[j][l - 1][tid] = basis_val<W>(o);
+                }
+            }
+            const int tb = paper ? cd.tup_begin : cd.tup_int;
+            const int32_t row0 = paper ? cd.row_begin : cd.row_int;
+            const W wb = paper ? (W)cd.b : (W)1;
+            if (k == 2) tma_tuples<PREC, MC, HC, 2>(p, c, tb, cd.tup_end, wb, m0, tid, s_cell, s_t, buf[b], row0, r.partial(), h, cnt);
+            else if (k == 1) tma_tuples<PREC, MC, HC, 1>(p, c, tb, cd.tup_end, wb, m0, tid, s_cell, s_t, buf[b], row0, r.partial(), h, cnt);
+            else tma_tuples<PREC, MC, HC, 0>(p, c, tb, cd.tup_end, wb, m0, tid, s_cell, s_t, buf[b], row0, r.partial(), h, cnt);
+            r.fold();
+        }
+        __syncthreads();  // everyone is done with buf[b]
+        if (tid == 0 && i + 2 < nproc) {
+            fence_proxy_async_smem();
+            issue(i + 2, b);
+        }
+    }
+    if (!valid) return;
+    const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+#pragma unroll
+    for (int o = 0; o < MC; ++o)
+        if (m0 + o < m) p.y[q * m + m0 + o] = (bad || failed) ? nanv : r.value(o);
+    if (HC && blockIdx.y == 0) {
+        if (p.hash) p.hash[q] = (bad || failed) ? 0 : h;
+        if (p.count) p.count[q] = (bad || failed) ? 0 : cnt;
+    }
+}
+
 template <int PREC, int MC>
 static cudaError_t launch_mc(const EvalParams &p, int kernel, bool hc, cudaStream_t st) {
+    if (kernel == 2) {
+        const int prec = PREC;
+        const int64_t stage = p.t.stage_bytes[p.form][prec];
+        const int buf = (int)((stage + 127) & ~127ll);
+        const int smem = tma_fixed_smem<PREC>() + 2 * buf;
+        dim3 grid2((unsigned)((p.n + TQ2 - 1) / TQ2), (unsigned)((p.m + MC - 1) / MC));
+        if (hc) {
+            cudaError_t e = cudaFuncSetAttribute(eval_tma_kernel<PREC, MC, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            eval_tma_kernel<PREC, MC, true><<<grid2, TQ2, smem, st>>>(p, buf);
+        } else {
+            cudaError_t e = cudaFuncSetAttribute(eval_tma_kernel<PREC, MC, false>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            eval_tma_kernel<PREC, MC, false><<<grid2, TQ2, smem, st>>>(p, buf);
+        }
+        return cudaGetLastError();
+    }
     dim3 grid((unsigned)((p.n + TQ - 1) / TQ), (unsigned)((p.m + MC - 1) / MC));
     if (kernel == 0) {
         if (hc) eval_tile_kernel<PREC, MC, true><<<grid, TQ, 0, st>>>(p);
@@ -420,7 +775,7 @@ int eval_mc_candidates(int precision, int kernel, int *out, int cap) {
 
 template <int PREC>
 static cudaError_t launch_prec(const EvalParams &p, int kernel, int mc, bool hc, cudaStream_t st) {
-    if (PREC == DDSG_F64) {
+    if constexpr (PREC == DDSG_F64) {
         switch (mc) {
             case 2: return launch_mc<PREC, 2>(p, kernel, hc, st);
             case 4: return launch_mc<PREC, 4>(p, kernel, hc, st);
@@ -463,6 +818,7 @@ cudaError_t launch_eval(const EvalArgs &a, cudaStream_t st) {
     p.hash = a.hash;
     p.count = a.count;
     p.form = a.form;
+    p.err = a.err;
     const bool hc = a.hash != nullptr || a.count != nullptr;
     const int mc = a.cfg.mc > 0 ? a.cfg.mc : default_mc(a.precision, a.m);
     if (a.precision == DDSG_F64) return launch_prec<DDSG_F64>(p, a.cfg.kernel, mc, hc, st);
@@ -508,7 +864,7 @@ __global__ void __launch_bounds__(128) hierarchize_kernel(const DevTables t, int
                     wv *= basis_to_f64(o.N, o.e);
                 }
                 if (!act) continue;
-                const int32_t q = t.slots[tu.slot_base + off];
+                const int32_t q = tuple_row(tu, off, t.slots);
                 if (q < 0) continue;
                 const double *a = t.alpha64 + (int64_t)q * mp + m0;
 #pragma unroll
@@ -518,7 +874,7 @@ __global__ void __launch_bounds__(128) hierarchize_kernel(const DevTables t, int
 #pragma unroll
             for (int o = 0; o < HC_CHUNK; ++o)
                 if (m0 + o < m)
-                    t.alpha64[(int64_t)pid * mp + m0 + o] = values[(int64_t)pid * m + m0 + o] - acc[o];
+                    t.alpha64[(int64_t)t.pt_dpos[pid] * mp + m0 + o] = values[(int64_t)pid * m + m0 + o] - acc[o];
         }
         __syncthreads();
     }
