@@ -509,7 +509,7 @@ static int upload_tables(hdmr *h) {
             }
             if (size > (1ull << 26)) return fail(DDSG_ERR_TABLE, "component %d: level tuple too fine for a dense cell directory", c);
             t.lsum = level_sum(key.data(), k);
-            t.ncell = (uint32_t)size;
+            t.nc1 = k >= 2 ? ncells(key[1]) : 1u;
             t.first = (int32_t)row;
             // present cells of this tuple, in increasing cell index
             std::vector<std::pair<uint64_t, int64_t>> cells;
@@ -588,6 +588,10 @@ static int upload_tables(hdmr *h) {
         }
         if ((rc = dev_upload(&t.proc[form], lst))) return rc;
         t.nproc[form] = (int32_t)lst.size();
+        for (int c2 = 0; c2 < C; ++c2) {
+            t.max_tuples = std::max(t.max_tuples, dc[c2].tup_end - dc[c2].tup_begin);
+            for (int j = 0; j < dc[c2].k; ++j) t.max_level = std::max<int32_t>(t.max_level, dc[c2].lmax[j]);
+        }
         t.stage_bytes[form][DDSG_F64] = rows_max * mp64 * 8;
         t.stage_bytes[form][DDSG_F32C] = rows_max * mp32 * 4;
     }

@@ -60,17 +60,17 @@ struct DevComp {
 struct DevTup {
     uint8_t lev[KMAX];
     int32_t first;      // device row of the tuple's first present point
-    int32_t slot_base;  // cell directory (only when ncell > 64)
+    int32_t slot_base;  // cell directory offset, or -1 when the tuple has <= 64 cells
     int32_t lsum;       // sum of (l_j - 1)
-    uint32_t ncell;     // cells of the level tuple (product of per-dim counts)
-    uint64_t mask;      // presence bit per cell when ncell <= 64
+    uint32_t nc1;       // cells of the second dimension's level (row stride of a 2D cell index)
+    uint64_t mask;      // presence bit per cell when slot_base < 0
 };
 
 // Device row of cell `off` of tuple tu, or -1 if that cell holds no point.
-// Rows of a tuple are stored in increasing cell order, so for ncell <= 64 the
-// row is first + (number of present cells below off): no memory access.
+// Rows of a tuple are stored in increasing cell order, so for tuples of <= 64
+// cells the row is first + (number of present cells below off): no memory access.
 __host__ __device__ inline int32_t tuple_row(const DevTup &tu, uint32_t off, const int32_t *slots) {
-    if (tu.ncell <= 64) {
+    if (tu.slot_base < 0) {
         if (!((tu.mask >> off) & 1ull)) return -1;
 #ifdef __CUDA_ARCH__
         return tu.first + __popcll(tu.mask & ((2ull << off) - 1ull)) - 1;
@@ -103,6 +103,8 @@ struct DevTables {
     int32_t *proc[2] = {nullptr, nullptr};
     int32_t nproc[2] = {0, 0};
     int64_t stage_bytes[2][2] = {{0, 0}, {0, 0}};  // [form][precision]
+    int32_t max_tuples = 0;                        // most level tuples in one component
+    int32_t max_level = 0;                         // highest 1D level present anywhere
 };
 
 // ---------------------------------------------------------------------------
@@ -181,7 +183,8 @@ struct EvalConfig {
 };
 
 constexpr int NKERNELS = 3;
-constexpr int64_t TMA_STAGE_MAX = 88 * 1024;  // largest per-component surplus block staged by TMA
+constexpr int64_t TMA_STAGE_MAX = 84 * 1024;  // largest per-component surplus block staged by TMA
+constexpr int TMA_TUP_MAX = 128;              // most level tuples of one component the staged kernel holds
 
 struct EvalArgs {
     const DevTables *t;       // host copy of the table pointers

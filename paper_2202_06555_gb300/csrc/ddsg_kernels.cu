@@ -329,7 +329,7 @@ __device__ __forceinline__ int32_t tile_probe(const DevTup &tu, const int32_t *s
             const uint32_t cb = s_cell[1][tu.lev[1] - 1][tid];
             cells[1] = cb;
             if ((ca | cb) & 0x80000000u) { w = (W)0; return -1; }
-            off = ca * ncells(tu.lev[1]) + cb;
+            off = ca * tu.nc1 + cb;
             wt = wb * (s_t[0][tu.lev[0] - 1][tid] * s_t[1][tu.lev[1] - 1][tid]);
         }
     }
@@ -532,13 +532,48 @@ __host__ __device__ constexpr int tma_fixed_smem() {
            (int)sizeof(typename std::conditional<PREC == DDSG_F64, double, float>::type) * 2 * LT * TQ2;
 }
 
+// bytes of one staging buffer: component struct, its level tuples, its surplus rows
+__host__ __device__ inline int tma_buf_bytes(int64_t stage) {
+    return 128 + TMA_TUP_MAX * (int)sizeof(DevTup) + (int)((stage + 127) & ~127ll);
+}
+
 bool eval_kernel_eligible(const DevTables &t, int kernel, int precision, int form) {
     if (kernel == 0 || kernel == 1) return true;
     if (kernel != 2) return false;
     if (!t.tile_ok) return false;   // the staged kernel handles only k <= 2, levels <= LT
+    if (t.max_tuples > TMA_TUP_MAX) return false;
     const int64_t fixed = precision == DDSG_F64 ? tma_fixed_smem<DDSG_F64>() : tma_fixed_smem<DDSG_F32C>();
     const int64_t bytes = t.stage_bytes[form][precision];
-    return bytes <= TMA_STAGE_MAX && fixed + 2 * ((bytes + 127) & ~127ll) <= kSmemLimit;
+    return bytes <= TMA_STAGE_MAX && fixed + 2 * (int64_t)tma_buf_bytes(bytes) <= kSmemLimit;
+}
+
+// 1D basis of levels 1..lm at fixed-point coordinate X into staging slot j:
+// cell (bit 15 = query on a face at that level) and hat value.
+template <int PREC>
+__device__ __forceinline__ void tma_stage(uint64_t X, int lm, int tid, uint16_t (*s_cell)[LT][TQ2],
+                                          typename Types<PREC>::W (*s_t)[LT][TQ2], int j) {
+    using W = typename Types<PREC>::W;
+    s_cell[j][0][tid] = 0;
+    s_t[j][0][tid] = (W)1;
+    if (lm >= 2) {
+        Basis1D o;
+        const bool act = basis1d(X, 2, o);
+        s_cell[j][1][tid] = act ? (uint16_t)o.cell : (uint16_t)0x8000u;
+        s_t[j][1][tid] = basis_val<W>(o);
+    }
+    for (int l = 3; l <= lm; ++l) {
+        // cell width 2^sh; position F in the cell; phi numerator N = min(F, 2^sh - F)
+        const int sh = 64 - l;
+        uint64_t cell = X >> sh;
+        const uint64_t nmax = (1ull << (l - 2)) - 1;
+        cell = cell > nmax ? nmax : cell;
+        const uint64_t F = X - (cell << sh);
+        const uint64_t R = (1ull << sh) - F;
+        const uint64_t N = F < R ? F : R;
+        s_cell[j][l - 1][tid] = N ? (uint16_t)cell : (uint16_t)0x8000u;
+        if constexpr (PREC == DDSG_F64) s_t[j][l - 1][tid] = basis_to_f64(N, sh - 1);
+        else s_t[j][l - 1][tid] = __uint2float_rn((uint32_t)(N >> (32 - l))) * pow2m_f(31);
+    }
 }
 
 template <int PREC, int K>
@@ -561,7 +596,7 @@ __device__ __forceinline__ int32_t tma_probe(const DevTup &tu, const int32_t *sl
             const uint32_t cb = s_cell[1][tu.lev[1] - 1][tid];
             cells[1] = cb;
             if ((ca | cb) & 0x8000u) { w = (W)0; return -1; }
-            off = ca * ncells(tu.lev[1]) + cb;
+            off = ca * tu.nc1 + cb;
             wt = wb * (s_t[0][tu.lev[0] - 1][tid] * s_t[1][tu.lev[1] - 1][tid]);
         }
     }
@@ -583,8 +618,9 @@ __device__ __forceinline__ void tma_load(typename Types<PREC>::V (&v)[MC / Types
     }
 }
 
+// Tuples [0, nt) of one staged component (tuple structs in shared memory).
 template <int PREC, int MC, bool HC, int K>
-__device__ __forceinline__ void tma_tuples(const EvalParams &p, int c, int tb, int te,
+__device__ __forceinline__ void tma_tuples(const EvalParams &p, int c, const DevTup *stup, int nt,
                                            typename Types<PREC>::W wb, int m0, int tid,
                                            const uint16_t (*s_cell)[LT][TQ2],
                                            const typename Types<PREC>::W (*s_t)[LT][TQ2],
@@ -593,10 +629,10 @@ __device__ __forceinline__ void tma_tuples(const EvalParams &p, int c, int tb, i
     using T = Types<PREC>;
     using W = typename T::W;
     const int mp = T::stride(p.t);
-    for (int ti = tb; ti < te; ti += 2) {
-        const bool two = ti + 1 < te;
-        const DevTup t0 = p.t.tups[ti];
-        const DevTup t1 = p.t.tups[two ? ti + 1 : ti];
+    for (int ti = 0; ti < nt; ti += 2) {
+        const bool two = ti + 1 < nt;
+        const DevTup t0 = stup[ti];
+        const DevTup t1 = stup[two ? ti + 1 : ti];
         W w0, w1;
         uint32_t c0[2] = {0, 0}, c1[2] = {0, 0};
         const int32_t r0 = tma_probe<PREC, K>(t0, p.t.slots, tid, s_cell, s_t, wb, w0, c0);
@@ -622,6 +658,10 @@ __device__ __forceinline__ void tma_tuples(const EvalParams &p, int c, int tb, i
     }
 }
 
+// Per evaluated component i, one TMA stage delivers into buffer i % 2:
+//   [0, 96)                         the component struct,
+//   [128, 128 + 32*TMA_TUP_MAX)     its level tuples (those the form evaluates),
+//   [128 + 32*TMA_TUP_MAX, ...)     its surplus rows (one contiguous row range).
 template <int PREC, int MC, bool HC>
 __global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, int buf_bytes) {
     using T = Types<PREC>;
@@ -631,10 +671,13 @@ __global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, in
     auto s_cell = reinterpret_cast<uint16_t (*)[LT][TQ2]>(smem + 128);
     auto s_t = reinterpret_cast<W (*)[LT][TQ2]>(smem + 128 + sizeof(uint16_t) * 2 * LT * TQ2);
     unsigned char *bufbase = smem + tma_fixed_smem<PREC>();
-    W *buf[2] = {reinterpret_cast<W *>(bufbase), reinterpret_cast<W *>(bufbase + buf_bytes)};
+    unsigned char *buf[2] = {bufbase, bufbase + buf_bytes};
+    constexpr int kTupOff = 128;
+    constexpr int kRowOff = 128 + TMA_TUP_MAX * (int)sizeof(DevTup);
 
     const int tid = threadIdx.x;
     const int64_t q = (int64_t)blockIdx.x * TQ2 + tid;
+    const int64_t qc = q < p.n ? q : p.n - 1;   // clamped index for prefetch loads
     const int m0 = blockIdx.y * MC;
     const int m = p.m;
     const bool valid = q < p.n;
@@ -645,21 +688,16 @@ __global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, in
     const W *galpha = T::alpha(p.t);
     const int mp = T::stride(p.t);
 
-    auto row_range = [&](int i, int32_t &r0, uint32_t &bytes) {
-        const DevComp &cd = p.t.comps[list[i]];
-        r0 = paper ? cd.row_begin : cd.row_int;
-        bytes = (uint32_t)((int64_t)(cd.row_end - r0) * mp * (int64_t)sizeof(W));
-    };
     auto issue = [&](int i, int b) {  // thread 0 only
-        int32_t r0;
-        uint32_t bytes;
-        row_range(i, r0, bytes);
-        if (bytes) {
-            mbar_expect_tx(&bar[b], bytes);
-            tma_bulk_g2s(buf[b], galpha + (int64_t)r0 * mp, bytes, &bar[b]);
-        } else {
-            mbar_arrive(&bar[b]);
-        }
+        const DevComp &cd = p.t.comps[list[i]];
+        const int32_t r0 = paper ? cd.row_begin : cd.row_int;
+        const int tb = paper ? cd.tup_begin : cd.tup_int;
+        const uint32_t rbytes = (uint32_t)((int64_t)(cd.row_end - r0) * mp * (int64_t)sizeof(W));
+        const uint32_t tbytes = (uint32_t)((cd.tup_end - tb) * (int)sizeof(DevTup));
+        mbar_expect_tx(&bar[b], (uint32_t)sizeof(DevComp) + tbytes + rbytes);
+        tma_bulk_g2s(buf[b], &cd, (uint32_t)sizeof(DevComp), &bar[b]);
+        if (tbytes) tma_bulk_g2s(buf[b] + kTupOff, p.t.tups + tb, tbytes, &bar[b]);
+        if (rbytes) tma_bulk_g2s(buf[b] + kRowOff, galpha + (int64_t)r0 * mp, rbytes, &bar[b]);
     };
 
     if (tid == 0) {
@@ -678,6 +716,15 @@ __global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, in
     uint64_t h = 0;
     int32_t cnt = 0;
     bool failed = false;
+    int staged0 = -1;              // dimension currently held in staging slot 0
+    const int lmax_all = p.t.max_level < LT ? p.t.max_level : LT;
+    // prefetch of the next component's second coordinate
+    uint64_t Xnext = 0;
+    int dnext = -1;
+    if (nproc > 0) {
+        const DevComp &c0 = p.t.comps[list[0]];
+        if (c0.k == 2) { dnext = c0.dims[1]; Xnext = p.X[(int64_t)dnext * p.n + qc]; }
+    }
     for (int i = 0; i < nproc; ++i) {
         const int b = i & 1;
         const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((i >> 1) & 1));
@@ -690,26 +737,30 @@ __global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, in
             if (i + 1 < nproc) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((i + 1) >> 1) & 1));
             break;
         }
+        const DevComp &cd = *reinterpret_cast<const DevComp *>(buf[b]);
         const int c = list[i];
-        const DevComp &cd = p.t.comps[c];
+        const int k = cd.k;
+        const uint64_t Xb = Xnext;
+        // prefetch the coordinate the next component needs in staging slot 1
+        if (i + 1 < nproc) {
+            const DevComp &cn = p.t.comps[list[i + 1]];
+            if (cn.k == 2) { dnext = cn.dims[1]; Xnext = p.X[(int64_t)dnext * p.n + qc]; }
+        }
         if (!bad) {
-            const int k = cd.k;
-            for (int j = 0; j < k; ++j) {
-                const uint64_t Xv = p.X[(int64_t)cd.dims[j] * p.n + q];
-                const int lm = cd.lmax[j];
-                for (int l = 1; l <= lm; ++l) {
-                    Basis1D o;
-                    const bool act = basis1d(Xv, l, o);
-                    s_cell[j][l - 1][tid] = act ? (uint16_t)o.cell : (uint16_t)0x8000u;
-                    s_t[j][l - 1][tid] = basis_val<W>(o);
-                }
+            if (k >= 1 && cd.dims[0] != staged0) {
+                tma_stage<PREC>(p.X[(int64_t)cd.dims[0] * p.n + q], k == 1 ? cd.lmax[0] : lmax_all, tid, s_cell, s_t, 0);
+                staged0 = k == 1 ? -1 : cd.dims[0];
             }
+            if (k == 2) tma_stage<PREC>(Xb, cd.lmax[1], tid, s_cell, s_t, 1);
             const int tb = paper ? cd.tup_begin : cd.tup_int;
+            const int nt = cd.tup_end - tb;
             const int32_t row0 = paper ? cd.row_begin : cd.row_int;
             const W wb = paper ? (W)cd.b : (W)1;
-            if (k == 2) tma_tuples<PREC, MC, HC, 2>(p, c, tb, cd.tup_end, wb, m0, tid, s_cell, s_t, buf[b], row0, r.partial(), h, cnt);
-            else if (k == 1) tma_tuples<PREC, MC, HC, 1>(p, c, tb, cd.tup_end, wb, m0, tid, s_cell, s_t, buf[b], row0, r.partial(), h, cnt);
-            else tma_tuples<PREC, MC, HC, 0>(p, c, tb, cd.tup_end, wb, m0, tid, s_cell, s_t, buf[b], row0, r.partial(), h, cnt);
+            const DevTup *stup = reinterpret_cast<const DevTup *>(buf[b] + kTupOff);
+            const W *srow = reinterpret_cast<const W *>(buf[b] + kRowOff);
+            if (k == 2) tma_tuples<PREC, MC, HC, 2>(p, c, stup, nt, wb, m0, tid, s_cell, s_t, srow, row0, r.partial(), h, cnt);
+            else if (k == 1) tma_tuples<PREC, MC, HC, 1>(p, c, stup, nt, wb, m0, tid, s_cell, s_t, srow, row0, r.partial(), h, cnt);
+            else tma_tuples<PREC, MC, HC, 0>(p, c, stup, nt, wb, m0, tid, s_cell, s_t, srow, row0, r.partial(), h, cnt);
             r.fold();
         }
         __syncthreads();  // everyone is done with buf[b]
@@ -734,7 +785,7 @@ static cudaError_t launch_mc(const EvalParams &p, int kernel, bool hc, cudaStrea
     if (kernel == 2) {
         const int prec = PREC;
         const int64_t stage = p.t.stage_bytes[p.form][prec];
-        const int buf = (int)((stage + 127) & ~127ll);
+        const int buf = tma_buf_bytes(stage);
         const int smem = tma_fixed_smem<PREC>() + 2 * buf;
         dim3 grid2((unsigned)((p.n + TQ2 - 1) / TQ2), (unsigned)((p.m + MC - 1) / MC));
         if (hc) {
