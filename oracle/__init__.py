@@ -91,7 +91,15 @@ def _declare(L):
 
 
 def _declare_irbc(L):
-    pass  # filled in by irbc.py when present
+    L.orc_irbc_params.restype = None
+    L.orc_irbc_params.argtypes = [C.c_int, _d, _d, _d, _d, _p, _p, _p]
+    L.orc_monomial_nodes.restype = None
+    L.orc_monomial_nodes.argtypes = [C.c_int, _p, _p]
+    L.orc_irbc_residual.restype = None
+    L.orc_irbc_residual.argtypes = [C.c_int, _p, _p, _p, C.c_int, _p, _p, _p, _p, _p, _p, _p, _p,
+                                    _p, C.c_int, _i64, _p, _p, _p, _p]
+    L.orc_lu_solve.restype = C.c_int
+    L.orc_lu_solve.argtypes = [C.c_int, _p, _p]
 
 
 def ptr(a):
@@ -368,3 +376,121 @@ def sg_point_count(d: int, level: int) -> int:
                     new[a + e] += ca * ne
         poly = new
     return sum(poly)
+
+
+# ---------------------------------------------------------------------------
+# IRBC model (Sec. 2.1): parameters, monomial rule, residuals, Newton
+# ---------------------------------------------------------------------------
+
+IRBC_TABLE1 = dict(beta=0.99, alpha=0.36, delta=0.01, sigma=0.01, rho=0.95, phi=0.5)
+IRBC_A_GAMMA = 0.25     # the undefined "a" of Table 1's gamma_j (reading)
+
+
+class IRBCOracle:
+    """Smooth IRBC equilibrium conditions (eq. model1, model2) at given states,
+    with the policy interpolated from an OracleDDSG over x = (a, k)."""
+
+    def __init__(self, N: int, lo=0.8, hi=1.2, **overrides):
+        self.N = N
+        p = dict(IRBC_TABLE1)
+        p.update(overrides)
+        self.p = p
+        A = C.c_double()
+        self.gamma = np.zeros(N)
+        self.tau = np.zeros(N)
+        lib().orc_irbc_params(N, IRBC_A_GAMMA, p["beta"], p["alpha"], p["delta"], C.byref(A),
+                              ptr(self.gamma), ptr(self.tau))
+        self.A = A.value
+        self.prm = np.array([p["beta"], p["alpha"], p["delta"], p["sigma"], p["rho"], p["phi"],
+                             self.A, 0.0])
+        self.lo, self.hi = lo, hi
+
+    def steady_lambda(self):
+        """lambda* with sum_j (lambda/tau_j)^(-gamma_j) = N (A - delta), by bisection
+        (the deterministic steady state k = k' = 1, a = 1 of eq. model2)."""
+        target = self.N * (self.A - self.p["delta"])
+        f = lambda lam: np.sum((lam / self.tau) ** (-self.gamma)) - target
+        lo, hi = 1e-8, 1e8
+        for _ in range(400):
+            mid = np.sqrt(lo * hi)
+            if f(mid) > 0:
+                lo = mid
+            else:
+                hi = mid
+        return np.sqrt(lo * hi)
+
+    def monomial(self, n=None):
+        n = self.N + 1 if n is None else n
+        nodes = np.zeros((2 * n, n))
+        w = np.zeros(2 * n)
+        lib().orc_monomial_nodes(n, ptr(nodes), ptr(w))
+        return nodes, w
+
+    def residual(self, E: OracleDDSG, states, guess, form=1, want_err=False):
+        t = E.tables()
+        states = np.ascontiguousarray(states, np.float64).reshape(-1, 2 * self.N)
+        guess = np.ascontiguousarray(guess, np.float64).reshape(-1, self.N + 1)
+        ns = states.shape[0]
+        r = np.zeros((ns, self.N + 1))
+        ee = np.zeros((ns, 2)) if want_err else None
+        b = E.b_coeffs()
+        lib().orc_irbc_residual(self.N, ptr(self.prm), ptr(self.gamma), ptr(self.tau),
+                                len(E.comps), ptr(t["k"]), ptr(t["dims"]), ptr(t["off"]),
+                                ptr(t["lv"]), ptr(t["ix"]), ptr(t["alpha"]), ptr(b), ptr(E.lo),
+                                ptr(E.hi), int(form), ns, ptr(states), ptr(guess), ptr(r), ptr(ee))
+        return (r, ee) if want_err else r
+
+    def newton(self, E, states, guess, form=1, tol=1e-10, max_it=30, fd=1e-7):
+        """Per-state FP64 Newton: forward-difference Jacobian, dense LU with
+        partial pivoting, backtracking on ||r||_2. Returns (solution, iterations,
+        final residual norms)."""
+        states = np.atleast_2d(states)
+        sol = np.array(np.atleast_2d(guess), dtype=np.float64)
+        its = np.zeros(states.shape[0], np.int32)
+        norms = np.zeros(states.shape[0])
+        n = self.N + 1
+        for s in range(states.shape[0]):
+            z = sol[s].copy()
+            r = self.residual(E, states[s:s + 1], z[None], form)[0]
+            for it in range(max_it):
+                if np.max(np.abs(r)) <= tol:
+                    break
+                J = np.zeros((n, n))
+                for j in range(n):
+                    h = fd * max(1.0, abs(z[j]))
+                    zp = z.copy()
+                    zp[j] += h
+                    J[:, j] = (self.residual(E, states[s:s + 1], zp[None], form)[0] - r) / h
+                dz = -r.copy()
+                Jc = np.ascontiguousarray(J)
+                if lib().orc_lu_solve(n, ptr(Jc), ptr(dz)) != 0:
+                    break
+                step = 1.0
+                nr = np.linalg.norm(r)
+                while step > 1e-4:
+                    zt = z + step * dz
+                    rt = self.residual(E, states[s:s + 1], zt[None], form)[0]
+                    if np.linalg.norm(rt) < nr:
+                        break
+                    step *= 0.5
+                z, r = zt, rt
+                its[s] = it + 1
+            sol[s] = z
+            norms[s] = np.max(np.abs(r))
+        return sol, its, norms
+
+
+def irbc_policy_ddsg(N: int, level: int, value_fn, lo=0.8, hi=1.2, pairs=True):
+    """Policy expansion over x = (a_1..a_N, k_1..k_N): the empty component, all
+    2N single dimensions and (optionally) the N pairs (a_j, k_j), each a regular
+    level-`level` grid, hierarchized from value_fn(dims, phys_coords)."""
+    d = 2 * N
+    E = OracleDDSG(d, N + 1, lo=np.full(d, lo), hi=np.full(d, hi))
+    comps = [()] + [(i,) for i in range(d)]
+    if pairs:
+        comps += [(j, N + j) for j in range(N)]
+    for u in comps:
+        E.add_regular(u, level)
+    E.fill_values(value_fn)
+    E.hierarchize()
+    return E

@@ -156,20 +156,25 @@ def irbc_states(seed: int, n: int, n_countries: int) -> np.ndarray:
 
 def irbc_policy_perturbation(seed: int, n_countries: int):
     """Coefficients of a smooth seeded perturbation of the constant policy:
-    returns (amp, freq) arrays of shape (N+1, 2N), amp ~ U[-1,1]*1e-2/(2N),
-    freq ~ U[0.5, 2]."""
+    returns (amp, freq, amp2): amp, freq of shape (N+1, 2N) with
+    amp ~ U[-1,1]*1e-2/(2N), freq ~ U[0.5, 2]; amp2 of shape (N+1, N),
+    ~ U[-1,1]*1e-2, weights of the pairwise terms in (a_j, k_j)."""
     N = n_countries
     amp = (uniform_matrix(seed + 5000, N + 1, 2 * N) * 2.0 - 1.0) * (1e-2 / (2 * N))
     freq = uniform_matrix(seed + 6000, N + 1, 2 * N, 0.5, 2.0)
-    return amp, freq
+    amp2 = (uniform_matrix(seed + 7000, N + 1, N) * 2.0 - 1.0) * 1e-2
+    return amp, freq, amp2
 
 
-def irbc_policy_values(base: np.ndarray, amp: np.ndarray, freq: np.ndarray, dims,
-                       coords_phys: np.ndarray) -> np.ndarray:
-    """Synthetic policy p(x) = base + sum_i amp[:, i] * sin(freq[:, i] * (x_i - 1)),
-    evaluated where only coordinates `dims` differ from the anchor (x_i = 1 at
-    the anchor, so the other terms vanish). coords_phys: (n, len(dims)) in
-    physical units. Returns (n, N+1)."""
+def irbc_policy_values(base: np.ndarray, pert, dims, coords_phys: np.ndarray) -> np.ndarray:
+    """Synthetic policy over x = (a_1..a_N, k_1..k_N):
+        p(x) = base + sum_i amp[:, i] sin(freq[:, i] (x_i - 1))
+                    + sum_j amp2[:, j] sin(8 (a_j - 1)) sin(8 (k_j - 1)),
+    evaluated where only the coordinates `dims` differ from the anchor (x = 1
+    there, so every other term vanishes). pert = (amp, freq, amp2) from
+    irbc_policy_perturbation. coords_phys: (n, len(dims)). Returns (n, N+1)."""
+    amp, freq, amp2 = pert
+    N = amp2.shape[1]
     coords_phys = np.asarray(coords_phys, dtype=np.float64)
     if coords_phys.ndim == 1:
         coords_phys = coords_phys.reshape(-1, len(dims))
@@ -177,4 +182,9 @@ def irbc_policy_values(base: np.ndarray, amp: np.ndarray, freq: np.ndarray, dims
     y = np.repeat(np.asarray(base, dtype=np.float64)[None, :], n, axis=0)
     for a, dim in enumerate(dims):
         y += amp[None, :, dim] * np.sin(freq[None, :, dim] * (coords_phys[:, a:a + 1] - 1.0))
+    pos = {dim: a for a, dim in enumerate(dims)}
+    for j in range(N):
+        if j in pos and N + j in pos:
+            y += amp2[None, :, j] * (np.sin(8.0 * (coords_phys[:, pos[j]:pos[j] + 1] - 1.0)) *
+                                     np.sin(8.0 * (coords_phys[:, pos[N + j]:pos[N + j] + 1] - 1.0)))
     return y
