@@ -41,6 +41,10 @@ WORKLOADS = {
                 queries="monomial", precision="f64", form="slicefree"),
     "sg4": dict(d=4, m=3, order=4, eps=None, level=5, Q=100_000, wid=synth.W_SG4,
                 queries="uniform", precision="f64", form="paper"),
+    # IRBC Euler-residual sweep: N = 150 (d = 300, m = 151), policy = empty + 300 singles +
+    # 150 (a_j, k_j) pairs on regular level-4 grids; 1e4 states x 302 monomial nodes
+    "irbc150": dict(d=300, m=151, N=150, level=4, states=10_000, wid=synth.W_IRBC150,
+                    precision="f32c", form="slicefree"),
 }
 
 FP32_LANES_PER_SM = 128
@@ -207,6 +211,133 @@ def run_reference(args, w):
 
 
 # ---------------------------------------------------------------------------
+# IRBC Euler-residual sweep (CUDA arm, and the oracle as the reference arm)
+# ---------------------------------------------------------------------------
+
+def irbc_workload(w, G=None):
+    """Table 1 model, synthetic policy (steady state + seeded perturbation),
+    states and the initial guess (k' = k, lambda = lambda*)."""
+    import paper_2202_06555_gb300 as GG
+    G = G or GG
+    N, level = w["N"], w["level"]
+    t1 = G.irbc_table1(N)
+    lam = synth.irbc_steady_lambda(t1["gamma"], t1["tau"], t1["A"], t1["delta"])
+    base = np.concatenate([np.ones(N), [lam]])
+    pert = synth.irbc_policy_perturbation(synth.BASE_SEED + w["wid"], N)
+    fn = lambda dims, X: synth.irbc_policy_values(base, pert, dims, X)
+    comps = [()] + [(i,) for i in range(2 * N)] + [(j, N + j) for j in range(N)]
+    S = synth.irbc_states(synth.BASE_SEED + w["wid"], w["states"], N)
+    g = np.ascontiguousarray(np.concatenate([S[:, N:], np.full((S.shape[0], 1), lam)], 1))
+    return t1, lam, fn, comps, S, g
+
+
+def run_irbc(args, w):
+    N, m, d = w["N"], w["m"], w["d"]
+    nq = 2 * (N + 1)
+    metric = METRIC
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return 0
+        import oracle as O
+        t1, lam, fn, comps, S, g = irbc_workload(w)
+        E = O.irbc_policy_ddsg(N, w["level"], fn)
+        I = O.IRBCOracle(N)
+        for _ in range(args.warmup):
+            I.residual(E, S[:1], g[:1])
+        per = 4
+        times = []
+        for s in range(args.steps):
+            t0 = time.perf_counter()
+            I.residual(E, S[s * per:(s + 1) * per], g[s * per:(s + 1) * per])
+            times.append(time.perf_counter() - t0)
+        ms = 1e3 * statistics.mean(times)
+        value = per * nq * m / (ms * 1e-3)
+        print(json.dumps({"impl": "reference", "metric": metric, "value": value, "unit": "evals/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "irbc150_euler_residual", "states_per_step": per},
+                          "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1,
+                                           "kind": "oracle", "sample": f"{per} states per step"},
+                          "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return 0
+    import torch
+    import paper_2202_06555_gb300 as G
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    G.load()
+    t1, lam, fn, comps, S, g = irbc_workload(w, G)
+    h = G.HDMR(d, m, 2, lo=np.full(d, 0.8), hi=np.full(d, 1.2))
+    for u in comps:
+        h.add_regular(list(u), w["level"])
+    vals = np.concatenate([fn(u, h.component_points(c)[2]) for c, u in enumerate(comps)])
+    h.hierarchize(torch.from_numpy(vals).cuda())
+    M = G.IRBC(**t1)
+    prec = G.F32C if w["precision"] == "f32c" else G.F64
+    form = G.FORM_SLICEFREE if w["form"] == "slicefree" else G.FORM_PAPER
+    ns = S.shape[0]
+    sd = torch.from_numpy(S).cuda()
+    gd = torch.from_numpy(g).cuda()
+    r = torch.empty((ns, N + 1), dtype=torch.float64, device="cuda")
+    nt = min(ns * nq, 65536)
+    xt = torch.from_numpy(np.ascontiguousarray(np.repeat(S[:nt // nq + 1, :], nq, 0)[:nt])).cuda()
+    yt = torch.empty((nt, m), dtype=torch.float64, device="cuda")
+    tuned = h.autotune(xt, yt, prec, form)
+    for _ in range(args.warmup):
+        M.residual(h, sd, gd, r, None, None, prec, form)
+    torch.cuda.synchronize()
+    h.profile(True)
+    h.profile_read(reset=True)
+    stream = torch.cuda.current_stream()
+    with ClockSampler(None) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            M.residual(h, sd, gd, r, None, None, prec, form)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    prof = h.profile_read(reset=True)
+    h.profile(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    value = ns * nq * m / (ms * 1e-3)
+    # Newton from the initial guess, FP64 vs F32C interpolation, same tolerance
+    newton = {}
+    for name, pr, tol in (("f64", G.F64, 1e-9), ("f32c", G.F32C, 1e-6)):
+        z = gd.clone()
+        it = torch.zeros(ns, dtype=torch.int32, device="cuda")
+        st = torch.zeros(ns, dtype=torch.int32, device="cuda")
+        nr = torch.zeros(ns, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        M.newton(h, sd, z, 12, tol, it, st, nr, pr, form)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        err = torch.zeros((ns, 2), dtype=torch.float64, device="cuda")
+        M.residual(h, sd, z, r, None, err, G.F64, form)
+        ee = err.cpu().numpy()
+        newton[name] = {"seconds": dt, "tol": tol, "iters_mean": float(it.double().mean().item()),
+                        "iters_max": int(it.max().item()),
+                        "converged": int((st == 0).sum().item()),
+                        "euler_error_log10_mean": float(np.log10(np.mean(ee[:, 0]))),
+                        "euler_error_log10_max": float(np.log10(np.max(ee[:, 0])))}
+    out = {"metric": metric, "value": value, "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32" if prec == G.F32C else "f64", "data": "synthetic",
+           "config": {"workload": "irbc150_euler_residual", "N": N, "d": d, "m": m,
+                      "states": ns, "nodes": nq, "evals_per_sweep": ns * nq,
+                      "policy": "empty + 2N singles + N (a_j,k_j) pairs, regular level 4",
+                      "precision": w["precision"], "form": w["form"],
+                      "schedule": {"kernel": ["tile", "per-tuple", "tma-staged tile"][tuned[0]],
+                                   "outputs_per_pass": tuned[1]}},
+           "kernels_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
+           "gpu_launches": sum(v[1] for v in prof.values()),
+           "newton": newton, "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # CUDA arm
 # ---------------------------------------------------------------------------
 
@@ -231,6 +362,8 @@ def main():
     if args.queries:
         w["Q"] = args.queries
     args.warmup = max(args.warmup, 3) if args.impl == "ddsg" else args.warmup
+    if args.workload == "irbc150":
+        return run_irbc(args, w)
     if args.impl == "reference":
         return run_reference(args, w)
 

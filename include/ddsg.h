@@ -269,6 +269,65 @@ int hdmr_profile(hdmr_t *h, int enable);
 int hdmr_profile_read(hdmr_t *h, double *ms_host /* DDSG_NKINDS */,
                       int64_t *launches_host /* DDSG_NKINDS */, int reset);
 
+/* ------------------------------------------------------------------------
+ * IRBC model step (Sec. 2.1): Euler equations (eq. model1), aggregate
+ * resource constraint (eq. model2), productivity law of motion (eq.
+ * law_of_motion); expectation by a degree-3 monomial rule over the N+1
+ * shocks (2(N+1) nodes +-sqrt(N+1) e_i, equal weights).
+ * ------------------------------------------------------------------------ */
+typedef struct irbc irbc_t;
+
+/* Table 1 values (beta, alpha, delta, sigma, rho, phi) and the aggregate
+ * productivity A = (1 - beta (1 - delta)) / (alpha beta); N countries. */
+typedef struct {
+    int32_t N;
+    double beta, alpha, delta, sigma, rho, phi, A;
+} irbc_params_t;
+
+/* New model; gamma_host, tau_host (length N, Table 1's gamma_j and tau_j) are
+ * copied. Makes no CUDA call. */
+int irbc_create(const irbc_params_t *prm, const double *gamma_host, const double *tau_host,
+                irbc_t **out);
+int irbc_destroy(irbc_t *model);
+
+/*
+ * euler_residual -- residuals at ns states for the policy guess.
+ *   policy: hierarchized hdmr_t over x = (a_1..a_N, k_1..k_N) (d = 2N) with
+ *           m = N+1 outputs (k'_1..k'_N, lambda); its domain clamps next states.
+ *   states_dev: ns x 2N, guess_dev: ns x (N+1) (k', lambda), resid_dev: ns x (N+1)
+ *           (rows j < N: eq. model1 of country j+1; row N: eq. model2).
+ *   jac_dev (nullable): ns x (N+1) x (N+1), row-major d resid / d guess, from the
+ *           hat slopes (right derivative at kinks, zero where k'_i is clamped)
+ *           and the chain rule. Needs every policy component that holds k_i to
+ *           be {k_i} or {a_i, k_i} (DDSG_ERR_ARG otherwise).
+ *   euler_err_dev (nullable): ns x 2, unit-free Euler error per state:
+ *           max_j |beta E_j / (lambda (1 + phi g_j)) - 1| and |resource| / sum_j Y_j.
+ *   precision/form: those of hdmr_eval for the policy interpolation; residual
+ *   arithmetic is FP64. Asynchronous on `stream`; uses a model workspace
+ *   (cudaMalloc, up to ~2 GiB; states are processed in chunks).
+ */
+int euler_residual(irbc_t *model, hdmr_t *policy, int64_t ns, const double *states_dev,
+                   const double *guess_dev, double *resid_dev, double *jac_dev,
+                   double *euler_err_dev, int precision, int form, ddsg_stream_t stream);
+
+/* Batched dense LU with partial pivoting (FP64): dx = -A^{-1} r for ns
+ * systems of size n (A_dev ns x n x n row-major, r_dev/dx_dev ns x n).
+ * status_dev[s] is set to 2 for an exactly singular pivot. n <= 165. */
+int irbc_lu_solve(int n, int64_t ns, const double *A_dev, const double *r_dev, double *dx_dev,
+                  int32_t *status_dev, ddsg_stream_t stream);
+
+/*
+ * irbc_newton -- per-state FP64 Newton on the residuals of euler_residual:
+ * analytic Jacobian, LU solve, backtracking on ||r||_2 (halving up to 11
+ * times). sol_dev (ns x (N+1)) holds the initial guess and receives the
+ * solution. Stops a state when ||r||_inf <= tol. Outputs (nullable):
+ * iters_dev, status_dev (0 converged, 1 max_it reached, 2 singular Jacobian),
+ * resnorm_dev (final ||r||_inf). Synchronizes `stream` between iterations.
+ */
+int irbc_newton(irbc_t *model, hdmr_t *policy, int64_t ns, const double *states_dev,
+                double *sol_dev, int max_it, double tol, int32_t *iters_dev, int32_t *status_dev,
+                double *resnorm_dev, int precision, int form, ddsg_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,11 @@ SIGNATURES = {
     "hdmr_autotune": (_int, [_p, _i64, _p, _p, _int, _int, _p, C.POINTER(_d)]),
     "hdmr_eval_noalloc": (_int, [_p, _i64, _p, _p, _int, _int, _p]),
     "hdmr_eval_noalloc_capacity": (_i64, [_int]),
+    "irbc_create": (_int, [_p, _p, _p, C.POINTER(_p)]),
+    "irbc_destroy": (_int, [_p]),
+    "euler_residual": (_int, [_p, _p, _i64, _p, _p, _p, _p, _p, _int, _int, _p]),
+    "irbc_lu_solve": (_int, [_int, _i64, _p, _p, _p, _p, _p]),
+    "irbc_newton": (_int, [_p, _p, _i64, _p, _p, _int, _d, _p, _p, _p, _int, _int, _p]),
     "hdmr_profile_read": (_int, [_p, _p, _p, _int]),
 }
 
@@ -304,3 +309,70 @@ def build_adaptive(h: HDMR, value_fn, eps_gamma: float, max_level: int, strict: 
         if h.refine(eps_gamma, max_level, strict, stream) == 0:
             break
     return np.concatenate(vals)
+
+
+class IrbcParams(C.Structure):
+    _fields_ = [("N", C.c_int32), ("beta", C.c_double), ("alpha", C.c_double),
+                ("delta", C.c_double), ("sigma", C.c_double), ("rho", C.c_double),
+                ("phi", C.c_double), ("A", C.c_double)]
+
+
+class IRBC:
+    """Smooth IRBC model step (Sec. 2.1) over a policy HDMR: residuals,
+    Jacobian and batched Newton (see include/ddsg.h)."""
+
+    def __init__(self, N: int, beta: float, alpha: float, delta: float, sigma: float, rho: float,
+                 phi: float, A: float, gamma, tau):
+        lib = load()
+        self.N = int(N)
+        self.prm = IrbcParams(self.N, beta, alpha, delta, sigma, rho, phi, A)
+        g = np.ascontiguousarray(gamma, np.float64)
+        t = np.ascontiguousarray(tau, np.float64)
+        h = C.c_void_p()
+        _check(lib.irbc_create(C.byref(self.prm), _np_ptr(g), _np_ptr(t), C.byref(h)), "irbc_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().irbc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def residual(self, policy: HDMR, states_dev, guess_dev, resid_dev, jac_dev=None, err_dev=None,
+                 precision: int = F64, form: int = FORM_SLICEFREE, stream=None):
+        _check(load().euler_residual(self._h, policy._h, states_dev.shape[0], _dev_ptr(states_dev),
+                                     _dev_ptr(guess_dev), _dev_ptr(resid_dev), _dev_ptr(jac_dev),
+                                     _dev_ptr(err_dev), int(precision), int(form), _stream_ptr(stream)),
+               "euler_residual")
+
+    def newton(self, policy: HDMR, states_dev, sol_dev, max_it: int = 30, tol: float = 1e-10,
+               iters_dev=None, status_dev=None, resnorm_dev=None, precision: int = F64,
+               form: int = FORM_SLICEFREE, stream=None):
+        _check(load().irbc_newton(self._h, policy._h, states_dev.shape[0], _dev_ptr(states_dev),
+                                  _dev_ptr(sol_dev), int(max_it), float(tol), _dev_ptr(iters_dev),
+                                  _dev_ptr(status_dev), _dev_ptr(resnorm_dev), int(precision),
+                                  int(form), _stream_ptr(stream)), "irbc_newton")
+
+
+def lu_solve(A_dev, r_dev, dx_dev, status_dev, stream=None):
+    ns, n = r_dev.shape
+    _check(load().irbc_lu_solve(n, ns, _dev_ptr(A_dev), _dev_ptr(r_dev), _dev_ptr(dx_dev),
+                                _dev_ptr(status_dev), _stream_ptr(stream)), "irbc_lu_solve")
+
+
+def irbc_table1(N: int, a_gamma: float = 0.25, beta: float = 0.99, alpha: float = 0.36,
+                delta: float = 0.01, sigma: float = 0.01, rho: float = 0.95, phi: float = 0.5):
+    """Table 1 calibration: A = (1 - beta (1 - delta)) / (alpha beta),
+    gamma_j = a + 0.75 (j - 1)/(N - 1) (a = 0.25 by default; a for N = 1),
+    tau_j = A^(1/gamma_j). Returns the keyword arguments of IRBC()."""
+    A = (1.0 - beta * (1.0 - delta)) / (alpha * beta)
+    j = np.arange(N, dtype=np.float64)
+    gamma = a_gamma + 0.75 * j / (N - 1) if N > 1 else np.full(1, a_gamma)
+    tau = A ** (1.0 / gamma)
+    return dict(N=N, beta=beta, alpha=alpha, delta=delta, sigma=sigma, rho=rho, phi=phi, A=A,
+                gamma=gamma, tau=tau)

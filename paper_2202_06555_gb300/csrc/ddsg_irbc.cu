@@ -1,0 +1,794 @@
+// ddsg_irbc.cu -- smooth IRBC model step on the GPU (Sec. 2.1 of the paper):
+// Euler-equation residuals (eq. model1) and the aggregate resource constraint
+// (eq. model2) at a batch of states, with the expectation taken by a degree-3
+// monomial rule over the 2(N+1) shocks; an analytic Jacobian; and a batched
+// FP64 Newton solve with dense LU and backtracking.
+//
+// Pipeline of one residual sweep (states processed in chunks that fit the
+// model's workspace):
+//   irbc_queries_kernel   next state x' = (a', k') at every (state, node)
+//                         (eq. law_of_motion), encoded into the evaluation
+//                         kernels' dimension-major fixed-point layout;
+//   launch_eval           the policy interpolant at all x' (FP64 or F32C);
+//   irbc_residual_kernel  one block per state: node sums in FP64, residuals,
+//                         Euler errors and the Jacobian's border and diagonal
+//                         pieces;
+//   irbc_jacobian_kernel  one thread per column i < N: the policy's derivative
+//                         in k'_i enters through the components holding dim N+i
+//                         (the (a_i, k_i) pair and the k_i single), whose other
+//                         coordinate a'_i takes only three values over the nodes
+//                         (no shock, +shock, -shock).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "ddsg_internal.h"
+
+using namespace ddsg;
+
+namespace {
+
+struct IrbcDev {
+    int N;
+    double beta, alpha, delta, sigma, rho, phi, A;
+    const double *gamma, *tau;
+};
+
+// Encode one physical coordinate exactly like the query encoder.
+__device__ __forceinline__ uint64_t encode_coord(double v, double lo, double span, bool &bad,
+                                                 unsigned long long &clamps) {
+    double c = (v - lo) / span;
+    if (!isfinite(v) || !isfinite(c)) {
+        bad = true;
+        return X_NAN;
+    }
+    if (c < 0.0) { c = 0.0; ++clamps; }
+    if (c > 1.0) { c = 1.0; ++clamps; }
+    const double yv = c * 4611686018427387904.0;
+    uint64_t Xv = (uint64_t)yv;
+    if ((double)Xv != yv) Xv |= 1ull;
+    return Xv;
+}
+
+// Next-period productivity of country j at the three distinct node values:
+// no shock on j (e0), +sqrt(N+1) (ep), -sqrt(N+1) (em), as exp(rho ln a + sigma (e_j + e)).
+__device__ __forceinline__ void next_a3(const IrbcDev &P, double a, double &e0, double &ep, double &em) {
+    const double h = sqrt((double)(P.N + 1));
+    const double la = log(a);
+    e0 = exp(P.rho * la + P.sigma * (0.0 + 0.0));
+    ep = exp(P.rho * la + P.sigma * (h + 0.0));
+    em = exp(P.rho * la + P.sigma * (-h + 0.0));
+}
+
+// Which of the three values node q gives to country j (nodes 2i / 2i+1 shock
+// country i by +/-; nodes 2N / 2N+1 shock every country through the global shock).
+__device__ __forceinline__ int node_variant(int q, int j, int N) {
+    if (q == 2 * j || q == 2 * N) return 1;
+    if (q == 2 * j + 1 || q == 2 * N + 1) return 2;
+    return 0;
+}
+
+// One thread per (state, dimension): writes that coordinate for all nq nodes.
+__global__ void irbc_queries_kernel(IrbcDev P, int64_t ns, const double *__restrict__ states,
+                                    const double *__restrict__ guess, const double *__restrict__ lo,
+                                    const double *__restrict__ span, uint64_t *__restrict__ X,
+                                    int32_t *__restrict__ flags, unsigned long long *__restrict__ stats) {
+    const int N = P.N, d = 2 * N, m = N + 1, nq = 2 * (N + 1);
+    const int64_t Q = ns * nq;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long clamps = 0;
+    if (idx < ns * d) {
+        const int64_t s = idx / d;
+        const int dim = (int)(idx - s * d);
+        bool bad = false;
+        uint64_t *Xrow = X + (int64_t)dim * Q + s * nq;
+        if (dim < N) {
+            double v[3];
+            next_a3(P, states[s * d + dim], v[0], v[1], v[2]);
+            uint64_t e[3];
+            const unsigned long long mult[3] = {(unsigned long long)(nq - 4), 2ull, 2ull};  // nodes per value
+            for (int t = 0; t < 3; ++t) {
+                unsigned long long c1 = 0;
+                e[t] = encode_coord(v[t], lo[dim], span[dim], bad, c1);
+                clamps += c1 * mult[t];
+            }
+            for (int q = 0; q < nq; ++q) Xrow[q] = e[node_variant(q, dim, N)];
+            if (!isfinite(states[s * d + N + dim])) bad = true;
+        } else {
+            const uint64_t e = encode_coord(guess[s * m + dim - N], lo[dim], span[dim], bad, clamps);
+            clamps *= (unsigned long long)nq;
+            for (int q = 0; q < nq; ++q) Xrow[q] = e;
+            if (dim == d - 1 && !isfinite(guess[s * m + N])) bad = true;
+        }
+        if (bad)
+            for (int q = 0; q < nq; ++q) flags[s * nq + q] = 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) clamps += __shfl_down_sync(0xffffffffu, clamps, o);
+    if ((threadIdx.x & 31) == 0 && clamps) atomicAdd(&stats[0], clamps);
+}
+
+// Per state (block): residuals, Euler errors and Jacobian pieces.
+// aux (per state, 7 x N): S1, SM, Dd, e0, ep, em, kp^(alpha-1).
+__global__ void __launch_bounds__(256) irbc_residual_kernel(IrbcDev P, int64_t s0, int64_t nsc,
+                                                            const double *__restrict__ states,
+                                                            const double *__restrict__ guess,
+                                                            const double *__restrict__ y,
+                                                            double *__restrict__ resid,
+                                                            double *__restrict__ err,
+                                                            double *__restrict__ jac,
+                                                            double *__restrict__ aux) {
+    const int N = P.N, d = 2 * N, m = N + 1, nq = 2 * (N + 1);
+    const int64_t sl = blockIdx.x;           // state within the chunk
+    const int64_t s = s0 + sl;                // global state
+    const double *a = states + s * d;
+    const double *k = states + s * d + N;
+    const double *kp = guess + s * m;
+    const double lam = guess[s * m + N];
+    const double w = 1.0 / (double)nq;
+    const double *ys = y + sl * nq * (int64_t)m;
+    double res = 0.0, ysum = 0.0, emax = 0.0, dlam = 0.0;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double e3[3];
+        next_a3(P, a[j], e3[0], e3[1], e3[2]);
+        const double g1 = kp[j] / k[j] - 1.0;
+        const double kpa = pow(kp[j], P.alpha - 1.0);
+        double E = 0.0, S1 = 0.0, SM = 0.0, Dd = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            const double ap = e3[node_variant(q, j, N)];
+            const double kpp = ys[(int64_t)q * m + j];
+            const double lamp = ys[(int64_t)q * m + N];
+            const double g2 = kpp / kp[j] - 1.0;
+            const double Mq = ap * P.A * P.alpha * kpa + (1.0 - P.delta) + 0.5 * P.phi * g2 * (g2 + 2.0);
+            E += w * lamp * Mq;
+            if (jac) {
+                S1 += w * lamp * 0.5 * P.phi * (2.0 * g2 + 2.0) / kp[j];
+                SM += w * Mq;
+                Dd += w * lamp * (ap * P.A * P.alpha * (P.alpha - 1.0) * kpa / kp[j] +
+                                  0.5 * P.phi * (2.0 * g2 + 2.0) * (-kpp / (kp[j] * kp[j])));
+            }
+        }
+        const double lhs = lam * (1.0 + P.phi * g1);
+        resid[s * m + j] = lhs - P.beta * E;
+        emax = fmax(emax, fabs(P.beta * E / lhs - 1.0));
+        const double Y = a[j] * P.A * pow(k[j], P.alpha);
+        ysum += Y;
+        const double cj = pow(lam / P.tau[j], -P.gamma[j]);
+        res += Y + k[j] * ((1.0 - P.delta) - 0.5 * P.phi * g1 * g1) - kp[j] - cj;
+        if (jac) {
+            double *J = jac + s * (int64_t)m * m;
+            J[(int64_t)j * m + N] = 1.0 + P.phi * g1;        // d r_j / d lambda
+            J[(int64_t)N * m + j] = -(1.0 + P.phi * g1);     // d resource / d k'_j
+            dlam += P.gamma[j] * cj / lam;                   // d resource / d lambda
+            double *ax = aux + sl * 7 * (int64_t)N;
+            ax[0 * N + j] = S1;
+            ax[1 * N + j] = SM;
+            ax[2 * N + j] = lam * P.phi / k[j] - P.beta * Dd;  // diagonal part of d r_j / d k'_j
+            ax[3 * N + j] = e3[0];
+            ax[4 * N + j] = e3[1];
+            ax[5 * N + j] = e3[2];
+            ax[6 * N + j] = kpa;
+        }
+    }
+    // block reductions (sum / max) in a fixed order
+    __shared__ double red[4][256];
+    red[0][threadIdx.x] = res;
+    red[1][threadIdx.x] = ysum;
+    red[2][threadIdx.x] = emax;
+    red[3][threadIdx.x] = dlam;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + o];
+            red[1][threadIdx.x] += red[1][threadIdx.x + o];
+            red[2][threadIdx.x] = fmax(red[2][threadIdx.x], red[2][threadIdx.x + o]);
+            red[3][threadIdx.x] += red[3][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        resid[s * m + N] = red[0][0];
+        if (err) {
+            err[s * 2 + 0] = red[2][0];
+            err[s * 2 + 1] = fabs(red[0][0]) / red[1][0];
+        }
+        if (jac) jac[s * (int64_t)m * m + (int64_t)N * m + N] = red[3][0];
+    }
+}
+
+// Right derivative in c of hat (l, cell containing X): +-2^(l-1), 0 at level 1.
+__device__ __forceinline__ double dhat(uint64_t X, int l, uint32_t &cell) {
+    if (l == 1) { cell = 0; return 0.0; }
+    if (l == 2) {
+        cell = X >= (1ull << 61) ? 1u : 0u;
+        return cell ? 2.0 : -2.0;
+    }
+    const int sh = 64 - l;
+    uint64_t c = X >> sh;
+    const uint64_t nmax = (1ull << (l - 2)) - 1;
+    if (c > nmax) c = nmax;
+    cell = (uint32_t)c;
+    const uint64_t F = X - (c << sh);
+    const double mag = (double)(1ull << (l - 1));
+    return F < (1ull << (sh - 1)) ? mag : -mag;
+}
+
+// Terms of d p(x)/d x_dim for one component whose other dimension (if any)
+// sits at Xo: appends (device row, weight) pairs; weight includes b and 1/span.
+struct DTerm { int32_t row; double w; };
+
+__device__ int comp_dterms(const DevTables &t, int c, int dk, uint64_t Xk, uint64_t Xo, double scale,
+                           bool paper, DTerm *out, int cap) {
+    const DevComp &cd = t.comps[c];
+    const double b = paper ? cd.b : 1.0;
+    if (b == 0.0) return 0;
+    const int tb = paper ? cd.tup_begin : cd.tup_int;
+    int n = 0;
+    for (int ti = tb; ti < cd.tup_end && n < cap; ++ti) {
+        const DevTup tu = t.tups[ti];
+        uint32_t off = 0;
+        double wt = b * scale;
+        bool act = true;
+        for (int j = 0; j < cd.k; ++j) {
+            const int l = tu.lev[j];
+            if (j == dk) {
+                uint32_t cell;
+                const double sl = dhat(Xk, l, cell);
+                if (sl == 0.0) { act = false; break; }
+                wt *= sl;
+                off = off * (j == 1 ? tu.nc1 : ncells(l)) + cell;
+            } else {
+                Basis1D o;
+                if (!basis1d(Xo, l, o)) { act = false; break; }
+                wt *= (double)o.N * ldexp(1.0, -o.e);
+                off = off * (j == 1 ? tu.nc1 : ncells(l)) + o.cell;
+            }
+        }
+        if (!act) continue;
+        const int32_t row = tuple_row(tu, off, t.slots);
+        if (row < 0) continue;
+        out[n].row = row;
+        out[n].w = wt;
+        ++n;
+    }
+    return n;
+}
+
+constexpr int DT_CAP = 48;
+
+// One thread per column i < N of each state's Jacobian (d r_j / d k'_i, j < N).
+__global__ void __launch_bounds__(128) irbc_jacobian_kernel(IrbcDev P, int64_t s0, int64_t nsc,
+                                                            DevTables t, int form,
+                                                            const int32_t *__restrict__ kcomps,
+                                                            const double *__restrict__ lo,
+                                                            const double *__restrict__ span,
+                                                            const double *__restrict__ guess,
+                                                            const double *__restrict__ y,
+                                                            const double *__restrict__ aux,
+                                                            double *__restrict__ jac) {
+    const int N = P.N, m = N + 1, nq = 2 * (N + 1);
+    const int64_t sl = blockIdx.y;
+    const int64_t s = s0 + sl;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const bool paper = form == DDSG_FORM_PAPER;
+    const double *kp = guess + s * m;
+    const double *ax = aux + sl * 7 * (int64_t)N;
+    const double *ys = y + sl * nq * (int64_t)m;
+    double *J = jac + s * (int64_t)m * m;
+    const double w = 1.0 / (double)nq;
+    const int dk = N + i;
+    // k'_i in canonical units; clamped (or at the top face) -> zero derivative
+    const double ck = (kp[i] - lo[dk]) / span[dk];
+    const bool live = ck >= 0.0 && ck < 1.0;
+    // derivative terms at the three values of a'_i
+    DTerm terms[3][DT_CAP];
+    int nt[3] = {0, 0, 0};
+    if (live) {
+        bool bad = false;
+        unsigned long long cl = 0;
+        const uint64_t Xk = encode_coord(kp[i], lo[dk], span[dk], bad, cl);
+        for (int v = 0; v < 3; ++v) {
+            const uint64_t Xa = encode_coord(ax[(3 + v) * N + i], lo[i], span[i], bad, cl);
+            for (int cc = 0; cc < 2; ++cc) {
+                const int c = kcomps[2 * i + cc];
+                if (c < 0) continue;
+                const DevComp &cd = t.comps[c];
+                const int kdim = cd.k == 2 ? 1 : 0;   // (a_i, k_i): k_i is the second dim
+                nt[v] += comp_dterms(t, c, kdim, Xk, Xa, 1.0 / span[dk], paper, terms[v] + nt[v],
+                                     DT_CAP - nt[v]);
+            }
+        }
+    }
+    const int mp = t.mp64;
+    // node indices whose a'_i is shocked: +: 2i, 2N ; -: 2i+1, 2N+1
+    const int qp0 = 2 * i, qp1 = 2 * N, qm0 = 2 * i + 1, qm1 = 2 * N + 1;
+    double dPN[3];
+    for (int v = 0; v < 3; ++v) {
+        double acc = 0.0;
+        for (int e = 0; e < nt[v]; ++e) acc += terms[v][e].w * t.alpha64[(int64_t)terms[v][e].row * mp + N];
+        dPN[v] = acc;
+    }
+    for (int j = 0; j < N; ++j) {
+        double dP[3];
+        for (int v = 0; v < 3; ++v) {
+            double acc = 0.0;
+            for (int e = 0; e < nt[v]; ++e) acc += terms[v][e].w * t.alpha64[(int64_t)terms[v][e].row * mp + j];
+            dP[v] = acc;
+        }
+        // per-node coefficient pieces of the four shocked nodes
+        const double kpa = ax[6 * N + j];
+        double s1[4], sM[4];
+        const int qs[4] = {qp0, qp1, qm0, qm1};
+        for (int u = 0; u < 4; ++u) {
+            const int q = qs[u];
+            const double kpp = ys[(int64_t)q * m + j];
+            const double lamp = ys[(int64_t)q * m + N];
+            const double g2 = kpp / kp[j] - 1.0;
+            const double ap = ax[(3 + node_variant(q, j, N)) * N + j];
+            s1[u] = w * lamp * 0.5 * P.phi * (2.0 * g2 + 2.0) / kp[j];
+            sM[u] = w * (ap * P.A * P.alpha * kpa + (1.0 - P.delta) + 0.5 * P.phi * g2 * (g2 + 2.0));
+        }
+        // node qp0 == qp1 only when i == N (never); qp1/qm1 are shared by all columns
+        const double S1 = ax[0 * N + j], SM = ax[1 * N + j];
+        const double s1b = S1 - s1[0] - s1[1] - s1[2] - s1[3];
+        const double sMb = SM - sM[0] - sM[1] - sM[2] - sM[3];
+        const double v = -P.beta * (s1b * dP[0] + (s1[0] + s1[1]) * dP[1] + (s1[2] + s1[3]) * dP[2] +
+                                    sMb * dPN[0] + (sM[0] + sM[1]) * dPN[1] + (sM[2] + sM[3]) * dPN[2]);
+        J[(int64_t)j * m + i] = v + (j == i ? ax[2 * N + j] : 0.0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// batched dense LU with partial pivoting (FP64, one block per system)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) lu_solve_kernel(int n, int64_t ns, const double *__restrict__ Ag,
+                                                       const double *__restrict__ bg, const int32_t *active,
+                                                       double *__restrict__ xg, int32_t *__restrict__ status) {
+    extern __shared__ double sm[];
+    double *A = sm;             // n x n
+    double *b = sm + n * n;     // n
+    __shared__ int piv;
+    __shared__ double pval[256];
+    __shared__ int pidx[256];
+    const int64_t s = blockIdx.x;
+    if (active && !active[s]) return;
+    const double *As = Ag + s * (int64_t)n * n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = As[e];
+    for (int e = threadIdx.x; e < n; e += blockDim.x) b[e] = -bg[s * n + e];
+    __syncthreads();
+    bool singular = false;
+    for (int c = 0; c < n; ++c) {
+        // pivot: largest |A[r][c]| for r >= c (ties -> smallest r)
+        double best = -1.0;
+        int bi = c;
+        for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
+            const double v = fabs(A[r * n + c]);
+            if (v > best) { best = v; bi = r; }
+        }
+        pval[threadIdx.x] = best;
+        pidx[threadIdx.x] = bi;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                const double v2 = pval[threadIdx.x + o];
+                const int i2 = pidx[threadIdx.x + o];
+                if (v2 > pval[threadIdx.x] || (v2 == pval[threadIdx.x] && i2 < pidx[threadIdx.x])) {
+                    pval[threadIdx.x] = v2;
+                    pidx[threadIdx.x] = i2;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) piv = pidx[0];
+        __syncthreads();
+        const int p = piv;
+        if (!(pval[0] > 0.0)) { singular = true; break; }
+        if (p != c) {
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                const double tmp = A[c * n + j];
+                A[c * n + j] = A[p * n + j];
+                A[p * n + j] = tmp;
+            }
+            if (threadIdx.x == 0) {
+                const double tmp = b[c];
+                b[c] = b[p];
+                b[p] = tmp;
+            }
+        }
+        __syncthreads();
+        const double inv = 1.0 / A[c * n + c];
+        for (int r = c + 1 + threadIdx.x; r < n; r += blockDim.x) {
+            const double f = A[r * n + c] * inv;
+            A[r * n + c] = f;
+            for (int j = c + 1; j < n; ++j) A[r * n + j] -= f * A[c * n + j];
+            b[r] -= f * b[c];
+        }
+        __syncthreads();
+    }
+    if (singular) {
+        if (threadIdx.x == 0) status[s] = 2;
+        return;
+    }
+    // back substitution (one thread; n is small)
+    if (threadIdx.x == 0) {
+        for (int r = n - 1; r >= 0; --r) {
+            double acc = b[r];
+            for (int j = r + 1; j < n; ++j) acc -= A[r * n + j] * b[j];
+            b[r] = acc / A[r * n + r];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) xg[s * n + e] = b[e];
+}
+
+// ---------------------------------------------------------------------------
+// Newton helpers: norms, trial points, acceptance
+// ---------------------------------------------------------------------------
+
+__global__ void norms_kernel(int n, int64_t ns, const double *__restrict__ r, double *__restrict__ n2,
+                             double *__restrict__ ninf) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    double a = 0.0, b = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double v = r[s * n + j];
+        a += v * v;
+        b = fmax(b, fabs(v));
+        if (!isfinite(v)) { a = INFINITY; b = INFINITY; }
+    }
+    n2[s] = sqrt(a);
+    ninf[s] = b;
+}
+
+__global__ void trial_kernel(int n, int64_t ns, const double *__restrict__ z, const double *__restrict__ dz,
+                             const double *__restrict__ step, const int32_t *__restrict__ active,
+                             double *__restrict__ zt) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ns * n) return;
+    const int64_t s = e / n;
+    zt[e] = active[s] ? z[e] + step[s] * dz[e] : z[e];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+struct irbc {
+    irbc_params_t p;
+    std::vector<double> gamma, tau;
+    int device = -1;
+    double *gamma_d = nullptr, *tau_d = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+namespace {
+
+int ensure(irbc *M, size_t bytes) {
+    if (bytes <= M->ws_bytes) return DDSG_OK;
+    cudaFree(M->ws);
+    M->ws = nullptr;
+    M->ws_bytes = 0;
+    if (cudaMalloc(&M->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(DDSG_ERR_OOM, "IRBC workspace allocation failed");
+    }
+    M->ws_bytes = bytes;
+    return DDSG_OK;
+}
+
+IrbcDev dev_params(const irbc *M) {
+    IrbcDev P;
+    P.N = M->p.N;
+    P.beta = M->p.beta;
+    P.alpha = M->p.alpha;
+    P.delta = M->p.delta;
+    P.sigma = M->p.sigma;
+    P.rho = M->p.rho;
+    P.phi = M->p.phi;
+    P.A = M->p.A;
+    P.gamma = M->gamma_d;
+    P.tau = M->tau_d;
+    return P;
+}
+
+constexpr size_t kWsCap = (size_t)2 << 30;   // residual workspace per chunk of states
+
+// Component ids holding dim N+i: [2i] = the (i, N+i) pair (or -1), [2i+1] = the
+// single N+i (or -1). Fails if any other component contains dim N+i.
+int k_components(hdmr_t *h, int N, std::vector<int32_t> &out) {
+    int32_t nc = 0;
+    int64_t np = 0;
+    int rc = hdmr_num_components(h, &nc, &np);
+    if (rc) return rc;
+    out.assign(2 * N, -1);
+    for (int32_t c = 0; c < nc; ++c) {
+        int32_t k = 0, dims[DDSG_KMAX];
+        hdmr_component_info(h, c, &k, dims, nullptr, nullptr);
+        for (int j = 0; j < k; ++j) {
+            if (dims[j] < N) continue;
+            const int i = dims[j] - N;
+            if (k == 1) out[2 * i + 1] = c;
+            else if (k == 2 && dims[0] == i) out[2 * i] = c;
+            else return set_error(DDSG_ERR_ARG, "euler_residual: the Jacobian needs every component holding k_i to be {k_i} or {a_i, k_i}");
+        }
+    }
+    return DDSG_OK;
+}
+
+}  // namespace
+
+extern "C" int irbc_create(const irbc_params_t *prm, const double *gamma_host, const double *tau_host,
+                           irbc_t **out) {
+    if (!prm || !gamma_host || !tau_host || !out) return set_error(DDSG_ERR_ARG, "irbc_create: NULL argument");
+    if (prm->N < 1 || prm->N > 4096) return set_error(DDSG_ERR_ARG, "irbc_create: N out of range");
+    irbc *M = new (std::nothrow) irbc();
+    if (!M) return set_error(DDSG_ERR_OOM, "irbc_create: host allocation failed");
+    M->p = *prm;
+    M->gamma.assign(gamma_host, gamma_host + prm->N);
+    M->tau.assign(tau_host, tau_host + prm->N);
+    *out = M;
+    return DDSG_OK;
+}
+
+extern "C" int irbc_destroy(irbc_t *M) {
+    if (!M) return DDSG_OK;
+    cudaFree(M->gamma_d);
+    cudaFree(M->tau_d);
+    cudaFree(M->ws);
+    delete M;
+    return DDSG_OK;
+}
+
+static int bind_device(irbc *M) {
+    if (M->device >= 0) return DDSG_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return set_error(DDSG_ERR_CUDA, "IRBC: no CUDA device");
+    const size_t nb = sizeof(double) * M->p.N;
+    if (cudaMalloc(&M->gamma_d, nb) != cudaSuccess || cudaMalloc(&M->tau_d, nb) != cudaSuccess ||
+        cudaMemcpy(M->gamma_d, M->gamma.data(), nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(M->tau_d, M->tau.data(), nb, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(DDSG_ERR_CUDA, "IRBC: parameter upload failed");
+    }
+    M->device = dev;
+    return DDSG_OK;
+}
+
+extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const double *states_dev,
+                              const double *guess_dev, double *resid_dev, double *jac_dev,
+                              double *euler_err_dev, int precision, int form, ddsg_stream_t stream) {
+    if (!M || !policy || ns < 0 || (ns > 0 && (!states_dev || !guess_dev || !resid_dev)))
+        return set_error(DDSG_ERR_ARG, "euler_residual: bad argument");
+    if (ns == 0) return DDSG_OK;
+    HandleView v;
+    int rc = handle_eval_view(policy, precision, form, &v);
+    if (rc) return rc;
+    const int N = M->p.N, d = 2 * N, m = N + 1, nq = 2 * (N + 1);
+    if (v.d != d || v.m != m) return set_error(DDSG_ERR_ARG, "euler_residual: the policy must map 2N states to N+1 outputs");
+    if ((rc = bind_device(M))) return rc;
+    std::vector<int32_t> kc;
+    int32_t *kc_dev = nullptr;
+    if (jac_dev) {
+        if ((rc = k_components(policy, N, kc))) return rc;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // per state: X (d*nq*8) + flags (nq*4) + y (nq*m*8) + aux (7N*8)
+    const size_t per_state = (size_t)nq * (d * 8 + 4 + m * 8) + (size_t)7 * N * 8;
+    int64_t chunk = std::max<int64_t>(1, (int64_t)(kWsCap / per_state));
+    chunk = std::min<int64_t>(chunk, ns);
+    const size_t kc_bytes = jac_dev ? ((sizeof(int32_t) * kc.size() + 255) & ~(size_t)255) : 0;
+    if ((rc = ensure(M, per_state * chunk + 4096 + kc_bytes))) return rc;
+    unsigned char *base = static_cast<unsigned char *>(M->ws);
+    if (jac_dev) {
+        kc_dev = reinterpret_cast<int32_t *>(base);
+        if (cudaMemcpyAsync(kc_dev, kc.data(), sizeof(int32_t) * kc.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return set_error(DDSG_ERR_CUDA, "euler_residual: copy failed");
+        base += kc_bytes;
+    }
+    const IrbcDev P = dev_params(M);
+    for (int64_t s0 = 0; s0 < ns; s0 += chunk) {
+        const int64_t nsc = std::min<int64_t>(chunk, ns - s0);
+        const int64_t Q = nsc * nq;
+        uint64_t *X = reinterpret_cast<uint64_t *>(base);
+        int32_t *flags = reinterpret_cast<int32_t *>(X + (int64_t)d * Q);
+        double *y = reinterpret_cast<double *>(((uintptr_t)(flags + Q) + 255) & ~(uintptr_t)255);
+        double *aux = y + Q * m;
+        cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int32_t) * Q, st);
+        if (e == cudaSuccess) {
+            const int64_t th = nsc * d;
+            irbc_queries_kernel<<<(unsigned)((th + 255) / 256), 256, 0, st>>>(
+                P, nsc, states_dev + s0 * d, guess_dev + s0 * m, v.lo, v.span, X, flags,
+                reinterpret_cast<unsigned long long *>(v.stats));
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            EvalArgs a;
+            a.t = v.tables;
+            a.d = d;
+            a.m = m;
+            a.n = Q;
+            a.X = X;
+            a.y = y;
+            a.hash = nullptr;
+            a.count = nullptr;
+            a.form = form;
+            a.precision = precision;
+            a.cfg = v.cfg;
+            a.err = reinterpret_cast<unsigned long long *>(v.stats + 2);
+            e = launch_eval(a, st);
+        }
+        if (e == cudaSuccess) {
+            irbc_residual_kernel<<<(unsigned)nsc, 256, 0, st>>>(P, s0, nsc, states_dev, guess_dev, y, resid_dev,
+                                                               euler_err_dev, jac_dev, aux);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && jac_dev) {
+            dim3 grid((unsigned)((N + 127) / 128), (unsigned)nsc);
+            irbc_jacobian_kernel<<<grid, 128, 0, st>>>(P, s0, nsc, *v.tables, form, kc_dev, v.lo, v.span,
+                                                       guess_dev, y, aux, jac_dev);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return set_error(DDSG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return DDSG_OK;
+}
+
+extern "C" int irbc_lu_solve(int n, int64_t ns, const double *A_dev, const double *r_dev, double *dx_dev,
+                             int32_t *status_dev, ddsg_stream_t stream) {
+    if (n < 1 || ns < 0) return set_error(DDSG_ERR_ARG, "irbc_lu_solve: bad size");
+    if (ns == 0) return DDSG_OK;
+    const size_t smem = sizeof(double) * ((size_t)n * n + n);
+    if (smem > 220 * 1024) return set_error(DDSG_ERR_ARG, "irbc_lu_solve: system too large for shared memory (n <= 165)");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        lu_solve_kernel<<<(unsigned)ns, 256, smem, st>>>(n, ns, A_dev, r_dev, nullptr, dx_dev, status_dev);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return set_error(DDSG_ERR_CUDA, cudaGetErrorString(e));
+    return DDSG_OK;
+}
+
+extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *states_dev, double *sol_dev,
+                           int max_it, double tol, int32_t *iters_dev, int32_t *status_dev,
+                           double *resnorm_dev, int precision, int form, ddsg_stream_t stream) {
+    if (!M || !policy || ns < 0 || max_it < 0 || !(tol > 0.0))
+        return set_error(DDSG_ERR_ARG, "irbc_newton: bad argument");
+    if (ns == 0) return DDSG_OK;
+    if ((ns > 0) && (!states_dev || !sol_dev)) return set_error(DDSG_ERR_ARG, "irbc_newton: NULL states or solution");
+    const int N = M->p.N, n = N + 1;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // Newton buffers (separate from the residual workspace): r, J, dz, zt, rt, norms, steps, flags
+    double *r = nullptr, *J = nullptr, *dz = nullptr, *zt = nullptr, *rt = nullptr;
+    double *n2 = nullptr, *ninf = nullptr, *n2t = nullptr, *ninft = nullptr, *step = nullptr;
+    int32_t *active = nullptr, *stat = nullptr;
+    auto bytes = [&](size_t k) { return sizeof(double) * k; };
+    auto rnd = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    // sub-buffer sizes, each rounded to 256 bytes; the block is exactly their sum
+    const size_t szv = rnd(bytes((size_t)ns * n)), szJ = rnd(bytes((size_t)ns * n * n)),
+                 szs = rnd(bytes((size_t)ns)), szi = rnd(sizeof(int32_t) * (size_t)ns);
+    const size_t tot = 4 * szv + szJ + 5 * szs + 2 * szi;
+    void *blk = nullptr;
+    if (cudaMalloc(&blk, tot) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(DDSG_ERR_OOM, "irbc_newton: buffers unavailable");
+    }
+    unsigned char *p = static_cast<unsigned char *>(blk);
+    auto take = [&](size_t rounded) { unsigned char *q = p; p += rounded; return q; };
+    r = (double *)take(szv);
+    rt = (double *)take(szv);
+    dz = (double *)take(szv);
+    zt = (double *)take(szv);
+    J = (double *)take(szJ);
+    n2 = (double *)take(szs);
+    ninf = (double *)take(szs);
+    n2t = (double *)take(szs);
+    ninft = (double *)take(szs);
+    step = (double *)take(szs);
+    active = (int32_t *)take(szi);
+    stat = (int32_t *)take(szi);
+    if ((size_t)(p - static_cast<unsigned char *>(blk)) != tot) {
+        cudaFree(blk);
+        return set_error(DDSG_ERR_STATE, "irbc_newton: internal buffer layout mismatch");
+    }
+    std::vector<double> h_n2(ns), h_ninf(ns), h_n2t(ns), h_step(ns);
+    std::vector<int32_t> h_active(ns, 1), h_iters(ns, 0), h_stat(ns, 1);   // 1 = max-iter until converged
+    int rc = DDSG_OK;
+    auto fail_cuda = [&](cudaError_t e) { rc = set_error(DDSG_ERR_CUDA, cudaGetErrorString(e)); };
+    const unsigned nb = (unsigned)((ns + 255) / 256);
+    for (int it = 0; it <= max_it && rc == DDSG_OK; ++it) {
+        rc = euler_residual(M, policy, ns, states_dev, sol_dev, r, it < max_it ? J : nullptr, nullptr,
+                            precision, form, stream);
+        if (rc) break;
+        norms_kernel<<<nb, 256, 0, st>>>(n, ns, r, n2, ninf);
+        cudaError_t e = cudaMemcpyAsync(h_n2.data(), n2, bytes(ns), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_ninf.data(), ninf, bytes(ns), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { fail_cuda(e); break; }
+        int64_t live = 0;
+        for (int64_t s = 0; s < ns; ++s) {
+            if (h_active[s] && h_ninf[s] <= tol) {
+                h_active[s] = 0;
+                h_stat[s] = 0;
+            }
+            live += h_active[s];
+        }
+        if (live == 0 || it == max_it) break;
+        // Newton step dz = -J^-1 r (all states; converged ones are not applied)
+        e = cudaMemsetAsync(stat, 0, sizeof(int32_t) * ns, st);
+        if (e != cudaSuccess) { fail_cuda(e); break; }
+        rc = irbc_lu_solve(n, ns, J, r, dz, stat, stream);
+        if (rc) break;
+        std::vector<int32_t> h_lu(ns);
+        e = cudaMemcpyAsync(h_lu.data(), stat, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { fail_cuda(e); break; }
+        for (int64_t s = 0; s < ns; ++s) {
+            if (h_active[s] && h_lu[s] == 2) {
+                h_active[s] = 0;
+                h_stat[s] = 2;   // singular Jacobian
+            }
+            h_step[s] = 1.0;
+        }
+        // backtracking on ||r||_2: halve per state until the norm decreases
+        std::vector<int32_t> pending = h_active;
+        for (int ls = 0; ls < 12; ++ls) {
+            int64_t np = 0;
+            for (int64_t s = 0; s < ns; ++s) np += pending[s];
+            if (np == 0) break;
+            e = cudaMemcpyAsync(active, pending.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(step, h_step.data(), bytes(ns), cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) { fail_cuda(e); break; }
+            trial_kernel<<<(unsigned)((ns * n + 255) / 256), 256, 0, st>>>(n, ns, sol_dev, dz, step, active, zt);
+            rc = euler_residual(M, policy, ns, states_dev, zt, rt, nullptr, nullptr, precision, form, stream);
+            if (rc) break;
+            norms_kernel<<<nb, 256, 0, st>>>(n, ns, rt, n2t, ninft);
+            e = cudaMemcpyAsync(h_n2t.data(), n2t, bytes(ns), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) { fail_cuda(e); break; }
+            std::vector<int32_t> acc(ns, 0);
+            int64_t na = 0;
+            for (int64_t s = 0; s < ns; ++s) {
+                if (!pending[s]) continue;
+                if (h_n2t[s] < h_n2[s] || ls == 11) {
+                    acc[s] = 1;
+                    pending[s] = 0;
+                    ++na;
+                } else {
+                    h_step[s] *= 0.5;
+                }
+            }
+            if (na) {
+                // copy accepted trial points into the solution
+                for (int64_t s = 0; s < ns; ++s)
+                    if (acc[s]) {
+                        e = cudaMemcpyAsync(sol_dev + s * n, zt + s * n, bytes(n), cudaMemcpyDeviceToDevice, st);
+                        if (e != cudaSuccess) break;
+                    }
+                if (e != cudaSuccess) { fail_cuda(e); break; }
+            }
+        }
+        for (int64_t s = 0; s < ns; ++s)
+            if (h_active[s]) h_iters[s] = it + 1;
+    }
+    if (rc == DDSG_OK) {
+        cudaError_t e = cudaSuccess;
+        if (iters_dev) e = cudaMemcpyAsync(iters_dev, h_iters.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && status_dev)
+            e = cudaMemcpyAsync(status_dev, h_stat.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && resnorm_dev)
+            e = cudaMemcpyAsync(resnorm_dev, ninf, bytes(ns), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) fail_cuda(e);
+    }
+    cudaFree(blk);
+    return rc;
+}

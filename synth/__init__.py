@@ -188,3 +188,20 @@ def irbc_policy_values(base: np.ndarray, pert, dims, coords_phys: np.ndarray) ->
             y += amp2[None, :, j] * (np.sin(8.0 * (coords_phys[:, pos[j]:pos[j] + 1] - 1.0)) *
                                      np.sin(8.0 * (coords_phys[:, pos[N + j]:pos[N + j] + 1] - 1.0)))
     return y
+
+
+def irbc_steady_lambda(gamma, tau, A: float, delta: float) -> float:
+    """Multiplier of the deterministic steady state (a = k = k' = 1): the lambda
+    solving sum_j (lambda / tau_j)^(-gamma_j) = N (A - delta), by bisection.
+    Used as the base value of the synthetic policy."""
+    gamma = np.asarray(gamma, np.float64)
+    tau = np.asarray(tau, np.float64)
+    target = gamma.size * (A - delta)
+    lo, hi = 1e-8, 1e8
+    for _ in range(400):
+        mid = math.sqrt(lo * hi)
+        if np.sum((mid / tau) ** (-gamma)) > target:
+            lo = mid
+        else:
+            hi = mid
+    return math.sqrt(lo * hi)

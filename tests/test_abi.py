@@ -116,3 +116,23 @@ def test_b_coefficients_non_closed_set_match_oracle():
         h.add_regular(list(u), 2)
         E.add_regular(u, 2)
     assert np.array_equal(h.b_coeffs(), E.b_coeffs())
+
+
+def test_table1_helper_matches_oracle():
+    for N in (1, 3, 150):
+        t = G.irbc_table1(N)
+        I = O.IRBCOracle(N)
+        assert abs(t["A"] - I.A) <= 1e-16 * I.A
+        assert np.allclose(t["gamma"], I.gamma, rtol=0, atol=1e-15)
+        assert np.allclose(t["tau"], I.tau, rtol=1e-14)
+
+
+def test_irbc_create_validates():
+    lib = G.load()
+    h = C.c_void_p()
+    prm = G.IrbcParams(0, 0.99, 0.36, 0.01, 0.01, 0.95, 0.5, 1.0)
+    g = np.ones(1)
+    assert lib.irbc_create(C.byref(prm), G._np_ptr(g), G._np_ptr(g), C.byref(h)) == -1
+    prm.N = 1
+    assert lib.irbc_create(C.byref(prm), G._np_ptr(g), G._np_ptr(g), C.byref(h)) == 0
+    assert lib.irbc_destroy(h) == 0

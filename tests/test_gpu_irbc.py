@@ -1,0 +1,156 @@
+"""GPU parity of the IRBC model step (euler_residual, Jacobian, LU, Newton)
+against the CPU oracle (Sec. 2.1: eq. model1, model2, law_of_motion).
+
+Bars: residuals FP64 |dr| <= 1e-11 * scale, F32C <= 1e-6 * scale with
+scale = |lambda (1 + phi g)| + beta |E| per row (the two sides of eq. model1;
+the resource row uses sum_j Y_j); Jacobian vs central differences of the
+oracle's residual: |dJ| <= 1e-5 * max(1, |J|) (finite-difference truncation);
+Newton: both sides converge to ||r||_inf <= 1e-10 and agree to 1e-7."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2202_06555_gb300 as G
+    G.load()
+    return G
+
+
+def make_model(G, N, level=4, sigma=0.01, seed=synth.BASE_SEED + synth.W_IRBC150, amp=1.0):
+    I = O.IRBCOracle(N, sigma=sigma)
+    lam = I.steady_lambda()
+    base = np.concatenate([np.ones(N), [lam]])
+    pert = synth.irbc_policy_perturbation(seed, N)
+    pert = tuple(p * amp if i != 1 else p for i, p in enumerate(pert))
+    fn = lambda dims, X: synth.irbc_policy_values(base, pert, dims, X)
+    E = O.irbc_policy_ddsg(N, level, fn)
+    d = 2 * N
+    h = G.HDMR(d, N + 1, 2, lo=np.full(d, 0.8), hi=np.full(d, 1.2))
+    comps = [()] + [(i,) for i in range(d)] + [(j, N + j) for j in range(N)]
+    for u in comps:
+        h.add_regular(list(u), level)
+    vals = np.concatenate([fn(u, h.component_points(c)[2]) for c, u in enumerate(comps)])
+    h.hierarchize(torch.from_numpy(vals).cuda())
+    M = G.IRBC(N, I.p["beta"], I.p["alpha"], I.p["delta"], I.p["sigma"], I.p["rho"], I.p["phi"],
+               I.A, I.gamma, I.tau)
+    return I, E, h, M, lam
+
+
+def states_and_guess(N, ns, lam, seed):
+    S = synth.irbc_states(seed, ns, N)
+    g = np.concatenate([S[:, N:] * (1.0 + 0.01 * (synth.uniform_matrix(seed + 1, ns, N) - 0.5)),
+                        lam * (1.0 + 0.02 * (synth.uniform_matrix(seed + 2, ns, 1) - 0.5))], 1)
+    return S, np.ascontiguousarray(g)
+
+
+def gpu_residual(M, h, S, g, prec, form, jac=False):
+    ns, N = S.shape[0], M.N
+    sd = torch.from_numpy(S).cuda()
+    gd = torch.from_numpy(g).cuda()
+    r = torch.zeros((ns, N + 1), dtype=torch.float64, device="cuda")
+    e = torch.zeros((ns, 2), dtype=torch.float64, device="cuda")
+    J = torch.zeros((ns, N + 1, N + 1), dtype=torch.float64, device="cuda") if jac else None
+    M.residual(h, sd, gd, r, J, e, prec, form)
+    torch.cuda.synchronize()
+    return r.cpu().numpy(), e.cpu().numpy(), (J.cpu().numpy() if jac else None)
+
+
+def scales(I, S, g, r):
+    N = I.N
+    k = S[:, N:]
+    lhs = np.abs(g[:, N:N + 1] * (1 + I.p["phi"] * (g[:, :N] / k - 1)))
+    sc = np.concatenate([2 * lhs + np.abs(r[:, :N]),
+                         np.sum(S[:, :N] * I.A * k ** I.p["alpha"], 1, keepdims=True)], 1)
+    return sc
+
+
+@pytest.mark.parametrize("N,ns", [(10, 200), (150, 8)])
+def test_residual_matches_oracle(G, N, ns):
+    I, E, h, M, lam = make_model(G, N)
+    S, g = states_and_guess(N, ns, lam, synth.BASE_SEED + 401)
+    # The paper form sums b_v-weighted component interpolants (b_empty = 1 - N):
+    # FP32 rounding is amplified by sum_v |b_v| (the cancellation the slice-free
+    # form removes), so its F32C bar is u_32-sized times that factor.
+    bsum = float(np.sum(np.abs(E.b_coeffs())))
+    for form in (1, 0):
+        r_ref, e_ref = I.residual(E, S, g, form=form, want_err=True)
+        sc = scales(I, S, g, r_ref)
+        for prec, tol in ((0, 1e-11), (1, 1e-6 if form == 1 else 1e-7 * bsum)):
+            r, e, _ = gpu_residual(M, h, S, g, prec, form)
+            assert np.all(np.abs(r - r_ref) <= tol * sc), (form, prec, np.max(np.abs(r - r_ref) / sc))
+            # Euler error = |beta E / lhs - 1|: compare absolutely (it subtracts numbers near 1)
+            assert np.allclose(e, e_ref, rtol=0, atol=tol if prec else 1e-11)
+
+
+def test_steady_state_residual_is_zero(G):
+    N = 6
+    I, E, h, M, lam = make_model(G, N, sigma=0.0, amp=0.0)
+    S = np.ones((3, 2 * N))
+    g = np.tile(np.concatenate([np.ones(N), [lam]]), (3, 1))
+    for prec in (0, 1):
+        r, e, _ = gpu_residual(M, h, S, g, prec, 1)
+        assert np.max(np.abs(r)) < (1e-12 if prec == 0 else 1e-6)
+
+
+def test_jacobian_matches_central_differences(G):
+    N = 4
+    I, E, h, M, lam = make_model(G, N)
+    S, g = states_and_guess(N, 5, lam, synth.BASE_SEED + 402)
+    _, _, J = gpu_residual(M, h, S, g, 0, 1, jac=True)
+    eps = 1e-6
+    for s in range(S.shape[0]):
+        Jfd = np.zeros((N + 1, N + 1))
+        for c in range(N + 1):
+            gp = g[s].copy(); gp[c] += eps
+            gm = g[s].copy(); gm[c] -= eps
+            Jfd[:, c] = (I.residual(E, S[s:s + 1], gp[None])[0] - I.residual(E, S[s:s + 1], gm[None])[0]) / (2 * eps)
+        assert np.all(np.abs(J[s] - Jfd) <= 1e-5 * np.maximum(1.0, np.abs(Jfd))), (s, np.max(np.abs(J[s] - Jfd)))
+
+
+def test_lu_solve_batched(G):
+    rng = np.random.default_rng(5)
+    ns, n = 7, 12
+    A = rng.normal(size=(ns, n, n)) + 4 * np.eye(n)
+    r = rng.normal(size=(ns, n))
+    A[3] = 0.0   # a singular system
+    Ad = torch.from_numpy(A).cuda()
+    rd = torch.from_numpy(r).cuda()
+    dx = torch.zeros((ns, n), dtype=torch.float64, device="cuda")
+    st = torch.zeros(ns, dtype=torch.int32, device="cuda")
+    G.lu_solve(Ad, rd, dx, st)
+    torch.cuda.synchronize()
+    dx, st = dx.cpu().numpy(), st.cpu().numpy()
+    for s in range(ns):
+        if s == 3:
+            assert st[s] == 2
+        else:
+            assert st[s] == 0 and np.allclose(A[s] @ dx[s], -r[s], atol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_newton_matches_oracle(G, prec):
+    N = 5
+    I, E, h, M, lam = make_model(G, N)
+    S, g = states_and_guess(N, 6, lam, synth.BASE_SEED + 403)
+    sol_ref, its_ref, nrm_ref = I.newton(E, S, g, tol=1e-10)
+    assert np.all(nrm_ref <= 1e-10)
+    sd = torch.from_numpy(S).cuda()
+    z = torch.from_numpy(g.copy()).cuda()
+    it = torch.zeros(S.shape[0], dtype=torch.int32, device="cuda")
+    stt = torch.zeros(S.shape[0], dtype=torch.int32, device="cuda")
+    nr = torch.zeros(S.shape[0], dtype=torch.float64, device="cuda")
+    tol = 1e-10 if prec == 0 else 1e-6
+    M.newton(h, sd, z, 30, tol, it, stt, nr, prec, 1)
+    torch.cuda.synchronize()
+    assert np.all(stt.cpu().numpy() == 0) and np.all(nr.cpu().numpy() <= tol)
+    assert np.all(it.cpu().numpy() <= 10)
+    assert np.allclose(z.cpu().numpy(), sol_ref, atol=1e-7 if prec == 0 else 1e-5)
