@@ -328,6 +328,12 @@ int irbc_newton(irbc_t *model, hdmr_t *policy, int64_t ns, const double *states_
                 double *sol_dev, int max_it, double tol, int32_t *iters_dev, int32_t *status_dev,
                 double *resnorm_dev, int precision, int form, ddsg_stream_t stream);
 
+/* Kernel timing of a model (as hdmr_profile/hdmr_profile_read). Kinds:
+ * 0 next-state queries, 1 policy interpolation, 2 residual sums, 3 Jacobian,
+ * 4 LU solves, 5 Newton norms/trial points; arrays hold DDSG_NKINDS entries. */
+int irbc_profile(irbc_t *model, int enable);
+int irbc_profile_read(irbc_t *model, double *ms_host, int64_t *launches_host, int reset);
+
 #ifdef __cplusplus
 }
 #endif

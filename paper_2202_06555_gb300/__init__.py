@@ -61,6 +61,8 @@ SIGNATURES = {
     "euler_residual": (_int, [_p, _p, _i64, _p, _p, _p, _p, _p, _int, _int, _p]),
     "irbc_lu_solve": (_int, [_int, _i64, _p, _p, _p, _p, _p]),
     "irbc_newton": (_int, [_p, _p, _i64, _p, _p, _int, _d, _p, _p, _p, _int, _int, _p]),
+    "irbc_profile": (_int, [_p, _int]),
+    "irbc_profile_read": (_int, [_p, _p, _p, _int]),
     "hdmr_profile_read": (_int, [_p, _p, _p, _int]),
 }
 
@@ -357,6 +359,25 @@ class IRBC:
                                   _dev_ptr(sol_dev), int(max_it), float(tol), _dev_ptr(iters_dev),
                                   _dev_ptr(status_dev), _dev_ptr(resnorm_dev), int(precision),
                                   int(form), _stream_ptr(stream)), "irbc_newton")
+
+
+IRBC_KINDS = ["queries", "eval", "residual", "jacobian", "lu", "newton_aux", "k6", "k7"]
+
+
+def _irbc_profile(self, enable=True):
+    _check(load().irbc_profile(self._h, int(bool(enable))), "irbc_profile")
+
+
+def _irbc_profile_read(self, reset=True):
+    ms = np.zeros(8)
+    n = np.zeros(8, np.int64)
+    _check(load().irbc_profile_read(self._h, _np_ptr(ms), _np_ptr(n), int(bool(reset))),
+           "irbc_profile_read")
+    return {IRBC_KINDS[i]: (float(ms[i]), int(n[i])) for i in range(8) if n[i]}
+
+
+IRBC.profile = _irbc_profile
+IRBC.profile_read = _irbc_profile_read
 
 
 def lu_solve(A_dev, r_dev, dx_dev, status_dev, stream=None):

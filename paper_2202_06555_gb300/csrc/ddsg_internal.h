@@ -36,6 +36,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/ddsg.h"
 
 namespace ddsg {
@@ -222,6 +224,57 @@ struct HandleView {
     EvalConfig cfg;
 };
 int handle_eval_view(hdmr_t *h, int precision, int form, HandleView *v);
+
+// Event-based kernel tracer (host): brackets launches with CUDA events on the
+// launching stream while enabled; read() waits for them and sums per kind.
+struct Tracer {
+    static constexpr int NK = 8;
+    bool on = false;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    double ms[NK] = {0};
+    int64_t n[NK] = {0};
+    cudaEvent_t take() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+    }
+    struct Scope {
+        Tracer *t; int kind; cudaStream_t st; cudaEvent_t a = nullptr, b = nullptr;
+        Scope(Tracer *t_, int k, cudaStream_t s) : t(t_), kind(k), st(s) {
+            if (!t->on) return;
+            a = t->take(); b = t->take();
+            if (a) cudaEventRecord(a, st);
+        }
+        ~Scope() {
+            if (!t->on || !a || !b) return;
+            cudaEventRecord(b, st);
+            t->recs.push_back({kind, a, b});
+        }
+    };
+    void read(double *out_ms, int64_t *out_n, bool reset) {
+        for (auto &r : recs) {
+            float f = 0.f;
+            if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&f, r.a, r.b) == cudaSuccess) {
+                ms[r.kind] += f;
+                n[r.kind] += 1;
+            }
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        recs.clear();
+        for (int k = 0; k < NK; ++k) {
+            if (out_ms) out_ms[k] = ms[k];
+            if (out_n) out_n[k] = n[k];
+            if (reset) { ms[k] = 0; n[k] = 0; }
+        }
+    }
+    ~Tracer() {
+        for (auto &r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
 int set_error(int code, const char *msg);
 
 cudaError_t launch_to_f32(const double *a, int mp64, float *b, int mp32, int64_t P, int m,

@@ -462,6 +462,7 @@ __global__ void trial_kernel(int n, int64_t ns, const double *__restrict__ z, co
 
 struct irbc {
     irbc_params_t p;
+    Tracer tr;   // kinds: 0 queries, 1 eval, 2 residual, 3 jacobian, 4 lu, 5 newton helpers
     std::vector<double> gamma, tau;
     int device = -1;
     double *gamma_d = nullptr, *tau_d = nullptr;
@@ -603,6 +604,7 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
         double *aux = y + Q * m;
         cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int32_t) * Q, st);
         if (e == cudaSuccess) {
+            Tracer::Scope ts(&M->tr, 0, st);
             const int64_t th = nsc * d;
             irbc_queries_kernel<<<(unsigned)((th + 255) / 256), 256, 0, st>>>(
                 P, nsc, states_dev + s0 * d, guess_dev + s0 * m, v.lo, v.span, X, flags,
@@ -623,14 +625,17 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
             a.precision = precision;
             a.cfg = v.cfg;
             a.err = reinterpret_cast<unsigned long long *>(v.stats + 2);
+            Tracer::Scope ts(&M->tr, 1, st);
             e = launch_eval(a, st);
         }
         if (e == cudaSuccess) {
+            Tracer::Scope ts(&M->tr, 2, st);
             irbc_residual_kernel<<<(unsigned)nsc, 256, 0, st>>>(P, s0, nsc, states_dev, guess_dev, y, resid_dev,
                                                                euler_err_dev, jac_dev, aux);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess && jac_dev) {
+            Tracer::Scope ts(&M->tr, 3, st);
             dim3 grid((unsigned)((N + 127) / 128), (unsigned)nsc);
             irbc_jacobian_kernel<<<grid, 128, 0, st>>>(P, s0, nsc, *v.tables, form, kc_dev, v.lo, v.span,
                                                        guess_dev, y, aux, jac_dev);
@@ -708,7 +713,10 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
         rc = euler_residual(M, policy, ns, states_dev, sol_dev, r, it < max_it ? J : nullptr, nullptr,
                             precision, form, stream);
         if (rc) break;
-        norms_kernel<<<nb, 256, 0, st>>>(n, ns, r, n2, ninf);
+        {
+            Tracer::Scope ts(&M->tr, 5, st);
+            norms_kernel<<<nb, 256, 0, st>>>(n, ns, r, n2, ninf);
+        }
         cudaError_t e = cudaMemcpyAsync(h_n2.data(), n2, bytes(ns), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_ninf.data(), ninf, bytes(ns), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -725,7 +733,10 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
         // Newton step dz = -J^-1 r (all states; converged ones are not applied)
         e = cudaMemsetAsync(stat, 0, sizeof(int32_t) * ns, st);
         if (e != cudaSuccess) { fail_cuda(e); break; }
-        rc = irbc_lu_solve(n, ns, J, r, dz, stat, stream);
+        {
+            Tracer::Scope ts(&M->tr, 4, st);
+            rc = irbc_lu_solve(n, ns, J, r, dz, stat, stream);
+        }
         if (rc) break;
         std::vector<int32_t> h_lu(ns);
         e = cudaMemcpyAsync(h_lu.data(), stat, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, st);
@@ -747,10 +758,16 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
             e = cudaMemcpyAsync(active, pending.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(step, h_step.data(), bytes(ns), cudaMemcpyHostToDevice, st);
             if (e != cudaSuccess) { fail_cuda(e); break; }
-            trial_kernel<<<(unsigned)((ns * n + 255) / 256), 256, 0, st>>>(n, ns, sol_dev, dz, step, active, zt);
+            {
+                Tracer::Scope ts(&M->tr, 5, st);
+                trial_kernel<<<(unsigned)((ns * n + 255) / 256), 256, 0, st>>>(n, ns, sol_dev, dz, step, active, zt);
+            }
             rc = euler_residual(M, policy, ns, states_dev, zt, rt, nullptr, nullptr, precision, form, stream);
             if (rc) break;
-            norms_kernel<<<nb, 256, 0, st>>>(n, ns, rt, n2t, ninft);
+            {
+                Tracer::Scope ts(&M->tr, 5, st);
+                norms_kernel<<<nb, 256, 0, st>>>(n, ns, rt, n2t, ninft);
+            }
             e = cudaMemcpyAsync(h_n2t.data(), n2t, bytes(ns), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) { fail_cuda(e); break; }
@@ -791,4 +808,16 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
     }
     cudaFree(blk);
     return rc;
+}
+
+extern "C" int irbc_profile(irbc_t *M, int enable) {
+    if (!M) return set_error(DDSG_ERR_ARG, "irbc_profile: NULL model");
+    M->tr.on = enable != 0;
+    return DDSG_OK;
+}
+
+extern "C" int irbc_profile_read(irbc_t *M, double *ms, int64_t *launches, int reset) {
+    if (!M) return set_error(DDSG_ERR_ARG, "irbc_profile_read: NULL model");
+    M->tr.read(ms, launches, reset != 0);
+    return DDSG_OK;
 }
