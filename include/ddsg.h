@@ -334,6 +334,41 @@ int irbc_newton(irbc_t *model, hdmr_t *policy, int64_t ns, const double *states_
 int irbc_profile(irbc_t *model, int enable);
 int irbc_profile_read(irbc_t *model, double *ms_host, int64_t *launches_host, int reset);
 
+/* ------------------------------------------------------------------------
+ * Warm-start network (no paper counterpart: the paper solves every grid
+ * point from the previous policy; this MLP only proposes Newton initial
+ * guesses). Hidden layers use the exact-erf GELU, the last layer is linear;
+ * inputs are normalized as (x - in_shift) * in_scale and the network is
+ * trained (mean squared error) on targets normalized as
+ * (y - out_shift) * out_scale. GEMMs are hand-written BF16 tensor-core
+ * kernels (mma.sync m16n8k16, FP32 accumulate); master weights and Adam
+ * (beta 0.9/0.999, eps 1e-8) are FP32.
+ * ------------------------------------------------------------------------ */
+typedef struct mlp mlp_t;
+
+/* sizes: nlayers+1 widths (input .. output). params_host (nullable): packed
+ * FP32 parameters, per layer W (out x in, row-major) then b; NULL draws
+ * W ~ U(-1/sqrt(in), 1/sqrt(in)) from SplitMix64(seed) and b = 0. No CUDA call. */
+int mlp_create(int nlayers, const int32_t *sizes, const float *params_host, uint64_t seed,
+               mlp_t **out);
+int mlp_destroy(mlp_t *net);
+/* Affine normalizations (host arrays; set before the first GPU call). */
+int mlp_set_normalization(mlp_t *net, const double *in_shift, const double *in_scale,
+                          const double *out_shift, const double *out_scale);
+/* One Adam step on B rows: x_dev B x in (FP64), y_dev B x out (FP64).
+ * loss_dev (nullable, device FP64) receives the batch loss. Asynchronous. */
+int mlp_train_step(mlp_t *net, int64_t B, const double *x_dev, const double *y_dev, float lr,
+                   double *loss_dev, ddsg_stream_t stream);
+/* y_dev (B x out, FP64, physical units) = network(x_dev). Asynchronous. */
+int mlp_infer(mlp_t *net, int64_t B, const double *x_dev, double *y_dev, ddsg_stream_t stream);
+/* Packed parameters / gradients of the last train step (FP32, host). Synchronous. */
+int64_t mlp_num_params(const mlp_t *net);
+int mlp_get_params(mlp_t *net, float *host);
+int mlp_get_grads(mlp_t *net, float *host);
+/* Kernel timing: kinds 0 forward GEMMs, 1 backward GEMMs, 2 loss/normalization, 3 Adam. */
+int mlp_profile(mlp_t *net, int enable);
+int mlp_profile_read(mlp_t *net, double *ms_host, int64_t *launches_host, int reset);
+
 #ifdef __cplusplus
 }
 #endif

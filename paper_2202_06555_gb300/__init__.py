@@ -62,6 +62,16 @@ SIGNATURES = {
     "irbc_lu_solve": (_int, [_int, _i64, _p, _p, _p, _p, _p]),
     "irbc_newton": (_int, [_p, _p, _i64, _p, _p, _int, _d, _p, _p, _p, _int, _int, _p]),
     "irbc_profile": (_int, [_p, _int]),
+    "mlp_create": (_int, [_int, _p, _p, C.c_uint64, C.POINTER(_p)]),
+    "mlp_destroy": (_int, [_p]),
+    "mlp_set_normalization": (_int, [_p, _p, _p, _p, _p]),
+    "mlp_train_step": (_int, [_p, _i64, _p, _p, C.c_float, _p, _p]),
+    "mlp_infer": (_int, [_p, _i64, _p, _p, _p]),
+    "mlp_num_params": (_i64, [_p]),
+    "mlp_get_params": (_int, [_p, _p]),
+    "mlp_get_grads": (_int, [_p, _p]),
+    "mlp_profile": (_int, [_p, _int]),
+    "mlp_profile_read": (_int, [_p, _p, _p, _int]),
     "irbc_profile_read": (_int, [_p, _p, _p, _int]),
     "hdmr_profile_read": (_int, [_p, _p, _p, _int]),
 }
@@ -397,3 +407,72 @@ def irbc_table1(N: int, a_gamma: float = 0.25, beta: float = 0.99, alpha: float 
     tau = A ** (1.0 / gamma)
     return dict(N=N, beta=beta, alpha=alpha, delta=delta, sigma=sigma, rho=rho, phi=phi, A=A,
                 gamma=gamma, tau=tau)
+
+
+class MLP:
+    """Warm-start network (see include/ddsg.h): BF16 tensor-core training and
+    inference kernels, FP32 master weights and Adam."""
+
+    def __init__(self, sizes, params=None, seed: int = 0, in_shift=None, in_scale=None,
+                 out_shift=None, out_scale=None):
+        lib = load()
+        self.sizes = [int(s) for s in sizes]
+        sz = np.ascontiguousarray(self.sizes, np.int32)
+        prm = None if params is None else np.ascontiguousarray(params, np.float32)
+        h = C.c_void_p()
+        _check(lib.mlp_create(len(self.sizes) - 1, _np_ptr(sz), _np_ptr(prm), int(seed), C.byref(h)),
+               "mlp_create")
+        self._h = h
+        if in_shift is not None:
+            arrs = [np.ascontiguousarray(a, np.float64) for a in (in_shift, in_scale, out_shift, out_scale)]
+            _check(lib.mlp_set_normalization(self._h, *[_np_ptr(a) for a in arrs]), "mlp_set_normalization")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def train_step(self, x_dev, y_dev, lr: float, loss_dev=None, stream=None):
+        _check(load().mlp_train_step(self._h, x_dev.shape[0], _dev_ptr(x_dev), _dev_ptr(y_dev),
+                                     float(lr), _dev_ptr(loss_dev), _stream_ptr(stream)), "mlp_train_step")
+
+    def infer(self, x_dev, y_dev, stream=None):
+        _check(load().mlp_infer(self._h, x_dev.shape[0], _dev_ptr(x_dev), _dev_ptr(y_dev),
+                                _stream_ptr(stream)), "mlp_infer")
+
+    def _unpack(self, flat):
+        W, b, off = [], [], 0
+        for l in range(len(self.sizes) - 1):
+            ni, no = self.sizes[l], self.sizes[l + 1]
+            W.append(flat[off:off + ni * no].reshape(no, ni).astype(np.float64))
+            off += ni * no
+            b.append(flat[off:off + no].astype(np.float64))
+            off += no
+        return W, b
+
+    def params(self):
+        flat = np.zeros(load().mlp_num_params(self._h), np.float32)
+        _check(load().mlp_get_params(self._h, _np_ptr(flat)), "mlp_get_params")
+        return self._unpack(flat)
+
+    def grads(self):
+        flat = np.zeros(load().mlp_num_params(self._h), np.float32)
+        _check(load().mlp_get_grads(self._h, _np_ptr(flat)), "mlp_get_grads")
+        return self._unpack(flat)
+
+    def profile(self, enable=True):
+        _check(load().mlp_profile(self._h, int(bool(enable))), "mlp_profile")
+
+    def profile_read(self, reset=True):
+        ms = np.zeros(8)
+        n = np.zeros(8, np.int64)
+        _check(load().mlp_profile_read(self._h, _np_ptr(ms), _np_ptr(n), int(bool(reset))),
+               "mlp_profile_read")
+        names = ["gemm_fwd", "gemm_bwd", "aux", "adam", "k4", "k5", "k6", "k7"]
+        return {names[i]: (float(ms[i]), int(n[i])) for i in range(8) if n[i]}
