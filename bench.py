@@ -45,6 +45,10 @@ WORKLOADS = {
     # 150 (a_j, k_j) pairs on regular level-4 grids; 1e4 states x 302 monomial nodes
     "irbc150": dict(d=300, m=151, N=150, level=4, states=10_000, wid=synth.W_IRBC150,
                     precision="f32c", form="slicefree"),
+    # learned warm start: N = 20 (d = 40, m = 21), 1e6 training pairs, 5e4 test states
+    "warmstart20": dict(d=40, m=21, N=20, level=4, states=50_000, train=1_000_000,
+                        wid=synth.W_IRBC20, precision="f64", form="slicefree", epochs=10,
+                        batch=4096),
 }
 
 FP32_LANES_PER_SM = 128
@@ -337,6 +341,118 @@ def run_irbc(args, w):
     return 0
 
 
+def run_warmstart(args, w):
+    """Time-iteration step at N = 20 with a learned Newton warm start."""
+    import torch
+    import paper_2202_06555_gb300 as G
+    if args.impl == "reference":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the warm-start study has no CPU reference arm (GPU-only training)"}))
+        return 0
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    G.load()
+    N, d, m = w["N"], w["d"], w["m"]
+    t1, lam, fn, comps, _, _ = irbc_workload(dict(w, states=1), G)
+    h = G.HDMR(d, m, 2, lo=np.full(d, 0.8), hi=np.full(d, 1.2))
+    for u in comps:
+        h.add_regular(list(u), w["level"])
+    vals = np.concatenate([fn(u, h.component_points(c)[2]) for c, u in enumerate(comps)])
+    h.hierarchize(torch.from_numpy(vals).cuda())
+    M = G.IRBC(**t1)
+    form = G.FORM_SLICEFREE
+
+    def policy_guess(Sd):
+        y = torch.empty((Sd.shape[0], m), dtype=torch.float64, device="cuda")
+        h.eval(Sd, y, G.F64, form)
+        return y
+
+    def solve(Sd, z, prec, tol):
+        it = torch.zeros(Sd.shape[0], dtype=torch.int32, device="cuda")
+        st = torch.zeros(Sd.shape[0], dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        M.newton(h, Sd, z, 30, tol, it, st, None, prec, form)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, it, st
+
+    # 1) training pairs: Euler-equation solutions from the previous policy's guesses
+    Str = torch.from_numpy(synth.irbc_states(synth.BASE_SEED + w["wid"] + 1, w["train"], N)).cuda()
+    ztr = policy_guess(Str)
+    t_data, it_tr, st_tr = solve(Str, ztr, G.F32C, 1e-8)
+    ok = st_tr == 0
+    Str, ztr = Str[ok].contiguous(), ztr[ok].contiguous()
+    # 2) train the network (BF16 tensor-core kernels)
+    mu = ztr.mean(0).cpu().numpy()
+    sd = ztr.std(0).cpu().numpy() + 1e-12
+    sizes = [d, 256, 256, 256, m]
+    net = G.MLP(sizes, seed=synth.BASE_SEED, in_shift=np.full(d, 1.0), in_scale=np.full(d, 5.0),
+                out_shift=mu, out_scale=1.0 / sd)
+    ntr, bs = Str.shape[0], w["batch"]
+    steps = w["epochs"] * (ntr // bs)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    perm_seed = synth.BASE_SEED + 17
+    torch.cuda.synchronize()
+    net.profile(True)
+    net.profile_read(reset=True)
+    t0 = time.perf_counter()
+    losses = []
+    for s in range(steps):
+        ep, k = divmod(s, ntr // bs)
+        lr = 1e-3 * 0.5 * (1.0 + math.cos(math.pi * s / steps))   # cosine decay
+        net.train_step(Str[k * bs:(k + 1) * bs], ztr[k * bs:(k + 1) * bs], lr, loss)
+        if k == 0:
+            losses.append(loss)
+            loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    tprof = net.profile_read(reset=True)
+    net.profile(False)
+    # 3) Newton at new states: previous policy vs network guess, same tolerance
+    Ste = torch.from_numpy(synth.irbc_states(synth.BASE_SEED + w["wid"] + 2, w["states"], N)).cuda()
+    res = {}
+    for name in ("previous_policy", "network"):
+        if name == "network":
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            z = torch.empty((Ste.shape[0], m), dtype=torch.float64, device="cuda")
+            net.infer(Ste, z)
+            torch.cuda.synchronize()
+            t_guess = time.perf_counter() - t0
+        else:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            z = policy_guess(Ste)
+            torch.cuda.synchronize()
+            t_guess = time.perf_counter() - t0
+        g0 = z.clone()
+        t_newton, it, st = solve(Ste, z, G.F64, 1e-10)
+        r = torch.empty((Ste.shape[0], m), dtype=torch.float64, device="cuda")
+        err = torch.empty((Ste.shape[0], 2), dtype=torch.float64, device="cuda")
+        M.residual(h, Ste, z, r, None, err, G.F64, form)
+        ee = err.cpu().numpy()
+        res[name] = {"guess_seconds": t_guess, "newton_seconds": t_newton,
+                     "iters_mean": float(it.double().mean().item()), "iters_max": int(it.max().item()),
+                     "converged": int((st == 0).sum().item()),
+                     "guess_error_max": float((g0 - z).abs().max().item()),
+                     "euler_error_log10_mean": float(np.log10(np.mean(ee[:, 0]))),
+                     "euler_error_log10_max": float(np.log10(np.max(ee[:, 0])))}
+    out = {"metric": "Newton time at 5e4 states, learned vs previous-policy warm start", "value":
+           res["network"]["newton_seconds"] + res["network"]["guess_seconds"], "unit": "s",
+           "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "bf16",
+           "config": {"workload": "irbc20_warm_start", "N": N, "train_pairs": int(ntr),
+                      "mlp": sizes, "epochs": w["epochs"], "batch": bs, "train_steps": steps,
+                      "newton_tol": 1e-10},
+           "data_generation": {"seconds": t_data, "iters_mean": float(it_tr.double().mean().item())},
+           "training": {"seconds": t_train, "samples_per_s": steps * bs / t_train,
+                        "loss_first": float(losses[0].item()), "loss_last": float(losses[-1].item()),
+                        "kernels_ms": {k: v[0] for k, v in tprof.items()},
+                        "launches": sum(v[1] for v in tprof.values())},
+           "newton": res,
+           "speedup_newton": res["previous_policy"]["newton_seconds"] / res["network"]["newton_seconds"]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------------------
 # CUDA arm
 # ---------------------------------------------------------------------------
@@ -364,6 +480,8 @@ def main():
     args.warmup = max(args.warmup, 3) if args.impl == "ddsg" else args.warmup
     if args.workload == "irbc150":
         return run_irbc(args, w)
+    if args.workload == "warmstart20":
+        return run_warmstart(args, w)
     if args.impl == "reference":
         return run_reference(args, w)
 

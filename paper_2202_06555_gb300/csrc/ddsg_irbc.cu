@@ -270,9 +270,9 @@ __global__ void __launch_bounds__(128) irbc_jacobian_kernel(IrbcDev P, int64_t s
                                                             const double *__restrict__ aux,
                                                             double *__restrict__ jac) {
     const int N = P.N, m = N + 1, nq = 2 * (N + 1);
-    const int64_t sl = blockIdx.y;
+    const int64_t sl = blockIdx.x;                      // state within the chunk (grid.x: no 65535 limit)
     const int64_t s = s0 + sl;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const bool paper = form == DDSG_FORM_PAPER;
     const double *kp = guess + s * m;
@@ -636,7 +636,7 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
         }
         if (e == cudaSuccess && jac_dev) {
             Tracer::Scope ts(&M->tr, 3, st);
-            dim3 grid((unsigned)((N + 127) / 128), (unsigned)nsc);
+            dim3 grid((unsigned)nsc, (unsigned)((N + 127) / 128));
             irbc_jacobian_kernel<<<grid, 128, 0, st>>>(P, s0, nsc, *v.tables, form, kc_dev, v.lo, v.span,
                                                        guess_dev, y, aux, jac_dev);
             e = cudaGetLastError();
