@@ -467,6 +467,8 @@ def main():
     ap.add_argument("--precision", default=None, choices=["f32c", "f64"])
     ap.add_argument("--form", default=None, choices=["slicefree", "paper"])
     ap.add_argument("--queries", type=int, default=None)
+    ap.add_argument("--schedule", default=None,
+                    help="KERNEL:MC (0 tile, 1 per-tuple, 2 TMA-staged; MC outputs per pass); skips the autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     args = ap.parse_args()
@@ -535,7 +537,12 @@ def main():
 
     # batching schedule: autotune kernel / output chunk on a subset of the queries
     nt = min(n, 131072)
-    tuned = h.autotune(x[:nt], y[:nt], prec, form)
+    if args.schedule:
+        kern, mc = (int(v) for v in args.schedule.split(":"))
+        h.set_eval_config(prec, form, kern, mc)
+        tuned, nt = (kern, mc), 0
+    else:
+        tuned = h.autotune(x[:nt], y[:nt], prec, form)
     for _ in range(args.warmup):
         h.eval(x, y, prec, form)
     torch.cuda.synchronize()
@@ -636,6 +643,20 @@ def main():
            "e2e": {"value": world * n * w["m"] / e2e_s, "unit": "evals/s",
                    "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(n * w["m"] * 8),
                    "ms_per_step": e2e_s * 1e3}}
+
+    # -- the same step replayed from a CUDA graph (launch overhead removed) -------
+    h.eval_graph(x, y, prec, form)
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        h.eval_graph(x, y, prec, form)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    g_ms = g0.elapsed_time(g1) / args.steps
+    out["graph_replay"] = {"ms_per_step": g_ms, "value": world * n * w["m"] / (g_ms * 1e-3),
+                           "unit": "evals/s", "note": "hdmr_eval_graph: encode + fused eval captured once"}
 
     # -- precision: FP32-compensated vs the plain FP64 GPU form -----------------
     if rank == 0 and not args.no_fp64 and prec == G.F32C:

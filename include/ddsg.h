@@ -229,6 +229,24 @@ int hdmr_eval_noalloc(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, 
 /* Largest n hdmr_eval_noalloc accepts for dimension d (0 if d < 1). */
 int64_t hdmr_eval_noalloc_capacity(int d);
 
+/*
+ * hdmr_eval_graph -- hdmr_eval (no hash/count outputs) replayed from a CUDA
+ * graph. Each time-iteration step of Sec. 2.2 (and each Newton iteration inside
+ * it) evaluates the same policy at same-sized state sets, so the launches of
+ * one evaluation (query encoding and the fused all-component kernel) are
+ * captured once and replayed. The handle caches one executable graph for the
+ * last (n, x_dev, y_dev, precision, form, schedule); a call with any of them
+ * different, or after the grid, the hierarchized tables' storage or the
+ * workspace size changed, captures again (allocations happen before capture).
+ * The graph reads x_dev and writes y_dev by address: refill x_dev in place
+ * between calls. The replay runs on a handle-owned stream ordered after the
+ * work already queued on `stream`, and work queued on `stream` afterwards runs
+ * after it. Same results as hdmr_eval, bit for bit. Tracing counts each replay
+ * under DDSG_K_GRAPH. Not thread-safe per handle (nor is any call).
+ */
+int hdmr_eval_graph(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int precision,
+                    int form, ddsg_stream_t stream);
+
 /* Pre-size the eval workspace for up to n queries (no allocation in later evals). */
 int hdmr_reserve(hdmr_t *h, int64_t n);
 
@@ -263,6 +281,7 @@ enum {
     DDSG_K_HIER = 2,     /* hierarchization                      */
     DDSG_K_CONVERT = 3,  /* FP64 -> FP32 surplus copy            */
     DDSG_K_COPY = 4,     /* host<->device copies of hdmr_eval_host */
+    DDSG_K_GRAPH = 5,    /* one graph replay of hdmr_eval_graph   */
     DDSG_NKINDS = 8
 };
 int hdmr_profile(hdmr_t *h, int enable);

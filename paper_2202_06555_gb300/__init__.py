@@ -55,6 +55,7 @@ SIGNATURES = {
     "hdmr_get_eval_config": (_int, [_p, _int, _int, C.POINTER(_int), C.POINTER(_int)]),
     "hdmr_autotune": (_int, [_p, _i64, _p, _p, _int, _int, _p, C.POINTER(_d)]),
     "hdmr_eval_noalloc": (_int, [_p, _i64, _p, _p, _int, _int, _p]),
+    "hdmr_eval_graph": (_int, [_p, _i64, _p, _p, _int, _int, _p]),
     "hdmr_eval_noalloc_capacity": (_i64, [_int]),
     "irbc_create": (_int, [_p, _p, _p, C.POINTER(_p)]),
     "irbc_destroy": (_int, [_p]),
@@ -76,7 +77,7 @@ SIGNATURES = {
     "hdmr_profile_read": (_int, [_p, _p, _p, _int]),
 }
 
-KERNEL_KINDS = ["encode", "eval", "hierarchize", "convert", "copy", "k5", "k6", "k7"]
+KERNEL_KINDS = ["encode", "eval", "hierarchize", "convert", "copy", "graph", "k6", "k7"]
 
 _lib = None
 
@@ -249,6 +250,13 @@ class HDMR:
         n = x_dev.shape[0]
         _check(load().hdmr_eval_noalloc(self._h, n, _dev_ptr(x_dev), _dev_ptr(y_dev), int(precision),
                                         int(form), _stream_ptr(stream)), "hdmr_eval_noalloc")
+
+    def eval_graph(self, x_dev, y_dev, precision: int = F64, form: int = FORM_PAPER, stream=None):
+        """hdmr_eval replayed from a cached CUDA graph (captured on the first call
+        for these buffers, sizes and schedule); same results bit for bit."""
+        n = x_dev.shape[0]
+        _check(load().hdmr_eval_graph(self._h, n, _dev_ptr(x_dev), _dev_ptr(y_dev), int(precision),
+                                      int(form), _stream_ptr(stream)), "hdmr_eval_graph")
 
     def noalloc_capacity(self) -> int:
         return int(load().hdmr_eval_noalloc_capacity(self.d))

@@ -79,6 +79,20 @@ struct hdmr {
     size_t hbuf_bytes = 0;
     // evaluation kernel choice per [precision][form] (autotuned or heuristic)
     EvalConfig cfg[2][2];
+    // graph replay of hdmr_eval_graph: one cached executable graph for the
+    // last (n, x, y, precision, form, schedule, table generation), replayed on
+    // a handle-owned stream ordered against the caller's stream by events
+    uint64_t gen = 1;               // bumped whenever a captured pointer may change
+    bool capturing = false;         // ProfScope records nothing while capturing
+    cudaGraphExec_t gexec = nullptr;
+    int64_t g_n = -1;
+    const double *g_x = nullptr;
+    double *g_y = nullptr;
+    int g_prec = -1, g_form = -1;
+    EvalConfig g_cfg;
+    uint64_t g_gen = 0;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev[2] = {nullptr, nullptr};
     // tracing
     bool prof = false;
     struct Rec { int kind; cudaEvent_t a, b; };
@@ -105,7 +119,7 @@ struct ProfScope {
         return e;
     }
     ProfScope(hdmr *h_, int kind_, cudaStream_t st_) : h(h_), kind(kind_), st(st_) {
-        if (!h->prof) return;
+        if (!h->prof || h->capturing) return;
         a = take(h);
         b = take(h);
         if (a) cudaEventRecord(a, st);
@@ -144,6 +158,10 @@ static void free_tables(DevTables &t) {
     cudaFree(t.pt_dpos);
     cudaFree(t.proc[0]);
     cudaFree(t.proc[1]);
+    cudaFree(t.stage_rec[0]);
+    cudaFree(t.stage_rec[1]);
+    cudaFree(t.pdims[0]);
+    cudaFree(t.pdims[1]);
     t = DevTables();
 }
 
@@ -209,6 +227,10 @@ extern "C" int hdmr_destroy(hdmr_t *h) {
     cudaFree(h->hbuf);
     for (auto &r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h->pool) cudaEventDestroy(e);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
+    for (auto e : h->gev)
+        if (e) cudaEventDestroy(e);
     delete h;
     return DDSG_OK;
 }
@@ -470,7 +492,7 @@ static int upload_tables(hdmr *h) {
         d.b = h->b[c];
         for (int64_t p = 0; p < np; ++p)
             for (int j = 0; j < k; ++j) d.lmax[j] = std::max<uint8_t>(d.lmax[j], cp.lv[p * k + j]);
-        if (k > 2 || d.lmax[0] > LT || d.lmax[1] > LT) all_tile = false;
+        if (k > 2 || d.lmax[0] > LT || d.lmax[1] > LT || h->d > 65536) all_tile = false;
         // group points by level tuple
         std::map<std::vector<uint8_t>, std::vector<int64_t>> bytup;
         for (int64_t p = 0; p < np; ++p) {
@@ -588,6 +610,21 @@ static int upload_tables(hdmr *h) {
         }
         if ((rc = dev_upload(&t.proc[form], lst))) return rc;
         t.nproc[form] = (int32_t)lst.size();
+        std::vector<int4> recs;
+        std::vector<uint32_t> pds;
+        for (int c : lst) {
+            const DevComp &d = dc[c];
+            const int32_t r0 = form == DDSG_FORM_PAPER ? d.row_begin : d.row_int;
+            const int32_t tb = form == DDSG_FORM_PAPER ? d.tup_begin : d.tup_int;
+            const uint32_t nrows = (uint32_t)(d.row_end - r0), nt = (uint32_t)(d.tup_end - tb);
+            // fields fit whenever the component fits the staged kernel (rows < 2^20, tuples < 2^11)
+            recs.push_back(make_int4(c, r0, (int)((nrows & 0xfffffu) | ((nt & 0x7ffu) << 20)), tb));
+            const uint32_t d0 = d.k >= 1 ? (uint32_t)d.dims[0] : 0u;
+            const uint32_t d1 = d.k >= 2 ? (uint32_t)d.dims[1] : d0;
+            pds.push_back((d0 & 0xffffu) | (d1 << 16));
+        }
+        if ((rc = dev_upload(&t.stage_rec[form], recs))) return rc;
+        if ((rc = dev_upload(&t.pdims[form], pds))) return rc;
         for (int c2 = 0; c2 < C; ++c2) {
             t.max_tuples = std::max(t.max_tuples, dc[c2].tup_end - dc[c2].tup_begin);
             for (int j = 0; j < dc[c2].k; ++j) t.max_level = std::max<int32_t>(t.max_level, dc[c2].lmax[j]);
@@ -601,6 +638,7 @@ static int upload_tables(hdmr *h) {
     CUDA_TRY(cudaMemset(t.alpha32, 0, sizeof(float) * (size_t)P * t.mp32));
     h->uploaded = true;
     h->have_alpha = false;
+    ++h->gen;
     return DDSG_OK;
 }
 
@@ -767,6 +805,7 @@ static int ensure_ws(hdmr *h, int64_t n) {
     cudaFree(h->ws);
     h->ws = nullptr;
     h->ws_bytes = 0;
+    ++h->gen;
     if (cudaMalloc(&h->ws, need) != cudaSuccess) {
         cudaGetLastError();
         return fail(DDSG_ERR_OOM, "hdmr_eval: workspace of %zu bytes unavailable", need);
@@ -824,6 +863,75 @@ extern "C" int hdmr_eval(hdmr_t *h, int64_t n, const double *x_dev, double *y_de
         ProfScope ps(h, DDSG_K_EVAL, st);
         CUDA_TRY(launch_eval(a, st));
     }
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_eval_graph(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int precision,
+                               int form, ddsg_stream_t stream) {
+    if (!h) return fail(DDSG_ERR_ARG, "hdmr_eval_graph: NULL handle");
+    if (n < 0) return fail(DDSG_ERR_ARG, "hdmr_eval_graph: n < 0");
+    if (n == 0) return DDSG_OK;
+    if (!x_dev || !y_dev) return fail(DDSG_ERR_ARG, "hdmr_eval_graph: NULL x or y");
+    if (precision != DDSG_F64 && precision != DDSG_F32C)
+        return fail(DDSG_ERR_ARG, "hdmr_eval_graph: unknown precision %d", precision);
+    if (form != DDSG_FORM_PAPER && form != DDSG_FORM_SLICEFREE)
+        return fail(DDSG_ERR_ARG, "hdmr_eval_graph: unknown form %d", form);
+    if (!h->uploaded || !h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_eval_graph: call hdmr_hierarchize first");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(DDSG_ERR_CUDA, "hdmr_eval_graph: cannot select device");
+    if (!eval_kernel_eligible(h->dt, h->cfg[precision][form].kernel, precision, form))
+        h->cfg[precision][form] = EvalConfig();
+    int rc = ensure_ws(h, n);   // any allocation happens before the capture
+    if (rc) return rc;
+    if (!h->gstream) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+        for (auto &e : h->gev) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const EvalConfig cfg = h->cfg[precision][form];
+    const bool hit = h->gexec && h->g_n == n && h->g_x == x_dev && h->g_y == y_dev && h->g_prec == precision &&
+                     h->g_form == form && h->g_cfg.kernel == cfg.kernel && h->g_cfg.mc == cfg.mc &&
+                     h->g_gen == h->gen;
+    if (!hit) {
+        if (h->gexec) {
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+        CUDA_TRY(cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeRelaxed));
+        h->capturing = true;
+        rc = hdmr_eval(h, n, x_dev, y_dev, precision, form, nullptr, nullptr,
+                       reinterpret_cast<ddsg_stream_t>(h->gstream));
+        h->capturing = false;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(h->gstream, &graph);
+        if (rc || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return rc ? rc : fail(DDSG_ERR_CUDA, "hdmr_eval_graph: capture failed: %s", cudaGetErrorString(ec));
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&h->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            h->gexec = nullptr;
+            cudaGetLastError();
+            return fail(DDSG_ERR_CUDA, "hdmr_eval_graph: instantiate failed: %s", cudaGetErrorString(ei));
+        }
+        h->g_n = n;
+        h->g_x = x_dev;
+        h->g_y = y_dev;
+        h->g_prec = precision;
+        h->g_form = form;
+        h->g_cfg = cfg;
+        h->g_gen = h->gen;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaEventRecord(h->gev[0], st));
+    CUDA_TRY(cudaStreamWaitEvent(h->gstream, h->gev[0], 0));
+    {
+        ProfScope ps(h, DDSG_K_GRAPH, h->gstream);
+        CUDA_TRY(cudaGraphLaunch(h->gexec, h->gstream));
+    }
+    CUDA_TRY(cudaEventRecord(h->gev[1], h->gstream));
+    CUDA_TRY(cudaStreamWaitEvent(st, h->gev[1], 0));
     return DDSG_OK;
 }
 

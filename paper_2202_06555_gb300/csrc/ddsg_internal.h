@@ -104,6 +104,11 @@ struct DevTables {
     // the largest surplus block (bytes, FP32 and FP64) one of them stages
     int32_t *proc[2] = {nullptr, nullptr};
     int32_t nproc[2] = {0, 0};
+    // per processed component (same order), for the TMA-staged kernel:
+    // {component, first staged row, rows | tuples << 20, first tuple}
+    int4 *stage_rec[2] = {nullptr, nullptr};
+    // dims[0] | dims[1] << 16 (dims[1] = dims[0] when k = 1; 0 when k = 0)
+    uint32_t *pdims[2] = {nullptr, nullptr};
     int64_t stage_bytes[2][2] = {{0, 0}, {0, 0}};  // [form][precision]
     int32_t max_tuples = 0;                        // most level tuples in one component
     int32_t max_level = 0;                         // highest 1D level present anywhere

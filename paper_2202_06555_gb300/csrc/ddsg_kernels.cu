@@ -483,6 +483,8 @@ __global__ void __launch_bounds__(TQ) eval_tile_kernel(const EvalParams p) {
 constexpr int TQ2 = 256;
 constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait calls before giving up
 constexpr int kSmemLimit = 232448;          // opt-in shared memory per block (227 KiB)
+constexpr int TMA_NBUF_MAX = 3;             // staging buffers of the TMA-staged kernel
+constexpr int TMA_PB_MAX = 32;              // tuples probed per pass of the TMA-staged kernel
 
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
     return (uint32_t)__cvta_generic_to_shared(ptr);
@@ -537,14 +539,37 @@ __host__ __device__ inline int tma_buf_bytes(int64_t stage) {
     return 128 + TMA_TUP_MAX * (int)sizeof(DevTup) + (int)((stage + 127) & ~127ll);
 }
 
+// shared memory of one probed tuple: a row index and a weight per query
+inline int tma_probe_bytes(int precision) {
+    return TQ2 * (4 + (precision == DDSG_F64 ? 8 : 4));
+}
+
+// Staging buffers (3 when they fit, else 2) and probe batch (tuples probed per
+// pass, at most the largest tuple count and TMA_PB_MAX) that fit in shared
+// memory beside the fixed part; pb = 0 when not even two tuples fit.
+inline void tma_layout(const DevTables &t, int precision, int fixed, int buf, int &nbuf, int &pb) {
+    const int want = t.max_tuples < 2 ? 2 : (t.max_tuples < TMA_PB_MAX ? t.max_tuples : TMA_PB_MAX);
+    const int per = tma_probe_bytes(precision);
+    for (nbuf = TMA_NBUF_MAX; nbuf >= 2; --nbuf) {
+        const int64_t left = (int64_t)kSmemLimit - fixed - (int64_t)nbuf * buf;
+        pb = left > 0 ? (int)(left / per) : 0;
+        if (pb > want) pb = want;
+        if (pb >= (want < 8 ? want : 8) || nbuf == 2) break;
+    }
+    if (pb < 2) pb = 0;
+}
+
 bool eval_kernel_eligible(const DevTables &t, int kernel, int precision, int form) {
     if (kernel == 0 || kernel == 1) return true;
     if (kernel != 2) return false;
     if (!t.tile_ok) return false;   // the staged kernel handles only k <= 2, levels <= LT
     if (t.max_tuples > TMA_TUP_MAX) return false;
-    const int64_t fixed = precision == DDSG_F64 ? tma_fixed_smem<DDSG_F64>() : tma_fixed_smem<DDSG_F32C>();
+    const int fixed = precision == DDSG_F64 ? tma_fixed_smem<DDSG_F64>() : tma_fixed_smem<DDSG_F32C>();
     const int64_t bytes = t.stage_bytes[form][precision];
-    return bytes <= TMA_STAGE_MAX && fixed + 2 * (int64_t)tma_buf_bytes(bytes) <= kSmemLimit;
+    if (bytes > TMA_STAGE_MAX) return false;
+    int nbuf = 0, pb = 0;
+    tma_layout(t, precision, fixed, tma_buf_bytes(bytes), nbuf, pb);
+    return pb > 0;
 }
 
 // 1D basis of levels 1..lm at fixed-point coordinate X into staging slot j:
@@ -576,6 +601,11 @@ __device__ __forceinline__ void tma_stage(uint64_t X, int lm, int tid, uint16_t 
     }
 }
 
+// Probe one level tuple for this thread's query: the staged row of the point
+// whose support holds the query (-1 if there is none) and its weight
+// wb * prod_j phi_j (zero on a miss). Selects instead of branches, apart from
+// the warp-uniform test for a slot-directory tuple. A face flag (bit 15 of a
+// staged cell) masks to cell 0, so off stays inside the tuple's cells.
 template <int PREC, int K>
 __device__ __forceinline__ int32_t tma_probe(const DevTup &tu, const int32_t *slots, int tid,
                                             const uint16_t (*s_cell)[LT][TQ2],
@@ -583,132 +613,239 @@ __device__ __forceinline__ int32_t tma_probe(const DevTup &tu, const int32_t *sl
                                             typename Types<PREC>::W wb, typename Types<PREC>::W &w,
                                             uint32_t *cells) {
     using W = typename Types<PREC>::W;
-    uint32_t off = 0;
+    uint32_t off = 0, face = 0;
     W wt = wb;
     if (K >= 1) {
         const uint32_t ca = s_cell[0][tu.lev[0] - 1][tid];
         cells[0] = ca;
+        face = ca;
+        off = ca & 0x7fffu;
         if (K == 1) {
-            if (ca & 0x8000u) { w = (W)0; return -1; }
-            off = ca;
             wt = wb * s_t[0][tu.lev[0] - 1][tid];
         } else {
             const uint32_t cb = s_cell[1][tu.lev[1] - 1][tid];
             cells[1] = cb;
-            if ((ca | cb) & 0x8000u) { w = (W)0; return -1; }
-            off = ca * tu.nc1 + cb;
+            face |= cb;
+            off = off * tu.nc1 + (cb & 0x7fffu);
             wt = wb * (s_t[0][tu.lev[0] - 1][tid] * s_t[1][tu.lev[1] - 1][tid]);
         }
     }
-    const int32_t row = tuple_row(tu, off, slots);
+    int32_t row;
+    if (tu.slot_base < 0) {
+        const uint32_t o6 = off & 63u;
+        const bool present = !(face & 0x8000u) && ((tu.mask >> o6) & 1ull);
+        row = present ? tu.first + __popcll(tu.mask & ((2ull << o6) - 1ull)) - 1 : -1;
+    } else {
+        const int32_t s = slots[tu.slot_base + off];
+        row = (face & 0x8000u) ? -1 : s;
+    }
     w = row >= 0 ? wt : (W)0;
     return row;
 }
 
-template <int PREC, int MC>
-__device__ __forceinline__ void tma_load(typename Types<PREC>::V (&v)[MC / Types<PREC>::VW],
-                                         const typename Types<PREC>::W *sbuf, int32_t srow, bool hit,
-                                         int m0, int mp) {
-    using T = Types<PREC>;
-    const typename T::V *src = reinterpret_cast<const typename T::V *>(sbuf + (int64_t)(hit ? srow : 0) * mp + m0);
-#pragma unroll
-    for (int g = 0; g < MC / T::VW; ++g) {
-        if (hit && m0 + g * T::VW < mp) v[g] = src[g];
-        else memset(&v[g], 0, sizeof(v[g]));
+// Probe phase: tuples [0, nb) of stup for this thread's query. Per tuple u the
+// staged row to read goes to s_prow[u*TQ2 + tid] and the weight to s_pw; each
+// thread reads back only its own column, so no barrier is needed. The point
+// hash and count of the parity checks are taken here. A miss has the weight
+// zero and reads the tuple's first row (finite), so that the accumulate phase
+// loads unconditionally.
+template <int PREC, int K, bool HC>
+__device__ __forceinline__ void tma_probe_batch(const EvalParams &p, int c, const DevTup *stup, int nb,
+                                                typename Types<PREC>::W wb, int tid,
+                                                const uint16_t (*s_cell)[LT][TQ2],
+                                                const typename Types<PREC>::W (*s_t)[LT][TQ2], int32_t row0,
+                                                int32_t *s_prow, typename Types<PREC>::W *s_pw, uint64_t &h,
+                                                int32_t &cnt) {
+    using W = typename Types<PREC>::W;
+#pragma unroll 4
+    for (int u = 0; u < nb; ++u) {
+        const DevTup &tu = stup[u];
+        W w;
+        uint32_t cl[2] = {0, 0};
+        const int32_t row = tma_probe<PREC, K>(tu, p.t.slots, tid, s_cell, s_t, wb, w, cl);
+        const bool hit = row >= 0;
+        s_prow[u * TQ2 + tid] = (hit ? row : tu.first) - row0;
+        s_pw[u * TQ2 + tid] = w;
+        if (HC && hit) {
+            h ^= point_key(c, K, tu.lev, cl);
+            ++cnt;
+        }
     }
 }
 
-// Tuples [0, nt) of one staged component (tuple structs in shared memory).
+// Accumulate phase: acc += w_u * row_u[m0, m0+MC) over the nb probed tuples,
+// software-pipelined over two register slots. With U = 2 a slot holds one of
+// the two rows of a step; with U = 1 (an output chunk too wide for two rows)
+// slot 0 holds the first half of the row and slot 1 the second. Each slot is
+// accumulated and at once refilled from the next step's row, so one slot's
+// loads are in flight while the other's FMAs issue; the (row, weight) pairs
+// are read two steps ahead. Row loads are unconditional (a miss reads a real,
+// finite row with the weight zero); FULL: the chunk lies inside the padded row.
+template <int PREC, int MC, bool FULL>
+__device__ __forceinline__ void tma_accumulate(const int32_t *s_prow, const typename Types<PREC>::W *s_pw,
+                                               int nb, int tid, const typename Types<PREC>::W *sbuf, int m0,
+                                               int mp, typename Types<PREC>::W (&acc)[MC]) {
+    using T = Types<PREC>;
+    using W = typename T::W;
+    using V = typename T::V;
+    constexpr int G = MC / T::VW;                                   // vectors per chunk
+    constexpr int U = (PREC == DDSG_F32C && MC > 28) ? 1 : 2;       // tuples per step
+    constexpr int SV = U == 2 ? G : (G + 1) / 2;                    // vectors per slot
+    V v[2][SV];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int g = 0; g < SV; ++g) memset(&v[s][g], 0, sizeof(v[s][g]));
+
+    auto load_slot = [&](int s, int32_t rr) {
+        const int g0 = U == 2 ? 0 : s * SV;
+        const int ng = U == 2 ? G : (s == 0 ? SV : G - SV);
+        const V *src = reinterpret_cast<const V *>(sbuf + (int64_t)rr * mp + m0);
+#pragma unroll
+        for (int g = 0; g < SV; ++g)
+            if (g < ng && (FULL || m0 + (g0 + g) * T::VW < mp)) v[s][g] = src[g0 + g];
+    };
+    auto fma_slot = [&](int s, W wt) {
+        const int g0 = U == 2 ? 0 : s * SV;
+        const int ng = U == 2 ? G : (s == 0 ? SV : G - SV);
+        if (PREC == DDSG_F64 && wt == (W)0) return;   // FP64 issues no FMA for a miss
+#pragma unroll
+        for (int g = 0; g < SV; ++g) {
+            if (g < ng) {
+                if constexpr (T::VW == 4) {
+                    acc[4 * (g0 + g) + 0] = fmaf(wt, v[s][g].x, acc[4 * (g0 + g) + 0]);
+                    acc[4 * (g0 + g) + 1] = fmaf(wt, v[s][g].y, acc[4 * (g0 + g) + 1]);
+                    acc[4 * (g0 + g) + 2] = fmaf(wt, v[s][g].z, acc[4 * (g0 + g) + 2]);
+                    acc[4 * (g0 + g) + 3] = fmaf(wt, v[s][g].w, acc[4 * (g0 + g) + 3]);
+                } else {
+                    acc[2 * (g0 + g) + 0] = fma(wt, v[s][g].x, acc[2 * (g0 + g) + 0]);
+                    acc[2 * (g0 + g) + 1] = fma(wt, v[s][g].y, acc[2 * (g0 + g) + 1]);
+                }
+            }
+        }
+    };
+    // (row, weight) of tuple t; past the batch: the last tuple's row, weight zero
+    auto rd = [&](int t, int32_t &rr, W &ww) {
+        const int tc = t < nb ? t : nb - 1;
+        rr = s_prow[tc * TQ2 + tid];
+        const W x = s_pw[tc * TQ2 + tid];
+        ww = t < nb ? x : (W)0;
+    };
+
+    int32_t r1[U], r2[U];
+    W w0[U], w1[U], w2[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) rd(u, r1[u], w0[u]);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) load_slot(s, r1[U == 2 ? s : 0]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) rd(U + u, r1[u], w1[u]);
+    for (int t = 0; t < nb; t += U) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) rd(t + 2 * U + u, r2[u], w2[u]);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int u = U == 2 ? s : 0;
+            fma_slot(s, w0[u]);
+            load_slot(s, r1[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            w0[u] = w1[u];
+            r1[u] = r2[u];
+            w1[u] = w2[u];
+        }
+    }
+}
+
 template <int PREC, int MC, bool HC, int K>
-__device__ __forceinline__ void tma_tuples(const EvalParams &p, int c, const DevTup *stup, int nt,
+__device__ __forceinline__ void tma_tuples(const EvalParams &p, int c, const DevTup *stup, int nt, int pb,
                                            typename Types<PREC>::W wb, int m0, int tid,
                                            const uint16_t (*s_cell)[LT][TQ2],
                                            const typename Types<PREC>::W (*s_t)[LT][TQ2],
                                            const typename Types<PREC>::W *sbuf, int32_t row0,
+                                           int32_t *s_prow, typename Types<PREC>::W *s_pw,
                                            typename Types<PREC>::W (&acc)[MC], uint64_t &h, int32_t &cnt) {
-    using T = Types<PREC>;
-    using W = typename T::W;
-    const int mp = T::stride(p.t);
-    for (int ti = 0; ti < nt; ti += 2) {
-        const bool two = ti + 1 < nt;
-        const DevTup t0 = stup[ti];
-        const DevTup t1 = stup[two ? ti + 1 : ti];
-        W w0, w1;
-        uint32_t c0[2] = {0, 0}, c1[2] = {0, 0};
-        const int32_t r0 = tma_probe<PREC, K>(t0, p.t.slots, tid, s_cell, s_t, wb, w0, c0);
-        int32_t r1 = tma_probe<PREC, K>(t1, p.t.slots, tid, s_cell, s_t, wb, w1, c1);
-        if (!two) {
-            r1 = -1;
-            w1 = (W)0;
-        }
-        typename T::V v0[MC / T::VW], v1[MC / T::VW];
-        tma_load<PREC, MC>(v0, sbuf, r0 - row0, r0 >= 0, m0, mp);
-        tma_load<PREC, MC>(v1, sbuf, r1 - row0, r1 >= 0, m0, mp);
-        if constexpr (PREC == DDSG_F64) {
-            if (r0 >= 0) tile_fma<PREC, MC>(acc, w0, v0);
-            if (r1 >= 0) tile_fma<PREC, MC>(acc, w1, v1);
-        } else {
-            tile_fma<PREC, MC>(acc, w0, v0);
-            tile_fma<PREC, MC>(acc, w1, v1);
-        }
-        if (HC) {
-            if (r0 >= 0) { h ^= point_key(c, K, t0.lev, c0); ++cnt; }
-            if (r1 >= 0) { h ^= point_key(c, K, t1.lev, c1); ++cnt; }
-        }
+    const int mp = Types<PREC>::stride(p.t);
+    for (int t0 = 0; t0 < nt; t0 += pb) {
+        const int nb = nt - t0 < pb ? nt - t0 : pb;
+        tma_probe_batch<PREC, K, HC>(p, c, stup + t0, nb, wb, tid, s_cell, s_t, row0, s_prow, s_pw, h, cnt);
+        if (m0 + MC <= mp) tma_accumulate<PREC, MC, true>(s_prow, s_pw, nb, tid, sbuf, m0, mp, acc);
+        else tma_accumulate<PREC, MC, false>(s_prow, s_pw, nb, tid, sbuf, m0, mp, acc);
     }
 }
 
-// Per evaluated component i, one TMA stage delivers into buffer i % 2:
+// Per evaluated component j, one TMA stage delivers into buffer j % nbuf:
 //   [0, 96)                         the component struct,
 //   [128, 128 + 32*TMA_TUP_MAX)     its level tuples (those the form evaluates),
 //   [128 + 32*TMA_TUP_MAX, ...)     its surplus rows (one contiguous row range).
+// full[b] completes when a stage has landed; empty[b] when every warp is done
+// with it. Thread 0 stages component i+2 at the end of iteration i, into the
+// buffer that component i+2-nbuf used: with nbuf = 3 warps may drift one
+// component apart without a block barrier. Coordinates of component i+1 are
+// loaded during component i from a per-component dims record, so no load
+// stalls the start of a component. Every wait is bounded; a warp that gives up
+// counts the timeout, marks its queries NaN and leaves the loop, and before
+// the block exits thread 0 waits (bounded) for the copies it issued.
 template <int PREC, int MC, bool HC>
-__global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, int buf_bytes) {
+__global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, int buf_bytes, int nbuf, int pb) {
     using T = Types<PREC>;
     using W = typename T::W;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + TMA_NBUF_MAX;
     auto s_cell = reinterpret_cast<uint16_t (*)[LT][TQ2]>(smem + 128);
     auto s_t = reinterpret_cast<W (*)[LT][TQ2]>(smem + 128 + sizeof(uint16_t) * 2 * LT * TQ2);
     unsigned char *bufbase = smem + tma_fixed_smem<PREC>();
-    unsigned char *buf[2] = {bufbase, bufbase + buf_bytes};
+    int32_t *s_prow = reinterpret_cast<int32_t *>(bufbase + (size_t)nbuf * buf_bytes);
+    W *s_pw = reinterpret_cast<W *>(s_prow + (size_t)pb * TQ2);
     constexpr int kTupOff = 128;
     constexpr int kRowOff = 128 + TMA_TUP_MAX * (int)sizeof(DevTup);
+    constexpr int kWarps = TQ2 / 32;
 
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const int64_t q = (int64_t)blockIdx.x * TQ2 + tid;
-    const int64_t qc = q < p.n ? q : p.n - 1;   // clamped index for prefetch loads
+    const int64_t qc = q < p.n ? q : p.n - 1;   // clamped index for coordinate loads
     const int m0 = blockIdx.y * MC;
     const int m = p.m;
     const bool valid = q < p.n;
     const bool bad = !valid || p.flags[q] != 0;
     const bool paper = p.form == DDSG_FORM_PAPER;
-    const int32_t *list = p.t.proc[p.form];
     const int nproc = p.t.nproc[p.form];
+    const int4 *recs = p.t.stage_rec[p.form];
+    const uint32_t *pdims = p.t.pdims[p.form];
     const W *galpha = T::alpha(p.t);
     const int mp = T::stride(p.t);
 
-    auto issue = [&](int i, int b) {  // thread 0 only
-        const DevComp &cd = p.t.comps[list[i]];
-        const int32_t r0 = paper ? cd.row_begin : cd.row_int;
-        const int tb = paper ? cd.tup_begin : cd.tup_int;
-        const uint32_t rbytes = (uint32_t)((int64_t)(cd.row_end - r0) * mp * (int64_t)sizeof(W));
-        const uint32_t tbytes = (uint32_t)((cd.tup_end - tb) * (int)sizeof(DevTup));
-        mbar_expect_tx(&bar[b], (uint32_t)sizeof(DevComp) + tbytes + rbytes);
-        tma_bulk_g2s(buf[b], &cd, (uint32_t)sizeof(DevComp), &bar[b]);
-        if (tbytes) tma_bulk_g2s(buf[b] + kTupOff, p.t.tups + tb, tbytes, &bar[b]);
-        if (rbytes) tma_bulk_g2s(buf[b] + kRowOff, galpha + (int64_t)r0 * mp, rbytes, &bar[b]);
+    // thread 0: stage processed component j (record rec) into buffer j % nbuf
+    auto issue = [&](int j, int4 rec) {
+        const int b = j % nbuf;
+        const uint32_t nrows = (uint32_t)rec.z & 0xfffffu, nt = (uint32_t)rec.z >> 20;
+        const uint32_t rbytes = nrows * (uint32_t)mp * (uint32_t)sizeof(W);
+        const uint32_t tbytes = nt * (uint32_t)sizeof(DevTup);
+        unsigned char *dst = bufbase + (size_t)b * buf_bytes;
+        mbar_expect_tx(&full[b], (uint32_t)sizeof(DevComp) + tbytes + rbytes);
+        tma_bulk_g2s(dst, p.t.comps + rec.x, (uint32_t)sizeof(DevComp), &full[b]);
+        if (tbytes) tma_bulk_g2s(dst + kTupOff, p.t.tups + rec.w, tbytes, &full[b]);
+        if (rbytes) tma_bulk_g2s(dst + kRowOff, galpha + (int64_t)rec.y * mp, rbytes, &full[b]);
     };
 
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int b = 0; b < nbuf; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], kWarps);
+        }
         mbar_fence_init();
     }
     __syncthreads();
+    int nissued = 0;
+    int4 rec_next = make_int4(0, 0, 0, 0);
     if (tid == 0) {
-        if (nproc > 0) issue(0, 0);
-        if (nproc > 1) issue(1, 1);
+        if (nproc > 0) issue(0, recs[0]);
+        if (nproc > 1) issue(1, recs[1]);
+        nissued = nproc < 2 ? nproc : 2;
+        if (nproc > 2) rec_next = recs[2];
     }
 
     Result<PREC, MC> r;
@@ -718,56 +855,81 @@ __global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, in
     bool failed = false;
     int staged0 = -1;              // dimension currently held in staging slot 0
     const int lmax_all = p.t.max_level < LT ? p.t.max_level : LT;
-    // prefetch of the next component's second coordinate
-    uint64_t Xnext = 0;
-    int dnext = -1;
+    uint64_t Xc0 = 0, Xc1 = 0;     // coordinates of the current component's dims
+    uint32_t pd_next = 0;          // dims record of the next component
     if (nproc > 0) {
-        const DevComp &c0 = p.t.comps[list[0]];
-        if (c0.k == 2) { dnext = c0.dims[1]; Xnext = p.X[(int64_t)dnext * p.n + qc]; }
+        const uint32_t pd = pdims[0];
+        Xc0 = p.X[(int64_t)(pd & 0xffffu) * p.n + qc];
+        Xc1 = p.X[(int64_t)(pd >> 16) * p.n + qc];
     }
+    if (nproc > 1) pd_next = pdims[1];
+    int b = 0;
+    uint32_t ph = 0;
     for (int i = 0; i < nproc; ++i) {
-        const int b = i & 1;
-        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((i >> 1) & 1));
-        if (__syncthreads_or(!ok)) {
-            // a staging copy did not arrive: record it, wait (bounded) for the
-            // copies this block still has in flight, then give up on the block
+        uint64_t Xn0 = 0, Xn1 = 0;
+        if (i + 1 < nproc) {
+            Xn0 = p.X[(int64_t)(pd_next & 0xffffu) * p.n + qc];
+            Xn1 = p.X[(int64_t)(pd_next >> 16) * p.n + qc];
+        }
+        if (i + 2 < nproc) pd_next = pdims[i + 2];
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[b], ph))) {
             failed = true;
-            if (tid == 0 && p.err) atomicAdd(p.err, 1ull);
-            mbar_wait_bounded(&bar[b], (uint32_t)((i >> 1) & 1));
-            if (i + 1 < nproc) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((i + 1) >> 1) & 1));
+            if (lane == 0 && p.err) atomicAdd(p.err, 1ull);
             break;
         }
-        const DevComp &cd = *reinterpret_cast<const DevComp *>(buf[b]);
-        const int c = list[i];
-        const int k = cd.k;
-        const uint64_t Xb = Xnext;
-        // prefetch the coordinate the next component needs in staging slot 1
-        if (i + 1 < nproc) {
-            const DevComp &cn = p.t.comps[list[i + 1]];
-            if (cn.k == 2) { dnext = cn.dims[1]; Xnext = p.X[(int64_t)dnext * p.n + qc]; }
-        }
+        const unsigned char *buf = bufbase + (size_t)b * buf_bytes;
+        const DevComp &cd = *reinterpret_cast<const DevComp *>(buf);
         if (!bad) {
+            const int k = cd.k;
             if (k >= 1 && cd.dims[0] != staged0) {
-                tma_stage<PREC>(p.X[(int64_t)cd.dims[0] * p.n + q], k == 1 ? cd.lmax[0] : lmax_all, tid, s_cell, s_t, 0);
+                tma_stage<PREC>(Xc0, k == 1 ? cd.lmax[0] : lmax_all, tid, s_cell, s_t, 0);
                 staged0 = k == 1 ? -1 : cd.dims[0];
             }
-            if (k == 2) tma_stage<PREC>(Xb, cd.lmax[1], tid, s_cell, s_t, 1);
+            if (k == 2) tma_stage<PREC>(Xc1, cd.lmax[1], tid, s_cell, s_t, 1);
+            const int c = HC ? p.t.proc[p.form][i] : 0;
             const int tb = paper ? cd.tup_begin : cd.tup_int;
             const int nt = cd.tup_end - tb;
             const int32_t row0 = paper ? cd.row_begin : cd.row_int;
             const W wb = paper ? (W)cd.b : (W)1;
-            const DevTup *stup = reinterpret_cast<const DevTup *>(buf[b] + kTupOff);
-            const W *srow = reinterpret_cast<const W *>(buf[b] + kRowOff);
-            if (k == 2) tma_tuples<PREC, MC, HC, 2>(p, c, stup, nt, wb, m0, tid, s_cell, s_t, srow, row0, r.partial(), h, cnt);
-            else if (k == 1) tma_tuples<PREC, MC, HC, 1>(p, c, stup, nt, wb, m0, tid, s_cell, s_t, srow, row0, r.partial(), h, cnt);
-            else tma_tuples<PREC, MC, HC, 0>(p, c, stup, nt, wb, m0, tid, s_cell, s_t, srow, row0, r.partial(), h, cnt);
+            const DevTup *stup = reinterpret_cast<const DevTup *>(buf + kTupOff);
+            const W *srow = reinterpret_cast<const W *>(buf + kRowOff);
+            if (k == 2) tma_tuples<PREC, MC, HC, 2>(p, c, stup, nt, pb, wb, m0, tid, s_cell, s_t, srow, row0, s_prow, s_pw, r.partial(), h, cnt);
+            else if (k == 1) tma_tuples<PREC, MC, HC, 1>(p, c, stup, nt, pb, wb, m0, tid, s_cell, s_t, srow, row0, s_prow, s_pw, r.partial(), h, cnt);
+            else tma_tuples<PREC, MC, HC, 0>(p, c, stup, nt, pb, wb, m0, tid, s_cell, s_t, srow, row0, s_prow, s_pw, r.partial(), h, cnt);
             r.fold();
         }
-        __syncthreads();  // everyone is done with buf[b]
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[b]);
+        // producer: once every warp is done with component i+2-nbuf, stage i+2 in its buffer
+        int pfail = 0;
         if (tid == 0 && i + 2 < nproc) {
-            fence_proxy_async_smem();
-            issue(i + 2, b);
+            const int j = i + 2;
+            if (j >= nbuf && !mbar_wait_bounded(&empty[j % nbuf], (uint32_t)(((j - nbuf) / nbuf) & 1))) {
+                pfail = 1;
+            } else {
+                fence_proxy_async_smem();
+                issue(j, rec_next);
+                nissued = j + 1;
+                if (j + 1 < nproc) rec_next = recs[j + 1];
+            }
         }
+        if (__shfl_sync(0xffffffffu, pfail, 0)) {
+            failed = true;
+            if (lane == 0 && p.err) atomicAdd(p.err, 1ull);
+            break;
+        }
+        Xc0 = Xn0;
+        Xc1 = Xn1;
+        if (++b == nbuf) {
+            b = 0;
+            ph ^= 1u;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // a block that gave up may still have copies in flight: let them land
+        for (int j = nissued > nbuf ? nissued - nbuf : 0; j < nissued; ++j)
+            mbar_wait_bounded(&full[j % nbuf], (uint32_t)((j / nbuf) & 1));
     }
     if (!valid) return;
     const double nanv = __longlong_as_double(0x7ff8000000000000ll);
@@ -786,18 +948,20 @@ static cudaError_t launch_mc(const EvalParams &p, int kernel, bool hc, cudaStrea
         const int prec = PREC;
         const int64_t stage = p.t.stage_bytes[p.form][prec];
         const int buf = tma_buf_bytes(stage);
-        const int smem = tma_fixed_smem<PREC>() + 2 * buf;
+        int nbuf = 0, pb = 0;
+        tma_layout(p.t, PREC, tma_fixed_smem<PREC>(), buf, nbuf, pb);
+        const int smem = tma_fixed_smem<PREC>() + nbuf * buf + pb * tma_probe_bytes(PREC);
         dim3 grid2((unsigned)((p.n + TQ2 - 1) / TQ2), (unsigned)((p.m + MC - 1) / MC));
         if (hc) {
             cudaError_t e = cudaFuncSetAttribute(eval_tma_kernel<PREC, MC, true>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
-            eval_tma_kernel<PREC, MC, true><<<grid2, TQ2, smem, st>>>(p, buf);
+            eval_tma_kernel<PREC, MC, true><<<grid2, TQ2, smem, st>>>(p, buf, nbuf, pb);
         } else {
             cudaError_t e = cudaFuncSetAttribute(eval_tma_kernel<PREC, MC, false>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
-            eval_tma_kernel<PREC, MC, false><<<grid2, TQ2, smem, st>>>(p, buf);
+            eval_tma_kernel<PREC, MC, false><<<grid2, TQ2, smem, st>>>(p, buf, nbuf, pb);
         }
         return cudaGetLastError();
     }
