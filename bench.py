@@ -71,6 +71,27 @@ def comp_list(w):
     return full_order_components(w["d"], w["order"])
 
 
+# DRAM traffic of the evaluation kernel from one ncu capture (profiles/
+# eval_tma_d100_ncu_full.md: d=100 tables, 32768 queries, TMA-staged kernel at
+# 52 outputs per pass), per query; scaled to a full launch by the query count.
+# Valid only for the kernel sources it was taken on (checked by hash).
+EVAL_TRAFFIC = {"workload": "d100", "schedule": (2, 52), "dram_bytes_per_query": 210224896 / 32768,
+                "sha1": {"ddsg_kernels.cu": "e9ef86f4009a1c92761de5edfd68c9fb6639e6de",
+                         "ddsg_internal.h": "74f20921f3dac1edc2476ed883c1c071259d09de"}}
+
+
+def eval_traffic(workload, schedule, n):
+    import hashlib
+    t = EVAL_TRAFFIC
+    if workload != t["workload"] or tuple(schedule) != t["schedule"]:
+        return None
+    for f, h in t["sha1"].items():
+        path = os.path.join(ROOT, "paper_2202_06555_gb300", "csrc", f)
+        if hashlib.sha1(open(path, "rb").read()).hexdigest() != h:
+            return None
+    return t["dram_bytes_per_query"] * n
+
+
 def make_queries(w, rank=0):
     seed = synth.BASE_SEED + w["wid"] + 7919 * rank
     if w["queries"] == "monomial":
@@ -633,7 +654,8 @@ def main():
                       "build_s": t_build},
            "gpu_launches": launches,
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                        "frac": achieved / peak, "traffic": eval_traffic(args.workload, tuned[:2], n),
+                        "peak_source": peak_src,
                         "kernel": "eval", "kernel_ms": eval_avg_ms,
                         "flops_per_launch": flops_per_launch},
            "hbm_roofline": {"bytes_per_step": hbm_bytes, "frac": hbm_frac, "peak_gbs": hbm_peak,
