@@ -202,6 +202,22 @@ def oracle_rate(E, w, X, budget_s):
     return used * w["m"] / t_used, used
 
 
+def oracle_rate_threads(E, w, X, n, threads):
+    """Oracle evaluation rate with `threads` host threads, each evaluating a
+    contiguous share of X[:n] (the C oracle releases the GIL; its code is the
+    same as in the single-thread run); returns evals/s."""
+    from concurrent.futures import ThreadPoolExecutor
+    form = 1 if w["form"] == "slicefree" else 0
+    E.tables()
+    E.b_coeffs()
+    bounds = [(n * t // threads, n * (t + 1) // threads) for t in range(threads)]
+    with ThreadPoolExecutor(threads) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(lambda b: E.eval(X[b[0]:b[1]], form=form), bounds))
+        dt = time.perf_counter() - t0
+    return n * w["m"] / dt
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -705,7 +721,10 @@ def main():
     # -- CPU baseline: the oracle on a bounded sample (rank 0, N=1 only) --------
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         E = oracle_build(w)
-        rate, used = oracle_rate(E, w, X, 20.0)
+        rate, used = oracle_rate(E, w, X, 10.0)
+        threads = max(1, os.cpu_count() or 1)
+        n_par = min(X.shape[0], used * threads)
+        rate_par = oracle_rate_threads(E, w, X, n_par, threads) if threads > 1 else rate
         # precision against the FP64 oracle on the sample (scale max(|y|, S))
         r = E.eval(X[:min(used, 400)], form=1 if w["form"] == "slicefree" else 0, want=("y", "S"))
         ys = y[:min(used, 400)].cpu().numpy()   # y holds the last timed step's result
@@ -715,9 +734,11 @@ def main():
                                   "rms_rel": float(np.sqrt(np.mean(relo ** 2))),
                                   "per_output_max": [float(v) for v in relo.max(0)],
                                   "scale": "max(|y|, sum of |terms|)"}
-        out["cpu_baseline"] = {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                               "sample": f"first {used} of the {n} queries, single thread "
-                                         f"(~20 s of CPU work)"}
+        out["cpu_baseline"] = {"value": rate_par, "unit": "evals/s", "cores": threads, "kind": "oracle",
+                               "sample": f"first {n_par} of the {n} queries over {threads} host threads "
+                                         f"(~10 s of CPU work)",
+                               "single_thread": {"value": rate, "sample": f"first {used} queries, "
+                                                                          f"~10 s"}}
     if rank == 0:
         print(json.dumps(out), flush=True)
     h.close()
