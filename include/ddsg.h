@@ -329,6 +329,22 @@ int euler_residual(irbc_t *model, hdmr_t *policy, int64_t ns, const double *stat
                    const double *guess_dev, double *resid_dev, double *jac_dev,
                    double *euler_err_dev, int precision, int form, ddsg_stream_t stream);
 
+/*
+ * irbc_set_node_mode -- how euler_residual (and so irbc_newton) obtains the
+ * policy at the 2(N+1) monomial-rule nodes of each state.
+ *   DDSG_IRBC_NODES_ALL (default): the interpolant at every node, as written.
+ *   DDSG_IRBC_NODES_DELTA: the nodes of one state differ only in a' (footnote
+ *     to Sec. 2.1's expectation: country node +-i shocks a'_i alone, the two
+ *     global nodes shock every a'). The policy is interpolated at the no-shock
+ *     state and the two global nodes; at country node +-i it is the no-shock
+ *     policy plus, for each component holding a_i, that component at the
+ *     shocked a'_i minus it at the no-shock a'_i (exact by the additive cut-HDMR
+ *     form; differences are rounding only). Needs no assumption on the
+ *     component set. About N times less interpolation work.
+ */
+enum { DDSG_IRBC_NODES_ALL = 0, DDSG_IRBC_NODES_DELTA = 1 };
+int irbc_set_node_mode(irbc_t *model, int mode);
+
 /* Batched dense LU with partial pivoting (FP64): dx = -A^{-1} r for ns
  * systems of size n (A_dev ns x n x n row-major, r_dev/dx_dev ns x n).
  * status_dev[s] is set to 2 for an exactly singular pivot. n <= 165. */
@@ -349,7 +365,8 @@ int irbc_newton(irbc_t *model, hdmr_t *policy, int64_t ns, const double *states_
 
 /* Kernel timing of a model (as hdmr_profile/hdmr_profile_read). Kinds:
  * 0 next-state queries, 1 policy interpolation, 2 residual sums, 3 Jacobian,
- * 4 LU solves, 5 Newton norms/trial points; arrays hold DDSG_NKINDS entries. */
+ * 4 LU solves, 5 Newton norms/trial points, 6 node-shortcut deltas; arrays
+ * hold DDSG_NKINDS entries. */
 int irbc_profile(irbc_t *model, int enable);
 int irbc_profile_read(irbc_t *model, double *ms_host, int64_t *launches_host, int reset);
 

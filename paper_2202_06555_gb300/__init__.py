@@ -74,6 +74,7 @@ SIGNATURES = {
     "mlp_profile": (_int, [_p, _int]),
     "mlp_profile_read": (_int, [_p, _p, _p, _int]),
     "irbc_profile_read": (_int, [_p, _p, _p, _int]),
+    "irbc_set_node_mode": (_int, [_p, _int]),
     "hdmr_profile_read": (_int, [_p, _p, _p, _int]),
 }
 
@@ -363,6 +364,11 @@ class IRBC:
         except Exception:
             pass
 
+    def set_node_mode(self, mode: int):
+        """NODES_ALL: interpolate every monomial node; NODES_DELTA: the no-shock
+        state and the two global nodes, country nodes by component deltas."""
+        _check(load().irbc_set_node_mode(self._h, int(mode)), "irbc_set_node_mode")
+
     def residual(self, policy: HDMR, states_dev, guess_dev, resid_dev, jac_dev=None, err_dev=None,
                  precision: int = F64, form: int = FORM_SLICEFREE, stream=None):
         _check(load().euler_residual(self._h, policy._h, states_dev.shape[0], _dev_ptr(states_dev),
@@ -379,7 +385,8 @@ class IRBC:
                                   int(form), _stream_ptr(stream)), "irbc_newton")
 
 
-IRBC_KINDS = ["queries", "eval", "residual", "jacobian", "lu", "newton_aux", "k6", "k7"]
+IRBC_KINDS = ["queries", "eval", "residual", "jacobian", "lu", "newton_aux", "node_delta", "k7"]
+NODES_ALL, NODES_DELTA = 0, 1
 
 
 def _irbc_profile(self, enable=True):

@@ -454,6 +454,182 @@ __global__ void trial_kernel(int n, int64_t ns, const double *__restrict__ z, co
     zt[e] = active[s] ? z[e] + step[s] * dz[e] : z[e];
 }
 
+// ---------------------------------------------------------------------------
+// node shortcut: the 2(N+1) next states of one state differ only in a'. For a
+// country node (2i or 2i+1) only a'_i moves off its no-shock value, so the
+// policy there is the no-shock policy plus, for each component holding a_i,
+// that component at the shocked a'_i minus it at the no-shock a'_i. Only the
+// no-shock state and the two global-shock nodes (2N, 2N+1: every a' shocked)
+// are interpolated in full.
+// ---------------------------------------------------------------------------
+
+// 3 queries per state: 0 no shock, 1 every country +, 2 every country - (the
+// global nodes). Clamps are counted with the multiplicity the 2(N+1) node
+// queries would have, so the clamp counter agrees with the full path.
+__global__ void irbc_queries3_kernel(IrbcDev P, int64_t ns, const double *__restrict__ states,
+                                     const double *__restrict__ guess, const double *__restrict__ lo,
+                                     const double *__restrict__ span, uint64_t *__restrict__ X,
+                                     int32_t *__restrict__ flags, unsigned long long *__restrict__ stats) {
+    const int N = P.N, d = 2 * N, m = N + 1, nq = 2 * (N + 1);
+    const int64_t Q3 = ns * 3;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long clamps = 0;
+    if (idx < ns * d) {
+        const int64_t s = idx / d;
+        const int dim = (int)(idx - s * d);
+        bool bad = false;
+        uint64_t *Xrow = X + (int64_t)dim * Q3 + s * 3;
+        if (dim < N) {
+            double v[3];
+            next_a3(P, states[s * d + dim], v[0], v[1], v[2]);
+            const unsigned long long mult[3] = {(unsigned long long)(nq - 4), 2ull, 2ull};
+            for (int t = 0; t < 3; ++t) {
+                unsigned long long c1 = 0;
+                Xrow[t] = encode_coord(v[t], lo[dim], span[dim], bad, c1);
+                clamps += c1 * mult[t];
+            }
+            if (!isfinite(states[s * d + N + dim])) bad = true;
+        } else {
+            const uint64_t e = encode_coord(guess[s * m + dim - N], lo[dim], span[dim], bad, clamps);
+            clamps *= (unsigned long long)nq;
+            for (int t = 0; t < 3; ++t) Xrow[t] = e;
+            if (dim == d - 1 && !isfinite(guess[s * m + N])) bad = true;
+        }
+        if (bad)
+            for (int t = 0; t < 3; ++t) flags[s * 3 + t] = 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) clamps += __shfl_down_sync(0xffffffffu, clamps, o);
+    if ((threadIdx.x & 31) == 0 && clamps) atomicAdd(&stats[0], clamps);
+}
+
+template <int PREC>
+struct DeltaT;
+template <>
+struct DeltaT<DDSG_F64> {
+    using W = double;
+    static __device__ __forceinline__ const double *alpha(const DevTables &t) { return t.alpha64; }
+    static __device__ __forceinline__ int stride(const DevTables &t) { return t.mp64; }
+};
+template <>
+struct DeltaT<DDSG_F32C> {
+    using W = float;
+    static __device__ __forceinline__ const float *alpha(const DevTables &t) { return t.alpha32; }
+    static __device__ __forceinline__ int stride(const DevTables &t) { return t.mp32; }
+};
+
+// acc[o] += coef * s_c(x)[m0 + o] for one component c at coordinates Xd (one per
+// component dimension), the tuples [tb, te) (interior ones in the slice-free form).
+template <int PREC, int MC>
+__device__ __forceinline__ void comp_at(const DevTables &t, const DevComp &cd, int tb, double coef,
+                                        const uint64_t *Xd, int m0, int mv,
+                                        typename DeltaT<PREC>::W (&acc)[MC]) {
+    using W = typename DeltaT<PREC>::W;
+    const W *alpha = DeltaT<PREC>::alpha(t);
+    const int mp = DeltaT<PREC>::stride(t);
+    for (int ti = tb; ti < cd.tup_end; ++ti) {
+        const DevTup tu = t.tups[ti];
+        uint32_t off = 0;
+        double w = coef;
+        bool act = true;
+        for (int j = 0; j < cd.k; ++j) {
+            Basis1D o;
+            const int l = tu.lev[j];
+            if (!basis1d(Xd[j], l, o)) { act = false; break; }
+            off = off * (j == 1 ? tu.nc1 : ncells(l)) + o.cell;
+            w *= (double)o.N * ldexp(1.0, -o.e);
+        }
+        if (!act) continue;
+        const int32_t row = tuple_row(tu, off, t.slots);
+        if (row < 0) continue;
+        const W *r = alpha + (int64_t)row * mp + m0;
+        const W ww = (W)w;
+#pragma unroll
+        for (int o = 0; o < MC; ++o)
+            if (o < mv) acc[o] += ww * r[o];
+    }
+}
+
+// One thread per (state, country i) and output chunk: the policy at the two
+// nodes that shock country i (2i: +, 2i+1: -) is the no-shock policy plus the
+// change of every component holding a_i when a'_i moves to its shocked value;
+// also copies the two global-shock rows. Writes the 2(N+1)-node policy array y
+// in the layout the residual and Jacobian kernels read.
+template <int PREC, int MC>
+__global__ void __launch_bounds__(128) irbc_delta_kernel(IrbcDev P, int64_t s0, int64_t nsc, DevTables t,
+                                                         int form, const int32_t *__restrict__ aoff,
+                                                         const int32_t *__restrict__ acomp,
+                                                         const double *__restrict__ states,
+                                                         const double *__restrict__ guess,
+                                                         const double *__restrict__ lo,
+                                                         const double *__restrict__ span,
+                                                         const double *__restrict__ y3, double *__restrict__ y) {
+    using W = typename DeltaT<PREC>::W;
+    const int N = P.N, d = 2 * N, m = N + 1, nq = 2 * (N + 1);
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nsc * N) return;
+    const int64_t sl = idx / N;
+    const int i = (int)(idx - sl * N);
+    const int64_t s = s0 + sl;
+    const int m0 = blockIdx.y * MC;
+    const int mv = min(MC, m - m0);
+    const bool paper = form == DDSG_FORM_PAPER;
+    W acc[3][MC];
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int o = 0; o < MC; ++o) acc[v][o] = (W)0;
+    bool bad = false;
+    unsigned long long cl = 0;
+    double e3[3];
+    next_a3(P, states[s * d + i], e3[0], e3[1], e3[2]);
+    uint64_t Xi[3];
+    for (int v = 0; v < 3; ++v) Xi[v] = encode_coord(e3[v], lo[i], span[i], bad, cl);
+    for (int e = aoff[i]; e < aoff[i + 1] && !bad; ++e) {
+        const DevComp &cd = t.comps[acomp[e]];
+        const double coef = paper ? cd.b : 1.0;
+        if (coef == 0.0) continue;
+        const int tb = paper ? cd.tup_begin : cd.tup_int;
+        uint64_t Xd[KMAX];
+        int pos = 0;
+        for (int j = 0; j < cd.k; ++j) {
+            const int dj = cd.dims[j];
+            if (dj == i) {
+                pos = j;
+                Xd[j] = 0;
+            } else if (dj < N) {
+                double f0, fp, fm;
+                next_a3(P, states[s * d + dj], f0, fp, fm);
+                Xd[j] = encode_coord(f0, lo[dj], span[dj], bad, cl);
+            } else {
+                Xd[j] = encode_coord(guess[s * m + dj - N], lo[dj], span[dj], bad, cl);
+            }
+        }
+        if (bad) break;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            Xd[pos] = Xi[v];
+            comp_at<PREC, MC>(t, cd, tb, coef, Xd, m0, mv, acc[v]);
+        }
+    }
+    const double *yb = y3 + (sl * 3) * (int64_t)m + m0;
+    double *yp = y + (sl * nq + 2 * i) * (int64_t)m + m0;
+    double *ym = y + (sl * nq + 2 * i + 1) * (int64_t)m + m0;
+#pragma unroll
+    for (int o = 0; o < MC; ++o) {
+        if (o < mv) {
+            const double b0 = (double)acc[0][o];
+            yp[o] = bad ? NAN : yb[o] + ((double)acc[1][o] - b0);
+            ym[o] = bad ? NAN : yb[o] + ((double)acc[2][o] - b0);
+        }
+    }
+    if (i == 0) {
+        for (int o = 0; o < mv; ++o) {
+            y[(sl * nq + 2 * N) * (int64_t)m + m0 + o] = y3[(sl * 3 + 1) * (int64_t)m + m0 + o];
+            y[(sl * nq + 2 * N + 1) * (int64_t)m + m0 + o] = y3[(sl * 3 + 2) * (int64_t)m + m0 + o];
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -462,6 +638,7 @@ __global__ void trial_kernel(int n, int64_t ns, const double *__restrict__ z, co
 
 struct irbc {
     irbc_params_t p;
+    int node_mode = DDSG_IRBC_NODES_ALL;
     Tracer tr;   // kinds: 0 queries, 1 eval, 2 residual, 3 jacobian, 4 lu, 5 newton helpers
     std::vector<double> gamma, tau;
     int device = -1;
@@ -524,7 +701,48 @@ int k_components(hdmr_t *h, int N, std::vector<int32_t> &out) {
     return DDSG_OK;
 }
 
+// CSR over the dims i < N (the a_i): the components that hold a_i.
+int a_components(hdmr_t *h, int N, std::vector<int32_t> &off, std::vector<int32_t> &ids) {
+    int32_t nc = 0;
+    int64_t np = 0;
+    int rc = hdmr_num_components(h, &nc, &np);
+    if (rc) return rc;
+    std::vector<std::vector<int32_t>> per(N);
+    for (int32_t c = 0; c < nc; ++c) {
+        int32_t kk = 0, dims[DDSG_KMAX];
+        hdmr_component_info(h, c, &kk, dims, nullptr, nullptr);
+        for (int j = 0; j < kk; ++j)
+            if (dims[j] < N) per[dims[j]].push_back(c);
+    }
+    off.assign(N + 1, 0);
+    ids.clear();
+    for (int i = 0; i < N; ++i) {
+        ids.insert(ids.end(), per[i].begin(), per[i].end());
+        off[i + 1] = (int32_t)ids.size();
+    }
+    return DDSG_OK;
+}
+
+template <int PREC, int MC>
+cudaError_t launch_delta(const IrbcDev &P, int64_t s0, int64_t nsc, const DevTables &t, int form,
+                         const int32_t *aoff, const int32_t *acomp, const double *states, const double *guess,
+                         const double *lo, const double *span, const double *y3, double *y, cudaStream_t st) {
+    const int m = P.N + 1;
+    dim3 grid((unsigned)((nsc * P.N + 127) / 128), (unsigned)((m + MC - 1) / MC));
+    irbc_delta_kernel<PREC, MC><<<grid, 128, 0, st>>>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span,
+                                                       y3, y);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+extern "C" int irbc_set_node_mode(irbc_t *M, int mode) {
+    if (!M) return set_error(DDSG_ERR_ARG, "irbc_set_node_mode: NULL model");
+    if (mode != DDSG_IRBC_NODES_ALL && mode != DDSG_IRBC_NODES_DELTA)
+        return set_error(DDSG_ERR_ARG, "irbc_set_node_mode: unknown mode");
+    M->node_mode = mode;
+    return DDSG_OK;
+}
 
 extern "C" int irbc_create(const irbc_params_t *prm, const double *gamma_host, const double *tau_host,
                            irbc_t **out) {
@@ -581,12 +799,22 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
         if ((rc = k_components(policy, N, kc))) return rc;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // per state: X (d*nq*8) + flags (nq*4) + y (nq*m*8) + aux (7N*8)
-    const size_t per_state = (size_t)nq * (d * 8 + 4 + m * 8) + (size_t)7 * N * 8;
+    const bool delta = M->node_mode == DDSG_IRBC_NODES_DELTA;
+    std::vector<int32_t> aoff, acomp;
+    if (delta && (rc = a_components(policy, N, aoff, acomp))) return rc;
+    // interpolated queries per state: all 2(N+1) nodes, or (node shortcut) the
+    // no-shock state and the two global-shock nodes
+    const int nqe = delta ? 3 : nq;
+    // per state: X (d*nqe*8) + flags (nqe*4) + y of the shortcut's 3 queries + y
+    // of all nodes (nq*m*8) + aux (7N*8)
+    const size_t per_state = (size_t)nqe * (d * 8 + 4) + (delta ? (size_t)3 * m * 8 : 0) +
+                             (size_t)nq * m * 8 + (size_t)7 * N * 8;
     int64_t chunk = std::max<int64_t>(1, (int64_t)(kWsCap / per_state));
     chunk = std::min<int64_t>(chunk, ns);
-    const size_t kc_bytes = jac_dev ? ((sizeof(int32_t) * kc.size() + 255) & ~(size_t)255) : 0;
-    if ((rc = ensure(M, per_state * chunk + 4096 + kc_bytes))) return rc;
+    auto rnd = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t kc_bytes = jac_dev ? rnd(sizeof(int32_t) * kc.size()) : 0;
+    const size_t ac_bytes = delta ? rnd(sizeof(int32_t) * aoff.size()) + rnd(sizeof(int32_t) * (acomp.size() + 1)) : 0;
+    if ((rc = ensure(M, per_state * chunk + 4096 + kc_bytes + ac_bytes))) return rc;
     unsigned char *base = static_cast<unsigned char *>(M->ws);
     if (jac_dev) {
         kc_dev = reinterpret_cast<int32_t *>(base);
@@ -594,21 +822,38 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
             return set_error(DDSG_ERR_CUDA, "euler_residual: copy failed");
         base += kc_bytes;
     }
+    int32_t *aoff_dev = nullptr, *acomp_dev = nullptr;
+    if (delta) {
+        aoff_dev = reinterpret_cast<int32_t *>(base);
+        acomp_dev = reinterpret_cast<int32_t *>(base + rnd(sizeof(int32_t) * aoff.size()));
+        if (cudaMemcpyAsync(aoff_dev, aoff.data(), sizeof(int32_t) * aoff.size(), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            (!acomp.empty() && cudaMemcpyAsync(acomp_dev, acomp.data(), sizeof(int32_t) * acomp.size(),
+                                               cudaMemcpyHostToDevice, st) != cudaSuccess))
+            return set_error(DDSG_ERR_CUDA, "euler_residual: copy failed");
+        base += ac_bytes;
+    }
     const IrbcDev P = dev_params(M);
     for (int64_t s0 = 0; s0 < ns; s0 += chunk) {
         const int64_t nsc = std::min<int64_t>(chunk, ns - s0);
-        const int64_t Q = nsc * nq;
+        const int64_t Q = nsc * nq, Qe = nsc * nqe;
         uint64_t *X = reinterpret_cast<uint64_t *>(base);
-        int32_t *flags = reinterpret_cast<int32_t *>(X + (int64_t)d * Q);
-        double *y = reinterpret_cast<double *>(((uintptr_t)(flags + Q) + 255) & ~(uintptr_t)255);
+        int32_t *flags = reinterpret_cast<int32_t *>(X + (int64_t)d * Qe);
+        double *y3 = reinterpret_cast<double *>(((uintptr_t)(flags + Qe) + 255) & ~(uintptr_t)255);
+        double *y = delta ? y3 + Qe * m : y3;
         double *aux = y + Q * m;
-        cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int32_t) * Q, st);
+        cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int32_t) * Qe, st);
         if (e == cudaSuccess) {
             Tracer::Scope ts(&M->tr, 0, st);
             const int64_t th = nsc * d;
-            irbc_queries_kernel<<<(unsigned)((th + 255) / 256), 256, 0, st>>>(
-                P, nsc, states_dev + s0 * d, guess_dev + s0 * m, v.lo, v.span, X, flags,
-                reinterpret_cast<unsigned long long *>(v.stats));
+            if (delta)
+                irbc_queries3_kernel<<<(unsigned)((th + 255) / 256), 256, 0, st>>>(
+                    P, nsc, states_dev + s0 * d, guess_dev + s0 * m, v.lo, v.span, X, flags,
+                    reinterpret_cast<unsigned long long *>(v.stats));
+            else
+                irbc_queries_kernel<<<(unsigned)((th + 255) / 256), 256, 0, st>>>(
+                    P, nsc, states_dev + s0 * d, guess_dev + s0 * m, v.lo, v.span, X, flags,
+                    reinterpret_cast<unsigned long long *>(v.stats));
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) {
@@ -616,9 +861,9 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
             a.t = v.tables;
             a.d = d;
             a.m = m;
-            a.n = Q;
+            a.n = Qe;
             a.X = X;
-            a.y = y;
+            a.y = y3;
             a.hash = nullptr;
             a.count = nullptr;
             a.form = form;
@@ -627,6 +872,15 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
             a.err = reinterpret_cast<unsigned long long *>(v.stats + 2);
             Tracer::Scope ts(&M->tr, 1, st);
             e = launch_eval(a, st);
+        }
+        if (e == cudaSuccess && delta) {
+            Tracer::Scope ts(&M->tr, 6, st);
+            if (precision == DDSG_F64)
+                e = launch_delta<DDSG_F64, 16>(P, s0, nsc, *v.tables, form, aoff_dev, acomp_dev, states_dev,
+                                               guess_dev, v.lo, v.span, y3, y, st);
+            else
+                e = launch_delta<DDSG_F32C, 16>(P, s0, nsc, *v.tables, form, aoff_dev, acomp_dev, states_dev,
+                                                guess_dev, v.lo, v.span, y3, y, st);
         }
         if (e == cudaSuccess) {
             Tracer::Scope ts(&M->tr, 2, st);

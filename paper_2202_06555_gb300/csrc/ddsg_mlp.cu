@@ -38,6 +38,7 @@ struct Epi {
     const float *bias;   // HIDDEN, LAST
     const float *zp;     // GELU_BWD: pre-activation of the layer below
     int ldzp;
+    int64_t zstride;     // STORE with split K: split z writes f + z * zstride
 };
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -56,11 +57,13 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
 
 // C[M x N] = op(A)[M x K] * op(B)[N x K]^T. TA: A is stored K x M (element
 // (m, k) at A[k*lda + m]); otherwise M x K. TB likewise for B (N x K or K x N).
-// M, N multiples of 64 and K a multiple of 32 (the callers pad).
+// M, N multiples of 64 and K a multiple of 32 (the callers pad). Split K: block
+// z of the grid's third dimension covers k in [z*kchunk, min(K, (z+1)*kchunk))
+// and (STORE only) writes its partial product at f + z * zstride.
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A,
                                                                  int lda, const __nv_bfloat16 *__restrict__ B, int ldb,
-                                                                 Epi e) {
+                                                                 Epi e, int kchunk) {
     __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PADK];
     __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PADK];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -75,13 +78,14 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(int M, int N, i
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
 
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    for (int k0 = kb; k0 < ke; k0 += BK) {
         for (int idx = tid; idx < BM * BK; idx += GEMM_THREADS) {
             int r, c;
             if (TA) { r = idx % BM; c = idx / BM; } else { r = idx / BK; c = idx % BK; }
             const int m = bm + r, k = k0 + c;
             __nv_bfloat16 v = __float2bfloat16(0.f);
-            if (m < M && k < K) v = TA ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k];
+            if (m < M && k < ke) v = TA ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k];
             As[r][c] = v;
         }
         for (int idx = tid; idx < BN * BK; idx += GEMM_THREADS) {
@@ -89,7 +93,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(int M, int N, i
             if (TB) { r = idx % BN; c = idx / BN; } else { r = idx / BK; c = idx % BK; }
             const int n = bn + r, k = k0 + c;
             __nv_bfloat16 v = __float2bfloat16(0.f);
-            if (n < N && k < K) v = TB ? B[(int64_t)k * ldb + n] : B[(int64_t)n * ldb + k];
+            if (n < N && k < ke) v = TB ? B[(int64_t)k * ldb + n] : B[(int64_t)n * ldb + k];
             Bs[r][c] = v;
         }
         __syncthreads();
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(int M, int N, i
                 if (row >= M || col >= N) continue;
                 const float v = acc[i][j][r];
                 if (EPI == EPI_STORE) {
-                    e.f[(int64_t)row * e.ldf + col] = v;
+                    e.f[(int64_t)blockIdx.z * e.zstride + (int64_t)row * e.ldf + col] = v;
                 } else if (EPI == EPI_HIDDEN) {
                     const float z = v + e.bias[col];
                     if (e.z) e.z[(int64_t)row * e.ldz + col] = z;
@@ -147,10 +151,22 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(int M, int N, i
 
 template <bool TA, bool TB, int EPI>
 cudaError_t gemm(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
-                 const Epi &e, cudaStream_t st) {
-    dim3 grid((unsigned)(N / BN), (unsigned)(M / BM));
-    gemm_bf16_kernel<TA, TB, EPI><<<grid, GEMM_THREADS, 0, st>>>(M, N, K, A, lda, B, ldb, e);
+                 const Epi &e, cudaStream_t st, int splits = 1, int kchunk = 0) {
+    dim3 grid((unsigned)(N / BN), (unsigned)(M / BM), (unsigned)splits);
+    gemm_bf16_kernel<TA, TB, EPI><<<grid, GEMM_THREADS, 0, st>>>(M, N, K, A, lda, B, ldb, e, splits > 1 ? kchunk : K);
     return cudaGetLastError();
+}
+
+// Split of the batch dimension (K of the weight-gradient GEMM) so that the
+// (Po/64) x (Pi/64) output tiles times the splits fill the SMs about twice;
+// chunks are multiples of BK.
+void grad_split(int64_t Bp, int Po, int Pi, int &splits, int &kchunk) {
+    const int tiles = (Po / BM) * (Pi / BN);
+    const int want = std::max(1, (2 * 152 + tiles - 1) / tiles);
+    const int64_t kmax = std::max<int64_t>(1, Bp / BK);
+    const int s = (int)std::min<int64_t>(want, kmax);
+    kchunk = (int)(((Bp + s - 1) / s + BK - 1) / BK * BK);
+    splits = (int)((Bp + kchunk - 1) / kchunk);
 }
 
 // x (B x n0, FP64 physical) -> (x - shift) * scale as BF16 in B_pad x P0 (zero padding)
@@ -191,12 +207,34 @@ __global__ void mlp_loss_kernel(int64_t B, int64_t Bp, int m, int PL, const floa
 }
 
 // column sums of dZ (Bp x P): one thread per column, rows in order
-__global__ void colsum_kernel(int64_t Bp, int P, const float *__restrict__ dZ, float *__restrict__ gb) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= P) return;
+// Partial column sums of dZ (Bp x P) over the rows [z*kchunk, min(Bp, (z+1)*kchunk))
+// of block z: 32 columns x 8 row lanes per block, part[z*P + c].
+__global__ void colsum_part_kernel(int64_t Bp, int P, int kchunk, const float *__restrict__ dZ,
+                                   float *__restrict__ part) {
+    __shared__ float s[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + tx;
+    const int64_t b0 = (int64_t)blockIdx.y * kchunk, b1 = min(Bp, b0 + kchunk);
+    float acc = 0.f;
+    if (c < P)
+        for (int64_t b = b0 + ty; b < b1; b += 8) acc += dZ[b * P + c];
+    s[ty][tx] = acc;
+    __syncthreads();
+    if (ty == 0 && c < P) {
+        float t = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t += s[i][tx];
+        part[(int64_t)blockIdx.y * P + c] = t;
+    }
+}
+
+// out[i] = sum over z of part[z*n + i], in z order (deterministic)
+__global__ void splitk_reduce_kernel(int splits, int64_t n, const float *__restrict__ part, float *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
     float s = 0.f;
-    for (int64_t b = 0; b < Bp; ++b) s += dZ[b * P + c];
-    gb[c] = s;
+    for (int z = 0; z < splits; ++z) s += part[(int64_t)z * n + i];
+    out[i] = s;
 }
 
 // Adam on one parameter tensor (FP32 master), refreshing its BF16 copy and,
@@ -326,6 +364,7 @@ struct WsView {
     float *Y;
     float *dZ[2];
     __nv_bfloat16 *dZb[2];
+    float *split;   // split-K partials of one layer's weight and bias gradients
 };
 
 int mlp_ws(mlp *M, int64_t Bp, WsView &v) {
@@ -338,6 +377,13 @@ int mlp_ws(mlp *M, int64_t Bp, WsView &v) {
     for (int l = 0; l + 1 < L; ++l) need += rnd((size_t)Bp * M->P[l + 1] * 4);
     need += rnd((size_t)Bp * M->P[L] * 4);
     need += 2 * rnd((size_t)Bp * Pmax * 4) + 2 * rnd((size_t)Bp * Pmax * 2);
+    size_t split_floats = 0;
+    for (int l = 0; l < L; ++l) {
+        int s = 1, kc = 0;
+        grad_split(Bp, M->P[l + 1], M->P[l], s, kc);
+        split_floats = std::max(split_floats, (size_t)s * ((size_t)M->P[l + 1] * M->P[l] + M->P[l + 1]));
+    }
+    need += rnd(split_floats * 4);
     if (Bp > M->cap) {
         cudaFree(M->ws);
         M->ws = nullptr;
@@ -357,6 +403,7 @@ int mlp_ws(mlp *M, int64_t Bp, WsView &v) {
     v.Y = (float *)take((size_t)Bp * M->P[L] * 4);
     for (int i = 0; i < 2; ++i) v.dZ[i] = (float *)take((size_t)Bp * Pmax * 4);
     for (int i = 0; i < 2; ++i) v.dZb[i] = (__nv_bfloat16 *)take((size_t)Bp * Pmax * 2);
+    v.split = (float *)take(split_floats * 4);
     return DDSG_OK;
 }
 
@@ -507,13 +554,22 @@ extern "C" int mlp_train_step(mlp_t *M, int64_t B, const double *x_dev, const do
     for (int l = L - 1; l >= 0 && e == cudaSuccess; --l) {
         Tracer::Scope ts(&M->tr, 1, st);
         const int Pi = M->P[l], Po = M->P[l + 1];
+        // gW = dZ^T (Po x Bp) * X_l (Bp x Pi): both operands stored transposed; the
+        // batch (K) is split over blocks, partials summed in split order
+        int splits = 1, kchunk = 0;
+        grad_split(Bp, Po, Pi, splits, kchunk);
+        const int64_t nw = (int64_t)Po * Pi;
+        float *pw = v.split, *pb = v.split + (int64_t)splits * nw;
         Epi g = {};
-        g.f = M->gW[l];
+        g.f = pw;
         g.ldf = Pi;
-        // gW = dZ^T (Po x Bp) * X_l (Bp x Pi): both operands stored transposed
-        e = gemm<true, true, EPI_STORE>(Po, Pi, (int)Bp, v.dZb[cur], Po, v.X[l], Pi, g, st);
+        g.zstride = nw;
+        e = gemm<true, true, EPI_STORE>(Po, Pi, (int)Bp, v.dZb[cur], Po, v.X[l], Pi, g, st, splits, kchunk);
         if (e == cudaSuccess) {
-            colsum_kernel<<<(unsigned)((Po + 127) / 128), 128, 0, st>>>(Bp, Po, v.dZ[cur], M->gb[l]);
+            colsum_part_kernel<<<dim3((unsigned)((Po + 31) / 32), (unsigned)splits), 256, 0, st>>>(Bp, Po, kchunk,
+                                                                                                v.dZ[cur], pb);
+            splitk_reduce_kernel<<<nblk(nw), 256, 0, st>>>(splits, nw, pw, M->gW[l]);
+            splitk_reduce_kernel<<<nblk(Po), 256, 0, st>>>(splits, Po, pb, M->gb[l]);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess && l > 0) {
