@@ -72,12 +72,13 @@ def comp_list(w):
 
 
 # DRAM traffic of the evaluation kernel from one ncu capture (profiles/
-# eval_tma_d100_ncu_full.md: d=100 tables, 32768 queries, TMA-staged kernel at
-# 52 outputs per pass), per query; scaled to a full launch by the query count.
+# eval_tma_d100_ncu_full.md: d=100 tables, 29184 queries, two-group TMA-staged
+# kernel at 28 outputs per group), per query; scaled to a full launch by the
+# query count.
 # Valid only for the kernel sources it was taken on (checked by hash).
-EVAL_TRAFFIC = {"workload": "d100", "schedule": (2, 52), "dram_bytes_per_query": 210224896 / 32768,
-                "sha1": {"ddsg_kernels.cu": "e9ef86f4009a1c92761de5edfd68c9fb6639e6de",
-                         "ddsg_internal.h": "74f20921f3dac1edc2476ed883c1c071259d09de"}}
+EVAL_TRAFFIC = {"workload": "d100", "schedule": (3, 28), "dram_bytes_per_query": (202206720 + 3965952) / 29184,
+                "sha1": {"ddsg_kernels.cu": "568423b2407be421b6d2b00b48511a7d04d64260",
+                         "ddsg_internal.h": "6c9dcc1d53f0f53a3ae86a24887ca81e5440dc88"}}
 
 
 def eval_traffic(workload, schedule, n):
@@ -398,7 +399,7 @@ def run_irbc(args, w):
                       "states": ns, "nodes": nq, "evals_per_sweep": ns * nq,
                       "policy": "empty + 2N singles + N (a_j,k_j) pairs, regular level 4",
                       "precision": w["precision"], "form": w["form"],
-                      "schedule": {"kernel": ["tile", "per-tuple", "tma-staged tile"][tuned[0]],
+                      "schedule": {"kernel": ["tile", "per-tuple", "tma-staged tile", "tma-staged, 2 warp groups"][tuned[0]],
                                    "outputs_per_pass": tuned[1]}},
            "kernels_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
            "gpu_launches": sum(v[1] for v in prof.values()),
@@ -692,7 +693,7 @@ def main():
                       "eps_gamma": w["eps"], "max_level": w["level"], "queries_per_gpu": n,
                       "precision": w["precision"], "form": w["form"],
                       "active_points_per_query": active_total / n,
-                      "schedule": {"kernel": ["tile", "per-tuple", "tma-staged tile"][tuned[0]], "outputs_per_pass": tuned[1],
+                      "schedule": {"kernel": ["tile", "per-tuple", "tma-staged tile", "tma-staged, 2 warp groups"][tuned[0]], "outputs_per_pass": tuned[1],
                                    "autotune_subset": nt},
                       "l2": "inputs larger than L2 (x %.2f GB, surpluses %.2f GB); no flush"
                             % (n * w["d"] * 8 / 1e9, npts * w["m"] * (4 if prec == G.F32C else 8) / 1e9),

@@ -474,13 +474,13 @@ __global__ void __launch_bounds__(TQ) eval_tile_kernel(const EvalParams p) {
 
 
 // ---------------------------------------------------------------------------
-// TMA-staged tile kernel: 256 queries per block; the surplus rows each
-// component contributes (all rows, or the interior rows for the slice-free
-// form) are one contiguous device-row range, copied into shared memory by a
-// bulk TMA copy two components ahead (double buffer, one mbarrier each).
+// TMA-staged tile kernel (kernel 2: one warp group, 256 queries per block;
+// kernel 3: two warp groups splitting each query's outputs, 192 queries per
+// block). The surplus rows each component contributes (all rows, or the
+// interior rows for the slice-free form) are one contiguous device-row range,
+// copied into shared memory by a bulk TMA copy two components ahead.
 // ---------------------------------------------------------------------------
 
-constexpr int TQ2 = 256;
 constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait calls before giving up
 constexpr int kSmemLimit = 232448;          // opt-in shared memory per block (227 KiB)
 constexpr int TMA_NBUF_MAX = 3;             // staging buffers of the TMA-staged kernel
@@ -528,10 +528,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
-template <int PREC>
-__host__ __device__ constexpr int tma_fixed_smem() {
-    return 128 + (int)sizeof(uint16_t) * 2 * LT * TQ2 +
-           (int)sizeof(typename std::conditional<PREC == DDSG_F64, double, float>::type) * 2 * LT * TQ2;
+// Block shape of the TMA-staged kernel with GR warp groups: QB queries per
+// block; each query's output chunk is split over GR threads (one per group).
+template <int GR>
+struct TmaShape {
+    static constexpr int QB = GR == 1 ? 256 : 192;   // queries per block
+    static constexpr int NT = QB * GR;               // threads per block
+    static constexpr int QW = QB / 32;               // query warps per group
+};
+
+// shared memory before the staging buffers: barriers, per-query 1D basis
+__host__ __device__ inline int tma_fixed_smem(int precision, int qb) {
+    return 128 + (int)sizeof(uint16_t) * 2 * LT * qb + (precision == DDSG_F64 ? 8 : 4) * 2 * LT * qb;
 }
 
 // bytes of one staging buffer: component struct, its level tuples, its surplus rows
@@ -540,16 +548,15 @@ __host__ __device__ inline int tma_buf_bytes(int64_t stage) {
 }
 
 // shared memory of one probed tuple: a row index and a weight per query
-inline int tma_probe_bytes(int precision) {
-    return TQ2 * (4 + (precision == DDSG_F64 ? 8 : 4));
+inline int tma_probe_bytes(int precision, int qb) {
+    return qb * (4 + (precision == DDSG_F64 ? 8 : 4));
 }
 
 // Staging buffers (3 when they fit, else 2) and probe batch (tuples probed per
 // pass, at most the largest tuple count and TMA_PB_MAX) that fit in shared
 // memory beside the fixed part; pb = 0 when not even two tuples fit.
-inline void tma_layout(const DevTables &t, int precision, int fixed, int buf, int &nbuf, int &pb) {
+inline void tma_layout(const DevTables &t, int fixed, int buf, int per, int &nbuf, int &pb) {
     const int want = t.max_tuples < 2 ? 2 : (t.max_tuples < TMA_PB_MAX ? t.max_tuples : TMA_PB_MAX);
-    const int per = tma_probe_bytes(precision);
     for (nbuf = TMA_NBUF_MAX; nbuf >= 2; --nbuf) {
         const int64_t left = (int64_t)kSmemLimit - fixed - (int64_t)nbuf * buf;
         pb = left > 0 ? (int)(left / per) : 0;
@@ -559,32 +566,35 @@ inline void tma_layout(const DevTables &t, int precision, int fixed, int buf, in
     if (pb < 2) pb = 0;
 }
 
+// queries per block of evaluation kernel `kernel` (2, 3: the TMA-staged kernel)
+static int tma_qb(int kernel) { return kernel == 3 ? TmaShape<2>::QB : TmaShape<1>::QB; }
+
 bool eval_kernel_eligible(const DevTables &t, int kernel, int precision, int form) {
     if (kernel == 0 || kernel == 1) return true;
-    if (kernel != 2) return false;
+    if (kernel != 2 && kernel != 3) return false;
     if (!t.tile_ok) return false;   // the staged kernel handles only k <= 2, levels <= LT
     if (t.max_tuples > TMA_TUP_MAX) return false;
-    const int fixed = precision == DDSG_F64 ? tma_fixed_smem<DDSG_F64>() : tma_fixed_smem<DDSG_F32C>();
+    const int qb = tma_qb(kernel);
     const int64_t bytes = t.stage_bytes[form][precision];
     if (bytes > TMA_STAGE_MAX) return false;
     int nbuf = 0, pb = 0;
-    tma_layout(t, precision, fixed, tma_buf_bytes(bytes), nbuf, pb);
+    tma_layout(t, tma_fixed_smem(precision, qb), tma_buf_bytes(bytes), tma_probe_bytes(precision, qb), nbuf, pb);
     return pb > 0;
 }
 
-// 1D basis of levels 1..lm at fixed-point coordinate X into staging slot j:
-// cell (bit 15 = query on a face at that level) and hat value.
-template <int PREC>
-__device__ __forceinline__ void tma_stage(uint64_t X, int lm, int tid, uint16_t (*s_cell)[LT][TQ2],
-                                          typename Types<PREC>::W (*s_t)[LT][TQ2], int j) {
+// 1D basis of levels 1..lm at fixed-point coordinate X into staging slot j of
+// query qi: cell (bit 15 = query on a face at that level) and hat value.
+template <int PREC, int QB>
+__device__ __forceinline__ void tma_stage(uint64_t X, int lm, int qi, uint16_t (*s_cell)[LT][QB],
+                                          typename Types<PREC>::W (*s_t)[LT][QB], int j) {
     using W = typename Types<PREC>::W;
-    s_cell[j][0][tid] = 0;
-    s_t[j][0][tid] = (W)1;
+    s_cell[j][0][qi] = 0;
+    s_t[j][0][qi] = (W)1;
     if (lm >= 2) {
         Basis1D o;
         const bool act = basis1d(X, 2, o);
-        s_cell[j][1][tid] = act ? (uint16_t)o.cell : (uint16_t)0x8000u;
-        s_t[j][1][tid] = basis_val<W>(o);
+        s_cell[j][1][qi] = act ? (uint16_t)o.cell : (uint16_t)0x8000u;
+        s_t[j][1][qi] = basis_val<W>(o);
     }
     for (int l = 3; l <= lm; ++l) {
         // cell width 2^sh; position F in the cell; phi numerator N = min(F, 2^sh - F)
@@ -595,39 +605,39 @@ __device__ __forceinline__ void tma_stage(uint64_t X, int lm, int tid, uint16_t 
         const uint64_t F = X - (cell << sh);
         const uint64_t R = (1ull << sh) - F;
         const uint64_t N = F < R ? F : R;
-        s_cell[j][l - 1][tid] = N ? (uint16_t)cell : (uint16_t)0x8000u;
-        if constexpr (PREC == DDSG_F64) s_t[j][l - 1][tid] = basis_to_f64(N, sh - 1);
-        else s_t[j][l - 1][tid] = __uint2float_rn((uint32_t)(N >> (32 - l))) * pow2m_f(31);
+        s_cell[j][l - 1][qi] = N ? (uint16_t)cell : (uint16_t)0x8000u;
+        if constexpr (PREC == DDSG_F64) s_t[j][l - 1][qi] = basis_to_f64(N, sh - 1);
+        else s_t[j][l - 1][qi] = __uint2float_rn((uint32_t)(N >> (32 - l))) * pow2m_f(31);
     }
 }
 
-// Probe one level tuple for this thread's query: the staged row of the point
-// whose support holds the query (-1 if there is none) and its weight
+// Probe one level tuple for query qi: the staged row of the point whose
+// support holds the query (-1 if there is none) and its weight
 // wb * prod_j phi_j (zero on a miss). Selects instead of branches, apart from
 // the warp-uniform test for a slot-directory tuple. A face flag (bit 15 of a
 // staged cell) masks to cell 0, so off stays inside the tuple's cells.
-template <int PREC, int K>
-__device__ __forceinline__ int32_t tma_probe(const DevTup &tu, const int32_t *slots, int tid,
-                                            const uint16_t (*s_cell)[LT][TQ2],
-                                            const typename Types<PREC>::W (*s_t)[LT][TQ2],
+template <int PREC, int K, int QB>
+__device__ __forceinline__ int32_t tma_probe(const DevTup &tu, const int32_t *slots, int qi,
+                                            const uint16_t (*s_cell)[LT][QB],
+                                            const typename Types<PREC>::W (*s_t)[LT][QB],
                                             typename Types<PREC>::W wb, typename Types<PREC>::W &w,
                                             uint32_t *cells) {
     using W = typename Types<PREC>::W;
     uint32_t off = 0, face = 0;
     W wt = wb;
     if (K >= 1) {
-        const uint32_t ca = s_cell[0][tu.lev[0] - 1][tid];
+        const uint32_t ca = s_cell[0][tu.lev[0] - 1][qi];
         cells[0] = ca;
         face = ca;
         off = ca & 0x7fffu;
         if (K == 1) {
-            wt = wb * s_t[0][tu.lev[0] - 1][tid];
+            wt = wb * s_t[0][tu.lev[0] - 1][qi];
         } else {
-            const uint32_t cb = s_cell[1][tu.lev[1] - 1][tid];
+            const uint32_t cb = s_cell[1][tu.lev[1] - 1][qi];
             cells[1] = cb;
             face |= cb;
             off = off * tu.nc1 + (cb & 0x7fffu);
-            wt = wb * (s_t[0][tu.lev[0] - 1][tid] * s_t[1][tu.lev[1] - 1][tid]);
+            wt = wb * (s_t[0][tu.lev[0] - 1][qi] * s_t[1][tu.lev[1] - 1][qi]);
         }
     }
     int32_t row;
@@ -643,29 +653,28 @@ __device__ __forceinline__ int32_t tma_probe(const DevTup &tu, const int32_t *sl
     return row;
 }
 
-// Probe phase: tuples [0, nb) of stup for this thread's query. Per tuple u the
-// staged row to read goes to s_prow[u*TQ2 + tid] and the weight to s_pw; each
-// thread reads back only its own column, so no barrier is needed. The point
-// hash and count of the parity checks are taken here. A miss has the weight
-// zero and reads the tuple's first row (finite), so that the accumulate phase
-// loads unconditionally.
-template <int PREC, int K, bool HC>
-__device__ __forceinline__ void tma_probe_batch(const EvalParams &p, int c, const DevTup *stup, int nb,
-                                                typename Types<PREC>::W wb, int tid,
-                                                const uint16_t (*s_cell)[LT][TQ2],
-                                                const typename Types<PREC>::W (*s_t)[LT][TQ2], int32_t row0,
+// Probe phase: tuples u = u0, u0 + du, ... below nb of stup for query qi. Per
+// tuple the staged row to read goes to s_prow[u*QB + qi] and the weight to
+// s_pw. The point hash and count of the parity checks are taken here. A miss
+// has the weight zero and reads the tuple's first row (finite), so that the
+// accumulate phase loads unconditionally.
+template <int PREC, int K, bool HC, int QB>
+__device__ __forceinline__ void tma_probe_batch(const EvalParams &p, int c, const DevTup *stup, int nb, int u0,
+                                                int du, typename Types<PREC>::W wb, int qi,
+                                                const uint16_t (*s_cell)[LT][QB],
+                                                const typename Types<PREC>::W (*s_t)[LT][QB], int32_t row0,
                                                 int32_t *s_prow, typename Types<PREC>::W *s_pw, uint64_t &h,
                                                 int32_t &cnt) {
     using W = typename Types<PREC>::W;
 #pragma unroll 4
-    for (int u = 0; u < nb; ++u) {
+    for (int u = u0; u < nb; u += du) {
         const DevTup &tu = stup[u];
         W w;
         uint32_t cl[2] = {0, 0};
-        const int32_t row = tma_probe<PREC, K>(tu, p.t.slots, tid, s_cell, s_t, wb, w, cl);
+        const int32_t row = tma_probe<PREC, K, QB>(tu, p.t.slots, qi, s_cell, s_t, wb, w, cl);
         const bool hit = row >= 0;
-        s_prow[u * TQ2 + tid] = (hit ? row : tu.first) - row0;
-        s_pw[u * TQ2 + tid] = w;
+        s_prow[u * QB + qi] = (hit ? row : tu.first) - row0;
+        s_pw[u * QB + qi] = w;
         if (HC && hit) {
             h ^= point_key(c, K, tu.lev, cl);
             ++cnt;
@@ -681,15 +690,14 @@ __device__ __forceinline__ void tma_probe_batch(const EvalParams &p, int c, cons
 // loads are in flight while the other's FMAs issue; the (row, weight) pairs
 // are read two steps ahead. Row loads are unconditional (a miss reads a real,
 // finite row with the weight zero); FULL: the chunk lies inside the padded row.
-template <int PREC, int MC, bool FULL>
+template <int PREC, int MC, bool FULL, int QB, int U>
 __device__ __forceinline__ void tma_accumulate(const int32_t *s_prow, const typename Types<PREC>::W *s_pw,
-                                               int nb, int tid, const typename Types<PREC>::W *sbuf, int m0,
+                                               int nb, int qi, const typename Types<PREC>::W *sbuf, int m0,
                                                int mp, typename Types<PREC>::W (&acc)[MC]) {
     using T = Types<PREC>;
     using W = typename T::W;
     using V = typename T::V;
     constexpr int G = MC / T::VW;                                   // vectors per chunk
-    constexpr int U = (PREC == DDSG_F32C && MC > 28) ? 1 : 2;       // tuples per step
     constexpr int SV = U == 2 ? G : (G + 1) / 2;                    // vectors per slot
     V v[2][SV];
 #pragma unroll
@@ -727,8 +735,8 @@ __device__ __forceinline__ void tma_accumulate(const int32_t *s_prow, const type
     // (row, weight) of tuple t; past the batch: the last tuple's row, weight zero
     auto rd = [&](int t, int32_t &rr, W &ww) {
         const int tc = t < nb ? t : nb - 1;
-        rr = s_prow[tc * TQ2 + tid];
-        const W x = s_pw[tc * TQ2 + tid];
+        rr = s_prow[tc * QB + qi];
+        const W x = s_pw[tc * QB + qi];
         ww = t < nb ? x : (W)0;
     };
 
@@ -758,21 +766,25 @@ __device__ __forceinline__ void tma_accumulate(const int32_t *s_prow, const type
     }
 }
 
-template <int PREC, int MC, bool HC, int K>
-__device__ __forceinline__ void tma_tuples(const EvalParams &p, int c, const DevTup *stup, int nt, int pb,
-                                           typename Types<PREC>::W wb, int m0, int tid,
-                                           const uint16_t (*s_cell)[LT][TQ2],
-                                           const typename Types<PREC>::W (*s_t)[LT][TQ2],
-                                           const typename Types<PREC>::W *sbuf, int32_t row0,
-                                           int32_t *s_prow, typename Types<PREC>::W *s_pw,
-                                           typename Types<PREC>::W (&acc)[MC], uint64_t &h, int32_t &cnt) {
-    const int mp = Types<PREC>::stride(p.t);
-    for (int t0 = 0; t0 < nt; t0 += pb) {
-        const int nb = nt - t0 < pb ? nt - t0 : pb;
-        tma_probe_batch<PREC, K, HC>(p, c, stup + t0, nb, wb, tid, s_cell, s_t, row0, s_prow, s_pw, h, cnt);
-        if (m0 + MC <= mp) tma_accumulate<PREC, MC, true>(s_prow, s_pw, nb, tid, sbuf, m0, mp, acc);
-        else tma_accumulate<PREC, MC, false>(s_prow, s_pw, nb, tid, sbuf, m0, mp, acc);
+// Barrier over the GR warps that share a query warp (named barrier 1 + qw);
+// with the OR of `pred` over them. A single group needs none.
+template <int GR>
+__device__ __forceinline__ bool group_sync_or(int qw, bool pred) {
+    if constexpr (GR == 1) {
+        return pred;
+    } else {
+        uint32_t r;
+        asm volatile(
+            "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+            : "=r"(r)
+            : "r"((uint32_t)pred), "r"(1 + qw), "r"(32 * GR)
+            : "memory");
+        return r != 0;
     }
+}
+template <int GR>
+__device__ __forceinline__ void group_sync(int qw) {
+    if constexpr (GR > 1) asm volatile("barrier.sync %0, %1;" ::"r"(1 + qw), "r"(32 * GR) : "memory");
 }
 
 // Per evaluated component j, one TMA stage delivers into buffer j % nbuf:
@@ -784,30 +796,46 @@ __device__ __forceinline__ void tma_tuples(const EvalParams &p, int c, const Dev
 // buffer that component i+2-nbuf used: with nbuf = 3 warps may drift one
 // component apart without a block barrier. Coordinates of component i+1 are
 // loaded during component i from a per-component dims record, so no load
-// stalls the start of a component. Every wait is bounded; a warp that gives up
-// counts the timeout, marks its queries NaN and leaves the loop, and before
-// the block exits thread 0 waits (bounded) for the copies it issued.
-template <int PREC, int MC, bool HC>
-__global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, int buf_bytes, int nbuf, int pb) {
+// stalls the start of a component.
+// GR warp groups: group g handles outputs [m0 + g*MC, m0 + (g+1)*MC) of the
+// same QB queries. With GR = 2 the two warps of a query warp split the work:
+// group 0 stages dimension 0 and probes the even tuples, group 1 stages
+// dimension 1 and probes the odd ones, both accumulate all tuples into their
+// own outputs; a named barrier per warp pair orders staging, probing and
+// accumulation. Every wait is bounded; a warp pair that gives up counts the
+// timeout, marks its queries NaN and leaves the loop together (the OR over
+// the pair is taken at its barrier), and before the block exits thread 0 waits
+// (bounded) for the copies it issued.
+template <int PREC, int MC, bool HC, int GR>
+__global__ void __launch_bounds__(TmaShape<GR>::NT, 1) eval_tma_kernel(const EvalParams p, int buf_bytes, int nbuf,
+                                                                        int pb) {
     using T = Types<PREC>;
     using W = typename T::W;
+    constexpr int QB = TmaShape<GR>::QB;
+    constexpr int QW = TmaShape<GR>::QW;
+    constexpr int kWarps = TmaShape<GR>::NT / 32;
+    // two rows in flight unless the output chunk alone fills the registers
+    constexpr int U = (PREC == DDSG_F32C && MC * GR > 28) ? 1 : 2;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + TMA_NBUF_MAX;
-    auto s_cell = reinterpret_cast<uint16_t (*)[LT][TQ2]>(smem + 128);
-    auto s_t = reinterpret_cast<W (*)[LT][TQ2]>(smem + 128 + sizeof(uint16_t) * 2 * LT * TQ2);
-    unsigned char *bufbase = smem + tma_fixed_smem<PREC>();
+    auto s_cell = reinterpret_cast<uint16_t (*)[LT][QB]>(smem + 128);
+    auto s_t = reinterpret_cast<W (*)[LT][QB]>(smem + 128 + sizeof(uint16_t) * 2 * LT * QB);
+    unsigned char *bufbase = smem + tma_fixed_smem(PREC, QB);
     int32_t *s_prow = reinterpret_cast<int32_t *>(bufbase + (size_t)nbuf * buf_bytes);
-    W *s_pw = reinterpret_cast<W *>(s_prow + (size_t)pb * TQ2);
+    W *s_pw = reinterpret_cast<W *>(s_prow + (size_t)pb * QB);
     constexpr int kTupOff = 128;
     constexpr int kRowOff = 128 + TMA_TUP_MAX * (int)sizeof(DevTup);
-    constexpr int kWarps = TQ2 / 32;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int64_t q = (int64_t)blockIdx.x * TQ2 + tid;
+    const int warp = tid >> 5;
+    const int grp = warp / QW;                 // output group of this thread
+    const int qw = warp - grp * QW;            // query warp within the group
+    const int qi = qw * 32 + lane;             // query within the block
+    const int64_t q = (int64_t)blockIdx.x * QB + qi;
     const int64_t qc = q < p.n ? q : p.n - 1;   // clamped index for coordinate loads
-    const int m0 = blockIdx.y * MC;
+    const int m0 = (blockIdx.y * GR + grp) * MC;
     const int m = p.m;
     const bool valid = q < p.n;
     const bool bad = !valid || p.flags[q] != 0;
@@ -853,6 +881,7 @@ __global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, in
     uint64_t h = 0;
     int32_t cnt = 0;
     bool failed = false;
+    int pfail = 0;                 // thread 0's refill wait gave up (warp-uniform)
     int staged0 = -1;              // dimension currently held in staging slot 0
     const int lmax_all = p.t.max_level < LT ? p.t.max_level : LT;
     uint64_t Xc0 = 0, Xc1 = 0;     // coordinates of the current component's dims
@@ -872,40 +901,52 @@ __global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, in
             Xn1 = p.X[(int64_t)(pd_next >> 16) * p.n + qc];
         }
         if (i + 2 < nproc) pd_next = pdims[i + 2];
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[b], ph))) {
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[b], ph));
+        if (group_sync_or<GR>(qw, !ok || pfail)) {
             failed = true;
             if (lane == 0 && p.err) atomicAdd(p.err, 1ull);
             break;
         }
         const unsigned char *buf = bufbase + (size_t)b * buf_bytes;
         const DevComp &cd = *reinterpret_cast<const DevComp *>(buf);
+        const int k = cd.k;
         if (!bad) {
-            const int k = cd.k;
-            if (k >= 1 && cd.dims[0] != staged0) {
-                tma_stage<PREC>(Xc0, k == 1 ? cd.lmax[0] : lmax_all, tid, s_cell, s_t, 0);
+            if (grp == 0 && k >= 1 && cd.dims[0] != staged0) {
+                tma_stage<PREC, QB>(Xc0, k == 1 ? cd.lmax[0] : lmax_all, qi, s_cell, s_t, 0);
                 staged0 = k == 1 ? -1 : cd.dims[0];
             }
-            if (k == 2) tma_stage<PREC>(Xc1, cd.lmax[1], tid, s_cell, s_t, 1);
-            const int c = HC ? p.t.proc[p.form][i] : 0;
-            const int tb = paper ? cd.tup_begin : cd.tup_int;
-            const int nt = cd.tup_end - tb;
-            const int32_t row0 = paper ? cd.row_begin : cd.row_int;
-            const W wb = paper ? (W)cd.b : (W)1;
-            const DevTup *stup = reinterpret_cast<const DevTup *>(buf + kTupOff);
-            const W *srow = reinterpret_cast<const W *>(buf + kRowOff);
-            if (k == 2) tma_tuples<PREC, MC, HC, 2>(p, c, stup, nt, pb, wb, m0, tid, s_cell, s_t, srow, row0, s_prow, s_pw, r.partial(), h, cnt);
-            else if (k == 1) tma_tuples<PREC, MC, HC, 1>(p, c, stup, nt, pb, wb, m0, tid, s_cell, s_t, srow, row0, s_prow, s_pw, r.partial(), h, cnt);
-            else tma_tuples<PREC, MC, HC, 0>(p, c, stup, nt, pb, wb, m0, tid, s_cell, s_t, srow, row0, s_prow, s_pw, r.partial(), h, cnt);
-            r.fold();
+            if (grp == GR - 1 && k == 2) tma_stage<PREC, QB>(Xc1, cd.lmax[1], qi, s_cell, s_t, 1);
         }
+        const int c = HC ? p.t.proc[p.form][i] : 0;
+        const int tb = paper ? cd.tup_begin : cd.tup_int;
+        const int nt = cd.tup_end - tb;
+        const int32_t row0 = paper ? cd.row_begin : cd.row_int;
+        const W wb = paper ? (W)cd.b : (W)1;
+        const DevTup *stup = reinterpret_cast<const DevTup *>(buf + kTupOff);
+        const W *srow = reinterpret_cast<const W *>(buf + kRowOff);
+        for (int t0 = 0; t0 < nt; t0 += pb) {
+            const int nb = nt - t0 < pb ? nt - t0 : pb;
+            group_sync<GR>(qw);   // staged basis visible; the partner is done with s_prow
+            if (!bad) {
+                if (k == 2) tma_probe_batch<PREC, 2, HC, QB>(p, c, stup + t0, nb, grp, GR, wb, qi, s_cell, s_t, row0, s_prow, s_pw, h, cnt);
+                else if (k == 1) tma_probe_batch<PREC, 1, HC, QB>(p, c, stup + t0, nb, grp, GR, wb, qi, s_cell, s_t, row0, s_prow, s_pw, h, cnt);
+                else tma_probe_batch<PREC, 0, HC, QB>(p, c, stup + t0, nb, grp, GR, wb, qi, s_cell, s_t, row0, s_prow, s_pw, h, cnt);
+            }
+            group_sync<GR>(qw);   // the partner's probes visible
+            if (!bad) {
+                if (m0 + MC <= mp) tma_accumulate<PREC, MC, true, QB, U>(s_prow, s_pw, nb, qi, srow, m0, mp, r.partial());
+                else tma_accumulate<PREC, MC, false, QB, U>(s_prow, s_pw, nb, qi, srow, m0, mp, r.partial());
+            }
+        }
+        if (!bad) r.fold();
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[b]);
         // producer: once every warp is done with component i+2-nbuf, stage i+2 in its buffer
-        int pfail = 0;
+        int pf = 0;
         if (tid == 0 && i + 2 < nproc) {
             const int j = i + 2;
             if (j >= nbuf && !mbar_wait_bounded(&empty[j % nbuf], (uint32_t)(((j - nbuf) / nbuf) & 1))) {
-                pfail = 1;
+                pf = 1;
             } else {
                 fence_proxy_async_smem();
                 issue(j, rec_next);
@@ -913,11 +954,7 @@ __global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, in
                 if (j + 1 < nproc) rec_next = recs[j + 1];
             }
         }
-        if (__shfl_sync(0xffffffffu, pfail, 0)) {
-            failed = true;
-            if (lane == 0 && p.err) atomicAdd(p.err, 1ull);
-            break;
-        }
+        pfail = __shfl_sync(0xffffffffu, pf, 0);
         Xc0 = Xn0;
         Xc1 = Xn1;
         if (++b == nbuf) {
@@ -931,39 +968,65 @@ __global__ void __launch_bounds__(TQ2, 1) eval_tma_kernel(const EvalParams p, in
         for (int j = nissued > nbuf ? nissued - nbuf : 0; j < nissued; ++j)
             mbar_wait_bounded(&full[j % nbuf], (uint32_t)((j / nbuf) & 1));
     }
+    if (HC && GR > 1) {
+        // the point hash and count of a query are split over its groups: combine
+        uint64_t *xh = reinterpret_cast<uint64_t *>(s_prow);
+        int32_t *xc = reinterpret_cast<int32_t *>(xh + QB);
+        if (grp == 1) {
+            xh[qi] = h;
+            xc[qi] = cnt;
+        }
+        __syncthreads();
+        if (grp == 0) {
+            h ^= xh[qi];
+            cnt += xc[qi];
+        }
+    }
     if (!valid) return;
     const double nanv = __longlong_as_double(0x7ff8000000000000ll);
 #pragma unroll
     for (int o = 0; o < MC; ++o)
         if (m0 + o < m) p.y[q * m + m0 + o] = (bad || failed) ? nanv : r.value(o);
-    if (HC && blockIdx.y == 0) {
+    if (HC && blockIdx.y == 0 && grp == 0) {
         if (p.hash) p.hash[q] = (bad || failed) ? 0 : h;
         if (p.count) p.count[q] = (bad || failed) ? 0 : cnt;
     }
 }
 
+template <int PREC, int MC, int GR>
+static cudaError_t launch_tma(const EvalParams &p, bool hc, cudaStream_t st) {
+    constexpr int QB = TmaShape<GR>::QB, NT = TmaShape<GR>::NT;
+    const int64_t stage = p.t.stage_bytes[p.form][PREC];
+    const int buf = tma_buf_bytes(stage);
+    int nbuf = 0, pb = 0;
+    const int fixed = tma_fixed_smem(PREC, QB);
+    tma_layout(p.t, fixed, buf, tma_probe_bytes(PREC, QB), nbuf, pb);
+    const int smem = fixed + nbuf * buf + pb * tma_probe_bytes(PREC, QB);
+    dim3 grid((unsigned)((p.n + QB - 1) / QB), (unsigned)((p.m + GR * MC - 1) / (GR * MC)));
+    if (hc) {
+        cudaError_t e = cudaFuncSetAttribute(eval_tma_kernel<PREC, MC, true, GR>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        eval_tma_kernel<PREC, MC, true, GR><<<grid, NT, smem, st>>>(p, buf, nbuf, pb);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(eval_tma_kernel<PREC, MC, false, GR>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        eval_tma_kernel<PREC, MC, false, GR><<<grid, NT, smem, st>>>(p, buf, nbuf, pb);
+    }
+    return cudaGetLastError();
+}
+
+// output chunks the two-group kernel is compiled for (per group)
+template <int PREC, int MC>
+constexpr bool kGr2Chunk = PREC == DDSG_F64 ? (MC == 4 || MC == 8 || MC == 16) : (MC == 8 || MC == 16 || MC == 28);
+
 template <int PREC, int MC>
 static cudaError_t launch_mc(const EvalParams &p, int kernel, bool hc, cudaStream_t st) {
-    if (kernel == 2) {
-        const int prec = PREC;
-        const int64_t stage = p.t.stage_bytes[p.form][prec];
-        const int buf = tma_buf_bytes(stage);
-        int nbuf = 0, pb = 0;
-        tma_layout(p.t, PREC, tma_fixed_smem<PREC>(), buf, nbuf, pb);
-        const int smem = tma_fixed_smem<PREC>() + nbuf * buf + pb * tma_probe_bytes(PREC);
-        dim3 grid2((unsigned)((p.n + TQ2 - 1) / TQ2), (unsigned)((p.m + MC - 1) / MC));
-        if (hc) {
-            cudaError_t e = cudaFuncSetAttribute(eval_tma_kernel<PREC, MC, true>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            eval_tma_kernel<PREC, MC, true><<<grid2, TQ2, smem, st>>>(p, buf, nbuf, pb);
-        } else {
-            cudaError_t e = cudaFuncSetAttribute(eval_tma_kernel<PREC, MC, false>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            eval_tma_kernel<PREC, MC, false><<<grid2, TQ2, smem, st>>>(p, buf, nbuf, pb);
-        }
-        return cudaGetLastError();
+    if (kernel == 2) return launch_tma<PREC, MC, 1>(p, hc, st);
+    if (kernel == 3) {
+        if constexpr (kGr2Chunk<PREC, MC>) return launch_tma<PREC, MC, 2>(p, hc, st);
+        else return cudaErrorInvalidValue;
     }
     dim3 grid((unsigned)((p.n + TQ - 1) / TQ), (unsigned)((p.m + MC - 1) / MC));
     if (kernel == 0) {
@@ -980,10 +1043,14 @@ static cudaError_t launch_mc(const EvalParams &p, int kernel, bool hc, cudaStrea
 static const int MC_F64[] = {2, 4, 6, 8, 12, 16};
 static const int MC_F32[] = {4, 8, 12, 16, 28, 52};
 
+// the two-group TMA kernel (3): chunks per group
+static const int MC_F64_GR2[] = {4, 8, 16};
+static const int MC_F32_GR2[] = {8, 16, 28};
+
 int eval_mc_candidates(int precision, int kernel, int *out, int cap) {
-    (void)kernel;
-    const int *src = precision == DDSG_F64 ? MC_F64 : MC_F32;
-    const int n = 6;
+    const int *src = kernel == 3 ? (precision == DDSG_F64 ? MC_F64_GR2 : MC_F32_GR2)
+                                 : (precision == DDSG_F64 ? MC_F64 : MC_F32);
+    const int n = kernel == 3 ? 3 : 6;
     for (int i = 0; i < n && i < cap; ++i) out[i] = src[i];
     return n < cap ? n : cap;
 }

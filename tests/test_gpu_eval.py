@@ -218,9 +218,10 @@ def test_every_kernel_config_matches_oracle(G):
     ref, h = build_pair(G, d, m, O.full_order_components(d, 2), fn, eps=1e-3, level=9)
     X = synth.uniform_queries(56, 700, d)
     mcs = {0: [2, 4, 6, 8, 12, 16], 1: [4, 8, 12, 16, 28, 52]}
+    mcs3 = {0: [4, 8, 16], 1: [8, 16, 28]}   # the two-group TMA kernel: chunk per group
     for prec in (0, 1):
-        for kernel in (0, 1, 2):
-            for mc in mcs[prec]:
+        for kernel in (0, 1, 2, 3):
+            for mc in (mcs3 if kernel == 3 else mcs)[prec]:
                 h.set_eval_config(prec, 1, kernel, mc)
                 h.set_eval_config(prec, 0, kernel, mc)
                 check_eval(h, ref, X, precs=(prec,))
@@ -228,7 +229,7 @@ def test_every_kernel_config_matches_oracle(G):
     yd = torch.empty((X.shape[0], m), dtype=torch.float64, device="cuda")
     for prec in (0, 1):
         kernel, mc, ms = h.autotune(xd, yd, prec, 1)
-        assert kernel in (0, 1, 2) and mc in mcs[prec] and ms > 0
+        assert kernel in (0, 1, 2, 3) and mc in (mcs3 if kernel == 3 else mcs)[prec] and ms > 0
         check_eval(h, ref, X, forms=(1,), precs=(prec,))
     with pytest.raises(G.DDSGError, match="not compiled"):
         h.set_eval_config(0, 0, 0, 5)
@@ -236,7 +237,7 @@ def test_every_kernel_config_matches_oracle(G):
 
 
 def test_staged_kernel_refuses_tables_it_cannot_hold(G):
-    """The TMA-staged kernel needs k <= 2 components; a 3D component makes it ineligible."""
+    """The TMA-staged kernels need k <= 2 components; a 3D component makes them ineligible."""
     d, m = 3, 2
     f = lambda X: np.stack([np.exp(-np.sum(X ** 2, 1)), np.prod(np.sin(3 * X + 1), 1)], 1)
     def fn(dims, X):
@@ -246,4 +247,6 @@ def test_staged_kernel_refuses_tables_it_cannot_hold(G):
     ref, h = build_pair(G, d, m, O.full_order_components(d, 3), fn, regular_level=4)
     with pytest.raises(G.DDSGError, match="cannot run"):
         h.set_eval_config(0, 0, 2, 2)
+    with pytest.raises(G.DDSGError, match="cannot run"):
+        h.set_eval_config(0, 0, 3, 4)
     check_eval(h, ref, synth.uniform_queries(33, 500, d))
