@@ -149,6 +149,16 @@ int hdmr_hierarchize(hdmr_t *h, const double *values_dev, ddsg_stream_t stream);
 int hdmr_refine(hdmr_t *h, double eps_gamma, int max_level, int strict, int64_t *n_new,
                 ddsg_stream_t stream);
 
+/*
+ * hdmr_quadrature -- the integral over [0,1]^k of every component interpolant
+ * (eq. 3.7; canonical coordinates): q_dev[c*m + o] = sum over the points of
+ * component c of alpha_p[o] * prod_j (1, 1/4 or 2^-(l-1) for level 1, 2, l >= 3).
+ * These feed the expansion criterion (eq. 3.18) and the active dimension
+ * selection (eq. 3.19). q_dev: device, ncomp*m FP64. FP64, asynchronous on
+ * `stream`; the handle must be hierarchized.
+ */
+int hdmr_quadrature(hdmr_t *h, double *q_dev, ddsg_stream_t stream);
+
 /* Copy FP64 surpluses of all points to the host (npts_total*m). Synchronous. */
 int hdmr_get_surpluses(const hdmr_t *h, double *alpha_host, ddsg_stream_t stream);
 

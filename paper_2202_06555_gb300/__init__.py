@@ -56,6 +56,7 @@ SIGNATURES = {
     "hdmr_autotune": (_int, [_p, _i64, _p, _p, _int, _int, _p, C.POINTER(_d)]),
     "hdmr_eval_noalloc": (_int, [_p, _i64, _p, _p, _int, _int, _p]),
     "hdmr_eval_graph": (_int, [_p, _i64, _p, _p, _int, _int, _p]),
+    "hdmr_quadrature": (_int, [_p, _p, _p]),
     "hdmr_eval_noalloc_capacity": (_i64, [_int]),
     "irbc_create": (_int, [_p, _p, _p, C.POINTER(_p)]),
     "irbc_destroy": (_int, [_p]),
@@ -258,6 +259,15 @@ class HDMR:
         n = x_dev.shape[0]
         _check(load().hdmr_eval_graph(self._h, n, _dev_ptr(x_dev), _dev_ptr(y_dev), int(precision),
                                       int(form), _stream_ptr(stream)), "hdmr_eval_graph")
+
+    def quadrature(self, stream=None):
+        """Integral of every component interpolant over its unit cube (eq. 3.7):
+        a (ncomp, m) FP64 device tensor."""
+        import torch
+        ncomp, _ = self.sizes()
+        q = torch.empty((ncomp, self.m), dtype=torch.float64, device="cuda")
+        _check(load().hdmr_quadrature(self._h, _dev_ptr(q), _stream_ptr(stream)), "hdmr_quadrature")
+        return q
 
     def noalloc_capacity(self) -> int:
         return int(load().hdmr_eval_noalloc_capacity(self.d))

@@ -664,6 +664,15 @@ extern "C" int hdmr_hierarchize(hdmr_t *h, const double *values_dev, ddsg_stream
     return DDSG_OK;
 }
 
+extern "C" int hdmr_quadrature(hdmr_t *h, double *q_dev, ddsg_stream_t stream) {
+    if (!h || !q_dev) return fail(DDSG_ERR_ARG, "hdmr_quadrature: NULL argument");
+    if (!h->uploaded || !h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_quadrature: call hdmr_hierarchize first");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(DDSG_ERR_CUDA, "hdmr_quadrature: cannot select device");
+    CUDA_TRY(launch_quadrature(h->dt, h->m, q_dev, reinterpret_cast<cudaStream_t>(stream)));
+    return DDSG_OK;
+}
+
 extern "C" int hdmr_get_surpluses(const hdmr_t *h, double *alpha_host, ddsg_stream_t stream) {
     if (!h || !alpha_host) return fail(DDSG_ERR_ARG, "hdmr_get_surpluses: NULL argument");
     if (!h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_get_surpluses: not hierarchized");

@@ -215,6 +215,7 @@ int eval_mc_candidates(int precision, int kernel, int *out, int cap);
 
 cudaError_t launch_eval(const EvalArgs &a, cudaStream_t st);
 
+cudaError_t launch_quadrature(const DevTables &t, int m, double *Q, cudaStream_t st);
 cudaError_t launch_hierarchize(const DevTables &t, int m, const double *values,
                                cudaStream_t st);
 

@@ -1168,6 +1168,33 @@ cudaError_t launch_hierarchize(const DevTables &t, int m, const double *values, 
     return cudaGetLastError();
 }
 
+// Quadrature of every component interpolant (eq. 3.7): Q[c][o] = sum over the
+// component's points (table order) of alpha_p[o] * prod_j int phi_{l_pj}, with
+// int phi = 1 (level 1), 1/4 (level 2), 2^-(l-1) (level l >= 3). One thread per
+// (component, output), FP64.
+__global__ void quadrature_kernel(const DevTables t, int m, double *__restrict__ Q) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)t.C * m) return;
+    const int c = (int)(e / m), o = (int)(e - (int64_t)c * m);
+    const DevComp &cd = t.comps[c];
+    double acc = 0.0;
+    for (int64_t pnt = cd.pt_begin; pnt < cd.pt_end; ++pnt) {
+        double w = 1.0;
+        for (int j = 0; j < cd.k; ++j) {
+            const int l = t.pt_lv[(int64_t)j * t.P + pnt];
+            w *= l == 1 ? 1.0 : (l == 2 ? 0.25 : ldexp(1.0, -(l - 1)));
+        }
+        acc += w * t.alpha64[(int64_t)t.pt_dpos[pnt] * t.mp64 + o];
+    }
+    Q[e] = acc;
+}
+
+cudaError_t launch_quadrature(const DevTables &t, int m, double *Q, cudaStream_t st) {
+    const int64_t n = (int64_t)t.C * m;
+    quadrature_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(t, m, Q);
+    return cudaGetLastError();
+}
+
 __global__ void to_f32_kernel(const double *__restrict__ a, int mp64, float *__restrict__ b, int mp32,
                               int64_t P, int m) {
     const int64_t total = P * (int64_t)mp32;

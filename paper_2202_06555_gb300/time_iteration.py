@@ -1,0 +1,227 @@
+"""Adaptive DDSG time iteration on the GPU (Alg. 1 around Alg. 2 of the paper)
+for the smooth IRBC model of Sec. 2.1.
+
+One time-iteration step builds the next policy p' as an adaptive DDSG
+expansion (Alg. 2) of the map x -> solve{FOC(. | x, p)}: every new grid point
+of every component is a cut state (anchor elsewhere) at which the Euler
+equations are solved by the GPU Newton (`irbc_newton`, policy p for the next
+period); surpluses, refinement (eq. 3.8) and component quadratures (eq. 3.7)
+are GPU calls; the expansion criterion (eq. 3.18) and the active dimension
+selection (eq. 3.19) act on the (components x outputs) quadrature table.
+The iteration stops when the Euler-equation errors of p' at test states fall
+below a threshold (Alg. 1) or after a fixed number of steps.
+
+This module only orchestrates calls into libddsg; all grid, surplus,
+interpolation and Newton work runs in its kernels.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+from . import F64, FORM_SLICEFREE, HDMR, NODES_DELTA
+
+
+def cut_quadratures(Q: np.ndarray, comps) -> np.ndarray:
+    """Integrals of the cut-HDMR component functions f_u (eq. ddsg2.2.6 on the
+    interpolants): Qf_u = sum over v subset of u of (-1)^{|u|-|v|} Q(I f(xbar \\ x_v))."""
+    pos = {u: c for c, u in enumerate(comps)}
+    Qf = np.zeros_like(Q)
+    for c, u in enumerate(comps):
+        for r in range(len(u) + 1):
+            sign = -1.0 if (len(u) - r) % 2 else 1.0
+            for v in itertools.combinations(u, r):
+                Qf[c] += sign * Q[pos[v]]
+    return Qf
+
+
+class StateSolver:
+    """x -> solve{FOC(. | x, p)} at a batch of states (FP64 Newton on the GPU,
+    started from the policy p itself)."""
+
+    def __init__(self, model, policy: HDMR, precision=F64, form=FORM_SLICEFREE, tol=1e-10, max_it=30,
+                 node_mode=NODES_DELTA):
+        self.model, self.policy = model, policy
+        self.precision, self.form, self.tol, self.max_it = precision, form, tol, max_it
+        self.node_mode = node_mode
+        self.calls = 0
+        self.points = 0
+        self.failed = 0
+        self.iterations = 0
+
+    def __call__(self, X: np.ndarray) -> np.ndarray:
+        import torch
+        n = X.shape[0]
+        m = self.policy.m
+        xd = torch.from_numpy(np.ascontiguousarray(X, np.float64)).cuda()
+        z = torch.empty((n, m), dtype=torch.float64, device="cuda")
+        self.policy.eval(xd, z, self.precision, self.form)
+        it = torch.zeros(n, dtype=torch.int32, device="cuda")
+        st = torch.zeros(n, dtype=torch.int32, device="cuda")
+        self.model.set_node_mode(self.node_mode)
+        self.model.newton(self.policy, xd, z, self.max_it, self.tol, it, st, None, self.precision, self.form)
+        torch.cuda.synchronize()
+        self.calls += 1
+        self.points += n
+        self.failed += int((st != 0).sum().item())
+        self.iterations += int(it.sum().item())
+        return z.cpu().numpy()
+
+
+def _adaptive(h: HDMR, known, solve, anchor, eps_gamma, level, strict=False, max_sweeps=64):
+    """Refine / hierarchize sweeps (eq. 3.8) until no point is added; the values
+    of all new points of all components are solved in one batch per sweep.
+    known: values of the leading components (in order), or None."""
+    import torch
+    ncomp, _ = h.sizes()
+    vals = list(known) + [None] * (ncomp - len(known))
+    for _ in range(max_sweeps):
+        need = []
+        for c in range(ncomp):
+            dims, npts, _ = h.component_info(c)
+            have = 0 if vals[c] is None else vals[c].shape[0]
+            if have < npts:
+                _, _, xs = h.component_points(c, have, npts - have)
+                X = np.tile(anchor, (npts - have, 1))
+                if len(dims):
+                    X[:, list(dims)] = xs
+                need.append((c, X))
+        if need:
+            sol = solve(np.concatenate([X for _, X in need]))
+            o = 0
+            for c, X in need:
+                part = sol[o:o + X.shape[0]]
+                o += X.shape[0]
+                vals[c] = part if vals[c] is None else np.concatenate([vals[c], part])
+        h.hierarchize(torch.from_numpy(np.ascontiguousarray(np.concatenate(vals))).cuda())
+        if h.refine(eps_gamma, level, strict) == 0:
+            break
+    return vals
+
+
+def build_ddsg(solve, d: int, m: int, order: int, level: int, eps_gamma: float, eps_eta: float,
+               eps_rho: float, lo, hi, candidates=None, strict=False):
+    """Alg. 2: the adaptive DDSG expansion of the map `solve` (states -> values).
+
+    Order by order k = 1..order: the candidate components of order k that hold
+    no rejected component are refined adaptively together with the accepted
+    lower-order ones; for k >= 2 a candidate is kept iff eta_u > eps_eta
+    (eq. 3.19), otherwise rejected with all its supersets; after the order,
+    rho (eq. 3.18) < eps_rho stops the expansion. candidates(k) optionally
+    restricts the order-k index sets (default: all k-subsets of the d dims).
+    Returns the handle holding the accepted components and an info dict."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    anchor = 0.5 * (lo + hi)
+    accepted = [()]
+    grids = {}            # u -> (levels, indices, values)
+    rejected = []
+    info = {"rho": [], "eta": {}, "rejected": [], "points": 0}
+    for k in range(1, order + 1):
+        pool = candidates(k) if candidates else itertools.combinations(range(d), k)
+        cand = [tuple(u) for u in pool if not any(set(z) <= set(u) for z in rejected)]
+        if not cand:
+            break
+        h = HDMR(d, m, order, lo=lo, hi=hi)
+        comps, known = [], []
+        for u in accepted:
+            if u in grids:
+                lv, ix, v = grids[u]
+                h.add_component(list(u), lv, ix)
+                known.append(v)
+            else:
+                h.add_regular(list(u), 2)   # the empty component, first pass only
+                known.append(None)
+            comps.append(u)
+        for u in cand:
+            h.add_regular(list(u), 2)
+            comps.append(u)
+        vals = _adaptive(h, known, solve, anchor, eps_gamma, level, strict)
+        Qf = cut_quadratures(h.quadrature().cpu().numpy(), comps)
+        lower = np.sum([Qf[c] for c, u in enumerate(comps) if len(u) <= k - 1], axis=0)
+        keep = []
+        for c, u in enumerate(comps):
+            if u not in grids:
+                lv, ix, _ = h.component_points(c)
+                grids[u] = (lv, ix, vals[c])
+            if len(u) != k:
+                continue
+            if k >= 2:
+                eta = float(np.linalg.norm(Qf[c]) / np.linalg.norm(lower))
+                info["eta"][u] = eta
+                if not eta > eps_eta:
+                    rejected.append(u)
+                    info["rejected"].append(u)
+                    continue
+            keep.append(c)
+        accepted += [comps[c] for c in keep]
+        rho = float(np.linalg.norm(np.sum([Qf[c] for c in keep], axis=0) if keep else np.zeros(m)) /
+                    np.linalg.norm(lower))
+        info["rho"].append(rho)
+        h.close()
+        if rho < eps_rho:
+            break
+    import torch
+    h = HDMR(d, m, order, lo=lo, hi=hi)
+    for u in accepted:
+        lv, ix, _ = grids[u]
+        h.add_component(list(u), lv, ix)
+    h.hierarchize(torch.from_numpy(np.ascontiguousarray(np.concatenate([grids[u][2] for u in accepted]))).cuda())
+    info["components"] = list(accepted)
+    info["points"] = int(h.sizes()[1])
+    return h, info
+
+
+def euler_errors(model, policy: HDMR, states: np.ndarray, precision=F64, form=FORM_SLICEFREE,
+                 node_mode=NODES_DELTA):
+    """Unit-free Euler-equation errors of a policy at states (the policy gives
+    both today's choice and next period's): per state max over countries of
+    |beta E / lhs - 1| and |resource| / output."""
+    import torch
+    n, N = states.shape[0], model.N
+    sd = torch.from_numpy(np.ascontiguousarray(states, np.float64)).cuda()
+    g = torch.empty((n, N + 1), dtype=torch.float64, device="cuda")
+    policy.eval(sd, g, precision, form)
+    r = torch.empty((n, N + 1), dtype=torch.float64, device="cuda")
+    e = torch.empty((n, 2), dtype=torch.float64, device="cuda")
+    model.set_node_mode(node_mode)
+    model.residual(policy, sd, g, r, None, e, precision, form)
+    torch.cuda.synchronize()
+    return e.cpu().numpy()
+
+
+def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps_gamma: float,
+                   eps_eta: float, eps_rho: float, lo, hi, test_states: np.ndarray, tol_euler=0.0,
+                   candidates=None, precision=F64, form=FORM_SLICEFREE, newton_tol=1e-10, max_it=30,
+                   node_mode=NODES_DELTA):
+    """Alg. 1: p <- build_ddsg(x -> solve{FOC(. | x, p)}) until the mean Euler
+    error at test_states is below tol_euler or `steps` steps are done.
+    Returns the last policy and one record per step."""
+    import torch
+    d, m = policy0.d, policy0.m
+    policy = policy0
+    history = []
+    sd = torch.from_numpy(np.ascontiguousarray(test_states, np.float64)).cuda()
+    for step in range(steps):
+        solve = StateSolver(model, policy, precision, form, newton_tol, max_it, node_mode)
+        new, info = build_ddsg(solve, d, m, order, level, eps_gamma, eps_eta, eps_rho, lo, hi, candidates)
+        e = euler_errors(model, new, test_states, precision, form, node_mode)
+        y0 = torch.empty((sd.shape[0], m), dtype=torch.float64, device="cuda")
+        y1 = torch.empty_like(y0)
+        policy.eval(sd, y0, precision, form)
+        new.eval(sd, y1, precision, form)
+        torch.cuda.synchronize()
+        history.append({"step": step, "points": info["points"], "components": len(info["components"]),
+                        "rho": info["rho"], "rejected": len(info["rejected"]),
+                        "newton_points": solve.points, "newton_failed": solve.failed,
+                        "newton_iters_mean": solve.iterations / max(1, solve.points),
+                        "euler_error_mean": float(np.mean(np.max(e, 1))),
+                        "euler_error_max": float(np.max(e)),
+                        "policy_change_max": float((y1 - y0).abs().max().item())})
+        if policy is not policy0:
+            policy.close()
+        policy = new
+        if history[-1]["euler_error_mean"] < tol_euler:
+            break
+    return policy, history

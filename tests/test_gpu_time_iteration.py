@@ -1,0 +1,104 @@
+"""GPU adaptive DDSG time iteration (paper_2202_06555_gb300.time_iteration)
+against the oracle's (oracle/time_iteration.py): GPU component quadratures
+drive eq. 3.18 / 3.19 to the closed-form values; one and two time-iteration
+steps give the oracle's component sets and policies (|dy| <= 1e-8 at fresh
+states); the iteration lowers the Euler errors."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from oracle.time_iteration import oracle_build_ddsg, oracle_solver, oracle_time_iteration
+from test_oracle_time_iteration import _abs_product, _initial_policy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2202_06555_gb300 as G
+    G.load()
+    return G
+
+
+def test_gpu_quadrature_matches_oracle(G):
+    d, m = 4, 3
+    c = synth.family_coeffs(synth.BASE_SEED + 61, m, d)
+    fn = lambda dims, X: synth.family_cut(c, dims, X)
+    ref = O.OracleDDSG(d, m)
+    h = G.HDMR(d, m, 2)
+    for u in O.full_order_components(d, 2):
+        ref.add_regular(u, 2)
+        h.add_regular(list(u), 2)
+    ref.build_adaptive(fn, 1e-3, 7)
+    G.build_adaptive(h, fn, 1e-3, 7)
+    q = h.quadrature().cpu().numpy()
+    Q = ref.quadrature()
+    assert np.allclose(q, Q, rtol=1e-13, atol=1e-15)
+
+
+def test_eta_rho_closed_forms_on_gpu(G):
+    from paper_2202_06555_gb300.time_iteration import build_ddsg
+    d, m = 3, 2
+    lo, hi = np.full(d, 0.8), np.full(d, 1.2)
+    h, info = build_ddsg(_abs_product, d, m, 2, 3, -1.0, -1.0, 0.0, lo, hi)
+    assert len(info["components"]) == 7
+    assert abs(info["eta"][(0, 1)] - 0.01 * np.sqrt(1.25) / np.sqrt(5.0)) < 1e-14
+    assert info["eta"][(0, 2)] < 1e-15 and info["eta"][(1, 2)] < 1e-15
+    assert info["rho"][0] < 1e-15 and abs(info["rho"][1] - info["eta"][(0, 1)]) < 1e-14
+    h2, info2 = build_ddsg(_abs_product, d, m, 2, 3, -1.0, 1e-6, 0.0, lo, hi)
+    assert info2["components"] == [(), (0,), (1,), (2,), (0, 1)]
+    X = synth.uniform_matrix(3, 50, d, 0.8, 1.2)
+    y = torch.empty((50, m), dtype=torch.float64, device="cuda")
+    h2.eval(torch.from_numpy(X).cuda(), y, G.F64, G.FORM_SLICEFREE)
+    torch.cuda.synchronize()
+    assert np.allclose(y.cpu().numpy(), _abs_product(X), atol=1e-14)
+
+
+def _gpu_initial_policy(G, I, N):
+    lam = I.steady_lambda()
+    d = 2 * N
+    h = G.HDMR(d, N + 1, 2, lo=np.full(d, 0.8), hi=np.full(d, 1.2))
+    comps = [()] + [(i,) for i in range(d)]
+    for u in comps:
+        h.add_regular(list(u), 2)
+    vals = []
+    for c, u in enumerate(comps):
+        _, _, xs = h.component_points(c)
+        y = np.tile(np.concatenate([np.ones(N), [lam]]), (xs.shape[0], 1))
+        for a, dim in enumerate(u):
+            if dim >= N:
+                y[:, dim - N] = xs[:, a]
+        vals.append(y)
+    h.hierarchize(torch.from_numpy(np.concatenate(vals)).cuda())
+    return h
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_time_iteration_matches_oracle(G, mode):
+    from paper_2202_06555_gb300.time_iteration import time_iteration
+    N = 2
+    d = 2 * N
+    I = O.IRBCOracle(N)
+    M = G.IRBC(N, I.p["beta"], I.p["alpha"], I.p["delta"], I.p["sigma"], I.p["rho"], I.p["phi"],
+               I.A, I.gamma, I.tau)
+    lo, hi = np.full(d, 0.8), np.full(d, 1.2)
+    pairs = lambda k: [(i,) for i in range(d)] if k == 1 else [(j, N + j) for j in range(N)]
+    T = synth.irbc_states(synth.BASE_SEED + 601, 64, N)
+    E0 = _initial_policy(I, N)
+    Eo, hist_o = oracle_time_iteration(I, E0, 2, 2, 3, -1.0, -1.0, 0.0, lo, hi, T, candidates=pairs)
+    h0 = _gpu_initial_policy(G, I, N)
+    hg, hist_g = time_iteration(M, h0, 2, 2, 3, -1.0, -1.0, 0.0, lo, hi, T, candidates=pairs,
+                                precision=G.F64, node_mode=mode)
+    assert [h["components"] for h in hist_g] == [len(h["info"]["components"]) for h in hist_o]
+    assert all(h["newton_failed"] == 0 for h in hist_g)
+    y = torch.empty((T.shape[0], N + 1), dtype=torch.float64, device="cuda")
+    hg.eval(torch.from_numpy(T).cuda(), y, G.F64, G.FORM_SLICEFREE)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(y.cpu().numpy() - Eo.eval(T, form=1)["y"])) <= 1e-8
+    for a, b in zip(hist_g, hist_o):
+        assert abs(a["euler_error_mean"] - b["euler_error_mean"]) <= 1e-8
+    assert hist_g[1]["euler_error_mean"] < hist_g[0]["euler_error_mean"]
