@@ -327,8 +327,10 @@ int irbc_destroy(irbc_t *model);
  *           (rows j < N: eq. model1 of country j+1; row N: eq. model2).
  *   jac_dev (nullable): ns x (N+1) x (N+1), row-major d resid / d guess, from the
  *           hat slopes (right derivative at kinks, zero where k'_i is clamped)
- *           and the chain rule. Needs every policy component that holds k_i to
- *           be {k_i} or {a_i, k_i} (DDSG_ERR_ARG otherwise).
+ *           and the chain rule. Needs every policy component that holds a k_i
+ *           to hold at most one a_j (any order-2 expansion qualifies;
+ *           DDSG_ERR_ARG otherwise); a column whose component has more active
+ *           points than the kernel's term buffer (48) is NaN.
  *   euler_err_dev (nullable): ns x 2, unit-free Euler error per state:
  *           max_j |beta E_j / (lambda (1 + phi g_j)) - 1| and |resource| / sum_j Y_j.
  *   precision/form: those of hdmr_eval for the policy interpolation; residual

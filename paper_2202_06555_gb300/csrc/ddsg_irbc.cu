@@ -14,10 +14,9 @@
 //                         Euler errors and the Jacobian's border and diagonal
 //                         pieces;
 //   irbc_jacobian_kernel  one thread per column i < N: the policy's derivative
-//                         in k'_i enters through the components holding dim N+i
-//                         (the (a_i, k_i) pair and the k_i single), whose other
-//                         coordinate a'_i takes only three values over the nodes
-//                         (no shock, +shock, -shock).
+//                         in k'_i enters through the components holding dim N+i,
+//                         whose a-coordinate (if any) takes only three values
+//                         over the nodes (no shock, +shock, -shock).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -216,33 +215,31 @@ __device__ __forceinline__ double dhat(uint64_t X, int l, uint32_t &cell) {
     return F < (1ull << (sh - 1)) ? mag : -mag;
 }
 
-// Terms of d p(x)/d x_dim for one component whose other dimension (if any)
-// sits at Xo: appends (device row, weight) pairs; weight includes b and 1/span.
+// Terms of d p(x)/d x_dpos for one component at coordinates Xd (one per
+// component dimension; position dpos is the differentiated one): appends
+// (device row, weight) pairs, the weight holding coef (b or 1) and 1/span.
+// Returns the number of terms, or -1 if there were more than cap.
 struct DTerm { int32_t row; double w; };
 
-__device__ int comp_dterms(const DevTables &t, int c, int dk, uint64_t Xk, uint64_t Xo, double scale,
-                           bool paper, DTerm *out, int cap) {
-    const DevComp &cd = t.comps[c];
-    const double b = paper ? cd.b : 1.0;
-    if (b == 0.0) return 0;
-    const int tb = paper ? cd.tup_begin : cd.tup_int;
+__device__ int comp_dterms(const DevTables &t, const DevComp &cd, int tb, int dpos, const uint64_t *Xd,
+                           double scale, DTerm *out, int cap) {
     int n = 0;
-    for (int ti = tb; ti < cd.tup_end && n < cap; ++ti) {
+    for (int ti = tb; ti < cd.tup_end; ++ti) {
         const DevTup tu = t.tups[ti];
         uint32_t off = 0;
-        double wt = b * scale;
+        double wt = scale;
         bool act = true;
         for (int j = 0; j < cd.k; ++j) {
             const int l = tu.lev[j];
-            if (j == dk) {
+            if (j == dpos) {
                 uint32_t cell;
-                const double sl = dhat(Xk, l, cell);
+                const double sl = dhat(Xd[j], l, cell);
                 if (sl == 0.0) { act = false; break; }
                 wt *= sl;
                 off = off * (j == 1 ? tu.nc1 : ncells(l)) + cell;
             } else {
                 Basis1D o;
-                if (!basis1d(Xo, l, o)) { act = false; break; }
+                if (!basis1d(Xd[j], l, o)) { act = false; break; }
                 wt *= (double)o.N * ldexp(1.0, -o.e);
                 off = off * (j == 1 ? tu.nc1 : ncells(l)) + o.cell;
             }
@@ -250,6 +247,7 @@ __device__ int comp_dterms(const DevTables &t, int c, int dk, uint64_t Xk, uint6
         if (!act) continue;
         const int32_t row = tuple_row(tu, off, t.slots);
         if (row < 0) continue;
+        if (n == cap) return -1;
         out[n].row = row;
         out[n].w = wt;
         ++n;
@@ -260,9 +258,18 @@ __device__ int comp_dterms(const DevTables &t, int c, int dk, uint64_t Xk, uint6
 constexpr int DT_CAP = 48;
 
 // One thread per column i < N of each state's Jacobian (d r_j / d k'_i, j < N).
+// k'_i enters the next-period policy through every component holding dim
+// N+i. For such a component u the coordinates of u at a node are the base
+// ones (no shock on u's country, if any) except at the nodes shocking u's
+// a-dimension (country c: nodes 2c, 2N get a'_c at +, nodes 2c+1, 2N+1 at -):
+// its slope in k'_i takes at most three values over the 2(N+1) nodes, and the
+// node sum splits into the base sum (total minus the four shocked nodes) plus
+// those four. Components holding k_i and more than one a-dimension make the
+// column NaN (the host refuses such sets).
 __global__ void __launch_bounds__(128) irbc_jacobian_kernel(IrbcDev P, int64_t s0, int64_t nsc,
                                                             DevTables t, int form,
-                                                            const int32_t *__restrict__ kcomps,
+                                                            const int32_t *__restrict__ koff,
+                                                            const int32_t *__restrict__ kids,
                                                             const double *__restrict__ lo,
                                                             const double *__restrict__ span,
                                                             const double *__restrict__ guess,
@@ -281,64 +288,86 @@ __global__ void __launch_bounds__(128) irbc_jacobian_kernel(IrbcDev P, int64_t s
     double *J = jac + s * (int64_t)m * m;
     const double w = 1.0 / (double)nq;
     const int dk = N + i;
+    for (int j = 0; j < N; ++j) J[(int64_t)j * m + i] = j == i ? ax[2 * N + j] : 0.0;
     // k'_i in canonical units; clamped (or at the top face) -> zero derivative
     const double ck = (kp[i] - lo[dk]) / span[dk];
-    const bool live = ck >= 0.0 && ck < 1.0;
-    // derivative terms at the three values of a'_i
+    if (!(ck >= 0.0 && ck < 1.0)) return;
+    bool bad = false;
+    unsigned long long cl = 0;
+    const uint64_t Xk = encode_coord(kp[i], lo[dk], span[dk], bad, cl);
+    const int mp = t.mp64;
     DTerm terms[3][DT_CAP];
-    int nt[3] = {0, 0, 0};
-    if (live) {
-        bool bad = false;
-        unsigned long long cl = 0;
-        const uint64_t Xk = encode_coord(kp[i], lo[dk], span[dk], bad, cl);
-        for (int v = 0; v < 3; ++v) {
-            const uint64_t Xa = encode_coord(ax[(3 + v) * N + i], lo[i], span[i], bad, cl);
-            for (int cc = 0; cc < 2; ++cc) {
-                const int c = kcomps[2 * i + cc];
-                if (c < 0) continue;
-                const DevComp &cd = t.comps[c];
-                const int kdim = cd.k == 2 ? 1 : 0;   // (a_i, k_i): k_i is the second dim
-                nt[v] += comp_dterms(t, c, kdim, Xk, Xa, 1.0 / span[dk], paper, terms[v] + nt[v],
-                                     DT_CAP - nt[v]);
+    for (int e = koff[i]; e < koff[i + 1]; ++e) {
+        const DevComp &cd = t.comps[kids[e]];
+        const double coef = paper ? cd.b : 1.0;
+        if (coef == 0.0) continue;
+        const int tb = paper ? cd.tup_begin : cd.tup_int;
+        uint64_t Xd[KMAX];
+        int dpos = 0, apos = -1, ctry = -1, na = 0;
+        for (int j = 0; j < cd.k; ++j) {
+            const int dim = cd.dims[j];
+            if (dim == dk) {
+                dpos = j;
+                Xd[j] = Xk;
+            } else if (dim < N) {
+                apos = j;
+                ctry = dim;
+                ++na;
+                Xd[j] = encode_coord(ax[3 * N + dim], lo[dim], span[dim], bad, cl);
+            } else {
+                Xd[j] = encode_coord(kp[dim - N], lo[dim], span[dim], bad, cl);
             }
         }
-    }
-    const int mp = t.mp64;
-    // node indices whose a'_i is shocked: +: 2i, 2N ; -: 2i+1, 2N+1
-    const int qp0 = 2 * i, qp1 = 2 * N, qm0 = 2 * i + 1, qm1 = 2 * N + 1;
-    double dPN[3];
-    for (int v = 0; v < 3; ++v) {
-        double acc = 0.0;
-        for (int e = 0; e < nt[v]; ++e) acc += terms[v][e].w * t.alpha64[(int64_t)terms[v][e].row * mp + N];
-        dPN[v] = acc;
-    }
-    for (int j = 0; j < N; ++j) {
-        double dP[3];
-        for (int v = 0; v < 3; ++v) {
+        int nt[3] = {0, 0, 0};
+        const int nv = na == 0 ? 1 : 3;
+        bool over = na > 1;
+        for (int v = 0; v < nv && !over; ++v) {
+            if (v > 0) Xd[apos] = encode_coord(ax[(3 + v) * N + ctry], lo[ctry], span[ctry], bad, cl);
+            nt[v] = comp_dterms(t, cd, tb, dpos, Xd, coef / span[dk], terms[v], DT_CAP);
+            if (nt[v] < 0) over = true;
+        }
+        if (over) {
+            for (int j = 0; j < N; ++j) J[(int64_t)j * m + i] = NAN;
+            return;
+        }
+        // node pieces of the shocked nodes of u's country: +: 2c, 2N ; -: 2c+1, 2N+1
+        double dPN[3];
+        for (int v = 0; v < nv; ++v) {
             double acc = 0.0;
-            for (int e = 0; e < nt[v]; ++e) acc += terms[v][e].w * t.alpha64[(int64_t)terms[v][e].row * mp + j];
-            dP[v] = acc;
+            for (int q = 0; q < nt[v]; ++q) acc += terms[v][q].w * t.alpha64[(int64_t)terms[v][q].row * mp + N];
+            dPN[v] = acc;
         }
-        // per-node coefficient pieces of the four shocked nodes
-        const double kpa = ax[6 * N + j];
-        double s1[4], sM[4];
-        const int qs[4] = {qp0, qp1, qm0, qm1};
-        for (int u = 0; u < 4; ++u) {
-            const int q = qs[u];
-            const double kpp = ys[(int64_t)q * m + j];
-            const double lamp = ys[(int64_t)q * m + N];
-            const double g2 = kpp / kp[j] - 1.0;
-            const double ap = ax[(3 + node_variant(q, j, N)) * N + j];
-            s1[u] = w * lamp * 0.5 * P.phi * (2.0 * g2 + 2.0) / kp[j];
-            sM[u] = w * (ap * P.A * P.alpha * kpa + (1.0 - P.delta) + 0.5 * P.phi * g2 * (g2 + 2.0));
+        for (int j = 0; j < N; ++j) {
+            double dP[3];
+            for (int v = 0; v < nv; ++v) {
+                double acc = 0.0;
+                for (int q = 0; q < nt[v]; ++q) acc += terms[v][q].w * t.alpha64[(int64_t)terms[v][q].row * mp + j];
+                dP[v] = acc;
+            }
+            const double S1 = ax[0 * N + j], SM = ax[1 * N + j];
+            double v0;
+            if (nv == 1) {
+                v0 = -P.beta * (S1 * dP[0] + SM * dPN[0]);
+            } else {
+                const double kpa = ax[6 * N + j];
+                double s1[4], sM[4];
+                const int qs[4] = {2 * ctry, 2 * N, 2 * ctry + 1, 2 * N + 1};
+                for (int u = 0; u < 4; ++u) {
+                    const int q = qs[u];
+                    const double kpp = ys[(int64_t)q * m + j];
+                    const double lamp = ys[(int64_t)q * m + N];
+                    const double g2 = kpp / kp[j] - 1.0;
+                    const double ap = ax[(3 + node_variant(q, j, N)) * N + j];
+                    s1[u] = w * lamp * 0.5 * P.phi * (2.0 * g2 + 2.0) / kp[j];
+                    sM[u] = w * (ap * P.A * P.alpha * kpa + (1.0 - P.delta) + 0.5 * P.phi * g2 * (g2 + 2.0));
+                }
+                const double s1b = S1 - s1[0] - s1[1] - s1[2] - s1[3];
+                const double sMb = SM - sM[0] - sM[1] - sM[2] - sM[3];
+                v0 = -P.beta * (s1b * dP[0] + (s1[0] + s1[1]) * dP[1] + (s1[2] + s1[3]) * dP[2] +
+                                sMb * dPN[0] + (sM[0] + sM[1]) * dPN[1] + (sM[2] + sM[3]) * dPN[2]);
+            }
+            J[(int64_t)j * m + i] += v0;
         }
-        // node qp0 == qp1 only when i == N (never); qp1/qm1 are shared by all columns
-        const double S1 = ax[0 * N + j], SM = ax[1 * N + j];
-        const double s1b = S1 - s1[0] - s1[1] - s1[2] - s1[3];
-        const double sMb = SM - sM[0] - sM[1] - sM[2] - sM[3];
-        const double v = -P.beta * (s1b * dP[0] + (s1[0] + s1[1]) * dP[1] + (s1[2] + s1[3]) * dP[2] +
-                                    sMb * dPN[0] + (sM[0] + sM[1]) * dPN[1] + (sM[2] + sM[3]) * dPN[2]);
-        J[(int64_t)j * m + i] = v + (j == i ? ax[2 * N + j] : 0.0);
     }
 }
 
@@ -679,24 +708,32 @@ IrbcDev dev_params(const irbc *M) {
 
 constexpr size_t kWsCap = (size_t)2 << 30;   // residual workspace per chunk of states
 
-// Component ids holding dim N+i: [2i] = the (i, N+i) pair (or -1), [2i+1] = the
-// single N+i (or -1). Fails if any other component contains dim N+i.
-int k_components(hdmr_t *h, int N, std::vector<int32_t> &out) {
+// CSR over the dims N+i (the k_i): the components that hold k_i. Fails if one
+// of them also holds more than one a-dimension (the Jacobian kernel handles
+// at most one shocked coordinate per component).
+int k_components(hdmr_t *h, int N, std::vector<int32_t> &off, std::vector<int32_t> &ids) {
     int32_t nc = 0;
     int64_t np = 0;
     int rc = hdmr_num_components(h, &nc, &np);
     if (rc) return rc;
-    out.assign(2 * N, -1);
+    std::vector<std::vector<int32_t>> per(N);
     for (int32_t c = 0; c < nc; ++c) {
-        int32_t k = 0, dims[DDSG_KMAX];
-        hdmr_component_info(h, c, &k, dims, nullptr, nullptr);
-        for (int j = 0; j < k; ++j) {
+        int32_t kk = 0, dims[DDSG_KMAX];
+        hdmr_component_info(h, c, &kk, dims, nullptr, nullptr);
+        int na = 0;
+        for (int j = 0; j < kk; ++j) na += dims[j] < N;
+        for (int j = 0; j < kk; ++j) {
             if (dims[j] < N) continue;
-            const int i = dims[j] - N;
-            if (k == 1) out[2 * i + 1] = c;
-            else if (k == 2 && dims[0] == i) out[2 * i] = c;
-            else return set_error(DDSG_ERR_ARG, "euler_residual: the Jacobian needs every component holding k_i to be {k_i} or {a_i, k_i}");
+            if (na > 1)
+                return set_error(DDSG_ERR_ARG, "euler_residual: the Jacobian needs every component holding a k_i to hold at most one a_j");
+            per[dims[j] - N].push_back(c);
         }
+    }
+    off.assign(N + 1, 0);
+    ids.clear();
+    for (int i = 0; i < N; ++i) {
+        ids.insert(ids.end(), per[i].begin(), per[i].end());
+        off[i + 1] = (int32_t)ids.size();
     }
     return DDSG_OK;
 }
@@ -793,10 +830,10 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
     const int N = M->p.N, d = 2 * N, m = N + 1, nq = 2 * (N + 1);
     if (v.d != d || v.m != m) return set_error(DDSG_ERR_ARG, "euler_residual: the policy must map 2N states to N+1 outputs");
     if ((rc = bind_device(M))) return rc;
-    std::vector<int32_t> kc;
-    int32_t *kc_dev = nullptr;
+    std::vector<int32_t> koff, kids;
+    int32_t *koff_dev = nullptr, *kids_dev = nullptr;
     if (jac_dev) {
-        if ((rc = k_components(policy, N, kc))) return rc;
+        if ((rc = k_components(policy, N, koff, kids))) return rc;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const bool delta = M->node_mode == DDSG_IRBC_NODES_DELTA;
@@ -812,13 +849,17 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
     int64_t chunk = std::max<int64_t>(1, (int64_t)(kWsCap / per_state));
     chunk = std::min<int64_t>(chunk, ns);
     auto rnd = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t kc_bytes = jac_dev ? rnd(sizeof(int32_t) * kc.size()) : 0;
+    const size_t kc_bytes = jac_dev ? rnd(sizeof(int32_t) * koff.size()) + rnd(sizeof(int32_t) * (kids.size() + 1)) : 0;
     const size_t ac_bytes = delta ? rnd(sizeof(int32_t) * aoff.size()) + rnd(sizeof(int32_t) * (acomp.size() + 1)) : 0;
     if ((rc = ensure(M, per_state * chunk + 4096 + kc_bytes + ac_bytes))) return rc;
     unsigned char *base = static_cast<unsigned char *>(M->ws);
     if (jac_dev) {
-        kc_dev = reinterpret_cast<int32_t *>(base);
-        if (cudaMemcpyAsync(kc_dev, kc.data(), sizeof(int32_t) * kc.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        koff_dev = reinterpret_cast<int32_t *>(base);
+        kids_dev = reinterpret_cast<int32_t *>(base + rnd(sizeof(int32_t) * koff.size()));
+        if (cudaMemcpyAsync(koff_dev, koff.data(), sizeof(int32_t) * koff.size(), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            (!kids.empty() && cudaMemcpyAsync(kids_dev, kids.data(), sizeof(int32_t) * kids.size(),
+                                              cudaMemcpyHostToDevice, st) != cudaSuccess))
             return set_error(DDSG_ERR_CUDA, "euler_residual: copy failed");
         base += kc_bytes;
     }
@@ -891,8 +932,8 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
         if (e == cudaSuccess && jac_dev) {
             Tracer::Scope ts(&M->tr, 3, st);
             dim3 grid((unsigned)nsc, (unsigned)((N + 127) / 128));
-            irbc_jacobian_kernel<<<grid, 128, 0, st>>>(P, s0, nsc, *v.tables, form, kc_dev, v.lo, v.span,
-                                                       guess_dev, y, aux, jac_dev);
+            irbc_jacobian_kernel<<<grid, 128, 0, st>>>(P, s0, nsc, *v.tables, form, koff_dev, kids_dev, v.lo,
+                                                       v.span, guess_dev, y, aux, jac_dev);
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) return set_error(DDSG_ERR_CUDA, cudaGetErrorString(e));

@@ -58,14 +58,15 @@ def test_delta_nodes_match_oracle_and_all_nodes(G, N, ns):
 
 
 def test_delta_nodes_general_component_set(G):
-    """Extra (a_0, a_1), (a_1, a_3) and (a_2, k_3) pairs with their own
-    interactions: the delta for country i sums every component holding a_i."""
+    """Extra (a_0, a_1), (a_1, a_3), (a_2, k_3) and (k_0, k_1) pairs with their
+    own interactions: the delta for country i sums every component holding
+    a_i, and the Jacobian column of k'_i every component holding k_i."""
     N, level = 5, 4
     I = O.IRBCOracle(N, sigma=0.01)
     lam = I.steady_lambda()
     base = np.concatenate([np.ones(N), [lam]])
     pert = synth.irbc_policy_perturbation(synth.BASE_SEED + 412, N)
-    extra = [(0, 1), (1, 3), (2, N + 3)]
+    extra = [(0, 1), (1, 3), (2, N + 3), (N + 0, N + 1)]
 
     def fn(dims, X):
         X = np.asarray(X, np.float64)
@@ -100,6 +101,18 @@ def test_delta_nodes_general_component_set(G):
             r, _, _ = run(G, M, h, S, g, prec, form, G.NODES_DELTA)
             tol = 1e-11 if prec == 0 else 1e-6 * float(np.sum(np.abs(E.b_coeffs())))
             assert np.all(np.abs(r - r_ref) <= tol * sc), (form, prec, np.max(np.abs(r - r_ref) / sc))
+    # the analytic Jacobian on this component set (k_i held by {k_i}, (a_i, k_i),
+    # (a_2, k_3) and (k_0, k_1)) against central differences of the oracle
+    eps = 1e-6
+    for mode in (G.NODES_ALL, G.NODES_DELTA):
+        _, _, J = run(G, M, h, S[:4], g[:4], 0, 1, mode, jac=True)
+        for s in range(4):
+            Jfd = np.zeros((N + 1, N + 1))
+            for c in range(N + 1):
+                gp = g[s].copy(); gp[c] += eps
+                gm = g[s].copy(); gm[c] -= eps
+                Jfd[:, c] = (I.residual(E, S[s:s + 1], gp[None])[0] - I.residual(E, S[s:s + 1], gm[None])[0]) / (2 * eps)
+            assert np.all(np.abs(J[s] - Jfd) <= 1e-5 * np.maximum(1.0, np.abs(Jfd))), (mode, s, np.max(np.abs(J[s] - Jfd)))
 
 
 def test_delta_nodes_newton_and_nonfinite_states(G):

@@ -77,8 +77,8 @@ def _gpu_initial_policy(G, I, N):
     return h
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_time_iteration_matches_oracle(G, mode):
+@pytest.mark.parametrize("mode,all_pairs", [(0, False), (1, False), (1, True)])
+def test_time_iteration_matches_oracle(G, mode, all_pairs):
     from paper_2202_06555_gb300.time_iteration import time_iteration
     N = 2
     d = 2 * N
@@ -86,7 +86,7 @@ def test_time_iteration_matches_oracle(G, mode):
     M = G.IRBC(N, I.p["beta"], I.p["alpha"], I.p["delta"], I.p["sigma"], I.p["rho"], I.p["phi"],
                I.A, I.gamma, I.tau)
     lo, hi = np.full(d, 0.8), np.full(d, 1.2)
-    pairs = lambda k: [(i,) for i in range(d)] if k == 1 else [(j, N + j) for j in range(N)]
+    pairs = None if all_pairs else (lambda k: [(i,) for i in range(d)] if k == 1 else [(j, N + j) for j in range(N)])
     T = synth.irbc_states(synth.BASE_SEED + 601, 64, N)
     E0 = _initial_policy(I, N)
     Eo, hist_o = oracle_time_iteration(I, E0, 2, 2, 3, -1.0, -1.0, 0.0, lo, hi, T, candidates=pairs)
