@@ -49,6 +49,11 @@ WORKLOADS = {
     "warmstart20": dict(d=40, m=21, N=20, level=4, states=50_000, train=1_000_000,
                         wid=synth.W_IRBC20, precision="f64", form="slicefree", epochs=10,
                         batch=4096),
+    # adaptive DDSG time iteration (Alg. 1 around Alg. 2): N = 10 (d = 20, m = 11), order 2
+    # over all pairs with eta / rho pruning, adaptive grids up to level 6
+    "ti10": dict(d=20, m=11, N=10, order=2, level=6, eps_gamma=1e-4, eps_eta=1e-5, eps_rho=1e-6,
+                 ti_steps=4, test_states=2000, wid=synth.W_IRBC20 + 10, precision="f64",
+                 form="slicefree"),
 }
 
 FP32_LANES_PER_SM = 128
@@ -408,6 +413,57 @@ def run_irbc(args, w):
     return 0
 
 
+def run_time_iteration(args, w):
+    """Adaptive DDSG time iteration of the smooth IRBC model on the GPU: per step
+    the seconds, grid points, Newton solves and the Euler errors at test states."""
+    if args.impl == "reference":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the time-iteration study has no timed CPU arm (the oracle version is a test pin)"}))
+        return 0
+    import torch
+    import paper_2202_06555_gb300 as G
+    from paper_2202_06555_gb300.time_iteration import time_iteration
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    G.load()
+    N, d, m = w["N"], w["d"], w["m"]
+    t1 = G.irbc_table1(N)
+    lam = synth.irbc_steady_lambda(t1["gamma"], t1["tau"], t1["A"], t1["delta"])
+    M = G.IRBC(**t1)
+    lo, hi = np.full(d, 0.8), np.full(d, 1.2)
+    # initial policy: k' = k, lambda = lambda* (exact on level-2 single-dimension grids)
+    h0 = G.HDMR(d, m, 2, lo=lo, hi=hi)
+    comps = [()] + [(i,) for i in range(d)]
+    for u in comps:
+        h0.add_regular(list(u), 2)
+    vals = []
+    for c, u in enumerate(comps):
+        _, _, xs = h0.component_points(c)
+        y = np.tile(np.concatenate([np.ones(N), [lam]]), (xs.shape[0], 1))
+        for a, dim in enumerate(u):
+            if dim >= N:
+                y[:, dim - N] = xs[:, a]
+        vals.append(y)
+    h0.hierarchize(torch.from_numpy(np.concatenate(vals)).cuda())
+    T = synth.irbc_states(synth.BASE_SEED + w["wid"], w["test_states"], N)
+    prec = G.F32C if w["precision"] == "f32c" else G.F64
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pol, hist = time_iteration(M, h0, w["ti_steps"], w["order"], w["level"], w["eps_gamma"], w["eps_eta"],
+                               w["eps_rho"], lo, hi, T, precision=prec, node_mode=G.NODES_DELTA)
+    torch.cuda.synchronize()
+    total = time.perf_counter() - t0
+    out = {"metric": "adaptive DDSG time-iteration step time (s) and Euler error, IRBC N=10",
+           "value": total / len(hist), "unit": "s/step", "higher_is_better": False, "n_gpus": 1,
+           "data": "synthetic", "dtype": "f64" if prec == G.F64 else "f32",
+           "config": {"workload": "ti10_ddsg_time_iteration", "N": N, "d": d, "m": m, "order": w["order"],
+                      "max_level": w["level"], "eps_gamma": w["eps_gamma"], "eps_eta": w["eps_eta"],
+                      "eps_rho": w["eps_rho"], "steps": len(hist), "test_states": w["test_states"],
+                      "candidates": "all k-subsets", "node_mode": "shortcut"},
+           "steps": hist}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_warmstart(args, w):
     """Time-iteration step at N = 20 with a learned Newton warm start."""
     import torch
@@ -551,6 +607,8 @@ def main():
         return run_irbc(args, w)
     if args.workload == "warmstart20":
         return run_warmstart(args, w)
+    if args.workload == "ti10":
+        return run_time_iteration(args, w)
     if args.impl == "reference":
         return run_reference(args, w)
 
