@@ -270,10 +270,12 @@ int hdmr_reserve(hdmr_t *h, int64_t n);
 int hdmr_stats(hdmr_t *h, int64_t *stats_host, int reset, ddsg_stream_t stream);
 
 /*
- * hdmr_eval_host -- hdmr_eval with HOST buffers: copies x_host (n*d) to a
- * handle-owned device buffer on `stream`, evaluates, copies y_host (n*m) back
- * and synchronizes `stream` before returning. Pinned host memory gives the
- * fastest copies. The whole round trip is the end-to-end cost of one call.
+ * hdmr_eval_host -- hdmr_eval with HOST buffers: evaluates x_host (n*d),
+ * copies the result into y_host (n*m) and synchronizes `stream` before
+ * returning. Page-locked x_host is read by the encoding kernel directly
+ * through its mapped device address (the transfer overlaps the encoding);
+ * other host memory is first copied to a handle-owned device buffer. The whole
+ * round trip is the end-to-end cost of one call.
  */
 int hdmr_eval_host(hdmr_t *h, int64_t n, const double *x_host, double *y_host, int precision,
                    int form, ddsg_stream_t stream);

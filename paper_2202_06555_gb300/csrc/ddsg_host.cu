@@ -952,27 +952,41 @@ extern "C" int hdmr_eval_host(hdmr_t *h, int64_t n, const double *x_host, double
     if (!x_host || !y_host) return fail(DDSG_ERR_ARG, "hdmr_eval_host: NULL x or y");
     if (!h->uploaded || !h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_eval_host: call hdmr_hierarchize first");
     DeviceGuard g(h->device);
+    // Page-locked (pinned) queries are read by the encoding kernel straight from
+    // host memory through their mapped device address: the transfer overlaps the
+    // encoding instead of preceding it. Other host memory is copied first.
+    auto mapped = [](const void *p) -> void * {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, p) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+            return pa.devicePointer;
+        cudaGetLastError();
+        return nullptr;
+    };
+    const double *x_mapped = static_cast<const double *>(mapped(x_host));
+    double *y_mapped = static_cast<double *>(mapped(y_host));
     const size_t xb = sizeof(double) * (size_t)n * h->d, yb = sizeof(double) * (size_t)n * h->m;
-    if (xb + yb > h->hbuf_bytes) {
+    const size_t need = (x_mapped ? 0 : xb) + (y_mapped ? 0 : yb) + 256;
+    if (need > h->hbuf_bytes) {
         cudaFree(h->hbuf);
         h->hbuf = nullptr;
         h->hbuf_bytes = 0;
-        if (cudaMalloc(&h->hbuf, xb + yb) != cudaSuccess) {
+        if (cudaMalloc(&h->hbuf, need) != cudaSuccess) {
             cudaGetLastError();
-            return fail(DDSG_ERR_OOM, "hdmr_eval_host: staging buffer of %zu bytes unavailable", xb + yb);
+            return fail(DDSG_ERR_OOM, "hdmr_eval_host: staging buffer of %zu bytes unavailable", need);
         }
-        h->hbuf_bytes = xb + yb;
+        h->hbuf_bytes = need;
     }
-    double *xd = reinterpret_cast<double *>(h->hbuf);
-    double *yd = xd + (size_t)n * h->d;
+    double *yd = reinterpret_cast<double *>(h->hbuf);
+    double *xd = yd + (y_mapped ? 0 : (size_t)n * h->m);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    {
+    if (!x_mapped) {
         ProfScope ps(h, DDSG_K_COPY, st);
         CUDA_TRY(cudaMemcpyAsync(xd, x_host, xb, cudaMemcpyHostToDevice, st));
     }
-    int rc = hdmr_eval(h, n, xd, yd, precision, form, nullptr, nullptr, stream);
+    int rc = hdmr_eval(h, n, x_mapped ? x_mapped : xd, y_mapped ? y_mapped : yd, precision, form, nullptr,
+                       nullptr, stream);
     if (rc) return rc;
-    {
+    if (!y_mapped) {
         ProfScope ps(h, DDSG_K_COPY, st);
         CUDA_TRY(cudaMemcpyAsync(y_host, yd, yb, cudaMemcpyDeviceToHost, st));
     }

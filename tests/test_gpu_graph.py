@@ -116,3 +116,24 @@ def test_graph_orders_against_the_callers_stream(G, pair):
     h.profile(False)
     assert np.array_equal(out.cpu().numpy(), _direct(h, x1, m, 1, 1))
     assert prof["graph"][1] == 4 and prof["graph"][0] > 0
+
+
+def test_eval_host_matches_device_eval(G, pair):
+    """hdmr_eval_host with pageable numpy buffers (copied) and with page-locked
+    buffers (read by the encoding kernel through their mapped address) gives
+    hdmr_eval's result bit for bit, twice in a row."""
+    ref, h = pair
+    m = ref.m
+    X = synth.uniform_queries(76, 1500, ref.d)
+    want = _direct(h, torch.from_numpy(X).cuda(), m, 1, 1)
+    y = np.zeros((X.shape[0], m))
+    for _ in range(2):
+        y[:] = -1.0
+        h.eval_host(np.ascontiguousarray(X), y, 1, 1)
+        assert np.array_equal(y, want)
+    xp = torch.from_numpy(X).pin_memory()
+    yp = torch.empty((X.shape[0], m), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        yp.fill_(-1.0)
+        h.eval_host(xp.numpy(), yp.numpy(), 1, 1)
+        assert np.array_equal(yp.numpy(), want)
