@@ -270,11 +270,12 @@ int hdmr_reserve(hdmr_t *h, int64_t n);
 int hdmr_stats(hdmr_t *h, int64_t *stats_host, int reset, ddsg_stream_t stream);
 
 /*
- * hdmr_eval_host -- hdmr_eval with HOST buffers: evaluates x_host (n*d),
- * copies the result into y_host (n*m) and synchronizes `stream` before
- * returning. Page-locked x_host is read by the encoding kernel directly
- * through its mapped device address (the transfer overlaps the encoding);
- * other host memory is first copied to a handle-owned device buffer. The whole
+ * hdmr_eval_host -- hdmr_eval with HOST buffers x_host (n*d) and y_host (n*m);
+ * synchronizes `stream` before returning. Page-locked buffers are accessed by
+ * the kernels through their mapped device addresses: the encoding kernel reads
+ * x_host and the evaluation kernel writes y_host directly, so the transfers
+ * overlap the computation. Other host memory goes through a handle-owned
+ * device buffer with a copy before (x) or after (y) the evaluation. The whole
  * round trip is the end-to-end cost of one call.
  */
 int hdmr_eval_host(hdmr_t *h, int64_t n, const double *x_host, double *y_host, int precision,
