@@ -98,6 +98,8 @@ def _declare_irbc(L):
     L.orc_irbc_residual.restype = None
     L.orc_irbc_residual.argtypes = [C.c_int, _p, _p, _p, C.c_int, _p, _p, _p, _p, _p, _p, _p, _p,
                                     _p, C.c_int, _i64, _p, _p, _p, _p]
+    L.orc_irbc_residual_irr.restype = None
+    L.orc_irbc_residual_irr.argtypes = L.orc_irbc_residual.argtypes
     L.orc_lu_solve.restype = C.c_int
     L.orc_lu_solve.argtypes = [C.c_int, _p, _p]
 
@@ -387,11 +389,16 @@ IRBC_A_GAMMA = 0.25     # the undefined "a" of Table 1's gamma_j (reading)
 
 
 class IRBCOracle:
-    """Smooth IRBC equilibrium conditions (eq. model1, model2) at given states,
-    with the policy interpolated from an OracleDDSG over x = (a, k)."""
+    """IRBC equilibrium conditions at given states, with the policy interpolated
+    from an OracleDDSG over x = (a, k). Smooth model (eq. model1, model2; policy
+    (k', lambda), m = N+1) or, with irreversible=True, the non-smooth model
+    (eq. modelkink1 with the complementarity as a Fischer-Burmeister equation,
+    and eq. model2; policy (k', mu, lambda), m = 2N+1)."""
 
-    def __init__(self, N: int, lo=0.8, hi=1.2, **overrides):
+    def __init__(self, N: int, lo=0.8, hi=1.2, irreversible=False, **overrides):
         self.N = N
+        self.irreversible = bool(irreversible)
+        self.m = 2 * N + 1 if irreversible else N + 1
         p = dict(IRBC_TABLE1)
         p.update(overrides)
         self.p = p
@@ -429,12 +436,13 @@ class IRBCOracle:
     def residual(self, E: OracleDDSG, states, guess, form=1, want_err=False):
         t = E.tables()
         states = np.ascontiguousarray(states, np.float64).reshape(-1, 2 * self.N)
-        guess = np.ascontiguousarray(guess, np.float64).reshape(-1, self.N + 1)
+        guess = np.ascontiguousarray(guess, np.float64).reshape(-1, self.m)
         ns = states.shape[0]
-        r = np.zeros((ns, self.N + 1))
+        r = np.zeros((ns, self.m))
         ee = np.zeros((ns, 2)) if want_err else None
         b = E.b_coeffs()
-        lib().orc_irbc_residual(self.N, ptr(self.prm), ptr(self.gamma), ptr(self.tau),
+        fn = lib().orc_irbc_residual_irr if self.irreversible else lib().orc_irbc_residual
+        fn(self.N, ptr(self.prm), ptr(self.gamma), ptr(self.tau),
                                 len(E.comps), ptr(t["k"]), ptr(t["dims"]), ptr(t["off"]),
                                 ptr(t["lv"]), ptr(t["ix"]), ptr(t["alpha"]), ptr(b), ptr(E.lo),
                                 ptr(E.hi), int(form), ns, ptr(states), ptr(guess), ptr(r), ptr(ee))
@@ -448,7 +456,7 @@ class IRBCOracle:
         sol = np.array(np.atleast_2d(guess), dtype=np.float64)
         its = np.zeros(states.shape[0], np.int32)
         norms = np.zeros(states.shape[0])
-        n = self.N + 1
+        n = self.m
         for s in range(states.shape[0]):
             z = sol[s].copy()
             r = self.residual(E, states[s:s + 1], z[None], form)[0]

@@ -120,6 +120,83 @@ void orc_irbc_residual(int N, const double *prm, const double *gamma, const doub
     free(pq);
 }
 
+/* Fischer-Burmeister function: zero iff a >= 0, b >= 0, a b = 0. */
+static double fb(double a, double b) { return a + b - sqrt(a * a + b * b); }
+
+/* Non-smooth IRBC (irreversible investment, eq. modelkink1 with the aggregate
+ * resource constraint eq. model2). The policy maps x = (a, k) to
+ * (k'_1..k'_N, mu_1..mu_N, lambda) (m = 2N+1); guess rows likewise.
+ * Residual rows: j < N the Euler equation of country j,
+ *   lambda (1 + phi g'_j) - mu_j - beta E[lambda' (a'_j A alpha k'^(alpha-1) + 1 - delta
+ *        + phi/2 g''_j (g''_j + 2)) - (1 - delta) mu'_j],
+ * N + j the complementarity 0 <= mu_j _|_ (k'_j - (1 - delta) k_j) >= 0 written
+ * as FB(mu_j, k'_j - (1 - delta) k_j) = 0, and 2N the resource constraint.
+ * euler_err (optional, ns x 2): max_j |beta E_j / (lambda (1 + phi g'_j) - mu_j) - 1|
+ * and |resource| / sum_j Y_j. Next states are clamped to [lo, hi] inside the
+ * interpolation, as in the smooth model. */
+void orc_irbc_residual_irr(int N, const double *prm, const double *gamma, const double *tau,
+                           int C, const int32_t *comp_k, const int32_t *comp_dims,
+                           const int64_t *comp_off, const uint8_t *levels, const uint32_t *indices,
+                           const double *alpha_tab, const double *b, const double *lo,
+                           const double *hi, int form, int64_t ns, const double *states,
+                           const double *guess, double *resid, double *euler_err)
+{
+    const double beta = prm[0], alpha = prm[1], delta = prm[2], sigma = prm[3], rho = prm[4],
+                 phi = prm[5], A = prm[6];
+    const int d = 2 * N, m = 2 * N + 1, nq = 2 * (N + 1);
+    double *nodes = (double *)malloc(sizeof(double) * (size_t)nq * (N + 1));
+    double *wts = (double *)malloc(sizeof(double) * (size_t)nq);
+    double *xq = (double *)malloc(sizeof(double) * (size_t)nq * d);
+    double *pq = (double *)malloc(sizeof(double) * (size_t)nq * m);
+    orc_monomial_nodes(N + 1, nodes, wts);
+    for (int64_t s = 0; s < ns; ++s) {
+        const double *a = &states[s * d];
+        const double *k = &states[s * d + N];
+        const double *kp = &guess[s * m];
+        const double *mu = &guess[s * m + N];
+        const double lam = guess[s * m + 2 * N];
+        for (int q = 0; q < nq; ++q) {
+            const double eg = nodes[q * (N + 1) + N];
+            for (int j = 0; j < N; ++j) {
+                xq[q * d + j] = exp(rho * log(a[j]) + sigma * (nodes[q * (N + 1) + j] + eg));
+                xq[q * d + N + j] = kp[j];
+            }
+        }
+        orc_eval(d, m, C, comp_k, comp_dims, comp_off, levels, indices, alpha_tab, b, lo, hi, form,
+                 nq, xq, pq, NULL, NULL, NULL);
+        double res = 0.0, ysum = 0.0, emax = 0.0;
+        for (int j = 0; j < N; ++j) {
+            const double g1 = kp[j] / k[j] - 1.0;
+            double E = 0.0;
+            for (int q = 0; q < nq; ++q) {
+                const double g2 = pq[q * m + j] / kp[j] - 1.0;
+                const double lamp = pq[q * m + 2 * N];
+                const double mup = pq[q * m + N + j];
+                E += wts[q] * (lamp * (xq[q * d + j] * A * alpha * pow(kp[j], alpha - 1.0) + (1.0 - delta) +
+                                       0.5 * phi * g2 * (g2 + 2.0)) -
+                               (1.0 - delta) * mup);
+            }
+            const double lhs = lam * (1.0 + phi * g1) - mu[j];
+            resid[s * m + j] = lhs - beta * E;
+            resid[s * m + N + j] = fb(mu[j], kp[j] - (1.0 - delta) * k[j]);
+            const double e = fabs(beta * E / lhs - 1.0);
+            if (e > emax) emax = e;
+            const double Y = a[j] * A * pow(k[j], alpha);
+            ysum += Y;
+            res += Y + k[j] * ((1.0 - delta) - 0.5 * phi * g1 * g1) - kp[j] - pow(lam / tau[j], -gamma[j]);
+        }
+        resid[s * m + 2 * N] = res;
+        if (euler_err) {
+            euler_err[s * 2 + 0] = emax;
+            euler_err[s * 2 + 1] = fabs(res) / ysum;
+        }
+    }
+    free(nodes);
+    free(wts);
+    free(xq);
+    free(pq);
+}
+
 /* Dense LU with partial pivoting and solve (row-major n x n), in place.
  * Returns 0, or -1 if a pivot is exactly zero. */
 int orc_lu_solve(int n, double *Amat, double *rhs)

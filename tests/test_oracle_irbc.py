@@ -111,3 +111,107 @@ def test_lu_solve_matches_numpy():
     assert np.allclose(A @ x, b, atol=1e-12)
     S = np.zeros((3, 3))
     assert O.lib().orc_lu_solve(3, O.ptr(S), O.ptr(np.ones(3))) == -1
+
+
+# --------------------------------------------------------------------------
+# non-smooth model (irreversible investment, eq. modelkink1)
+# --------------------------------------------------------------------------
+
+def _irr_policy(I, N, mu_fn, sigma_pert=0.0):
+    """Policy (k', mu, lambda) over x = (a, k): k' = k + a small seeded
+    perturbation, lambda = lambda*, mu = mu_fn(k, a) on the (k_j, a_j) pairs."""
+    lam = I.steady_lambda()
+    d, m = 2 * N, 2 * N + 1
+
+    def fn(dims, X):
+        X = np.asarray(X, np.float64).reshape(-1, len(dims)) if len(dims) else np.zeros((np.atleast_2d(X).shape[0], 0))
+        full = np.ones((X.shape[0], d))
+        if len(dims):
+            full[:, list(dims)] = X
+        y = np.zeros((X.shape[0], m))
+        y[:, :N] = full[:, N:] + sigma_pert * np.sin(5 * (full[:, :N] - 1))
+        y[:, N:2 * N] = mu_fn(full[:, N:], full[:, :N])
+        y[:, 2 * N] = lam
+        # cut-HDMR: keep only the part living on `dims` (anchor contributions are exact here)
+        return y
+
+    E = O.OracleDDSG(d, m, lo=np.full(d, 0.8), hi=np.full(d, 1.2))
+    for u in [()] + [(i,) for i in range(d)] + [(j, N + j) for j in range(N)]:
+        E.add_regular(u, 4)
+    E.fill_values(fn)
+    E.hierarchize()
+    return E, lam
+
+
+def test_fischer_burmeister_rows():
+    """Row N + j is FB(mu_j, k'_j - (1 - delta) k_j) = mu + I - sqrt(mu^2 + I^2):
+    zero on the complementarity set, 2 at (mu, I) = (3, 4)... scaled to the
+    chosen guesses."""
+    N = 2
+    I = O.IRBCOracle(N, irreversible=True)
+    E, lam = _irr_policy(I, N, lambda k, a: 0.0 * k)
+    s = np.ones((1, 2 * N))
+    dl = I.p["delta"]
+    for mu, inv, want in ((0.0, 0.02, 0.0), (0.5, 0.0, 0.0), (0.03, 0.04, 0.02), (0.0, -0.01, -0.02)):
+        g = np.concatenate([np.full(N, (1 - dl) + inv), np.full(N, mu), [lam]])[None]
+        r = I.residual(E, s, g)[0]
+        assert np.allclose(r[N:2 * N], want, atol=1e-15), (mu, inv, r[N:2 * N])
+
+
+def test_irreversible_reduces_to_smooth_when_mu_vanishes():
+    """With mu == 0 in the policy and the guess, the Euler rows of eq. modelkink1
+    are those of eq. model1 and the resource row is eq. model2."""
+    N = 3
+    Ii = O.IRBCOracle(N, irreversible=True)
+    Is = O.IRBCOracle(N)
+    E, lam = _irr_policy(Ii, N, lambda k, a: 0.0 * k, sigma_pert=0.01)
+    Es = O.OracleDDSG(2 * N, N + 1, lo=np.full(2 * N, 0.8), hi=np.full(2 * N, 1.2))
+    for c, u in enumerate(E.comps):
+        cs = Es.add_component(u, E.lv[c], E.ix[c])
+        Es.set_values(cs, E.values[c][:, list(range(N)) + [2 * N]])
+    Es.hierarchize()
+    rng = np.random.default_rng(4)
+    S = 0.9 + 0.2 * rng.random((5, 2 * N))
+    gk = S[:, N:] * (1 + 0.01 * rng.random((5, N)))
+    gi = np.concatenate([gk, np.zeros((5, N)), np.full((5, 1), lam)], 1)
+    gs = np.concatenate([gk, np.full((5, 1), lam)], 1)
+    for form in (0, 1):
+        ri, ei = Ii.residual(E, S, gi, form=form, want_err=True)
+        rs, es = Is.residual(Es, S, gs, form=form, want_err=True)
+        assert np.allclose(ri[:, :N], rs[:, :N], rtol=1e-12, atol=1e-13)
+        assert np.allclose(ri[:, 2 * N], rs[:, N], rtol=1e-12, atol=1e-13)
+        assert np.allclose(ei, es, rtol=1e-12, atol=1e-14)
+
+
+def test_irreversible_steady_state_and_newton():
+    """sigma = 0, a = k = 1: (k' = 1, mu = 0, lambda*) zeroes every row
+    (investment delta > 0, so the constraint is slack); Newton from a perturbed
+    guess returns there, and from a state whose capital must shrink it lands on
+    the constraint: k' = (1 - delta) k with mu > 0."""
+    N = 2
+    I = O.IRBCOracle(N, irreversible=True, sigma=0.0)
+    E, lam = _irr_policy(I, N, lambda k, a: 0.0 * k)
+    s = np.ones((1, 2 * N))
+    g = np.concatenate([np.ones(N), np.zeros(N), [lam]])[None]
+    assert np.max(np.abs(I.residual(E, s, g)[0])) < 1e-12
+    g0 = np.concatenate([[1.03, 0.98], [0.01, 0.0], [lam * 1.05]])[None]
+    sol, _, nrm = I.newton(E, s, g0)
+    assert nrm[0] < 1e-10 and np.allclose(sol[0], g[0], atol=1e-8)
+    # a continuation policy that returns capital to 1 (k' = 1 everywhere): a
+    # country holding k = 1.19 wants to disinvest faster than depreciation
+    const = lambda dims, X: np.tile(np.concatenate([np.ones(N), np.zeros(N), [lam]]), (np.atleast_2d(X).shape[0], 1))
+    E1 = O.OracleDDSG(2 * N, 2 * N + 1, lo=np.full(2 * N, 0.8), hi=np.full(2 * N, 1.2))
+    for u in [()] + [(i,) for i in range(2 * N)] + [(j, N + j) for j in range(N)]:
+        E1.add_regular(u, 3)
+    E1.fill_values(const)
+    E1.hierarchize()
+    dl = I.p["delta"]
+    for s2 in ([1.0, 1.0, 1.19, 1.0], [0.8, 1.0, 1.2, 1.0]):
+        s2 = np.array([s2])
+        sol2, _, nrm2 = I.newton(E1, s2, np.concatenate([[s2[0, 2], 1.0], [0.0, 0.0], [lam]])[None])
+        assert nrm2[0] < 1e-10
+        inv = sol2[0, :N] - (1 - dl) * s2[0, N:]
+        mu = sol2[0, N:2 * N]
+        assert np.all(inv > -1e-10) and np.all(mu > -1e-10) and np.all(np.abs(inv * mu) < 1e-10)
+        assert mu[0] > 1e-3 and abs(inv[0]) < 1e-10      # country 0 sits on the constraint
+        assert mu[1] == 0.0 and inv[1] > 1e-3            # country 1 invests
