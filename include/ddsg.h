@@ -327,7 +327,8 @@ int irbc_destroy(irbc_t *model);
  *   policy: hierarchized hdmr_t over x = (a_1..a_N, k_1..k_N) (d = 2N) with
  *           m = N+1 outputs (k'_1..k'_N, lambda); its domain clamps next states.
  *   states_dev: ns x 2N, guess_dev: ns x (N+1) (k', lambda), resid_dev: ns x (N+1)
- *           (rows j < N: eq. model1 of country j+1; row N: eq. model2).
+ *           (rows j < N: eq. model1 of country j+1; row N: eq. model2); with
+ *           irbc_set_irreversible the widths are 2N+1 (see there).
  *   jac_dev (nullable): ns x (N+1) x (N+1), row-major d resid / d guess, from the
  *           hat slopes (right derivative at kinks, zero where k'_i is clamped)
  *           and the chain rule. Needs every policy component that holds a k_i
@@ -358,6 +359,19 @@ int euler_residual(irbc_t *model, hdmr_t *policy, int64_t ns, const double *stat
  *     component set. About N times less interpolation work.
  */
 enum { DDSG_IRBC_NODES_ALL = 0, DDSG_IRBC_NODES_DELTA = 1 };
+
+/*
+ * irbc_set_irreversible -- switch the model to the non-smooth IRBC of Sec. 2.1
+ * (irreversible investment, eq. modelkink1). The policy then maps x = (a, k)
+ * to (k'_1..k'_N, mu_1..mu_N, lambda) (m = 2N+1; guesses and solutions the
+ * same). Residual rows: j < N the Euler equations with -mu_j today and
+ * (1 - delta) mu'_j inside the expectation; N + j the complementarity
+ * 0 <= mu_j _|_ k'_j - (1 - delta) k_j >= 0 as the Fischer-Burmeister
+ * equation mu + I - sqrt(mu^2 + I^2) = 0 (its Jacobian row uses a generalized
+ * derivative, 1 - 1/sqrt 2 per argument at mu = I = 0); 2N the resource
+ * constraint. Newton is then a semismooth Newton method. Needs 2N+1 <= 165.
+ */
+int irbc_set_irreversible(irbc_t *model, int on);
 int irbc_set_node_mode(irbc_t *model, int mode);
 
 /* Batched dense LU with partial pivoting (FP64): dx = -A^{-1} r for ns

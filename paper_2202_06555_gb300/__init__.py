@@ -76,6 +76,7 @@ SIGNATURES = {
     "mlp_profile_read": (_int, [_p, _p, _p, _int]),
     "irbc_profile_read": (_int, [_p, _p, _p, _int]),
     "irbc_set_node_mode": (_int, [_p, _int]),
+    "irbc_set_irreversible": (_int, [_p, _int]),
     "hdmr_profile_read": (_int, [_p, _p, _p, _int]),
 }
 
@@ -356,6 +357,7 @@ class IRBC:
                  phi: float, A: float, gamma, tau):
         lib = load()
         self.N = int(N)
+        self.m = self.N + 1
         self.prm = IrbcParams(self.N, beta, alpha, delta, sigma, rho, phi, A)
         g = np.ascontiguousarray(gamma, np.float64)
         t = np.ascontiguousarray(tau, np.float64)
@@ -373,6 +375,11 @@ class IRBC:
             self.close()
         except Exception:
             pass
+
+    def set_irreversible(self, on: bool = True):
+        """Non-smooth model (irreversible investment): policy (k', mu, lambda)."""
+        _check(load().irbc_set_irreversible(self._h, int(bool(on))), "irbc_set_irreversible")
+        self.m = 2 * self.N + 1 if on else self.N + 1
 
     def set_node_mode(self, mode: int):
         """NODES_ALL: interpolate every monomial node; NODES_DELTA: the no-shock

@@ -33,6 +33,8 @@ namespace {
 
 struct IrbcDev {
     int N;
+    int m;      // policy outputs: N + 1 (k', lambda) or 2N + 1 (k', mu, lambda)
+    int irr;    // irreversible investment (eq. modelkink1): mu_j and a complementarity row
     double beta, alpha, delta, sigma, rho, phi, A;
     const double *gamma, *tau;
 };
@@ -76,7 +78,7 @@ __global__ void irbc_queries_kernel(IrbcDev P, int64_t ns, const double *__restr
                                     const double *__restrict__ guess, const double *__restrict__ lo,
                                     const double *__restrict__ span, uint64_t *__restrict__ X,
                                     int32_t *__restrict__ flags, unsigned long long *__restrict__ stats) {
-    const int N = P.N, d = 2 * N, m = N + 1, nq = 2 * (N + 1);
+    const int N = P.N, d = 2 * N, m = P.m, nq = 2 * (N + 1);
     const int64_t Q = ns * nq;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long clamps = 0;
@@ -101,7 +103,9 @@ __global__ void irbc_queries_kernel(IrbcDev P, int64_t ns, const double *__restr
             const uint64_t e = encode_coord(guess[s * m + dim - N], lo[dim], span[dim], bad, clamps);
             clamps *= (unsigned long long)nq;
             for (int q = 0; q < nq; ++q) Xrow[q] = e;
-            if (dim == d - 1 && !isfinite(guess[s * m + N])) bad = true;
+            if (dim == d - 1)
+                for (int o = N; o < m; ++o)
+                    if (!isfinite(guess[s * m + o])) bad = true;
         }
         if (bad)
             for (int q = 0; q < nq; ++q) flags[s * nq + q] = 1;
@@ -110,7 +114,12 @@ __global__ void irbc_queries_kernel(IrbcDev P, int64_t ns, const double *__restr
     if ((threadIdx.x & 31) == 0 && clamps) atomicAdd(&stats[0], clamps);
 }
 
-// Per state (block): residuals, Euler errors and Jacobian pieces.
+// Per state (block): residuals, Euler errors and Jacobian pieces. Rows j < N:
+// the Euler equation of country j (eq. model1; with irreversible investment
+// eq. modelkink1, which adds -mu_j today and (1 - delta) mu'_j inside the
+// expectation); rows N + j (irreversible only): the complementarity
+// 0 <= mu_j _|_ k'_j - (1 - delta) k_j >= 0 as the Fischer-Burmeister equation
+// mu + I - sqrt(mu^2 + I^2) = 0; row m - 1: the resource constraint (eq. model2).
 // aux (per state, 7 x N): S1, SM, Dd, e0, ep, em, kp^(alpha-1).
 __global__ void __launch_bounds__(256) irbc_residual_kernel(IrbcDev P, int64_t s0, int64_t nsc,
                                                             const double *__restrict__ states,
@@ -120,13 +129,14 @@ __global__ void __launch_bounds__(256) irbc_residual_kernel(IrbcDev P, int64_t s
                                                             double *__restrict__ err,
                                                             double *__restrict__ jac,
                                                             double *__restrict__ aux) {
-    const int N = P.N, d = 2 * N, m = N + 1, nq = 2 * (N + 1);
+    const int N = P.N, d = 2 * N, m = P.m, nq = 2 * (N + 1);
+    const int L = m - 1;                      // lambda's position in the policy
     const int64_t sl = blockIdx.x;           // state within the chunk
     const int64_t s = s0 + sl;                // global state
     const double *a = states + s * d;
     const double *k = states + s * d + N;
     const double *kp = guess + s * m;
-    const double lam = guess[s * m + N];
+    const double lam = guess[s * m + L];
     const double w = 1.0 / (double)nq;
     const double *ys = y + sl * nq * (int64_t)m;
     double res = 0.0, ysum = 0.0, emax = 0.0, dlam = 0.0;
@@ -135,14 +145,16 @@ __global__ void __launch_bounds__(256) irbc_residual_kernel(IrbcDev P, int64_t s
         next_a3(P, a[j], e3[0], e3[1], e3[2]);
         const double g1 = kp[j] / k[j] - 1.0;
         const double kpa = pow(kp[j], P.alpha - 1.0);
+        const double mu = P.irr ? guess[s * m + N + j] : 0.0;
         double E = 0.0, S1 = 0.0, SM = 0.0, Dd = 0.0;
         for (int q = 0; q < nq; ++q) {
             const double ap = e3[node_variant(q, j, N)];
             const double kpp = ys[(int64_t)q * m + j];
-            const double lamp = ys[(int64_t)q * m + N];
+            const double lamp = ys[(int64_t)q * m + L];
             const double g2 = kpp / kp[j] - 1.0;
             const double Mq = ap * P.A * P.alpha * kpa + (1.0 - P.delta) + 0.5 * P.phi * g2 * (g2 + 2.0);
             E += w * lamp * Mq;
+            if (P.irr) E -= w * (1.0 - P.delta) * ys[(int64_t)q * m + N + j];
             if (jac) {
                 S1 += w * lamp * 0.5 * P.phi * (2.0 * g2 + 2.0) / kp[j];
                 SM += w * Mq;
@@ -150,18 +162,32 @@ __global__ void __launch_bounds__(256) irbc_residual_kernel(IrbcDev P, int64_t s
                                   0.5 * P.phi * (2.0 * g2 + 2.0) * (-kpp / (kp[j] * kp[j])));
             }
         }
-        const double lhs = lam * (1.0 + P.phi * g1);
+        const double lhs = lam * (1.0 + P.phi * g1) - mu;
         resid[s * m + j] = lhs - P.beta * E;
         emax = fmax(emax, fabs(P.beta * E / lhs - 1.0));
+        const double inv = kp[j] - (1.0 - P.delta) * k[j];
+        const double rr = sqrt(mu * mu + inv * inv);
+        if (P.irr) resid[s * m + N + j] = mu + inv - rr;
         const double Y = a[j] * P.A * pow(k[j], P.alpha);
         ysum += Y;
         const double cj = pow(lam / P.tau[j], -P.gamma[j]);
         res += Y + k[j] * ((1.0 - P.delta) - 0.5 * P.phi * g1 * g1) - kp[j] - cj;
         if (jac) {
             double *J = jac + s * (int64_t)m * m;
-            J[(int64_t)j * m + N] = 1.0 + P.phi * g1;        // d r_j / d lambda
-            J[(int64_t)N * m + j] = -(1.0 + P.phi * g1);     // d resource / d k'_j
+            J[(int64_t)j * m + L] = 1.0 + P.phi * g1;        // d r_j / d lambda
+            J[(int64_t)L * m + j] = -(1.0 + P.phi * g1);     // d resource / d k'_j
             dlam += P.gamma[j] * cj / lam;                   // d resource / d lambda
+            if (P.irr) {
+                for (int i = 0; i < N; ++i) J[(int64_t)j * m + N + i] = i == j ? -1.0 : 0.0;   // d r_j / d mu_i
+                J[(int64_t)L * m + N + j] = 0.0;                                              // d resource / d mu_j
+                // complementarity row: a generalized derivative of FB, (1 - 1/sqrt 2) at the kink
+                double *Jr = J + (int64_t)(N + j) * m;
+                for (int c = 0; c < m; ++c) Jr[c] = 0.0;
+                const double ga = rr > 0.0 ? 1.0 - mu / rr : 1.0 - 0.70710678118654752;
+                const double gb = rr > 0.0 ? 1.0 - inv / rr : 1.0 - 0.70710678118654752;
+                Jr[j] = gb;
+                Jr[N + j] = ga;
+            }
             double *ax = aux + sl * 7 * (int64_t)N;
             ax[0 * N + j] = S1;
             ax[1 * N + j] = SM;
@@ -189,12 +215,12 @@ __global__ void __launch_bounds__(256) irbc_residual_kernel(IrbcDev P, int64_t s
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        resid[s * m + N] = red[0][0];
+        resid[s * m + L] = red[0][0];
         if (err) {
             err[s * 2 + 0] = red[2][0];
             err[s * 2 + 1] = fabs(red[0][0]) / red[1][0];
         }
-        if (jac) jac[s * (int64_t)m * m + (int64_t)N * m + N] = red[3][0];
+        if (jac) jac[s * (int64_t)m * m + (int64_t)L * m + L] = red[3][0];
     }
 }
 
@@ -276,7 +302,8 @@ __global__ void __launch_bounds__(128) irbc_jacobian_kernel(IrbcDev P, int64_t s
                                                             const double *__restrict__ y,
                                                             const double *__restrict__ aux,
                                                             double *__restrict__ jac) {
-    const int N = P.N, m = N + 1, nq = 2 * (N + 1);
+    const int N = P.N, m = P.m, nq = 2 * (N + 1);
+    const int L = m - 1;   // lambda's position in the policy
     const int64_t sl = blockIdx.x;                      // state within the chunk (grid.x: no 65535 limit)
     const int64_t s = s0 + sl;
     const int i = blockIdx.y * blockDim.x + threadIdx.x;
@@ -334,7 +361,7 @@ __global__ void __launch_bounds__(128) irbc_jacobian_kernel(IrbcDev P, int64_t s
         double dPN[3];
         for (int v = 0; v < nv; ++v) {
             double acc = 0.0;
-            for (int q = 0; q < nt[v]; ++q) acc += terms[v][q].w * t.alpha64[(int64_t)terms[v][q].row * mp + N];
+            for (int q = 0; q < nt[v]; ++q) acc += terms[v][q].w * t.alpha64[(int64_t)terms[v][q].row * mp + L];
             dPN[v] = acc;
         }
         for (int j = 0; j < N; ++j) {
@@ -355,7 +382,7 @@ __global__ void __launch_bounds__(128) irbc_jacobian_kernel(IrbcDev P, int64_t s
                 for (int u = 0; u < 4; ++u) {
                     const int q = qs[u];
                     const double kpp = ys[(int64_t)q * m + j];
-                    const double lamp = ys[(int64_t)q * m + N];
+                    const double lamp = ys[(int64_t)q * m + L];
                     const double g2 = kpp / kp[j] - 1.0;
                     const double ap = ax[(3 + node_variant(q, j, N)) * N + j];
                     s1[u] = w * lamp * 0.5 * P.phi * (2.0 * g2 + 2.0) / kp[j];
@@ -365,6 +392,18 @@ __global__ void __launch_bounds__(128) irbc_jacobian_kernel(IrbcDev P, int64_t s
                 const double sMb = SM - sM[0] - sM[1] - sM[2] - sM[3];
                 v0 = -P.beta * (s1b * dP[0] + (s1[0] + s1[1]) * dP[1] + (s1[2] + s1[3]) * dP[2] +
                                 sMb * dPN[0] + (sM[0] + sM[1]) * dPN[1] + (sM[2] + sM[3]) * dPN[2]);
+            }
+            if (P.irr) {
+                // (1 - delta) mu'_j inside the expectation: its slope in k'_i at the nodes
+                double dM[3];
+                for (int v = 0; v < nv; ++v) {
+                    double acc = 0.0;
+                    for (int q = 0; q < nt[v]; ++q)
+                        acc += terms[v][q].w * t.alpha64[(int64_t)terms[v][q].row * mp + N + j];
+                    dM[v] = acc;
+                }
+                const double sumw = nv == 1 ? nq * w * dM[0] : w * ((nq - 4) * dM[0] + 2.0 * dM[1] + 2.0 * dM[2]);
+                v0 += P.beta * (1.0 - P.delta) * sumw;
             }
             J[(int64_t)j * m + i] += v0;
         }
@@ -499,7 +538,7 @@ __global__ void irbc_queries3_kernel(IrbcDev P, int64_t ns, const double *__rest
                                      const double *__restrict__ guess, const double *__restrict__ lo,
                                      const double *__restrict__ span, uint64_t *__restrict__ X,
                                      int32_t *__restrict__ flags, unsigned long long *__restrict__ stats) {
-    const int N = P.N, d = 2 * N, m = N + 1, nq = 2 * (N + 1);
+    const int N = P.N, d = 2 * N, m = P.m, nq = 2 * (N + 1);
     const int64_t Q3 = ns * 3;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long clamps = 0;
@@ -522,7 +561,9 @@ __global__ void irbc_queries3_kernel(IrbcDev P, int64_t ns, const double *__rest
             const uint64_t e = encode_coord(guess[s * m + dim - N], lo[dim], span[dim], bad, clamps);
             clamps *= (unsigned long long)nq;
             for (int t = 0; t < 3; ++t) Xrow[t] = e;
-            if (dim == d - 1 && !isfinite(guess[s * m + N])) bad = true;
+            if (dim == d - 1)
+                for (int o = N; o < m; ++o)
+                    if (!isfinite(guess[s * m + o])) bad = true;
         }
         if (bad)
             for (int t = 0; t < 3; ++t) flags[s * 3 + t] = 1;
@@ -593,7 +634,7 @@ __global__ void __launch_bounds__(128) irbc_delta_kernel(IrbcDev P, int64_t s0, 
                                                          const double *__restrict__ span,
                                                          const double *__restrict__ y3, double *__restrict__ y) {
     using W = typename DeltaT<PREC>::W;
-    const int N = P.N, d = 2 * N, m = N + 1, nq = 2 * (N + 1);
+    const int N = P.N, d = 2 * N, m = P.m, nq = 2 * (N + 1);
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nsc * N) return;
     const int64_t sl = idx / N;
@@ -668,6 +709,7 @@ __global__ void __launch_bounds__(128) irbc_delta_kernel(IrbcDev P, int64_t s0, 
 struct irbc {
     irbc_params_t p;
     int node_mode = DDSG_IRBC_NODES_ALL;
+    int irreversible = 0;   // non-smooth model: policy (k', mu, lambda)
     Tracer tr;   // kinds: 0 queries, 1 eval, 2 residual, 3 jacobian, 4 lu, 5 newton helpers
     std::vector<double> gamma, tau;
     int device = -1;
@@ -694,6 +736,8 @@ int ensure(irbc *M, size_t bytes) {
 IrbcDev dev_params(const irbc *M) {
     IrbcDev P;
     P.N = M->p.N;
+    P.irr = M->irreversible;
+    P.m = M->irreversible ? 2 * M->p.N + 1 : M->p.N + 1;
     P.beta = M->p.beta;
     P.alpha = M->p.alpha;
     P.delta = M->p.delta;
@@ -764,7 +808,7 @@ template <int PREC, int MC>
 cudaError_t launch_delta(const IrbcDev &P, int64_t s0, int64_t nsc, const DevTables &t, int form,
                          const int32_t *aoff, const int32_t *acomp, const double *states, const double *guess,
                          const double *lo, const double *span, const double *y3, double *y, cudaStream_t st) {
-    const int m = P.N + 1;
+    const int m = P.m;
     dim3 grid((unsigned)((nsc * P.N + 127) / 128), (unsigned)((m + MC - 1) / MC));
     irbc_delta_kernel<PREC, MC><<<grid, 128, 0, st>>>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span,
                                                        y3, y);
@@ -772,6 +816,14 @@ cudaError_t launch_delta(const IrbcDev &P, int64_t s0, int64_t nsc, const DevTab
 }
 
 }  // namespace
+
+extern "C" int irbc_set_irreversible(irbc_t *M, int on) {
+    if (!M) return set_error(DDSG_ERR_ARG, "irbc_set_irreversible: NULL model");
+    if (on && 2 * M->p.N + 1 > 165)
+        return set_error(DDSG_ERR_ARG, "irbc_set_irreversible: 2N+1 > 165 unknowns per state (batched LU limit)");
+    M->irreversible = on ? 1 : 0;
+    return DDSG_OK;
+}
 
 extern "C" int irbc_set_node_mode(irbc_t *M, int mode) {
     if (!M) return set_error(DDSG_ERR_ARG, "irbc_set_node_mode: NULL model");
@@ -827,8 +879,10 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
     HandleView v;
     int rc = handle_eval_view(policy, precision, form, &v);
     if (rc) return rc;
-    const int N = M->p.N, d = 2 * N, m = N + 1, nq = 2 * (N + 1);
-    if (v.d != d || v.m != m) return set_error(DDSG_ERR_ARG, "euler_residual: the policy must map 2N states to N+1 outputs");
+    const int N = M->p.N, d = 2 * N, m = M->irreversible ? 2 * N + 1 : N + 1, nq = 2 * (N + 1);
+    if (v.d != d || v.m != m)
+        return set_error(DDSG_ERR_ARG, M->irreversible ? "euler_residual: the policy must map 2N states to 2N+1 outputs (k', mu, lambda)"
+                                                       : "euler_residual: the policy must map 2N states to N+1 outputs");
     if ((rc = bind_device(M))) return rc;
     std::vector<int32_t> koff, kids;
     int32_t *koff_dev = nullptr, *kids_dev = nullptr;
@@ -964,7 +1018,7 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
         return set_error(DDSG_ERR_ARG, "irbc_newton: bad argument");
     if (ns == 0) return DDSG_OK;
     if ((ns > 0) && (!states_dev || !sol_dev)) return set_error(DDSG_ERR_ARG, "irbc_newton: NULL states or solution");
-    const int N = M->p.N, n = N + 1;
+    const int N = M->p.N, n = M->irreversible ? 2 * N + 1 : N + 1;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     // Newton buffers (separate from the residual workspace): r, J, dz, zt, rt, norms, steps, flags
     double *r = nullptr, *J = nullptr, *dz = nullptr, *zt = nullptr, *rt = nullptr;

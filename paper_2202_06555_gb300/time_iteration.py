@@ -179,11 +179,11 @@ def euler_errors(model, policy: HDMR, states: np.ndarray, precision=F64, form=FO
     both today's choice and next period's): per state max over countries of
     |beta E / lhs - 1| and |resource| / output."""
     import torch
-    n, N = states.shape[0], model.N
+    n, m = states.shape[0], policy.m
     sd = torch.from_numpy(np.ascontiguousarray(states, np.float64)).cuda()
-    g = torch.empty((n, N + 1), dtype=torch.float64, device="cuda")
+    g = torch.empty((n, m), dtype=torch.float64, device="cuda")
     policy.eval(sd, g, precision, form)
-    r = torch.empty((n, N + 1), dtype=torch.float64, device="cuda")
+    r = torch.empty((n, m), dtype=torch.float64, device="cuda")
     e = torch.empty((n, 2), dtype=torch.float64, device="cuda")
     model.set_node_mode(node_mode)
     model.residual(policy, sd, g, r, None, e, precision, form)
