@@ -54,6 +54,10 @@ WORKLOADS = {
     "ti10": dict(d=20, m=11, N=10, order=2, level=6, eps_gamma=1e-4, eps_eta=1e-5, eps_rho=1e-6,
                  ti_steps=4, test_states=2000, wid=synth.W_IRBC20 + 10, precision="f64",
                  form="slicefree"),
+    # the same on the non-smooth model (irreversible investment): N = 6, policy (k', mu, lambda)
+    "ti6irr": dict(d=12, m=13, N=6, order=2, level=6, eps_gamma=1e-4, eps_eta=1e-5, eps_rho=1e-6,
+                   ti_steps=4, test_states=2000, wid=synth.W_IRBC20 + 11, precision="f64",
+                   form="slicefree", irreversible=True),
 }
 
 FP32_LANES_PER_SM = 128
@@ -429,8 +433,11 @@ def run_time_iteration(args, w):
     t1 = G.irbc_table1(N)
     lam = synth.irbc_steady_lambda(t1["gamma"], t1["tau"], t1["A"], t1["delta"])
     M = G.IRBC(**t1)
+    irr = bool(w.get("irreversible"))
+    if irr:
+        M.set_irreversible(True)
     lo, hi = np.full(d, 0.8), np.full(d, 1.2)
-    # initial policy: k' = k, lambda = lambda* (exact on level-2 single-dimension grids)
+    # initial policy: k' = k, (mu = 0), lambda = lambda* (exact on level-2 single-dimension grids)
     h0 = G.HDMR(d, m, 2, lo=lo, hi=hi)
     comps = [()] + [(i,) for i in range(d)]
     for u in comps:
@@ -438,7 +445,7 @@ def run_time_iteration(args, w):
     vals = []
     for c, u in enumerate(comps):
         _, _, xs = h0.component_points(c)
-        y = np.tile(np.concatenate([np.ones(N), [lam]]), (xs.shape[0], 1))
+        y = np.tile(np.concatenate([np.ones(N)] + ([np.zeros(N)] if irr else []) + [[lam]]), (xs.shape[0], 1))
         for a, dim in enumerate(u):
             if dim >= N:
                 y[:, dim - N] = xs[:, a]
@@ -452,10 +459,12 @@ def run_time_iteration(args, w):
                                w["eps_rho"], lo, hi, T, precision=prec, node_mode=G.NODES_DELTA)
     torch.cuda.synchronize()
     total = time.perf_counter() - t0
-    out = {"metric": "adaptive DDSG time-iteration step time (s) and Euler error, IRBC N=10",
+    out = {"metric": "adaptive DDSG time-iteration step time (s) and Euler error, %s IRBC N=%d"
+                     % ("non-smooth" if irr else "smooth", N),
            "value": total / len(hist), "unit": "s/step", "higher_is_better": False, "n_gpus": 1,
            "data": "synthetic", "dtype": "f64" if prec == G.F64 else "f32",
-           "config": {"workload": "ti10_ddsg_time_iteration", "N": N, "d": d, "m": m, "order": w["order"],
+           "config": {"workload": f"{args.workload}_ddsg_time_iteration", "N": N, "d": d, "m": m,
+                      "order": w["order"], "irreversible": irr,
                       "max_level": w["level"], "eps_gamma": w["eps_gamma"], "eps_eta": w["eps_eta"],
                       "eps_rho": w["eps_rho"], "steps": len(hist), "test_states": w["test_states"],
                       "candidates": "all k-subsets", "node_mode": "shortcut"},
@@ -607,7 +616,7 @@ def main():
         return run_irbc(args, w)
     if args.workload == "warmstart20":
         return run_warmstart(args, w)
-    if args.workload == "ti10":
+    if args.workload in ("ti10", "ti6irr"):
         return run_time_iteration(args, w)
     if args.impl == "reference":
         return run_reference(args, w)

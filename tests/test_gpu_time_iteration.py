@@ -102,3 +102,46 @@ def test_time_iteration_matches_oracle(G, mode, all_pairs):
     for a, b in zip(hist_g, hist_o):
         assert abs(a["euler_error_mean"] - b["euler_error_mean"]) <= 1e-8
     assert hist_g[1]["euler_error_mean"] < hist_g[0]["euler_error_mean"]
+
+
+def test_irreversible_time_iteration_matches_oracle(G):
+    """Non-smooth model (policy (k', mu, lambda)): two adaptive time-iteration
+    steps over the (a_j, k_j) pairs, GPU vs oracle."""
+    from paper_2202_06555_gb300.time_iteration import time_iteration
+    N = 2
+    d, m = 2 * N, 2 * N + 1
+    I = O.IRBCOracle(N, irreversible=True)
+    lam = I.steady_lambda()
+    M = G.IRBC(N, I.p["beta"], I.p["alpha"], I.p["delta"], I.p["sigma"], I.p["rho"], I.p["phi"],
+               I.A, I.gamma, I.tau)
+    M.set_irreversible(True)
+    lo, hi = np.full(d, 0.8), np.full(d, 1.2)
+    comps = [()] + [(i,) for i in range(d)]
+
+    def init_vals(u, xs):
+        y = np.tile(np.concatenate([np.ones(N), np.zeros(N), [lam]]), (xs.shape[0], 1))
+        for a, dim in enumerate(u):
+            if dim >= N:
+                y[:, dim - N] = xs[:, a]
+        return y
+
+    E0 = O.OracleDDSG(d, m, lo=lo, hi=hi)
+    h0 = G.HDMR(d, m, 2, lo=lo, hi=hi)
+    for u in comps:
+        E0.add_regular(u, 2)
+        h0.add_regular(list(u), 2)
+    E0.fill_values(lambda dims, X: init_vals(dims, np.atleast_2d(X)))
+    E0.hierarchize()
+    h0.hierarchize(torch.from_numpy(np.concatenate(
+        [init_vals(u, h0.component_points(c)[2]) for c, u in enumerate(comps)])).cuda())
+    pairs = lambda k: [(i,) for i in range(d)] if k == 1 else [(j, N + j) for j in range(N)]
+    T = synth.irbc_states(synth.BASE_SEED + 602, 64, N)
+    Eo, hist_o = oracle_time_iteration(I, E0, 2, 2, 3, -1.0, -1.0, 0.0, lo, hi, T, candidates=pairs)
+    hg, hist_g = time_iteration(M, h0, 2, 2, 3, -1.0, -1.0, 0.0, lo, hi, T, candidates=pairs, precision=G.F64)
+    assert all(h["newton_failed"] == 0 for h in hist_g)
+    y = torch.empty((T.shape[0], m), dtype=torch.float64, device="cuda")
+    hg.eval(torch.from_numpy(T).cuda(), y, G.F64, G.FORM_SLICEFREE)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(y.cpu().numpy() - Eo.eval(T, form=1)["y"])) <= 1e-8
+    for a, b in zip(hist_g, hist_o):
+        assert abs(a["euler_error_mean"] - b["euler_error_mean"]) <= 1e-8
