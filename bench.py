@@ -733,6 +733,29 @@ def main():
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_frac = hbm_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak
 
+    # -- register-delivery floor of the gather (F32C on the staged kernels): every
+    # level tuple a warp of 32 queries visits moves one padded surplus row per lane
+    # (mp floats = mp/4 16-byte loads at 4 wavefronts each = mp wavefronts); the L1
+    # returns one 128-byte wavefront per clock per SM
+    l1 = None
+    if prec == G.F32C:
+        tuples = 0
+        for c in range(ncomp):
+            dims, npts, _ = h.component_info(c)
+            if len(dims) == 0:
+                tuples += 1   # the constant component's single point
+                continue
+            lv, _, _ = h.component_points(c)
+            inner = lv[np.all(lv >= 2, axis=1)] if w["form"] == "slicefree" else lv
+            tuples += len({tuple(r) for r in inner.tolist()})
+        mp = (w["m"] + 3) // 4 * 4
+        wavefronts = (n / 32.0) * tuples * mp
+        floor_ms = wavefronts / (N_SM * SM_MAX_MHZ * 1e6) * 1e3
+        l1 = {"bound": "shared-memory delivery to registers (128 B per clock per SM)",
+              "floor_ms": floor_ms, "kernel_ms": eval_avg_ms, "frac": floor_ms / eval_avg_ms,
+              "tuples_per_query": tuples, "wavefronts_per_32_query_tuples": mp,
+              "note": "lower bound for any kernel that gives each query thread its own copy of each hit row"}
+
     # -- end to end: host buffers through the C ABI ---------------------------
     xh = torch.from_numpy(X).pin_memory()
     yh = torch.empty((n, w["m"]), dtype=torch.float64).pin_memory()
@@ -773,6 +796,7 @@ def main():
                         "flops_per_launch": flops_per_launch},
            "hbm_roofline": {"bytes_per_step": hbm_bytes, "frac": hbm_frac, "peak_gbs": hbm_peak,
                             "note": "compulsory bytes / step time / measured copy bandwidth"},
+           "l1_roofline": l1,
            "kernels_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
            "clocks": clk.summary(),
            "e2e": {"value": world * n * w["m"] / e2e_s, "unit": "evals/s",
