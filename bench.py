@@ -408,7 +408,7 @@ def run_irbc(args, w):
                       "states": ns, "nodes": nq, "evals_per_sweep": ns * nq,
                       "policy": "empty + 2N singles + N (a_j,k_j) pairs, regular level 4",
                       "precision": w["precision"], "form": w["form"],
-                      "schedule": {"kernel": ["tile", "per-tuple", "tma-staged tile", "tma-staged, 2 warp groups"][tuned[0]],
+                      "schedule": {"kernel": ["tile", "per-tuple", "tma-staged tile", "tma-staged, 2 warp groups", "tma-staged, 3 warp groups"][tuned[0]],
                                    "outputs_per_pass": tuned[1]}},
            "kernels_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
            "gpu_launches": sum(v[1] for v in prof.values()),
@@ -783,7 +783,7 @@ def main():
                       "eps_gamma": w["eps"], "max_level": w["level"], "queries_per_gpu": n,
                       "precision": w["precision"], "form": w["form"],
                       "active_points_per_query": active_total / n,
-                      "schedule": {"kernel": ["tile", "per-tuple", "tma-staged tile", "tma-staged, 2 warp groups"][tuned[0]], "outputs_per_pass": tuned[1],
+                      "schedule": {"kernel": ["tile", "per-tuple", "tma-staged tile", "tma-staged, 2 warp groups", "tma-staged, 3 warp groups"][tuned[0]], "outputs_per_pass": tuned[1],
                                    "autotune_subset": nt},
                       "l2": "inputs larger than L2 (x %.2f GB, surpluses %.2f GB); no flush"
                             % (n * w["d"] * 8 / 1e9, npts * w["m"] * (4 if prec == G.F32C else 8) / 1e9),

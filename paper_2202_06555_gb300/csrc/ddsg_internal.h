@@ -189,7 +189,7 @@ struct EvalConfig {
     int mc = 0;               // outputs per thread and pass (0 = heuristic)
 };
 
-constexpr int NKERNELS = 4;
+constexpr int NKERNELS = 5;
 constexpr int64_t TMA_STAGE_MAX = 84 * 1024;  // largest per-component surplus block staged by TMA
 constexpr int TMA_TUP_MAX = 128;              // most level tuples of one component the staged kernel holds
 

@@ -532,7 +532,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // block; each query's output chunk is split over GR threads (one per group).
 template <int GR>
 struct TmaShape {
-    static constexpr int QB = GR == 1 ? 256 : 192;   // queries per block
+    static constexpr int QB = GR == 1 ? 256 : (GR == 2 ? 192 : 160);   // queries per block
     static constexpr int NT = QB * GR;               // threads per block
     static constexpr int QW = QB / 32;               // query warps per group
 };
@@ -555,30 +555,36 @@ inline int tma_probe_bytes(int precision, int qb) {
 // Staging buffers (3 when they fit, else 2) and probe batch (tuples probed per
 // pass, at most the largest tuple count and TMA_PB_MAX) that fit in shared
 // memory beside the fixed part; pb = 0 when not even two tuples fit.
-inline void tma_layout(const DevTables &t, int fixed, int buf, int per, int &nbuf, int &pb) {
-    const int want = t.max_tuples < 2 ? 2 : (t.max_tuples < TMA_PB_MAX ? t.max_tuples : TMA_PB_MAX);
+inline void tma_layout(const DevTables &t, int fixed, int buf, int per, int &nbuf, int &pb, int min_pb = 2) {
+    int want = t.max_tuples < 2 ? 2 : (t.max_tuples < TMA_PB_MAX ? t.max_tuples : TMA_PB_MAX);
+    if (want < min_pb) want = min_pb;
     for (nbuf = TMA_NBUF_MAX; nbuf >= 2; --nbuf) {
         const int64_t left = (int64_t)kSmemLimit - fixed - (int64_t)nbuf * buf;
         pb = left > 0 ? (int)(left / per) : 0;
         if (pb > want) pb = want;
         if (pb >= (want < 8 ? want : 8) || nbuf == 2) break;
     }
-    if (pb < 2) pb = 0;
+    if (pb < min_pb) pb = 0;
 }
 
-// queries per block of evaluation kernel `kernel` (2, 3: the TMA-staged kernel)
-static int tma_qb(int kernel) { return kernel == 3 ? TmaShape<2>::QB : TmaShape<1>::QB; }
+// queries per block of evaluation kernel `kernel` (2, 3, 4: the TMA-staged kernel
+// with 1, 2 or 3 warp groups)
+static int tma_qb(int kernel) {
+    return kernel == 4 ? TmaShape<3>::QB : (kernel == 3 ? TmaShape<2>::QB : TmaShape<1>::QB);
+}
 
 bool eval_kernel_eligible(const DevTables &t, int kernel, int precision, int form) {
     if (kernel == 0 || kernel == 1) return true;
-    if (kernel != 2 && kernel != 3) return false;
+    if (kernel < 2 || kernel > 4) return false;
     if (!t.tile_ok) return false;   // the staged kernel handles only k <= 2, levels <= LT
     if (t.max_tuples > TMA_TUP_MAX) return false;
     const int qb = tma_qb(kernel);
     const int64_t bytes = t.stage_bytes[form][precision];
     if (bytes > TMA_STAGE_MAX) return false;
     int nbuf = 0, pb = 0;
-    tma_layout(t, tma_fixed_smem(precision, qb), tma_buf_bytes(bytes), tma_probe_bytes(precision, qb), nbuf, pb);
+    // the groups' point hashes are combined through the probe area: GR tuples at least
+    tma_layout(t, tma_fixed_smem(precision, qb), tma_buf_bytes(bytes), tma_probe_bytes(precision, qb), nbuf, pb,
+               kernel - 1 > 2 ? kernel - 1 : 2);
     return pb > 0;
 }
 
@@ -971,15 +977,17 @@ __global__ void __launch_bounds__(TmaShape<GR>::NT, 1) eval_tma_kernel(const Eva
     if (HC && GR > 1) {
         // the point hash and count of a query are split over its groups: combine
         uint64_t *xh = reinterpret_cast<uint64_t *>(s_prow);
-        int32_t *xc = reinterpret_cast<int32_t *>(xh + QB);
-        if (grp == 1) {
-            xh[qi] = h;
-            xc[qi] = cnt;
+        int32_t *xc = reinterpret_cast<int32_t *>(xh + (GR - 1) * QB);
+        if (grp > 0) {
+            xh[(grp - 1) * QB + qi] = h;
+            xc[(grp - 1) * QB + qi] = cnt;
         }
         __syncthreads();
         if (grp == 0) {
-            h ^= xh[qi];
-            cnt += xc[qi];
+            for (int g = 0; g < GR - 1; ++g) {
+                h ^= xh[g * QB + qi];
+                cnt += xc[g * QB + qi];
+            }
         }
     }
     if (!valid) return;
@@ -1000,7 +1008,7 @@ static cudaError_t launch_tma(const EvalParams &p, bool hc, cudaStream_t st) {
     const int buf = tma_buf_bytes(stage);
     int nbuf = 0, pb = 0;
     const int fixed = tma_fixed_smem(PREC, QB);
-    tma_layout(p.t, fixed, buf, tma_probe_bytes(PREC, QB), nbuf, pb);
+    tma_layout(p.t, fixed, buf, tma_probe_bytes(PREC, QB), nbuf, pb, GR > 2 ? GR : 2);
     const int smem = fixed + nbuf * buf + pb * tma_probe_bytes(PREC, QB);
     dim3 grid((unsigned)((p.n + QB - 1) / QB), (unsigned)((p.m + GR * MC - 1) / (GR * MC)));
     if (hc) {
@@ -1017,15 +1025,25 @@ static cudaError_t launch_tma(const EvalParams &p, bool hc, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// output chunks the two-group kernel is compiled for (per group)
+// output chunks the two- and three-group kernels are compiled for (per group)
 template <int PREC, int MC>
 constexpr bool kGr2Chunk = PREC == DDSG_F64 ? (MC == 4 || MC == 8 || MC == 16) : (MC == 8 || MC == 16 || MC == 28);
+template <int PREC, int MC>
+constexpr bool kGr3Chunk = PREC == DDSG_F64 ? (MC == 4 || MC == 8) : (MC == 12 || MC == 20);
 
 template <int PREC, int MC>
 static cudaError_t launch_mc(const EvalParams &p, int kernel, bool hc, cudaStream_t st) {
+    if constexpr (MC == 20) {   // compiled for the three-group kernel only
+        if (kernel == 4) return launch_tma<PREC, MC, 3>(p, hc, st);
+        return cudaErrorInvalidValue;
+    } else {
     if (kernel == 2) return launch_tma<PREC, MC, 1>(p, hc, st);
     if (kernel == 3) {
         if constexpr (kGr2Chunk<PREC, MC>) return launch_tma<PREC, MC, 2>(p, hc, st);
+        else return cudaErrorInvalidValue;
+    }
+    if (kernel == 4) {
+        if constexpr (kGr3Chunk<PREC, MC>) return launch_tma<PREC, MC, 3>(p, hc, st);
         else return cudaErrorInvalidValue;
     }
     dim3 grid((unsigned)((p.n + TQ - 1) / TQ), (unsigned)((p.m + MC - 1) / MC));
@@ -1037,20 +1055,24 @@ static cudaError_t launch_mc(const EvalParams &p, int kernel, bool hc, cudaStrea
         else eval_lq_kernel<PREC, MC, false><<<grid, TQ, 0, st>>>(p);
     }
     return cudaGetLastError();
+    }
 }
 
 // compiled output-chunk sizes (multiples of the vector width)
 static const int MC_F64[] = {2, 4, 6, 8, 12, 16};
 static const int MC_F32[] = {4, 8, 12, 16, 28, 52};
 
-// the two-group TMA kernel (3): chunks per group
+// the two- and three-group TMA kernels (3, 4): chunks per group
 static const int MC_F64_GR2[] = {4, 8, 16};
 static const int MC_F32_GR2[] = {8, 16, 28};
+static const int MC_F64_GR3[] = {4, 8};
+static const int MC_F32_GR3[] = {12, 20};
 
 int eval_mc_candidates(int precision, int kernel, int *out, int cap) {
-    const int *src = kernel == 3 ? (precision == DDSG_F64 ? MC_F64_GR2 : MC_F32_GR2)
-                                 : (precision == DDSG_F64 ? MC_F64 : MC_F32);
-    const int n = kernel == 3 ? 3 : 6;
+    const bool f64 = precision == DDSG_F64;
+    const int *src = kernel == 4 ? (f64 ? MC_F64_GR3 : MC_F32_GR3)
+                     : kernel == 3 ? (f64 ? MC_F64_GR2 : MC_F32_GR2) : (f64 ? MC_F64 : MC_F32);
+    const int n = kernel == 4 ? 2 : (kernel == 3 ? 3 : 6);
     for (int i = 0; i < n && i < cap; ++i) out[i] = src[i];
     return n < cap ? n : cap;
 }
@@ -1072,6 +1094,7 @@ static cudaError_t launch_prec(const EvalParams &p, int kernel, int mc, bool hc,
             case 8: return launch_mc<PREC, 8>(p, kernel, hc, st);
             case 12: return launch_mc<PREC, 12>(p, kernel, hc, st);
             case 16: return launch_mc<PREC, 16>(p, kernel, hc, st);
+            case 20: return launch_mc<PREC, 20>(p, kernel, hc, st);
             case 28: return launch_mc<PREC, 28>(p, kernel, hc, st);
             default: return launch_mc<PREC, 52>(p, kernel, hc, st);
         }

@@ -219,9 +219,11 @@ def test_every_kernel_config_matches_oracle(G):
     X = synth.uniform_queries(56, 700, d)
     mcs = {0: [2, 4, 6, 8, 12, 16], 1: [4, 8, 12, 16, 28, 52]}
     mcs3 = {0: [4, 8, 16], 1: [8, 16, 28]}   # the two-group TMA kernel: chunk per group
+    mcs4 = {0: [4, 8], 1: [12, 20]}          # the three-group TMA kernel
+    pick = lambda kernel: mcs4 if kernel == 4 else (mcs3 if kernel == 3 else mcs)
     for prec in (0, 1):
-        for kernel in (0, 1, 2, 3):
-            for mc in (mcs3 if kernel == 3 else mcs)[prec]:
+        for kernel in (0, 1, 2, 3, 4):
+            for mc in pick(kernel)[prec]:
                 h.set_eval_config(prec, 1, kernel, mc)
                 h.set_eval_config(prec, 0, kernel, mc)
                 check_eval(h, ref, X, precs=(prec,))
@@ -229,7 +231,7 @@ def test_every_kernel_config_matches_oracle(G):
     yd = torch.empty((X.shape[0], m), dtype=torch.float64, device="cuda")
     for prec in (0, 1):
         kernel, mc, ms = h.autotune(xd, yd, prec, 1)
-        assert kernel in (0, 1, 2, 3) and mc in (mcs3 if kernel == 3 else mcs)[prec] and ms > 0
+        assert kernel in (0, 1, 2, 3, 4) and mc in pick(kernel)[prec] and ms > 0
         check_eval(h, ref, X, forms=(1,), precs=(prec,))
     with pytest.raises(G.DDSGError, match="not compiled"):
         h.set_eval_config(0, 0, 0, 5)
@@ -249,4 +251,6 @@ def test_staged_kernel_refuses_tables_it_cannot_hold(G):
         h.set_eval_config(0, 0, 2, 2)
     with pytest.raises(G.DDSGError, match="cannot run"):
         h.set_eval_config(0, 0, 3, 4)
+    with pytest.raises(G.DDSGError, match="cannot run"):
+        h.set_eval_config(0, 0, 4, 4)
     check_eval(h, ref, synth.uniform_queries(33, 500, d))
