@@ -54,6 +54,11 @@ WORKLOADS = {
     "ti10": dict(d=20, m=11, N=10, order=2, level=6, eps_gamma=1e-4, eps_eta=1e-5, eps_rho=1e-6,
                  ti_steps=4, test_states=2000, wid=synth.W_IRBC20 + 10, precision="f64",
                  form="slicefree"),
+    # Table 2's smooth d = 100 setting: N = 50, order 1, regular level-4 grids (801 points),
+    # iterated until the policy stops moving
+    "ti50": dict(d=100, m=51, N=50, order=1, level=4, eps_gamma=-1.0, eps_eta=-1.0, eps_rho=0.0,
+                 ti_steps=400, tol_change=1e-7, test_states=2000, wid=synth.W_D100 + 50, precision="f64",
+                 form="slicefree"),
     # the same on the non-smooth model (irreversible investment): N = 6, policy (k', mu, lambda)
     "ti6irr": dict(d=12, m=13, N=6, order=2, level=6, eps_gamma=1e-4, eps_eta=1e-5, eps_rho=1e-6,
                    ti_steps=4, test_states=2000, wid=synth.W_IRBC20 + 11, precision="f64",
@@ -210,6 +215,21 @@ def oracle_rate(E, w, X, budget_s):
             break
         n = max(1, min(X.shape[0] - used, int(n * 2 if dt < 0.2 * budget_s else n)))
     return used * w["m"] / t_used, used
+
+
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name, or implementer/part on Arm)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return None
+    for key in ("model name", "Model"):
+        for line in info:
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    impl = next((l.split(":", 1)[1].strip() for l in info if l.startswith("CPU implementer")), None)
+    part = next((l.split(":", 1)[1].strip() for l in info if l.startswith("CPU part")), None)
+    return f"implementer {impl}, part {part}" if impl else None
 
 
 def oracle_rate_threads(E, w, X, n, threads):
@@ -456,7 +476,8 @@ def run_time_iteration(args, w):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     pol, hist = time_iteration(M, h0, w["ti_steps"], w["order"], w["level"], w["eps_gamma"], w["eps_eta"],
-                               w["eps_rho"], lo, hi, T, precision=prec, node_mode=G.NODES_DELTA)
+                               w["eps_rho"], lo, hi, T, precision=prec, node_mode=G.NODES_DELTA,
+                               tol_change=w.get("tol_change", 0.0))
     torch.cuda.synchronize()
     total = time.perf_counter() - t0
     out = {"metric": "adaptive DDSG time-iteration step time (s) and Euler error, %s IRBC N=%d"
@@ -468,7 +489,16 @@ def run_time_iteration(args, w):
                       "max_level": w["level"], "eps_gamma": w["eps_gamma"], "eps_eta": w["eps_eta"],
                       "eps_rho": w["eps_rho"], "steps": len(hist), "test_states": w["test_states"],
                       "candidates": "all k-subsets", "node_mode": "shortcut"},
-           "steps": hist}
+           "final": {"steps": len(hist), "points": hist[-1]["points"],
+                     "euler_error_log10_mean": float(np.log10(hist[-1]["euler_error_mean"])),
+                     "euler_error_log10_max": float(np.log10(hist[-1]["euler_error_max"])),
+                     "policy_change_max": hist[-1]["policy_change_max"], "seconds": total},
+           "steps": hist if len(hist) <= 10 else hist[:3] + hist[-3:]}
+    if args.workload == "ti50":
+        # Table 2 of the paper (smooth IRBC, d = 100): context only, other hardware
+        out["paper_context"] = {"grid_points": 810, "euler_error_log10_avg_max": [-3.35, -2.21],
+                                "hours_per_iteration": 0.5, "nodes": 100,
+                                "hardware": "Cray XC50, 12-core CPU nodes, IPOPT per grid point"}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -616,7 +646,7 @@ def main():
         return run_irbc(args, w)
     if args.workload == "warmstart20":
         return run_warmstart(args, w)
-    if args.workload in ("ti10", "ti6irr"):
+    if args.workload in ("ti10", "ti6irr", "ti50"):
         return run_time_iteration(args, w)
     if args.impl == "reference":
         return run_reference(args, w)
@@ -856,6 +886,7 @@ def main():
                                   "per_output_max": [float(v) for v in relo.max(0)],
                                   "scale": "max(|y|, sum of |terms|)"}
         out["cpu_baseline"] = {"value": rate_par, "unit": "evals/s", "cores": threads, "kind": "oracle",
+                               "cpu": cpu_model(),
                                "sample": f"first {n_par} of the {n} queries over {threads} host threads "
                                          f"(~10 s of CPU work)",
                                "single_thread": {"value": rate, "sample": f"first {used} queries, "

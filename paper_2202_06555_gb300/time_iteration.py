@@ -194,9 +194,10 @@ def euler_errors(model, policy: HDMR, states: np.ndarray, precision=F64, form=FO
 def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps_gamma: float,
                    eps_eta: float, eps_rho: float, lo, hi, test_states: np.ndarray, tol_euler=0.0,
                    candidates=None, precision=F64, form=FORM_SLICEFREE, newton_tol=1e-10, max_it=30,
-                   node_mode=NODES_DELTA):
+                   node_mode=NODES_DELTA, tol_change=0.0):
     """Alg. 1: p <- build_ddsg(x -> solve{FOC(. | x, p)}) until the mean Euler
-    error at test_states is below tol_euler or `steps` steps are done.
+    error at test_states is below tol_euler, the largest policy change at the
+    test states is below tol_change, or `steps` steps are done.
     Returns the last policy and one record per step."""
     import torch
     d, m = policy0.d, policy0.m
@@ -222,6 +223,6 @@ def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps
         if policy is not policy0:
             policy.close()
         policy = new
-        if history[-1]["euler_error_mean"] < tol_euler:
+        if history[-1]["euler_error_mean"] < tol_euler or history[-1]["policy_change_max"] < tol_change:
             break
     return policy, history
