@@ -150,6 +150,22 @@ int hdmr_refine(hdmr_t *h, double eps_gamma, int max_level, int strict, int64_t 
                 ddsg_stream_t stream);
 
 /*
+ * Checkpoint / resume (no paper counterpart). hdmr_save writes the expansion
+ * (domain, anchor, every component's points, the FP64 surpluses) to one
+ * versioned binary file with a checksum; it needs a hierarchized handle and
+ * synchronizes the device. hdmr_load recreates a hierarchized handle on the
+ * current device from such a file (no values or hierarchization needed);
+ * a missing, foreign, truncated or corrupt file is DDSG_ERR_ARG. Results of
+ * hdmr_eval on the loaded handle equal the saved one's bit for bit.
+ * hdmr_shape returns d, m, order and the anchor / lo / hi host arrays (d each;
+ * any output may be NULL).
+ */
+int hdmr_save(const hdmr_t *h, const char *path);
+int hdmr_load(const char *path, hdmr_t **out);
+int hdmr_shape(const hdmr_t *h, int32_t *d, int32_t *m, int32_t *order, double *anchor_host,
+               double *lo_host, double *hi_host);
+
+/*
  * hdmr_quadrature -- the integral over [0,1]^k of every component interpolant
  * (eq. 3.7; canonical coordinates): q_dev[c*m + o] = sum over the points of
  * component c of alpha_p[o] * prod_j (1, 1/4 or 2^-(l-1) for level 1, 2, l >= 3).

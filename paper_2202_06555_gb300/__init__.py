@@ -57,6 +57,9 @@ SIGNATURES = {
     "hdmr_eval_noalloc": (_int, [_p, _i64, _p, _p, _int, _int, _p]),
     "hdmr_eval_graph": (_int, [_p, _i64, _p, _p, _int, _int, _p]),
     "hdmr_quadrature": (_int, [_p, _p, _p]),
+    "hdmr_save": (_int, [_p, C.c_char_p]),
+    "hdmr_load": (_int, [C.c_char_p, _p]),
+    "hdmr_shape": (_int, [_p, _p, _p, _p, _p, _p, _p]),
     "hdmr_eval_noalloc_capacity": (_i64, [_int]),
     "irbc_create": (_int, [_p, _p, _p, C.POINTER(_p)]),
     "irbc_destroy": (_int, [_p]),
@@ -260,6 +263,26 @@ class HDMR:
         n = x_dev.shape[0]
         _check(load().hdmr_eval_graph(self._h, n, _dev_ptr(x_dev), _dev_ptr(y_dev), int(precision),
                                       int(form), _stream_ptr(stream)), "hdmr_eval_graph")
+
+    def save(self, path: str):
+        """Checkpoint the hierarchized expansion to one file (hdmr_save)."""
+        _check(load().hdmr_save(self._h, os.fsencode(path)), "hdmr_save")
+
+    @classmethod
+    def load(cls, path: str) -> "HDMR":
+        """A hierarchized handle recreated from an hdmr_save file on the current device."""
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.hdmr_load(os.fsencode(path), C.byref(h)), "hdmr_load")
+        self = cls.__new__(cls)
+        self._h = h
+        d, m, order = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib.hdmr_shape(h, C.byref(d), C.byref(m), C.byref(order), None, None, None), "hdmr_shape")
+        self.d, self.m, self.order = d.value, m.value, order.value
+        self.anchor, self.lo, self.hi = np.zeros(self.d), np.zeros(self.d), np.zeros(self.d)
+        _check(lib.hdmr_shape(h, None, None, None, _np_ptr(self.anchor), _np_ptr(self.lo), _np_ptr(self.hi)),
+               "hdmr_shape")
+        return self
 
     def quadrature(self, stream=None):
         """Integral of every component interpolant over its unit cube (eq. 3.7):

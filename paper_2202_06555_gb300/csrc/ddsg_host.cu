@@ -664,6 +664,207 @@ extern "C" int hdmr_hierarchize(hdmr_t *h, const double *values_dev, ddsg_stream
     return DDSG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// checkpoint / resume: one binary file per expansion
+//   "DDSGHDMR", u32 version (1), u32 0, i32 d, m, order, ncomp, i64 P,
+//   f64 anchor[d], lo[d], hi[d],
+//   per component: i32 k, i32 dims[k], i64 npts, u8 levels[npts*k], u32 indices[npts*k],
+//   f64 surpluses[P*m] (points in component / table order),
+//   u64 FNV-1a of every byte after the 16-byte header.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr char kMagic[8] = {'D', 'D', 'S', 'G', 'H', 'D', 'M', 'R'};
+constexpr uint32_t kFileVersion = 1;
+
+uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t hsh = 0xcbf29ce484222325ull) {
+    for (size_t i = 0; i < n; ++i) {
+        hsh ^= p[i];
+        hsh *= 0x100000001b3ull;
+    }
+    return hsh;
+}
+
+struct Writer {
+    std::vector<unsigned char> buf;
+    template <typename T>
+    void put(const T *v, size_t n) {
+        const unsigned char *b = reinterpret_cast<const unsigned char *>(v);
+        buf.insert(buf.end(), b, b + sizeof(T) * n);
+    }
+    template <typename T>
+    void put1(T v) { put(&v, 1); }
+};
+
+struct Reader {
+    const unsigned char *p, *end;
+    bool ok = true;
+    template <typename T>
+    bool get(T *v, size_t n) {
+        const size_t b = sizeof(T) * n;
+        if (!ok || (size_t)(end - p) < b) return ok = false;
+        memcpy(v, p, b);
+        p += b;
+        return true;
+    }
+};
+
+}  // namespace
+
+extern "C" int hdmr_save(const hdmr_t *h, const char *path) {
+    if (!h || !path) return fail(DDSG_ERR_ARG, "hdmr_save: NULL argument");
+    if (!h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_save: hierarchize first");
+    std::vector<double> alpha((size_t)h->P * h->m);
+    int rc = hdmr_get_surpluses(h, alpha.data(), nullptr);
+    if (rc) return rc;
+    Writer w;
+    w.put(kMagic, 8);
+    w.put1<uint32_t>(kFileVersion);
+    w.put1<uint32_t>(0);
+    const size_t body = w.buf.size();
+    w.put1<int32_t>(h->d);
+    w.put1<int32_t>(h->m);
+    w.put1<int32_t>(h->order);
+    w.put1<int32_t>((int32_t)h->comps.size());
+    w.put1<int64_t>(h->P);
+    w.put(h->anchor.data(), h->d);
+    w.put(h->lo.data(), h->d);
+    w.put(h->hi.data(), h->d);
+    for (const Comp &c : h->comps) {
+        w.put1<int32_t>(c.k);
+        w.put(c.dims, c.k);
+        w.put1<int64_t>(c.npts());
+        if (c.k) {
+            w.put(c.lv.data(), c.lv.size());
+            w.put(c.ix.data(), c.ix.size());
+        }
+    }
+    w.put(alpha.data(), alpha.size());
+    w.put1<uint64_t>(fnv1a(w.buf.data() + body, w.buf.size() - body));
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(DDSG_ERR_ARG, "hdmr_save: cannot open %s", path);
+    const size_t wr = fwrite(w.buf.data(), 1, w.buf.size(), f);
+    const int cl = fclose(f);
+    if (wr != w.buf.size() || cl != 0) return fail(DDSG_ERR_ARG, "hdmr_save: write to %s failed", path);
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_load(const char *path, hdmr_t **out) {
+    if (!path || !out) return fail(DDSG_ERR_ARG, "hdmr_load: NULL argument");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(DDSG_ERR_ARG, "hdmr_load: cannot open %s", path);
+    std::vector<unsigned char> buf;
+    unsigned char chunk[1 << 16];
+    size_t got;
+    while ((got = fread(chunk, 1, sizeof chunk, f)) > 0) buf.insert(buf.end(), chunk, chunk + got);
+    fclose(f);
+    if (buf.size() < 16 + 8 || memcmp(buf.data(), kMagic, 8) != 0)
+        return fail(DDSG_ERR_ARG, "hdmr_load: %s is not an expansion file", path);
+    uint32_t version = 0;
+    memcpy(&version, buf.data() + 8, 4);
+    if (version != kFileVersion) return fail(DDSG_ERR_ARG, "hdmr_load: unsupported file version %u", version);
+    uint64_t sum = 0;
+    memcpy(&sum, buf.data() + buf.size() - 8, 8);
+    if (fnv1a(buf.data() + 16, buf.size() - 16 - 8) != sum)
+        return fail(DDSG_ERR_ARG, "hdmr_load: checksum mismatch (truncated or corrupt file)");
+    Reader r{buf.data() + 16, buf.data() + buf.size() - 8};
+    int32_t d = 0, m = 0, order = 0, nc = 0;
+    int64_t P = 0;
+    r.get(&d, 1);
+    r.get(&m, 1);
+    r.get(&order, 1);
+    r.get(&nc, 1);
+    r.get(&P, 1);
+    if (!r.ok || d < 1 || m < 1 || nc < 0 || P < 0 || (size_t)d > buf.size() || (size_t)nc > buf.size())
+        return fail(DDSG_ERR_ARG, "hdmr_load: bad header");
+    std::vector<double> anchor(d), lo(d), hi(d);
+    r.get(anchor.data(), d);
+    r.get(lo.data(), d);
+    r.get(hi.data(), d);
+    if (!r.ok) return fail(DDSG_ERR_ARG, "hdmr_load: truncated header");
+    hdmr_t *h = nullptr;
+    int rc = hdmr_create(d, m, order, anchor.data(), lo.data(), hi.data(), &h);
+    if (rc) return rc;
+    for (int32_t c = 0; c < nc; ++c) {
+        int32_t kk = -1, dims[KMAX];
+        int64_t npts = -1;
+        r.get(&kk, 1);
+        if (!r.ok || kk < 0 || kk > KMAX) {
+            hdmr_destroy(h);
+            return fail(DDSG_ERR_ARG, "hdmr_load: bad component record %d", c);
+        }
+        r.get(dims, kk);
+        r.get(&npts, 1);
+        if (!r.ok || npts < 0 || (size_t)npts > buf.size()) {
+            hdmr_destroy(h);
+            return fail(DDSG_ERR_ARG, "hdmr_load: bad component record %d", c);
+        }
+        std::vector<uint8_t> lv((size_t)npts * kk);
+        std::vector<uint32_t> ix((size_t)npts * kk);
+        r.get(lv.data(), lv.size());
+        r.get(ix.data(), ix.size());
+        if (!r.ok) {
+            hdmr_destroy(h);
+            return fail(DDSG_ERR_ARG, "hdmr_load: truncated component %d", c);
+        }
+        int32_t cid = 0;
+        if ((rc = hdmr_add_component(h, kk, dims, npts, kk ? lv.data() : nullptr, kk ? ix.data() : nullptr, &cid))) {
+            hdmr_destroy(h);
+            return rc;
+        }
+    }
+    if (h->P != P) {
+        hdmr_destroy(h);
+        return fail(DDSG_ERR_ARG, "hdmr_load: point count mismatch");
+    }
+    std::vector<double> alpha((size_t)P * m);
+    r.get(alpha.data(), alpha.size());
+    if (!r.ok || r.p != r.end) {
+        hdmr_destroy(h);
+        return fail(DDSG_ERR_ARG, "hdmr_load: surplus block has the wrong size");
+    }
+    // install the surpluses in device-row order (FP64, then the FP32 copy)
+    if ((rc = ensure_device(h))) {
+        hdmr_destroy(h);
+        return rc;
+    }
+    {
+        DeviceGuard g(h->device);
+        if (!h->uploaded && (rc = upload_tables(h))) {
+            hdmr_destroy(h);
+            return rc;
+        }
+        const int mp = h->dt.mp64;
+        std::vector<double> dev((size_t)P * mp, 0.0);
+        for (int64_t p = 0; p < P; ++p)
+            std::copy(&alpha[(size_t)p * m], &alpha[(size_t)p * m] + m, &dev[(size_t)h->dpos[p] * mp]);
+        if (cudaMemcpy(h->dt.alpha64, dev.data(), sizeof(double) * dev.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            launch_to_f32(h->dt.alpha64, h->dt.mp64, h->dt.alpha32, h->dt.mp32, h->P, h->m, nullptr) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess) {
+            cudaGetLastError();
+            hdmr_destroy(h);
+            return fail(DDSG_ERR_CUDA, "hdmr_load: surplus upload failed");
+        }
+        h->have_alpha = true;
+    }
+    *out = h;
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_shape(const hdmr_t *h, int32_t *d, int32_t *m, int32_t *order, double *anchor_host,
+                          double *lo_host, double *hi_host) {
+    if (!h) return fail(DDSG_ERR_ARG, "hdmr_shape: NULL handle");
+    if (d) *d = h->d;
+    if (m) *m = h->m;
+    if (order) *order = h->order;
+    if (anchor_host) std::copy(h->anchor.begin(), h->anchor.end(), anchor_host);
+    if (lo_host) std::copy(h->lo.begin(), h->lo.end(), lo_host);
+    if (hi_host) std::copy(h->hi.begin(), h->hi.end(), hi_host);
+    return DDSG_OK;
+}
+
 extern "C" int hdmr_quadrature(hdmr_t *h, double *q_dev, ddsg_stream_t stream) {
     if (!h || !q_dev) return fail(DDSG_ERR_ARG, "hdmr_quadrature: NULL argument");
     if (!h->uploaded || !h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_quadrature: call hdmr_hierarchize first");

@@ -194,10 +194,12 @@ def euler_errors(model, policy: HDMR, states: np.ndarray, precision=F64, form=FO
 def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps_gamma: float,
                    eps_eta: float, eps_rho: float, lo, hi, test_states: np.ndarray, tol_euler=0.0,
                    candidates=None, precision=F64, form=FORM_SLICEFREE, newton_tol=1e-10, max_it=30,
-                   node_mode=NODES_DELTA, tol_change=0.0):
+                   node_mode=NODES_DELTA, tol_change=0.0, checkpoint=None):
     """Alg. 1: p <- build_ddsg(x -> solve{FOC(. | x, p)}) until the mean Euler
     error at test_states is below tol_euler, the largest policy change at the
-    test states is below tol_change, or `steps` steps are done.
+    test states is below tol_change, or `steps` steps are done. With a
+    checkpoint path the policy is saved there after every step (hdmr_save);
+    HDMR.load of that file resumes the iteration as policy0.
     Returns the last policy and one record per step."""
     import torch
     d, m = policy0.d, policy0.m
@@ -220,6 +222,8 @@ def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps
                         "euler_error_mean": float(np.mean(np.max(e, 1))),
                         "euler_error_max": float(np.max(e)),
                         "policy_change_max": float((y1 - y0).abs().max().item())})
+        if checkpoint:
+            new.save(checkpoint)
         if policy is not policy0:
             policy.close()
         policy = new

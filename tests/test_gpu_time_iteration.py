@@ -145,3 +145,26 @@ def test_irreversible_time_iteration_matches_oracle(G):
     assert np.max(np.abs(y.cpu().numpy() - Eo.eval(T, form=1)["y"])) <= 1e-8
     for a, b in zip(hist_g, hist_o):
         assert abs(a["euler_error_mean"] - b["euler_error_mean"]) <= 1e-8
+
+
+def test_time_iteration_resumes_from_a_checkpoint(G, tmp_path):
+    """Two steps in one run equal one step, a save, a load and one more step."""
+    from paper_2202_06555_gb300.time_iteration import time_iteration
+    N = 2
+    d = 2 * N
+    I = O.IRBCOracle(N)
+    M = G.IRBC(N, I.p["beta"], I.p["alpha"], I.p["delta"], I.p["sigma"], I.p["rho"], I.p["phi"],
+               I.A, I.gamma, I.tau)
+    lo, hi = np.full(d, 0.8), np.full(d, 1.2)
+    T = synth.irbc_states(synth.BASE_SEED + 603, 32, N)
+    ck = str(tmp_path / "ti.ddsg")
+    h2, _ = time_iteration(M, _gpu_initial_policy(G, I, N), 2, 2, 4, 1e-4, 1e-5, 0.0, lo, hi, T)
+    h1, _ = time_iteration(M, _gpu_initial_policy(G, I, N), 1, 2, 4, 1e-4, 1e-5, 0.0, lo, hi, T, checkpoint=ck)
+    hr, _ = time_iteration(M, G.HDMR.load(ck), 1, 2, 4, 1e-4, 1e-5, 0.0, lo, hi, T)
+    x = torch.from_numpy(T).cuda()
+    ya = torch.empty((T.shape[0], N + 1), dtype=torch.float64, device="cuda")
+    yb = torch.empty_like(ya)
+    h2.eval(x, ya, G.F64, G.FORM_SLICEFREE)
+    hr.eval(x, yb, G.F64, G.FORM_SLICEFREE)
+    torch.cuda.synchronize()
+    assert torch.equal(ya, yb)
