@@ -66,6 +66,17 @@ const char *ddsg_last_error(void);
 const char *ddsg_version(void);
 
 /*
+ * ddsg_inject_alloc_failure -- TEST ONLY (no paper counterpart), process-wide:
+ * after `skip` more device allocations by the library succeed, the next
+ * `count` fail as on an exhausted device (nothing is allocated; the call that
+ * needed the memory returns DDSG_ERR_OOM). count = 0 turns the switch off.
+ * Every entry point leaves its handle consistent after such a failure: the
+ * same call succeeds once memory is available again. Negative arguments are
+ * DDSG_ERR_ARG. Makes no CUDA call.
+ */
+int ddsg_inject_alloc_failure(int skip, int count);
+
+/*
  * hdmr_create -- new empty expansion (Sec. 4.2, Alg. 2 inputs: anchor, order).
  *   d >= 1, m >= 1, 0 <= order <= DDSG_KMAX.
  *   anchor_host, lo_host, hi_host: length d, physical units, lo < hi.
@@ -144,6 +155,9 @@ int hdmr_hierarchize(hdmr_t *h, const double *values_dev, ddsg_stream_t stream);
  *               points inside the support of a rejected point are left out).
  * New points are appended per component in canonical order; *n_new = total.
  * Needs hierarchized surpluses (reads them back, synchronizing `stream`).
+ * A non-finite surplus (from a non-finite value given to hdmr_hierarchize)
+ * is DDSG_ERR_NUMERIC, naming the component, point and output; nothing is
+ * added then.
  * The new points need values before the next hdmr_hierarchize.
  */
 int hdmr_refine(hdmr_t *h, double eps_gamma, int max_level, int strict, int64_t *n_new,
@@ -273,6 +287,21 @@ int64_t hdmr_eval_noalloc_capacity(int d);
 int hdmr_eval_graph(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int precision,
                     int form, ddsg_stream_t stream);
 
+/*
+ * hdmr_set_fault_injection -- TEST ONLY (no paper counterpart): exercises the
+ * failure path of the TMA-staged evaluation kernels without faulting anything.
+ * From the processed component withhold_from on (-1: off, the default) the
+ * kernel's producer thread issues no staging copies, so the bounded waits on
+ * them (2^22 polls of mbarrier.try_wait) run out. A block that gives up writes
+ * NaN for its queries and counts one timeout per warp in hdmr_stats (stats[2]);
+ * the copies it did issue land before it exits and the context stays usable.
+ * Applies to hdmr_eval, hdmr_eval_host and hdmr_eval_graph of this handle
+ * (not to the evaluations inside euler_residual / irbc_newton). Only kernels
+ * 2-4 (hdmr_set_eval_config) stage; the others ignore the setting, which
+ * persists until set back to -1.
+ */
+int hdmr_set_fault_injection(hdmr_t *h, int withhold_from);
+
 /* Pre-size the eval workspace for up to n queries (no allocation in later evals). */
 int hdmr_reserve(hdmr_t *h, int64_t n);
 
@@ -284,6 +313,16 @@ int hdmr_reserve(hdmr_t *h, int64_t n);
  * Synchronizes `stream`. reset != 0 zeroes them afterwards.
  */
 int hdmr_stats(hdmr_t *h, int64_t *stats_host, int reset, ddsg_stream_t stream);
+
+/*
+ * hdmr_check -- status of the evaluations queued so far: synchronizes `stream`
+ * and returns DDSG_ERR_TIMEOUT if a staged evaluation kernel gave up a bounded
+ * wait since the counter was last cleared (by this call or a hdmr_stats
+ * reset): the queries of the blocks that gave up read NaN. The timeout
+ * counter is cleared when it is reported. DDSG_OK otherwise, and before the
+ * handle's first GPU use.
+ */
+int hdmr_check(hdmr_t *h, ddsg_stream_t stream);
 
 /*
  * hdmr_eval_host -- hdmr_eval with HOST buffers x_host (n*d) and y_host (n*m);

@@ -58,6 +58,9 @@ SIGNATURES = {
     "hdmr_eval_graph": (_int, [_p, _i64, _p, _p, _int, _int, _p]),
     "hdmr_quadrature": (_int, [_p, _p, _p]),
     "hdmr_save": (_int, [_p, C.c_char_p]),
+    "hdmr_set_fault_injection": (_int, [_p, _int]),
+    "hdmr_check": (_int, [_p, _p]),
+    "ddsg_inject_alloc_failure": (_int, [_int, _int]),
     "hdmr_load": (_int, [C.c_char_p, _p]),
     "hdmr_shape": (_int, [_p, _p, _p, _p, _p, _p, _p]),
     "hdmr_eval_noalloc_capacity": (_i64, [_int]),
@@ -89,7 +92,11 @@ _lib = None
 
 
 class DDSGError(RuntimeError):
-    pass
+    """A libddsg call returned an error; `code` is the DDSG_ERR_* value."""
+
+    def __init__(self, msg: str, code: int | None = None):
+        super().__init__(msg)
+        self.code = code
 
 
 def library_path() -> str:
@@ -117,7 +124,13 @@ def load(build_if_missing: bool = True):
 def _check(rc: int, what: str):
     if rc != 0:
         msg = load().ddsg_last_error().decode()
-        raise DDSGError(f"{what} failed ({ERRORS.get(rc, rc)}): {msg}")
+        raise DDSGError(f"{what} failed ({ERRORS.get(rc, rc)}): {msg}", rc)
+
+
+def inject_alloc_failure(skip: int = 0, count: int = 1):
+    """Test only, process-wide: after `skip` more device allocations by libddsg
+    succeed, the next `count` fail with DDSG_ERR_OOM; count=0 turns it off."""
+    _check(load().ddsg_inject_alloc_failure(int(skip), int(count)), "ddsg_inject_alloc_failure")
 
 
 def _np_ptr(a):
@@ -263,6 +276,17 @@ class HDMR:
         n = x_dev.shape[0]
         _check(load().hdmr_eval_graph(self._h, n, _dev_ptr(x_dev), _dev_ptr(y_dev), int(precision),
                                       int(form), _stream_ptr(stream)), "hdmr_eval_graph")
+
+    def set_fault_injection(self, withhold_from: int = -1):
+        """Test only: withhold the staged kernels' copies from a processed component
+        on, so their bounded waits run out (see hdmr_set_fault_injection)."""
+        _check(load().hdmr_set_fault_injection(self._h, int(withhold_from)),
+               "hdmr_set_fault_injection")
+
+    def check(self, stream=None):
+        """Raise DDSGError (DDSG_ERR_TIMEOUT) if a staged evaluation gave up a
+        bounded wait since the last check; synchronizes the stream."""
+        _check(load().hdmr_check(self._h, _stream_ptr(stream)), "hdmr_check")
 
     def save(self, path: str):
         """Checkpoint the hierarchized expansion to one file (hdmr_save)."""

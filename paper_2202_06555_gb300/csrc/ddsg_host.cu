@@ -14,6 +14,9 @@
 #include <unordered_map>
 #include <vector>
 
+#include <atomic>
+
+#include "ddsg_alloc.h"
 #include "ddsg_internal.h"
 
 using namespace ddsg;
@@ -43,6 +46,41 @@ static int fail(int code, const char *fmt, ...) {
     } while (0)
 
 extern "C" const char *ddsg_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// device allocation with the failure switch
+// ---------------------------------------------------------------------------
+
+static std::atomic<int> g_alloc_skip{0}, g_alloc_fail{0};
+
+cudaError_t ddsg::dev_alloc(void **ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (g_alloc_fail.load() > 0) {
+        if (g_alloc_skip.load() > 0) {
+            g_alloc_skip.fetch_sub(1);
+        } else {
+            g_alloc_fail.fetch_sub(1);
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
+extern "C" int ddsg_inject_alloc_failure(int skip, int count) {
+    if (skip < 0 || count < 0) return fail(DDSG_ERR_ARG, "ddsg_inject_alloc_failure: negative argument");
+    g_alloc_skip.store(count ? skip : 0);
+    g_alloc_fail.store(count);
+    return DDSG_OK;
+}
+
+#define ALLOC_TRY(ptr, bytes, what)                                                       \
+    do {                                                                                  \
+        if (dev_alloc((ptr), (bytes)) != cudaSuccess) {                                   \
+            cudaGetLastError();                                                           \
+            return fail(DDSG_ERR_OOM, "%s: %zu bytes of device memory unavailable", (what), \
+                        (size_t)(bytes));                                                 \
+        }                                                                                 \
+    } while (0)
 extern "C" const char *ddsg_version(void) { return "libddsg 0.1 (sm_103a)"; }
 
 // ---------------------------------------------------------------------------
@@ -82,6 +120,7 @@ struct hdmr {
     // graph replay of hdmr_eval_graph: one cached executable graph for the
     // last (n, x, y, precision, form, schedule, table generation), replayed on
     // a handle-owned stream ordered against the caller's stream by events
+    int fi_withhold = -1;           // failure-path test (hdmr_set_fault_injection)
     uint64_t gen = 1;               // bumped whenever a captured pointer may change
     bool capturing = false;         // ProfScope records nothing while capturing
     cudaGraphExec_t gexec = nullptr;
@@ -172,9 +211,21 @@ static int ensure_device(hdmr *h) {
     int dev = -1;
     CUDA_TRY(cudaGetDevice(&dev));
     const int d = h->d;
-    CUDA_TRY(cudaMalloc(&h->dlo, sizeof(double) * d));
-    CUDA_TRY(cudaMalloc(&h->dspan, sizeof(double) * d));
-    CUDA_TRY(cudaMalloc(&h->stats, sizeof(int64_t) * 4));
+    // a failed allocation leaves the handle unbound, with nothing held
+    auto undo = [h] {
+        cudaFree(h->dlo);
+        cudaFree(h->dspan);
+        cudaFree(h->stats);
+        h->dlo = h->dspan = nullptr;
+        h->stats = nullptr;
+    };
+    if (dev_alloc(&h->dlo, sizeof(double) * d) != cudaSuccess ||
+        dev_alloc(&h->dspan, sizeof(double) * d) != cudaSuccess ||
+        dev_alloc(&h->stats, sizeof(int64_t) * 4) != cudaSuccess) {
+        cudaGetLastError();
+        undo();
+        return fail(DDSG_ERR_OOM, "first device use: per-handle buffers unavailable");
+    }
     CUDA_TRY(cudaMemcpy(h->dlo, h->lo.data(), sizeof(double) * d, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(h->dspan, h->span.data(), sizeof(double) * d, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemset(h->stats, 0, sizeof(int64_t) * 4));
@@ -456,7 +507,7 @@ template <typename T>
 static int dev_upload(T **dst, const std::vector<T> &src) {
     *dst = nullptr;
     if (src.empty()) return DDSG_OK;
-    CUDA_TRY(cudaMalloc(dst, sizeof(T) * src.size()));
+    ALLOC_TRY(dst, sizeof(T) * src.size(), "grid tables");
     CUDA_TRY(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
     return DDSG_OK;
 }
@@ -632,8 +683,8 @@ static int upload_tables(hdmr *h) {
         t.stage_bytes[form][DDSG_F64] = rows_max * mp64 * 8;
         t.stage_bytes[form][DDSG_F32C] = rows_max * mp32 * 4;
     }
-    CUDA_TRY(cudaMalloc(&t.alpha64, sizeof(double) * (size_t)P * t.mp64));
-    CUDA_TRY(cudaMalloc(&t.alpha32, sizeof(float) * (size_t)P * t.mp32));
+    ALLOC_TRY(&t.alpha64, sizeof(double) * (size_t)P * t.mp64, "surpluses");
+    ALLOC_TRY(&t.alpha32, sizeof(float) * (size_t)P * t.mp32, "surpluses");
     CUDA_TRY(cudaMemset(t.alpha64, 0, sizeof(double) * (size_t)P * t.mp64));
     CUDA_TRY(cudaMemset(t.alpha32, 0, sizeof(float) * (size_t)P * t.mp32));
     h->uploaded = true;
@@ -928,6 +979,16 @@ extern "C" int hdmr_refine(hdmr_t *h, double eps, int max_level, int strict, int
     std::vector<double> alpha((size_t)h->P * m);
     int rc = hdmr_get_surpluses(h, alpha.data(), stream);
     if (rc) return rc;
+    // eq. 3.8 compares |alpha| with eps; a non-finite surplus (from a non-finite
+    // value handed to hdmr_hierarchize) would silently read as insignificant
+    for (size_t c = 0; c < h->comps.size(); ++c) {
+        const int64_t np = h->comps[c].npts();
+        const double *al = alpha.data() + (size_t)h->first_point[c] * m;
+        for (int64_t q = 0; q < np * m; ++q)
+            if (!std::isfinite(al[q]))
+                return fail(DDSG_ERR_NUMERIC, "hdmr_refine: surplus of component %zu, point %lld, output %d is not finite",
+                            c, (long long)(q / m), (int)(q % m));
+    }
     int64_t added = 0;
     for (size_t c = 0; c < h->comps.size(); ++c) {
         Comp &cp = h->comps[c];
@@ -1016,7 +1077,7 @@ static int ensure_ws(hdmr *h, int64_t n) {
     h->ws = nullptr;
     h->ws_bytes = 0;
     ++h->gen;
-    if (cudaMalloc(&h->ws, need) != cudaSuccess) {
+    if (dev_alloc(&h->ws, need) != cudaSuccess) {
         cudaGetLastError();
         return fail(DDSG_ERR_OOM, "hdmr_eval: workspace of %zu bytes unavailable", need);
     }
@@ -1069,10 +1130,18 @@ extern "C" int hdmr_eval(hdmr_t *h, int64_t n, const double *x_dev, double *y_de
     a.precision = precision;
     a.cfg = h->cfg[precision][form];
     a.err = reinterpret_cast<unsigned long long *>(h->stats + 2);
+    a.withhold_from = h->fi_withhold;
     {
         ProfScope ps(h, DDSG_K_EVAL, st);
         CUDA_TRY(launch_eval(a, st));
     }
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_set_fault_injection(hdmr_t *h, int withhold_from) {
+    if (!h || withhold_from < -1) return fail(DDSG_ERR_ARG, "hdmr_set_fault_injection: bad argument");
+    h->fi_withhold = withhold_from;
+    ++h->gen;
     return DDSG_OK;
 }
 
@@ -1171,7 +1240,7 @@ extern "C" int hdmr_eval_host(hdmr_t *h, int64_t n, const double *x_host, double
         cudaFree(h->hbuf);
         h->hbuf = nullptr;
         h->hbuf_bytes = 0;
-        if (cudaMalloc(&h->hbuf, need) != cudaSuccess) {
+        if (dev_alloc(&h->hbuf, need) != cudaSuccess) {
             cudaGetLastError();
             return fail(DDSG_ERR_OOM, "hdmr_eval_host: staging buffer of %zu bytes unavailable", need);
         }
@@ -1305,6 +1374,23 @@ extern "C" int hdmr_stats(hdmr_t *h, int64_t *stats_host, int reset, ddsg_stream
     CUDA_TRY(cudaMemcpyAsync(stats_host, h->stats, sizeof(int64_t) * 3, cudaMemcpyDeviceToHost, st));
     if (reset) CUDA_TRY(cudaMemsetAsync(h->stats, 0, sizeof(int64_t) * 4, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    return DDSG_OK;
+}
+
+extern "C" int hdmr_check(hdmr_t *h, ddsg_stream_t stream) {
+    if (!h) return fail(DDSG_ERR_ARG, "hdmr_check: NULL handle");
+    if (h->device < 0) return DDSG_OK;   // nothing ran yet
+    DeviceGuard g(h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int64_t timeouts = 0;
+    CUDA_TRY(cudaMemcpyAsync(&timeouts, h->stats + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (timeouts > 0) {
+        CUDA_TRY(cudaMemsetAsync(h->stats + 2, 0, sizeof(int64_t), st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return fail(DDSG_ERR_TIMEOUT, "%lld warps of the staged evaluation gave up a bounded wait; their queries read NaN",
+                    (long long)timeouts);
+    }
     return DDSG_OK;
 }
 

@@ -205,6 +205,9 @@ struct EvalArgs {
     int precision;            // DDSG_F64 / DDSG_F32C
     EvalConfig cfg;
     unsigned long long *err = nullptr;  // device word: bounded waits that gave up (nullable)
+    // failure-path test (hdmr_set_fault_injection): the staged kernels withhold the
+    // staging copies of processed components >= withhold_from (-1: none)
+    int withhold_from = -1;
 };
 
 // true if kernel `kernel` can run this handle/form/precision

@@ -25,6 +25,7 @@
 #include <string>
 #include <vector>
 
+#include "ddsg_alloc.h"
 #include "ddsg_internal.h"
 
 using namespace ddsg;
@@ -725,7 +726,7 @@ int ensure(irbc *M, size_t bytes) {
     cudaFree(M->ws);
     M->ws = nullptr;
     M->ws_bytes = 0;
-    if (cudaMalloc(&M->ws, bytes) != cudaSuccess) {
+    if (dev_alloc(&M->ws, bytes) != cudaSuccess) {
         cudaGetLastError();
         return set_error(DDSG_ERR_OOM, "IRBC workspace allocation failed");
     }
@@ -860,8 +861,14 @@ static int bind_device(irbc *M) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return set_error(DDSG_ERR_CUDA, "IRBC: no CUDA device");
     const size_t nb = sizeof(double) * M->p.N;
-    if (cudaMalloc(&M->gamma_d, nb) != cudaSuccess || cudaMalloc(&M->tau_d, nb) != cudaSuccess ||
-        cudaMemcpy(M->gamma_d, M->gamma.data(), nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (dev_alloc(&M->gamma_d, nb) != cudaSuccess || dev_alloc(&M->tau_d, nb) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(M->gamma_d);
+        cudaFree(M->tau_d);
+        M->gamma_d = M->tau_d = nullptr;
+        return set_error(DDSG_ERR_OOM, "IRBC: parameter buffers unavailable");
+    }
+    if (cudaMemcpy(M->gamma_d, M->gamma.data(), nb, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(M->tau_d, M->tau.data(), nb, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         return set_error(DDSG_ERR_CUDA, "IRBC: parameter upload failed");
@@ -1031,7 +1038,7 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
                  szs = rnd(bytes((size_t)ns)), szi = rnd(sizeof(int32_t) * (size_t)ns);
     const size_t tot = 4 * szv + szJ + 5 * szs + 2 * szi;
     void *blk = nullptr;
-    if (cudaMalloc(&blk, tot) != cudaSuccess) {
+    if (dev_alloc(&blk, tot) != cudaSuccess) {
         cudaGetLastError();
         return set_error(DDSG_ERR_OOM, "irbc_newton: buffers unavailable");
     }

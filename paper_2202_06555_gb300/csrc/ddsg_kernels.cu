@@ -13,6 +13,7 @@
 //   eval_lq          the same with the 1D basis recomputed per tuple (any k).
 //   hierarchize      surpluses layer by layer (Sec. 3.1), one block per component.
 #include <cuda_runtime.h>
+#include <climits>
 #include <stdint.h>
 
 #include <type_traits>
@@ -148,6 +149,8 @@ struct EvalParams {
     int32_t *count;
     int form;
     unsigned long long *err;
+    int issue_end;         // staging copies issued for processed components < issue_end only
+                           // (INT_MAX unless a failure-path test withholds them)
 };
 
 template <int PREC>
@@ -853,7 +856,9 @@ __global__ void __launch_bounds__(TmaShape<GR>::NT, 1) eval_tma_kernel(const Eva
     const int mp = T::stride(p.t);
 
     // thread 0: stage processed component j (record rec) into buffer j % nbuf
+    // (a failure-path test withholds the copies from p.issue_end on)
     auto issue = [&](int j, int4 rec) {
+        if (j >= p.issue_end) return;
         const int b = j % nbuf;
         const uint32_t nrows = (uint32_t)rec.z & 0xfffffu, nt = (uint32_t)rec.z >> 20;
         const uint32_t rbytes = nrows * (uint32_t)mp * (uint32_t)sizeof(W);
@@ -972,7 +977,7 @@ __global__ void __launch_bounds__(TmaShape<GR>::NT, 1) eval_tma_kernel(const Eva
     if (tid == 0) {
         // a block that gave up may still have copies in flight: let them land
         for (int j = nissued > nbuf ? nissued - nbuf : 0; j < nissued; ++j)
-            mbar_wait_bounded(&full[j % nbuf], (uint32_t)((j / nbuf) & 1));
+            if (j < p.issue_end) mbar_wait_bounded(&full[j % nbuf], (uint32_t)((j / nbuf) & 1));
     }
     if (HC && GR > 1) {
         // the point hash and count of a query are split over its groups: combine
@@ -1124,6 +1129,7 @@ cudaError_t launch_eval(const EvalArgs &a, cudaStream_t st) {
     p.count = a.count;
     p.form = a.form;
     p.err = a.err;
+    p.issue_end = a.withhold_from < 0 ? INT_MAX : a.withhold_from;
     const bool hc = a.hash != nullptr || a.count != nullptr;
     const int mc = a.cfg.mc > 0 ? a.cfg.mc : default_mc(a.precision, a.m);
     if (a.precision == DDSG_F64) return launch_prec<DDSG_F64>(p, a.cfg.kernel, mc, hc, st);

@@ -17,6 +17,7 @@
 #include <string>
 #include <vector>
 
+#include "ddsg_alloc.h"
 #include "ddsg_internal.h"
 
 using namespace ddsg;
@@ -307,11 +308,27 @@ struct mlp {
 
 namespace {
 
+// Device parameter buffers (not the batch workspace) back to nothing held.
+void release_params(mlp *M) {
+    for (int l = 0; l < (int)M->W.size(); ++l) {
+        cudaFree(M->W[l]); cudaFree(M->b[l]); cudaFree(M->gW[l]); cudaFree(M->gb[l]);
+        cudaFree(M->mW[l]); cudaFree(M->vW[l]); cudaFree(M->mb[l]); cudaFree(M->vb[l]);
+        cudaFree(M->Wb[l]); cudaFree(M->WbT[l]);
+    }
+    M->W.clear(); M->b.clear(); M->gW.clear(); M->gb.clear(); M->mW.clear();
+    M->vW.clear(); M->mb.clear(); M->vb.clear(); M->Wb.clear(); M->WbT.clear();
+    cudaFree(M->in_shift); cudaFree(M->in_scale); cudaFree(M->out_shift); cudaFree(M->out_scale);
+    cudaFree(M->loss);
+    M->in_shift = M->in_scale = M->out_shift = M->out_scale = nullptr;
+    M->loss = nullptr;
+}
+
 int mlp_bind(mlp *M) {
     if (M->device >= 0) return DDSG_OK;
+    release_params(M);   // what an earlier failed bind left behind
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return set_error(DDSG_ERR_CUDA, "mlp: no CUDA device");
-    auto alloc = [](void **p, size_t b) { return cudaMalloc(p, b) == cudaSuccess && cudaMemset(*p, 0, b) == cudaSuccess; };
+    auto alloc = [](void **p, size_t b) { return dev_alloc(p, b) == cudaSuccess && cudaMemset(*p, 0, b) == cudaSuccess; };
     const int L = M->L;
     M->W.assign(L, nullptr); M->b.assign(L, nullptr); M->gW.assign(L, nullptr); M->gb.assign(L, nullptr);
     M->mW.assign(L, nullptr); M->vW.assign(L, nullptr); M->mb.assign(L, nullptr); M->vb.assign(L, nullptr);
@@ -388,7 +405,7 @@ int mlp_ws(mlp *M, int64_t Bp, WsView &v) {
         cudaFree(M->ws);
         M->ws = nullptr;
         M->cap = 0;
-        if (cudaMalloc(&M->ws, need) != cudaSuccess) {
+        if (dev_alloc(&M->ws, need) != cudaSuccess) {
             cudaGetLastError();
             return set_error(DDSG_ERR_OOM, "mlp: batch workspace unavailable");
         }
@@ -476,13 +493,7 @@ extern "C" int mlp_create(int nlayers, const int32_t *sizes, const float *params
 
 extern "C" int mlp_destroy(mlp_t *M) {
     if (!M) return DDSG_OK;
-    for (int l = 0; l < (int)M->W.size(); ++l) {
-        cudaFree(M->W[l]); cudaFree(M->b[l]); cudaFree(M->gW[l]); cudaFree(M->gb[l]);
-        cudaFree(M->mW[l]); cudaFree(M->vW[l]); cudaFree(M->mb[l]); cudaFree(M->vb[l]);
-        cudaFree(M->Wb[l]); cudaFree(M->WbT[l]);
-    }
-    cudaFree(M->in_shift); cudaFree(M->in_scale); cudaFree(M->out_shift); cudaFree(M->out_scale);
-    cudaFree(M->loss);
+    release_params(M);
     cudaFree(M->ws);
     delete M;
     return DDSG_OK;

@@ -199,7 +199,8 @@ def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps
     error at test_states is below tol_euler, the largest policy change at the
     test states is below tol_change, or `steps` steps are done. With a
     checkpoint path the policy is saved there after every step (hdmr_save);
-    HDMR.load of that file resumes the iteration as policy0.
+    HDMR.load of that file resumes the iteration as policy0. Each step ends
+    with hdmr_check on both policies (DDSGError on a device wait that gave up).
     Returns the last policy and one record per step."""
     import torch
     d, m = policy0.d, policy0.m
@@ -215,6 +216,8 @@ def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps
         policy.eval(sd, y0, precision, form)
         new.eval(sd, y1, precision, form)
         torch.cuda.synchronize()
+        policy.check()                 # a staged evaluation that gave up a wait read NaN:
+        new.check()                    # stop with DDSG_ERR_TIMEOUT rather than iterate on it
         history.append({"step": step, "points": info["points"], "components": len(info["components"]),
                         "rho": info["rho"], "rejected": len(info["rejected"]),
                         "newton_points": solve.points, "newton_failed": solve.failed,

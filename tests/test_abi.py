@@ -136,3 +136,21 @@ def test_irbc_create_validates():
     prm.N = 1
     assert lib.irbc_create(C.byref(prm), G._np_ptr(g), G._np_ptr(g), C.byref(h)) == 0
     assert lib.irbc_destroy(h) == 0
+
+
+def test_test_switches_validate_without_a_gpu():
+    # allocation-failure switch: process-wide, no CUDA call
+    with pytest.raises(G.DDSGError, match="ERR_ARG") as ei:
+        G.inject_alloc_failure(-1, 1)
+    assert ei.value.code == -1
+    with pytest.raises(G.DDSGError, match="ERR_ARG"):
+        G.inject_alloc_failure(0, -1)
+    G.inject_alloc_failure(3, 2)
+    G.inject_alloc_failure(0, 0)
+    h = G.HDMR(3, 2, 1)
+    h.add_regular([0], 2)
+    assert G.load().hdmr_check(h._h, None) == 0   # nothing ran on a device: no status
+    with pytest.raises(G.DDSGError, match="ERR_ARG"):
+        h.set_fault_injection(-2)
+    h.set_fault_injection(4)
+    h.set_fault_injection(-1)
