@@ -77,6 +77,22 @@ const char *ddsg_version(void);
 int ddsg_inject_alloc_failure(int skip, int count);
 
 /*
+ * Checked builds (the library compiled with -DDDSG_CHECKED; no paper
+ * counterpart): the bounds-checked stand-in for a memory sanitizer. Every
+ * table index a kernel derives from the grid tables (cell offset, directory
+ * slot, device row against its component's rows, staged block, dimension,
+ * point and component ids) is tested before the access it guards; a failed
+ * test sets one bit per site in a process-wide check word and skips the access
+ * (the result of that query is wrong, nothing is touched out of bounds).
+ * ddsg_checked_build() is 1 in such a build, 0 otherwise.
+ * ddsg_take_check_word reads and clears the word: bit 0 cell, 1 slot, 2 row,
+ * 3 stage, 4 dimension, 5 point, 6 component (always 0 in release builds).
+ * Synchronous.
+ */
+int ddsg_checked_build(void);
+int ddsg_take_check_word(uint64_t *word);
+
+/*
  * hdmr_create -- new empty expansion (Sec. 4.2, Alg. 2 inputs: anchor, order).
  *   d >= 1, m >= 1, 0 <= order <= DDSG_KMAX.
  *   anchor_host, lo_host, hi_host: length d, physical units, lo < hi.
@@ -292,7 +308,7 @@ int hdmr_eval_graph(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, in
  * failure path of the TMA-staged evaluation kernels without faulting anything.
  * From the processed component withhold_from on (-1: off, the default) the
  * kernel's producer thread issues no staging copies, so the bounded waits on
- * them (2^22 polls of mbarrier.try_wait) run out. A block that gives up writes
+ * them (2^18 polls of mbarrier.try_wait, about one second) run out. A block that gives up writes
  * NaN for its queries and counts one timeout per warp in hdmr_stats (stats[2]);
  * the copies it did issue land before it exits and the context stays usable.
  * Applies to hdmr_eval, hdmr_eval_host and hdmr_eval_graph of this handle
@@ -319,8 +335,10 @@ int hdmr_stats(hdmr_t *h, int64_t *stats_host, int reset, ddsg_stream_t stream);
  * and returns DDSG_ERR_TIMEOUT if a staged evaluation kernel gave up a bounded
  * wait since the counter was last cleared (by this call or a hdmr_stats
  * reset): the queries of the blocks that gave up read NaN. The timeout
- * counter is cleared when it is reported. DDSG_OK otherwise, and before the
- * handle's first GPU use.
+ * counter is cleared when it is reported. In a checked build it then returns
+ * DDSG_ERR_TABLE (naming the sites) if any table index test failed since the
+ * check word was last taken, and clears the word. DDSG_OK otherwise, and
+ * before the handle's first GPU use.
  */
 int hdmr_check(hdmr_t *h, ddsg_stream_t stream);
 

@@ -61,6 +61,8 @@ SIGNATURES = {
     "hdmr_set_fault_injection": (_int, [_p, _int]),
     "hdmr_check": (_int, [_p, _p]),
     "ddsg_inject_alloc_failure": (_int, [_int, _int]),
+    "ddsg_checked_build": (_int, []),
+    "ddsg_take_check_word": (_int, [_p]),
     "hdmr_load": (_int, [C.c_char_p, _p]),
     "hdmr_shape": (_int, [_p, _p, _p, _p, _p, _p, _p]),
     "hdmr_eval_noalloc_capacity": (_i64, [_int]),
@@ -99,8 +101,14 @@ class DDSGError(RuntimeError):
         self.code = code
 
 
+def variant() -> str:
+    """Library variant this process loads: DDSG_VARIANT, "release" (default) or
+    "checked" (kernels with bounds-checked table indices)."""
+    return os.environ.get("DDSG_VARIANT", "release")
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.lib_path(variant())
 
 
 def load(build_if_missing: bool = True):
@@ -108,11 +116,12 @@ def load(build_if_missing: bool = True):
     global _lib
     if _lib is not None:
         return _lib
+    path = library_path()
     if build_if_missing:
-        _build.build()
-    if not os.path.exists(_build.LIB):
-        raise DDSGError(f"libddsg is not built ({_build.LIB}); run __graft_entry__.build()")
-    lib = C.CDLL(_build.LIB)
+        _build.build(variant=variant())
+    if not os.path.exists(path):
+        raise DDSGError(f"libddsg is not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.restype = res
@@ -125,6 +134,17 @@ def _check(rc: int, what: str):
     if rc != 0:
         msg = load().ddsg_last_error().decode()
         raise DDSGError(f"{what} failed ({ERRORS.get(rc, rc)}): {msg}", rc)
+
+
+CHECK_SITES = ["cell", "slot", "row", "stage", "dim", "point", "component"]
+
+
+def take_check_word() -> list[str]:
+    """Checked builds: the table-index test sites that failed since the last
+    call (and clear them); always [] in a release build."""
+    w = C.c_uint64()
+    _check(load().ddsg_take_check_word(C.byref(w)), "ddsg_take_check_word")
+    return [s for i, s in enumerate(CHECK_SITES) if w.value >> i & 1] + (["unreadable"] if w.value >> 63 & 1 else [])
 
 
 def inject_alloc_failure(skip: int = 0, count: int = 1):

@@ -3,6 +3,11 @@
 Each .cu translation unit under csrc/ is compiled in parallel to an object
 file, then linked into _build/libddsg.so. Rebuilds only when a source or
 header is newer than the library.
+
+Variant "checked" (_build/checked/libddsg_checked.so) is the same library
+compiled with -DDDSG_CHECKED: every table index the kernels derive is tested
+before use (the bounds-checked stand-in for a memory sanitizer). The Python
+binding loads it when DDSG_VARIANT=checked.
 """
 from __future__ import annotations
 
@@ -17,6 +22,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libddsg.so")
+VARIANTS = {"release": (BUILD, LIB, []),
+            "checked": (os.path.join(BUILD, "checked"), os.path.join(BUILD, "checked", "libddsg_checked.so"),
+                        ["-DDDSG_CHECKED=1"])}
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,22 +47,31 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def lib_path(variant: str = "release") -> str:
+    if variant not in VARIANTS:
+        raise ValueError(f"unknown libddsg variant {variant!r} (release, checked)")
+    return VARIANTS[variant][1]
+
+
+def needs_build(variant: str = "release") -> bool:
+    lib = lib_path(variant)
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    if not force and not needs_build():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, variant: str = "release") -> str:
+    lib = lib_path(variant)
+    if not force and not needs_build(variant):
+        return lib
+    out_dir, _, defines = VARIANTS[variant]
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_v else []
+    extra = (["-Xptxas", "-v"] if ptxas_v else []) + defines
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         cmd = [cc] + ARCH + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -67,15 +84,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         for _, err in results:
             if err:
                 sys.stderr.write(err)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True, ptxas_v="--ptxas-v" in sys.argv)
-    print(LIB)
+    v = "checked" if "--checked" in sys.argv else "release"
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_v="--ptxas-v" in sys.argv, variant=v))

@@ -81,7 +81,23 @@ extern "C" int ddsg_inject_alloc_failure(int skip, int count) {
                         (size_t)(bytes));                                                 \
         }                                                                                 \
     } while (0)
+#if defined(DDSG_CHECKED)
+extern "C" const char *ddsg_version(void) { return "libddsg 0.1 (sm_103a, checked)"; }
+extern "C" int ddsg_checked_build(void) { return 1; }
+#else
 extern "C" const char *ddsg_version(void) { return "libddsg 0.1 (sm_103a)"; }
+extern "C" int ddsg_checked_build(void) { return 0; }
+#endif
+
+extern "C" int ddsg_take_check_word(uint64_t *word) {
+    if (!word) return fail(DDSG_ERR_ARG, "ddsg_take_check_word: NULL argument");
+    *word = check_word_take_kernels() | check_word_take_irbc();
+    return DDSG_OK;
+}
+
+#if defined(DDSG_CHECKED)
+static const char *const kCheckSiteName[CK_NSITES] = {"cell", "slot", "row", "stage", "dim", "point", "component"};
+#endif
 
 // ---------------------------------------------------------------------------
 // handle
@@ -1391,6 +1407,15 @@ extern "C" int hdmr_check(hdmr_t *h, ddsg_stream_t stream) {
         return fail(DDSG_ERR_TIMEOUT, "%lld warps of the staged evaluation gave up a bounded wait; their queries read NaN",
                     (long long)timeouts);
     }
+#if defined(DDSG_CHECKED)
+    const uint64_t w = check_word_take_kernels() | check_word_take_irbc();
+    if (w) {
+        std::string sites;
+        for (int s = 0; s < CK_NSITES; ++s)
+            if (w >> s & 1) sites += std::string(sites.empty() ? "" : ", ") + kCheckSiteName[s];
+        return fail(DDSG_ERR_TABLE, "checked build: table index tests failed at: %s", sites.c_str());
+    }
+#endif
     return DDSG_OK;
 }
 

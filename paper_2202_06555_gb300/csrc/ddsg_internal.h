@@ -83,6 +83,61 @@ __host__ __device__ inline int32_t tuple_row(const DevTup &tu, uint32_t off, con
     return slots[tu.slot_base + off];
 }
 
+// ---------------------------------------------------------------------------
+// Checked builds (-DDDSG_CHECKED): the bounds-checked stand-in for a memory
+// sanitizer. Every table index a kernel derives from the tables is tested
+// before the access it guards. A failed test sets its site's bit in the
+// module's check word and the access is skipped: that query's result is wrong,
+// but nothing is read or written out of bounds. Release builds compile every
+// test to `true` (the expression is not even evaluated).
+// ---------------------------------------------------------------------------
+enum CheckSite : int {
+    CK_CELL = 0,   // cell offset of a presence-mask tuple < 64
+    CK_SLOT = 1,   // cell-directory index < S
+    CK_ROW = 2,    // device row inside its component's rows
+    CK_STAGE = 3,  // staged block inside its shared-memory buffer and the tables
+    CK_DIM = 4,    // dimension index < d
+    CK_POINT = 5,  // point id < P (hierarchization layers)
+    CK_COMP = 6,   // component id < C (component lists)
+    CK_NSITES = 7
+};
+
+#if defined(DDSG_CHECKED) && defined(__CUDACC__)
+static __device__ unsigned long long g_check_word;   // one per module
+__device__ __forceinline__ bool check_site(bool ok, int site) {
+    if (!ok) atomicOr(&g_check_word, 1ull << site);
+    return ok;
+}
+#define DDSG_CK(cond, site) ::ddsg::check_site((cond), (site))
+#else
+#define DDSG_CK(cond, site) true
+#endif
+
+#if defined(__CUDACC__)
+// tuple_row with the checked-build tests: the cell offset of a presence-mask
+// tuple, the directory index (S entries) and the row against [lo, hi), the
+// rows of the tuple's component.
+__device__ __forceinline__ int32_t tuple_row_at(const DevTup &tu, uint32_t off, const int32_t *slots,
+                                                int64_t S, int32_t lo, int32_t hi) {
+#if defined(DDSG_CHECKED)
+    if (tu.slot_base < 0 ? !DDSG_CK(off < 64u, CK_CELL) : !DDSG_CK((int64_t)tu.slot_base + off < S, CK_SLOT))
+        return -1;
+    const int32_t r = tuple_row(tu, off, slots);
+    return (r < 0 || DDSG_CK(r >= lo && r < hi, CK_ROW)) ? r : -1;
+#else
+    (void)S;
+    (void)lo;
+    (void)hi;
+    return tuple_row(tu, off, slots);
+#endif
+}
+#endif
+
+// Check words of the modules with kernels, read and cleared (host; synchronous).
+// Always 0 in release builds.
+unsigned long long check_word_take_kernels();
+unsigned long long check_word_take_irbc();
+
 struct DevTables {
     int32_t C = 0, T = 0;
     int64_t P = 0, S = 0;
@@ -113,6 +168,24 @@ struct DevTables {
     int32_t max_tuples = 0;                        // most level tuples in one component
     int32_t max_level = 0;                         // highest 1D level present anywhere
 };
+
+#if defined(__CUDACC__)
+// Checked builds: component id c < C, with k <= KMAX and every dimension < d.
+__device__ __forceinline__ bool comp_ok(const DevTables &t, int c, int d) {
+#if defined(DDSG_CHECKED)
+    if (!DDSG_CK(c >= 0 && c < t.C, CK_COMP)) return false;
+    const DevComp &cd = t.comps[c];
+    bool ok = cd.k >= 0 && cd.k <= KMAX;
+    for (int j = 0; ok && j < cd.k; ++j) ok = cd.dims[j] >= 0 && cd.dims[j] < d;
+    return DDSG_CK(ok, CK_DIM);
+#else
+    (void)t;
+    (void)c;
+    (void)d;
+    return true;
+#endif
+}
+#endif
 
 // ---------------------------------------------------------------------------
 // 1D basis on the fixed-point coordinate (boundary-augmented hats, Sec. 3.1)

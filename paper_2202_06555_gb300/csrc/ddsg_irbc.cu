@@ -272,7 +272,7 @@ __device__ int comp_dterms(const DevTables &t, const DevComp &cd, int tb, int dp
             }
         }
         if (!act) continue;
-        const int32_t row = tuple_row(tu, off, t.slots);
+        const int32_t row = tuple_row_at(tu, off, t.slots, t.S, cd.row_begin, cd.row_end);
         if (row < 0) continue;
         if (n == cap) return -1;
         out[n].row = row;
@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(128) irbc_jacobian_kernel(IrbcDev P, int64_t s
     const int mp = t.mp64;
     DTerm terms[3][DT_CAP];
     for (int e = koff[i]; e < koff[i + 1]; ++e) {
+        if (!comp_ok(t, kids[e], 2 * N)) continue;
         const DevComp &cd = t.comps[kids[e]];
         const double coef = paper ? cd.b : 1.0;
         if (coef == 0.0) continue;
@@ -610,7 +611,7 @@ __device__ __forceinline__ void comp_at(const DevTables &t, const DevComp &cd, i
             w *= (double)o.N * ldexp(1.0, -o.e);
         }
         if (!act) continue;
-        const int32_t row = tuple_row(tu, off, t.slots);
+        const int32_t row = tuple_row_at(tu, off, t.slots, t.S, cd.row_begin, cd.row_end);
         if (row < 0) continue;
         const W *r = alpha + (int64_t)row * mp + m0;
         const W ww = (W)w;
@@ -656,6 +657,7 @@ __global__ void __launch_bounds__(128) irbc_delta_kernel(IrbcDev P, int64_t s0, 
     uint64_t Xi[3];
     for (int v = 0; v < 3; ++v) Xi[v] = encode_coord(e3[v], lo[i], span[i], bad, cl);
     for (int e = aoff[i]; e < aoff[i + 1] && !bad; ++e) {
+        if (!comp_ok(t, acomp[e], d)) continue;
         const DevComp &cd = t.comps[acomp[e]];
         const double coef = paper ? cd.b : 1.0;
         if (coef == 0.0) continue;
@@ -1177,3 +1179,21 @@ extern "C" int irbc_profile_read(irbc_t *M, double *ms, int64_t *launches, int r
     M->tr.read(ms, launches, reset != 0);
     return DDSG_OK;
 }
+
+namespace ddsg {
+// Check word of this module, read and cleared (all bits set if it cannot be read).
+unsigned long long check_word_take_irbc() {
+#if defined(DDSG_CHECKED)
+    unsigned long long w = 0;
+    const unsigned long long z = 0;
+    if (cudaMemcpyFromSymbol(&w, g_check_word, sizeof w) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_check_word, &z, sizeof z) != cudaSuccess) {
+        cudaGetLastError();
+        return ~0ull;
+    }
+    return w;
+#else
+    return 0;
+#endif
+}
+}  // namespace ddsg

@@ -242,7 +242,7 @@ __device__ __forceinline__ void comp_generic(const EvalParams &p, const DevComp 
     using W = typename Types<PREC>::W;
     const int k = cd.k;
     uint64_t Xd[KMAX];
-    for (int j = 0; j < k; ++j) Xd[j] = p.X[(int64_t)cd.dims[j] * p.n + q];
+    for (int j = 0; j < k; ++j) Xd[j] = DDSG_CK(cd.dims[j] < p.d, CK_DIM) ? p.X[(int64_t)cd.dims[j] * p.n + q] : 0ull;
     const int tb = paper ? cd.tup_begin : cd.tup_int;
     const W *alpha = Types<PREC>::alpha(p.t);
     const int mp = Types<PREC>::stride(p.t);
@@ -261,7 +261,7 @@ __device__ __forceinline__ void comp_generic(const EvalParams &p, const DevComp 
             w = w * basis_val<W>(o);
         }
         if (!act) continue;
-        const int32_t pid = tuple_row(tu, off, p.t.slots);
+        const int32_t pid = tuple_row_at(tu, off, p.t.slots, p.t.S, cd.row_begin, cd.row_end);
         if (pid < 0) continue;
         if (paper) w = (W)cd.b * w;
         accumulate<PREC, MC>(acc, w, alpha + (int64_t)pid * mp, m0, mp);
@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(128) eval_lq_kernel(const EvalParams p) {
     int32_t cnt = 0;
     const bool paper = p.form == DDSG_FORM_PAPER;
     for (int c = 0; c < p.t.C; ++c) {
+        if (!comp_ok(p.t, c, p.d)) continue;
         const DevComp &cd = p.t.comps[c];
         if (paper && cd.b == 0.0) continue;
         comp_generic<PREC, MC, HC>(p, cd, c, q, paper, m0, r.partial(), h, cnt);
@@ -313,7 +314,8 @@ constexpr int TQ = 128;  // queries per block of the tile kernel
 // device row (-1 if the query's cell holds no point or the query sits on a
 // cell face) and the basis weight (0 when there is no point).
 template <int PREC, int K>
-__device__ __forceinline__ int32_t tile_probe(const DevTup &tu, const int32_t *slots, int tid,
+__device__ __forceinline__ int32_t tile_probe(const DevTup &tu, const int32_t *slots, int64_t S, int32_t lo,
+                                             int32_t hi, int tid,
                                              const uint32_t (*s_cell)[LT][TQ],
                                              const typename Types<PREC>::W (*s_t)[LT][TQ],
                                              typename Types<PREC>::W wb,
@@ -336,7 +338,7 @@ __device__ __forceinline__ int32_t tile_probe(const DevTup &tu, const int32_t *s
             wt = wb * (s_t[0][tu.lev[0] - 1][tid] * s_t[1][tu.lev[1] - 1][tid]);
         }
     }
-    const int32_t row = tuple_row(tu, off, slots);
+    const int32_t row = tuple_row_at(tu, off, slots, S, lo, hi);
     w = row >= 0 ? wt : (W)0;
     return row;
 }
@@ -386,14 +388,19 @@ __device__ __forceinline__ void tile_tuples(const EvalParams &p, int c, int tb, 
     using W = typename T::W;
     const W *alpha = T::alpha(p.t);
     const int mp = T::stride(p.t);
+#if defined(DDSG_CHECKED)
+    const int32_t lo = p.t.comps[c].row_begin, hi = p.t.comps[c].row_end;
+#else
+    const int32_t lo = 0, hi = 0;
+#endif
     for (int ti = tb; ti < te; ti += 2) {
         const bool two = ti + 1 < te;
         const DevTup t0 = p.t.tups[ti];
         const DevTup t1 = p.t.tups[two ? ti + 1 : ti];
         W w0, w1;
         uint32_t c0[2] = {0, 0}, c1[2] = {0, 0};
-        const int32_t r0 = tile_probe<PREC, K>(t0, p.t.slots, tid, s_cell, s_t, wb, w0, c0);
-        int32_t r1 = tile_probe<PREC, K>(t1, p.t.slots, tid, s_cell, s_t, wb, w1, c1);
+        const int32_t r0 = tile_probe<PREC, K>(t0, p.t.slots, p.t.S, lo, hi, tid, s_cell, s_t, wb, w0, c0);
+        int32_t r1 = tile_probe<PREC, K>(t1, p.t.slots, p.t.S, lo, hi, tid, s_cell, s_t, wb, w1, c1);
         if (!two) {
             r1 = -1;
             w1 = (W)0;
@@ -448,7 +455,7 @@ __global__ void __launch_bounds__(TQ) eval_tile_kernel(const EvalParams p) {
             }
             // stage the 1D basis of each dimension, levels 1..lmax
             for (int j = 0; j < k; ++j) {
-                const uint64_t Xv = p.X[(int64_t)cd.dims[j] * p.n + q];
+                const uint64_t Xv = DDSG_CK(cd.dims[j] < p.d, CK_DIM) ? p.X[(int64_t)cd.dims[j] * p.n + q] : 0ull;
                 const int lm = cd.lmax[j];
                 for (int l = 1; l <= lm; ++l) {
                     Basis1D o;
@@ -484,7 +491,11 @@ __global__ void __launch_bounds__(TQ) eval_tile_kernel(const EvalParams p) {
 // copied into shared memory by a bulk TMA copy two components ahead.
 // ---------------------------------------------------------------------------
 
-constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait calls before giving up
+// try_wait calls before a wait gives up. A try_wait that finds the phase still
+// open suspends the thread for about 3.7 us on GB300 (2^22 of them took 15.6 s),
+// so this is about one second: far above any real wait here (a component's
+// staging copy, or the block finishing one component: well under a millisecond).
+constexpr uint32_t kWaitLimit = 1u << 18;
 constexpr int kSmemLimit = 232448;          // opt-in shared memory per block (227 KiB)
 constexpr int TMA_NBUF_MAX = 3;             // staging buffers of the TMA-staged kernel
 constexpr int TMA_PB_MAX = 32;              // tuples probed per pass of the TMA-staged kernel
@@ -626,7 +637,7 @@ __device__ __forceinline__ void tma_stage(uint64_t X, int lm, int qi, uint16_t (
 // the warp-uniform test for a slot-directory tuple. A face flag (bit 15 of a
 // staged cell) masks to cell 0, so off stays inside the tuple's cells.
 template <int PREC, int K, int QB>
-__device__ __forceinline__ int32_t tma_probe(const DevTup &tu, const int32_t *slots, int qi,
+__device__ __forceinline__ int32_t tma_probe(const DevTup &tu, const int32_t *slots, int64_t S, int qi,
                                             const uint16_t (*s_cell)[LT][QB],
                                             const typename Types<PREC>::W (*s_t)[LT][QB],
                                             typename Types<PREC>::W wb, typename Types<PREC>::W &w,
@@ -652,10 +663,10 @@ __device__ __forceinline__ int32_t tma_probe(const DevTup &tu, const int32_t *sl
     int32_t row;
     if (tu.slot_base < 0) {
         const uint32_t o6 = off & 63u;
-        const bool present = !(face & 0x8000u) && ((tu.mask >> o6) & 1ull);
+        const bool present = !(face & 0x8000u) && DDSG_CK(off < 64u, CK_CELL) && ((tu.mask >> o6) & 1ull);
         row = present ? tu.first + __popcll(tu.mask & ((2ull << o6) - 1ull)) - 1 : -1;
     } else {
-        const int32_t s = slots[tu.slot_base + off];
+        const int32_t s = DDSG_CK((int64_t)tu.slot_base + off < S, CK_SLOT) ? slots[tu.slot_base + off] : -1;
         row = (face & 0x8000u) ? -1 : s;
     }
     w = row >= 0 ? wt : (W)0;
@@ -672,7 +683,7 @@ __device__ __forceinline__ void tma_probe_batch(const EvalParams &p, int c, cons
                                                 int du, typename Types<PREC>::W wb, int qi,
                                                 const uint16_t (*s_cell)[LT][QB],
                                                 const typename Types<PREC>::W (*s_t)[LT][QB], int32_t row0,
-                                                int32_t *s_prow, typename Types<PREC>::W *s_pw, uint64_t &h,
+                                                int32_t row_end, int32_t *s_prow, typename Types<PREC>::W *s_pw, uint64_t &h,
                                                 int32_t &cnt) {
     using W = typename Types<PREC>::W;
 #pragma unroll 4
@@ -680,9 +691,15 @@ __device__ __forceinline__ void tma_probe_batch(const EvalParams &p, int c, cons
         const DevTup &tu = stup[u];
         W w;
         uint32_t cl[2] = {0, 0};
-        const int32_t row = tma_probe<PREC, K, QB>(tu, p.t.slots, qi, s_cell, s_t, wb, w, cl);
-        const bool hit = row >= 0;
-        s_prow[u * QB + qi] = (hit ? row : tu.first) - row0;
+        const int32_t row = tma_probe<PREC, K, QB>(tu, p.t.slots, p.t.S, qi, s_cell, s_t, wb, w, cl);
+        const bool hit = row >= 0 && DDSG_CK(row >= row0 && row < row_end, CK_ROW);
+        const int32_t first = DDSG_CK(tu.first >= row0 && tu.first < row_end, CK_ROW) ? tu.first : row0;
+#if defined(DDSG_CHECKED)
+        if (!hit) w = (W)0;
+#else
+        (void)row_end;
+#endif
+        s_prow[u * QB + qi] = (hit ? row : first) - row0;
         s_pw[u * QB + qi] = w;
         if (HC && hit) {
             h ^= point_key(c, K, tu.lev, cl);
@@ -863,6 +880,12 @@ __global__ void __launch_bounds__(TmaShape<GR>::NT, 1) eval_tma_kernel(const Eva
         const uint32_t nrows = (uint32_t)rec.z & 0xfffffu, nt = (uint32_t)rec.z >> 20;
         const uint32_t rbytes = nrows * (uint32_t)mp * (uint32_t)sizeof(W);
         const uint32_t tbytes = nt * (uint32_t)sizeof(DevTup);
+        // (a failed test withholds the copy: the waits on it run out, the block writes NaN)
+        if (!DDSG_CK(rec.x >= 0 && rec.x < p.t.C && nt <= (uint32_t)TMA_TUP_MAX &&
+                         (int64_t)kRowOff + rbytes <= (int64_t)buf_bytes && rec.w >= 0 &&
+                         (int64_t)rec.w + nt <= (int64_t)p.t.T && rec.y >= 0 && (int64_t)rec.y + nrows <= p.t.P,
+                     CK_STAGE))
+            return;
         unsigned char *dst = bufbase + (size_t)b * buf_bytes;
         mbar_expect_tx(&full[b], (uint32_t)sizeof(DevComp) + tbytes + rbytes);
         tma_bulk_g2s(dst, p.t.comps + rec.x, (uint32_t)sizeof(DevComp), &full[b]);
@@ -899,8 +922,8 @@ __global__ void __launch_bounds__(TmaShape<GR>::NT, 1) eval_tma_kernel(const Eva
     uint32_t pd_next = 0;          // dims record of the next component
     if (nproc > 0) {
         const uint32_t pd = pdims[0];
-        Xc0 = p.X[(int64_t)(pd & 0xffffu) * p.n + qc];
-        Xc1 = p.X[(int64_t)(pd >> 16) * p.n + qc];
+        Xc0 = DDSG_CK((pd & 0xffffu) < (uint32_t)p.d, CK_DIM) ? p.X[(int64_t)(pd & 0xffffu) * p.n + qc] : 0ull;
+        Xc1 = DDSG_CK((pd >> 16) < (uint32_t)p.d, CK_DIM) ? p.X[(int64_t)(pd >> 16) * p.n + qc] : 0ull;
     }
     if (nproc > 1) pd_next = pdims[1];
     int b = 0;
@@ -908,8 +931,8 @@ __global__ void __launch_bounds__(TmaShape<GR>::NT, 1) eval_tma_kernel(const Eva
     for (int i = 0; i < nproc; ++i) {
         uint64_t Xn0 = 0, Xn1 = 0;
         if (i + 1 < nproc) {
-            Xn0 = p.X[(int64_t)(pd_next & 0xffffu) * p.n + qc];
-            Xn1 = p.X[(int64_t)(pd_next >> 16) * p.n + qc];
+            Xn0 = DDSG_CK((pd_next & 0xffffu) < (uint32_t)p.d, CK_DIM) ? p.X[(int64_t)(pd_next & 0xffffu) * p.n + qc] : 0ull;
+            Xn1 = DDSG_CK((pd_next >> 16) < (uint32_t)p.d, CK_DIM) ? p.X[(int64_t)(pd_next >> 16) * p.n + qc] : 0ull;
         }
         if (i + 2 < nproc) pd_next = pdims[i + 2];
         const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[b], ph));
@@ -939,9 +962,9 @@ __global__ void __launch_bounds__(TmaShape<GR>::NT, 1) eval_tma_kernel(const Eva
             const int nb = nt - t0 < pb ? nt - t0 : pb;
             group_sync<GR>(qw);   // staged basis visible; the partner is done with s_prow
             if (!bad) {
-                if (k == 2) tma_probe_batch<PREC, 2, HC, QB>(p, c, stup + t0, nb, grp, GR, wb, qi, s_cell, s_t, row0, s_prow, s_pw, h, cnt);
-                else if (k == 1) tma_probe_batch<PREC, 1, HC, QB>(p, c, stup + t0, nb, grp, GR, wb, qi, s_cell, s_t, row0, s_prow, s_pw, h, cnt);
-                else tma_probe_batch<PREC, 0, HC, QB>(p, c, stup + t0, nb, grp, GR, wb, qi, s_cell, s_t, row0, s_prow, s_pw, h, cnt);
+                if (k == 2) tma_probe_batch<PREC, 2, HC, QB>(p, c, stup + t0, nb, grp, GR, wb, qi, s_cell, s_t, row0, cd.row_end, s_prow, s_pw, h, cnt);
+                else if (k == 1) tma_probe_batch<PREC, 1, HC, QB>(p, c, stup + t0, nb, grp, GR, wb, qi, s_cell, s_t, row0, cd.row_end, s_prow, s_pw, h, cnt);
+                else tma_probe_batch<PREC, 0, HC, QB>(p, c, stup + t0, nb, grp, GR, wb, qi, s_cell, s_t, row0, cd.row_end, s_prow, s_pw, h, cnt);
             }
             group_sync<GR>(qw);   // the partner's probes visible
             if (!bad) {
@@ -1156,6 +1179,9 @@ __global__ void __launch_bounds__(128) hierarchize_kernel(const DevTables t, int
             const int pl = w / nchunks;
             const int m0 = (w - pl * nchunks) * HC_CHUNK;
             const int pid = t.layer_pts[lb + pl];
+            if (!DDSG_CK(pid >= 0 && pid < t.P && t.pt_dpos[pid] >= cd.row_begin && t.pt_dpos[pid] < cd.row_end,
+                         CK_POINT))
+                continue;
             uint64_t Xp[KMAX];
             for (int j = 0; j < k; ++j)
                 Xp[j] = node_X(t.pt_lv[(int64_t)j * t.P + pid], t.pt_ix[(int64_t)j * t.P + pid]);
@@ -1175,7 +1201,7 @@ __global__ void __launch_bounds__(128) hierarchize_kernel(const DevTables t, int
                     wv *= basis_to_f64(o.N, o.e);
                 }
                 if (!act) continue;
-                const int32_t q = tuple_row(tu, off, t.slots);
+                const int32_t q = tuple_row_at(tu, off, t.slots, t.S, cd.row_begin, cd.row_end);
                 if (q < 0) continue;
                 const double *a = t.alpha64 + (int64_t)q * mp + m0;
 #pragma unroll
@@ -1242,6 +1268,22 @@ cudaError_t launch_to_f32(const double *a, int mp64, float *b, int mp32, int64_t
     if (blocks > 152 * 32) blocks = 152 * 32;
     to_f32_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, mp64, b, mp32, P, m);
     return cudaGetLastError();
+}
+
+// Check word of this module, read and cleared (all bits set if it cannot be read).
+unsigned long long check_word_take_kernels() {
+#if defined(DDSG_CHECKED)
+    unsigned long long w = 0;
+    const unsigned long long z = 0;
+    if (cudaMemcpyFromSymbol(&w, g_check_word, sizeof w) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_check_word, &z, sizeof z) != cudaSuccess) {
+        cudaGetLastError();
+        return ~0ull;
+    }
+    return w;
+#else
+    return 0;
+#endif
 }
 
 }  // namespace ddsg

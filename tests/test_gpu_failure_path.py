@@ -1,6 +1,6 @@
 """Failure path of the TMA-staged evaluation kernels, exercised without a fault.
 
-Every mbarrier wait in those kernels is bounded (2^22 polls). The test switch
+Every mbarrier wait in those kernels is bounded (2^18 polls, about a second). The test switch
 hdmr_set_fault_injection withholds the staging copies from one processed
 component on, so the waits on them run out. Expected:
   - every query of every block that gave up reads NaN;
