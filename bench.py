@@ -90,9 +90,9 @@ def comp_list(w):
 # kernel at 28 outputs per group), per query; scaled to a full launch by the
 # query count.
 # Valid only for the kernel sources it was taken on (checked by hash).
-EVAL_TRAFFIC = {"workload": "d100", "schedule": (3, 28), "dram_bytes_per_query": (202179328 + 3883776) / 29184,
-                "sha1": {"ddsg_kernels.cu": "bc1d16e9b8ba725f72d730177496e58cf825658e",
-                         "ddsg_internal.h": "b5851db099bf603876353c443b6561fc5cd61795"}}
+EVAL_TRAFFIC = {"workload": "d100", "schedule": (3, 28), "dram_bytes_per_query": (201362176 + 3748352) / 29184,
+                "sha1": {"ddsg_kernels.cu": "ef773b62c5c0c2928f0e37be3d040b7ba7f8b407",
+                         "ddsg_internal.h": "4dbdf87f7d04934a20ec267386c110fcd439a05c"}}
 
 
 def eval_traffic(workload, schedule, n):
@@ -408,10 +408,14 @@ def run_irbc(args, w):
         st = torch.zeros(ns, dtype=torch.int32, device="cuda")
         nr = torch.zeros(ns, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
+        M.profile(True)
+        M.profile_read(reset=True)
         t0 = time.perf_counter()
         M.newton(h, sd, z, 12, tol, it, st, nr, pr, form)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        prof_n = M.profile_read(reset=True)
+        M.profile(False)
         err = torch.zeros((ns, 2), dtype=torch.float64, device="cuda")
         M.set_node_mode(G.NODES_ALL)
         M.residual(h, sd, z, r, None, err, G.F64, form)
@@ -420,7 +424,9 @@ def run_irbc(args, w):
                         "iters_max": int(it.max().item()),
                         "converged": int((st == 0).sum().item()),
                         "euler_error_log10_mean": float(np.log10(np.mean(ee[:, 0]))),
-                        "euler_error_log10_max": float(np.log10(np.max(ee[:, 0])))}
+                        "euler_error_log10_max": float(np.log10(np.max(ee[:, 0]))),
+                        "kernels_ms_total": {kk: vv[0] for kk, vv in prof_n.items()},
+                        "launches": sum(vv[1] for vv in prof_n.values())}
     out = {"metric": metric, "value": value, "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32" if prec == G.F32C else "f64", "data": "synthetic",
