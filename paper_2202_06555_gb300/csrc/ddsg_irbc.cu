@@ -416,9 +416,12 @@ __global__ void __launch_bounds__(128) irbc_jacobian_kernel(IrbcDev P, int64_t s
 // batched dense LU with partial pivoting (FP64, one block per system)
 // ---------------------------------------------------------------------------
 
+// (redo != 0: solve only the systems whose status is 3, the ones the mixed-precision
+// kernel below could not refine, and set their status to 0 or 2)
 __global__ void __launch_bounds__(256) lu_solve_kernel(int n, int64_t ns, const double *__restrict__ Ag,
                                                        const double *__restrict__ bg, const int32_t *active,
-                                                       double *__restrict__ xg, int32_t *__restrict__ status) {
+                                                       double *__restrict__ xg, int32_t *__restrict__ status,
+                                                       int redo) {
     extern __shared__ double sm[];
     double *A = sm;             // n x n
     double *b = sm + n * n;     // n
@@ -427,6 +430,7 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(int n, int64_t ns, const 
     __shared__ int pidx[256];
     const int64_t s = blockIdx.x;
     if (active && !active[s]) return;
+    if (redo && status[s] != 3) return;
     const double *As = Ag + s * (int64_t)n * n;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = As[e];
     for (int e = threadIdx.x; e < n; e += blockDim.x) b[e] = -bg[s * n + e];
@@ -494,6 +498,198 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(int n, int64_t ns, const 
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n; e += blockDim.x) xg[s * n + e] = b[e];
+    if (redo && threadIdx.x == 0) status[s] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// batched LU, mixed precision: factor in FP32 in shared memory, refine in FP64
+// (iterative refinement: solve with the FP32 factors, form the residual
+// b - A x in FP64 from the original matrix, solve for the correction, repeat).
+// On GB300 FP32 arithmetic is far faster than FP64 and the FP32 factors take
+// half the shared memory (two systems per SM). Each system's refinement stops
+// once the correction is below 2^-46 of the solution (FP64 accuracy); a
+// system that does not get there (condition number near 1/u_32 or worse)
+// gets status 3 and is solved again by the FP64 kernel above.
+// ---------------------------------------------------------------------------
+
+constexpr int LUM_THREADS = 256;
+constexpr int LUM_WARPS = LUM_THREADS / 32;
+constexpr int LUM_SOLVES = 6;   // first solve + up to 5 corrections
+
+inline size_t lum_smem_bytes(int n) {
+    const int ld = n | 1;
+    const size_t a = ((size_t)n * ld * sizeof(float) + 15) & ~(size_t)15;
+    return a + (size_t)n * (2 * sizeof(double) + sizeof(float) + sizeof(int));
+}
+
+// max over the block (every thread gets the result); red holds LUM_WARPS values
+__device__ __forceinline__ double lum_block_max(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = red[0];
+    for (int w = 1; w < LUM_WARPS; ++w) r = fmax(r, red[w]);
+    return r;
+}
+
+// y <- U^-1 L^-1 y in place (L unit lower, U upper, both in A with stride ld):
+// 32-row blocks, the diagonal block solved by warp 0 with shuffles, the rest
+// of the rows updated by all threads.
+__device__ __forceinline__ void lum_solve(const float *A, int ld, int n, float *y) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int kb = min(32, n - k0);
+        if (tid < 32) {
+            float v = lane < kb ? y[k0 + lane] : 0.0f;
+            for (int k = 0; k < kb; ++k) {
+                const float yk = __shfl_sync(0xffffffffu, v, k);
+                if (lane > k && lane < kb) v = fmaf(-A[(k0 + lane) * ld + k0 + k], yk, v);
+            }
+            if (lane < kb) y[k0 + lane] = v;
+        }
+        __syncthreads();
+        for (int r = k0 + kb + tid; r < n; r += LUM_THREADS) {
+            float acc = y[r];
+            for (int k = 0; k < kb; ++k) acc = fmaf(-A[r * ld + k0 + k], y[k0 + k], acc);
+            y[r] = acc;
+        }
+        __syncthreads();
+    }
+    for (int k1 = n; k1 > 0; k1 -= 32) {
+        const int k0 = k1 > 32 ? k1 - 32 : 0, kb = k1 - k0;
+        if (tid < 32) {
+            float v = lane < kb ? y[k0 + lane] : 0.0f;
+            for (int k = kb - 1; k >= 0; --k) {
+                if (lane == k) v = v / A[(k0 + k) * ld + k0 + k];
+                const float xk = __shfl_sync(0xffffffffu, v, k);
+                if (lane < k) v = fmaf(-A[(k0 + lane) * ld + k0 + k], xk, v);
+            }
+            if (lane < kb) y[k0 + lane] = v;
+        }
+        __syncthreads();
+        for (int r = tid; r < k0; r += LUM_THREADS) {
+            float acc = y[r];
+            for (int k = 0; k < kb; ++k) acc = fmaf(-A[r * ld + k0 + k], y[k0 + k], acc);
+            y[r] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(LUM_THREADS, 2) lu_mixed_kernel(int n, int64_t ns, const double *__restrict__ Ag,
+                                                                  const double *__restrict__ bg,
+                                                                  const int32_t *__restrict__ active,
+                                                                  double *__restrict__ xg,
+                                                                  int32_t *__restrict__ status) {
+    extern __shared__ float4 lum_raw[];
+    const int ld = n | 1;   // odd row stride: column reads hit distinct banks
+    float *A = reinterpret_cast<float *>(lum_raw);
+    double *x = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(lum_raw) +
+                                           (((size_t)n * ld * sizeof(float) + 15) & ~(size_t)15));
+    double *res = x + n;
+    float *y = reinterpret_cast<float *>(res + n);
+    int *perm = reinterpret_cast<int *>(y + n);
+    __shared__ float pmax[LUM_WARPS];
+    __shared__ int pidx[LUM_WARPS];
+    __shared__ double red[LUM_WARPS];
+    const int64_t s = blockIdx.x;
+    if (active && !active[s]) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double *As = Ag + s * (int64_t)n * n;
+    for (int e = tid; e < n * n; e += LUM_THREADS) {
+        const int r = e / n;
+        A[r * ld + (e - r * n)] = (float)As[e];
+    }
+    for (int r = tid; r < n; r += LUM_THREADS) perm[r] = r;
+    __syncthreads();
+    // factor P A = L U (rows swapped whole, as in LAPACK getrf)
+    bool singular = false;
+    for (int c = 0; c < n; ++c) {
+        // pivot: largest |A[r][c]|, r >= c (ties: smallest r; NaN never wins)
+        float best = -1.0f;
+        int bi = n;
+        for (int r = c + tid; r < n; r += LUM_THREADS) {
+            const float a = fabsf(A[r * ld + c]);
+            if (a > best) { best = a; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float b2 = __shfl_xor_sync(0xffffffffu, best, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (b2 > best || (b2 == best && i2 < bi)) { best = b2; bi = i2; }
+        }
+        if (lane == 0) { pmax[warp] = best; pidx[warp] = bi; }
+        __syncthreads();
+        best = pmax[0];
+        bi = pidx[0];
+        for (int w = 1; w < LUM_WARPS; ++w)
+            if (pmax[w] > best || (pmax[w] == best && pidx[w] < bi)) { best = pmax[w]; bi = pidx[w]; }
+        if (!(best > 0.0f) || bi >= n) { singular = true; break; }
+        if (bi != c) {
+            for (int j = tid; j < n; j += LUM_THREADS) {
+                const float t = A[c * ld + j];
+                A[c * ld + j] = A[bi * ld + j];
+                A[bi * ld + j] = t;
+            }
+            if (tid == 0) {
+                const int t = perm[c];
+                perm[c] = perm[bi];
+                perm[bi] = t;
+            }
+        }
+        __syncthreads();
+        const float inv = 1.0f / A[c * ld + c];
+        for (int r = c + 1 + warp; r < n; r += LUM_WARPS) {
+            const float l = A[r * ld + c] * inv;
+            for (int j = c + 1 + lane; j < n; j += 32) A[r * ld + j] = fmaf(-l, A[c * ld + j], A[r * ld + j]);
+            if (lane == 0) A[r * ld + c] = l;
+        }
+        __syncthreads();
+    }
+    if (singular) {
+        if (tid == 0) status[s] = 2;
+        return;
+    }
+    // the system A x = -r: start from x = 0, residual = -r
+    for (int i = tid; i < n; i += LUM_THREADS) {
+        x[i] = 0.0;
+        res[i] = -bg[s * n + i];
+    }
+    __syncthreads();
+    bool done = false;
+    for (int it = 0; it < LUM_SOLVES && !done; ++it) {
+        // correction d = A^-1 res through the FP32 factors (res scaled to O(1))
+        // (a non-finite entry counts as infinite: fmax alone would skip a NaN)
+        double sc = 0.0;
+        for (int i = tid; i < n; i += LUM_THREADS) sc = fmax(sc, isfinite(res[i]) ? fabs(res[i]) : HUGE_VAL);
+        sc = lum_block_max(sc, red);
+        if (sc == 0.0) { done = true; break; }    // exact
+        if (!(sc < HUGE_VAL)) break;              // non-finite: left to the FP64 kernel
+        for (int i = tid; i < n; i += LUM_THREADS) y[i] = (float)(res[perm[i]] / sc);
+        __syncthreads();
+        lum_solve(A, ld, n, y);
+        double dmax = 0.0, xmax = 0.0;
+        for (int i = tid; i < n; i += LUM_THREADS) {
+            const double d = sc * (double)y[i];
+            x[i] += d;
+            dmax = fmax(dmax, isfinite(d) ? fabs(d) : HUGE_VAL);
+            xmax = fmax(xmax, isfinite(x[i]) ? fabs(x[i]) : HUGE_VAL);
+        }
+        dmax = lum_block_max(dmax, red);
+        xmax = lum_block_max(xmax, red);
+        if (!(xmax < HUGE_VAL)) break;
+        if (dmax <= xmax * 0x1p-46) { done = true; break; }
+        // residual -r - A x in FP64 (a warp per row, lanes along the row)
+        for (int r = warp; r < n; r += LUM_WARPS) {
+            double acc = 0.0;
+            for (int j = lane; j < n; j += 32) acc = fma(As[(int64_t)r * n + j], x[j], acc);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) res[r] = -bg[s * n + r] - acc;
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += LUM_THREADS) xg[s * n + i] = x[i];
+    if (tid == 0) status[s] = done ? 0 : 3;
 }
 
 // ---------------------------------------------------------------------------
@@ -1010,10 +1206,18 @@ extern "C" int irbc_lu_solve(int n, int64_t ns, const double *A_dev, const doubl
     if (ns == 0) return DDSG_OK;
     const size_t smem = sizeof(double) * ((size_t)n * n + n);
     if (smem > 220 * 1024) return set_error(DDSG_ERR_ARG, "irbc_lu_solve: system too large for shared memory (n <= 165)");
+    if (!A_dev || !r_dev || !dx_dev || !status_dev) return set_error(DDSG_ERR_ARG, "irbc_lu_solve: NULL argument");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem_m = lum_smem_bytes(n);
+    cudaError_t e = cudaFuncSetAttribute(lu_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
     if (e == cudaSuccess) {
-        lu_solve_kernel<<<(unsigned)ns, 256, smem, st>>>(n, ns, A_dev, r_dev, nullptr, dx_dev, status_dev);
+        lu_mixed_kernel<<<(unsigned)ns, LUM_THREADS, smem_m, st>>>(n, ns, A_dev, r_dev, nullptr, dx_dev, status_dev);
+        e = cudaGetLastError();
+    }
+    // the systems the FP32 factors could not refine (status 3), again in FP64
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        lu_solve_kernel<<<(unsigned)ns, 256, smem, st>>>(n, ns, A_dev, r_dev, nullptr, dx_dev, status_dev, 1);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return set_error(DDSG_ERR_CUDA, cudaGetErrorString(e));

@@ -136,6 +136,41 @@ def test_lu_solve_batched(G):
             assert st[s] == 0 and np.allclose(A[s] @ dx[s], -r[s], atol=1e-12)
 
 
+def test_lu_solve_n151_mixed_precision_and_fallback(G):
+    """Systems of the N=150 model's size. The FP32 factors with FP64 refinement
+    must reach FP64 backward error. Systems too ill-conditioned for FP32
+    (condition numbers 1e9 and 1e12) must come back just as accurate through
+    the FP64 re-solve, and an exactly singular one must be flagged."""
+    rng = np.random.default_rng(17)
+    n = 151
+    conds = [1.0, 1e2, 1e4, 1e6, 1e9, 1e12]
+    A, R = [], []
+    for i in range(24):
+        c = conds[i % len(conds)]
+        q1, _ = np.linalg.qr(rng.normal(size=(n, n)))
+        q2, _ = np.linalg.qr(rng.normal(size=(n, n)))
+        A.append(q1 @ np.diag(np.logspace(0, -np.log10(c), n)) @ q2 * rng.uniform(0.1, 10.0))
+        R.append(rng.normal(size=n))
+    A.append(rng.normal(size=(n, n)))
+    A[-1][:, 7] = 0.0                      # singular
+    R.append(rng.normal(size=n))
+    A, R = np.array(A), np.array(R)
+    ns = A.shape[0]
+    dx = torch.zeros((ns, n), dtype=torch.float64, device="cuda")
+    st = torch.full((ns,), 9, dtype=torch.int32, device="cuda")
+    G.lu_solve(torch.from_numpy(A).cuda(), torch.from_numpy(R).cuda(), dx, st)
+    torch.cuda.synchronize()
+    dx, st = dx.cpu().numpy(), st.cpu().numpy()
+    assert st[-1] == 2
+    for s in range(ns - 1):
+        assert st[s] == 0, (s, st[s])
+        back = np.abs(A[s] @ dx[s] + R[s]).max() / (np.abs(A[s]).sum(1).max() * np.abs(dx[s]).max() + np.abs(R[s]).max())
+        assert back <= 1e-14, (s, conds[s % len(conds)], back)
+        ref = np.linalg.solve(A[s], -R[s])
+        fwd = np.abs(dx[s] - ref).max() / np.abs(ref).max()
+        assert fwd <= 1e-15 * conds[s % len(conds)] * n, (s, fwd)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_newton_matches_oracle(G, prec):
     N = 5
