@@ -447,9 +447,13 @@ enum { DDSG_IRBC_NODES_ALL = 0, DDSG_IRBC_NODES_DELTA = 1 };
 int irbc_set_irreversible(irbc_t *model, int on);
 int irbc_set_node_mode(irbc_t *model, int mode);
 
-/* Batched dense LU with partial pivoting (FP64): dx = -A^{-1} r for ns
- * systems of size n (A_dev ns x n x n row-major, r_dev/dx_dev ns x n).
- * status_dev[s] is set to 2 for an exactly singular pivot. n <= 165. */
+/* Batched dense LU with partial pivoting: dx = -A^{-1} r for ns systems of
+ * size n (A_dev ns x n x n row-major FP64, r_dev/dx_dev ns x n), to FP64
+ * accuracy. Factored in FP32 and refined in FP64 against A (iterative
+ * refinement); a system the FP32 factors cannot refine (condition number
+ * near 1/u_32 or beyond) is factored again in FP64. status_dev[s]: 0 solved,
+ * 1 solved by the FP64 factorization, 2 exactly singular pivot (dx_dev[s]
+ * undefined). n <= 165. */
 int irbc_lu_solve(int n, int64_t ns, const double *A_dev, const double *r_dev, double *dx_dev,
                   int32_t *status_dev, ddsg_stream_t stream);
 

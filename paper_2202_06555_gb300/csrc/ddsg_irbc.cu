@@ -147,22 +147,30 @@ __global__ void __launch_bounds__(256) irbc_residual_kernel(IrbcDev P, int64_t s
         const double g1 = kp[j] / k[j] - 1.0;
         const double kpa = pow(kp[j], P.alpha - 1.0);
         const double mu = P.irr ? guess[s * m + N + j] : 0.0;
-        double E = 0.0, S1 = 0.0, SM = 0.0, Dd = 0.0;
+        // node sums with the node weight w and the node-independent factors taken
+        // out (FP64 division is slow here: one reciprocal of k'_j per j, none per node)
+        const double ikp = 1.0 / kp[j];
+        const double cA = P.A * P.alpha * kpa;
+        double Es = 0.0, Ms = 0.0, S1s = 0.0, SMs = 0.0, Ds = 0.0;
         for (int q = 0; q < nq; ++q) {
             const double ap = e3[node_variant(q, j, N)];
             const double kpp = ys[(int64_t)q * m + j];
             const double lamp = ys[(int64_t)q * m + L];
-            const double g2 = kpp / kp[j] - 1.0;
-            const double Mq = ap * P.A * P.alpha * kpa + (1.0 - P.delta) + 0.5 * P.phi * g2 * (g2 + 2.0);
-            E += w * lamp * Mq;
-            if (P.irr) E -= w * (1.0 - P.delta) * ys[(int64_t)q * m + N + j];
+            const double g2 = kpp * ikp - 1.0;
+            const double Mq = ap * cA + (1.0 - P.delta) + 0.5 * P.phi * g2 * (g2 + 2.0);
+            Es += lamp * Mq;
+            if (P.irr) Ms += ys[(int64_t)q * m + N + j];
             if (jac) {
-                S1 += w * lamp * 0.5 * P.phi * (2.0 * g2 + 2.0) / kp[j];
-                SM += w * Mq;
-                Dd += w * lamp * (ap * P.A * P.alpha * (P.alpha - 1.0) * kpa / kp[j] +
-                                  0.5 * P.phi * (2.0 * g2 + 2.0) * (-kpp / (kp[j] * kp[j])));
+                S1s += lamp * (g2 + 1.0);
+                SMs += Mq;
+                Ds += lamp * (ap * cA * (P.alpha - 1.0) - P.phi * (g2 + 1.0) * kpp * ikp);
             }
         }
+        // E = sum_q w lambda' M_q (- (1 - delta) w mu'_j when irreversible);
+        // S1 = sum_q w lambda' phi (g2 + 1) / k'_j, SM = sum_q w M_q,
+        // Dd = d/dk'_j of sum_q w lambda' M_q at fixed next-period policy
+        const double E = w * Es - (P.irr ? w * (1.0 - P.delta) * Ms : 0.0);
+        const double S1 = w * P.phi * ikp * S1s, SM = w * SMs, Dd = w * ikp * Ds;
         const double lhs = lam * (1.0 + P.phi * g1) - mu;
         resid[s * m + j] = lhs - P.beta * E;
         emax = fmax(emax, fabs(P.beta * E / lhs - 1.0));
@@ -246,10 +254,30 @@ __device__ __forceinline__ double dhat(uint64_t X, int l, uint32_t &cell) {
 // component dimension; position dpos is the differentiated one): appends
 // (device row, weight) pairs, the weight holding coef (b or 1) and 1/span.
 // Returns the number of terms, or -1 if there were more than cap.
-struct DTerm { int32_t row; double w; };
+// Surplus table and row stride of each evaluation precision: FP64 rows, or
+// the FP32 rows that F32C multiplies in FP32.
+template <int PREC>
+struct DeltaT;
+template <>
+struct DeltaT<DDSG_F64> {
+    using W = double;
+    static __device__ __forceinline__ const double *alpha(const DevTables &t) { return t.alpha64; }
+    static __device__ __forceinline__ int stride(const DevTables &t) { return t.mp64; }
+};
+template <>
+struct DeltaT<DDSG_F32C> {
+    using W = float;
+    static __device__ __forceinline__ const float *alpha(const DevTables &t) { return t.alpha32; }
+    static __device__ __forceinline__ int stride(const DevTables &t) { return t.mp32; }
+};
 
+// (device row, weight) of one term; the weight in the precision the terms are summed in
+template <class W>
+struct DTerm { int32_t row; W w; };
+
+template <class W>
 __device__ int comp_dterms(const DevTables &t, const DevComp &cd, int tb, int dpos, const uint64_t *Xd,
-                           double scale, DTerm *out, int cap) {
+                           double scale, DTerm<W> *out, int cap) {
     int n = 0;
     for (int ti = tb; ti < cd.tup_end; ++ti) {
         const DevTup tu = t.tups[ti];
@@ -276,7 +304,7 @@ __device__ int comp_dterms(const DevTables &t, const DevComp &cd, int tb, int dp
         if (row < 0) continue;
         if (n == cap) return -1;
         out[n].row = row;
-        out[n].w = wt;
+        out[n].w = (W)wt;
         ++n;
     }
     return n;
@@ -284,7 +312,7 @@ __device__ int comp_dterms(const DevTables &t, const DevComp &cd, int tb, int dp
 
 constexpr int DT_CAP = 48;
 
-// One thread per column i < N of each state's Jacobian (d r_j / d k'_i, j < N).
+// Jacobian columns d r_j / d k'_i (j < N) of each state, one block per state.
 // k'_i enters the next-period policy through every component holding dim
 // N+i. For such a component u the coordinates of u at a node are the base
 // ones (no shock on u's country, if any) except at the nodes shocking u's
@@ -292,124 +320,269 @@ constexpr int DT_CAP = 48;
 // its slope in k'_i takes at most three values over the 2(N+1) nodes, and the
 // node sum splits into the base sum (total minus the four shocked nodes) plus
 // those four. Components holding k_i and more than one a-dimension make the
-// column NaN (the host refuses such sets).
-__global__ void __launch_bounds__(128) irbc_jacobian_kernel(IrbcDev P, int64_t s0, int64_t nsc,
-                                                            DevTables t, int form,
-                                                            const int32_t *__restrict__ koff,
-                                                            const int32_t *__restrict__ kids,
-                                                            const double *__restrict__ lo,
-                                                            const double *__restrict__ span,
-                                                            const double *__restrict__ guess,
-                                                            const double *__restrict__ y,
-                                                            const double *__restrict__ aux,
-                                                            double *__restrict__ jac) {
+// column NaN (the host refuses such sets), and so does a column whose
+// derivative terms do not fit the shared pool.
+// Phase 1: a thread per (column i, component) group finds the derivative terms
+// (device row, weight) of each of its up to three variants and appends them to
+// a shared pool. Phase 2: a warp per column, lanes over the outputs j, sums
+// weight x surplus row over each variant's terms, so every term's row is read
+// coalesced, and adds the node factors of output j.
+// PREC: F64 sums the derivative terms in FP64 from the FP64 surpluses; F32C
+// multiplies and sums them in FP32 from the FP32 surpluses (Newton needs the
+// Jacobian only to FP32 accuracy; the residual itself stays FP64).
+constexpr int JAC_THREADS = 256;
+constexpr int JAC_KJ = 6;   // outputs per lane: N <= 32 * JAC_KJ = 192
+
+struct JGroup {
+    int32_t i, ctry, nv, off[3], cnt[3];
+    double dPN[3];
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, int64_t s0, int64_t nsc,
+                                                                   DevTables t, int form,
+                                                                   const int32_t *__restrict__ koff,
+                                                                   const int32_t *__restrict__ kids,
+                                                                   const double *__restrict__ lo,
+                                                                   const double *__restrict__ span,
+                                                                   const double *__restrict__ guess,
+                                                                   const double *__restrict__ y,
+                                                                   const double *__restrict__ aux,
+                                                                   double *__restrict__ jac, int pool_cap) {
+    using W = typename DeltaT<PREC>::W;
     const int N = P.N, m = P.m, nq = 2 * (N + 1);
     const int L = m - 1;   // lambda's position in the policy
-    const int64_t sl = blockIdx.x;                      // state within the chunk (grid.x: no 65535 limit)
+    const int64_t sl = blockIdx.x;   // state within the chunk (grid.x: no 65535 limit)
     const int64_t s = s0 + sl;
-    const int i = blockIdx.y * blockDim.x + threadIdx.x;
-    if (i >= N) return;
     const bool paper = form == DDSG_FORM_PAPER;
     const double *kp = guess + s * m;
     const double *ax = aux + sl * 7 * (int64_t)N;
     const double *ys = y + sl * nq * (int64_t)m;
     double *J = jac + s * (int64_t)m * m;
     const double w = 1.0 / (double)nq;
-    const int dk = N + i;
-    for (int j = 0; j < N; ++j) J[(int64_t)j * m + i] = j == i ? ax[2 * N + j] : 0.0;
-    // k'_i in canonical units; clamped (or at the top face) -> zero derivative
-    const double ck = (kp[i] - lo[dk]) / span[dk];
-    if (!(ck >= 0.0 && ck < 1.0)) return;
-    bool bad = false;
-    unsigned long long cl = 0;
-    const uint64_t Xk = encode_coord(kp[i], lo[dk], span[dk], bad, cl);
-    const int mp = t.mp64;
-    DTerm terms[3][DT_CAP];
-    for (int e = koff[i]; e < koff[i + 1]; ++e) {
-        if (!comp_ok(t, kids[e], 2 * N)) continue;
-        const DevComp &cd = t.comps[kids[e]];
-        const double coef = paper ? cd.b : 1.0;
-        if (coef == 0.0) continue;
-        const int tb = paper ? cd.tup_begin : cd.tup_int;
-        uint64_t Xd[KMAX];
-        int dpos = 0, apos = -1, ctry = -1, na = 0;
-        for (int j = 0; j < cd.k; ++j) {
-            const int dim = cd.dims[j];
-            if (dim == dk) {
-                dpos = j;
-                Xd[j] = Xk;
-            } else if (dim < N) {
-                apos = j;
-                ctry = dim;
-                ++na;
-                Xd[j] = encode_coord(ax[3 * N + dim], lo[dim], span[dim], bad, cl);
-            } else {
-                Xd[j] = encode_coord(kp[dim - N], lo[dim], span[dim], bad, cl);
-            }
-        }
-        int nt[3] = {0, 0, 0};
-        const int nv = na == 0 ? 1 : 3;
-        bool over = na > 1;
-        for (int v = 0; v < nv && !over; ++v) {
-            if (v > 0) Xd[apos] = encode_coord(ax[(3 + v) * N + ctry], lo[ctry], span[ctry], bad, cl);
-            nt[v] = comp_dterms(t, cd, tb, dpos, Xd, coef / span[dk], terms[v], DT_CAP);
-            if (nt[v] < 0) over = true;
-        }
-        if (over) {
-            for (int j = 0; j < N; ++j) J[(int64_t)j * m + i] = NAN;
-            return;
-        }
-        // node pieces of the shocked nodes of u's country: +: 2c, 2N ; -: 2c+1, 2N+1
-        double dPN[3];
-        for (int v = 0; v < nv; ++v) {
-            double acc = 0.0;
-            for (int q = 0; q < nt[v]; ++q) acc += terms[v][q].w * t.alpha64[(int64_t)terms[v][q].row * mp + L];
-            dPN[v] = acc;
-        }
-        for (int j = 0; j < N; ++j) {
-            double dP[3];
-            for (int v = 0; v < nv; ++v) {
-                double acc = 0.0;
-                for (int q = 0; q < nt[v]; ++q) acc += terms[v][q].w * t.alpha64[(int64_t)terms[v][q].row * mp + j];
-                dP[v] = acc;
-            }
-            const double S1 = ax[0 * N + j], SM = ax[1 * N + j];
-            double v0;
-            if (nv == 1) {
-                v0 = -P.beta * (S1 * dP[0] + SM * dPN[0]);
-            } else {
-                const double kpa = ax[6 * N + j];
-                double s1[4], sM[4];
-                const int qs[4] = {2 * ctry, 2 * N, 2 * ctry + 1, 2 * N + 1};
-                for (int u = 0; u < 4; ++u) {
-                    const int q = qs[u];
-                    const double kpp = ys[(int64_t)q * m + j];
-                    const double lamp = ys[(int64_t)q * m + L];
-                    const double g2 = kpp / kp[j] - 1.0;
-                    const double ap = ax[(3 + node_variant(q, j, N)) * N + j];
-                    s1[u] = w * lamp * 0.5 * P.phi * (2.0 * g2 + 2.0) / kp[j];
-                    sM[u] = w * (ap * P.A * P.alpha * kpa + (1.0 - P.delta) + 0.5 * P.phi * g2 * (g2 + 2.0));
-                }
-                const double s1b = S1 - s1[0] - s1[1] - s1[2] - s1[3];
-                const double sMb = SM - sM[0] - sM[1] - sM[2] - sM[3];
-                v0 = -P.beta * (s1b * dP[0] + (s1[0] + s1[1]) * dP[1] + (s1[2] + s1[3]) * dP[2] +
-                                sMb * dPN[0] + (sM[0] + sM[1]) * dPN[1] + (sM[2] + sM[3]) * dPN[2]);
-            }
-            if (P.irr) {
-                // (1 - delta) mu'_j inside the expectation: its slope in k'_i at the nodes
-                double dM[3];
-                for (int v = 0; v < nv; ++v) {
-                    double acc = 0.0;
-                    for (int q = 0; q < nt[v]; ++q)
-                        acc += terms[v][q].w * t.alpha64[(int64_t)terms[v][q].row * mp + N + j];
-                    dM[v] = acc;
-                }
-                const double sumw = nv == 1 ? nq * w * dM[0] : w * ((nq - 4) * dM[0] + 2.0 * dM[1] + 2.0 * dM[2]);
-                v0 += P.beta * (1.0 - P.delta) * sumw;
-            }
-            J[(int64_t)j * m + i] += v0;
+    const W *alpha = DeltaT<PREC>::alpha(t);
+    const int mp = DeltaT<PREC>::stride(t);
+    const int G = koff[N];
+    extern __shared__ float4 jac_raw[];
+    JGroup *grp = reinterpret_cast<JGroup *>(jac_raw);
+    int32_t *colstate = reinterpret_cast<int32_t *>(grp + G);   // 0 normal, 1 clamped, 2 NaN
+    // per output j, in W: S1, SM, 1/k'_j, A alpha k'^(alpha-1), and s1, sM at the
+    // two global-shock nodes 2N (+) and 2N+1 (-), which every column shares
+    W *oj = reinterpret_cast<W *>(reinterpret_cast<unsigned char *>(jac_raw) +
+                                  ((sizeof(JGroup) * G + sizeof(int32_t) * N + 15) & ~(size_t)15));
+    W *oS1 = oj, *oSM = oj + N, *oik = oj + 2 * N, *ocA = oj + 3 * N;
+    W *os1p = oj + 4 * N, *osMp = oj + 5 * N, *os1m = oj + 6 * N, *osMm = oj + 7 * N;
+    DTerm<W> *pool = reinterpret_cast<DTerm<W> *>(
+        reinterpret_cast<unsigned char *>(oj) + ((sizeof(W) * 8 * N + 15) & ~(size_t)15));
+    __shared__ int cursor;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) cursor = 0;
+    for (int i = tid; i < N; i += JAC_THREADS) {
+        // k'_i in canonical units; clamped (or at the top face) -> zero derivative
+        const double ck = (kp[i] - lo[N + i]) / span[N + i];
+        colstate[i] = (ck >= 0.0 && ck < 1.0) ? 0 : 1;
+        const int j = i;
+        const double ik = 1.0 / kp[j], cA = P.A * P.alpha * ax[6 * N + j];
+        oS1[j] = (W)ax[0 * N + j];
+        oSM[j] = (W)ax[1 * N + j];
+        oik[j] = (W)ik;
+        ocA[j] = (W)cA;
+        for (int u = 0; u < 2; ++u) {
+            const int q = 2 * N + u;   // global node: every a' shocked, variant 1 (+) or 2 (-)
+            const double kpp = ys[(int64_t)q * m + j], lamp = ys[(int64_t)q * m + L];
+            const double g2 = kpp * ik - 1.0;
+            const double s1 = w * lamp * P.phi * (g2 + 1.0) * ik;
+            const double sM = w * (ax[(4 + u) * N + j] * cA + (1.0 - P.delta) + 0.5 * P.phi * g2 * (g2 + 2.0));
+            (u == 0 ? os1p : os1m)[j] = (W)s1;
+            (u == 0 ? osMp : osMm)[j] = (W)sM;
         }
     }
+    __syncthreads();
+    // phase 1: the terms of every (column, component) group
+    for (int g = tid; g < G; g += JAC_THREADS) {
+        int lo_i = 0, hi_i = N;   // column i: koff[i] <= g < koff[i + 1]
+        while (hi_i - lo_i > 1) {
+            const int mid = (lo_i + hi_i) >> 1;
+            if (koff[mid] <= g) lo_i = mid; else hi_i = mid;
+        }
+        const int i = lo_i, dk = N + i;
+        JGroup gr;
+        gr.i = i;
+        gr.ctry = -1;
+        gr.nv = 0;
+        for (int v = 0; v < 3; ++v) { gr.off[v] = 0; gr.cnt[v] = 0; gr.dPN[v] = 0.0; }
+        if (colstate[i] == 0 && comp_ok(t, kids[g], 2 * N)) {
+            const DevComp &cd = t.comps[kids[g]];
+            const double coef = paper ? cd.b : 1.0;
+            if (coef != 0.0) {
+                bool bad = false;
+                unsigned long long cl = 0;
+                const int tb = paper ? cd.tup_begin : cd.tup_int;
+                uint64_t Xd[KMAX];
+                int dpos = 0, apos = -1, ctry = -1, na = 0;
+                for (int j = 0; j < cd.k; ++j) {
+                    const int dim = cd.dims[j];
+                    if (dim == dk) {
+                        dpos = j;
+                        Xd[j] = encode_coord(kp[i], lo[dk], span[dk], bad, cl);
+                    } else if (dim < N) {
+                        apos = j;
+                        ctry = dim;
+                        ++na;
+                        Xd[j] = encode_coord(ax[3 * N + dim], lo[dim], span[dim], bad, cl);
+                    } else {
+                        Xd[j] = encode_coord(kp[dim - N], lo[dim], span[dim], bad, cl);
+                    }
+                }
+                const int nv = na == 0 ? 1 : 3;
+                bool over = na > 1;
+                DTerm<W> loc[DT_CAP];
+                for (int v = 0; v < nv && !over; ++v) {
+                    if (v > 0) Xd[apos] = encode_coord(ax[(3 + v) * N + ctry], lo[ctry], span[ctry], bad, cl);
+                    const int nt = comp_dterms(t, cd, tb, dpos, Xd, coef / span[dk], loc, DT_CAP);
+                    if (nt < 0) { over = true; break; }
+                    const int off = atomicAdd(&cursor, nt);
+                    if (off + nt > pool_cap) { over = true; break; }
+                    W acc = (W)0;
+                    for (int q = 0; q < nt; ++q) {
+                        pool[off + q] = loc[q];
+                        acc += loc[q].w * alpha[(int64_t)loc[q].row * mp + L];
+                    }
+                    gr.off[v] = off;
+                    gr.cnt[v] = nt;
+                    gr.dPN[v] = (double)acc;
+                }
+                if (over) {
+                    colstate[i] = 2;
+                } else {
+                    gr.nv = nv;
+                    gr.ctry = ctry;
+                }
+            }
+        }
+        grp[g] = gr;
+    }
+    __syncthreads();
+    // phase 2: a warp per column i, lane outputs j = lane + 32 k; the node
+    // factors in W (FP32 in the F32C mode, like the derivative sums)
+    const W beta = (W)P.beta, phi = (W)P.phi, ww = (W)w, omd = (W)(1.0 - P.delta);
+    for (int i = warp; i < N; i += JAC_THREADS / 32) {
+        const int cs = colstate[i];
+        double acc[JAC_KJ];
+#pragma unroll
+        for (int kk = 0; kk < JAC_KJ; ++kk) acc[kk] = 0.0;
+        if (cs == 0) {
+            for (int g = koff[i]; g < koff[i + 1]; ++g) {
+                const JGroup &gr = grp[g];
+                const int nv = gr.nv;
+                if (nv == 0) continue;
+                // dPv[kk] = sum over the terms of variant v of weight x surplus row at output j
+                // (dMv: at output N + j, the multiplier mu'_j of the irreversible model)
+                W dP0[JAC_KJ], dP1[JAC_KJ], dP2[JAC_KJ], dM0[JAC_KJ], dM1[JAC_KJ], dM2[JAC_KJ];
+                auto sumv = [&](int v, W (&oP)[JAC_KJ], W (&oM)[JAC_KJ]) {
+                    W a1[JAC_KJ], a2[JAC_KJ];
+#pragma unroll
+                    for (int kk = 0; kk < JAC_KJ; ++kk) { a1[kk] = (W)0; a2[kk] = (W)0; }
+                    for (int q = 0; q < gr.cnt[v]; ++q) {
+                        const DTerm<W> tq = pool[gr.off[v] + q];
+                        const W *row = alpha + (int64_t)tq.row * mp;
+#pragma unroll
+                        for (int kk = 0; kk < JAC_KJ; ++kk) {
+                            const int j = lane + 32 * kk;
+                            if (j < N) {
+                                a1[kk] += tq.w * row[j];
+                                if (P.irr) a2[kk] += tq.w * row[N + j];
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < JAC_KJ; ++kk) { oP[kk] = a1[kk]; oM[kk] = a2[kk]; }
+                };
+                sumv(0, dP0, dM0);
+                if (nv == 3) {
+                    sumv(1, dP1, dM1);
+                    sumv(2, dP2, dM2);
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < JAC_KJ; ++kk) dP1[kk] = dP2[kk] = dM1[kk] = dM2[kk] = (W)0;
+                }
+                const int ctry = gr.ctry;
+                const W dPN0 = (W)gr.dPN[0], dPN1 = (W)gr.dPN[1], dPN2 = (W)gr.dPN[2];
+#pragma unroll
+                for (int kk = 0; kk < JAC_KJ; ++kk) {
+                    const int j = lane + 32 * kk;
+                    if (j >= N) continue;
+                    W v0;
+                    if (nv == 1) {
+                        v0 = -beta * (oS1[j] * dP0[kk] + oSM[j] * dPN0);
+                    } else {
+                        // the country nodes of u's country c: 2c (a'_c at +) and 2c+1 (-);
+                        // a'_j moves there only when j = c. The global nodes come from oj.
+                        const W ik = oik[j], cA = ocA[j];
+                        W s1c[2], sMc[2];
+                        for (int u = 0; u < 2; ++u) {
+                            const int q = 2 * ctry + u;
+                            const W kpp = (W)ys[(int64_t)q * m + j];
+                            const W lamp = (W)ys[(int64_t)q * m + L];
+                            const W g2 = kpp * ik - (W)1;
+                            const W ap = (W)ax[(j == ctry ? 4 + u : 3) * N + j];
+                            s1c[u] = ww * lamp * phi * (g2 + (W)1) * ik;
+                            sMc[u] = ww * (ap * cA + omd + (W)0.5 * phi * g2 * (g2 + (W)2));
+                        }
+                        const W s1P = s1c[0] + os1p[j], s1M = s1c[1] + os1m[j];
+                        const W sMP = sMc[0] + osMp[j], sMM = sMc[1] + osMm[j];
+                        const W s1b = oS1[j] - s1P - s1M, sMb = oSM[j] - sMP - sMM;
+                        v0 = -beta * (s1b * dP0[kk] + s1P * dP1[kk] + s1M * dP2[kk] + sMb * dPN0 + sMP * dPN1 + sMM * dPN2);
+                    }
+                    if (P.irr) {
+                        // (1 - delta) mu'_j inside the expectation: its slope in k'_i at the nodes
+                        const W sumw = nv == 1 ? (W)nq * ww * dM0[kk]
+                                               : ww * ((W)(nq - 4) * dM0[kk] + (W)2 * dM1[kk] + (W)2 * dM2[kk]);
+                        v0 += beta * omd * sumw;
+                    }
+                    acc[kk] += (double)v0;
+                }
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < JAC_KJ; ++kk) {
+            const int j = lane + 32 * kk;
+            if (j < N) J[(int64_t)j * m + i] = cs == 2 ? NAN : (j == i ? ax[2 * N + j] : 0.0) + acc[kk];
+        }
+    }
+}
+
+// Shared memory of the Jacobian kernel: the groups, the column states and a
+// term pool of up to kJacSmem bytes in all (worst case: DT_CAP terms per
+// group and variant; a column whose terms do not fit is NaN).
+constexpr size_t kJacSmem = 160 * 1024;
+
+static cudaError_t launch_jacobian(int precision, const IrbcDev &P, int64_t s0, int64_t nsc, const DevTables &t,
+                                   int form, int G, const int32_t *koff, const int32_t *kids, const double *lo,
+                                   const double *span, const double *guess, const double *y, const double *aux,
+                                   double *jac, cudaStream_t st) {
+    const size_t wsz = precision == DDSG_F64 ? sizeof(double) : sizeof(float);
+    const size_t fixed = ((sizeof(JGroup) * G + sizeof(int32_t) * P.N + 15) & ~(size_t)15) +
+                         ((wsz * 8 * P.N + 15) & ~(size_t)15);
+    const size_t term = precision == DDSG_F64 ? sizeof(DTerm<double>) : sizeof(DTerm<float>);
+    if (fixed + 64 * term > kJacSmem) return cudaErrorInvalidValue;
+    const size_t worst = (size_t)G * 3 * DT_CAP;
+    const size_t cap = std::min(worst, (kJacSmem - fixed) / term);
+    const size_t smem = fixed + cap * term;
+    cudaError_t e;
+    if (precision == DDSG_F64) {
+        e = cudaFuncSetAttribute(irbc_jacobian_kernel<DDSG_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            irbc_jacobian_kernel<DDSG_F64><<<(unsigned)nsc, JAC_THREADS, smem, st>>>(
+                P, s0, nsc, t, form, koff, kids, lo, span, guess, y, aux, jac, (int)cap);
+    } else {
+        e = cudaFuncSetAttribute(irbc_jacobian_kernel<DDSG_F32C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            irbc_jacobian_kernel<DDSG_F32C><<<(unsigned)nsc, JAC_THREADS, smem, st>>>(
+                P, s0, nsc, t, form, koff, kids, lo, span, guess, y, aux, jac, (int)cap);
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -417,7 +590,7 @@ __global__ void __launch_bounds__(128) irbc_jacobian_kernel(IrbcDev P, int64_t s
 // ---------------------------------------------------------------------------
 
 // (redo != 0: solve only the systems whose status is 3, the ones the mixed-precision
-// kernel below could not refine, and set their status to 0 or 2)
+// kernel below could not refine, and set their status to 1 (solved here) or 2)
 __global__ void __launch_bounds__(256) lu_solve_kernel(int n, int64_t ns, const double *__restrict__ Ag,
                                                        const double *__restrict__ bg, const int32_t *active,
                                                        double *__restrict__ xg, int32_t *__restrict__ status,
@@ -498,7 +671,7 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(int n, int64_t ns, const 
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n; e += blockDim.x) xg[s * n + e] = b[e];
-    if (redo && threadIdx.x == 0) status[s] = 0;
+    if (redo && threadIdx.x == 0) status[s] = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -507,14 +680,16 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(int n, int64_t ns, const 
 // b - A x in FP64 from the original matrix, solve for the correction, repeat).
 // On GB300 FP32 arithmetic is far faster than FP64 and the FP32 factors take
 // half the shared memory (two systems per SM). Each system's refinement stops
-// once the correction is below 2^-46 of the solution (FP64 accuracy); a
-// system that does not get there (condition number near 1/u_32 or worse)
-// gets status 3 and is solved again by the FP64 kernel above.
+// once the correction is below 2^-46 of the solution (FP64 accuracy). The
+// corrections shrink by about cond(A) u_32 per step; a system whose
+// correction stops halving, or that needs more than LUM_SOLVES solves
+// (condition number near 1/u_32 or worse), gets status 3 and is solved again
+// by the FP64 kernel above.
 // ---------------------------------------------------------------------------
 
 constexpr int LUM_THREADS = 256;
 constexpr int LUM_WARPS = LUM_THREADS / 32;
-constexpr int LUM_SOLVES = 6;   // first solve + up to 5 corrections
+constexpr int LUM_SOLVES = 12;  // first solve + up to 11 corrections (each must halve the last)
 
 inline size_t lum_smem_bytes(int n) {
     const int ld = n | 1;
@@ -657,6 +832,7 @@ __global__ void __launch_bounds__(LUM_THREADS, 2) lu_mixed_kernel(int n, int64_t
     }
     __syncthreads();
     bool done = false;
+    double dprev = HUGE_VAL;
     for (int it = 0; it < LUM_SOLVES && !done; ++it) {
         // correction d = A^-1 res through the FP32 factors (res scaled to O(1))
         // (a non-finite entry counts as infinite: fmax alone would skip a NaN)
@@ -679,6 +855,8 @@ __global__ void __launch_bounds__(LUM_THREADS, 2) lu_mixed_kernel(int n, int64_t
         xmax = lum_block_max(xmax, red);
         if (!(xmax < HUGE_VAL)) break;
         if (dmax <= xmax * 0x1p-46) { done = true; break; }
+        if (it > 0 && !(dmax <= 0.5 * dprev)) break;   // not converging: left to FP64
+        dprev = dmax;
         // residual -r - A x in FP64 (a warp per row, lanes along the row)
         for (int r = warp; r < n; r += LUM_WARPS) {
             double acc = 0.0;
@@ -709,6 +887,14 @@ __global__ void norms_kernel(int n, int64_t ns, const double *__restrict__ r, do
     }
     n2[s] = sqrt(a);
     ninf[s] = b;
+}
+
+// z[s] = zt[s] for the states whose trial point was accepted
+__global__ void accept_kernel(int n, int64_t ns, const int32_t *__restrict__ acc, const double *__restrict__ zt,
+                              double *__restrict__ z) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ns * n) return;
+    if (acc[e / n]) z[e] = zt[e];
 }
 
 __global__ void trial_kernel(int n, int64_t ns, const double *__restrict__ z, const double *__restrict__ dz,
@@ -769,21 +955,6 @@ __global__ void irbc_queries3_kernel(IrbcDev P, int64_t ns, const double *__rest
     for (int o = 16; o > 0; o >>= 1) clamps += __shfl_down_sync(0xffffffffu, clamps, o);
     if ((threadIdx.x & 31) == 0 && clamps) atomicAdd(&stats[0], clamps);
 }
-
-template <int PREC>
-struct DeltaT;
-template <>
-struct DeltaT<DDSG_F64> {
-    using W = double;
-    static __device__ __forceinline__ const double *alpha(const DevTables &t) { return t.alpha64; }
-    static __device__ __forceinline__ int stride(const DevTables &t) { return t.mp64; }
-};
-template <>
-struct DeltaT<DDSG_F32C> {
-    using W = float;
-    static __device__ __forceinline__ const float *alpha(const DevTables &t) { return t.alpha32; }
-    static __device__ __forceinline__ int stride(const DevTables &t) { return t.mp32; }
-};
 
 // acc[o] += coef * s_c(x)[m0 + o] for one component c at coordinates Xd (one per
 // component dimension), the tuples [tb, te) (interior ones in the slice-free form).
@@ -915,6 +1086,8 @@ struct irbc {
     double *gamma_d = nullptr, *tau_d = nullptr;
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    void *nws = nullptr;      // Newton buffers (kept between solves)
+    size_t nws_bytes = 0;
 };
 
 namespace {
@@ -1050,6 +1223,7 @@ extern "C" int irbc_destroy(irbc_t *M) {
     cudaFree(M->gamma_d);
     cudaFree(M->tau_d);
     cudaFree(M->ws);
+    cudaFree(M->nws);
     delete M;
     return DDSG_OK;
 }
@@ -1093,6 +1267,11 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
     int32_t *koff_dev = nullptr, *kids_dev = nullptr;
     if (jac_dev) {
         if ((rc = k_components(policy, N, koff, kids))) return rc;
+        if (N > 32 * JAC_KJ)
+            return set_error(DDSG_ERR_ARG, "euler_residual: the Jacobian supports N <= 192");
+        if (((sizeof(JGroup) * kids.size() + sizeof(int32_t) * N + 15) & ~(size_t)15) +
+                ((sizeof(double) * 8 * N + 15) & ~(size_t)15) + 64 * sizeof(DTerm<double>) > kJacSmem)
+            return set_error(DDSG_ERR_ARG, "euler_residual: too many components hold a k dimension for the Jacobian");
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const bool delta = M->node_mode == DDSG_IRBC_NODES_DELTA;
@@ -1190,10 +1369,8 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
         }
         if (e == cudaSuccess && jac_dev) {
             Tracer::Scope ts(&M->tr, 3, st);
-            dim3 grid((unsigned)nsc, (unsigned)((N + 127) / 128));
-            irbc_jacobian_kernel<<<grid, 128, 0, st>>>(P, s0, nsc, *v.tables, form, koff_dev, kids_dev, v.lo,
-                                                       v.span, guess_dev, y, aux, jac_dev);
-            e = cudaGetLastError();
+            e = launch_jacobian(precision, P, s0, nsc, *v.tables, form, (int)kids.size(), koff_dev, kids_dev, v.lo,
+                                v.span, guess_dev, y, aux, jac_dev, st);
         }
         if (e != cudaSuccess) return set_error(DDSG_ERR_CUDA, cudaGetErrorString(e));
     }
@@ -1242,12 +1419,18 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
     // sub-buffer sizes, each rounded to 256 bytes; the block is exactly their sum
     const size_t szv = rnd(bytes((size_t)ns * n)), szJ = rnd(bytes((size_t)ns * n * n)),
                  szs = rnd(bytes((size_t)ns)), szi = rnd(sizeof(int32_t) * (size_t)ns);
-    const size_t tot = 4 * szv + szJ + 5 * szs + 2 * szi;
-    void *blk = nullptr;
-    if (dev_alloc(&blk, tot) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(DDSG_ERR_OOM, "irbc_newton: buffers unavailable");
+    const size_t tot = 4 * szv + szJ + 5 * szs + 3 * szi;
+    if (tot > M->nws_bytes) {
+        cudaFree(M->nws);
+        M->nws = nullptr;
+        M->nws_bytes = 0;
+        if (dev_alloc(&M->nws, tot) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(DDSG_ERR_OOM, "irbc_newton: buffers unavailable");
+        }
+        M->nws_bytes = tot;
     }
+    void *blk = M->nws;
     unsigned char *p = static_cast<unsigned char *>(blk);
     auto take = [&](size_t rounded) { unsigned char *q = p; p += rounded; return q; };
     r = (double *)take(szv);
@@ -1262,10 +1445,9 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
     step = (double *)take(szs);
     active = (int32_t *)take(szi);
     stat = (int32_t *)take(szi);
-    if ((size_t)(p - static_cast<unsigned char *>(blk)) != tot) {
-        cudaFree(blk);
+    int32_t *accd = (int32_t *)take(szi);
+    if ((size_t)(p - static_cast<unsigned char *>(blk)) != tot)
         return set_error(DDSG_ERR_STATE, "irbc_newton: internal buffer layout mismatch");
-    }
     std::vector<double> h_n2(ns), h_ninf(ns), h_n2t(ns), h_step(ns);
     std::vector<int32_t> h_active(ns, 1), h_iters(ns, 0), h_stat(ns, 1);   // 1 = max-iter until converged
     int rc = DDSG_OK;
@@ -1346,12 +1528,15 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
                 }
             }
             if (na) {
-                // copy accepted trial points into the solution
-                for (int64_t s = 0; s < ns; ++s)
-                    if (acc[s]) {
-                        e = cudaMemcpyAsync(sol_dev + s * n, zt + s * n, bytes(n), cudaMemcpyDeviceToDevice, st);
-                        if (e != cudaSuccess) break;
-                    }
+                // copy accepted trial points into the solution (acc is read before the
+                // stream reaches the next host synchronization, so it must outlive the copy)
+                e = cudaMemcpyAsync(accd, acc.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st);
+                if (e == cudaSuccess) {
+                    Tracer::Scope ts(&M->tr, 5, st);
+                    accept_kernel<<<(unsigned)((ns * n + 255) / 256), 256, 0, st>>>(n, ns, accd, zt, sol_dev);
+                    e = cudaGetLastError();
+                }
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
                 if (e != cudaSuccess) { fail_cuda(e); break; }
             }
         }
@@ -1368,7 +1553,6 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) fail_cuda(e);
     }
-    cudaFree(blk);
     return rc;
 }
 

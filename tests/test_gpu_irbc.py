@@ -163,7 +163,11 @@ def test_lu_solve_n151_mixed_precision_and_fallback(G):
     dx, st = dx.cpu().numpy(), st.cpu().numpy()
     assert st[-1] == 2
     for s in range(ns - 1):
-        assert st[s] == 0, (s, st[s])
+        c = conds[s % len(conds)]
+        if c <= 1e2 or c >= 1e9:
+            assert st[s] == (1 if c >= 1e9 else 0), (s, c, st[s])   # 1: the FP64 re-solve ran
+        else:
+            assert st[s] in (0, 1), (s, c, st[s])
         back = np.abs(A[s] @ dx[s] + R[s]).max() / (np.abs(A[s]).sum(1).max() * np.abs(dx[s]).max() + np.abs(R[s]).max())
         assert back <= 1e-14, (s, conds[s % len(conds)], back)
         ref = np.linalg.solve(A[s], -R[s])
