@@ -122,7 +122,10 @@ __global__ void irbc_queries_kernel(IrbcDev P, int64_t ns, const double *__restr
 // 0 <= mu_j _|_ k'_j - (1 - delta) k_j >= 0 as the Fischer-Burmeister equation
 // mu + I - sqrt(mu^2 + I^2) = 0; row m - 1: the resource constraint (eq. model2).
 // aux (per state, 7 x N): S1, SM, Dd, e0, ep, em, kp^(alpha-1).
-__global__ void __launch_bounds__(256) irbc_residual_kernel(IrbcDev P, int64_t s0, int64_t nsc,
+// Block: RES_THREADS at most (N rounded up to a warp), threads over countries j.
+constexpr int RES_THREADS = 256;
+
+__global__ void __launch_bounds__(RES_THREADS) irbc_residual_kernel(IrbcDev P, int64_t s0, int64_t nsc,
                                                             const double *__restrict__ states,
                                                             const double *__restrict__ guess,
                                                             const double *__restrict__ y,
@@ -148,22 +151,34 @@ __global__ void __launch_bounds__(256) irbc_residual_kernel(IrbcDev P, int64_t s
         const double kpa = pow(kp[j], P.alpha - 1.0);
         const double mu = P.irr ? guess[s * m + N + j] : 0.0;
         // node sums with the node weight w and the node-independent factors taken
-        // out (FP64 division is slow here: one reciprocal of k'_j per j, none per node)
+        // out (FP64 is GB300's slow unit: one reciprocal of k'_j per j, none per
+        // node). With r = k''_j / k'_j (g2 = r - 1):
+        //   M_q = a' A alpha k'^(alpha-1) + (1 - delta) + phi/2 (r^2 - 1),
+        //   d/dk'_j [lambda' M_q] at fixed next-period policy
+        //       = lambda' (a' A alpha (alpha-1) k'^(alpha-1) - phi r^2) / k'_j,
+        // the a'-dependent constants taken once per shock variant.
         const double ikp = 1.0 / kp[j];
         const double cA = P.A * P.alpha * kpa;
+        const double hphi = 0.5 * P.phi;
+        const double mb0 = e3[0] * cA + ((1.0 - P.delta) - hphi), mb1 = e3[1] * cA + ((1.0 - P.delta) - hphi),
+                     mb2 = e3[2] * cA + ((1.0 - P.delta) - hphi);
+        const double db0 = e3[0] * cA * (P.alpha - 1.0), db1 = e3[1] * cA * (P.alpha - 1.0),
+                     db2 = e3[2] * cA * (P.alpha - 1.0);
         double Es = 0.0, Ms = 0.0, S1s = 0.0, SMs = 0.0, Ds = 0.0;
+#pragma unroll 4
         for (int q = 0; q < nq; ++q) {
-            const double ap = e3[node_variant(q, j, N)];
+            const int vv = node_variant(q, j, N);
             const double kpp = ys[(int64_t)q * m + j];
             const double lamp = ys[(int64_t)q * m + L];
-            const double g2 = kpp * ikp - 1.0;
-            const double Mq = ap * cA + (1.0 - P.delta) + 0.5 * P.phi * g2 * (g2 + 2.0);
-            Es += lamp * Mq;
+            const double r = kpp * ikp;
+            const double hr = hphi * r;
+            const double Mq = fma(hr, r, vv == 0 ? mb0 : (vv == 1 ? mb1 : mb2));
+            Es = fma(lamp, Mq, Es);
             if (P.irr) Ms += ys[(int64_t)q * m + N + j];
             if (jac) {
-                S1s += lamp * (g2 + 1.0);
+                S1s = fma(lamp, r, S1s);
                 SMs += Mq;
-                Ds += lamp * (ap * cA * (P.alpha - 1.0) - P.phi * (g2 + 1.0) * kpp * ikp);
+                Ds = fma(lamp, fma(-2.0 * hr, r, vv == 0 ? db0 : (vv == 1 ? db1 : db2)), Ds);
             }
         }
         // E = sum_q w lambda' M_q (- (1 - delta) w mu'_j when irreversible);
@@ -207,29 +222,37 @@ __global__ void __launch_bounds__(256) irbc_residual_kernel(IrbcDev P, int64_t s
             ax[6 * N + j] = kpa;
         }
     }
-    // block reductions (sum / max) in a fixed order
-    __shared__ double red[4][256];
-    red[0][threadIdx.x] = res;
-    red[1][threadIdx.x] = ysum;
-    red[2][threadIdx.x] = emax;
-    red[3][threadIdx.x] = dlam;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            red[0][threadIdx.x] += red[0][threadIdx.x + o];
-            red[1][threadIdx.x] += red[1][threadIdx.x + o];
-            red[2][threadIdx.x] = fmax(red[2][threadIdx.x], red[2][threadIdx.x + o]);
-            red[3][threadIdx.x] += red[3][threadIdx.x + o];
-        }
-        __syncthreads();
+    // block reductions (sum / max) in a fixed order: warp butterflies, then the
+    // warps' partials in warp order (any block size that is a multiple of 32)
+    __shared__ double red[4][RES_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        res += __shfl_xor_sync(0xffffffffu, res, o);
+        ysum += __shfl_xor_sync(0xffffffffu, ysum, o);
+        emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        dlam += __shfl_xor_sync(0xffffffffu, dlam, o);
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = res;
+        red[1][warp] = ysum;
+        red[2][warp] = emax;
+        red[3][warp] = dlam;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        resid[s * m + L] = red[0][0];
-        if (err) {
-            err[s * 2 + 0] = red[2][0];
-            err[s * 2 + 1] = fabs(red[0][0]) / red[1][0];
+        double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+        for (int wq = 0; wq < (int)(blockDim.x >> 5); ++wq) {
+            r0 += red[0][wq];
+            r1 += red[1][wq];
+            r2 = fmax(r2, red[2][wq]);
+            r3 += red[3][wq];
         }
-        if (jac) jac[s * (int64_t)m * m + (int64_t)L * m + L] = red[3][0];
+        resid[s * m + L] = r0;
+        if (err) {
+            err[s * 2 + 0] = r2;
+            err[s * 2 + 1] = fabs(r0) / r1;
+        }
+        if (jac) jac[s * (int64_t)m * m + (int64_t)L * m + L] = r3;
     }
 }
 
@@ -689,6 +712,7 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(int n, int64_t ns, const 
 
 constexpr int LUM_THREADS = 256;
 constexpr int LUM_WARPS = LUM_THREADS / 32;
+constexpr int LUM_KJ = 6;       // pivot-row entries per lane: n <= 192
 constexpr int LUM_SOLVES = 12;  // first solve + up to 11 corrections (each must halve the last)
 
 inline size_t lum_smem_bytes(int n) {
@@ -814,9 +838,22 @@ __global__ void __launch_bounds__(LUM_THREADS, 2) lu_mixed_kernel(int n, int64_t
         }
         __syncthreads();
         const float inv = 1.0f / A[c * ld + c];
+        // this lane's entries of the pivot row, j = c + 1 + lane + 32 kk, held in
+        // registers for the whole column (n <= 32 * LUM_KJ)
+        float prow[LUM_KJ];
+#pragma unroll
+        for (int kk = 0; kk < LUM_KJ; ++kk) {
+            const int j = c + 1 + lane + 32 * kk;
+            prow[kk] = j < n ? A[c * ld + j] : 0.0f;
+        }
         for (int r = c + 1 + warp; r < n; r += LUM_WARPS) {
             const float l = A[r * ld + c] * inv;
-            for (int j = c + 1 + lane; j < n; j += 32) A[r * ld + j] = fmaf(-l, A[c * ld + j], A[r * ld + j]);
+#pragma unroll
+            for (int kk = 0; kk < LUM_KJ; ++kk) {
+                const int j = c + 1 + lane + 32 * kk;
+                if (j < n) A[r * ld + j] = fmaf(-l, prow[kk], A[r * ld + j]);
+            }
+            __syncwarp();   // every lane has read A[r][c] before it becomes the multiplier
             if (lane == 0) A[r * ld + c] = l;
         }
         __syncthreads();
@@ -992,7 +1029,11 @@ __device__ __forceinline__ void comp_at(const DevTables &t, const DevComp &cd, i
 // nodes that shock country i (2i: +, 2i+1: -) is the no-shock policy plus the
 // change of every component holding a_i when a'_i moves to its shocked value;
 // also copies the two global-shock rows. Writes the 2(N+1)-node policy array y
-// in the layout the residual and Jacobian kernels read.
+// in the layout the residual and Jacobian kernels read. The three values of
+// a'_i are taken one after another (no shock, +, -), so a thread holds two
+// accumulator chunks, not three.
+constexpr int DLT_MC = 32;   // outputs per thread
+
 template <int PREC, int MC>
 __global__ void __launch_bounds__(128) irbc_delta_kernel(IrbcDev P, int64_t s0, int64_t nsc, DevTables t,
                                                          int form, const int32_t *__restrict__ aoff,
@@ -1012,55 +1053,49 @@ __global__ void __launch_bounds__(128) irbc_delta_kernel(IrbcDev P, int64_t s0, 
     const int m0 = blockIdx.y * MC;
     const int mv = min(MC, m - m0);
     const bool paper = form == DDSG_FORM_PAPER;
-    W acc[3][MC];
-#pragma unroll
-    for (int v = 0; v < 3; ++v)
-#pragma unroll
-        for (int o = 0; o < MC; ++o) acc[v][o] = (W)0;
     bool bad = false;
     unsigned long long cl = 0;
     double e3[3];
     next_a3(P, states[s * d + i], e3[0], e3[1], e3[2]);
     uint64_t Xi[3];
     for (int v = 0; v < 3; ++v) Xi[v] = encode_coord(e3[v], lo[i], span[i], bad, cl);
-    for (int e = aoff[i]; e < aoff[i + 1] && !bad; ++e) {
-        if (!comp_ok(t, acomp[e], d)) continue;
-        const DevComp &cd = t.comps[acomp[e]];
-        const double coef = paper ? cd.b : 1.0;
-        if (coef == 0.0) continue;
-        const int tb = paper ? cd.tup_begin : cd.tup_int;
-        uint64_t Xd[KMAX];
-        int pos = 0;
-        for (int j = 0; j < cd.k; ++j) {
-            const int dj = cd.dims[j];
-            if (dj == i) {
-                pos = j;
-                Xd[j] = 0;
-            } else if (dj < N) {
-                double f0, fp, fm;
-                next_a3(P, states[s * d + dj], f0, fp, fm);
-                Xd[j] = encode_coord(f0, lo[dj], span[dj], bad, cl);
-            } else {
-                Xd[j] = encode_coord(guess[s * m + dj - N], lo[dj], span[dj], bad, cl);
-            }
-        }
-        if (bad) break;
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            Xd[pos] = Xi[v];
-            comp_at<PREC, MC>(t, cd, tb, coef, Xd, m0, mv, acc[v]);
-        }
-    }
     const double *yb = y3 + (sl * 3) * (int64_t)m + m0;
-    double *yp = y + (sl * nq + 2 * i) * (int64_t)m + m0;
-    double *ym = y + (sl * nq + 2 * i + 1) * (int64_t)m + m0;
+    // the components holding a_i at a'_i = value v (0 no shock, 1 +, 2 -), into acc
+    auto sweep = [&](int v, W (&acc)[MC]) {
 #pragma unroll
-    for (int o = 0; o < MC; ++o) {
-        if (o < mv) {
-            const double b0 = (double)acc[0][o];
-            yp[o] = bad ? NAN : yb[o] + ((double)acc[1][o] - b0);
-            ym[o] = bad ? NAN : yb[o] + ((double)acc[2][o] - b0);
+        for (int o = 0; o < MC; ++o) acc[o] = (W)0;
+        for (int e = aoff[i]; e < aoff[i + 1] && !bad; ++e) {
+            if (!comp_ok(t, acomp[e], d)) continue;
+            const DevComp &cd = t.comps[acomp[e]];
+            const double coef = paper ? cd.b : 1.0;
+            if (coef == 0.0) continue;
+            const int tb = paper ? cd.tup_begin : cd.tup_int;
+            uint64_t Xd[KMAX];
+            for (int j = 0; j < cd.k; ++j) {
+                const int dj = cd.dims[j];
+                if (dj == i) {
+                    Xd[j] = Xi[v];
+                } else if (dj < N) {
+                    double f0, fp, fm;
+                    next_a3(P, states[s * d + dj], f0, fp, fm);
+                    Xd[j] = encode_coord(f0, lo[dj], span[dj], bad, cl);
+                } else {
+                    Xd[j] = encode_coord(guess[s * m + dj - N], lo[dj], span[dj], bad, cl);
+                }
+            }
+            if (bad) break;
+            comp_at<PREC, MC>(t, cd, tb, coef, Xd, m0, mv, acc);
         }
+    };
+    W acc0[MC];
+    sweep(0, acc0);
+    for (int v = 1; v < 3; ++v) {
+        W acc[MC];
+        sweep(v, acc);
+        double *yo = y + (sl * nq + 2 * i + (v - 1)) * (int64_t)m + m0;
+#pragma unroll
+        for (int o = 0; o < MC; ++o)
+            if (o < mv) yo[o] = bad ? NAN : yb[o] + ((double)acc[o] - (double)acc0[o]);
     }
     if (i == 0) {
         for (int o = 0; o < mv; ++o) {
@@ -1176,14 +1211,14 @@ int a_components(hdmr_t *h, int N, std::vector<int32_t> &off, std::vector<int32_
     return DDSG_OK;
 }
 
-template <int PREC, int MC>
+template <int PREC>
 cudaError_t launch_delta(const IrbcDev &P, int64_t s0, int64_t nsc, const DevTables &t, int form,
                          const int32_t *aoff, const int32_t *acomp, const double *states, const double *guess,
                          const double *lo, const double *span, const double *y3, double *y, cudaStream_t st) {
     const int m = P.m;
-    dim3 grid((unsigned)((nsc * P.N + 127) / 128), (unsigned)((m + MC - 1) / MC));
-    irbc_delta_kernel<PREC, MC><<<grid, 128, 0, st>>>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span,
-                                                       y3, y);
+    dim3 grid((unsigned)((nsc * P.N + 127) / 128), (unsigned)((m + DLT_MC - 1) / DLT_MC));
+    irbc_delta_kernel<PREC, DLT_MC><<<grid, 128, 0, st>>>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span,
+                                                          y3, y);
     return cudaGetLastError();
 }
 
@@ -1355,15 +1390,16 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
         if (e == cudaSuccess && delta) {
             Tracer::Scope ts(&M->tr, 6, st);
             if (precision == DDSG_F64)
-                e = launch_delta<DDSG_F64, 16>(P, s0, nsc, *v.tables, form, aoff_dev, acomp_dev, states_dev,
+                e = launch_delta<DDSG_F64>(P, s0, nsc, *v.tables, form, aoff_dev, acomp_dev, states_dev,
                                                guess_dev, v.lo, v.span, y3, y, st);
             else
-                e = launch_delta<DDSG_F32C, 16>(P, s0, nsc, *v.tables, form, aoff_dev, acomp_dev, states_dev,
+                e = launch_delta<DDSG_F32C>(P, s0, nsc, *v.tables, form, aoff_dev, acomp_dev, states_dev,
                                                 guess_dev, v.lo, v.span, y3, y, st);
         }
         if (e == cudaSuccess) {
             Tracer::Scope ts(&M->tr, 2, st);
-            irbc_residual_kernel<<<(unsigned)nsc, 256, 0, st>>>(P, s0, nsc, states_dev, guess_dev, y, resid_dev,
+            const int rt = std::min(RES_THREADS, (N + 31) / 32 * 32);
+            irbc_residual_kernel<<<(unsigned)nsc, rt, 0, st>>>(P, s0, nsc, states_dev, guess_dev, y, resid_dev,
                                                                euler_err_dev, jac_dev, aux);
             e = cudaGetLastError();
         }
