@@ -45,6 +45,10 @@ WORKLOADS = {
     # 150 (a_j, k_j) pairs on regular level-4 grids; 1e4 states x 302 monomial nodes
     "irbc150": dict(d=300, m=151, N=150, level=4, states=10_000, wid=synth.W_IRBC150,
                     precision="f32c", form="slicefree"),
+    # the Newton solve of the same model alone: node shortcut, F32C interpolation, FP64
+    # residual and solves, from the initial guess to ||r||_inf <= 1e-6 (1e-10 in FP64)
+    "irbc150newton": dict(d=300, m=151, N=150, level=4, states=10_000, wid=synth.W_IRBC150,
+                          precision="f32c", form="slicefree"),
     # learned warm start: N = 20 (d = 40, m = 21), 1e6 training pairs, 5e4 test states
     "warmstart20": dict(d=40, m=21, N=20, level=4, states=50_000, train=1_000_000,
                         wid=synth.W_IRBC20, precision="f64", form="slicefree", epochs=10,
@@ -443,6 +447,104 @@ def run_irbc(args, w):
     return 0
 
 
+def run_irbc_newton(args, w):
+    """Newton solves of the N = 150 model at w["states"] states (node shortcut):
+    warm-up solves, then timed solves, each from the same initial guess; one more
+    traced solve gives the per-kernel split."""
+    N, m, d = w["N"], w["m"], w["d"]
+    tol = 1e-6 if w["precision"] == "f32c" else 1e-10
+    metric = "Newton solve time at N=150 (node shortcut; FP64 residual and solves)"
+    t1, lam, fn, comps, S, g = irbc_workload(w)
+    ns = S.shape[0]
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return 0
+        import oracle as O
+        E = O.irbc_policy_ddsg(N, w["level"], fn)
+        I = O.IRBCOracle(N)
+        per = 1
+        for _ in range(args.warmup):
+            I.newton(E, S[:per], g[:per], tol=tol)
+        times = []
+        for s in range(args.steps):
+            t0 = time.perf_counter()
+            I.newton(E, S[s * per:(s + 1) * per], g[s * per:(s + 1) * per], tol=tol)
+            times.append(time.perf_counter() - t0)
+        ms = 1e3 * statistics.mean(times) * ns / per   # scaled to the workload's states
+        print(json.dumps({"impl": "reference", "metric": metric, "value": ms, "unit": "ms",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "irbc150_newton", "states": ns},
+                          "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                                           "sample": f"{per} state per step, scaled to {ns} states"},
+                          "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return 0
+    import torch
+    import paper_2202_06555_gb300 as G
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    G.load()
+    h = G.HDMR(d, m, 2, lo=np.full(d, 0.8), hi=np.full(d, 1.2))
+    for u in comps:
+        h.add_regular(list(u), w["level"])
+    vals = np.concatenate([fn(u, h.component_points(c)[2]) for c, u in enumerate(comps)])
+    h.hierarchize(torch.from_numpy(vals).cuda())
+    M = G.IRBC(**t1)
+    M.set_node_mode(G.NODES_DELTA)
+    prec = G.F32C if w["precision"] == "f32c" else G.F64
+    form = G.FORM_SLICEFREE if w["form"] == "slicefree" else G.FORM_PAPER
+    sd = torch.from_numpy(S).cuda()
+    g0 = torch.from_numpy(g).cuda()
+    z = torch.empty_like(g0)
+    it = torch.zeros(ns, dtype=torch.int32, device="cuda")
+    st = torch.zeros_like(it)
+    nr = torch.zeros(ns, dtype=torch.float64, device="cuda")
+
+    def solve():
+        z.copy_(g0)
+        M.newton(h, sd, z, 12, tol, it, st, nr, prec, form)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    times = []
+    with ClockSampler(None) as clk:
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times)
+    M.profile(True)
+    M.profile_read(reset=True)
+    solve()
+    torch.cuda.synchronize()
+    prof = M.profile_read(reset=True)
+    M.profile(False)
+    err = torch.zeros((ns, 2), dtype=torch.float64, device="cuda")
+    r = torch.zeros((ns, m), dtype=torch.float64, device="cuda")
+    M.set_node_mode(G.NODES_ALL)
+    M.residual(h, sd, z, r, None, err, G.F64, form)
+    ee = err.cpu().numpy()
+    print(json.dumps({"metric": metric, "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f32" if prec == G.F32C else "f64", "data": "synthetic",
+                      "config": {"workload": "irbc150_newton", "N": N, "states": ns, "tol": tol,
+                                 "precision": w["precision"], "form": w["form"], "node_mode": "shortcut"},
+                      "iters_mean": float(it.double().mean().item()), "converged": int((st == 0).sum().item()),
+                      "euler_error_log10_mean": float(np.log10(np.mean(ee[:, 0]))),
+                      "euler_error_log10_max": float(np.log10(np.max(ee[:, 0]))),
+                      "kernels_ms": {kk: vv[0] for kk, vv in prof.items()},
+                      "gpu_launches": sum(vv[1] for vv in prof.values()),
+                      "clocks": clk.summary()}), flush=True)
+    return 0
+
+
 def run_time_iteration(args, w):
     """Adaptive DDSG time iteration of the smooth IRBC model on the GPU: per step
     the seconds, grid points, Newton solves and the Euler errors at test states."""
@@ -650,6 +752,10 @@ def main():
     args.warmup = max(args.warmup, 3) if args.impl == "ddsg" else args.warmup
     if args.workload == "irbc150":
         return run_irbc(args, w)
+    if args.workload == "irbc150newton":
+        if args.queries:
+            w["states"] = args.queries
+        return run_irbc_newton(args, w)
     if args.workload == "warmstart20":
         return run_warmstart(args, w)
     if args.workload in ("ti10", "ti6irr", "ti50"):
