@@ -507,6 +507,21 @@ int mlp_infer(mlp_t *net, int64_t B, const double *x_dev, double *y_dev, ddsg_st
 int64_t mlp_num_params(const mlp_t *net);
 int mlp_get_params(mlp_t *net, float *host);
 int mlp_get_grads(mlp_t *net, float *host);
+
+/*
+ * mlp_save / mlp_load -- checkpoint / resume of a network (no paper
+ * counterpart): layer sizes, normalization, FP32 master weights, both Adam
+ * moments and the Adam step count, in one versioned file ending in an FNV-1a
+ * checksum. A loaded network continues training where the saved one stopped:
+ * the same further steps give the same weights bit for bit. mlp_save
+ * synchronizes the device; mlp_load makes no CUDA call (the network binds at
+ * its first GPU use). A missing, foreign, truncated or corrupt file is
+ * DDSG_ERR_ARG. mlp_shape: the layer count and the L+1 widths (sizes_host
+ * nullable).
+ */
+int mlp_save(mlp_t *net, const char *path);
+int mlp_load(const char *path, mlp_t **out);
+int mlp_shape(const mlp_t *net, int32_t *nlayers, int32_t *sizes_host);
 /* Kernel timing: kinds 0 forward GEMMs, 1 backward GEMMs, 2 loss/normalization, 3 Adam. */
 int mlp_profile(mlp_t *net, int enable);
 int mlp_profile_read(mlp_t *net, double *ms_host, int64_t *launches_host, int reset);

@@ -62,6 +62,9 @@ SIGNATURES = {
     "hdmr_check": (_int, [_p, _p]),
     "ddsg_inject_alloc_failure": (_int, [_int, _int]),
     "ddsg_checked_build": (_int, []),
+    "mlp_save": (_int, [_p, C.c_char_p]),
+    "mlp_load": (_int, [C.c_char_p, _p]),
+    "mlp_shape": (_int, [_p, _p, _p]),
     "ddsg_take_check_word": (_int, [_p]),
     "hdmr_load": (_int, [C.c_char_p, _p]),
     "hdmr_shape": (_int, [_p, _p, _p, _p, _p, _p, _p]),
@@ -537,6 +540,25 @@ class MLP:
         except Exception:
             pass
 
+    def save(self, path: str):
+        """Checkpoint: sizes, normalization, weights, Adam moments and step (mlp_save)."""
+        _check(load().mlp_save(self._h, os.fsencode(path)), "mlp_save")
+
+    @classmethod
+    def load(cls, path: str) -> "MLP":
+        """A network recreated from an mlp_save file; training resumes exactly."""
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.mlp_load(os.fsencode(path), C.byref(h)), "mlp_load")
+        self = cls.__new__(cls)
+        self._h = h
+        L = C.c_int32()
+        _check(lib.mlp_shape(h, C.byref(L), None), "mlp_shape")
+        sz = np.zeros(L.value + 1, np.int32)
+        _check(lib.mlp_shape(h, None, _np_ptr(sz)), "mlp_shape")
+        self.sizes = [int(s) for s in sz]
+        return self
+
     def train_step(self, x_dev, y_dev, lr: float, loss_dev=None, stream=None):
         _check(load().mlp_train_step(self._h, x_dev.shape[0], _dev_ptr(x_dev), _dev_ptr(y_dev),
                                      float(lr), _dev_ptr(loss_dev), _stream_ptr(stream)), "mlp_train_step")
@@ -555,10 +577,14 @@ class MLP:
             off += no
         return W, b
 
-    def params(self):
+    def flat_params(self):
+        """FP32 parameters in the packed layout of mlp_create / mlp_save."""
         flat = np.zeros(load().mlp_num_params(self._h), np.float32)
         _check(load().mlp_get_params(self._h, _np_ptr(flat)), "mlp_get_params")
-        return self._unpack(flat)
+        return flat
+
+    def params(self):
+        return self._unpack(self.flat_params())
 
     def grads(self):
         flat = np.zeros(load().mlp_num_params(self._h), np.float32)

@@ -18,6 +18,7 @@
 
 #include "ddsg_alloc.h"
 #include "ddsg_internal.h"
+#include "ddsg_io.h"
 
 using namespace ddsg;
 
@@ -745,37 +746,8 @@ namespace {
 constexpr char kMagic[8] = {'D', 'D', 'S', 'G', 'H', 'D', 'M', 'R'};
 constexpr uint32_t kFileVersion = 1;
 
-uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t hsh = 0xcbf29ce484222325ull) {
-    for (size_t i = 0; i < n; ++i) {
-        hsh ^= p[i];
-        hsh *= 0x100000001b3ull;
-    }
-    return hsh;
-}
-
-struct Writer {
-    std::vector<unsigned char> buf;
-    template <typename T>
-    void put(const T *v, size_t n) {
-        const unsigned char *b = reinterpret_cast<const unsigned char *>(v);
-        buf.insert(buf.end(), b, b + sizeof(T) * n);
-    }
-    template <typename T>
-    void put1(T v) { put(&v, 1); }
-};
-
-struct Reader {
-    const unsigned char *p, *end;
-    bool ok = true;
-    template <typename T>
-    bool get(T *v, size_t n) {
-        const size_t b = sizeof(T) * n;
-        if (!ok || (size_t)(end - p) < b) return ok = false;
-        memcpy(v, p, b);
-        p += b;
-        return true;
-    }
-};
+using io::Reader;
+using io::Writer;
 
 }  // namespace
 
@@ -786,10 +758,7 @@ extern "C" int hdmr_save(const hdmr_t *h, const char *path) {
     int rc = hdmr_get_surpluses(h, alpha.data(), nullptr);
     if (rc) return rc;
     Writer w;
-    w.put(kMagic, 8);
-    w.put1<uint32_t>(kFileVersion);
-    w.put1<uint32_t>(0);
-    const size_t body = w.buf.size();
+    w.header(kMagic, kFileVersion);
     w.put1<int32_t>(h->d);
     w.put1<int32_t>(h->m);
     w.put1<int32_t>(h->order);
@@ -808,35 +777,24 @@ extern "C" int hdmr_save(const hdmr_t *h, const char *path) {
         }
     }
     w.put(alpha.data(), alpha.size());
-    w.put1<uint64_t>(fnv1a(w.buf.data() + body, w.buf.size() - body));
-    FILE *f = fopen(path, "wb");
-    if (!f) return fail(DDSG_ERR_ARG, "hdmr_save: cannot open %s", path);
-    const size_t wr = fwrite(w.buf.data(), 1, w.buf.size(), f);
-    const int cl = fclose(f);
-    if (wr != w.buf.size() || cl != 0) return fail(DDSG_ERR_ARG, "hdmr_save: write to %s failed", path);
+    w.seal();
+    if (!io::write_file(path, w.buf)) return fail(DDSG_ERR_ARG, "hdmr_save: write to %s failed", path);
     return DDSG_OK;
 }
 
 extern "C" int hdmr_load(const char *path, hdmr_t **out) {
     if (!path || !out) return fail(DDSG_ERR_ARG, "hdmr_load: NULL argument");
     *out = nullptr;
-    FILE *f = fopen(path, "rb");
-    if (!f) return fail(DDSG_ERR_ARG, "hdmr_load: cannot open %s", path);
     std::vector<unsigned char> buf;
-    unsigned char chunk[1 << 16];
-    size_t got;
-    while ((got = fread(chunk, 1, sizeof chunk, f)) > 0) buf.insert(buf.end(), chunk, chunk + got);
-    fclose(f);
-    if (buf.size() < 16 + 8 || memcmp(buf.data(), kMagic, 8) != 0)
-        return fail(DDSG_ERR_ARG, "hdmr_load: %s is not an expansion file", path);
+    if (!io::read_file(path, buf)) return fail(DDSG_ERR_ARG, "hdmr_load: cannot open %s", path);
+    Reader r{nullptr, nullptr};
     uint32_t version = 0;
-    memcpy(&version, buf.data() + 8, 4);
-    if (version != kFileVersion) return fail(DDSG_ERR_ARG, "hdmr_load: unsupported file version %u", version);
-    uint64_t sum = 0;
-    memcpy(&sum, buf.data() + buf.size() - 8, 8);
-    if (fnv1a(buf.data() + 16, buf.size() - 16 - 8) != sum)
-        return fail(DDSG_ERR_ARG, "hdmr_load: checksum mismatch (truncated or corrupt file)");
-    Reader r{buf.data() + 16, buf.data() + buf.size() - 8};
+    switch (io::open_body(buf, kMagic, kFileVersion, r, &version)) {
+        case 1: return fail(DDSG_ERR_ARG, "hdmr_load: %s is not an expansion file", path);
+        case 2: return fail(DDSG_ERR_ARG, "hdmr_load: unsupported file version %u", version);
+        case 3: return fail(DDSG_ERR_ARG, "hdmr_load: checksum mismatch (truncated or corrupt file)");
+        default: break;
+    }
     int32_t d = 0, m = 0, order = 0, nc = 0;
     int64_t P = 0;
     r.get(&d, 1);

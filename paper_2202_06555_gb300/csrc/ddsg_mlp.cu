@@ -19,6 +19,7 @@
 
 #include "ddsg_alloc.h"
 #include "ddsg_internal.h"
+#include "ddsg_io.h"
 
 using namespace ddsg;
 
@@ -297,6 +298,7 @@ struct mlp {
     std::vector<__nv_bfloat16 *> Wb, WbT;
     double *in_shift = nullptr, *in_scale = nullptr, *out_shift = nullptr, *out_scale = nullptr;
     std::vector<float> init;      // packed FP32 parameters before upload
+    std::vector<float> init_m, init_v;   // packed Adam moments before upload (empty: zero)
     std::vector<double> norm;     // in_shift, in_scale, out_shift, out_scale
     int64_t step = 0;
     // batch workspace
@@ -343,17 +345,20 @@ int mlp_bind(mlp *M) {
                   alloc((void **)&M->mb[l], Po * 4) && alloc((void **)&M->vb[l], Po * 4) &&
                   alloc((void **)&M->Wb[l], nw * 2) && alloc((void **)&M->WbT[l], nw * 2);
         if (!ok) return set_error(DDSG_ERR_OOM, "mlp: parameter allocation failed");
-        // scatter the packed logical parameters into the padded layout
-        std::vector<float> w(nw, 0.f), bb(Po, 0.f);
+        // scatter the packed logical parameters (and saved Adam moments) into the padded layout
         const int ni = M->n[l], no = M->n[l + 1];
-        for (int r = 0; r < no; ++r)
-            for (int c = 0; c < ni; ++c) w[(size_t)r * Pi + c] = M->init[off + (size_t)r * ni + c];
-        off += (size_t)no * ni;
-        for (int r = 0; r < no; ++r) bb[r] = M->init[off + r];
-        off += no;
-        if (cudaMemcpy(M->W[l], w.data(), nw * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(M->b[l], bb.data(), Po * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-            return set_error(DDSG_ERR_CUDA, "mlp: parameter upload failed");
+        auto upload = [&](const std::vector<float> &src, float *dW, float *db) {
+            std::vector<float> w(nw, 0.f), bb(Po, 0.f);
+            for (int r = 0; r < no; ++r)
+                for (int c = 0; c < ni; ++c) w[(size_t)r * Pi + c] = src[off + (size_t)r * ni + c];
+            for (int r = 0; r < no; ++r) bb[r] = src[off + (size_t)no * ni + r];
+            return cudaMemcpy(dW, w.data(), nw * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+                   cudaMemcpy(db, bb.data(), Po * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+        };
+        bool up = upload(M->init, M->W[l], M->b[l]);
+        if (up && !M->init_m.empty()) up = upload(M->init_m, M->mW[l], M->mb[l]) && upload(M->init_v, M->vW[l], M->vb[l]);
+        off += (size_t)no * ni + no;
+        if (!up) return set_error(DDSG_ERR_CUDA, "mlp: parameter upload failed");
         to_bf16_kernel<<<nblk(nw), 256>>>((int64_t)nw, Po, Pi, M->W[l], M->Wb[l], M->WbT[l]);
         if (cudaGetLastError() != cudaSuccess) return set_error(DDSG_ERR_CUDA, "mlp: conversion failed");
     }
@@ -617,11 +622,15 @@ extern "C" int mlp_train_step(mlp_t *M, int64_t B, const double *x_dev, const do
 
 // Packed logical parameters (per layer W row-major out x in, then b) or the
 // gradients of the last train step, FP32, to the host. Synchronous.
-static int mlp_copy_out(mlp_t *M, bool grads, float *host) {
+// which: 0 parameters, 1 gradients of the last step, 2 / 3 Adam first / second moments;
+// packed logical layout (per layer W row-major n_out x n_in, then b)
+static int mlp_copy_out(mlp_t *M, int which, float *host) {
     if (!M || !host) return set_error(DDSG_ERR_ARG, "mlp: NULL argument");
     if (M->device < 0) {
-        if (grads) return set_error(DDSG_ERR_STATE, "mlp_get_grads: no train step yet");
-        std::copy(M->init.begin(), M->init.end(), host);
+        if (which == 1) return set_error(DDSG_ERR_STATE, "mlp_get_grads: no train step yet");
+        const std::vector<float> &src = which == 0 ? M->init : (which == 2 ? M->init_m : M->init_v);
+        if (src.empty()) std::fill(host, host + M->init.size(), 0.f);
+        else std::copy(src.begin(), src.end(), host);
         return DDSG_OK;
     }
     if (cudaDeviceSynchronize() != cudaSuccess) return set_error(DDSG_ERR_CUDA, "mlp: synchronize failed");
@@ -629,8 +638,10 @@ static int mlp_copy_out(mlp_t *M, bool grads, float *host) {
     for (int l = 0; l < M->L; ++l) {
         const int Pi = M->P[l], Po = M->P[l + 1], ni = M->n[l], no = M->n[l + 1];
         std::vector<float> w((size_t)Pi * Po), bb(Po);
-        if (cudaMemcpy(w.data(), grads ? M->gW[l] : M->W[l], w.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(bb.data(), grads ? M->gb[l] : M->b[l], bb.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        const float *sW = which == 0 ? M->W[l] : which == 1 ? M->gW[l] : which == 2 ? M->mW[l] : M->vW[l];
+        const float *sb = which == 0 ? M->b[l] : which == 1 ? M->gb[l] : which == 2 ? M->mb[l] : M->vb[l];
+        if (cudaMemcpy(w.data(), sW, w.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(bb.data(), sb, bb.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
             return set_error(DDSG_ERR_CUDA, "mlp: copy failed");
         for (int r = 0; r < no; ++r)
             for (int c = 0; c < ni; ++c) host[off + (size_t)r * ni + c] = w[(size_t)r * Pi + c];
@@ -641,8 +652,95 @@ static int mlp_copy_out(mlp_t *M, bool grads, float *host) {
     return DDSG_OK;
 }
 
-extern "C" int mlp_get_params(mlp_t *M, float *host) { return mlp_copy_out(M, false, host); }
-extern "C" int mlp_get_grads(mlp_t *M, float *host) { return mlp_copy_out(M, true, host); }
+extern "C" int mlp_get_params(mlp_t *M, float *host) { return mlp_copy_out(M, 0, host); }
+extern "C" int mlp_get_grads(mlp_t *M, float *host) { return mlp_copy_out(M, 1, host); }
+
+// ---------------------------------------------------------------------------
+// checkpoint / resume: one file per network (layout in ddsg_io.h):
+//   i32 L, i32 sizes[L+1], i64 Adam step, f64 normalization[2 n_0 + 2 n_L],
+//   f32 parameters[np], f32 Adam m[np], f32 Adam v[np] (packed logical layout)
+// ---------------------------------------------------------------------------
+
+constexpr char kMlpMagic[8] = {'D', 'D', 'S', 'G', 'M', 'L', 'P', 'N'};
+constexpr uint32_t kMlpVersion = 1;
+
+extern "C" int mlp_save(mlp_t *M, const char *path) {
+    if (!M || !path) return set_error(DDSG_ERR_ARG, "mlp_save: NULL argument");
+    const size_t np = M->init.size();
+    std::vector<float> prm(np), mm(np), vv(np);
+    int rc = mlp_copy_out(M, 0, prm.data());
+    if (!rc) rc = mlp_copy_out(M, 2, mm.data());
+    if (!rc) rc = mlp_copy_out(M, 3, vv.data());
+    if (rc) return rc;
+    std::vector<double> nrm = M->norm;
+    if (M->device >= 0) {
+        // the normalization lives on the device once bound (it cannot change then)
+        const int n0 = M->n[0], nL = M->n[M->L];
+        if (cudaMemcpy(nrm.data(), M->in_shift, n0 * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(nrm.data() + n0, M->in_scale, n0 * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(nrm.data() + 2 * n0, M->out_shift, nL * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(nrm.data() + 2 * n0 + nL, M->out_scale, nL * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return set_error(DDSG_ERR_CUDA, "mlp_save: copy failed");
+    }
+    io::Writer w;
+    w.header(kMlpMagic, kMlpVersion);
+    w.put1<int32_t>(M->L);
+    for (int l = 0; l <= M->L; ++l) w.put1<int32_t>(M->n[l]);
+    w.put1<int64_t>(M->step);
+    w.put(nrm.data(), nrm.size());
+    w.put(prm.data(), np);
+    w.put(mm.data(), np);
+    w.put(vv.data(), np);
+    w.seal();
+    if (!io::write_file(path, w.buf)) return set_error(DDSG_ERR_ARG, "mlp_save: write failed");
+    return DDSG_OK;
+}
+
+extern "C" int mlp_load(const char *path, mlp_t **out) {
+    if (!path || !out) return set_error(DDSG_ERR_ARG, "mlp_load: NULL argument");
+    *out = nullptr;
+    std::vector<unsigned char> buf;
+    if (!io::read_file(path, buf)) return set_error(DDSG_ERR_ARG, "mlp_load: cannot open the file");
+    io::Reader r{nullptr, nullptr};
+    switch (io::open_body(buf, kMlpMagic, kMlpVersion, r)) {
+        case 1: return set_error(DDSG_ERR_ARG, "mlp_load: not a network file");
+        case 2: return set_error(DDSG_ERR_ARG, "mlp_load: unsupported file version");
+        case 3: return set_error(DDSG_ERR_ARG, "mlp_load: checksum mismatch (truncated or corrupt file)");
+        default: break;
+    }
+    int32_t L = 0;
+    if (!r.get(&L, 1) || L < 1 || L > 16) return set_error(DDSG_ERR_ARG, "mlp_load: bad layer count");
+    std::vector<int32_t> sizes(L + 1);
+    int64_t step = 0;
+    if (!r.get(sizes.data(), sizes.size()) || !r.get(&step, 1) || step < 0)
+        return set_error(DDSG_ERR_ARG, "mlp_load: truncated header");
+    size_t np = 0;
+    for (int l = 0; l <= L; ++l)
+        if (sizes[l] < 1 || sizes[l] > 8192) return set_error(DDSG_ERR_ARG, "mlp_load: layer width out of range");
+    for (int l = 0; l < L; ++l) np += (size_t)sizes[l] * sizes[l + 1] + sizes[l + 1];
+    std::vector<double> nrm(2 * (size_t)sizes[0] + 2 * (size_t)sizes[L]);
+    std::vector<float> prm(np), mm(np), vv(np);
+    if (!r.get(nrm.data(), nrm.size()) || !r.get(prm.data(), np) || !r.get(mm.data(), np) || !r.get(vv.data(), np) ||
+        r.p != r.end)
+        return set_error(DDSG_ERR_ARG, "mlp_load: file size does not match its header");
+    mlp_t *M = nullptr;
+    int rc = mlp_create(L, sizes.data(), prm.data(), 0, &M);
+    if (rc) return rc;
+    M->norm = nrm;
+    M->step = step;
+    M->init_m = std::move(mm);
+    M->init_v = std::move(vv);
+    *out = M;
+    return DDSG_OK;
+}
+
+extern "C" int mlp_shape(const mlp_t *M, int32_t *nlayers, int32_t *sizes_host) {
+    if (!M) return set_error(DDSG_ERR_ARG, "mlp_shape: NULL network");
+    if (nlayers) *nlayers = M->L;
+    if (sizes_host)
+        for (int l = 0; l <= M->L; ++l) sizes_host[l] = M->n[l];
+    return DDSG_OK;
+}
 
 extern "C" int64_t mlp_num_params(const mlp_t *M) {
     if (!M) return 0;

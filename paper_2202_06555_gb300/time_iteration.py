@@ -17,6 +17,8 @@ interpolation and Newton work runs in its kernels.
 from __future__ import annotations
 
 import itertools
+import json
+import os
 
 import numpy as np
 
@@ -194,20 +196,22 @@ def euler_errors(model, policy: HDMR, states: np.ndarray, precision=F64, form=FO
 def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps_gamma: float,
                    eps_eta: float, eps_rho: float, lo, hi, test_states: np.ndarray, tol_euler=0.0,
                    candidates=None, precision=F64, form=FORM_SLICEFREE, newton_tol=1e-10, max_it=30,
-                   node_mode=NODES_DELTA, tol_change=0.0, checkpoint=None):
+                   node_mode=NODES_DELTA, tol_change=0.0, checkpoint=None, start_step=0, history0=None):
     """Alg. 1: p <- build_ddsg(x -> solve{FOC(. | x, p)}) until the mean Euler
     error at test_states is below tol_euler, the largest policy change at the
     test states is below tol_change, or `steps` steps are done. With a
-    checkpoint path the policy is saved there after every step (hdmr_save);
-    HDMR.load of that file resumes the iteration as policy0. Each step ends
-    with hdmr_check on both policies (DDSGError on a device wait that gave up).
-    Returns the last policy and one record per step."""
+    checkpoint path the policy is saved there after every step (hdmr_save) and
+    the step count and history beside it (checkpoint + ".json"); resume() reads
+    both back, and passing them as policy0, start_step and history0 continues
+    the iteration. Each step ends with hdmr_check on both policies (DDSGError
+    on a device wait that gave up). Returns the last policy and one record per
+    step (history0's records first)."""
     import torch
     d, m = policy0.d, policy0.m
     policy = policy0
-    history = []
+    history = list(history0 or [])
     sd = torch.from_numpy(np.ascontiguousarray(test_states, np.float64)).cuda()
-    for step in range(steps):
+    for step in range(start_step, start_step + steps):
         solve = StateSolver(model, policy, precision, form, newton_tol, max_it, node_mode)
         new, info = build_ddsg(solve, d, m, order, level, eps_gamma, eps_eta, eps_rho, lo, hi, candidates)
         e = euler_errors(model, new, test_states, precision, form, node_mode)
@@ -226,10 +230,40 @@ def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps
                         "euler_error_max": float(np.max(e)),
                         "policy_change_max": float((y1 - y0).abs().max().item())})
         if checkpoint:
-            new.save(checkpoint)
+            save_checkpoint(checkpoint, new, step + 1, history)
         if policy is not policy0:
             policy.close()
         policy = new
         if history[-1]["euler_error_mean"] < tol_euler or history[-1]["policy_change_max"] < tol_change:
             break
     return policy, history
+
+
+def _file_checksum(path: str) -> str:
+    """The FNV-1a checksum that ends a libddsg checkpoint file, as hex."""
+    with open(path, "rb") as f:
+        f.seek(-8, os.SEEK_END)
+        return f.read(8)[::-1].hex()
+
+
+def save_checkpoint(path: str, policy: HDMR, steps_done: int, history) -> None:
+    """The policy (hdmr_save) at `path` and {steps_done, history, the policy
+    file's checksum} at path + ".json"; each written to a temporary name and
+    then moved into place."""
+    policy.save(path + ".tmp")
+    os.replace(path + ".tmp", path)
+    rec = {"steps_done": int(steps_done), "history": history, "policy_checksum": _file_checksum(path)}
+    with open(path + ".json.tmp", "w") as f:
+        json.dump(rec, f)
+    os.replace(path + ".json.tmp", path + ".json")
+
+
+def resume(path: str):
+    """(policy, steps_done, history) from a time-iteration checkpoint. Refuses a
+    record that does not belong to the policy file next to it (an interrupted
+    save): ValueError."""
+    with open(path + ".json") as f:
+        rec = json.load(f)
+    if rec.get("policy_checksum") != _file_checksum(path):
+        raise ValueError(f"{path}.json does not match {path} (interrupted save)")
+    return HDMR.load(path), int(rec["steps_done"]), rec["history"]

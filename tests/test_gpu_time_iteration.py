@@ -160,7 +160,11 @@ def test_time_iteration_resumes_from_a_checkpoint(G, tmp_path):
     ck = str(tmp_path / "ti.ddsg")
     h2, _ = time_iteration(M, _gpu_initial_policy(G, I, N), 2, 2, 4, 1e-4, 1e-5, 0.0, lo, hi, T)
     h1, _ = time_iteration(M, _gpu_initial_policy(G, I, N), 1, 2, 4, 1e-4, 1e-5, 0.0, lo, hi, T, checkpoint=ck)
-    hr, _ = time_iteration(M, G.HDMR.load(ck), 1, 2, 4, 1e-4, 1e-5, 0.0, lo, hi, T)
+    from paper_2202_06555_gb300.time_iteration import resume
+    p0, done, hist = resume(ck)
+    assert done == 1 and len(hist) == 1 and hist[0]["step"] == 0
+    hr, hist2 = time_iteration(M, p0, 1, 2, 4, 1e-4, 1e-5, 0.0, lo, hi, T, start_step=done, history0=hist)
+    assert [r["step"] for r in hist2] == [0, 1]
     x = torch.from_numpy(T).cuda()
     ya = torch.empty((T.shape[0], N + 1), dtype=torch.float64, device="cuda")
     yb = torch.empty_like(ya)
