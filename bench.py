@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -136,7 +137,7 @@ class ClockSampler:
     def __init__(self, uuid):
         self.uuid = uuid
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"ddsg_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

@@ -4,7 +4,7 @@ Plain numpy restatement of the warm-start network: an MLP with GELU hidden
 activations (exact erf form), mean-squared error on affinely normalized
 targets, hand-derived backward pass and Adam. It checks the GPU's BF16
 tensor-core training and inference kernels. (The paper uses no neural network;
-this network only proposes Newton initial guesses, the solve stays the judge.)
+this network only proposes Newton initial guesses; the solve decides the answer.)
 """
 from __future__ import annotations
 

@@ -1,6 +1,7 @@
 """GPU parity of libddsg against the CPU oracle, through the C ABI.
 
-Bars (written here, derived in the design doc):
+Bars (from the arithmetic: FP64 rounding over S, FP32 products folded into a
+compensated FP32 sum for F32C):
   index work (grid point sets, active-set counts and hashes): bit-exact;
   FP64:  |y_gpu - y_oracle| <= 1e-12 * max(|y|, S), S = sum of |terms| (oracle);
   F32C:  |y_gpu - y_oracle| <= 1e-6  * max(|y|, S);
