@@ -1025,14 +1025,17 @@ __device__ __forceinline__ void comp_at(const DevTables &t, const DevComp &cd, i
     }
 }
 
-// One thread per (state, country i) and output chunk: the policy at the two
-// nodes that shock country i (2i: +, 2i+1: -) is the no-shock policy plus the
-// change of every component holding a_i when a'_i moves to its shocked value;
-// also copies the two global-shock rows. Writes the 2(N+1)-node policy array y
-// in the layout the residual and Jacobian kernels read. The three values of
-// a'_i are taken one after another (no shock, +, -), so a thread holds two
-// accumulator chunks, not three.
-constexpr int DLT_MC = 32;   // outputs per thread
+// One thread per (state, country i): the policy at the two nodes that shock
+// country i (2i: +, 2i+1: -) is the no-shock policy plus the change of every
+// component holding a_i when a'_i moves to its shocked value; the thread with
+// i = 0 also copies the two global-shock rows. Writes the 2(N+1)-node policy
+// array y in the layout the residual and Jacobian kernels read. For each value
+// of a'_i (no shock, +, -) the thread finds the active (row, weight) terms of
+// its components once, then sweeps the outputs in chunks of MC (when there are
+// more terms than the list holds it walks the tuples again for every chunk,
+// in the same order). The no-shock pass stores -sum into both node rows; the
+// + and - passes turn that into no-shock policy + (sum - no-shock sum).
+constexpr int DLT_MC = 32;   // outputs per chunk
 
 template <int PREC, int MC>
 __global__ void __launch_bounds__(128) irbc_delta_kernel(IrbcDev P, int64_t s0, int64_t nsc, DevTables t,
@@ -1044,14 +1047,14 @@ __global__ void __launch_bounds__(128) irbc_delta_kernel(IrbcDev P, int64_t s0, 
                                                          const double *__restrict__ span,
                                                          const double *__restrict__ y3, double *__restrict__ y) {
     using W = typename DeltaT<PREC>::W;
+    const W *alpha = DeltaT<PREC>::alpha(t);
+    const int mp = DeltaT<PREC>::stride(t);
     const int N = P.N, d = 2 * N, m = P.m, nq = 2 * (N + 1);
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nsc * N) return;
     const int64_t sl = idx / N;
     const int i = (int)(idx - sl * N);
     const int64_t s = s0 + sl;
-    const int m0 = blockIdx.y * MC;
-    const int mv = min(MC, m - m0);
     const bool paper = form == DDSG_FORM_PAPER;
     bool bad = false;
     unsigned long long cl = 0;
@@ -1059,48 +1062,103 @@ __global__ void __launch_bounds__(128) irbc_delta_kernel(IrbcDev P, int64_t s0, 
     next_a3(P, states[s * d + i], e3[0], e3[1], e3[2]);
     uint64_t Xi[3];
     for (int v = 0; v < 3; ++v) Xi[v] = encode_coord(e3[v], lo[i], span[i], bad, cl);
-    const double *yb = y3 + (sl * 3) * (int64_t)m + m0;
-    // the components holding a_i at a'_i = value v (0 no shock, 1 +, 2 -), into acc
-    auto sweep = [&](int v, W (&acc)[MC]) {
-#pragma unroll
-        for (int o = 0; o < MC; ++o) acc[o] = (W)0;
-        for (int e = aoff[i]; e < aoff[i + 1] && !bad; ++e) {
+    const double *yb = y3 + (sl * 3) * (int64_t)m;
+    double *yp = y + (sl * nq + 2 * i) * (int64_t)m;
+    double *ym = yp + m;
+    DTerm<W> terms[DT_CAP];
+    // coordinates of component cd with a'_i = value v (false: a non-finite one)
+    auto coords = [&](const DevComp &cd, int v, uint64_t *Xd) -> bool {
+        bool bd = false;
+        for (int j = 0; j < cd.k; ++j) {
+            const int dj = cd.dims[j];
+            if (dj == i) {
+                Xd[j] = Xi[v];
+            } else if (dj < N) {
+                double f0, fp, fm;
+                next_a3(P, states[s * d + dj], f0, fp, fm);
+                Xd[j] = encode_coord(f0, lo[dj], span[dj], bd, cl);
+            } else {
+                Xd[j] = encode_coord(guess[s * m + dj - N], lo[dj], span[dj], bd, cl);
+            }
+        }
+        return !bd;
+    };
+    for (int v = 0; v < 3; ++v) {
+        // the active terms of every component holding a_i at a'_i = value v
+        int nt = 0;
+        bool over = false;
+        for (int e = aoff[i]; e < aoff[i + 1] && !bad && !over; ++e) {
             if (!comp_ok(t, acomp[e], d)) continue;
             const DevComp &cd = t.comps[acomp[e]];
             const double coef = paper ? cd.b : 1.0;
             if (coef == 0.0) continue;
             const int tb = paper ? cd.tup_begin : cd.tup_int;
             uint64_t Xd[KMAX];
-            for (int j = 0; j < cd.k; ++j) {
-                const int dj = cd.dims[j];
-                if (dj == i) {
-                    Xd[j] = Xi[v];
-                } else if (dj < N) {
-                    double f0, fp, fm;
-                    next_a3(P, states[s * d + dj], f0, fp, fm);
-                    Xd[j] = encode_coord(f0, lo[dj], span[dj], bad, cl);
-                } else {
-                    Xd[j] = encode_coord(guess[s * m + dj - N], lo[dj], span[dj], bad, cl);
+            if (!coords(cd, v, Xd)) { bad = true; break; }
+            for (int ti = tb; ti < cd.tup_end; ++ti) {
+                const DevTup tu = t.tups[ti];
+                uint32_t off = 0;
+                double w = coef;
+                bool act = true;
+                for (int j = 0; j < cd.k; ++j) {
+                    Basis1D o;
+                    const int l = tu.lev[j];
+                    if (!basis1d(Xd[j], l, o)) { act = false; break; }
+                    off = off * (j == 1 ? tu.nc1 : ncells(l)) + o.cell;
+                    w *= (double)o.N * ldexp(1.0, -o.e);
+                }
+                if (!act) continue;
+                const int32_t row = tuple_row_at(tu, off, t.slots, t.S, cd.row_begin, cd.row_end);
+                if (row < 0) continue;
+                if (nt == DT_CAP) { over = true; break; }   // more terms than the list holds
+                terms[nt].row = row;
+                terms[nt].w = (W)w;
+                ++nt;
+            }
+        }
+        // outputs in chunks: sum of weight x surplus over the terms, in W
+        for (int m0 = 0; m0 < m; m0 += MC) {
+            const int mv = min(MC, m - m0);
+            W acc[MC];
+#pragma unroll
+            for (int o = 0; o < MC; ++o) acc[o] = (W)0;
+            if (!over) {
+                for (int q = 0; q < nt; ++q) {
+                    const W *r = alpha + (int64_t)terms[q].row * mp + m0;
+                    const W ww = terms[q].w;
+#pragma unroll
+                    for (int o = 0; o < MC; ++o)
+                        if (o < mv) acc[o] += ww * r[o];
+                }
+            } else {
+                for (int e = aoff[i]; e < aoff[i + 1] && !bad; ++e) {
+                    if (!comp_ok(t, acomp[e], d)) continue;
+                    const DevComp &cd = t.comps[acomp[e]];
+                    const double coef = paper ? cd.b : 1.0;
+                    if (coef == 0.0) continue;
+                    uint64_t Xd[KMAX];
+                    if (!coords(cd, v, Xd)) { bad = true; break; }
+                    comp_at<PREC, MC>(t, cd, paper ? cd.tup_begin : cd.tup_int, coef, Xd, m0, mv, acc);
                 }
             }
-            if (bad) break;
-            comp_at<PREC, MC>(t, cd, tb, coef, Xd, m0, mv, acc);
-        }
-    };
-    W acc0[MC];
-    sweep(0, acc0);
-    for (int v = 1; v < 3; ++v) {
-        W acc[MC];
-        sweep(v, acc);
-        double *yo = y + (sl * nq + 2 * i + (v - 1)) * (int64_t)m + m0;
 #pragma unroll
-        for (int o = 0; o < MC; ++o)
-            if (o < mv) yo[o] = bad ? NAN : yb[o] + ((double)acc[o] - (double)acc0[o]);
+            for (int o = 0; o < MC; ++o) {
+                if (o < mv) {
+                    if (v == 0) {
+                        yp[m0 + o] = -(double)acc[o];
+                        ym[m0 + o] = -(double)acc[o];
+                    } else {
+                        double *yo = v == 1 ? yp : ym;
+                        yo[m0 + o] = bad ? NAN : yb[m0 + o] + ((double)acc[o] + yo[m0 + o]);
+                    }
+                }
+            }
+        }
     }
     if (i == 0) {
-        for (int o = 0; o < mv; ++o) {
-            y[(sl * nq + 2 * N) * (int64_t)m + m0 + o] = y3[(sl * 3 + 1) * (int64_t)m + m0 + o];
-            y[(sl * nq + 2 * N + 1) * (int64_t)m + m0 + o] = y3[(sl * 3 + 2) * (int64_t)m + m0 + o];
+        for (int o = 0; o < m; ++o) {
+            y[(sl * nq + 2 * N) * (int64_t)m + o] = y3[(sl * 3 + 1) * (int64_t)m + o];
+            y[(sl * nq + 2 * N + 1) * (int64_t)m + o] = y3[(sl * 3 + 2) * (int64_t)m + o];
         }
     }
 }
@@ -1215,10 +1273,8 @@ template <int PREC>
 cudaError_t launch_delta(const IrbcDev &P, int64_t s0, int64_t nsc, const DevTables &t, int form,
                          const int32_t *aoff, const int32_t *acomp, const double *states, const double *guess,
                          const double *lo, const double *span, const double *y3, double *y, cudaStream_t st) {
-    const int m = P.m;
-    dim3 grid((unsigned)((nsc * P.N + 127) / 128), (unsigned)((m + DLT_MC - 1) / DLT_MC));
-    irbc_delta_kernel<PREC, DLT_MC><<<grid, 128, 0, st>>>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span,
-                                                          y3, y);
+    irbc_delta_kernel<PREC, DLT_MC><<<(unsigned)((nsc * P.N + 127) / 128), 128, 0, st>>>(
+        P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, y);
     return cudaGetLastError();
 }
 

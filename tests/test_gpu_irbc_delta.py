@@ -139,3 +139,38 @@ def test_delta_nodes_newton_and_nonfinite_states(G):
     assert bad[2] and bad[4] and not bad[[0, 1, 3, 5]].any()
     with pytest.raises(G.DDSGError, match="ERR_ARG"):
         M.set_node_mode(7)
+
+
+def test_delta_nodes_with_more_terms_than_the_list_holds(G):
+    """Every pair at level 7 (N = 3): a_i is held by 6 components with up to
+    7 + 5 x 28 tuples, more active terms per a'-value than the delta kernel's
+    term list, so it walks the tuples again per output chunk. Same results as
+    the all-node path and the oracle."""
+    N, level = 3, 7
+    I = O.IRBCOracle(N, sigma=0.01)
+    lam = I.steady_lambda()
+    base = np.concatenate([np.ones(N), [lam]])
+    pert = synth.irbc_policy_perturbation(synth.BASE_SEED + 414, N)
+    fn = lambda dims, X: synth.irbc_policy_values(base, pert, dims, X)
+    d = 2 * N
+    comps = O.full_order_components(d, 2)
+    E = O.OracleDDSG(d, N + 1, lo=np.full(d, 0.8), hi=np.full(d, 1.2))
+    h = G.HDMR(d, N + 1, 2, lo=np.full(d, 0.8), hi=np.full(d, 1.2))
+    for u in comps:
+        E.add_regular(u, level)
+        h.add_regular(list(u), level)
+    E.fill_values(fn)
+    E.hierarchize()
+    vals = np.concatenate([fn(u, h.component_points(c)[2]) for c, u in enumerate(comps)])
+    h.hierarchize(torch.from_numpy(vals).cuda())
+    M = G.IRBC(N, I.p["beta"], I.p["alpha"], I.p["delta"], I.p["sigma"], I.p["rho"], I.p["phi"],
+               I.A, I.gamma, I.tau)
+    S, g = states_and_guess(N, 48, lam, synth.BASE_SEED + 415)
+    r_ref = I.residual(E, S, g, form=1)
+    sc = scales(I, S, g, r_ref)
+    for prec in (0, 1):
+        r_d, _, _ = run(G, M, h, S, g, prec, 1, G.NODES_DELTA)
+        r_a, _, _ = run(G, M, h, S, g, prec, 1, G.NODES_ALL)
+        assert np.all(np.abs(r_d - r_a) <= (1e-13 if prec == 0 else 1e-6) * sc), (prec, np.max(np.abs(r_d - r_a) / sc))
+        if prec == 0:
+            assert np.all(np.abs(r_d - r_ref) <= 1e-11 * sc), np.max(np.abs(r_d - r_ref) / sc)
