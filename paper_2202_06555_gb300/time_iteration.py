@@ -19,6 +19,7 @@ from __future__ import annotations
 import itertools
 import json
 import os
+import time
 
 import numpy as np
 
@@ -212,6 +213,7 @@ def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps
     history = list(history0 or [])
     sd = torch.from_numpy(np.ascontiguousarray(test_states, np.float64)).cuda()
     for step in range(start_step, start_step + steps):
+        t_step = time.perf_counter()
         solve = StateSolver(model, policy, precision, form, newton_tol, max_it, node_mode)
         new, info = build_ddsg(solve, d, m, order, level, eps_gamma, eps_eta, eps_rho, lo, hi, candidates)
         e = euler_errors(model, new, test_states, precision, form, node_mode)
@@ -228,7 +230,8 @@ def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps
                         "newton_iters_mean": solve.iterations / max(1, solve.points),
                         "euler_error_mean": float(np.mean(np.max(e, 1))),
                         "euler_error_max": float(np.max(e)),
-                        "policy_change_max": float((y1 - y0).abs().max().item())})
+                        "policy_change_max": float((y1 - y0).abs().max().item()),
+                        "seconds": time.perf_counter() - t_step})
         if checkpoint:
             save_checkpoint(checkpoint, new, step + 1, history)
         if policy is not policy0:
