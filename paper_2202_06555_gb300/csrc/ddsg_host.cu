@@ -19,6 +19,7 @@
 #include "ddsg_alloc.h"
 #include "ddsg_internal.h"
 #include "ddsg_io.h"
+#include "ddsg_tables.h"
 
 using namespace ddsg;
 
@@ -126,6 +127,7 @@ struct hdmr {
     bool have_alpha = false;  // alpha64/alpha32 valid
     std::vector<double> b;
     std::vector<int32_t> dpos;  // device row of each point (host copy)
+    std::vector<int32_t> ntup[2];   // level tuples per component walked in each form (set at upload)
     double *dlo = nullptr, *dspan = nullptr;
     int64_t *stats = nullptr;
     void *ws = nullptr;
@@ -668,6 +670,9 @@ static int upload_tables(hdmr *h) {
     // per-form component lists and the largest staged surplus block
     const int64_t mp64 = (h->m + 1) & ~1, mp32 = (h->m + 3) & ~3;
     for (int form = 0; form < 2; ++form) {
+        h->ntup[form].resize(C);
+        for (int c = 0; c < C; ++c)
+            h->ntup[form][c] = dc[c].tup_end - (form == DDSG_FORM_PAPER ? dc[c].tup_begin : dc[c].tup_int);
         std::vector<int32_t> lst;
         int64_t rows_max = 0;
         for (int c = 0; c < C; ++c) {
@@ -1382,6 +1387,13 @@ extern "C" int hdmr_check(hdmr_t *h, ddsg_stream_t stream) {
 // ---------------------------------------------------------------------------
 
 namespace ddsg {
+int handle_comp_tuples(hdmr_t *h, int form, std::vector<int32_t> &out) {
+    if (!h || form < 0 || form > 1) return fail(DDSG_ERR_ARG, "NULL handle or unknown form");
+    if (!h->uploaded || h->ntup[form].size() != h->comps.size()) return fail(DDSG_ERR_STATE, "call hdmr_hierarchize first");
+    out = h->ntup[form];
+    return DDSG_OK;
+}
+
 int handle_eval_view(hdmr_t *h, int precision, int form, HandleView *v) {
     if (!h || !v) return fail(DDSG_ERR_ARG, "NULL handle");
     if (precision != DDSG_F64 && precision != DDSG_F32C) return fail(DDSG_ERR_ARG, "unknown precision %d", precision);

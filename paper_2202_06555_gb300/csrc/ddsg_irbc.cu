@@ -27,6 +27,7 @@
 
 #include "ddsg_alloc.h"
 #include "ddsg_internal.h"
+#include "ddsg_tables.h"
 
 using namespace ddsg;
 
@@ -576,21 +577,21 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
 }
 
 // Shared memory of the Jacobian kernel: the groups, the column states and a
-// term pool of up to kJacSmem bytes in all (worst case: DT_CAP terms per
-// group and variant; a column whose terms do not fit is NaN).
+// term pool sized for the most terms one state can collect (`terms`, from the
+// tables' tuple counts), within kJacSmem bytes in all (a column whose terms
+// do not fit is NaN). A pool sized to the tables lets several blocks share an SM.
 constexpr size_t kJacSmem = 160 * 1024;
 
 static cudaError_t launch_jacobian(int precision, const IrbcDev &P, int64_t s0, int64_t nsc, const DevTables &t,
-                                   int form, int G, const int32_t *koff, const int32_t *kids, const double *lo,
-                                   const double *span, const double *guess, const double *y, const double *aux,
-                                   double *jac, cudaStream_t st) {
+                                   int form, int G, int64_t terms, const int32_t *koff, const int32_t *kids,
+                                   const double *lo, const double *span, const double *guess, const double *y,
+                                   const double *aux, double *jac, cudaStream_t st) {
     const size_t wsz = precision == DDSG_F64 ? sizeof(double) : sizeof(float);
     const size_t fixed = ((sizeof(JGroup) * G + sizeof(int32_t) * P.N + 15) & ~(size_t)15) +
                          ((wsz * 8 * P.N + 15) & ~(size_t)15);
     const size_t term = precision == DDSG_F64 ? sizeof(DTerm<double>) : sizeof(DTerm<float>);
     if (fixed + 64 * term > kJacSmem) return cudaErrorInvalidValue;
-    const size_t worst = (size_t)G * 3 * DT_CAP;
-    const size_t cap = std::min(worst, (kJacSmem - fixed) / term);
+    const size_t cap = std::min<size_t>(std::max<int64_t>(terms, 1), (kJacSmem - fixed) / term);
     const size_t smem = fixed + cap * term;
     cudaError_t e;
     if (precision == DDSG_F64) {
@@ -1220,12 +1221,19 @@ constexpr size_t kWsCap = (size_t)2 << 30;   // residual workspace per chunk of 
 // CSR over the dims N+i (the k_i): the components that hold k_i. Fails if one
 // of them also holds more than one a-dimension (the Jacobian kernel handles
 // at most one shocked coordinate per component).
-int k_components(hdmr_t *h, int N, std::vector<int32_t> &off, std::vector<int32_t> &ids) {
+// terms: the most derivative terms one state's Jacobian can collect in `form`
+// (each level tuple gives at most one per a'-value of its component, and the
+// kernel keeps at most DT_CAP per group and value).
+int k_components(hdmr_t *h, int N, int form, std::vector<int32_t> &off, std::vector<int32_t> &ids,
+                 int64_t &terms) {
     int32_t nc = 0;
     int64_t np = 0;
     int rc = hdmr_num_components(h, &nc, &np);
     if (rc) return rc;
+    std::vector<int32_t> ntup;
+    if ((rc = handle_comp_tuples(h, form, ntup))) return rc;
     std::vector<std::vector<int32_t>> per(N);
+    terms = 0;
     for (int32_t c = 0; c < nc; ++c) {
         int32_t kk = 0, dims[DDSG_KMAX];
         hdmr_component_info(h, c, &kk, dims, nullptr, nullptr);
@@ -1236,6 +1244,7 @@ int k_components(hdmr_t *h, int N, std::vector<int32_t> &off, std::vector<int32_
             if (na > 1)
                 return set_error(DDSG_ERR_ARG, "euler_residual: the Jacobian needs every component holding a k_i to hold at most one a_j");
             per[dims[j] - N].push_back(c);
+            terms += (int64_t)(na ? 3 : 1) * std::min<int32_t>(ntup[c], DT_CAP);
         }
     }
     off.assign(N + 1, 0);
@@ -1355,9 +1364,10 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
                                                        : "euler_residual: the policy must map 2N states to N+1 outputs");
     if ((rc = bind_device(M))) return rc;
     std::vector<int32_t> koff, kids;
+    int64_t jac_terms = 0;
     int32_t *koff_dev = nullptr, *kids_dev = nullptr;
     if (jac_dev) {
-        if ((rc = k_components(policy, N, koff, kids))) return rc;
+        if ((rc = k_components(policy, N, form, koff, kids, jac_terms))) return rc;
         if (N > 32 * JAC_KJ)
             return set_error(DDSG_ERR_ARG, "euler_residual: the Jacobian supports N <= 192");
         if (((sizeof(JGroup) * kids.size() + sizeof(int32_t) * N + 15) & ~(size_t)15) +
@@ -1461,8 +1471,8 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
         }
         if (e == cudaSuccess && jac_dev) {
             Tracer::Scope ts(&M->tr, 3, st);
-            e = launch_jacobian(precision, P, s0, nsc, *v.tables, form, (int)kids.size(), koff_dev, kids_dev, v.lo,
-                                v.span, guess_dev, y, aux, jac_dev, st);
+            e = launch_jacobian(precision, P, s0, nsc, *v.tables, form, (int)kids.size(), jac_terms, koff_dev,
+                                kids_dev, v.lo, v.span, guess_dev, y, aux, jac_dev, st);
         }
         if (e != cudaSuccess) return set_error(DDSG_ERR_CUDA, cudaGetErrorString(e));
     }
