@@ -460,10 +460,13 @@ int irbc_lu_solve(int n, int64_t ns, const double *A_dev, const double *r_dev, d
 /*
  * irbc_newton -- per-state FP64 Newton on the residuals of euler_residual:
  * analytic Jacobian, LU solve, backtracking on ||r||_2 (halving up to 11
- * times). sol_dev (ns x (N+1)) holds the initial guess and receives the
- * solution. Stops a state when ||r||_inf <= tol. Outputs (nullable):
- * iters_dev, status_dev (0 converged, 1 max_it reached, 2 singular Jacobian),
- * resnorm_dev (final ||r||_inf). Synchronizes `stream` between iterations.
+ * times). sol_dev (ns x m: m = N+1, or 2N+1 with irreversible investment)
+ * holds the initial guess and receives the solution. Stops a state when
+ * ||r||_inf <= tol. Outputs (nullable): iters_dev, status_dev (0 converged,
+ * 1 max_it reached, 2 singular Jacobian), resnorm_dev (final ||r||_inf).
+ * Synchronizes `stream` between iterations. Its device buffers (about
+ * ns * m^2 * 8 bytes for the Jacobians) stay on the model for later calls and
+ * are freed by irbc_destroy.
  */
 int irbc_newton(irbc_t *model, hdmr_t *policy, int64_t ns, const double *states_dev,
                 double *sol_dev, int max_it, double tol, int32_t *iters_dev, int32_t *status_dev,

@@ -122,7 +122,8 @@ __global__ void irbc_queries_kernel(IrbcDev P, int64_t ns, const double *__restr
 // expectation); rows N + j (irreversible only): the complementarity
 // 0 <= mu_j _|_ k'_j - (1 - delta) k_j >= 0 as the Fischer-Burmeister equation
 // mu + I - sqrt(mu^2 + I^2) = 0; row m - 1: the resource constraint (eq. model2).
-// aux (per state, 7 x N): S1, SM, Dd, e0, ep, em, kp^(alpha-1).
+// aux (per state, 7 x N): S1, SM, the diagonal part of d r_j / d k'_j, the three
+// a'_j values (no shock, +, -), k'_j^(alpha-1); the Jacobian kernel reads them.
 // Block: RES_THREADS at most (N rounded up to a warp), threads over countries j.
 constexpr int RES_THREADS = 256;
 
