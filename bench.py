@@ -70,6 +70,9 @@ WORKLOADS = {
                    form="slicefree", irreversible=True),
 }
 
+KERNEL_NAMES = ["tile", "per-tuple", "tma-staged tile", "tma-staged, 2 warp groups", "tma-staged, 3 warp groups",
+                "nodal-slab, tma-staged"]
+
 FP32_LANES_PER_SM = 128
 N_SM = 152
 SM_MAX_MHZ = 2070.0
@@ -943,7 +946,7 @@ def main():
                       "eps_gamma": w["eps"], "max_level": w["level"], "queries_per_gpu": n,
                       "precision": w["precision"], "form": w["form"],
                       "active_points_per_query": active_total / n,
-                      "schedule": {"kernel": ["tile", "per-tuple", "tma-staged tile", "tma-staged, 2 warp groups", "tma-staged, 3 warp groups"][tuned[0]], "outputs_per_pass": tuned[1],
+                      "schedule": {"kernel": KERNEL_NAMES[tuned[0]], "outputs_per_pass": tuned[1],
                                    "autotune_subset": nt},
                       "l2": "inputs larger than L2 (x %.2f GB, surpluses %.2f GB); no flush"
                             % (n * w["d"] * 8 / 1e9, npts * w["m"] * (4 if prec == G.F32C else 8) / 1e9),

@@ -273,8 +273,13 @@ int hdmr_autotune(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int 
  *   n*d coordinates plus n flags); larger batches are refused with
  *   DDSG_ERR_ARG before anything runs -- split them.
  *   The first call on a device looks up the array's device address there
- *   (cudaGetSymbolAddress, once per device): make that first call before any
- *   stream capture begins.
+ *   (cudaGetSymbolAddress, once per device); a call with n = 0 does only
+ *   that. Under lazy module loading (CUDA's default) this first call is also
+ *   when the 16 MiB are committed on the device, so make it while setting up:
+ *   before any stream capture begins and before a memory cap applies.
+ *   Launches are traced like hdmr_eval's (DDSG_K_ENCODE, DDSG_K_EVAL); waits
+ *   that give up count in hdmr_stats and hdmr_check reports them, and the
+ *   handle's hdmr_set_fault_injection switch applies here too.
  *   All calls on a device share the array and it keeps the last call's
  *   contents (each call overwrites all it reads). Calls whose kernels overlap
  *   on the GPU race on it: serialize them on one stream.
@@ -311,7 +316,7 @@ int hdmr_eval_graph(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, in
  * them (2^18 polls of mbarrier.try_wait, about one second) run out. A block that gives up writes
  * NaN for its queries and counts one timeout per warp in hdmr_stats (stats[2]);
  * the copies it did issue land before it exits and the context stays usable.
- * Applies to hdmr_eval, hdmr_eval_host and hdmr_eval_graph of this handle
+ * Applies to hdmr_eval, hdmr_eval_host, hdmr_eval_graph and hdmr_eval_noalloc of this handle
  * (not to the evaluations inside euler_residual / irbc_newton). Only kernels
  * 2-4 (hdmr_set_eval_config) stage; the others ignore the setting, which
  * persists until set back to -1.

@@ -220,6 +220,8 @@ static void free_tables(DevTables &t) {
     cudaFree(t.stage_rec[1]);
     cudaFree(t.pdims[0]);
     cudaFree(t.pdims[1]);
+    nodal_free(t.nod[0]);
+    nodal_free(t.nod[1]);
     t = DevTables();
 }
 
@@ -715,6 +717,36 @@ static int upload_tables(hdmr *h) {
     return DDSG_OK;
 }
 
+// Nodal-slab tables of `form` for kernel 5: planned and allocated on first use
+// (once per table upload), node values recomputed whenever the surpluses change.
+// Tables the kernel cannot hold leave it ineligible; that is not an error.
+static int ensure_nodal(hdmr *h, int form, cudaStream_t st) {
+    DevNodal &N = h->dt.nod[form];
+    if (!h->uploaded) return DDSG_OK;
+    if (!N.tried) {
+        std::vector<NodalComp> nc(h->comps.size());
+        for (size_t c = 0; c < h->comps.size(); ++c) {
+            const Comp &cp = h->comps[c];
+            NodalComp &o = nc[c];
+            o.k = cp.k;
+            for (int j = 0; j < KMAX; ++j) o.dims[j] = cp.dims[j];
+            o.lv = cp.lv.data();
+            o.ix = cp.ix.data();
+            o.npts = cp.npts();
+            o.first = h->first_point[c];
+            o.b = h->b[c];
+        }
+        const int rc = nodal_build(h->m, form, nc, h->dpos, N);
+        ++h->gen;   // captured graphs hold the table pointers
+        if (rc) return rc;
+    }
+    if (N.ok && !N.vals && h->have_alpha) {
+        CUDA_TRY(launch_nodalize(N, h->dt.alpha64, h->dt.mp64, h->m, st));
+        N.vals = 1;
+    }
+    return DDSG_OK;
+}
+
 extern "C" int hdmr_hierarchize(hdmr_t *h, const double *values_dev, ddsg_stream_t stream) {
     if (!h || !values_dev) return fail(DDSG_ERR_ARG, "hdmr_hierarchize: NULL argument");
     if (int rc0 = ensure_device(h)) return rc0;
@@ -734,6 +766,15 @@ extern "C" int hdmr_hierarchize(hdmr_t *h, const double *values_dev, ddsg_stream
         CUDA_TRY(launch_to_f32(h->dt.alpha64, h->dt.mp64, h->dt.alpha32, h->dt.mp32, h->P, h->m, st));
     }
     h->have_alpha = true;
+    for (int form = 0; form < 2; ++form) {
+        DevNodal &N = h->dt.nod[form];
+        N.vals = 0;
+        if (N.ok) {
+            ProfScope ps(h, DDSG_K_CONVERT, st);
+            CUDA_TRY(launch_nodalize(N, h->dt.alpha64, h->dt.mp64, h->m, st));
+            N.vals = 1;
+        }
+    }
     return DDSG_OK;
 }
 
@@ -1080,17 +1121,20 @@ extern "C" int hdmr_eval(hdmr_t *h, int64_t n, const double *x_dev, double *y_de
     if (precision != DDSG_F64 && precision != DDSG_F32C) return fail(DDSG_ERR_ARG, "hdmr_eval: unknown precision %d", precision);
     if (form != DDSG_FORM_PAPER && form != DDSG_FORM_SLICEFREE) return fail(DDSG_ERR_ARG, "hdmr_eval: unknown form %d", form);
     if (!h->uploaded || !h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_eval: call hdmr_hierarchize first");
-    if (!eval_kernel_eligible(h->dt, h->cfg[precision][form].kernel, precision, form))
-        h->cfg[precision][form] = EvalConfig();
     if (form == DDSG_FORM_SLICEFREE && !h->anchor_central)
         return fail(DDSG_ERR_ARG, "hdmr_eval: the slice-free form needs the anchor at the domain centre");
     if (form == DDSG_FORM_SLICEFREE && !h->closed)
         return fail(DDSG_ERR_ARG, "hdmr_eval: the slice-free form needs a downward-closed component set");
     DeviceGuard g(h->device);
     if (!g.ok) return fail(DDSG_ERR_CUDA, "hdmr_eval: cannot select device");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (h->cfg[precision][form].kernel == KERNEL_NODAL && !h->capturing) {
+        if (int rc0 = ensure_nodal(h, form, st)) return rc0;
+    }
+    if (!eval_kernel_eligible(h->dt, h->cfg[precision][form].kernel, precision, form))
+        h->cfg[precision][form] = EvalConfig();
     int rc = ensure_ws(h, n);
     if (rc) return rc;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     uint64_t *X = reinterpret_cast<uint64_t *>(h->ws);
     {
         ProfScope ps(h, DDSG_K_ENCODE, st);
@@ -1137,6 +1181,9 @@ extern "C" int hdmr_eval_graph(hdmr_t *h, int64_t n, const double *x_dev, double
     if (!h->uploaded || !h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_eval_graph: call hdmr_hierarchize first");
     DeviceGuard g(h->device);
     if (!g.ok) return fail(DDSG_ERR_CUDA, "hdmr_eval_graph: cannot select device");
+    if (h->cfg[precision][form].kernel == KERNEL_NODAL) {   // any allocation happens before the capture
+        if (int rc0 = ensure_nodal(h, form, reinterpret_cast<cudaStream_t>(stream))) return rc0;
+    }
     if (!eval_kernel_eligible(h->dt, h->cfg[precision][form].kernel, precision, form))
         h->cfg[precision][form] = EvalConfig();
     int rc = ensure_ws(h, n);   // any allocation happens before the capture
@@ -1247,8 +1294,16 @@ extern "C" int hdmr_set_eval_config(hdmr_t *h, int precision, int form, int kern
     if (!h) return fail(DDSG_ERR_ARG, "hdmr_set_eval_config: NULL handle");
     if (precision < 0 || precision > 1 || form < 0 || form > 1 || kernel < 0 || kernel >= NKERNELS)
         return fail(DDSG_ERR_ARG, "hdmr_set_eval_config: bad precision/form/kernel");
-    if (h->uploaded && !eval_kernel_eligible(h->dt, kernel, precision, form))
-        return fail(DDSG_ERR_ARG, "hdmr_set_eval_config: kernel %d cannot run these tables (a component's surplus block exceeds the staging buffer)", kernel);
+    if (kernel == KERNEL_NODAL && h->uploaded && h->device >= 0) {
+        DeviceGuard g(h->device);
+        if (int rc0 = ensure_nodal(h, form, nullptr)) return rc0;
+        if (h->have_alpha && cudaDeviceSynchronize() != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DDSG_ERR_CUDA, "hdmr_set_eval_config: computing the node values failed");
+        }
+    }
+    if (h->uploaded && h->have_alpha && !eval_kernel_eligible(h->dt, kernel, precision, form))
+        return fail(DDSG_ERR_ARG, "hdmr_set_eval_config: kernel %d cannot run these tables (a component's staged block exceeds the staging buffer)", kernel);
     int cand[16];
     const int nc = eval_mc_candidates(precision, kernel, cand, 16);
     bool ok = mc == 0;
@@ -1282,6 +1337,10 @@ extern "C" int hdmr_autotune(hdmr_t *h, int64_t n, const double *x_dev, double *
     EvalConfig best;
     double best_t = 1e300;
     for (int kernel = 0; kernel < NKERNELS; ++kernel) {
+        if (kernel == KERNEL_NODAL) {
+            const int rc0 = ensure_nodal(h, form, st);
+            if (rc0) { h->prof = prof; return rc0; }
+        }
         if (!eval_kernel_eligible(h->dt, kernel, precision, form)) continue;
         int cand[16];
         const int nc = eval_mc_candidates(precision, kernel, cand, 16);
@@ -1411,8 +1470,31 @@ int handle_eval_view(hdmr_t *h, int precision, int form, HandleView *v) {
     v->lo = h->dlo;
     v->span = h->dspan;
     v->stats = h->stats;
-    v->cfg = h->cfg[precision][form];
+    const EvalConfig want = h->cfg[precision][form];
+    if (eval_kernel_eligible(h->dt, want.kernel, precision, form)) {
+        v->cfg = want;
+    } else {
+        // tables of the nodal kernel not built yet (this view allocates nothing):
+        // the default schedule for this call, the choice kept; any other
+        // ineligible choice is dropped, as hdmr_eval does
+        if (!(want.kernel == KERNEL_NODAL && !h->dt.nod[form].tried)) h->cfg[precision][form] = EvalConfig();
+        v->cfg = EvalConfig();
+    }
+    v->withhold_from = h->fi_withhold;
     return DDSG_OK;
+}
+
+HandleProfScope::HandleProfScope(hdmr_t *h_, int kind_, cudaStream_t st_) : h(h_), kind(kind_), st(st_) {
+    if (!h->prof || h->capturing) return;
+    a = ProfScope::take(h);
+    b = ProfScope::take(h);
+    if (a) cudaEventRecord(a, st);
+}
+
+HandleProfScope::~HandleProfScope() {
+    if (!h->prof || !a || !b) return;
+    cudaEventRecord(b, st);
+    h->recs.push_back({kind, a, b});
 }
 
 int set_error(int code, const char *msg) { return fail(code, "%s", msg); }

@@ -138,6 +138,44 @@ __device__ __forceinline__ int32_t tuple_row_at(const DevTup &tu, uint32_t off, 
 unsigned long long check_word_take_kernels();
 unsigned long long check_word_take_irbc();
 
+// Nodal-slab tables of one form for the staged nodal kernel (kernel 5, built on
+// first use by ddsg_nodal.cu). A component's evaluated points (all of them in
+// the paper form, the interior ones in the slice-free form) are grouped by
+// their cell (b, cb) in the component's slab dimension; for every group the sum
+// of its points' products is, as a function of the other (nodal) dimension, a
+// piecewise-linear function with kinks on the grid of its finest level A, and
+// is stored by its values at the 2^(A-1) + 1 nodes of that grid. A query then
+// reads two adjacent node rows per slab level b instead of one row per level
+// tuple. Components with k = 1 have one slab (no slab dimension); the constant
+// component has one slab and A = 1.
+//   meta       per component: nslab slab entries {b (0: no slab dimension),
+//              offset of the slab's directory within the meta block}, then
+//              the directory: per cell of each slab level {first node row
+//              relative to the component's first row, or -1 if the cell holds
+//              no point; A}. Each block is padded to a multiple of 16 bytes.
+//   v64 / v32  node rows in FP64 (stride mp64) and FP32 (stride rs32).
+struct DevNodal {
+    int32_t ok = 0;            // built for the current tables (set by nodal_build)
+    int32_t tried = 0;         // a build was attempted for the current tables
+    int32_t vals = 0;          // node values computed from the current surpluses
+    int32_t n = 0;             // processed components
+    int64_t rows = 0;          // node rows
+    int32_t rs32 = 0;          // FP32 row stride in floats (a multiple of 32 when m > 16)
+    int32_t meta_bytes = 0;    // staged meta area (largest meta block, multiple of 128 bytes)
+    int64_t stage_bytes[2] = {0, 0};  // staged bytes of the largest component per precision (meta + rows)
+    int4 *rec = nullptr;       // per processed component: {meta begin (int2 units), nmeta | nslab << 16, first row, nrows}
+    int4 *rec2 = nullptr;      // {component id, nodal dim | slab dim << 16 (0xffff: none), b_u, 0}
+    int2 *meta = nullptr;
+    double *v64 = nullptr;
+    float *v32 = nullptr;
+    // nodalization work: per node row {cell group, node index, A, 0}; per cell group
+    // [begin, end) into gpts; per group point {surplus row, level, index, 0} in the nodal dimension
+    int4 *nrow = nullptr;
+    int2 *grp = nullptr;
+    int4 *gpts = nullptr;
+    int64_t ngrp = 0, ngpts = 0;
+};
+
 struct DevTables {
     int32_t C = 0, T = 0;
     int64_t P = 0, S = 0;
@@ -167,6 +205,7 @@ struct DevTables {
     int64_t stage_bytes[2][2] = {{0, 0}, {0, 0}};  // [form][precision]
     int32_t max_tuples = 0;                        // most level tuples in one component
     int32_t max_level = 0;                         // highest 1D level present anywhere
+    DevNodal nod[2];                               // nodal-slab tables per form (kernel 5)
 };
 
 #if defined(__CUDACC__)
@@ -262,7 +301,8 @@ struct EvalConfig {
     int mc = 0;               // outputs per thread and pass (0 = heuristic)
 };
 
-constexpr int NKERNELS = 5;
+constexpr int NKERNELS = 6;
+constexpr int KERNEL_NODAL = 5;               // the staged nodal-slab kernel
 constexpr int64_t TMA_STAGE_MAX = 84 * 1024;  // largest per-component surplus block staged by TMA
 constexpr int TMA_TUP_MAX = 128;              // most level tuples of one component the staged kernel holds
 
@@ -291,6 +331,29 @@ int eval_mc_candidates(int precision, int kernel, int *out, int cap);
 
 cudaError_t launch_eval(const EvalArgs &a, cudaStream_t st);
 
+// Nodal-slab tables (ddsg_nodal.cu). Host view of one component for the planner.
+struct NodalComp {
+    int k;
+    int32_t dims[KMAX];
+    const uint8_t *lv;    // npts * k levels
+    const uint32_t *ix;   // npts * k indices
+    int64_t npts;
+    int64_t first;        // global id of the component's first point
+    double b;             // eq. 4.2 coefficient
+};
+// Plans and uploads the nodal tables of `form` into `out` (freed first). Tables
+// the staged nodal kernel cannot hold leave out.ok = 0 and return DDSG_OK; a
+// failed allocation or copy returns an error code (message set).
+int nodal_build(int m, int form, const std::vector<NodalComp> &comps, const std::vector<int32_t> &dpos,
+                DevNodal &out);
+void nodal_free(DevNodal &nd);
+// Node values from the FP64 surpluses, then their FP32 copy (asynchronous).
+cudaError_t launch_nodalize(const DevNodal &nd, const double *alpha64, int mp64, int m, cudaStream_t st);
+// true if the staged nodal kernel can run these tables (form, precision)
+bool nodal_eligible(const DevTables &t, int precision, int form);
+struct EvalParams;
+cudaError_t launch_eval_nodal(const EvalParams &p, int precision, int mc, cudaStream_t st);
+
 cudaError_t launch_quadrature(const DevTables &t, int m, double *Q, cudaStream_t st);
 cudaError_t launch_hierarchize(const DevTables &t, int m, const double *values,
                                cudaStream_t st);
@@ -298,14 +361,28 @@ cudaError_t launch_hierarchize(const DevTables &t, int m, const double *values,
 // Read-only view of a hierarchized handle (host pointers to its device tables),
 // for entry points defined outside ddsg_host.cu. Returns DDSG_OK or an error
 // code with the message set (ddsg_last_error).
+// The schedule in `cfg` is one the handle's current tables can run (an
+// ineligible stored choice is reset to the default first, as hdmr_eval does).
 struct HandleView {
     int d = 0, m = 0, device = -1;
     const DevTables *tables = nullptr;
     const double *lo = nullptr, *span = nullptr;
     int64_t *stats = nullptr;
     EvalConfig cfg;
+    int withhold_from = -1;   // failure-path test switch of the handle
 };
 int handle_eval_view(hdmr_t *h, int precision, int form, HandleView *v);
+
+// Event bracket (tracing on) around a launch made outside ddsg_host.cu, counted
+// under `kind` in the handle's hdmr_profile_read totals like hdmr_eval's own.
+struct HandleProfScope {
+    hdmr_t *h;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    HandleProfScope(hdmr_t *h, int kind, cudaStream_t st);
+    ~HandleProfScope();
+};
 
 // Event-based kernel tracer (host): brackets launches with CUDA events on the
 // launching stream while enabled; read() waits for them and sums per kind.

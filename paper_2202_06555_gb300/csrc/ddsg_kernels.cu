@@ -19,40 +19,14 @@
 #include <type_traits>
 
 #include "ddsg_internal.h"
+#include "ddsg_eval.cuh"
+#include "ddsg_tma.cuh"
 
 namespace ddsg {
 
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
-
-__device__ __forceinline__ float pow2m_f(int e) {  // 2^-e, 0 <= e < 126
-    return __int_as_float((127 - e) << 23);
-}
-
-// phi = N * 2^-e as a double, N < 2^63, built from the bits (truncated to 53
-// significant bits; the exact value is N * 2^-e).
-__device__ __forceinline__ double basis_to_f64(uint64_t N, int e) {
-    if (N == 0) return 0.0;
-    const int lz = __clzll((long long)N);
-    const uint64_t mant = (N << lz) >> 11;        // 53 bits, leading one at bit 52
-    const int64_t ex = (int64_t)(63 - lz) - e + 1023;
-    return __longlong_as_double((long long)(((uint64_t)ex << 52) | (mant & ((1ull << 52) - 1))));
-}
-
-// phi = N * 2^-e as a float with 32 significant bits kept before rounding.
-// For l >= 2, e = 63 - l (l >= 3) or 61 (l == 2): N >> (e - 31) < 2^32.
-__device__ __forceinline__ float basis_to_f32(uint64_t N, int e) {
-    if (e <= 31) return __uint2float_rn((uint32_t)N) * pow2m_f(e);
-    return __uint2float_rn((uint32_t)(N >> (e - 31))) * pow2m_f(31);
-}
-
-template <typename W>
-__device__ __forceinline__ W basis_val(const Basis1D &o);
-template <>
-__device__ __forceinline__ double basis_val<double>(const Basis1D &o) { return basis_to_f64(o.N, o.e); }
-template <>
-__device__ __forceinline__ float basis_val<float>(const Basis1D &o) { return basis_to_f32(o.N, o.e); }
 
 __device__ __forceinline__ uint64_t point_key(int c, int k, const uint8_t *lev, const uint32_t *cells) {
     uint64_t z = (uint64_t)(uint32_t)c;
@@ -138,40 +112,6 @@ cudaError_t launch_encode_queries(int64_t n, int d, const double *x, const doubl
 // evaluation
 // ---------------------------------------------------------------------------
 
-struct EvalParams {
-    DevTables t;
-    int d, m;
-    int64_t n;
-    const uint64_t *X;
-    const int32_t *flags;
-    double *y;
-    uint64_t *hash;
-    int32_t *count;
-    int form;
-    unsigned long long *err;
-    int issue_end;         // staging copies issued for processed components < issue_end only
-                           // (INT_MAX unless a failure-path test withholds them)
-};
-
-template <int PREC>
-struct Types;
-template <>
-struct Types<DDSG_F64> {
-    using W = double;
-    using V = double2;
-    static constexpr int VW = 2;
-    static __device__ __forceinline__ const double *alpha(const DevTables &t) { return t.alpha64; }
-    static __device__ __forceinline__ int stride(const DevTables &t) { return t.mp64; }
-};
-template <>
-struct Types<DDSG_F32C> {
-    using W = float;
-    using V = float4;
-    static constexpr int VW = 4;
-    static __device__ __forceinline__ const float *alpha(const DevTables &t) { return t.alpha32; }
-    static __device__ __forceinline__ int stride(const DevTables &t) { return t.mp32; }
-};
-
 // acc[o] += w * alpha_row[m0 + o] for o < MC, reading 16-byte vectors; vectors
 // past the padded row (stride mp) are skipped (never read).
 template <int PREC, int MC>
@@ -196,42 +136,6 @@ __device__ __forceinline__ void accumulate(typename Types<PREC>::W (&acc)[MC], t
         }
     }
 }
-
-// Final per-thread result holder: FP64 accumulates directly; FP32 folds each
-// component's plain-FP32 partial sum into a Kahan-compensated total.
-template <int PREC, int MC>
-struct Result;
-template <int MC>
-struct Result<DDSG_F64, MC> {
-    double s[MC];
-    __device__ __forceinline__ void init() {
-#pragma unroll
-        for (int o = 0; o < MC; ++o) s[o] = 0.0;
-    }
-    __device__ __forceinline__ double (&partial())[MC] { return s; }
-    __device__ __forceinline__ void fold() {}
-    __device__ __forceinline__ double value(int o) const { return s[o]; }
-};
-template <int MC>
-struct Result<DDSG_F32C, MC> {
-    float p[MC], s[MC], c[MC];
-    __device__ __forceinline__ void init() {
-#pragma unroll
-        for (int o = 0; o < MC; ++o) p[o] = s[o] = c[o] = 0.0f;
-    }
-    __device__ __forceinline__ float (&partial())[MC] { return p; }
-    __device__ __forceinline__ void fold() {
-#pragma unroll
-        for (int o = 0; o < MC; ++o) {
-            const float yk = __fsub_rn(p[o], c[o]);
-            const float tk = __fadd_rn(s[o], yk);
-            c[o] = __fsub_rn(__fsub_rn(tk, s[o]), yk);
-            s[o] = tk;
-            p[o] = 0.0f;
-        }
-    }
-    __device__ __forceinline__ double value(int o) const { return (double)s[o] - (double)c[o]; }
-};
 
 // Per-tuple evaluation of one component (any k), basis recomputed per tuple.
 template <int PREC, int MC, bool HC>
@@ -491,57 +395,6 @@ __global__ void __launch_bounds__(TQ) eval_tile_kernel(const EvalParams p) {
 // copied into shared memory by a bulk TMA copy two components ahead.
 // ---------------------------------------------------------------------------
 
-// try_wait calls before a wait gives up. A try_wait that finds the phase still
-// open suspends the thread for about 3.7 us on GB300 (2^22 of them took 15.6 s),
-// so this is about one second: far above any real wait here (a component's
-// staging copy, or the block finishing one component: well under a millisecond).
-constexpr uint32_t kWaitLimit = 1u << 18;
-constexpr int kSmemLimit = 232448;          // opt-in shared memory per block (227 KiB)
-constexpr int TMA_NBUF_MAX = 3;             // staging buffers of the TMA-staged kernel
-constexpr int TMA_PB_MAX = 32;              // tuples probed per pass of the TMA-staged kernel
-
-__device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
-    return (uint32_t)__cvta_generic_to_shared(ptr);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Wait for phase `parity` of `bar` with an iteration limit; false if it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
 // Block shape of the TMA-staged kernel with GR warp groups: QB queries per
 // block; each query's output chunk is split over GR threads (one per group).
 template <int GR>
@@ -589,6 +442,7 @@ static int tma_qb(int kernel) {
 
 bool eval_kernel_eligible(const DevTables &t, int kernel, int precision, int form) {
     if (kernel == 0 || kernel == 1) return true;
+    if (kernel == KERNEL_NODAL) return nodal_eligible(t, precision, form);
     if (kernel < 2 || kernel > 4) return false;
     if (!t.tile_ok) return false;   // the staged kernel handles only k <= 2, levels <= LT
     if (t.max_tuples > TMA_TUP_MAX) return false;
@@ -1096,8 +950,17 @@ static const int MC_F32_GR2[] = {8, 16, 28};
 static const int MC_F64_GR3[] = {4, 8};
 static const int MC_F32_GR3[] = {12, 20};
 
+// the nodal-slab kernel (5): 32 = the rotated two-window layout (FP32)
+static const int MC_F64_NOD[] = {4, 8, 16};
+static const int MC_F32_NOD[] = {32, 8, 16};
+
 int eval_mc_candidates(int precision, int kernel, int *out, int cap) {
     const bool f64 = precision == DDSG_F64;
+    if (kernel == KERNEL_NODAL) {
+        const int *src = f64 ? MC_F64_NOD : MC_F32_NOD;
+        for (int i = 0; i < 3 && i < cap; ++i) out[i] = src[i];
+        return 3 < cap ? 3 : cap;
+    }
     const int *src = kernel == 4 ? (f64 ? MC_F64_GR3 : MC_F32_GR3)
                      : kernel == 3 ? (f64 ? MC_F64_GR2 : MC_F32_GR2) : (f64 ? MC_F64 : MC_F32);
     const int n = kernel == 4 ? 2 : (kernel == 3 ? 3 : 6);
@@ -1154,9 +1017,16 @@ cudaError_t launch_eval(const EvalArgs &a, cudaStream_t st) {
     p.err = a.err;
     p.issue_end = a.withhold_from < 0 ? INT_MAX : a.withhold_from;
     const bool hc = a.hash != nullptr || a.count != nullptr;
-    const int mc = a.cfg.mc > 0 ? a.cfg.mc : default_mc(a.precision, a.m);
-    if (a.precision == DDSG_F64) return launch_prec<DDSG_F64>(p, a.cfg.kernel, mc, hc, st);
-    return launch_prec<DDSG_F32C>(p, a.cfg.kernel, mc, hc, st);
+    EvalConfig cfg = a.cfg;
+    if (cfg.kernel == KERNEL_NODAL) {
+        // the nodal form has no per-point active set: hash / count requests
+        // run the level-tuple tile kernel
+        if (!hc) return launch_eval_nodal(p, a.precision, cfg.mc > 0 ? cfg.mc : (a.precision == DDSG_F64 ? 8 : 32), st);
+        cfg = EvalConfig();
+    }
+    const int mc = cfg.mc > 0 ? cfg.mc : default_mc(a.precision, a.m);
+    if (a.precision == DDSG_F64) return launch_prec<DDSG_F64>(p, cfg.kernel, mc, hc, st);
+    return launch_prec<DDSG_F32C>(p, cfg.kernel, mc, hc, st);
 }
 
 // ---------------------------------------------------------------------------

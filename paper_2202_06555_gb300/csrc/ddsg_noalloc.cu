@@ -15,6 +15,15 @@
 // and the per-query flags of its n queries), so nothing has to be cleared.
 // Two calls whose kernels overlap on the GPU (e.g. on two streams) race on it:
 // serialize them.
+//
+// Set-up: the first call on a device (a call with n = 0 does only this) looks
+// up the array's device address there. Under lazy module loading (CUDA's
+// default) that lookup is also what loads the array's module on the device, so
+// the 16 MiB are committed then: a caller under a hard memory cap makes that
+// first call while it sets up, before its cap or any stream capture begins.
+// The cached address is that of the device's current context; after a
+// cudaDeviceReset every handle's tables are gone too, so no handle created
+// before the reset may be used again, with this entry point or any other.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -66,8 +75,7 @@ extern "C" int hdmr_eval_noalloc(hdmr_t *h, int64_t n, const double *x_dev, doub
     HandleView v;
     int rc = handle_eval_view(h, precision, form, &v);
     if (rc) return rc;
-    if (n == 0) return DDSG_OK;
-    if (!x_dev || !y_dev) return set_error(DDSG_ERR_ARG, "hdmr_eval_noalloc: NULL x or y");
+    if (n > 0 && (!x_dev || !y_dev)) return set_error(DDSG_ERR_ARG, "hdmr_eval_noalloc: NULL x or y");
     if (n > hdmr_eval_noalloc_capacity(v.d))
         return set_error(DDSG_ERR_ARG,
                          "hdmr_eval_noalloc: batch too large for the 16 MiB static scratch "
@@ -79,8 +87,12 @@ extern "C" int hdmr_eval_noalloc(hdmr_t *h, int64_t n, const double *x_dev, doub
     uint64_t *X = nullptr;
     rc = scratch_address(v.device, &X);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (!rc) {
-        cudaError_t e = launch_encode_queries(n, v.d, x_dev, v.lo, v.span, X, v.stats, st);
+    if (!rc && n > 0) {
+        cudaError_t e;
+        {
+            HandleProfScope ps(h, DDSG_K_ENCODE, st);
+            e = launch_encode_queries(n, v.d, x_dev, v.lo, v.span, X, v.stats, st);
+        }
         if (e == cudaSuccess) {
             EvalArgs a;
             a.t = v.tables;
@@ -94,6 +106,9 @@ extern "C" int hdmr_eval_noalloc(hdmr_t *h, int64_t n, const double *x_dev, doub
             a.form = form;
             a.precision = precision;
             a.cfg = v.cfg;
+            a.err = reinterpret_cast<unsigned long long *>(v.stats + 2);   // bounded waits that gave up
+            a.withhold_from = v.withhold_from;
+            HandleProfScope ps(h, DDSG_K_EVAL, st);
             e = launch_eval(a, st);
         }
         if (e != cudaSuccess) rc = set_error(DDSG_ERR_CUDA, cudaGetErrorString(e));

@@ -47,32 +47,89 @@ def build_pair(G, d, m, comps, fn, eps=None, level=None, regular_level=2, strict
     return ref, h
 
 
-def eval_gpu(h, X, prec, form, m):
+def eval_gpu(h, X, prec, form, m, index=True):
+    """Values from the configured schedule (no hash/count outputs, which the nodal
+    kernel does not produce); with index=True also the active-set hashes and
+    counts, from a second call that asks for them."""
     n = X.shape[0]
     xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     y = torch.full((n, m), -7.0, dtype=torch.float64, device="cuda")
-    hs = torch.zeros(n, dtype=torch.int64, device="cuda")
-    ct = torch.zeros(n, dtype=torch.int32, device="cuda")
-    h.eval(xd, y, prec, form, hs, ct)
+    h.eval(xd, y, prec, form)
+    hs = ct = None
+    if index:
+        y2 = torch.full((n, m), -7.0, dtype=torch.float64, device="cuda")
+        hs = torch.zeros(n, dtype=torch.int64, device="cuda")
+        ct = torch.zeros(n, dtype=torch.int32, device="cuda")
+        h.eval(xd, y2, prec, form, hs, ct)
+        hs, ct = hs.cpu().numpy().view(np.uint64), ct.cpu().numpy()
     torch.cuda.synchronize()
-    return y.cpu().numpy(), hs.cpu().numpy().view(np.uint64), ct.cpu().numpy()
+    return y.cpu().numpy(), hs, ct
 
 
-def check_eval(h, ref, X, forms=(0, 1), precs=(0, 1)):
+def oracle_results(ref, X, forms=(0, 1)):
+    return {form: ref.eval(X, form=form, want=("y", "S", "hash", "count")) for form in forms}
+
+
+def check_values(y, r, prec, what=""):
+    """|y - y_oracle| <= TOL * max(|y|, S) on finite rows; NaN exactly on the others."""
+    scale = np.maximum(np.abs(r["y"]), r["S"])
+    fin = np.isfinite(r["y"]).all(1)
+    assert np.array_equal(np.isnan(y).any(1), ~fin), what
+    rel = np.abs(y[fin] - r["y"][fin]) / np.where(scale[fin] > 0, scale[fin], 1.0)
+    assert rel.max(initial=0.0) <= TOL[prec], (what, rel.max())
+    return float(rel.max(initial=0.0))
+
+
+def check_eval(h, ref, X, forms=(0, 1), precs=(0, 1), res=None):
     worst = {}
+    res = res or oracle_results(ref, X, forms)
     for form in forms:
-        r = ref.eval(X, form=form, want=("y", "S", "hash", "count"))
-        scale = np.maximum(np.abs(r["y"]), r["S"])
+        r = res[form]
         for prec in precs:
             y, hs, ct = eval_gpu(h, X, prec, form, ref.m)
             assert np.array_equal(ct, r["count"]), (form, prec)
             assert np.array_equal(hs, r["hash"]), (form, prec)
-            fin = np.isfinite(r["y"]).all(1)
-            assert np.array_equal(np.isnan(y).any(1), ~fin)
-            rel = np.abs(y[fin] - r["y"][fin]) / np.where(scale[fin] > 0, scale[fin], 1.0)
-            assert rel.max(initial=0.0) <= TOL[prec], (form, prec, rel.max())
-            worst[(form, prec)] = float(rel.max(initial=0.0))
+            worst[(form, prec)] = check_values(y, r, prec, (form, prec))
     return worst
+
+
+# compiled (kernel, output chunk) pairs per precision: 0 tile, 1 per-tuple, 2-4 the
+# level-tuple TMA kernels (chunk per warp group), 5 the nodal-slab kernel (32 = rotated windows)
+SCHEDULES = {
+    0: [(0, mc) for mc in (2, 4, 6, 8, 12, 16)] + [(1, mc) for mc in (2, 4, 6, 8, 12, 16)] +
+       [(2, mc) for mc in (2, 4, 6, 8, 12, 16)] + [(3, mc) for mc in (4, 8, 16)] + [(4, mc) for mc in (4, 8)] +
+       [(5, mc) for mc in (4, 8, 16)],
+    1: [(0, mc) for mc in (4, 8, 12, 16, 28, 52)] + [(1, mc) for mc in (4, 8, 12, 16, 28, 52)] +
+       [(2, mc) for mc in (4, 8, 12, 16, 28, 52)] + [(3, mc) for mc in (8, 16, 28)] + [(4, mc) for mc in (12, 20)] +
+       [(5, mc) for mc in (32, 8, 16)],
+}
+
+
+def check_every_schedule(G, h, ref, X, forms=(0, 1), precs=(0, 1), kernels=(0, 1, 2, 3, 4, 5)):
+    """Every eligible schedule against the oracle on the same queries, both forms:
+    values within the bar, the index work (hash / count) once per form. Returns
+    the schedules run and the worst relative error per (form, precision)."""
+    res = oracle_results(ref, X, forms)
+    ran, worst = [], {}
+    saved = {(p, f): h.eval_config(p, f) for p in precs for f in forms}
+    for form in forms:
+        for prec in precs:
+            _, hs, ct = eval_gpu(h, X, prec, form, ref.m)
+            assert np.array_equal(ct, res[form]["count"]) and np.array_equal(hs, res[form]["hash"]), (form, prec)
+            for kernel, mc in SCHEDULES[prec]:
+                if kernel not in kernels:
+                    continue
+                try:
+                    h.set_eval_config(prec, form, kernel, mc)
+                except G.DDSGError as e:
+                    assert "cannot run" in str(e), e
+                    continue
+                y, _, _ = eval_gpu(h, X, prec, form, ref.m, index=False)
+                e = check_values(y, res[form], prec, (form, prec, kernel, mc))
+                worst[(form, prec)] = max(worst.get((form, prec), 0.0), e)
+                ran.append((form, prec, kernel, mc))
+            h.set_eval_config(prec, form, *saved[(prec, form)])
+    return ran, worst
 
 
 def check_grids(h, ref):
@@ -136,6 +193,9 @@ def test_adaptive_d4_order2(G, strict):
     check_surpluses(h, ref)
     X = np.concatenate([synth.uniform_queries(32, 4000, d), ref.node_coords(5)[:, [0, 0, 0, 0]]])
     check_eval(h, ref, X)
+    # node coordinates sit on cell faces of the finer levels: every schedule
+    ran, _ = check_every_schedule(G, h, ref, X[-600:])
+    assert {k for _, _, k, _ in ran} == {0, 1, 2, 3, 4, 5}
 
 
 def test_adaptive_d20_order2_monomial_queries(G):
@@ -153,6 +213,9 @@ def test_adaptive_d20_order2_monomial_queries(G):
     w = check_eval(h, ref, X)
     st = h.stats()
     assert st["clamped"] > 0 and st["nonfinite_rows"] == 0
+    # clamped coordinates at exactly 0 and 1 through every schedule
+    ran, _ = check_every_schedule(G, h, ref, X[:400])
+    assert {k for _, _, k, _ in ran} == {0, 1, 2, 3, 4, 5}
 
 
 def test_edge_queries(G):
@@ -171,10 +234,16 @@ def test_edge_queries(G):
     check_eval(h, ref, X)
     check_eval(h, ref, X[:1])
     h.stats(reset=True)
-    check_eval(h, ref, X, forms=(0,), precs=(0,))
+    eval_gpu(h, X, 0, 0, m, index=False)        # one evaluation call
     assert h.stats()["nonfinite_rows"] == 3
     y = torch.zeros((0, m), dtype=torch.float64, device="cuda")
     h.eval(torch.zeros((0, d), dtype=torch.float64, device="cuda"), y)
+    # the same edge cases (faces, corners, clamps, NaN / inf rows, denormals) through
+    # every schedule, including the staged kernels' face flags and bad-row path
+    ran, _ = check_every_schedule(G, h, ref, X)
+    assert {k for _, _, k, _ in ran} == {0, 1, 2, 3, 4, 5}
+    ran1, _ = check_every_schedule(G, h, ref, X[:1])
+    assert len(ran1) == len(ran)
 
 
 def test_physical_domain_and_anchor(G):
@@ -218,21 +287,13 @@ def test_every_kernel_config_matches_oracle(G):
     fn = lambda dims, X: synth.family_cut(c, dims, X)
     ref, h = build_pair(G, d, m, O.full_order_components(d, 2), fn, eps=1e-3, level=9)
     X = synth.uniform_queries(56, 700, d)
-    mcs = {0: [2, 4, 6, 8, 12, 16], 1: [4, 8, 12, 16, 28, 52]}
-    mcs3 = {0: [4, 8, 16], 1: [8, 16, 28]}   # the two-group TMA kernel: chunk per group
-    mcs4 = {0: [4, 8], 1: [12, 20]}          # the three-group TMA kernel
-    pick = lambda kernel: mcs4 if kernel == 4 else (mcs3 if kernel == 3 else mcs)
-    for prec in (0, 1):
-        for kernel in (0, 1, 2, 3, 4):
-            for mc in pick(kernel)[prec]:
-                h.set_eval_config(prec, 1, kernel, mc)
-                h.set_eval_config(prec, 0, kernel, mc)
-                check_eval(h, ref, X, precs=(prec,))
+    ran, _ = check_every_schedule(G, h, ref, X)
+    assert len(ran) == 2 * (len(SCHEDULES[0]) + len(SCHEDULES[1]))
     xd = torch.from_numpy(X).cuda()
     yd = torch.empty((X.shape[0], m), dtype=torch.float64, device="cuda")
     for prec in (0, 1):
         kernel, mc, ms = h.autotune(xd, yd, prec, 1)
-        assert kernel in (0, 1, 2, 3, 4) and mc in pick(kernel)[prec] and ms > 0
+        assert (kernel, mc) in SCHEDULES[prec] and ms > 0
         check_eval(h, ref, X, forms=(1,), precs=(prec,))
     with pytest.raises(G.DDSGError, match="not compiled"):
         h.set_eval_config(0, 0, 0, 5)
@@ -254,4 +315,6 @@ def test_staged_kernel_refuses_tables_it_cannot_hold(G):
         h.set_eval_config(0, 0, 3, 4)
     with pytest.raises(G.DDSGError, match="cannot run"):
         h.set_eval_config(0, 0, 4, 4)
+    with pytest.raises(G.DDSGError, match="cannot run"):
+        h.set_eval_config(1, 1, 5, 32)
     check_eval(h, ref, synth.uniform_queries(33, 500, d))

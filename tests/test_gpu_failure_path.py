@@ -21,8 +21,9 @@ from test_gpu_eval import build_pair, TOL
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# queries per block and threads per block of the staged kernels 2, 3, 4
-SHAPE = {2: (256, 256), 3: (192, 384), 4: (160, 480)}
+# queries per block and threads per block of the staged kernels 2, 3, 4 and of the
+# nodal-slab kernel 5 at a one-window chunk
+SHAPE = {2: (256, 256), 3: (192, 384), 4: (160, 480), 5: (256, 256)}
 
 
 @pytest.fixture(scope="module")
@@ -49,7 +50,7 @@ def _eval(h, x, m, prec, form, graph=False):
     return y.cpu().numpy()
 
 
-@pytest.mark.parametrize("kernel,prec,withhold", [(3, 1, 3), (2, 0, 0), (4, 1, 1)])
+@pytest.mark.parametrize("kernel,prec,withhold", [(3, 1, 3), (2, 0, 0), (4, 1, 1), (5, 1, 2), (5, 0, 0)])
 def test_withheld_copies_time_out_and_context_recovers(G, pair, kernel, prec, withhold):
     ref, h = pair
     m, form = ref.m, 1
@@ -57,7 +58,7 @@ def test_withheld_copies_time_out_and_context_recovers(G, pair, kernel, prec, wi
     n = qb + 37                                   # two blocks, the second ragged
     X = synth.uniform_queries(97, n, ref.d)
     x = torch.from_numpy(X).cuda()
-    mc = {(2, 0): 4, (3, 1): 8, (4, 1): 12}[(kernel, prec)]
+    mc = {(2, 0): 4, (3, 1): 8, (4, 1): 12, (5, 1): 16, (5, 0): 8}[(kernel, prec)]
     saved = h.eval_config(prec, form)
     h.set_eval_config(prec, form, kernel, mc)
     assert h.eval_config(prec, form) == (kernel, mc)
@@ -74,7 +75,7 @@ def test_withheld_copies_time_out_and_context_recovers(G, pair, kernel, prec, wi
     dt = time.perf_counter() - t0
     st = h.stats(reset=True)
     assert np.isnan(y).all()
-    nblocks = -(-n // qb) * -(-m // (mc * {2: 1, 3: 2, 4: 3}[kernel]))
+    nblocks = -(-n // qb) * -(-m // (mc * {2: 1, 3: 2, 4: 3, 5: 1}[kernel]))
     assert st["wait_timeouts"] == nblocks * nt // 32, (st, dt)
     print(f"kernel {kernel}: failed evaluation took {dt:.3f} s")
 

@@ -1,9 +1,12 @@
-"""Parity at the full workload sizes, in the launch configuration bench.py
+"""Parity at the full workload sizes, in the launch configurations bench.py
 times, on outputs the oracle can compute one by one: d = 100 (2e6 uniform
-queries, FP32-compensated, slice-free, the two-group TMA kernel at 28 outputs
-per group) and d = 20 (4.4e5 monomial-shaped queries, FP64). Sampled rows are
-checked against the oracle's brute force (values, active-point counts and
-hashes); every row is checked for finiteness."""
+queries, FP32-compensated, slice-free; the nodal-slab kernel with its rotated
+two-window layout and the two-group level-tuple TMA kernel at 28 outputs per
+group) and d = 20 (4.4e5 monomial-shaped queries, FP64; the tile kernel and the
+nodal-slab kernel). Sampled rows of the timed launch (no hash / count outputs)
+are checked against the oracle's brute force; the active-point counts and
+hashes of the same rows come from the level-tuple kernels (the nodal form has
+no per-point active set); every row is checked for finiteness."""
 import numpy as np
 import pytest
 
@@ -47,12 +50,13 @@ def _check(G, ref, h, X, prec, form, kernel, mc, tol, nsample=48):
     y2 = torch.empty_like(y)
     h.eval(x, y2, prec, form)            # the timed launch (no hash / count outputs)
     torch.cuda.synchronize()
-    assert torch.equal(y, y2)
-    assert bool(torch.isfinite(y).all())
+    if kernel != 5:
+        assert torch.equal(y, y2)
+    assert bool(torch.isfinite(y2).all())
     idx = np.unique(np.concatenate([[0, 1, n - 2, n - 1],
                                     (synth.uniform(synth.BASE_SEED + 900, nsample) * n).astype(np.int64)]))
     r = ref.eval(X[idx], form=form, want=("y", "S", "hash", "count"))
-    ys = y[torch.from_numpy(idx).cuda()].cpu().numpy()
+    ys = y2[torch.from_numpy(idx).cuda()].cpu().numpy()
     scale = np.maximum(np.abs(r["y"]), r["S"])
     assert np.max(np.abs(ys - r["y"]) / scale) <= tol
     assert np.array_equal(ct[torch.from_numpy(idx).cuda()].cpu().numpy(), r["count"])
@@ -60,16 +64,24 @@ def _check(G, ref, h, X, prec, form, kernel, mc, tol, nsample=48):
     assert h.stats()["wait_timeouts"] == 0
 
 
-def test_d100_two_million_queries_f32c(G):
+@pytest.fixture(scope="module")
+def d100(G):
     ref, h = _pair(G, 100, 51, synth.W_D100)
     assert h.sizes() == (5051, 1357149)
     X = synth.uniform_queries(synth.BASE_SEED + synth.W_D100, 2_000_000, 100)
-    _check(G, ref, h, X, G.F32C, G.FORM_SLICEFREE, 3, 28, 1e-6)
+    return ref, h, X
 
 
-def test_d20_monomial_queries_f64(G):
+@pytest.mark.parametrize("kernel,mc", [(5, 32), (3, 28)])
+def test_d100_two_million_queries_f32c(G, d100, kernel, mc):
+    ref, h, X = d100
+    _check(G, ref, h, X, G.F32C, G.FORM_SLICEFREE, kernel, mc, 1e-6)
+
+
+@pytest.mark.parametrize("kernel,mc", [(0, 12), (5, 8)])
+def test_d20_monomial_queries_f64(G, kernel, mc):
     ref, h = _pair(G, 20, 11, synth.W_D20)
     assert h.sizes() == (211, 52981)
     X = synth.monomial_shaped_queries(synth.BASE_SEED + synth.W_D20, 20_000, 10)
     assert X.shape[0] == 440_000
-    _check(G, ref, h, X, G.F64, G.FORM_SLICEFREE, 0, 12, 1e-12, nsample=200)
+    _check(G, ref, h, X, G.F64, G.FORM_SLICEFREE, kernel, mc, 1e-12, nsample=200)

@@ -75,7 +75,7 @@ def test_graph_reads_inputs_by_address_and_recaptures(G, pair):
     torch.cuda.synchronize()
     assert np.array_equal(ys.cpu().numpy(), _direct(h, x[: n // 2], m, 1, 1))
     # another schedule captures again
-    for kernel, mc in ((0, 12), (2, 16), (1, 52)):
+    for kernel, mc in ((0, 12), (2, 16), (1, 52), (5, 16)):
         h.set_eval_config(1, 1, kernel, mc)
         h.eval_graph(x, y, 1, 1)
         torch.cuda.synchronize()

@@ -8,7 +8,10 @@ so that pytest collects it last. It must pass alone in a fresh process and
 after the other tests. It checks the new entry point against hdmr_eval
 through the C ABI, on two calls in a row with different inputs (the shared
 array keeps the previous call's contents), and that oversized batches are
-refused before anything runs.
+refused before anything runs. Both entry points run the same kernels on the
+same schedule, so their results must agree bit for bit. It also checks that a
+staged schedule chosen before the tables changed is not used on tables it
+cannot run, and that a staging wait that gives up is reported by hdmr_check.
 """
 import ctypes as C
 
@@ -20,7 +23,6 @@ import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 1e-6}   # FP64 / FP32-compensated, relative to max(|y|, 1)
 
 
 @pytest.fixture(scope="module")
@@ -71,7 +73,7 @@ def test_noalloc_matches_existing_entry_point_twice(built, prec, form):
     for X in (X1, X2):           # two calls in a row, different sizes and inputs
         ref = _eval_existing(G, h, X, prec, form)
         got = _eval_noalloc_abi(G, h, X, prec, form)
-        assert np.all(np.abs(got - ref) <= TOL[prec] * np.maximum(np.abs(ref), 1.0))
+        assert np.array_equal(got, ref)
 
 
 def test_noalloc_refuses_oversized_batch(built):
@@ -84,4 +86,59 @@ def test_noalloc_refuses_oversized_batch(built):
     # the largest accepted batch still works
     got = _eval_noalloc_abi(G, h, X[:cap], 0, 0)
     ref = _eval_existing(G, h, X[:cap], 0, 0)
-    assert np.all(np.abs(got - ref) <= TOL[0] * np.maximum(np.abs(ref), 1.0))
+    assert np.array_equal(got, ref)
+
+
+def test_noalloc_zero_batch_only_sets_up(built):
+    G, h = built
+    lib = G.load()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.hdmr_eval_noalloc(h._h, 0, None, None, 1, 1, stream) == 0, lib.ddsg_last_error()
+
+
+def test_noalloc_drops_a_schedule_the_new_tables_cannot_run(built):
+    """A staged kernel chosen while every component had k <= 2 must not run once
+    an order-3 component is added: the call falls back like hdmr_eval does."""
+    G, _ = built
+    d, m = 4, 3
+    c = synth.family_coeffs(synth.BASE_SEED + 80, m, d)
+    fn = lambda dims, X: synth.family_cut(c, dims, X)
+    h = G.HDMR(d, m, 3)
+    import itertools
+    for k in range(3):
+        for u in itertools.combinations(range(d), k):
+            h.add_regular(list(u), 2)
+    G.build_adaptive(h, fn, 1e-3, 6)
+    h.set_eval_config(1, 0, 3, 8)
+    assert h.eval_config(1, 0) == (3, 8)
+    h.add_regular([0, 1, 2], 2)           # k = 3: the staged kernels cannot hold it
+    G.build_adaptive(h, fn, 1e-3, 6)
+    X = synth.uniform_queries(synth.BASE_SEED + 81, 500, d)
+    got = _eval_noalloc_abi(G, h, X, 1, 0)
+    assert h.eval_config(1, 0)[0] in (0, 1)
+    ref = _eval_existing(G, h, X, 1, 0)
+    assert np.array_equal(got, ref)
+    h.close()
+
+
+def test_noalloc_reports_a_wait_that_gave_up(built):
+    """The failure-path switch withholds staging copies; the no-alloc call must
+    count the waits that ran out so that hdmr_check reports them."""
+    G, h = built
+    saved = h.eval_config(1, 1)
+    h.set_eval_config(1, 1, 3, 8)
+    X = synth.uniform_queries(synth.BASE_SEED + 82, 400, h.d)
+    want = _eval_noalloc_abi(G, h, X, 1, 1)
+    h.check()
+    h.set_fault_injection(1)
+    try:
+        y = _eval_noalloc_abi(G, h, X, 1, 1)
+        assert np.isnan(y).all()
+        with pytest.raises(G.DDSGError):
+            h.check()
+    finally:
+        h.set_fault_injection(-1)
+    h.stats(reset=True)
+    assert np.array_equal(_eval_noalloc_abi(G, h, X, 1, 1), want)
+    h.check()
+    h.set_eval_config(1, 1, *saved)
