@@ -585,6 +585,294 @@ __global__ void __launch_bounds__(NodShape<GR>::NT, 1) eval_nodal_kernel(const E
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32-compensated nodal-slab kernel with paired FP32 arithmetic: the node rows
+// of a thread's 32-output window are read as eight 16-byte chunks in the order
+// s ^ (lane mod 8) (s = 0..7), so the 8 lanes of a quarter-warp read 8 different
+// bank groups; each chunk feeds two fma.rn.f32x2 per row. The per-component
+// partials (pairs of FP32) are folded every second component into a Kahan
+// total (add / sub .rn.f32x2, no contraction).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Slab cell and hat value from x31 = X >> 31 (31 fraction bits) for slab levels
+// b <= 10 (at least 23 bits of the position inside the cell), else from X.
+__device__ __forceinline__ void slab_basis_f32(uint64_t X, uint32_t x31, int b, uint32_t &cb, float &phi) {
+    if (b <= 1) {
+        cb = 0;
+        phi = 1.0f;
+    } else if (b == 2) {
+        const uint32_t half = 1u << 30;
+        cb = x31 >= half ? 1u : 0u;
+        phi = __uint2float_rn(x31 >= half ? x31 - half : half - x31) * pow2m_f(30);
+    } else if (b <= 10) {
+        const int sh = 33 - b;
+        uint32_t cell = x31 >> sh;
+        const uint32_t nmax = (1u << (b - 2)) - 1u;
+        cell = cell > nmax ? nmax : cell;
+        const uint32_t F = x31 - (cell << sh);
+        const uint32_t R = (1u << sh) - F;
+        cb = cell;
+        phi = __uint2float_rn(F < R ? F : R) * pow2m_f(sh - 1);
+    } else {
+        slab_basis<DDSG_F32C>(X, b, cb, phi);
+    }
+}
+
+// Node interval and position from x31 for nodal levels A <= 10, else from X.
+__device__ __forceinline__ void node_pos_f32(uint64_t X, uint32_t x31, int A, uint32_t &kk, float &t) {
+    if (A <= 10) {
+        const int sh = 32 - A;
+        uint32_t k = x31 >> sh;
+        const uint32_t kmax = (1u << (A - 1)) - 1u;
+        k = k > kmax ? kmax : k;
+        kk = k;
+        t = __uint2float_rn(x31 - (k << sh)) * pow2m_f(sh);
+    } else {
+        node_pos<DDSG_F32C>(X, A, kk, t);
+    }
+}
+
+struct NodProbe {
+    int32_t r0;     // first of the two node rows (staged row index), 0 when inactive
+    float w0, w1;   // weights of rows r0 and r0 + 1 (zero when inactive)
+    bool act;
+};
+
+// Slab sl of the staged component: cell, directory entry, node interval, weights.
+__device__ __forceinline__ NodProbe nodal_probe(const int2 *meta, int sl, int nmeta, int nrows, uint64_t Xs,
+                                                uint32_t xs31, uint64_t Xn, uint32_t xn31, bool bad, float wb) {
+    NodProbe pr;
+    const int2 se = meta[sl];
+    uint32_t cb;
+    float phi;
+    slab_basis_f32(Xs, xs31, se.x, cb, phi);
+    const int di = se.y + (int)cb;
+    const int2 de = DDSG_CK(di >= 0 && di < nmeta, CK_STAGE) ? meta[di] : make_int2(-1, 1);
+    pr.act = !bad && de.x >= 0 && phi != 0.0f;
+    uint32_t kk = 0;
+    float t = 0.0f;
+    node_pos_f32(Xn, xn31, pr.act ? de.y : 1, kk, t);
+    pr.r0 = pr.act ? de.x + (int32_t)kk : 0;
+    if (!DDSG_CK(pr.r0 >= 0 && pr.r0 + 1 < nrows, CK_ROW)) {
+        pr.act = false;
+        pr.r0 = 0;
+    }
+    (void)nmeta;
+    (void)nrows;
+    const float pw = phi * wb;
+    pr.w1 = pr.act ? pw * t : 0.0f;
+    pr.w0 = pr.act ? pw * (1.0f - t) : 0.0f;
+    return pr;
+}
+
+template <int GR>
+__global__ void __launch_bounds__(NodShape<GR>::NT, 1) eval_nodal_f32x2_kernel(const EvalParams p, int buf_bytes,
+                                                                              int nbuf) {
+    constexpr int QB = NodShape<GR>::QB;
+    constexpr int QW = NodShape<GR>::QW;
+    constexpr int kWarps = NodShape<GR>::NT / 32;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + TMA_NBUF_MAX;
+    unsigned char *bufbase = smem + 128;
+
+    const DevNodal &N = p.t.nod[p.form];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int grp = warp / QW;
+    const int qw = warp - grp * QW;
+    const int qi = qw * 32 + lane;
+    const int64_t q = (int64_t)blockIdx.x * QB + qi;
+    const int64_t qc = q < p.n ? q : p.n - 1;
+    const bool valid = q < p.n;
+    const bool bad = !valid || p.flags[q] != 0;
+    const bool paper = p.form == DDSG_FORM_PAPER;
+    const int m = p.m;
+    const int rs = N.rs32;
+    const int m0 = (blockIdx.y * GR + grp) * 32;
+    const bool wact = m0 < rs;
+    const int nproc = N.n;
+    const int meta_bytes = N.meta_bytes;
+    const int l8 = lane & 7;
+
+    auto issue = [&](int j, int4 rec) {
+        if (j >= p.issue_end) return;
+        const int b = j % nbuf;
+        const uint32_t nmeta = (uint32_t)rec.y & 0xffffu;
+        const uint32_t mbytes = (nmeta * 8u + 15u) & ~15u;
+        const uint32_t rbytes = (uint32_t)rec.w * (uint32_t)rs * 4u;
+        if (!DDSG_CK(mbytes <= (uint32_t)meta_bytes && (int64_t)meta_bytes + rbytes <= (int64_t)buf_bytes &&
+                         rec.z >= 0 && (int64_t)rec.z + rec.w <= N.rows,
+                     CK_STAGE))
+            return;
+        unsigned char *dst = bufbase + (size_t)b * buf_bytes;
+        mbar_expect_tx(&full[b], mbytes + rbytes);
+        tma_bulk_g2s(dst, N.meta + rec.x, mbytes, &full[b]);
+        if (rbytes) tma_bulk_g2s(dst + meta_bytes, N.v32 + (int64_t)rec.z * rs, rbytes, &full[b]);
+    };
+
+    if (tid == 0) {
+        for (int b = 0; b < nbuf; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], kWarps);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int nissued = 0;
+    int4 rec_next = make_int4(0, 0, 0, 0);
+    if (tid == 0) {
+        if (nproc > 0) issue(0, N.rec[0]);
+        if (nproc > 1) issue(1, N.rec[1]);
+        nissued = nproc < 2 ? nproc : 2;
+        if (nproc > 2) rec_next = N.rec[2];
+    }
+
+    uint64_t acc[16], ks[16], kc[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc[u] = ks[u] = kc[u] = 0ull;
+    auto fold = [&]() {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const uint64_t yk = f2_sub(acc[u], kc[u]);
+            const uint64_t tk = f2_add(ks[u], yk);
+            kc[u] = f2_sub(f2_sub(tk, ks[u]), yk);
+            ks[u] = tk;
+            acc[u] = 0ull;
+        }
+    };
+    bool failed = false;
+    int pfail = 0;
+    auto coord = [&](uint32_t dim) -> uint64_t {
+        if (dim == kNone) return 0ull;
+        return DDSG_CK(dim < (uint32_t)p.d, CK_DIM) ? p.X[(int64_t)dim * p.n + qc] : 0ull;
+    };
+    int4 rc = nproc > 0 ? N.rec[0] : make_int4(0, 0, 0, 0);
+    int4 r2c = nproc > 0 ? N.rec2[0] : make_int4(0, 0, 0, 0);
+    int4 r2n = nproc > 1 ? N.rec2[1] : make_int4(0, 0, 0, 0);
+    uint64_t Xn = coord((uint32_t)r2c.y & 0xffffu), Xs = coord((uint32_t)r2c.y >> 16);
+    int b = 0;
+    uint32_t ph = 0;
+    for (int i = 0; i < nproc; ++i) {
+        int4 rcn = make_int4(0, 0, 0, 0), r2nn = make_int4(0, 0, 0, 0);
+        uint64_t Xnn = 0, Xsn = 0;
+        if (i + 1 < nproc) {
+            rcn = N.rec[i + 1];
+            Xnn = coord((uint32_t)r2n.y & 0xffffu);
+            Xsn = coord((uint32_t)r2n.y >> 16);
+        }
+        if (i + 2 < nproc) r2nn = N.rec2[i + 2];
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[b], ph));
+        if (!ok || pfail) {
+            failed = true;
+            if (lane == 0 && p.err) atomicAdd(p.err, 1ull);
+            break;
+        }
+        const unsigned char *buf = bufbase + (size_t)b * buf_bytes;
+        const int2 *meta = reinterpret_cast<const int2 *>(buf);
+        const unsigned char *srow = buf + meta_bytes + (size_t)m0 * 4;   // this window of row 0
+        const int nslab = rc.y >> 16;
+        const int nmeta = rc.y & 0xffff;
+        const int nrows = rc.w;
+        const float wb = paper ? (float)r2c.z : 1.0f;
+        const uint32_t xs31 = (uint32_t)(Xs >> 31), xn31 = (uint32_t)(Xn >> 31);
+        const int rstride = rs * 4;
+        // warp-uniform: every lane runs the slab loop (it votes); lanes without a
+        // valid, finite query are inactive (weights zero, row 0)
+        if (wact && nslab > 0) {
+            NodProbe pr = nodal_probe(meta, 0, nmeta, nrows, Xs, xs31, Xn, xn31, bad, wb);
+            for (int sl = 0; sl < nslab; ++sl) {
+                NodProbe nx;
+                if (sl + 1 < nslab) nx = nodal_probe(meta, sl + 1, nmeta, nrows, Xs, xs31, Xn, xn31, bad, wb);
+                if (__any_sync(0xffffffffu, pr.act)) {
+                    const unsigned char *R0 = srow + (size_t)pr.r0 * rstride;
+                    const uint64_t w0 = f2_pack(pr.w0, pr.w0), w1 = f2_pack(pr.w1, pr.w1);
+#pragma unroll
+                    for (int s = 0; s < 8; ++s) {
+                        const int off = (s ^ l8) << 4;
+                        const ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(R0 + off);
+                        const ulonglong2 a1 = *reinterpret_cast<const ulonglong2 *>(R0 + rstride + off);
+                        acc[2 * s] = f2_fma(w1, a1.x, f2_fma(w0, a0.x, acc[2 * s]));
+                        acc[2 * s + 1] = f2_fma(w1, a1.y, f2_fma(w0, a0.y, acc[2 * s + 1]));
+                    }
+                }
+                pr = nx;
+            }
+        }
+        if ((i & 1) || i + 1 == nproc) fold();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[b]);
+        // producer: once every warp is done with component i+2-nbuf, stage i+2 in its buffer
+        int pf = 0;
+        if (tid == 0 && i + 2 < nproc) {
+            const int j = i + 2;
+            if (j >= nbuf && !mbar_wait_bounded(&empty[j % nbuf], (uint32_t)(((j - nbuf) / nbuf) & 1))) {
+                pf = 1;
+            } else {
+                fence_proxy_async_smem();
+                issue(j, rec_next);
+                nissued = j + 1;
+                if (j + 1 < nproc) rec_next = N.rec[j + 1];
+            }
+        }
+        pfail = __shfl_sync(0xffffffffu, pf, 0);
+        rc = rcn;
+        r2c = r2n;
+        r2n = r2nn;
+        Xn = Xnn;
+        Xs = Xsn;
+        if (++b == nbuf) {
+            b = 0;
+            ph ^= 1u;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int j = nissued > nbuf ? nissued - nbuf : 0; j < nissued; ++j)
+            if (j < p.issue_end) mbar_wait_bounded(&full[j % nbuf], (uint32_t)((j / nbuf) & 1));
+    }
+    if (!valid || !wact) return;
+    const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int o0 = m0 + ((s ^ l8) << 2);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float s0, s1, c0, c1;
+            f2_unpack(ks[2 * s + h], s0, s1);
+            f2_unpack(kc[2 * s + h], c0, c1);
+            const int o = o0 + 2 * h;
+            if (o < m) p.y[q * m + o] = (bad || failed) ? nanv : (double)s0 - (double)c0;
+            if (o + 1 < m) p.y[q * m + o + 1] = (bad || failed) ? nanv : (double)s1 - (double)c1;
+        }
+    }
+}
+
 bool nodal_eligible(const DevTables &t, int precision, int form) {
     const DevNodal &N = t.nod[form];
     if (!N.ok || !N.vals) return false;
@@ -608,11 +896,25 @@ static cudaError_t launch_nodal(const EvalParams &p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <int GR>
+static cudaError_t launch_nodal_f32x2(const EvalParams &p, cudaStream_t st) {
+    constexpr int QB = NodShape<GR>::QB, NT = NodShape<GR>::NT;
+    const DevNodal &N = p.t.nod[p.form];
+    const int buf = (int)((N.stage_bytes[DDSG_F32C] + 127) & ~127ll);
+    const int nbuf = 128 + 3 * (int64_t)buf <= kSmemLimit ? 3 : 2;
+    const int smem = 128 + nbuf * buf;
+    dim3 grid((unsigned)((p.n + QB - 1) / QB), (unsigned)((N.rs32 + 32 * GR - 1) / (32 * GR)));
+    cudaError_t e = cudaFuncSetAttribute(eval_nodal_f32x2_kernel<GR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    eval_nodal_f32x2_kernel<GR><<<grid, NT, smem, st>>>(p, buf, nbuf);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_eval_nodal(const EvalParams &p, int precision, int mc, cudaStream_t st) {
     const DevNodal &N = p.t.nod[p.form];
     if (precision == DDSG_F32C) {
         if (mc == 32 && N.rs32 % 32 == 0)
-            return N.rs32 > 32 ? launch_nodal<DDSG_F32C, 32, 2>(p, st) : launch_nodal<DDSG_F32C, 32, 1>(p, st);
+            return N.rs32 > 32 ? launch_nodal_f32x2<2>(p, st) : launch_nodal_f32x2<1>(p, st);
         if (mc == 8) return launch_nodal<DDSG_F32C, 8, 1>(p, st);
         return launch_nodal<DDSG_F32C, 16, 1>(p, st);
     }
