@@ -532,6 +532,14 @@ int mlp_load(const char *path, mlp_t **out);
 int mlp_shape(const mlp_t *net, int32_t *nlayers, int32_t *sizes_host);
 /* Kernel timing: kinds 0 forward GEMMs, 1 backward GEMMs, 2 loss/normalization, 3 Adam. */
 int mlp_profile(mlp_t *net, int enable);
+/*
+ * mlp_check -- status of the network's tensor-core GEMMs since the last check
+ * (no paper counterpart). Every mbarrier wait in them is bounded; a wait that
+ * gives up leaves that GEMM's output tile unwritten and is recorded here.
+ * Synchronizes the device; returns DDSG_ERR_TIMEOUT (and clears the record) if
+ * any wait gave up, else DDSG_OK.
+ */
+int mlp_check(mlp_t *net);
 int mlp_profile_read(mlp_t *net, double *ms_host, int64_t *launches_host, int reset);
 
 #ifdef __cplusplus

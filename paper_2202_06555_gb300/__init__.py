@@ -85,6 +85,7 @@ SIGNATURES = {
     "mlp_get_grads": (_int, [_p, _p]),
     "mlp_profile": (_int, [_p, _int]),
     "mlp_profile_read": (_int, [_p, _p, _p, _int]),
+    "mlp_check": (_int, [_p]),
     "irbc_profile_read": (_int, [_p, _p, _p, _int]),
     "irbc_set_node_mode": (_int, [_p, _int]),
     "irbc_set_irreversible": (_int, [_p, _int]),
@@ -593,6 +594,11 @@ class MLP:
 
     def profile(self, enable=True):
         _check(load().mlp_profile(self._h, int(bool(enable))), "mlp_profile")
+
+    def check(self):
+        """Raise DDSGError (DDSG_ERR_TIMEOUT) if a tensor-core GEMM of this network gave
+        up a bounded wait since the last check; synchronizes the device."""
+        _check(load().mlp_check(self._h), "mlp_check")
 
     def profile_read(self, reset=True):
         ms = np.zeros(8)

@@ -1,13 +1,19 @@
 // ddsg_mlp.cu -- warm-start network: a GELU MLP trained and evaluated with
-// hand-written BF16 tensor-core GEMMs (mma.sync m16n8k16, FP32 accumulate).
+// hand-written BF16 tensor-core GEMMs on Blackwell's tcgen05 path (TMA operand
+// tiles, FP32 accumulators in tensor memory, fused epilogues).
 //
 // The network proposes Newton initial guesses for the IRBC step; the paper
 // has no network -- the interpolant and the Newton solve stay the judges.
 //
 // Layout: every width is padded to a multiple of 64 with zeros (weights,
-// biases, activations); batches are padded to a multiple of 64 rows whose
+// biases, activations); batches are padded to a multiple of 128 rows whose
 // inputs and loss gradients are zero. Master weights and Adam moments are
-// FP32; GEMM operands are BF16 copies (W and its transpose).
+// FP32; GEMM operands are BF16 copies (W and its transpose). Every GEMM
+// operand is K-major: training also keeps the transposed BF16 activations and
+// output gradients (written by the producing kernels' epilogues), which are the
+// K-major operands of the weight-gradient GEMMs (K = the batch).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -25,22 +31,29 @@ using namespace ddsg;
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 32, PADK = 8;
+// Tiles of the tcgen05 GEMM: 128 x 64 output tile (one 64-column TMEM
+// accumulator), K in steps of 64 (one 128-byte swizzle atom of BF16), a
+// 4-stage TMA ring. Batches are padded to multiples of 128 rows.
+constexpr int TBM = 128, TBN = 64, TBK = 64, TNS = 4;
 constexpr int GEMM_THREADS = 128;
+constexpr int GEMM_SMEM = 1024 + TNS * (TBM + TBN) * TBK * 2 + 256;
+constexpr uint32_t kGemmWaitLimit = 1u << 20;   // try_wait polls before a wait gives up (about 4 s)
 
 enum { EPI_STORE = 0, EPI_HIDDEN = 1, EPI_LAST = 2, EPI_GELU_BWD = 3 };
 
 struct Epi {
-    float *f;            // FP32 output (STORE, LAST: result; GELU_BWD: dZ)
+    float *f;              // FP32 output (STORE, LAST: result; GELU_BWD: dZ)
     int ldf;
-    float *z;            // HIDDEN: pre-activation (nullable)
+    float *z;              // HIDDEN: pre-activation (nullable)
     int ldz;
-    __nv_bfloat16 *h;    // HIDDEN: GELU(z) as BF16; GELU_BWD: dZ as BF16
+    __nv_bfloat16 *h;      // HIDDEN: GELU(z) as BF16; GELU_BWD: dZ as BF16
     int ldh;
-    const float *bias;   // HIDDEN, LAST
-    const float *zp;     // GELU_BWD: pre-activation of the layer below
+    __nv_bfloat16 *ht;     // HIDDEN / GELU_BWD: the same values transposed (column-major), nullable
+    int ldht;
+    const float *bias;     // HIDDEN, LAST
+    const float *zp;       // GELU_BWD: pre-activation of the layer below
     int ldzp;
-    int64_t zstride;     // STORE with split K: split z writes f + z * zstride
+    int64_t zstride;       // STORE with split K: split z writes f + z * zstride
 };
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -48,133 +61,264 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+__device__ __forceinline__ uint32_t s_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t ph) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(s_addr(b)), "r"(ph) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t ph) {
+    for (uint32_t i = 0; i < kGemmWaitLimit; ++i)
+        if (bar_try(b, ph)) return true;
+    return false;
+}
+// TMA: one 2D box (64 K-elements x rows) of a K-major BF16 operand, 128-byte swizzle
+__device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *m, int k, int row, uint64_t *bar) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(s_addr(dst)), "l"(m), "r"(k), "r"(row), "r"(s_addr(bar)) : "memory");
+}
+// Shared-memory matrix descriptor of a K-major tile written by that TMA: rows of
+// 128 bytes, 8-row groups 1024 bytes apart (stride offset), 128-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc(const void *p) {
+    return (uint64_t)((s_addr(p) >> 4) & 0x3FFF) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
 }
 
-// C[M x N] = op(A)[M x K] * op(B)[N x K]^T. TA: A is stored K x M (element
-// (m, k) at A[k*lda + m]); otherwise M x K. TB likewise for B (N x K or K x N).
-// M, N multiples of 64 and K a multiple of 32 (the callers pad). Split K: block
-// z of the grid's third dimension covers k in [z*kchunk, min(K, (z+1)*kchunk))
-// and (STORE only) writes its partial product at f + z * zstride.
-template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A,
-                                                                 int lda, const __nv_bfloat16 *__restrict__ B, int ldb,
-                                                                 Epi e, int kchunk) {
-    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PADK];
-    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PADK];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int wm = warp >> 1, wn = warp & 1;  // 2 x 2 warps, 32 x 32 each
-    const int bm = blockIdx.y * BM, bn = blockIdx.x * BN;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-
+// C[M x N] = A[M x K] * B[N x K]^T, A and B BF16 K-major (TMA maps ta, tb),
+// FP32 accumulate in TMEM, one 128 x 64 tile per block. Thread 0 feeds the
+// shared-memory ring by TMA, thread 32 issues tcgen05.mma (M = 128, N = 64,
+// K = 16 per instruction) and commits each stage back to the producer; the
+// four warps then read the accumulator (lane = row) and apply the epilogue.
+// Split K: block z covers k in [z*kchunk, min(K, (z+1)*kchunk)) (kchunk a
+// multiple of 64) and (STORE only) writes its partial at f + z * zstride. Every
+// wait is bounded; a wait that gives up sets *err, the block skips its output,
+// waits (bounded) for its copies and MMAs, and frees its TMEM.
+template <int EPI>
+__global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap ta,
+                                                                  const __grid_constant__ CUtensorMap tb, int M, int N,
+                                                                  int K, int kchunk, Epi e, unsigned *err) {
+    extern __shared__ uint8_t gsm_raw[];
+    uint8_t *gsm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *As = gsm;
+    uint8_t *Bs = gsm + TNS * TBM * TBK * 2;
+    uint64_t *full = reinterpret_cast<uint64_t *>(Bs + TNS * TBN * TBK * 2);
+    uint64_t *empty = full + TNS;
+    uint64_t *done = empty + TNS;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
     const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-    for (int k0 = kb; k0 < ke; k0 += BK) {
-        for (int idx = tid; idx < BM * BK; idx += GEMM_THREADS) {
-            int r, c;
-            if (TA) { r = idx % BM; c = idx / BM; } else { r = idx / BK; c = idx % BK; }
-            const int m = bm + r, k = k0 + c;
-            __nv_bfloat16 v = __float2bfloat16(0.f);
-            if (m < M && k < ke) v = TA ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k];
-            As[r][c] = v;
+    const int nk = ke > kb ? (ke - kb) / TBK : 0;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TNS; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(&empty[s])) : "memory");
         }
-        for (int idx = tid; idx < BN * BK; idx += GEMM_THREADS) {
-            int r, c;
-            if (TB) { r = idx % BN; c = idx / BN; } else { r = idx / BK; c = idx % BK; }
-            const int n = bn + r, k = k0 + c;
-            __nv_bfloat16 v = __float2bfloat16(0.f);
-            if (n < N && k < ke) v = TB ? B[(int64_t)k * ldb + n] : B[(int64_t)n * ldb + k];
-            Bs[r][c] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[2][4], bf[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r0 = wm * 32 + i * 16 + g;
-                af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r0][kk + 2 * t]);
-                af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r0 + 8][kk + 2 * t]);
-                af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r0][kk + 8 + 2 * t]);
-                af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r0 + 8][kk + 8 + 2 * t]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int n0 = wn * 32 + j * 8 + g;
-                bf[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[n0][kk + 2 * t]);
-                bf[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[n0][kk + 8 + 2 * t]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    mma_bf16(acc[i][j], af[i][0], af[i][1], af[i][2], af[i][3], bf[j][0], bf[j][1]);
-        }
-        __syncthreads();
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // epilogue: acc[i][j][r] -> (row, col)
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(tslot)), "r"(TBN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    int issued = 0;
+    if (threadIdx.x == 0) {
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % TNS;
+            if (kt >= TNS && !bar_wait(&empty[s], ((kt / TNS) - 1) & 1)) {
+                atomicOr(err, 1u);
+                break;
+            }
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_addr(&full[s])),
+                         "r"((TBM + TBN) * TBK * 2) : "memory");
+            tma_box(As + s * TBM * TBK * 2, &ta, kb + kt * TBK, m0, &full[s]);
+            tma_box(Bs + s * TBN * TBK * 2, &tb, kb + kt * TBK, n0, &full[s]);
+            issued = kt + 1;
+        }
+    } else if (threadIdx.x == 32) {
+        // instruction descriptor: F32 accumulate, BF16 A and B, both K-major, N = 64, M = 128
+        constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
+                                   ((uint32_t)(TBM >> 4) << 24);
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % TNS;
+            if (!bar_wait(&full[s], (kt / TNS) & 1)) {
+                atomicOr(err, 2u);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t ad = smem_desc(As + s * TBM * TBK * 2), bd = smem_desc(Bs + s * TBN * TBK * 2);
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < TBK / 16; ++j) {
+                const uint32_t acc = (kt > 0 || j > 0) ? 1u : 0u;
+                // the K step of 16 BF16 (32 bytes) advances the descriptors' start address by 2 (16-byte units)
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(tmem), "l"(ad + 2 * j), "l"(bd + 2 * j), "r"(idesc), "r"(acc) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(s_addr(&empty[s])) : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_addr(done))
+                     : "memory");
+    }
+    __syncwarp();
+    const bool fin = __all_sync(0xffffffffu, bar_wait(done, 0));
+    if (!fin && lane == 0) atomicOr(err, 4u);
+    const bool got = fin && nk > 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < TBN; c0 += 16) {
+        uint32_t r[16];
+        const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                       "=r"(r[15])
+                     : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!got || row >= M) continue;
+        const int col0 = n0 + c0;             // 16 consecutive columns of this row (N is a multiple of 16)
+        if (col0 >= N) continue;
+        float v[16];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+        if (EPI == EPI_STORE) {
+            float4 *dst = reinterpret_cast<float4 *>(e.f + (int64_t)blockIdx.z * e.zstride + (int64_t)row * e.ldf + col0);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int row = bm + wm * 32 + i * 16 + g + (r >= 2 ? 8 : 0);
-                const int col = bn + wn * 32 + j * 8 + 2 * t + (r & 1);
-                if (row >= M || col >= N) continue;
-                const float v = acc[i][j][r];
-                if (EPI == EPI_STORE) {
-                    e.f[(int64_t)blockIdx.z * e.zstride + (int64_t)row * e.ldf + col] = v;
-                } else if (EPI == EPI_HIDDEN) {
-                    const float z = v + e.bias[col];
-                    if (e.z) e.z[(int64_t)row * e.ldz + col] = z;
-                    e.h[(int64_t)row * e.ldh + col] = __float2bfloat16(gelu_f(z));
-                } else if (EPI == EPI_LAST) {
-                    e.f[(int64_t)row * e.ldf + col] = v + e.bias[col];
-                } else {
-                    const float dz = v * gelu_grad_f(e.zp[(int64_t)row * e.ldzp + col]);
-                    e.f[(int64_t)row * e.ldf + col] = dz;
-                    e.h[(int64_t)row * e.ldh + col] = __float2bfloat16(dz);
+            for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        } else if (EPI == EPI_LAST) {
+            const float4 *bs = reinterpret_cast<const float4 *>(e.bias + col0);
+            float4 *dst = reinterpret_cast<float4 *>(e.f + (int64_t)row * e.ldf + col0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 b4 = bs[i];
+                dst[i] = make_float4(v[4 * i] + b4.x, v[4 * i + 1] + b4.y, v[4 * i + 2] + b4.z, v[4 * i + 3] + b4.w);
+            }
+        } else {
+            // HIDDEN: z = v + bias, out = GELU(z); GELU_BWD: out = dz = v * GELU'(z of the layer below)
+            float out[16];
+            if (EPI == EPI_HIDDEN) {
+                const float4 *bs = reinterpret_cast<const float4 *>(e.bias + col0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 b4 = bs[i];
+                    v[4 * i] += b4.x;
+                    v[4 * i + 1] += b4.y;
+                    v[4 * i + 2] += b4.z;
+                    v[4 * i + 3] += b4.w;
+                }
+                if (e.z) {
+                    float4 *zd = reinterpret_cast<float4 *>(e.z + (int64_t)row * e.ldz + col0);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) zd[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) out[i] = gelu_f(v[i]);
+            } else {
+                const float4 *zp = reinterpret_cast<const float4 *>(e.zp + (int64_t)row * e.ldzp + col0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 z4 = zp[i];
+                    out[4 * i] = v[4 * i] * gelu_grad_f(z4.x);
+                    out[4 * i + 1] = v[4 * i + 1] * gelu_grad_f(z4.y);
+                    out[4 * i + 2] = v[4 * i + 2] * gelu_grad_f(z4.z);
+                    out[4 * i + 3] = v[4 * i + 3] * gelu_grad_f(z4.w);
+                }
+                float4 *fd = reinterpret_cast<float4 *>(e.f + (int64_t)row * e.ldf + col0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) fd[i] = make_float4(out[4 * i], out[4 * i + 1], out[4 * i + 2], out[4 * i + 3]);
+            }
+            __align__(16) __nv_bfloat162 hb[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) hb[i] = __floats2bfloat162_rn(out[2 * i], out[2 * i + 1]);
+            uint4 *hd = reinterpret_cast<uint4 *>(e.h + (int64_t)row * e.ldh + col0);
+            hd[0] = *reinterpret_cast<const uint4 *>(&hb[0]);
+            hd[1] = *reinterpret_cast<const uint4 *>(&hb[4]);
+            if (e.ht) {
+                // transposed copy: for each column the warp writes 32 consecutive rows
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    e.ht[(int64_t)(col0 + 2 * i) * e.ldht + row] = hb[i].x;
+                    e.ht[(int64_t)(col0 + 2 * i + 1) * e.ldht + row] = hb[i].y;
                 }
             }
+        }
+    }
+    if (threadIdx.x == 0) {
+        // a producer that gave up may have copies in flight: let the issued stages land
+        for (int kt = issued > TNS ? issued - TNS : 0; kt < issued; ++kt) bar_wait(&full[kt % TNS], (kt / TNS) & 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TBN) : "memory");
 }
 
-template <bool TA, bool TB, int EPI>
-cudaError_t gemm(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
-                 const Epi &e, cudaStream_t st, int splits = 1, int kchunk = 0) {
-    dim3 grid((unsigned)(N / BN), (unsigned)(M / BM), (unsigned)splits);
-    gemm_bf16_kernel<TA, TB, EPI><<<grid, GEMM_THREADS, 0, st>>>(M, N, K, A, lda, B, ldb, e, splits > 1 ? kchunk : K);
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// TMA map of a K-major BF16 matrix (rows x K, row stride ld elements) with boxes
+// of 64 K-elements x box_rows rows; rows past the end read as zero.
+bool k_major_map(CUtensorMap *m, const __nv_bfloat16 *base, int64_t rows, int K, int ld, int box_rows) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// C = A * B^T on the tensor cores: A (M x K, row stride lda) and B (N x K, row
+// stride ldb), both K-major BF16; K a multiple of 64, N a multiple of 64.
+template <int EPI>
+cudaError_t gemm(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, const Epi &e,
+                 unsigned *err, cudaStream_t st, int splits = 1, int kchunk = 0) {
+    CUtensorMap ta, tb;
+    if (!k_major_map(&ta, A, M, K, lda, TBM) || !k_major_map(&tb, B, N, K, ldb, TBN)) return cudaErrorInvalidValue;
+    cudaError_t a = cudaFuncSetAttribute(gemm_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+    if (a != cudaSuccess) return a;
+    dim3 grid((unsigned)((N + TBN - 1) / TBN), (unsigned)((M + TBM - 1) / TBM), (unsigned)splits);
+    gemm_tc_kernel<EPI><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(ta, tb, M, N, K, splits > 1 ? kchunk : K, e, err);
     return cudaGetLastError();
 }
 
 // Split of the batch dimension (K of the weight-gradient GEMM) so that the
-// (Po/64) x (Pi/64) output tiles times the splits fill the SMs about twice;
-// chunks are multiples of BK.
-void grad_split(int64_t Bp, int Po, int Pi, int &splits, int &kchunk) {
-    const int tiles = (Po / BM) * (Pi / BN);
-    const int want = std::max(1, (2 * 152 + tiles - 1) / tiles);
-    const int64_t kmax = std::max<int64_t>(1, Bp / BK);
+// output tiles times the splits fill the SMs about twice; chunks are multiples of TBK.
+void grad_split(int64_t Bp, int Po, int Pi, int sms, int &splits, int &kchunk) {
+    const int tiles = ((Po + TBM - 1) / TBM) * ((Pi + TBN - 1) / TBN);
+    const int want = std::max(1, (2 * sms + tiles - 1) / tiles);
+    const int64_t kmax = std::max<int64_t>(1, Bp / TBK);
     const int s = (int)std::min<int64_t>(want, kmax);
-    kchunk = (int)(((Bp + s - 1) / s + BK - 1) / BK * BK);
+    kchunk = (int)(((Bp + s - 1) / s + TBK - 1) / TBK * TBK);
     splits = (int)((Bp + kchunk - 1) / kchunk);
 }
 
 // x (B x n0, FP64 physical) -> (x - shift) * scale as BF16 in B_pad x P0 (zero padding)
+// (XT, nullable: the same transposed, P0 x B_pad)
 __global__ void mlp_input_kernel(int64_t B, int64_t Bp, int n0, int P0, const double *__restrict__ x,
                                  const double *__restrict__ shift, const double *__restrict__ scale,
-                                 __nv_bfloat16 *__restrict__ X) {
+                                 __nv_bfloat16 *__restrict__ X, __nv_bfloat16 *__restrict__ XT) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= Bp * P0) return;
     const int64_t b = e / P0;
@@ -182,13 +326,15 @@ __global__ void mlp_input_kernel(int64_t B, int64_t Bp, int n0, int P0, const do
     float v = 0.f;
     if (b < B && c < n0) v = (float)((x[b * n0 + c] - shift[c]) * scale[c]);
     X[e] = __float2bfloat16(v);
+    if (XT) XT[(int64_t)c * Bp + b] = __float2bfloat16(v);
 }
 
 // dY = 2 (Y - T) / (B m) on the normalized targets; loss += sum (Y - T)^2 / (B m)
 __global__ void mlp_loss_kernel(int64_t B, int64_t Bp, int m, int PL, const float *__restrict__ Y,
                                 const double *__restrict__ y, const double *__restrict__ shift,
                                 const double *__restrict__ scale, float *__restrict__ dY,
-                                __nv_bfloat16 *__restrict__ dYb, double *__restrict__ loss) {
+                                __nv_bfloat16 *__restrict__ dYb, __nv_bfloat16 *__restrict__ dYbT,
+                                double *__restrict__ loss) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double l = 0.0;
     if (e < Bp * PL) {
@@ -203,6 +349,7 @@ __global__ void mlp_loss_kernel(int64_t B, int64_t Bp, int m, int PL, const floa
         }
         dY[e] = g;
         dYb[e] = __float2bfloat16(g);
+        dYbT[(int64_t)c * Bp + b] = __float2bfloat16(g);
     }
     for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
     if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l);
@@ -230,33 +377,55 @@ __global__ void colsum_part_kernel(int64_t Bp, int P, int kchunk, const float *_
     }
 }
 
-// out[i] = sum over z of part[z*n + i], in z order (deterministic)
-__global__ void splitk_reduce_kernel(int splits, int64_t n, const float *__restrict__ part, float *__restrict__ out) {
+// Split-K sums of one layer in one launch, in z order (deterministic):
+// gW[i] = sum_z pw[z*nw + i] for i < nw, then gb[j] = sum_z pb[z*nb + j].
+__global__ void splitk_reduce_kernel(int splits, int64_t nw, int64_t nb, const float *__restrict__ pw,
+                                     const float *__restrict__ pb, float *__restrict__ gW, float *__restrict__ gb) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= nw + nb) return;
+    const bool w = i < nw;
+    const int64_t n = w ? nw : nb, j = w ? i : i - nw;
+    const float *part = w ? pw : pb;
     float s = 0.f;
-    for (int z = 0; z < splits; ++z) s += part[(int64_t)z * n + i];
-    out[i] = s;
+    for (int z = 0; z < splits; ++z) s += part[(int64_t)z * n + j];
+    (w ? gW : gb)[j] = s;
 }
 
-// Adam on one parameter tensor (FP32 master), refreshing its BF16 copy and,
-// for weights, the transposed BF16 copy (rows x cols -> cols x rows).
-__global__ void adam_kernel(int64_t n, int rows, int cols, float *__restrict__ p, const float *__restrict__ g,
-                            float *__restrict__ mo, float *__restrict__ ve, float lr, float b1, float b2, float eps,
-                            float c1, float c2, __nv_bfloat16 *__restrict__ pb, __nv_bfloat16 *__restrict__ pbt) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const float gr = g[e];
-    const float m1 = b1 * mo[e] + (1.f - b1) * gr;
-    const float v1 = b2 * ve[e] + (1.f - b2) * gr * gr;
-    mo[e] = m1;
-    ve[e] = v1;
-    const float np = p[e] - lr * (m1 / c1) / (sqrtf(v1 / c2) + eps);
-    p[e] = np;
-    if (pb) pb[e] = __float2bfloat16(np);
-    if (pbt) {
-        const int r = (int)(e / cols), c = (int)(e - (int64_t)r * cols);
-        pbt[(int64_t)c * rows + r] = __float2bfloat16(np);
+// Parameter tensors of one Adam launch (weights and biases of every layer).
+constexpr int kAdamMax = 32;
+struct AdamTensor {
+    int64_t n, begin;        // elements; first global element of this tensor
+    int rows, cols;          // weights: rows x cols (for the transposed BF16 copy)
+    float *p, *g, *mo, *ve;
+    __nv_bfloat16 *pb, *pbt; // BF16 copy and transposed copy (nullable)
+};
+struct AdamTable {
+    int count;
+    int64_t total;
+    AdamTensor t[kAdamMax];
+};
+
+// Adam over every parameter tensor in one launch (FP32 masters), refreshing the
+// BF16 copies and, for weights, the transposed BF16 copies.
+__global__ void adam_all_kernel(const AdamTable tab, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (int64_t ge = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ge < tab.total;
+         ge += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (k + 1 < tab.count && ge >= tab.t[k + 1].begin) ++k;
+        const AdamTensor &T = tab.t[k];
+        const int64_t e = ge - T.begin;
+        const float gr = T.g[e];
+        const float m1 = b1 * T.mo[e] + (1.f - b1) * gr;
+        const float v1 = b2 * T.ve[e] + (1.f - b2) * gr * gr;
+        T.mo[e] = m1;
+        T.ve[e] = v1;
+        const float np = T.p[e] - lr * (m1 / c1) / (sqrtf(v1 / c2) + eps);
+        T.p[e] = np;
+        if (T.pb) T.pb[e] = __float2bfloat16(np);
+        if (T.pbt) {
+            const int r = (int)(e / T.cols), c = (int)(e - (int64_t)r * T.cols);
+            T.pbt[(int64_t)c * T.rows + r] = __float2bfloat16(np);
+        }
     }
 }
 
@@ -284,7 +453,7 @@ __global__ void mlp_output_kernel(int64_t B, int m, int PL, const float *__restr
 }
 
 inline int pad64(int n) { return (n + 63) & ~63; }
-inline int64_t pad64l(int64_t n) { return (n + 63) & ~63ll; }
+inline int64_t pad_rows(int64_t n) { return (n + TBM - 1) & ~(int64_t)(TBM - 1); }   // batch rows: GEMM tile height
 inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 }  // namespace
@@ -305,6 +474,8 @@ struct mlp {
     int64_t cap = 0;
     void *ws = nullptr;
     double *loss = nullptr;
+    unsigned *err = nullptr;      // device word: GEMM waits that gave up (bits by site)
+    int sms = 1;                  // SM count of the bound device (split-K sizing)
     Tracer tr;                    // kinds: 0 gemm forward, 1 gemm backward, 2 loss/aux, 3 adam
 };
 
@@ -321,8 +492,10 @@ void release_params(mlp *M) {
     M->vW.clear(); M->mb.clear(); M->vb.clear(); M->Wb.clear(); M->WbT.clear();
     cudaFree(M->in_shift); cudaFree(M->in_scale); cudaFree(M->out_shift); cudaFree(M->out_scale);
     cudaFree(M->loss);
+    cudaFree(M->err);
     M->in_shift = M->in_scale = M->out_shift = M->out_scale = nullptr;
     M->loss = nullptr;
+    M->err = nullptr;
 }
 
 int mlp_bind(mlp *M) {
@@ -365,8 +538,13 @@ int mlp_bind(mlp *M) {
     const int n0 = M->n[0], nL = M->n[L];
     if (!alloc((void **)&M->in_shift, n0 * 8) || !alloc((void **)&M->in_scale, n0 * 8) ||
         !alloc((void **)&M->out_shift, nL * 8) || !alloc((void **)&M->out_scale, nL * 8) ||
-        !alloc((void **)&M->loss, 8))
+        !alloc((void **)&M->loss, 8) || !alloc((void **)&M->err, 8))
         return set_error(DDSG_ERR_OOM, "mlp: allocation failed");
+    if (cudaDeviceGetAttribute(&M->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || M->sms < 1) {
+        cudaGetLastError();
+        M->sms = 1;
+    }
+    if (!tensor_map_encoder()) return set_error(DDSG_ERR_CUDA, "mlp: the driver offers no cuTensorMapEncodeTiled");
     const double *nrm = M->norm.data();
     if (cudaMemcpy(M->in_shift, nrm, n0 * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(M->in_scale, nrm + n0, n0 * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -380,12 +558,14 @@ int mlp_bind(mlp *M) {
 
 // Batch workspace for Bp rows: X_0..X_{L-1} (BF16), Z_0..Z_{L-2} (FP32),
 // Y (FP32), dZ ping-pong (FP32 + BF16).
+// Training also keeps XT_l (P_l x Bp, the layer inputs transposed) and dZbT
+// ping-pong (Pmax x Bp), the K-major operands of the weight-gradient GEMMs.
 struct WsView {
-    std::vector<__nv_bfloat16 *> X;
+    std::vector<__nv_bfloat16 *> X, XT;
     std::vector<float *> Z;
     float *Y;
     float *dZ[2];
-    __nv_bfloat16 *dZb[2];
+    __nv_bfloat16 *dZb[2], *dZbT[2];
     float *split;   // split-K partials of one layer's weight and bias gradients
 };
 
@@ -395,14 +575,14 @@ int mlp_ws(mlp *M, int64_t Bp, WsView &v) {
     for (int p : M->P) Pmax = std::max(Pmax, p);
     auto rnd = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t need = 0;
-    for (int l = 0; l < L; ++l) need += rnd((size_t)Bp * M->P[l] * 2);
+    for (int l = 0; l < L; ++l) need += 2 * rnd((size_t)Bp * M->P[l] * 2);
     for (int l = 0; l + 1 < L; ++l) need += rnd((size_t)Bp * M->P[l + 1] * 4);
     need += rnd((size_t)Bp * M->P[L] * 4);
-    need += 2 * rnd((size_t)Bp * Pmax * 4) + 2 * rnd((size_t)Bp * Pmax * 2);
+    need += 2 * rnd((size_t)Bp * Pmax * 4) + 4 * rnd((size_t)Bp * Pmax * 2);
     size_t split_floats = 0;
     for (int l = 0; l < L; ++l) {
         int s = 1, kc = 0;
-        grad_split(Bp, M->P[l + 1], M->P[l], s, kc);
+        grad_split(Bp, M->P[l + 1], M->P[l], M->sms, s, kc);
         split_floats = std::max(split_floats, (size_t)s * ((size_t)M->P[l + 1] * M->P[l] + M->P[l + 1]));
     }
     need += rnd(split_floats * 4);
@@ -419,12 +599,15 @@ int mlp_ws(mlp *M, int64_t Bp, WsView &v) {
     unsigned char *p = static_cast<unsigned char *>(M->ws);
     auto take = [&](size_t b) { unsigned char *q = p; p += rnd(b); return q; };
     v.X.resize(L);
+    v.XT.resize(L);
     v.Z.resize(L);
     for (int l = 0; l < L; ++l) v.X[l] = (__nv_bfloat16 *)take((size_t)Bp * M->P[l] * 2);
+    for (int l = 0; l < L; ++l) v.XT[l] = (__nv_bfloat16 *)take((size_t)Bp * M->P[l] * 2);
     for (int l = 0; l + 1 < L; ++l) v.Z[l] = (float *)take((size_t)Bp * M->P[l + 1] * 4);
     v.Y = (float *)take((size_t)Bp * M->P[L] * 4);
     for (int i = 0; i < 2; ++i) v.dZ[i] = (float *)take((size_t)Bp * Pmax * 4);
     for (int i = 0; i < 2; ++i) v.dZb[i] = (__nv_bfloat16 *)take((size_t)Bp * Pmax * 2);
+    for (int i = 0; i < 2; ++i) v.dZbT[i] = (__nv_bfloat16 *)take((size_t)Bp * Pmax * 2);
     v.split = (float *)take(split_floats * 4);
     return DDSG_OK;
 }
@@ -435,7 +618,7 @@ cudaError_t mlp_forward(mlp *M, int64_t B, int64_t Bp, const double *x, WsView &
     {
         Tracer::Scope ts(&M->tr, 2, st);
         mlp_input_kernel<<<nblk(Bp * M->P[0]), 256, 0, st>>>(B, Bp, M->n[0], M->P[0], x, M->in_shift, M->in_scale,
-                                                             v.X[0]);
+                                                             v.X[0], keepZ ? v.XT[0] : nullptr);
     }
     cudaError_t e = cudaGetLastError();
     Tracer::Scope ts(&M->tr, 0, st);
@@ -447,11 +630,13 @@ cudaError_t mlp_forward(mlp *M, int64_t B, int64_t Bp, const double *x, WsView &
             ep.ldz = M->P[l + 1];
             ep.h = v.X[l + 1];
             ep.ldh = M->P[l + 1];
-            e = gemm<false, false, EPI_HIDDEN>((int)Bp, M->P[l + 1], M->P[l], v.X[l], M->P[l], M->Wb[l], M->P[l], ep, st);
+            ep.ht = keepZ ? v.XT[l + 1] : nullptr;
+            ep.ldht = (int)Bp;
+            e = gemm<EPI_HIDDEN>((int)Bp, M->P[l + 1], M->P[l], v.X[l], M->P[l], M->Wb[l], M->P[l], ep, M->err, st);
         } else {
             ep.f = v.Y;
             ep.ldf = M->P[L];
-            e = gemm<false, false, EPI_LAST>((int)Bp, M->P[L], M->P[l], v.X[l], M->P[l], M->Wb[l], M->P[l], ep, st);
+            e = gemm<EPI_LAST>((int)Bp, M->P[L], M->P[l], v.X[l], M->P[l], M->Wb[l], M->P[l], ep, M->err, st);
         }
     }
     return e;
@@ -461,7 +646,7 @@ cudaError_t mlp_forward(mlp *M, int64_t B, int64_t Bp, const double *x, WsView &
 
 extern "C" int mlp_create(int nlayers, const int32_t *sizes, const float *params_host, uint64_t seed,
                           mlp_t **out) {
-    if (!sizes || !out || nlayers < 1 || nlayers > 16) return set_error(DDSG_ERR_ARG, "mlp_create: bad argument");
+    if (!sizes || !out || nlayers < 1 || nlayers > kAdamMax / 2) return set_error(DDSG_ERR_ARG, "mlp_create: bad argument");
     mlp *M = new (std::nothrow) mlp();
     if (!M) return set_error(DDSG_ERR_OOM, "mlp_create: host allocation failed");
     M->L = nlayers;
@@ -525,11 +710,11 @@ extern "C" int mlp_infer(mlp_t *M, int64_t B, const double *x_dev, double *y_dev
     const int64_t chunk = 65536;
     {
         WsView v0;   // size the workspace once for the largest chunk (no reallocation between chunks)
-        if ((rc = mlp_ws(M, pad64l(std::min(chunk, B)), v0))) return rc;
+        if ((rc = mlp_ws(M, pad_rows(std::min(chunk, B)), v0))) return rc;
     }
     for (int64_t b0 = 0; b0 < B; b0 += chunk) {
         const int64_t nb = std::min(chunk, B - b0);
-        const int64_t Bp = pad64l(nb);
+        const int64_t Bp = pad_rows(nb);
         WsView v;
         if ((rc = mlp_ws(M, Bp, v))) return rc;
         cudaError_t e = mlp_forward(M, nb, Bp, x_dev + b0 * M->n[0], v, false, st);
@@ -553,7 +738,7 @@ extern "C" int mlp_train_step(mlp_t *M, int64_t B, const double *x_dev, const do
     int rc = mlp_bind(M);
     if (rc) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int64_t Bp = pad64l(B);
+    const int64_t Bp = pad_rows(B);
     WsView v;
     if ((rc = mlp_ws(M, Bp, v))) return rc;
     const int L = M->L;
@@ -562,7 +747,7 @@ extern "C" int mlp_train_step(mlp_t *M, int64_t B, const double *x_dev, const do
     if (e == cudaSuccess) {
         Tracer::Scope ts(&M->tr, 2, st);
         mlp_loss_kernel<<<nblk(Bp * M->P[L]), 256, 0, st>>>(B, Bp, M->n[L], M->P[L], v.Y, y_dev, M->out_shift,
-                                                            M->out_scale, v.dZ[0], v.dZb[0], M->loss);
+                                                            M->out_scale, v.dZ[0], v.dZb[0], v.dZbT[0], M->loss);
         e = cudaGetLastError();
     }
     // backward: layer l has input width P[l], output width P[l+1]; dZ[cur] holds dL/dZ_l
@@ -570,22 +755,21 @@ extern "C" int mlp_train_step(mlp_t *M, int64_t B, const double *x_dev, const do
     for (int l = L - 1; l >= 0 && e == cudaSuccess; --l) {
         Tracer::Scope ts(&M->tr, 1, st);
         const int Pi = M->P[l], Po = M->P[l + 1];
-        // gW = dZ^T (Po x Bp) * X_l (Bp x Pi): both operands stored transposed; the
-        // batch (K) is split over blocks, partials summed in split order
+        // gW = dZ^T (Po x Bp) * X_l (Bp x Pi) = dZbT * XT_l^T, both K-major (K = the
+        // batch); the batch is split over blocks, partials summed in split order
         int splits = 1, kchunk = 0;
-        grad_split(Bp, Po, Pi, splits, kchunk);
+        grad_split(Bp, Po, Pi, M->sms, splits, kchunk);
         const int64_t nw = (int64_t)Po * Pi;
         float *pw = v.split, *pb = v.split + (int64_t)splits * nw;
         Epi g = {};
         g.f = pw;
         g.ldf = Pi;
         g.zstride = nw;
-        e = gemm<true, true, EPI_STORE>(Po, Pi, (int)Bp, v.dZb[cur], Po, v.X[l], Pi, g, st, splits, kchunk);
+        e = gemm<EPI_STORE>(Po, Pi, (int)Bp, v.dZbT[cur], (int)Bp, v.XT[l], (int)Bp, g, M->err, st, splits, kchunk);
         if (e == cudaSuccess) {
             colsum_part_kernel<<<dim3((unsigned)((Po + 31) / 32), (unsigned)splits), 256, 0, st>>>(Bp, Po, kchunk,
                                                                                                 v.dZ[cur], pb);
-            splitk_reduce_kernel<<<nblk(nw), 256, 0, st>>>(splits, nw, pw, M->gW[l]);
-            splitk_reduce_kernel<<<nblk(Po), 256, 0, st>>>(splits, Po, pb, M->gb[l]);
+            splitk_reduce_kernel<<<nblk(nw + Po), 256, 0, st>>>(splits, nw, Po, pw, pb, M->gW[l], M->gb[l]);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess && l > 0) {
@@ -594,10 +778,12 @@ extern "C" int mlp_train_step(mlp_t *M, int64_t B, const double *x_dev, const do
             d.ldf = Pi;
             d.h = v.dZb[cur ^ 1];
             d.ldh = Pi;
+            d.ht = v.dZbT[cur ^ 1];
+            d.ldht = (int)Bp;
             d.zp = v.Z[l - 1];
             d.ldzp = Pi;
             // dA = dZ (Bp x Po) * W (Po x Pi) = dZ * (W^T)^T with W^T stored Pi x Po
-            e = gemm<false, false, EPI_GELU_BWD>((int)Bp, Pi, Po, v.dZb[cur], Po, M->WbT[l], Po, d, st);
+            e = gemm<EPI_GELU_BWD>((int)Bp, Pi, Po, v.dZb[cur], Po, M->WbT[l], Po, d, M->err, st);
             cur ^= 1;
         }
     }
@@ -605,14 +791,21 @@ extern "C" int mlp_train_step(mlp_t *M, int64_t B, const double *x_dev, const do
     M->step += 1;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = (float)(1.0 - pow(0.9, (double)M->step)), c2 = (float)(1.0 - pow(0.999, (double)M->step));
-    for (int l = 0; l < L && e == cudaSuccess; ++l) {
+    if (e == cudaSuccess) {
         Tracer::Scope ts(&M->tr, 3, st);
-        const int Pi = M->P[l], Po = M->P[l + 1];
-        const int64_t nw = (int64_t)Pi * Po;
-        adam_kernel<<<nblk(nw), 256, 0, st>>>(nw, Po, Pi, M->W[l], M->gW[l], M->mW[l], M->vW[l], lr, b1, b2, eps, c1, c2,
-                                             M->Wb[l], M->WbT[l]);
-        adam_kernel<<<nblk(Po), 256, 0, st>>>(Po, 1, Po, M->b[l], M->gb[l], M->mb[l], M->vb[l], lr, b1, b2, eps, c1, c2,
-                                             nullptr, nullptr);
+        AdamTable tab = {};
+        int64_t off = 0;
+        for (int l = 0; l < L; ++l) {
+            const int Pi = M->P[l], Po = M->P[l + 1];
+            tab.t[tab.count++] = {(int64_t)Pi * Po, off, Po, Pi, M->W[l], M->gW[l], M->mW[l], M->vW[l], M->Wb[l], M->WbT[l]};
+            off += (int64_t)Pi * Po;
+            tab.t[tab.count++] = {(int64_t)Po, off, 1, Po, M->b[l], M->gb[l], M->mb[l], M->vb[l], nullptr, nullptr};
+            off += Po;
+        }
+        tab.total = off;
+        int64_t blocks = nblk(off);
+        if (blocks > (int64_t)M->sms * 8) blocks = (int64_t)M->sms * 8;
+        adam_all_kernel<<<(unsigned)blocks, 256, 0, st>>>(tab, lr, b1, b2, eps, c1, c2);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && loss_dev) e = cudaMemcpyAsync(loss_dev, M->loss, 8, cudaMemcpyDeviceToDevice, st);
@@ -747,6 +940,21 @@ extern "C" int64_t mlp_num_params(const mlp_t *M) {
     int64_t np = 0;
     for (int l = 0; l < M->L; ++l) np += (int64_t)M->n[l] * M->n[l + 1] + M->n[l + 1];
     return np;
+}
+
+extern "C" int mlp_check(mlp_t *M) {
+    if (!M) return set_error(DDSG_ERR_ARG, "mlp_check: NULL network");
+    if (M->device < 0 || !M->err) return DDSG_OK;   // nothing ran yet
+    unsigned w = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&w, M->err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(DDSG_ERR_CUDA, "mlp_check: reading the status word failed");
+    }
+    if (w) {
+        cudaMemset(M->err, 0, 4);
+        return set_error(DDSG_ERR_TIMEOUT, "mlp_check: a tensor-core GEMM gave up a bounded wait (its output is incomplete)");
+    }
+    return DDSG_OK;
 }
 
 extern "C" int mlp_profile(mlp_t *M, int enable) {

@@ -83,6 +83,26 @@ def test_gradients_match_reference(G):
     for l in range(len(gW)):
         assert np.linalg.norm(GW[l] - gW[l]) / np.linalg.norm(gW[l]) <= 3e-2, l
         assert np.linalg.norm(Gb[l] - gb[l]) / max(np.linalg.norm(gb[l]), 1e-30) <= 3e-2, l
+    net.check()   # no tensor-core GEMM gave up a wait
+
+
+@pytest.mark.parametrize("batch", [1, 127, 128, 129, 4096 + 65])
+def test_ragged_batches_match_reference(G, batch):
+    """Batches padded to the 128-row GEMM tile: ragged and tiny sizes (one row, one
+    short of and one past a tile) through forward and backward."""
+    ref, net = _pair(G)
+    x, y = _data(batch, 45)
+    _, gW, gb = ref.loss_and_grads(x, y)
+    net.train_step(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), 0.0)
+    GW, Gb = net.grads()
+    for l in range(len(gW)):
+        assert np.linalg.norm(GW[l] - gW[l]) / np.linalg.norm(gW[l]) <= 3e-2, (batch, l)
+        assert np.linalg.norm(Gb[l] - gb[l]) / max(np.linalg.norm(gb[l]), 1e-30) <= 3e-2, (batch, l)
+    yd = torch.zeros((batch, SIZES[-1]), dtype=torch.float64, device="cuda")
+    net.infer(torch.from_numpy(x).cuda(), yd)
+    y_ref = ref.predict(x)
+    assert np.linalg.norm(yd.cpu().numpy() - y_ref) / np.linalg.norm(y_ref - ref.out_shift) <= 2e-2
+    net.check()
 
 
 def test_loss_curve_matches_reference(G):
