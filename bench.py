@@ -73,10 +73,46 @@ WORKLOADS = {
 KERNEL_NAMES = ["tile", "per-tuple", "tma-staged tile", "tma-staged, 2 warp groups", "tma-staged, 3 warp groups",
                 "nodal-slab, tma-staged"]
 
-FP32_LANES_PER_SM = 128
-N_SM = 152
-SM_MAX_MHZ = 2070.0
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (no tensor path)
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 schedulers x 32), for the nominal figure only
+
+
+def device_facts(local):
+    """SM count (from the device) and maximum SM clock (nvidia-smi, else the
+    device's clock attribute) of the GPU this rank uses."""
+    import torch
+    props = torch.cuda.get_device_properties(local)
+    sms = int(props.multi_processor_count)
+    mhz = None
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(local), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        mhz = float(out.stdout.strip().splitlines()[0])
+    except Exception:
+        mhz = None
+    if not mhz:
+        try:
+            mhz = float(getattr(props, "clock_rate", 0)) / 1e3 or None
+        except Exception:
+            mhz = None
+    return sms, mhz
+
+
+def measure_fma_peaks(G, uuid):
+    """FMA throughput measured on this device by the library's probe
+    (csrc/ddsg_probe.cu: 8 independent chains per thread, 16 warps per
+    scheduler), with the SM clocks sampled while it runs."""
+    res = {}
+    with ClockSampler(uuid) as clk:
+        for name, kind in (("fp64_fma", 0), ("fp32_fma", 1), ("fp32_fma_x2", 2)):
+            best = 0.0
+            for _ in range(3):
+                t, _ = G.probe_fma(kind)
+                best = max(best, t)
+            res[name] = best
+    res["fp32"] = max(res["fp32_fma"], res["fp32_fma_x2"])
+    res["source"] = "ddsg_probe_fma (paper_2202_06555_gb300/csrc/ddsg_probe.cu), best of 3 launches"
+    res["clocks"] = clk.summary()
+    return res
 
 
 def full_order_components(d, order):
@@ -101,6 +137,14 @@ def comp_list(w):
 EVAL_TRAFFIC = {"workload": "d100", "schedule": (3, 28), "dram_bytes_per_query": (201362176 + 3748352) / 29184,
                 "sha1": {"ddsg_kernels.cu": "ef773b62c5c0c2928f0e37be3d040b7ba7f8b407",
                          "ddsg_internal.h": "4dbdf87f7d04934a20ec267386c110fcd439a05c"}}
+
+
+def measured_peaks():
+    """MEASURED_PEAKS.json (driver-written per pod), or {} where absent."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
 
 
 def eval_traffic(workload, schedule, n):
@@ -348,9 +392,28 @@ def run_irbc(args, w):
                                   "d2h_bytes_per_step": 0}}), flush=True)
         return 0
     import torch
-    import paper_2202_06555_gb300 as G
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    out = measure_irbc(w, args.steps, args.warmup)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# Newton variants of the N = 150 step: (name, precision, tolerance, node mode)
+IRBC_NEWTON_ALL = (("f64", "F64", 1e-6, "NODES_ALL"), ("f32c", "F32C", 1e-6, "NODES_ALL"),
+                   ("f64_tight", "F64", 1e-10, "NODES_ALL"),
+                   ("f32c_node_shortcut", "F32C", 1e-6, "NODES_DELTA"),
+                   ("f64_tight_node_shortcut", "F64", 1e-10, "NODES_DELTA"))
+
+
+def measure_irbc(w, steps, warmup, newton_variants=IRBC_NEWTON_ALL):
+    """Euler-residual sweep of the N = 150 model on the GPU (all nodes, then the
+    node shortcut) and Newton solves per variant; returns the JSON record."""
+    import torch
+    import paper_2202_06555_gb300 as G
     G.load()
+    N, m, d = w["N"], w["m"], w["d"]
+    nq = 2 * (N + 1)
+    metric = "Euler-residual policy evals/s (states x monomial nodes x outputs) at N=150"
     t1, lam, fn, comps, S, g = irbc_workload(w, G)
     h = G.HDMR(d, m, 2, lo=np.full(d, 0.8), hi=np.full(d, 1.2))
     for u in comps:
@@ -368,7 +431,7 @@ def run_irbc(args, w):
     xt = torch.from_numpy(np.ascontiguousarray(np.repeat(S[:nt // nq + 1, :], nq, 0)[:nt])).cuda()
     yt = torch.empty((nt, m), dtype=torch.float64, device="cuda")
     tuned = h.autotune(xt, yt, prec, form)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         M.residual(h, sd, gd, r, None, None, prec, form)
     torch.cuda.synchronize()
     M.profile(True)
@@ -378,13 +441,13 @@ def run_irbc(args, w):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             M.residual(h, sd, gd, r, None, None, prec, form)
         e1.record(stream)
         torch.cuda.synchronize()
     prof = M.profile_read(reset=True)
     M.profile(False)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     value = ns * nq * m / (ms * 1e-3)
     # the node shortcut (a separate form: the plain sweep above is the metric)
     M.set_node_mode(G.NODES_DELTA)
@@ -396,14 +459,14 @@ def run_irbc(args, w):
     d0 = torch.cuda.Event(enable_timing=True)
     d1 = torch.cuda.Event(enable_timing=True)
     d0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         M.residual(h, sd, gd, r_d, None, None, prec, form)
     d1.record(stream)
     torch.cuda.synchronize()
     prof_d = M.profile_read(reset=True)
     M.profile(False)
     M.set_node_mode(G.NODES_ALL)
-    ms_d = d0.elapsed_time(d1) / args.steps
+    ms_d = d0.elapsed_time(d1) / steps
     M.residual(h, sd, gd, r, None, None, prec, form)
     scale = r.abs().clamp_min(1.0)
     shortcut = {"ms_per_step": ms_d, "value": ns * nq * m / (ms_d * 1e-3), "unit": "evals/s",
@@ -412,10 +475,8 @@ def run_irbc(args, w):
                 "kernels_ms": {k: v[0] / max(1, v[1]) for k, v in prof_d.items()}}
     # Newton from the initial guess, FP64 vs F32C interpolation, same tolerance
     newton = {}
-    for name, pr, tol, mode in (("f64", G.F64, 1e-6, G.NODES_ALL), ("f32c", G.F32C, 1e-6, G.NODES_ALL),
-                                ("f64_tight", G.F64, 1e-10, G.NODES_ALL),
-                                ("f32c_node_shortcut", G.F32C, 1e-6, G.NODES_DELTA),
-                                ("f64_tight_node_shortcut", G.F64, 1e-10, G.NODES_DELTA)):
+    for name, prn, tol, moden in newton_variants:
+        pr, mode = getattr(G, prn), getattr(G, moden)
         M.set_node_mode(mode)
         z = gd.clone()
         it = torch.zeros(ns, dtype=torch.int32, device="cuda")
@@ -441,20 +502,20 @@ def run_irbc(args, w):
                         "euler_error_log10_max": float(np.log10(np.max(ee[:, 0]))),
                         "kernels_ms_total": {kk: vv[0] for kk, vv in prof_n.items()},
                         "launches": sum(vv[1] for vv in prof_n.values())}
-    out = {"metric": metric, "value": value, "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+    out = {"metric": metric, "value": value, "unit": "evals/s", "n_gpus": 1, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32" if prec == G.F32C else "f64", "data": "synthetic",
            "config": {"workload": "irbc150_euler_residual", "N": N, "d": d, "m": m,
                       "states": ns, "nodes": nq, "evals_per_sweep": ns * nq,
                       "policy": "empty + 2N singles + N (a_j,k_j) pairs, regular level 4",
                       "precision": w["precision"], "form": w["form"],
-                      "schedule": {"kernel": ["tile", "per-tuple", "tma-staged tile", "tma-staged, 2 warp groups", "tma-staged, 3 warp groups"][tuned[0]],
-                                   "outputs_per_pass": tuned[1]}},
+                      "schedule": {"kernel": KERNEL_NAMES[tuned[0]], "outputs_per_pass": tuned[1]}},
            "kernels_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
            "gpu_launches": sum(v[1] for v in prof.values()),
            "node_shortcut": shortcut, "newton": newton, "clocks": clk.summary()}
-    print(json.dumps(out), flush=True)
-    return 0
+    h.close()
+    M.close()
+    return out
 
 
 def run_irbc_newton(args, w):
@@ -641,6 +702,26 @@ def run_warmstart(args, w):
                           "the warm-start study has no CPU reference arm (GPU-only training)"}))
         return 0
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    out = measure_warmstart(w)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def mlp_gemm_flops(sizes, padded, rows):
+    """FLOPs of the padded GEMMs one training step (forward, input-gradient and
+    weight-gradient GEMMs) and one forward pass run on `rows` batch rows."""
+    P = [(v + 63) // 64 * 64 for v in sizes] if padded else list(sizes)
+    fwd = sum(2.0 * rows * P[l] * P[l + 1] for l in range(len(P) - 1))
+    dgrad = sum(2.0 * rows * P[l] * P[l + 1] for l in range(1, len(P) - 1))
+    return fwd, fwd + dgrad + fwd
+
+
+def measure_warmstart(w):
+    """Time-iteration step at N = 20 with a learned Newton warm start: training
+    pairs from Newton solves, BF16 tensor-core training, Newton from the
+    previous policy vs from the network. Returns the JSON record."""
+    import torch
+    import paper_2202_06555_gb300 as G
     G.load()
     N, d, m = w["N"], w["d"], w["m"]
     t1, lam, fn, comps, _, _ = irbc_workload(dict(w, states=1), G)
@@ -727,6 +808,13 @@ def run_warmstart(args, w):
                      "guess_error_max": float((g0 - z).abs().max().item()),
                      "euler_error_log10_mean": float(np.log10(np.mean(ee[:, 0]))),
                      "euler_error_log10_max": float(np.log10(np.max(ee[:, 0])))}
+    # per-GEMM throughput: padded GEMM FLOPs of the timed steps over the traced GEMM time
+    rows = (bs + 127) // 128 * 128
+    f_fwd, f_step = mlp_gemm_flops(sizes, True, rows)
+    gemm_ms = tprof.get("gemm_fwd", (0.0, 0))[0] + tprof.get("gemm_bwd", (0.0, 0))[0]
+    peaks = measured_peaks()
+    bf16_peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1719.5)))
+    achieved = steps * f_step / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
     out = {"metric": "Newton time at 5e4 states, learned vs previous-policy warm start", "value":
            res["network"]["newton_seconds"] + res["network"]["guess_seconds"], "unit": "s",
            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "bf16",
@@ -738,10 +826,116 @@ def run_warmstart(args, w):
                         "loss_first": float(losses[0].item()), "loss_last": float(losses[-1].item()),
                         "kernels_ms": {k: v[0] for k, v in tprof.items()},
                         "launches": sum(v[1] for v in tprof.values())},
+           "roofline": {"bound": "tensor", "kernel": "gemm_tc_kernel (tcgen05.mma kind::f16, BF16 in, FP32 accumulate)",
+                        "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                        "frac": achieved / bf16_peak if achieved else None, "traffic": None,
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS, of measured)",
+                        "flops_per_step": f_step, "gemm_ms_per_step": gemm_ms / max(1, steps),
+                        "note": "GEMMs of 4096-row batches over widths <= 256: launch- and latency-bound, "
+                                "the traced time includes each launch's event brackets"},
            "newton": res,
            "speedup_newton": res["previous_policy"]["newton_seconds"] / res["network"]["newton_seconds"]}
-    print(json.dumps(out), flush=True)
-    return 0
+    h.close()
+    M.close()
+    net.close()
+    return out
+
+
+def measure_eval_light(w, steps, warmup, uuid, fma):
+    """One evaluation workload on the GPU (build, autotune, timed steps with the
+    clocks sampled, roofline against the measured FMA peak); returns its record."""
+    import torch
+    import paper_2202_06555_gb300 as G
+    G.load()
+    prec = G.F32C if w["precision"] == "f32c" else G.F64
+    form = G.FORM_SLICEFREE if w["form"] == "slicefree" else G.FORM_PAPER
+    h = G.HDMR(w["d"], w["m"], w["order"])
+    fn = value_fn(w)
+    for u in comp_list(w):
+        h.add_regular(list(u), 2)
+    G.build_adaptive(h, fn, w["eps"], w["level"])
+    h1 = G.HDMR(w["d"], w["m"], 1)
+    for u in full_order_components(w["d"], 1):
+        h1.add_regular(list(u), 2)
+    G.build_adaptive(h1, fn, w["eps"], w["level"])
+    X = make_queries(w)
+    n = X.shape[0]
+    x = torch.from_numpy(X).cuda()
+    y = torch.empty((n, w["m"]), dtype=torch.float64, device="cuda")
+    cnt = torch.empty(n, dtype=torch.int32, device="cuda")
+    h.eval(x, y, prec, form, None, cnt)
+    torch.cuda.synchronize()
+    A = float(cnt.double().sum().item())
+    h1.eval(x, y, prec, form, None, cnt)
+    torch.cuda.synchronize()
+    A1 = float(cnt.double().sum().item())
+    h1.close()
+    flops = (2.0 * w["m"] + 1.0) * A + 2.0 * (A - A1) + (A1 - n)
+    ncomp = h.sizes()[0]
+    tuned = h.autotune(x[:min(n, 131072)], y[:min(n, 131072)], prec, form)
+    for _ in range(warmup):
+        h.eval(x, y, prec, form)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    h.profile(True)
+    h.profile_read(reset=True)
+    with ClockSampler(uuid) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            h.eval(x, y, prec, form)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    prof = h.profile_read(reset=True)
+    h.profile(False)
+    ms = e0.elapsed_time(e1) / steps
+    ev_ms = prof.get("eval", (0.0, 1))[0] / max(1, prof.get("eval", (0.0, 1))[1])
+    peak = fma["fp32"] if prec == G.F32C else fma["fp64_fma"]
+    achieved = flops / (ev_ms * 1e-3) / 1e12
+    h.close()
+    return {"metric": metric_for(w), "value": n * w["m"] / (ms * 1e-3), "unit": "evals/s", "ms_per_step": ms,
+            "steps": steps, "warmup": warmup, "dtype": "f32" if prec == G.F32C else "f64",
+            "config": {"workload": "ddsg_d%d" % w["d"], "d": w["d"], "m": w["m"], "queries": n,
+                       "components": ncomp, "precision": w["precision"], "form": w["form"],
+                       "schedule": {"kernel": KERNEL_NAMES[tuned[0]], "outputs_per_pass": tuned[1]},
+                       "active_points_per_query": A / n},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "eval", "kernel_ms": ev_ms,
+                         "peak_source": "measured (of measured): ddsg_probe_fma %s chains" %
+                                        ("FP32" if prec == G.F32C else "FP64"),
+                         "flops_per_launch": flops},
+            "kernels_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
+            "clocks": clk.summary()}
+
+
+def run_extra_configs(uuid, fma):
+    """The other configurations of the benchmark, each bounded to seconds of GPU
+    time: d = 20 FP64 interpolation (4.4e5 monomial-shaped queries), the N = 150
+    Euler-residual sweep with Newton solves (node shortcut FP32C vs FP64 at the
+    same Euler error, and all nodes in FP32C), and the N = 20 learned warm start."""
+    import torch
+    out = {}
+    t0 = time.perf_counter()
+    out["c2_d20_f64"] = measure_eval_light(dict(WORKLOADS["d20"]), 5, 3, uuid, fma)
+    out["c2_d20_f64"]["wall_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rec = measure_irbc(dict(WORKLOADS["irbc150"]), 5, 3,
+                       newton_variants=(("f32c_node_shortcut", "F32C", 1e-6, "NODES_DELTA"),
+                                        ("f64_tight_node_shortcut", "F64", 1e-10, "NODES_DELTA"),
+                                        ("f32c", "F32C", 1e-6, "NODES_ALL")))
+    ev = rec["kernels_ms"]
+    rec["roofline"] = {"bound": "latency", "kernel": "irbc residual sweep (eval dominates)",
+                       "kernel_ms": ev, "traffic": None,
+                       "note": "per-kernel split in kernels_ms; profiles/irbc150_newton_kernels.md gives each limiter"}
+    rec["wall_s"] = time.perf_counter() - t0
+    out["c4_irbc150"] = rec
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rec = measure_warmstart(dict(WORKLOADS["warmstart20"]))
+    rec["wall_s"] = time.perf_counter() - t0
+    out["c5_warmstart20"] = rec
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -762,6 +956,8 @@ def main():
                     help="KERNEL:MC (0 tile, 1 per-tuple, 2 TMA-staged; MC outputs per pass); skips the autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations (d = 20, N = 150 Euler step, N = 20 warm start)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.precision:
@@ -829,8 +1025,22 @@ def main():
     h.eval(x, y, prec, form, None, cnt)
     torch.cuda.synchronize()
     active_total = float(cnt.double().sum().item())
-    k_mean = 2.0 if w["order"] >= 2 else 1.0
-    flops_per_launch = active_total * (2.0 * w["m"] + (k_mean - 1.0))
+    # algorithmic flops: (2m + k + 1) per active point of a k-dimensional component.
+    # The order-<=1 part of the expansion (the same 1D grids: refinement is per
+    # component) counts the active points of components with k <= 1; the
+    # constant component has exactly one per query.
+    active_le1 = active_total
+    if w["eps"] is not None and w["order"] >= 2:
+        h1 = G.HDMR(w["d"], w["m"], 1)
+        for u in full_order_components(w["d"], 1):
+            h1.add_regular(list(u), 2)
+        G.build_adaptive(h1, fn, w["eps"], w["level"])
+        h1.eval(x, y, prec, form, None, cnt)
+        torch.cuda.synchronize()
+        active_le1 = float(cnt.double().sum().item())
+        h1.close()
+    k_sum = 2.0 * (active_total - active_le1) + (active_le1 - n)
+    flops_per_launch = (2.0 * w["m"] + 1.0) * active_total + k_sum
 
     # batching schedule: autotune kernel / output chunk on a subset of the queries
     nt = min(n, 131072)
@@ -880,44 +1090,59 @@ def main():
     eval_avg_ms = eval_ms / max(1, eval_n)
 
     # -- roofline of the dominant kernel (interpolation) ----------------------
+    # peak: the FMA rate measured on this device by the library's probe
+    # (ddsg_probe_fma), beside the nominal figure from the SM count and clock
+    n_sm, sm_mhz = device_facts(local)
+    fma = measure_fma_peaks(G, uuid)
+    nominal_fp32 = n_sm * FP32_LANES_PER_SM * 2 * (sm_mhz or 0.0) * 1e6 / 1e12
     if prec == G.F32C:
-        peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        peak_src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+        peak = fma["fp32"]
+        peak_src = ("measured (of measured): ddsg_probe_fma FP32 chains, %.1f TFLOP/s; nominal %d SMs x %d lanes "
+                    "x 2 flop x %.0f MHz = %.1f" % (peak, n_sm, FP32_LANES_PER_SM, sm_mhz or 0.0, nominal_fp32))
     else:
-        peak = FP64_PEAK_TFLOPS
-        peak_src = "nominal GB300 FP64 1.25 TFLOP/s"
+        peak = fma["fp64_fma"]
+        peak_src = "measured (of measured): ddsg_probe_fma FP64 chains, %.2f TFLOP/s" % peak
     achieved = flops_per_launch / (eval_avg_ms * 1e-3) / 1e12
     hbm_bytes = n * w["d"] * 8 + n * w["m"] * 8 + npts * w["m"] * (4 if prec == G.F32C else 8)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_frac = hbm_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak
 
-    # -- register-delivery floor of the gather (F32C on the staged kernels): every
-    # level tuple a warp of 32 queries visits moves one padded surplus row per lane
-    # (mp floats = mp/4 16-byte loads at 4 wavefronts each = mp wavefronts); the L1
-    # returns one 128-byte wavefront per clock per SM
+    # -- register-delivery floor of the gather (F32C on the staged kernels): the
+    # L1 returns one 128-byte wavefront per clock per SM. Level-tuple kernels:
+    # every level tuple a warp of 32 queries visits moves one padded surplus row
+    # per lane (mp floats = mp wavefronts). Nodal-slab kernel: every node row
+    # moves rs floats per lane (rs = m rounded up to 32: rs wavefronts), at the
+    # node rows per query of its tables.
     l1 = None
     if prec == G.F32C:
-        tuples = 0
-        for c in range(ncomp):
-            dims, _, _ = h.component_info(c)
-            if len(dims) == 0:
-                tuples += 1   # the constant component's single point
-                continue
-            lv, _, _ = h.component_points(c)
-            inner = lv[np.all(lv >= 2, axis=1)] if w["form"] == "slicefree" else lv
-            tuples += len({tuple(r) for r in inner.tolist()})
-        mp = (w["m"] + 3) // 4 * 4
-        wavefronts = (n / 32.0) * tuples * mp
-        floor_ms = wavefronts / (N_SM * SM_MAX_MHZ * 1e6) * 1e3
-        l1 = {"bound": "shared-memory delivery to registers (128 B per clock per SM)",
-              "floor_ms": floor_ms, "kernel_ms": eval_avg_ms, "frac": floor_ms / eval_avg_ms,
-              "tuples_per_query": tuples, "wavefronts_per_32_query_tuples": mp,
-              "note": "lower bound for any kernel that gives each query thread its own copy of each hit row"}
+        wclk = n_sm * (sm_mhz or 2070.0) * 1e6
+        if tuned[0] == 5:
+            _, nrows, rows_q = h.nodal_info(form)
+            rs = (w["m"] + 31) // 32 * 32 if w["m"] > 16 else (w["m"] + 3) // 4 * 4
+            floor_ms = (n / 32.0) * rows_q * rs / wclk * 1e3
+            l1 = {"bound": "shared-memory delivery to registers (128 B per clock per SM)",
+                  "floor_ms": floor_ms, "kernel_ms": eval_avg_ms, "frac": floor_ms / eval_avg_ms,
+                  "node_rows_per_query": rows_q, "node_rows_stored": nrows,
+                  "wavefronts_per_32_query_rows": rs,
+                  "note": "nodal-slab kernel: each query reads two node rows per slab level; "
+                          "lane-rotated 16-byte chunks make every warp load conflict-free"}
+        else:
+            tuples = 0
+            for c in range(ncomp):
+                dims, _, _ = h.component_info(c)
+                if len(dims) == 0:
+                    tuples += 1   # the constant component's single point
+                    continue
+                lv, _, _ = h.component_points(c)
+                inner = lv[np.all(lv >= 2, axis=1)] if w["form"] == "slicefree" else lv
+                tuples += len({tuple(r) for r in inner.tolist()})
+            mp = (w["m"] + 3) // 4 * 4
+            floor_ms = (n / 32.0) * tuples * mp / wclk * 1e3
+            l1 = {"bound": "shared-memory delivery to registers (128 B per clock per SM)",
+                  "floor_ms": floor_ms, "kernel_ms": eval_avg_ms, "frac": floor_ms / eval_avg_ms,
+                  "tuples_per_query": tuples, "wavefronts_per_32_query_tuples": mp,
+                  "note": "lower bound for a level-tuple kernel that gives each query thread its own copy of each hit row"}
 
     # -- end to end: host buffers through the C ABI ---------------------------
     xh = torch.from_numpy(X).pin_memory()
@@ -956,7 +1181,11 @@ def main():
                         "frac": achieved / peak, "traffic": eval_traffic(args.workload, tuned[:2], n),
                         "peak_source": peak_src,
                         "kernel": "eval", "kernel_ms": eval_avg_ms,
-                        "flops_per_launch": flops_per_launch},
+                        "flops_per_launch": flops_per_launch,
+                        "flop_count": "sum over queries and active points of (2m + k + 1), k the component's order",
+                        "active_points": active_total, "active_points_order_le1": active_le1},
+           "fma_peaks": fma,
+           "device": {"sms": n_sm, "sm_max_mhz": sm_mhz},
            "hbm_roofline": {"bytes_per_step": hbm_bytes, "frac": hbm_frac, "peak_gbs": hbm_peak,
                             "note": "compulsory bytes / step time / measured copy bandwidth"},
            "l1_roofline": l1,
@@ -1024,9 +1253,17 @@ def main():
                                          f"(~10 s of CPU work)",
                                "single_thread": {"value": rate, "sample": f"first {used} queries, "
                                                                           f"~10 s"}}
+    # -- the other configurations, each bounded (rank 0, N = 1, default workload) --
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "d100":
+        h.close()
+        h = None
+        t0 = time.perf_counter()
+        out["configs"] = run_extra_configs(uuid, fma)
+        out["configs"]["wall_s"] = time.perf_counter() - t0
     if rank == 0:
         print(json.dumps(out), flush=True)
-    h.close()
+    if h is not None:
+        h.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

@@ -245,20 +245,37 @@ int hdmr_eval(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int prec
 /*
  * Evaluation kernel choice (the batching schedule). kernel 0 = tile kernel
  * (1D bases of a component staged once per dimension and level), kernel 1 =
- * per-tuple kernel, kernel 2 = tile kernel whose component surplus blocks are
- * staged into shared memory by TMA bulk copies, double-buffered (needs every
- * evaluated component's block to fit the staging buffer; refused otherwise);
- * mc = outputs per thread and pass (0 = the
- * heuristic: smallest compiled chunk >= m). hdmr_autotune times every compiled
- * pair on the caller's queries (x_dev, n; y_dev is scratch output) and keeps
- * the fastest for (precision, form); *best_ms (nullable) gets its time.
- * Autotuning runs the evaluation about 36 times: tune on a representative
- * subset of the queries.
+ * per-tuple kernel, kernels 2-4 = tile kernels whose component surplus blocks
+ * are staged into shared memory by TMA bulk copies, three-deep (one, two or
+ * three warp groups per query; need every evaluated component's block to fit
+ * the staging buffer, k <= 2 and levels <= 15; refused otherwise), kernel 5 =
+ * the staged nodal-slab kernel: each component's interpolant stored by node
+ * values along one dimension per cell of the other (hdmr_nodal_info), two node
+ * rows per slab level and query instead of one surplus row per level tuple
+ * (k <= 2; its tables are planned and uploaded on first use, which allocates).
+ * Kernel 5 has no per-point active set: a call with hash_dev or count_dev
+ * evaluates with kernel 0. mc = outputs per thread and pass (0 = the
+ * heuristic: smallest compiled chunk >= m; kernel 5: 32 = the FP32 layout of
+ * 32-output windows read in a bank-conflict-free rotated order). hdmr_autotune
+ * times every compiled pair on the caller's queries (x_dev, n; y_dev is
+ * scratch output) and keeps the fastest for (precision, form); *best_ms
+ * (nullable) gets its time. Autotuning runs the evaluation about 40 times:
+ * tune on a representative subset of the queries.
  */
 int hdmr_set_eval_config(hdmr_t *h, int precision, int form, int kernel, int mc);
 int hdmr_get_eval_config(const hdmr_t *h, int precision, int form, int *kernel, int *mc);
 int hdmr_autotune(hdmr_t *h, int64_t n, const double *x_dev, double *y_dev, int precision,
                   int form, ddsg_stream_t stream, double *best_ms);
+
+/*
+ * hdmr_nodal_info -- the nodal-slab tables of evaluation kernel 5 for `form`
+ * (no paper counterpart: a change of basis of the component interpolants of
+ * Sec. 3.1). Plans and uploads them if they are not built yet (allocates).
+ * *eligible: 1 if kernel 5 can hold these tables; *rows: node rows stored;
+ * *rows_per_query: node rows a query uniformly distributed in the domain reads,
+ * summed over the components (the kernel's work per query). Pointers nullable.
+ */
+int hdmr_nodal_info(hdmr_t *h, int form, int32_t *eligible, int64_t *rows, double *rows_per_query);
 
 /*
  * hdmr_eval_noalloc -- hdmr_eval (no hash/count outputs) that allocates no
@@ -532,6 +549,16 @@ int mlp_load(const char *path, mlp_t **out);
 int mlp_shape(const mlp_t *net, int32_t *nlayers, int32_t *sizes_host);
 /* Kernel timing: kinds 0 forward GEMMs, 1 backward GEMMs, 2 loss/normalization, 3 Adam. */
 int mlp_profile(mlp_t *net, int enable);
+/*
+ * ddsg_probe_fma -- measured FMA throughput of the current device (no paper
+ * counterpart): the peak the evaluation kernels' ALU rooflines divide by.
+ * kind 0: FP64 fma; 1: FP32 fmaf; 2: paired FP32 (fma.rn.f32x2). Runs 8
+ * independent chains per thread on 8 blocks of 256 threads per SM, times the
+ * second of two launches with CUDA events; *tflops = 2 flops per FMA / time,
+ * *ms (nullable) the launch time. Synchronous; allocates 16 bytes.
+ */
+int ddsg_probe_fma(int kind, double *tflops, double *ms);
+
 /*
  * mlp_check -- status of the network's tensor-core GEMMs since the last check
  * (no paper counterpart). Every mbarrier wait in them is bounded; a wait that

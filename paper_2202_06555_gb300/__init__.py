@@ -86,6 +86,8 @@ SIGNATURES = {
     "mlp_profile": (_int, [_p, _int]),
     "mlp_profile_read": (_int, [_p, _p, _p, _int]),
     "mlp_check": (_int, [_p]),
+    "ddsg_probe_fma": (_int, [_int, _p, _p]),
+    "hdmr_nodal_info": (_int, [_p, _int, _p, _p, _p]),
     "irbc_profile_read": (_int, [_p, _p, _p, _int]),
     "irbc_set_node_mode": (_int, [_p, _int]),
     "irbc_set_irreversible": (_int, [_p, _int]),
@@ -176,6 +178,14 @@ def _stream_ptr(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return C.c_void_p(stream.cuda_stream)
+
+
+def probe_fma(kind: int):
+    """Measured FMA throughput of the current device: kind 0 FP64, 1 FP32, 2 paired
+    FP32 (fma.rn.f32x2). Returns (TFLOP/s, ms of the timed launch)."""
+    t, ms = C.c_double(), C.c_double()
+    _check(load().ddsg_probe_fma(int(kind), C.byref(t), C.byref(ms)), "ddsg_probe_fma")
+    return t.value, ms.value
 
 
 class HDMR:
@@ -353,6 +363,13 @@ class HDMR:
         _check(load().hdmr_eval_host(self._h, n, C.c_void_p(x_host.ctypes.data),
                                      C.c_void_p(y_host.ctypes.data), int(precision), int(form),
                                      _stream_ptr(stream)), "hdmr_eval_host")
+
+    def nodal_info(self, form: int = FORM_SLICEFREE):
+        """Tables of the nodal-slab kernel (planned if needed): (eligible, node rows,
+        node rows read per uniformly distributed query)."""
+        e, r, q = C.c_int32(), C.c_int64(), C.c_double()
+        _check(load().hdmr_nodal_info(self._h, int(form), C.byref(e), C.byref(r), C.byref(q)), "hdmr_nodal_info")
+        return bool(e.value), r.value, q.value
 
     def set_eval_config(self, precision: int, form: int, kernel: int, mc: int):
         _check(load().hdmr_set_eval_config(self._h, precision, form, kernel, mc),

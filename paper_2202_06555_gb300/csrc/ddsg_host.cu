@@ -1314,6 +1314,18 @@ extern "C" int hdmr_set_eval_config(hdmr_t *h, int precision, int form, int kern
     return DDSG_OK;
 }
 
+extern "C" int hdmr_nodal_info(hdmr_t *h, int form, int32_t *eligible, int64_t *rows, double *rows_per_query) {
+    if (!h || form < 0 || form > 1) return fail(DDSG_ERR_ARG, "hdmr_nodal_info: bad argument");
+    if (!h->uploaded || h->device < 0) return fail(DDSG_ERR_STATE, "hdmr_nodal_info: call hdmr_hierarchize first");
+    DeviceGuard g(h->device);
+    if (int rc0 = ensure_nodal(h, form, nullptr)) return rc0;
+    const DevNodal &N = h->dt.nod[form];
+    if (eligible) *eligible = N.ok ? 1 : 0;
+    if (rows) *rows = N.rows;
+    if (rows_per_query) *rows_per_query = N.erows;
+    return DDSG_OK;
+}
+
 extern "C" int hdmr_get_eval_config(const hdmr_t *h, int precision, int form, int *kernel, int *mc) {
     if (!h || precision < 0 || precision > 1 || form < 0 || form > 1)
         return fail(DDSG_ERR_ARG, "hdmr_get_eval_config: bad argument");

@@ -174,6 +174,7 @@ struct DevNodal {
     int2 *grp = nullptr;
     int4 *gpts = nullptr;
     int64_t ngrp = 0, ngpts = 0;
+    double erows = 0;          // node rows a uniformly distributed query reads, summed over components
 };
 
 struct DevTables {
@@ -289,6 +290,10 @@ __host__ __device__ inline uint64_t mix64(uint64_t z) {
 // ---------------------------------------------------------------------------
 // kernel launchers (ddsg_kernels.cu)
 // ---------------------------------------------------------------------------
+
+// SM count of the current device (1 if it cannot be read): grid caps of the
+// grid-stride kernels.
+int device_sm_count();
 
 cudaError_t launch_encode_queries(int64_t n, int d, const double *x, const double *lo,
                                   const double *span, uint64_t *X, int64_t *stats,

@@ -96,13 +96,23 @@ __global__ void __launch_bounds__(256) encode_queries_kernel(int64_t n, int d, c
     if ((threadIdx.x & 31) == 0 && clamps) atomicAdd(&stats[0], clamps);
 }
 
+int device_sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
 cudaError_t launch_encode_queries(int64_t n, int d, const double *x, const double *lo,
                                   const double *span, uint64_t *X, int64_t *stats,
                                   cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     int32_t *flags = reinterpret_cast<int32_t *>(X + n * (int64_t)d);
     int64_t blocks = (n + 31) / 32;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    const int64_t cap = (int64_t)device_sm_count() * 16;
+    if (blocks > cap) blocks = cap;
     encode_queries_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, d, x, lo, span, X, flags,
                                                            reinterpret_cast<unsigned long long *>(stats));
     return cudaGetLastError();
@@ -1135,7 +1145,8 @@ cudaError_t launch_to_f32(const double *a, int mp64, float *b, int mp32, int64_t
                           cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
     int64_t blocks = (P * mp32 + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    const int64_t cap = (int64_t)device_sm_count() * 32;
+    if (blocks > cap) blocks = cap;
     to_f32_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, mp64, b, mp32, P, m);
     return cudaGetLastError();
 }

@@ -198,13 +198,16 @@ int nodal_build(int m, int form, const std::vector<NodalComp> &comps, const std:
         const uint32_t dn = ndim >= 0 ? (uint32_t)c.dims[ndim] : kNone;
         const uint32_t ds = sdim >= 0 ? (uint32_t)c.dims[sdim] : kNone;
         rec2.push_back(make_int4(ci, (int)(dn | (ds << 16)), (int)c.b, 0));
+        out.erows += P.erows;
         meta_max = std::max<int64_t>(meta_max, ((int64_t)nmeta * 8 + 15) & ~15ll);
         rows_max = std::max<int64_t>(rows_max, row);
         rows_total += row;
         if (meta.size() >= (size_t)INT_MAX) return DDSG_OK;
     }
+    const double erows = out.erows;
     out.n = (int32_t)rec.size();
     out.rows = rows_total;
+    out.erows = erows;
     out.rs32 = rs32;
     out.meta_bytes = (int32_t)((meta_max + 127) & ~127ll);
     out.stage_bytes[DDSG_F64] = out.meta_bytes + rows_max * mp64 * 8;
@@ -286,20 +289,11 @@ __global__ void nodal_to_f32_kernel(const double *__restrict__ v64, int mp64, fl
     }
 }
 
-static int sm_count() {
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-        cudaGetLastError();
-        return 1;
-    }
-    return n > 0 ? n : 1;
-}
-
 cudaError_t launch_nodalize(const DevNodal &nd, const double *alpha64, int mp64, int m, cudaStream_t st) {
     if (!nd.ok || nd.rows <= 0) return cudaSuccess;
     const int64_t total = nd.rows * (int64_t)m;
     int64_t blocks = (total + 255) / 256;
-    const int64_t cap = (int64_t)sm_count() * 16;
+    const int64_t cap = (int64_t)device_sm_count() * 16;
     if (blocks > cap) blocks = cap;
     nodalize_kernel<<<(unsigned)blocks, 256, 0, st>>>(nd.nrow, nd.rows, nd.grp, nd.gpts, alpha64, mp64, m, nd.v64);
     cudaError_t e = cudaGetLastError();
