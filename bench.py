@@ -129,14 +129,21 @@ def comp_list(w):
     return full_order_components(w["d"], w["order"])
 
 
-# DRAM traffic of the evaluation kernel from one ncu capture (profiles/
-# eval_tma_d100_ncu_full.md: d=100 tables, 29184 queries, two-group TMA-staged
-# kernel at 28 outputs per group), per query; scaled to a full launch by the
-# query count.
-# Valid only for the kernel sources it was taken on (checked by hash).
-EVAL_TRAFFIC = {"workload": "d100", "schedule": (3, 28), "dram_bytes_per_query": (201362176 + 3748352) / 29184,
-                "sha1": {"ddsg_kernels.cu": "ef773b62c5c0c2928f0e37be3d040b7ba7f8b407",
-                         "ddsg_internal.h": "4dbdf87f7d04934a20ec267386c110fcd439a05c"}}
+# DRAM traffic of the evaluation kernel from one ncu capture per schedule, per
+# query; scaled to a full launch by the query count (the tables stream through
+# L2 once per wave of resident blocks, so traffic grows with the queries).
+#   (5, 32): profiles/eval_nodal_d100_ncu_full.md -- the nodal-slab kernel, d=100
+#            tables, 29184 queries (one wave of 152 blocks of 192 queries);
+#   (3, 28): profiles/eval_tma_d100_ncu_full.md -- the two-group level-tuple
+#            TMA kernel at 28 outputs per group, same tables and queries.
+# Valid only for the kernel sources each was taken on (checked by hash).
+EVAL_TRAFFIC = [
+    {"workload": "d100", "schedule": (5, 32), "dram_bytes_per_query": (355433472 + 4008448) / 29184,
+     "sha1": {"ddsg_nodal.cu": "c3418abccc98544024d6121b90a3260f2c5968df",
+              "ddsg_eval.cuh": "a190d34e3b3fe0a7095a2f5ca6734106056dd7c9",
+              "ddsg_internal.h": "35e5d984e243926340ad5cc33984726f9818640e",
+              "ddsg_tma.cuh": "3d90c7da8651e19c5d8c36464fa0ee4bdc3e1dbd"}},
+]
 
 
 def measured_peaks():
@@ -149,14 +156,15 @@ def measured_peaks():
 
 def eval_traffic(workload, schedule, n):
     import hashlib
-    t = EVAL_TRAFFIC
-    if workload != t["workload"] or tuple(schedule) != t["schedule"]:
-        return None
-    for f, h in t["sha1"].items():
-        path = os.path.join(ROOT, "paper_2202_06555_gb300", "csrc", f)
-        if hashlib.sha1(open(path, "rb").read()).hexdigest() != h:
-            return None
-    return t["dram_bytes_per_query"] * n
+    for t in EVAL_TRAFFIC:
+        if workload != t["workload"] or tuple(schedule) != t["schedule"]:
+            continue
+        for f, h in t["sha1"].items():
+            path = os.path.join(ROOT, "paper_2202_06555_gb300", "csrc", f)
+            if hashlib.sha1(open(path, "rb").read()).hexdigest() != h:
+                return None
+        return t["dram_bytes_per_query"] * n
+    return None
 
 
 def make_queries(w, rank=0):
