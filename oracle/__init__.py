@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-std=c11", "-o", tmp] + srcs + ["-lm"]
+               "-std=c11", "-pthread", "-o", tmp] + srcs + ["-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _SO)
     return _SO
@@ -84,6 +84,9 @@ def _declare(L):
     L.orc_refine.restype = _i64
     L.orc_refine.argtypes = [C.c_int, C.c_int, _i64, _i64, _p, _p, _p, _d, C.c_int, C.c_int,
                              _i64, _p, _p]
+    L.orc_active_pruned.restype = C.c_int
+    L.orc_active_pruned.argtypes = [C.c_int, C.c_int, _p, _p, _p, _p, _p, _p, _p, _p, C.c_int, _i64,
+                                    _p, _p, _p, C.c_int]
     L.orc_quadrature.restype = None
     L.orc_quadrature.argtypes = [C.c_int, C.c_int, _p, _p, _p, _p, _p, _p]
     if hasattr(L, "orc_irbc_residual"):
@@ -300,6 +303,23 @@ class OracleDDSG:
             if arr is not None:
                 out[name] = arr
         return out
+
+    def active_pruned(self, x, form=0, threads=1):
+        """Active-set hashes and counts (as eval's hash / count) by tree descent from
+        each component's root (a child is visited only from an active parent);
+        `threads` host threads over the queries. Returns (hash, count)."""
+        t = self.tables()
+        x = np.ascontiguousarray(x, np.float64).reshape(-1, self.d)
+        n = x.shape[0]
+        b = self.b_coeffs()
+        h = np.zeros(n, np.uint64)
+        cnt = np.zeros(n, np.int32)
+        rc = lib().orc_active_pruned(self.d, len(self.comps), ptr(t["k"]), ptr(t["dims"]), ptr(t["off"]),
+                                     ptr(t["lv"]), ptr(t["ix"]), ptr(b), ptr(self.lo), ptr(self.hi),
+                                     int(form), n, ptr(x), ptr(h), ptr(cnt), int(threads))
+        if rc != 0:
+            raise ValueError("a component has no root point (1, ..., 1)")
+        return h, cnt
 
     def eval_telescopic(self, x):
         t = self.tables()

@@ -26,6 +26,7 @@
  * (tests/test_oracle_pins.py); all functions below are pinned.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -576,4 +577,181 @@ void orc_quadrature(int m, int C, const int32_t *comp_k, const int64_t *comp_off
             for (int j = 0; j < m; ++j) Q[c * m + j] += w * alpha[p * m + j];
         }
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Pruned active sets: tree descent (Sec. 3.1, eq. 3.3)                */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The support of a child (one dimension refined one level) lies inside its
+ * parent's support, so every active point's parents are active, and every
+ * point of a grid built by refinement is reached from the root (1, ..., 1) by
+ * a chain of existing parent -> child links. The active set of a query is
+ * therefore found by a breadth-first descent that starts at the root and visits
+ * a child only from an active parent and only if the child's own hat is
+ * nonzero in the refined dimension (its other dimensions equal the parent's).
+ * Points are looked up in a per-call copy of each component's points sorted
+ * by (levels, indices). Only the index work is computed: the XOR of the point
+ * keys and the count of the active points the form sums (form 1: all levels
+ * >= 2), exactly as orc_eval's hash and count outputs. Queries run in parallel
+ * over `threads` POSIX threads (0: one), each with its own visit stamps.
+ * Returns 0, or -1 if a component has no root point (then nothing is written).
+ */
+typedef struct {
+    int32_t comp, k;
+    uint8_t lv[KMAX];
+    uint32_t ix[KMAX];
+    int64_t orig;          /* index of the point in the caller's tables */
+} ppt_t;
+
+static int cmp_ppt(const void *A, const void *B)
+{
+    const ppt_t *a = (const ppt_t *)A, *b = (const ppt_t *)B;
+    if (a->comp != b->comp) return a->comp < b->comp ? -1 : 1;
+    for (int j = 0; j < a->k; ++j)
+        if (a->lv[j] != b->lv[j]) return a->lv[j] < b->lv[j] ? -1 : 1;
+    for (int j = 0; j < a->k; ++j)
+        if (a->ix[j] != b->ix[j]) return a->ix[j] < b->ix[j] ? -1 : 1;
+    return 0;
+}
+
+typedef struct {
+    int d, C, form;
+    const int32_t *comp_k, *comp_dims;
+    const int64_t *comp_off;
+    const ppt_t *pts;          /* all points, sorted by (component, levels, indices) */
+    const int64_t *root;       /* per component: position of its root in pts */
+    const double *b, *lo, *hi, *x;
+    uint64_t *hash;
+    int32_t *count;
+    int64_t q0, q1;
+    int64_t P;
+} prune_job_t;
+
+static int64_t find_sorted(const ppt_t *pts, int64_t p0, int64_t p1, const ppt_t *key)
+{
+    int64_t lo = p0, hi = p1;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        int c = cmp_ppt(&pts[mid], key);
+        if (c == 0) return mid;
+        if (c < 0) lo = mid + 1; else hi = mid;
+    }
+    return -1;
+}
+
+static void *prune_worker(void *arg)
+{
+    prune_job_t *J = (prune_job_t *)arg;
+    const int d = J->d;
+    int64_t *stamp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(J->P > 0 ? J->P : 1));
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)(J->P > 0 ? J->P : 1));
+    double *xc = (double *)malloc(sizeof(double) * (size_t)d);
+    for (int64_t i = 0; i < J->P; ++i) stamp[i] = -1;
+    for (int64_t q = J->q0; q < J->q1; ++q) {
+        int finite = 1;
+        for (int i = 0; i < d; ++i) {
+            double v = J->x[q * d + i];
+            if (!isfinite(v) || !isfinite((v - J->lo[i]) / (J->hi[i] - J->lo[i]))) finite = 0;
+            xc[i] = canon(v, J->lo[i], J->hi[i]);
+        }
+        uint64_t h = 0;
+        int32_t cnt = 0;
+        if (finite) {
+            for (int c = 0; c < J->C; ++c) {
+                if (J->form == 0 && J->b[c] == 0.0) continue;
+                const int k = J->comp_k[c];
+                const int32_t *dims = &J->comp_dims[c * KMAX];
+                const int64_t p0 = J->comp_off[c], p1 = J->comp_off[c + 1];
+                int64_t head = 0, tail = 0;
+                queue[tail++] = J->root[c];
+                stamp[J->root[c]] = q;
+                while (head < tail) {
+                    const ppt_t *p = &J->pts[queue[head++]];
+                    int interior = 1;
+                    for (int j = 0; j < k; ++j) if (p->lv[j] < 2) interior = 0;
+                    if (J->form == 0 || interior) {
+                        h ^= orc_point_key(c, k, p->lv, p->ix);
+                        ++cnt;
+                    }
+                    for (int j = 0; j < k; ++j) {
+                        uint32_t ci[2];
+                        const int nc = children1d(p->lv[j], p->ix[j], ci);
+                        for (int t = 0; t < nc; ++t) {
+                            if (!orc_active1d(p->lv[j] + 1, ci[t], xc[dims[j]])) continue;
+                            ppt_t key = *p;
+                            key.lv[j] = (uint8_t)(p->lv[j] + 1);
+                            key.ix[j] = ci[t];
+                            const int64_t f = find_sorted(J->pts, p0, p1, &key);
+                            if (f >= 0 && stamp[f] != q) {
+                                stamp[f] = q;
+                                queue[tail++] = f;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (J->hash) J->hash[q] = h;
+        if (J->count) J->count[q] = cnt;
+    }
+    free(stamp);
+    free(queue);
+    free(xc);
+    return NULL;
+}
+
+int orc_active_pruned(int d, int C, const int32_t *comp_k, const int32_t *comp_dims,
+                      const int64_t *comp_off, const uint8_t *levels, const uint32_t *indices,
+                      const double *b, const double *lo, const double *hi, int form, int64_t n,
+                      const double *x, uint64_t *hash, int32_t *count, int threads)
+{
+    const int64_t P = comp_off[C];
+    ppt_t *pts = (ppt_t *)malloc(sizeof(ppt_t) * (size_t)(P > 0 ? P : 1));
+    int64_t *root = (int64_t *)malloc(sizeof(int64_t) * (size_t)(C > 0 ? C : 1));
+    int rc = 0;
+    for (int c = 0; c < C; ++c)
+        for (int64_t p = comp_off[c]; p < comp_off[c + 1]; ++p) {
+            ppt_t *t = &pts[p];
+            memset(t, 0, sizeof *t);
+            t->comp = c;
+            t->k = comp_k[c];
+            for (int j = 0; j < comp_k[c]; ++j) {
+                t->lv[j] = levels[p * KMAX + j];
+                t->ix[j] = indices[p * KMAX + j];
+            }
+            t->orig = p;
+        }
+    qsort(pts, (size_t)P, sizeof(ppt_t), cmp_ppt);
+    for (int c = 0; c < C && rc == 0; ++c) {
+        ppt_t key;
+        memset(&key, 0, sizeof key);
+        key.comp = c;
+        key.k = comp_k[c];
+        for (int j = 0; j < comp_k[c]; ++j) { key.lv[j] = 1; key.ix[j] = 1; }
+        root[c] = find_sorted(pts, comp_off[c], comp_off[c + 1], &key);
+        if (root[c] < 0) rc = -1;
+    }
+    if (rc == 0) {
+        if (threads < 1) threads = 1;
+        if (threads > 256) threads = 256;
+        prune_job_t jobs[256];
+        pthread_t tid[256];
+        for (int t = 0; t < threads; ++t) {
+            prune_job_t *J = &jobs[t];
+            J->d = d; J->C = C; J->form = form;
+            J->comp_k = comp_k; J->comp_dims = comp_dims; J->comp_off = comp_off;
+            J->pts = pts; J->root = root; J->b = b; J->lo = lo; J->hi = hi; J->x = x;
+            J->hash = hash; J->count = count; J->P = P;
+            J->q0 = n * t / threads;
+            J->q1 = n * (t + 1) / threads;
+        }
+        for (int t = 1; t < threads; ++t) pthread_create(&tid[t], NULL, prune_worker, &jobs[t]);
+        prune_worker(&jobs[0]);
+        for (int t = 1; t < threads; ++t) pthread_join(tid[t], NULL);
+    }
+    free(pts);
+    free(root);
+    return rc;
 }

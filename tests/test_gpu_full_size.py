@@ -78,6 +78,28 @@ def test_d100_two_million_queries_f32c(G, d100, kernel, mc):
     _check(G, ref, h, X, G.F32C, G.FORM_SLICEFREE, kernel, mc, 1e-6)
 
 
+def test_d100_active_sets_against_the_pruned_oracle(G, d100):
+    """Active-set hashes and counts of all 2e6 queries from the GPU (level-tuple
+    kernel with hash / count outputs); every 488th query (4,099 of them) is
+    compared with the oracle's pruned tree descent, on all host threads. (The
+    descent runs at a few hundred d = 100 queries per second per eight threads,
+    so the whole 2e6 would take hours.)"""
+    import os
+    ref, h, X = d100
+    n = X.shape[0]
+    x = torch.from_numpy(X).cuda()
+    y = torch.empty((n, ref.m), dtype=torch.float64, device="cuda")
+    hs = torch.empty(n, dtype=torch.int64, device="cuda")
+    ct = torch.empty(n, dtype=torch.int32, device="cuda")
+    h.eval(x, y, G.F32C, G.FORM_SLICEFREE, hs, ct)
+    torch.cuda.synchronize()
+    idx = np.arange(0, n, 488)
+    ph, pc = ref.active_pruned(X[idx], 1, threads=os.cpu_count() or 1)
+    assert np.array_equal(ct.cpu().numpy()[idx], pc)
+    assert np.array_equal(hs.cpu().numpy().view(np.uint64)[idx], ph)
+    assert int(ct.min().item()) > 0
+
+
 @pytest.mark.parametrize("kernel,mc", [(0, 12), (5, 8)])
 def test_d20_monomial_queries_f64(G, kernel, mc):
     ref, h = _pair(G, 20, 11, synth.W_D20)

@@ -99,7 +99,9 @@ def test_delta_nodes_general_component_set(G):
         sc = scales(I, S, g, r_ref)
         for prec in (0, 1):
             r, _, _ = run(G, M, h, S, g, prec, form, G.NODES_DELTA)
-            tol = 1e-11 if prec == 0 else 1e-6 * float(np.sum(np.abs(E.b_coeffs())))
+            # the bars of the all-node tests: FP64 1e-11; F32C 1e-6 (slice-free),
+            # 1e-7 x sum |b| (paper form, whose terms carry the coefficients b)
+            tol = 1e-11 if prec == 0 else (1e-6 if form == 1 else 1e-7 * float(np.sum(np.abs(E.b_coeffs()))))
             assert np.all(np.abs(r - r_ref) <= tol * sc), (form, prec, np.max(np.abs(r - r_ref) / sc))
     # the analytic Jacobian on this component set (k_i held by {k_i}, (a_i, k_i),
     # (a_2, k_3) and (k_0, k_1)) against central differences of the oracle

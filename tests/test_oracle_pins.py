@@ -528,6 +528,47 @@ def test_p12_active_set_count_and_hash_regular_4d():
     assert E.eval(xn, want=("count",))["count"][0] < 70
 
 
+def test_p12_pruned_descent_equals_brute_force():
+    """The pruned mode (tree descent from each component's root, a child visited
+    only from an active parent) finds the same active sets as the brute force,
+    which tests every point: C1 (d = 4 regular level-5 grid), the C2 expansion
+    (d = 20, order 2, adaptive to level 10, both forms, clamped monomial-shaped
+    queries) and an adaptive d = 4 expansion at nodes, faces, corners and
+    non-finite rows."""
+    d, m = 4, 3
+    c = synth.family_coeffs(synth.BASE_SEED + synth.W_SG4, m, d)
+    E = O.OracleDDSG(d, m)
+    E.add_regular((0, 1, 2, 3), 5)
+    E.fill_values(lambda dims, X: synth.family_cut(c, dims, X))
+    E.hierarchize()
+    X = synth.uniform_queries(5, 2000, d)
+    r = E.eval(X, form=0, want=("hash", "count"))
+    h, cnt = E.active_pruned(X, 0, threads=4)
+    assert np.array_equal(h, r["hash"]) and np.array_equal(cnt, r["count"])
+
+    d, m = 20, 11
+    c = synth.family_coeffs(synth.BASE_SEED + synth.W_D20, m, d)
+    E = O.OracleDDSG(d, m)
+    for u in O.full_order_components(d, 2):
+        E.add_regular(u, 2)
+    E.build_adaptive(lambda dims, X: synth.family_cut(c, dims, X), 1e-3, 10)
+    X = synth.monomial_shaped_queries(synth.BASE_SEED + synth.W_D20, 20, 10, s=0.05)
+    for form in (0, 1):
+        r = E.eval(X, form=form, want=("hash", "count"))
+        h, cnt = E.active_pruned(X, form, threads=3)
+        assert np.array_equal(h, r["hash"]) and np.array_equal(cnt, r["count"]), form
+
+    E, _ = _adaptive_d4()
+    pts = [np.zeros(4), np.ones(4), np.full(4, 0.5), np.array([0.25, 0.75, 0.125, 0.375]),
+           np.array([np.nan, 0.2, 0.3, 0.4]), np.array([0.2, np.inf, 0.3, 0.1])]
+    pts += [row for row in E.node_coords(len(E.comps) - 1)[:, [0, 0, 0, 0]][:40]]
+    X = np.concatenate([np.array(pts), synth.uniform_queries(6, 300, 4)])
+    for form in (0, 1):
+        r = E.eval(X, form=form, want=("hash", "count"))
+        h, cnt = E.active_pruned(X, form, threads=2)
+        assert np.array_equal(h, r["hash"]) and np.array_equal(cnt, r["count"]), form
+
+
 def test_eval_clamps_to_domain():
     f = lambda X: np.stack([X[:, 0] + 2 * X[:, 1]], 1)
     E = O.OracleDDSG(2, 1, lo=[-1.0, 2.0], hi=[1.0, 4.0])
