@@ -205,6 +205,22 @@ int hdmr_shape(const hdmr_t *h, int32_t *d, int32_t *m, int32_t *order, double *
  */
 int hdmr_quadrature(hdmr_t *h, double *q_dev, ddsg_stream_t stream);
 
+/*
+ * hdmr_expansion_norms -- the criteria of Alg. 2 for the components of order k,
+ * from the component integrals of hdmr_quadrature:
+ *   qf_host (ncomp*m, nullable): the cut-HDMR component integrals
+ *     Qf_u = sum over v subset of u of (-1)^(|u|-|v|) Q_v (every subset of every
+ *     component must itself be a component: DDSG_ERR_ARG otherwise);
+ *   eta_host (ncomp, nullable): eq. 3.19, eta_u = ||Qf_u||_2 / ||sum_{|v|<=k-1} Qf_v||_2
+ *     for |u| = k, NaN for the other components;
+ *   *rho_all (nullable): eq. 3.18 over all components of order k;
+ *   *rho_kept (nullable): the same over those kept (eta_u > eps_eta; all of them
+ *     when k = 1).
+ * FP64; synchronous on `stream`; allocates ncomp*m doubles of device scratch.
+ */
+int hdmr_expansion_norms(hdmr_t *h, int k, double eps_eta, double *qf_host, double *eta_host, double *rho_all,
+                         double *rho_kept, ddsg_stream_t stream);
+
 /* Copy FP64 surpluses of all points to the host (npts_total*m). Synchronous. */
 int hdmr_get_surpluses(const hdmr_t *h, double *alpha_host, ddsg_stream_t stream);
 
@@ -415,6 +431,16 @@ typedef struct {
  * copied. Makes no CUDA call. */
 int irbc_create(const irbc_params_t *prm, const double *gamma_host, const double *tau_host,
                 irbc_t **out);
+/* New model calibrated as in Table 1: the caller gives N, the curvature offset
+ * a_gamma (0.25 in Table 1), beta, alpha, delta, sigma, rho and phi; the
+ * library derives A = (1 - beta (1 - delta)) / (alpha beta), gamma_j = a_gamma +
+ * 0.75 (j - 1) / (N - 1) (a_gamma when N = 1) and tau_j = A^(1 / gamma_j).
+ * DDSG_ERR_ARG for N outside [1, 4096] or beta, alpha outside (0, 1), delta
+ * outside [0, 1), a_gamma <= 0. Makes no CUDA call. */
+int irbc_create_table1(int N, double a_gamma, double beta, double alpha, double delta, double sigma,
+                       double rho, double phi, irbc_t **out);
+/* The model's parameters (prm), gamma_j and tau_j (length N); pointers nullable. */
+int irbc_get_params(const irbc_t *model, irbc_params_t *prm, double *gamma_host, double *tau_host);
 int irbc_destroy(irbc_t *model);
 
 /*

@@ -70,6 +70,9 @@ SIGNATURES = {
     "hdmr_shape": (_int, [_p, _p, _p, _p, _p, _p, _p]),
     "hdmr_eval_noalloc_capacity": (_i64, [_int]),
     "irbc_create": (_int, [_p, _p, _p, C.POINTER(_p)]),
+    "irbc_create_table1": (_int, [_int, _d, _d, _d, _d, _d, _d, _d, C.POINTER(_p)]),
+    "irbc_get_params": (_int, [_p, _p, _p, _p]),
+    "hdmr_expansion_norms": (_int, [_p, _int, _d, _p, _p, _p, _p, _p]),
     "irbc_destroy": (_int, [_p]),
     "euler_residual": (_int, [_p, _p, _i64, _p, _p, _p, _p, _p, _int, _int, _p]),
     "irbc_lu_solve": (_int, [_int, _i64, _p, _p, _p, _p, _p]),
@@ -364,6 +367,19 @@ class HDMR:
                                      C.c_void_p(y_host.ctypes.data), int(precision), int(form),
                                      _stream_ptr(stream)), "hdmr_eval_host")
 
+    def expansion_norms(self, k: int, eps_eta: float = -1.0, stream=None):
+        """Alg. 2's criteria for the order-k components (hdmr_expansion_norms): the
+        cut-HDMR component integrals Qf (ncomp, m), eta per component (eq. 3.19; NaN
+        off order k), rho over all order-k components and over those with
+        eta > eps_eta (eq. 3.18)."""
+        nc, _ = self.sizes()
+        qf = np.zeros((nc, self.m))
+        eta = np.zeros(nc)
+        ra, rk = C.c_double(), C.c_double()
+        _check(load().hdmr_expansion_norms(self._h, int(k), float(eps_eta), _np_ptr(qf), _np_ptr(eta),
+                                           C.byref(ra), C.byref(rk), _stream_ptr(stream)), "hdmr_expansion_norms")
+        return qf, eta, ra.value, rk.value
+
     def nodal_info(self, form: int = FORM_SLICEFREE):
         """Tables of the nodal-slab kernel (planned if needed): (eligible, node rows,
         node rows read per uniformly distributed query)."""
@@ -518,15 +534,22 @@ def lu_solve(A_dev, r_dev, dx_dev, status_dev, stream=None):
 
 def irbc_table1(N: int, a_gamma: float = 0.25, beta: float = 0.99, alpha: float = 0.36,
                 delta: float = 0.01, sigma: float = 0.01, rho: float = 0.95, phi: float = 0.5):
-    """Table 1 calibration: A = (1 - beta (1 - delta)) / (alpha beta),
-    gamma_j = a + 0.75 (j - 1)/(N - 1) (a = 0.25 by default; a for N = 1),
-    tau_j = A^(1/gamma_j). Returns the keyword arguments of IRBC()."""
-    A = (1.0 - beta * (1.0 - delta)) / (alpha * beta)
-    j = np.arange(N, dtype=np.float64)
-    gamma = a_gamma + 0.75 * j / (N - 1) if N > 1 else np.full(1, a_gamma)
-    tau = A ** (1.0 / gamma)
-    return dict(N=N, beta=beta, alpha=alpha, delta=delta, sigma=sigma, rho=rho, phi=phi, A=A,
-                gamma=gamma, tau=tau)
+    """Table 1 calibration as libddsg derives it (irbc_create_table1): A, gamma_j
+    and tau_j read back from a model the library creates. Returns the keyword
+    arguments of IRBC()."""
+    lib = load()
+    h = _p()
+    _check(lib.irbc_create_table1(int(N), float(a_gamma), float(beta), float(alpha), float(delta),
+                                  float(sigma), float(rho), float(phi), C.byref(h)), "irbc_create_table1")
+    try:
+        prm = IrbcParams()
+        gamma = np.zeros(int(N))
+        tau = np.zeros(int(N))
+        _check(lib.irbc_get_params(h, C.byref(prm), _np_ptr(gamma), _np_ptr(tau)), "irbc_get_params")
+    finally:
+        lib.irbc_destroy(h)
+    return dict(N=int(N), beta=prm.beta, alpha=prm.alpha, delta=prm.delta, sigma=prm.sigma, rho=prm.rho,
+                phi=prm.phi, A=prm.A, gamma=gamma, tau=tau)
 
 
 class MLP:

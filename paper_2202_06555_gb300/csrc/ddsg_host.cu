@@ -945,6 +945,68 @@ extern "C" int hdmr_quadrature(hdmr_t *h, double *q_dev, ddsg_stream_t stream) {
     return DDSG_OK;
 }
 
+// Expansion and active-dimension criteria of Alg. 2 from the component
+// integrals (eq. 3.7): the cut-HDMR component integrals by inclusion-exclusion
+// over the subsets of each component (every subset must be a component),
+// eta_u (eq. 3.19) for the components of order k and rho (eq. 3.18).
+extern "C" int hdmr_expansion_norms(hdmr_t *h, int k, double eps_eta, double *qf_host, double *eta_host,
+                                    double *rho_all, double *rho_kept, ddsg_stream_t stream) {
+    if (!h || k < 1) return fail(DDSG_ERR_ARG, "hdmr_expansion_norms: bad argument");
+    if (!h->uploaded || !h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_expansion_norms: call hdmr_hierarchize first");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(DDSG_ERR_CUDA, "hdmr_expansion_norms: cannot select device");
+    const int C = (int)h->comps.size(), m = h->m;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    double *qd = nullptr;
+    ALLOC_TRY(&qd, sizeof(double) * (size_t)C * m, "hdmr_expansion_norms");
+    std::vector<double> Q((size_t)C * m);
+    cudaError_t e = launch_quadrature(h->dt, m, qd, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Q.data(), qd, sizeof(double) * Q.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(qd);
+    if (e != cudaSuccess) return fail(DDSG_ERR_CUDA, "hdmr_expansion_norms: %s", cudaGetErrorString(e));
+    // component index by dimension set
+    std::map<std::vector<int32_t>, int> index;
+    for (int c = 0; c < C; ++c) index[std::vector<int32_t>(h->comps[c].dims, h->comps[c].dims + h->comps[c].k)] = c;
+    std::vector<double> Qf((size_t)C * m, 0.0);
+    for (int c = 0; c < C; ++c) {
+        const int kc = h->comps[c].k;
+        for (uint32_t mask = 0; mask < (1u << kc); ++mask) {
+            std::vector<int32_t> v;
+            for (int j = 0; j < kc; ++j)
+                if (mask >> j & 1u) v.push_back(h->comps[c].dims[j]);
+            auto it = index.find(v);
+            if (it == index.end()) return fail(DDSG_ERR_ARG, "hdmr_expansion_norms: component %d lacks a subset component", c);
+            const double sign = ((kc - (int)v.size()) & 1) ? -1.0 : 1.0;
+            for (int o = 0; o < m; ++o) Qf[(size_t)c * m + o] += sign * Q[(size_t)it->second * m + o];
+        }
+    }
+    std::vector<double> lower(m, 0.0), num_all(m, 0.0), num_kept(m, 0.0);
+    for (int c = 0; c < C; ++c)
+        if (h->comps[c].k <= k - 1)
+            for (int o = 0; o < m; ++o) lower[o] += Qf[(size_t)c * m + o];
+    auto norm = [m](const double *v) {
+        double s = 0.0;
+        for (int o = 0; o < m; ++o) s += v[o] * v[o];
+        return sqrt(s);
+    };
+    const double nl = norm(lower.data());
+    for (int c = 0; c < C; ++c) {
+        double eta = NAN;
+        if (h->comps[c].k == k) {
+            eta = norm(&Qf[(size_t)c * m]) / nl;
+            for (int o = 0; o < m; ++o) num_all[o] += Qf[(size_t)c * m + o];
+            if (k < 2 || eta > eps_eta)
+                for (int o = 0; o < m; ++o) num_kept[o] += Qf[(size_t)c * m + o];
+        }
+        if (eta_host) eta_host[c] = eta;
+    }
+    if (qf_host) std::copy(Qf.begin(), Qf.end(), qf_host);
+    if (rho_all) *rho_all = norm(num_all.data()) / nl;
+    if (rho_kept) *rho_kept = norm(num_kept.data()) / nl;
+    return DDSG_OK;
+}
+
 extern "C" int hdmr_get_surpluses(const hdmr_t *h, double *alpha_host, ddsg_stream_t stream) {
     if (!h || !alpha_host) return fail(DDSG_ERR_ARG, "hdmr_get_surpluses: NULL argument");
     if (!h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_get_surpluses: not hierarchized");

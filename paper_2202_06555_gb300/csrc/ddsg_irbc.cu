@@ -1319,6 +1319,42 @@ extern "C" int irbc_create(const irbc_params_t *prm, const double *gamma_host, c
     return DDSG_OK;
 }
 
+// Table 1 of the paper: productivity A = (1 - beta (1 - delta)) / (alpha beta),
+// utility curvatures gamma_j = a + 0.75 (j - 1) / (N - 1) (a alone when N = 1,
+// j = 1..N) and weights tau_j = A^(1 / gamma_j), so that the steady state has
+// k_j = 1 for every country.
+extern "C" int irbc_create_table1(int N, double a_gamma, double beta, double alpha, double delta, double sigma,
+                                  double rho, double phi, irbc_t **out) {
+    if (!out) return set_error(DDSG_ERR_ARG, "irbc_create_table1: NULL argument");
+    if (N < 1 || N > 4096) return set_error(DDSG_ERR_ARG, "irbc_create_table1: N out of range");
+    if (!(beta > 0.0 && beta < 1.0) || !(alpha > 0.0 && alpha < 1.0) || !(delta >= 0.0 && delta < 1.0) ||
+        !(a_gamma > 0.0))
+        return set_error(DDSG_ERR_ARG, "irbc_create_table1: parameter out of range");
+    irbc_params_t prm;
+    prm.N = N;
+    prm.beta = beta;
+    prm.alpha = alpha;
+    prm.delta = delta;
+    prm.sigma = sigma;
+    prm.rho = rho;
+    prm.phi = phi;
+    prm.A = (1.0 - beta * (1.0 - delta)) / (alpha * beta);
+    std::vector<double> gamma(N), tau(N);
+    for (int j = 0; j < N; ++j) {
+        gamma[j] = N > 1 ? a_gamma + 0.75 * (double)j / (double)(N - 1) : a_gamma;
+        tau[j] = pow(prm.A, 1.0 / gamma[j]);
+    }
+    return irbc_create(&prm, gamma.data(), tau.data(), out);
+}
+
+extern "C" int irbc_get_params(const irbc_t *M, irbc_params_t *prm, double *gamma_host, double *tau_host) {
+    if (!M) return set_error(DDSG_ERR_ARG, "irbc_get_params: NULL model");
+    if (prm) *prm = M->p;
+    if (gamma_host) std::copy(M->gamma.begin(), M->gamma.end(), gamma_host);
+    if (tau_host) std::copy(M->tau.begin(), M->tau.end(), tau_host);
+    return DDSG_OK;
+}
+
 extern "C" int irbc_destroy(irbc_t *M) {
     if (!M) return DDSG_OK;
     cudaFree(M->gamma_d);

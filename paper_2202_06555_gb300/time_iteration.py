@@ -26,19 +26,6 @@ import numpy as np
 from . import F64, FORM_SLICEFREE, HDMR, NODES_DELTA
 
 
-def cut_quadratures(Q: np.ndarray, comps) -> np.ndarray:
-    """Integrals of the cut-HDMR component functions f_u (eq. ddsg2.2.6 on the
-    interpolants): Qf_u = sum over v subset of u of (-1)^{|u|-|v|} Q(I f(xbar \\ x_v))."""
-    pos = {u: c for c, u in enumerate(comps)}
-    Qf = np.zeros_like(Q)
-    for c, u in enumerate(comps):
-        for r in range(len(u) + 1):
-            sign = -1.0 if (len(u) - r) % 2 else 1.0
-            for v in itertools.combinations(u, r):
-                Qf[c] += sign * Q[pos[v]]
-    return Qf
-
-
 class StateSolver:
     """x -> solve{FOC(. | x, p)} at a batch of states (FP64 Newton on the GPU,
     started from the policy p itself)."""
@@ -141,8 +128,9 @@ def build_ddsg(solve, d: int, m: int, order: int, level: int, eps_gamma: float, 
             h.add_regular(list(u), 2)
             comps.append(u)
         vals = _adaptive(h, known, solve, anchor, eps_gamma, level, strict)
-        Qf = cut_quadratures(h.quadrature().cpu().numpy(), comps)
-        lower = np.sum([Qf[c] for c, u in enumerate(comps) if len(u) <= k - 1], axis=0)
+        # eq. 3.19 per order-k component and eq. 3.18 over the kept ones, from the
+        # component integrals (eq. 3.7), computed by libddsg
+        _, eta_c, _, rho = h.expansion_norms(k, eps_eta)
         keep = []
         for c, u in enumerate(comps):
             if u not in grids:
@@ -151,7 +139,7 @@ def build_ddsg(solve, d: int, m: int, order: int, level: int, eps_gamma: float, 
             if len(u) != k:
                 continue
             if k >= 2:
-                eta = float(np.linalg.norm(Qf[c]) / np.linalg.norm(lower))
+                eta = float(eta_c[c])
                 info["eta"][u] = eta
                 if not eta > eps_eta:
                     rejected.append(u)
@@ -159,9 +147,7 @@ def build_ddsg(solve, d: int, m: int, order: int, level: int, eps_gamma: float, 
                     continue
             keep.append(c)
         accepted += [comps[c] for c in keep]
-        rho = float(np.linalg.norm(np.sum([Qf[c] for c in keep], axis=0) if keep else np.zeros(m)) /
-                    np.linalg.norm(lower))
-        info["rho"].append(rho)
+        info["rho"].append(float(rho))
         h.close()
         if rho < eps_rho:
             break

@@ -127,6 +127,20 @@ def test_table1_helper_matches_oracle():
         assert np.allclose(t["tau"], I.tau, rtol=1e-14)
 
 
+def test_irbc_create_table1_validates():
+    """The Table 1 constructor refuses out-of-range calibrations before anything runs."""
+    lib = G.load()
+    h = C.c_void_p()
+    ok = (3, 0.25, 0.99, 0.36, 0.01, 0.01, 0.95, 0.5)
+    assert lib.irbc_create_table1(*ok, C.byref(h)) == 0
+    assert lib.irbc_destroy(h) == 0
+    for bad in ((0,) + ok[1:], (3, 0.0) + ok[2:], (3, 0.25, 1.0) + ok[3:], (3, 0.25, 0.99, 0.0) + ok[4:],
+                (3, 0.25, 0.99, 0.36, 1.0) + ok[5:]):
+        assert lib.irbc_create_table1(*bad, C.byref(h)) == -1, bad
+    t = G.irbc_table1(1)
+    assert t["gamma"].tolist() == [0.25] and abs(t["tau"][0] - t["A"] ** 4) <= 1e-15 * t["A"] ** 4
+
+
 def test_irbc_create_validates():
     lib = G.load()
     h = C.c_void_p()

@@ -40,6 +40,43 @@ def test_gpu_quadrature_matches_oracle(G):
     assert np.allclose(q, Q, rtol=1e-13, atol=1e-15)
 
 
+@pytest.mark.parametrize("d,order", [(4, 2), (5, 3)])
+def test_expansion_norms_match_oracle(G, d, order):
+    """hdmr_expansion_norms (the cut-HDMR component integrals by inclusion-exclusion,
+    eta per component, eq. 3.19, and rho, eq. 3.18) against the oracle's
+    expansion_rho / active_eta on an adaptive expansion of the kinked family."""
+    m = 3
+    c = synth.family_coeffs(synth.BASE_SEED + 62 + d, m, d)
+    fn = lambda dims, X: synth.family_cut(c, dims, X)
+    ref = O.OracleDDSG(d, m)
+    h = G.HDMR(d, m, order)
+    comps = O.full_order_components(d, order)
+    for u in comps:
+        ref.add_regular(u, 2)
+        h.add_regular(list(u), 2)
+    ref.build_adaptive(fn, 1e-3, 6)
+    G.build_adaptive(h, fn, 1e-3, 6)
+    Qf_ref = ref.cut_component_quadratures()
+    for k in range(1, order + 1):
+        qf, eta, rho_all, rho_kept = h.expansion_norms(k, eps_eta=-1.0)
+        assert np.allclose(qf, Qf_ref, rtol=1e-12, atol=1e-15)
+        assert abs(rho_all - ref.expansion_rho(k)) <= 1e-12 * max(1.0, ref.expansion_rho(k))
+        assert rho_kept == rho_all
+        for ci, u in enumerate(comps):
+            if len(u) == k:
+                assert abs(eta[ci] - ref.active_eta(u)) <= 1e-12 * max(1.0, ref.active_eta(u)), u
+            else:
+                assert np.isnan(eta[ci])
+    # a threshold between the order-2 etas: rho over the components above it only
+    qf, eta, _, _ = h.expansion_norms(2)
+    thr = float(np.nanmedian(eta))
+    _, _, _, rho_kept = h.expansion_norms(2, eps_eta=thr)
+    lower = qf[[ci for ci, u in enumerate(comps) if len(u) <= 1]].sum(0)
+    kept = qf[[ci for ci, u in enumerate(comps) if len(u) == 2 and eta[ci] > thr]].sum(0)
+    assert abs(rho_kept - np.linalg.norm(kept) / np.linalg.norm(lower)) <= 1e-12
+    h.close()
+
+
 def test_eta_rho_closed_forms_on_gpu(G):
     from paper_2202_06555_gb300.time_iteration import build_ddsg
     d, m = 3, 2
