@@ -167,12 +167,20 @@ def eval_traffic(workload, schedule, n):
     return None
 
 
-def make_queries(w, rank=0):
-    seed = synth.BASE_SEED + w["wid"] + 7919 * rank
+def make_queries(w, rank=0, world=1):
+    """This rank's queries: its contiguous slice (shard.query_slice) of one seeded
+    batch of world x Q queries (weak scaling: Q per rank; rank 0 of 1 gets the
+    whole single-GPU batch)."""
+    from paper_2202_06555_gb300.shard import query_slice
+    seed = synth.BASE_SEED + w["wid"]
     if w["queries"] == "monomial":
         N = w["d"] // 2
-        return synth.monomial_shaped_queries(seed, w["Q"] // (2 * (N + 1)), N)
-    return synth.uniform_queries(seed, w["Q"], w["d"])
+        per = 2 * (N + 1)
+        ns = w["Q"] // per
+        lo, hi = query_slice(ns * world, rank, world)
+        return synth.monomial_shaped_queries(seed, ns * world, N)[lo * per:hi * per]
+    lo, hi = query_slice(w["Q"] * world, rank, world)
+    return synth.uniform_queries_rows(seed, lo, hi, w["d"])
 
 
 def value_fn(w):
@@ -1021,7 +1029,7 @@ def main():
     t_build = time.perf_counter() - t0
     ncomp, npts = h.sizes()
 
-    X = make_queries(w, rank)
+    X = make_queries(w, rank, world)
     n = X.shape[0]
     x = torch.from_numpy(X).cuda()
     y = torch.empty((n, w["m"]), dtype=torch.float64, device="cuda")

@@ -24,6 +24,7 @@ import time
 import numpy as np
 
 from . import F64, FORM_SLICEFREE, HDMR, NODES_DELTA
+from .shard import allgather_rows, component_partition
 
 
 class StateSolver:
@@ -59,13 +60,47 @@ class StateSolver:
         return z.cpu().numpy()
 
 
-def _adaptive(h: HDMR, known, solve, anchor, eps_gamma, level, strict=False, max_sweeps=64):
+def _rank(group):
+    if group is None:
+        return 0
+    import torch.distributed as dist
+    return dist.get_rank(group)
+
+
+def _solve_partitioned(solve, need, m, group):
+    """Values at the new points of every component, the components split over the
+    ranks of `group` by cost (new points x outputs; shard.component_partition,
+    the same on every rank without communication). Each rank solves its
+    components' points, then the value rows are all-gathered (shard.allgather_rows,
+    Alg. 2's synchronize), so every rank returns the whole batch."""
+    import torch.distributed as dist
+    world, rank = dist.get_world_size(group), dist.get_rank(group)
+    sizes = [X.shape[0] for _, X in need]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    parts = component_partition([n * m for n in sizes], world)
+    mine = parts[rank]
+    if mine:
+        sol_mine = solve(np.concatenate([need[i][1] for i in mine]))
+        ids = np.concatenate([np.arange(offs[i], offs[i + 1]) for i in mine])
+    else:
+        sol_mine = np.zeros((0, m))
+        ids = np.zeros(0, np.int64)
+    return allgather_rows(sol_mine, ids, int(offs[-1]), group)
+
+
+def _adaptive(h: HDMR, known, solve, anchor, eps_gamma, level, strict=False, max_sweeps=64, group=None):
     """Refine / hierarchize sweeps (eq. 3.8) until no point is added; the values
-    of all new points of all components are solved in one batch per sweep.
+    of all new points of all components are solved in one batch per sweep (split
+    over the ranks of `group` by component when it has more than one rank; each
+    rank then hierarchizes the whole, identical table).
     known: values of the leading components (in order), or None."""
     import torch
     ncomp, _ = h.sizes()
     vals = list(known) + [None] * (ncomp - len(known))
+    multi = False
+    if group is not None:
+        import torch.distributed as dist
+        multi = dist.get_world_size(group) > 1
     for _ in range(max_sweeps):
         need = []
         for c in range(ncomp):
@@ -78,7 +113,10 @@ def _adaptive(h: HDMR, known, solve, anchor, eps_gamma, level, strict=False, max
                     X[:, list(dims)] = xs
                 need.append((c, X))
         if need:
-            sol = solve(np.concatenate([X for _, X in need]))
+            if multi:
+                sol = _solve_partitioned(solve, need, h.m, group)
+            else:
+                sol = solve(np.concatenate([X for _, X in need]))
             o = 0
             for c, X in need:
                 part = sol[o:o + X.shape[0]]
@@ -91,7 +129,7 @@ def _adaptive(h: HDMR, known, solve, anchor, eps_gamma, level, strict=False, max
 
 
 def build_ddsg(solve, d: int, m: int, order: int, level: int, eps_gamma: float, eps_eta: float,
-               eps_rho: float, lo, hi, candidates=None, strict=False):
+               eps_rho: float, lo, hi, candidates=None, strict=False, group=None):
     """Alg. 2: the adaptive DDSG expansion of the map `solve` (states -> values).
 
     Order by order k = 1..order: the candidate components of order k that hold
@@ -100,6 +138,9 @@ def build_ddsg(solve, d: int, m: int, order: int, level: int, eps_gamma: float, 
     (eq. 3.19), otherwise rejected with all its supersets; after the order,
     rho (eq. 3.18) < eps_rho stops the expansion. candidates(k) optionally
     restricts the order-k index sets (default: all k-subsets of the d dims).
+    With a torch.distributed `group` of several ranks, the values at new grid
+    points are solved component-partitioned over the ranks and all-gathered
+    (every rank builds the same expansion).
     Returns the handle holding the accepted components and an info dict."""
     lo = np.asarray(lo, np.float64)
     hi = np.asarray(hi, np.float64)
@@ -127,7 +168,7 @@ def build_ddsg(solve, d: int, m: int, order: int, level: int, eps_gamma: float, 
         for u in cand:
             h.add_regular(list(u), 2)
             comps.append(u)
-        vals = _adaptive(h, known, solve, anchor, eps_gamma, level, strict)
+        vals = _adaptive(h, known, solve, anchor, eps_gamma, level, strict, group=group)
         # eq. 3.19 per order-k component and eq. 3.18 over the kept ones, from the
         # component integrals (eq. 3.7), computed by libddsg
         _, eta_c, _, rho = h.expansion_norms(k, eps_eta)
@@ -183,7 +224,8 @@ def euler_errors(model, policy: HDMR, states: np.ndarray, precision=F64, form=FO
 def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps_gamma: float,
                    eps_eta: float, eps_rho: float, lo, hi, test_states: np.ndarray, tol_euler=0.0,
                    candidates=None, precision=F64, form=FORM_SLICEFREE, newton_tol=1e-10, max_it=30,
-                   node_mode=NODES_DELTA, tol_change=0.0, checkpoint=None, start_step=0, history0=None):
+                   node_mode=NODES_DELTA, tol_change=0.0, checkpoint=None, start_step=0, history0=None,
+                   group=None):
     """Alg. 1: p <- build_ddsg(x -> solve{FOC(. | x, p)}) until the mean Euler
     error at test_states is below tol_euler, the largest policy change at the
     test states is below tol_change, or `steps` steps are done. With a
@@ -201,7 +243,8 @@ def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps
     for step in range(start_step, start_step + steps):
         t_step = time.perf_counter()
         solve = StateSolver(model, policy, precision, form, newton_tol, max_it, node_mode)
-        new, info = build_ddsg(solve, d, m, order, level, eps_gamma, eps_eta, eps_rho, lo, hi, candidates)
+        new, info = build_ddsg(solve, d, m, order, level, eps_gamma, eps_eta, eps_rho, lo, hi, candidates,
+                               group=group)
         e = euler_errors(model, new, test_states, precision, form, node_mode)
         y0 = torch.empty((sd.shape[0], m), dtype=torch.float64, device="cuda")
         y1 = torch.empty_like(y0)
@@ -218,7 +261,7 @@ def time_iteration(model, policy0: HDMR, steps: int, order: int, level: int, eps
                         "euler_error_max": float(np.max(e)),
                         "policy_change_max": float((y1 - y0).abs().max().item()),
                         "seconds": time.perf_counter() - t_step})
-        if checkpoint:
+        if checkpoint and _rank(group) == 0:     # one writer when the ranks share a file system
             save_checkpoint(checkpoint, new, step + 1, history)
         if policy is not policy0:
             policy.close()

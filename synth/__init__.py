@@ -117,6 +117,12 @@ def uniform_queries(seed: int, n: int, d: int) -> np.ndarray:
     return uniform_matrix(seed + 2000, n, d)
 
 
+def uniform_queries_rows(seed: int, lo: int, hi: int, d: int) -> np.ndarray:
+    """Rows lo..hi-1 of uniform_queries(seed, n, d) for any n >= hi, drawn directly
+    from their place in the stream (no prefix is generated)."""
+    return uniform(seed + 2000, (hi - lo) * d, offset=lo * d).reshape(hi - lo, d)
+
+
 def monomial_shaped_queries(seed: int, n_states: int, n_countries: int, s: float = 0.01):
     """States U[0,1]^(2N) (first N coordinates: productivity block, last N:
     capital block), each expanded into 2(N+1) shifted copies: copy +-i moves

@@ -108,3 +108,45 @@ def test_two_gloo_ranks_shard_and_gather(tmp_path):
         assert np.array_equal(r[k]["A"], A)
         assert float(r[k]["t"]) == 2.0
     assert int(r[0]["n_mine"]) > 0 and int(r[1]["n_mine"]) > 0
+
+
+def _solve_worker(rank, world, port, out_dir):
+    from paper_2202_06555_gb300.time_iteration import _solve_partitioned
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        m = 3
+        need = [(c, synth.uniform_matrix(70 + c, n, 5)) for c, n in enumerate([4, 0, 9, 1, 6, 2, 2])]
+        calls = []
+
+        def solve(X):
+            calls.append(X.shape[0])
+            return np.stack([X.sum(1), X[:, 0] * X[:, 1], np.sin(X[:, 2])], 1)
+        sol = _solve_partitioned(solve, need, m, dist.group.WORLD)
+        np.savez(os.path.join(out_dir, f"s{rank}.npz"), sol=sol, solved=np.array(sum(calls)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_partitioned_node_solves_equal_one_batch(tmp_path):
+    """The time iteration's component-partitioned solve: each rank solves the
+    new points of its share of the components (by cost), the rows are
+    all-gathered, and every rank returns the single-process batch exactly."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_solve_worker, args=(r, 2, port, str(tmp_path))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    assert all(p.exitcode == 0 for p in procs)
+    need = [(c, synth.uniform_matrix(70 + c, n, 5)) for c, n in enumerate([4, 0, 9, 1, 6, 2, 2])]
+    X = np.concatenate([x for _, x in need])
+    want = np.stack([X.sum(1), X[:, 0] * X[:, 1], np.sin(X[:, 2])], 1)
+    r = [np.load(tmp_path / f"s{k}.npz") for k in range(2)]
+    for k in range(2):
+        assert np.array_equal(r[k]["sol"], want)
+    assert int(r[0]["solved"]) + int(r[1]["solved"]) == X.shape[0]
+    assert int(r[0]["solved"]) > 0 and int(r[1]["solved"]) > 0
