@@ -71,7 +71,7 @@ WORKLOADS = {
 }
 
 KERNEL_NAMES = ["tile", "per-tuple", "tma-staged tile", "tma-staged, 2 warp groups", "tma-staged, 3 warp groups",
-                "nodal-slab, tma-staged"]
+                "nodal-slab, tma-staged", "nodal-slab, tma-staged, Kahan totals in tensor memory"]
 
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 schedulers x 32), for the nominal figure only
 
@@ -1133,7 +1133,7 @@ def main():
     l1 = None
     if prec == G.F32C:
         wclk = n_sm * (sm_mhz or 2070.0) * 1e6
-        if tuned[0] == 5:
+        if tuned[0] in (5, 6):
             _, nrows, rows_q = h.nodal_info(form)
             rs = (w["m"] + 31) // 32 * 32 if w["m"] > 16 else (w["m"] + 3) // 4 * 4
             floor_ms = (n / 32.0) * rows_q * rs / wclk * 1e3

@@ -1190,7 +1190,7 @@ extern "C" int hdmr_eval(hdmr_t *h, int64_t n, const double *x_dev, double *y_de
     DeviceGuard g(h->device);
     if (!g.ok) return fail(DDSG_ERR_CUDA, "hdmr_eval: cannot select device");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (h->cfg[precision][form].kernel == KERNEL_NODAL && !h->capturing) {
+    if (kernel_is_nodal(h->cfg[precision][form].kernel) && !h->capturing) {
         if (int rc0 = ensure_nodal(h, form, st)) return rc0;
     }
     if (!eval_kernel_eligible(h->dt, h->cfg[precision][form].kernel, precision, form))
@@ -1243,7 +1243,7 @@ extern "C" int hdmr_eval_graph(hdmr_t *h, int64_t n, const double *x_dev, double
     if (!h->uploaded || !h->have_alpha) return fail(DDSG_ERR_STATE, "hdmr_eval_graph: call hdmr_hierarchize first");
     DeviceGuard g(h->device);
     if (!g.ok) return fail(DDSG_ERR_CUDA, "hdmr_eval_graph: cannot select device");
-    if (h->cfg[precision][form].kernel == KERNEL_NODAL) {   // any allocation happens before the capture
+    if (kernel_is_nodal(h->cfg[precision][form].kernel)) {   // any allocation happens before the capture
         if (int rc0 = ensure_nodal(h, form, reinterpret_cast<cudaStream_t>(stream))) return rc0;
     }
     if (!eval_kernel_eligible(h->dt, h->cfg[precision][form].kernel, precision, form))
@@ -1356,7 +1356,7 @@ extern "C" int hdmr_set_eval_config(hdmr_t *h, int precision, int form, int kern
     if (!h) return fail(DDSG_ERR_ARG, "hdmr_set_eval_config: NULL handle");
     if (precision < 0 || precision > 1 || form < 0 || form > 1 || kernel < 0 || kernel >= NKERNELS)
         return fail(DDSG_ERR_ARG, "hdmr_set_eval_config: bad precision/form/kernel");
-    if (kernel == KERNEL_NODAL && h->uploaded && h->device >= 0) {
+    if (kernel_is_nodal(kernel) && h->uploaded && h->device >= 0) {
         DeviceGuard g(h->device);
         if (int rc0 = ensure_nodal(h, form, nullptr)) return rc0;
         if (h->have_alpha && cudaDeviceSynchronize() != cudaSuccess) {
@@ -1411,7 +1411,7 @@ extern "C" int hdmr_autotune(hdmr_t *h, int64_t n, const double *x_dev, double *
     EvalConfig best;
     double best_t = 1e300;
     for (int kernel = 0; kernel < NKERNELS; ++kernel) {
-        if (kernel == KERNEL_NODAL) {
+        if (kernel_is_nodal(kernel)) {
             const int rc0 = ensure_nodal(h, form, st);
             if (rc0) { h->prof = prof; return rc0; }
         }
@@ -1551,7 +1551,7 @@ int handle_eval_view(hdmr_t *h, int precision, int form, HandleView *v) {
         // tables of the nodal kernel not built yet (this view allocates nothing):
         // the default schedule for this call, the choice kept; any other
         // ineligible choice is dropped, as hdmr_eval does
-        if (!(want.kernel == KERNEL_NODAL && !h->dt.nod[form].tried)) h->cfg[precision][form] = EvalConfig();
+        if (!(kernel_is_nodal(want.kernel) && !h->dt.nod[form].tried)) h->cfg[precision][form] = EvalConfig();
         v->cfg = EvalConfig();
     }
     v->withhold_from = h->fi_withhold;

@@ -306,8 +306,10 @@ struct EvalConfig {
     int mc = 0;               // outputs per thread and pass (0 = heuristic)
 };
 
-constexpr int NKERNELS = 6;
+constexpr int NKERNELS = 7;
 constexpr int KERNEL_NODAL = 5;               // the staged nodal-slab kernel
+constexpr int KERNEL_NODAL_TMEM = 6;          // the same, Kahan totals in tensor memory (FP32C)
+inline bool kernel_is_nodal(int k) { return k == KERNEL_NODAL || k == KERNEL_NODAL_TMEM; }
 constexpr int64_t TMA_STAGE_MAX = 84 * 1024;  // largest per-component surplus block staged by TMA
 constexpr int TMA_TUP_MAX = 128;              // most level tuples of one component the staged kernel holds
 
@@ -358,6 +360,7 @@ cudaError_t launch_nodalize(const DevNodal &nd, const double *alpha64, int mp64,
 bool nodal_eligible(const DevTables &t, int precision, int form);
 struct EvalParams;
 cudaError_t launch_eval_nodal(const EvalParams &p, int precision, int mc, cudaStream_t st);
+cudaError_t launch_eval_nodal_tmem(const EvalParams &p, cudaStream_t st);
 
 cudaError_t launch_quadrature(const DevTables &t, int m, double *Q, cudaStream_t st);
 cudaError_t launch_hierarchize(const DevTables &t, int m, const double *values,

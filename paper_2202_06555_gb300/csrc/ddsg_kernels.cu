@@ -453,6 +453,8 @@ static int tma_qb(int kernel) {
 bool eval_kernel_eligible(const DevTables &t, int kernel, int precision, int form) {
     if (kernel == 0 || kernel == 1) return true;
     if (kernel == KERNEL_NODAL) return nodal_eligible(t, precision, form);
+    if (kernel == KERNEL_NODAL_TMEM)
+        return precision == DDSG_F32C && nodal_eligible(t, precision, form) && t.nod[form].rs32 % 32 == 0;
     if (kernel < 2 || kernel > 4) return false;
     if (!t.tile_ok) return false;   // the staged kernel handles only k <= 2, levels <= LT
     if (t.max_tuples > TMA_TUP_MAX) return false;
@@ -971,6 +973,11 @@ int eval_mc_candidates(int precision, int kernel, int *out, int cap) {
         for (int i = 0; i < 3 && i < cap; ++i) out[i] = src[i];
         return 3 < cap ? 3 : cap;
     }
+    if (kernel == KERNEL_NODAL_TMEM) {   // FP32C only: 32-output windows
+        if (cap < 1) return 0;
+        out[0] = 32;
+        return 1;
+    }
     const int *src = kernel == 4 ? (f64 ? MC_F64_GR3 : MC_F32_GR3)
                      : kernel == 3 ? (f64 ? MC_F64_GR2 : MC_F32_GR2) : (f64 ? MC_F64 : MC_F32);
     const int n = kernel == 4 ? 2 : (kernel == 3 ? 3 : 6);
@@ -1028,10 +1035,13 @@ cudaError_t launch_eval(const EvalArgs &a, cudaStream_t st) {
     p.issue_end = a.withhold_from < 0 ? INT_MAX : a.withhold_from;
     const bool hc = a.hash != nullptr || a.count != nullptr;
     EvalConfig cfg = a.cfg;
-    if (cfg.kernel == KERNEL_NODAL) {
+    if (kernel_is_nodal(cfg.kernel)) {
         // the nodal form has no per-point active set: hash / count requests
         // run the level-tuple tile kernel
-        if (!hc) return launch_eval_nodal(p, a.precision, cfg.mc > 0 ? cfg.mc : (a.precision == DDSG_F64 ? 8 : 32), st);
+        if (!hc) {
+            if (cfg.kernel == KERNEL_NODAL_TMEM && a.precision == DDSG_F32C) return launch_eval_nodal_tmem(p, st);
+            return launch_eval_nodal(p, a.precision, cfg.mc > 0 ? cfg.mc : (a.precision == DDSG_F64 ? 8 : 32), st);
+        }
         cfg = EvalConfig();
     }
     const int mc = cfg.mc > 0 ? cfg.mc : default_mc(a.precision, a.m);

@@ -867,6 +867,267 @@ __global__ void __launch_bounds__(NodShape<GR>::NT, 1) eval_nodal_f32x2_kernel(c
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same kernel with the Kahan totals in tensor memory (kernel 6). Between
+// folds a thread keeps only its 32-output partial in registers; the totals s
+// and compensations c (64 FP32 per thread) live in tensor memory, which this
+// path otherwise leaves unused. Each warp owns 64 columns of its lane quarter
+// (lanes 32 (w mod 4) ..): 16 warps x 64 columns = 256 columns per block. A
+// fold reads 8 outputs' (s, c) at a time (tcgen05.ld 32x32b.x8), updates them
+// and writes them back (tcgen05.st), so it holds 16 more registers, not 64.
+// Fewer registers allow 256 queries per block in 16 warps per SM.
+// ---------------------------------------------------------------------------
+
+constexpr int kTmQB = 256;                 // queries per block
+constexpr int kTmNT = 2 * kTmQB;           // two output windows
+constexpr uint32_t kTmCols = 256;          // tensor-memory columns per block
+
+__device__ __forceinline__ void tm_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tm_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t u2pack(uint32_t a, uint32_t b) { return (uint64_t)a | ((uint64_t)b << 32); }
+
+__global__ void __launch_bounds__(kTmNT, 1) eval_nodal_tmem_kernel(const EvalParams p, int buf_bytes, int nbuf) {
+    constexpr int QW = kTmQB / 32;
+    constexpr int kWarps = kTmNT / 32;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + TMA_NBUF_MAX;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 96);
+    unsigned char *bufbase = smem + 128;
+
+    const DevNodal &N = p.t.nod[p.form];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int grp = warp / QW;
+    const int qw = warp - grp * QW;
+    const int qi = qw * 32 + lane;
+    const int64_t q = (int64_t)blockIdx.x * kTmQB + qi;
+    const int64_t qc = q < p.n ? q : p.n - 1;
+    const bool valid = q < p.n;
+    const bool bad = !valid || p.flags[q] != 0;
+    const bool paper = p.form == DDSG_FORM_PAPER;
+    const int m = p.m;
+    const int rs = N.rs32;
+    const int m0 = (blockIdx.y * 2 + grp) * 32;
+    const bool wact = m0 < rs;
+    const int nproc = N.n;
+    const int meta_bytes = N.meta_bytes;
+    const int l8 = lane & 7;
+
+    auto issue = [&](int j, int4 rec) {
+        if (j >= p.issue_end) return;
+        const int b = j % nbuf;
+        const uint32_t nmeta = (uint32_t)rec.y & 0xffffu;
+        const uint32_t mbytes = (nmeta * 8u + 15u) & ~15u;
+        const uint32_t rbytes = (uint32_t)rec.w * (uint32_t)rs * 4u;
+        if (!DDSG_CK(mbytes <= (uint32_t)meta_bytes && (int64_t)meta_bytes + rbytes <= (int64_t)buf_bytes &&
+                         rec.z >= 0 && (int64_t)rec.z + rec.w <= N.rows,
+                     CK_STAGE))
+            return;
+        unsigned char *dst = bufbase + (size_t)b * buf_bytes;
+        mbar_expect_tx(&full[b], mbytes + rbytes);
+        tma_bulk_g2s(dst, N.meta + rec.x, mbytes, &full[b]);
+        if (rbytes) tma_bulk_g2s(dst + meta_bytes, N.v32 + (int64_t)rec.z * rs, rbytes, &full[b]);
+    };
+
+    if (tid == 0) {
+        for (int b = 0; b < nbuf; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], kWarps);
+        }
+        mbar_fence_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(kTmCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // this warp's 64 columns of its lane quarter: s in [0, 32), c in [32, 64)
+    const uint32_t tbase = *tslot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
+    {
+        const uint32_t z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) tm_st8(tbase + 8 * k, z);
+        tm_wait_st();
+    }
+    int nissued = 0;
+    int4 rec_next = make_int4(0, 0, 0, 0);
+    if (tid == 0) {
+        if (nproc > 0) issue(0, N.rec[0]);
+        if (nproc > 1) issue(1, N.rec[1]);
+        nissued = nproc < 2 ? nproc : 2;
+        if (nproc > 2) rec_next = N.rec[2];
+    }
+
+    uint64_t acc[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc[u] = 0ull;
+    // Kahan fold of the partial into the totals in tensor memory, 8 outputs at a time
+    auto fold = [&]() {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t sv[8], cv[8];
+            tm_ld8(tbase + 8 * k, sv);
+            tm_ld8(tbase + 32 + 8 * k, cv);
+            tm_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t s2 = u2pack(sv[2 * u], sv[2 * u + 1]);
+                const uint64_t c2 = u2pack(cv[2 * u], cv[2 * u + 1]);
+                const uint64_t yk = f2_sub(acc[4 * k + u], c2);
+                const uint64_t tk = f2_add(s2, yk);
+                const uint64_t cn = f2_sub(f2_sub(tk, s2), yk);
+                sv[2 * u] = (uint32_t)tk;
+                sv[2 * u + 1] = (uint32_t)(tk >> 32);
+                cv[2 * u] = (uint32_t)cn;
+                cv[2 * u + 1] = (uint32_t)(cn >> 32);
+                acc[4 * k + u] = 0ull;
+            }
+            tm_st8(tbase + 8 * k, sv);
+            tm_st8(tbase + 32 + 8 * k, cv);
+        }
+        tm_wait_st();
+    };
+    bool failed = false;
+    int pfail = 0;
+    auto coord = [&](uint32_t dim) -> uint64_t {
+        if (dim == kNone) return 0ull;
+        return DDSG_CK(dim < (uint32_t)p.d, CK_DIM) ? p.X[(int64_t)dim * p.n + qc] : 0ull;
+    };
+    int4 rc = nproc > 0 ? N.rec[0] : make_int4(0, 0, 0, 0);
+    int4 r2c = nproc > 0 ? N.rec2[0] : make_int4(0, 0, 0, 0);
+    int4 r2n = nproc > 1 ? N.rec2[1] : make_int4(0, 0, 0, 0);
+    uint64_t Xn = coord((uint32_t)r2c.y & 0xffffu), Xs = coord((uint32_t)r2c.y >> 16);
+    int b = 0;
+    uint32_t ph = 0;
+    for (int i = 0; i < nproc; ++i) {
+        int4 rcn = make_int4(0, 0, 0, 0), r2nn = make_int4(0, 0, 0, 0);
+        uint64_t Xnn = 0, Xsn = 0;
+        if (i + 1 < nproc) {
+            rcn = N.rec[i + 1];
+            Xnn = coord((uint32_t)r2n.y & 0xffffu);
+            Xsn = coord((uint32_t)r2n.y >> 16);
+        }
+        if (i + 2 < nproc) r2nn = N.rec2[i + 2];
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[b], ph));
+        if (!ok || pfail) {
+            failed = true;
+            if (lane == 0 && p.err) atomicAdd(p.err, 1ull);
+            break;
+        }
+        const unsigned char *buf = bufbase + (size_t)b * buf_bytes;
+        const int2 *meta = reinterpret_cast<const int2 *>(buf);
+        const unsigned char *srow = buf + meta_bytes + (size_t)m0 * 4;
+        const int nslab = rc.y >> 16;
+        const int nmeta = rc.y & 0xffff;
+        const int nrows = rc.w;
+        const float wb = paper ? (float)r2c.z : 1.0f;
+        const uint32_t xs31 = (uint32_t)(Xs >> 31), xn31 = (uint32_t)(Xn >> 31);
+        const int rstride = rs * 4;
+        if (wact && nslab > 0) {
+            NodProbe pr = nodal_probe(meta, 0, nmeta, nrows, Xs, xs31, Xn, xn31, bad, wb);
+            for (int sl = 0; sl < nslab; ++sl) {
+                NodProbe nx;
+                if (sl + 1 < nslab) nx = nodal_probe(meta, sl + 1, nmeta, nrows, Xs, xs31, Xn, xn31, bad, wb);
+                if (__any_sync(0xffffffffu, pr.act)) {
+                    const unsigned char *R0 = srow + (size_t)pr.r0 * rstride;
+                    const uint64_t w0 = f2_pack(pr.w0, pr.w0), w1 = f2_pack(pr.w1, pr.w1);
+#pragma unroll
+                    for (int s = 0; s < 8; ++s) {
+                        const int off = (s ^ l8) << 4;
+                        const ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(R0 + off);
+                        const ulonglong2 a1 = *reinterpret_cast<const ulonglong2 *>(R0 + rstride + off);
+                        acc[2 * s] = f2_fma(w1, a1.x, f2_fma(w0, a0.x, acc[2 * s]));
+                        acc[2 * s + 1] = f2_fma(w1, a1.y, f2_fma(w0, a0.y, acc[2 * s + 1]));
+                    }
+                }
+                pr = nx;
+            }
+        }
+        if ((i & 1) || i + 1 == nproc) fold();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[b]);
+        int pf = 0;
+        if (tid == 0 && i + 2 < nproc) {
+            const int j = i + 2;
+            if (j >= nbuf && !mbar_wait_bounded(&empty[j % nbuf], (uint32_t)(((j - nbuf) / nbuf) & 1))) {
+                pf = 1;
+            } else {
+                fence_proxy_async_smem();
+                issue(j, rec_next);
+                nissued = j + 1;
+                if (j + 1 < nproc) rec_next = N.rec[j + 1];
+            }
+        }
+        pfail = __shfl_sync(0xffffffffu, pf, 0);
+        rc = rcn;
+        r2c = r2n;
+        r2n = r2nn;
+        Xn = Xnn;
+        Xs = Xsn;
+        if (++b == nbuf) {
+            b = 0;
+            ph ^= 1u;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int j = nissued > nbuf ? nissued - nbuf : 0; j < nissued; ++j)
+            if (j < p.issue_end) mbar_wait_bounded(&full[j % nbuf], (uint32_t)((j / nbuf) & 1));
+    }
+    // totals out of tensor memory (every lane of the warp takes part in the loads)
+    const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t sv[8], cv[8];
+        tm_ld8(tbase + 8 * k, sv);
+        tm_ld8(tbase + 32 + 8 * k, cv);
+        tm_wait_ld();
+        if (valid && wact) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int s = 2 * k + (u >> 1);           // 16-byte chunk slot of these two outputs
+                const int o = m0 + ((s ^ l8) << 2) + 2 * (u & 1);
+                const double v0 = (double)__uint_as_float(sv[2 * u]) - (double)__uint_as_float(cv[2 * u]);
+                const double v1 = (double)__uint_as_float(sv[2 * u + 1]) - (double)__uint_as_float(cv[2 * u + 1]);
+                if (o < m) p.y[q * m + o] = (bad || failed) ? nanv : v0;
+                if (o + 1 < m) p.y[q * m + o + 1] = (bad || failed) ? nanv : v1;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(kTmCols) : "memory");
+}
+
+static cudaError_t launch_nodal_tmem(const EvalParams &p, cudaStream_t st) {
+    const DevNodal &N = p.t.nod[p.form];
+    const int buf = (int)((N.stage_bytes[DDSG_F32C] + 127) & ~127ll);
+    const int nbuf = 128 + 3 * (int64_t)buf <= kSmemLimit ? 3 : 2;
+    const int smem = 128 + nbuf * buf;
+    dim3 grid((unsigned)((p.n + kTmQB - 1) / kTmQB), (unsigned)((N.rs32 + 63) / 64));
+    cudaError_t e = cudaFuncSetAttribute(eval_nodal_tmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    eval_nodal_tmem_kernel<<<grid, kTmNT, smem, st>>>(p, buf, nbuf);
+    return cudaGetLastError();
+}
+
 bool nodal_eligible(const DevTables &t, int precision, int form) {
     const DevNodal &N = t.nod[form];
     if (!N.ok || !N.vals) return false;
@@ -903,6 +1164,8 @@ static cudaError_t launch_nodal_f32x2(const EvalParams &p, cudaStream_t st) {
     eval_nodal_f32x2_kernel<GR><<<grid, NT, smem, st>>>(p, buf, nbuf);
     return cudaGetLastError();
 }
+
+cudaError_t launch_eval_nodal_tmem(const EvalParams &p, cudaStream_t st) { return launch_nodal_tmem(p, st); }
 
 cudaError_t launch_eval_nodal(const EvalParams &p, int precision, int mc, cudaStream_t st) {
     const DevNodal &N = p.t.nod[p.form];

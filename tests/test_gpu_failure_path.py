@@ -36,6 +36,42 @@ def G():
 
 
 @pytest.fixture(scope="module")
+def pair_wide(G):
+    d, m = 6, 20      # 20 outputs: the 32-output FP32 window of kernel 6
+    c = synth.family_coeffs(synth.BASE_SEED + 84, m, d)
+    fn = lambda dims, X: synth.family_cut(c, dims, X)
+    return build_pair(G, d, m, O.full_order_components(d, 2), fn, eps=1e-3, level=7)
+
+
+def test_tmem_kernel_withheld_copies_time_out_and_recover(G, pair_wide):
+    """Kernel 6 (Kahan totals in tensor memory): waits on withheld copies run out,
+    every output is NaN, one timeout per warp, the tensor memory is freed (the
+    next launches allocate it again) and the next evaluation is bit-identical."""
+    ref, h = pair_wide
+    m, form, prec = ref.m, 1, 1
+    n = 256 + 41
+    X = synth.uniform_queries(95, n, ref.d)
+    x = torch.from_numpy(X).cuda()
+    saved = h.eval_config(prec, form)
+    h.set_eval_config(prec, form, 6, 32)
+    h.stats(reset=True)
+    want = _eval(h, x, m, prec, form)
+    assert h.stats(reset=True)["wait_timeouts"] == 0
+    r = ref.eval(X, form=form, want=("y", "S"))
+    assert (np.abs(want - r["y"]) / np.maximum(np.abs(r["y"]), r["S"])).max() <= TOL[prec]
+    h.set_fault_injection(2)
+    y = _eval(h, x, m, prec, form)
+    st = h.stats(reset=True)
+    assert np.isnan(y).all()
+    assert st["wait_timeouts"] == 2 * 512 // 32        # two blocks of 16 warps
+    h.set_fault_injection(-1)
+    for _ in range(3):
+        assert np.array_equal(_eval(h, x, m, prec, form), want)
+    assert h.stats(reset=True)["wait_timeouts"] == 0
+    h.set_eval_config(prec, form, *saved)
+
+
+@pytest.fixture(scope="module")
 def pair(G):
     d, m = 6, 5
     c = synth.family_coeffs(synth.BASE_SEED + 83, m, d)
