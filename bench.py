@@ -132,12 +132,17 @@ def comp_list(w):
 # DRAM traffic of the evaluation kernel from one ncu capture per schedule, per
 # query; scaled to a full launch by the query count (the tables stream through
 # L2 once per wave of resident blocks, so traffic grows with the queries).
+#   (6, 32): profiles/eval_nodal_tmem_d100_ncu_full.md -- the nodal-slab kernel with
+#            its Kahan totals in tensor memory, d=100 tables, 38912 queries (one wave
+#            of 152 blocks of 256 queries);
 #   (5, 32): profiles/eval_nodal_d100_ncu_full.md -- the nodal-slab kernel, d=100
 #            tables, 29184 queries (one wave of 152 blocks of 192 queries);
 #   (3, 28): profiles/eval_tma_d100_ncu_full.md -- the two-group level-tuple
 #            TMA kernel at 28 outputs per group, same tables and queries.
 # Valid only for the kernel sources each was taken on (checked by hash).
 EVAL_TRAFFIC = [
+    {"workload": "d100", "schedule": (6, 32), "dram_bytes_per_query": (364539392 + 4058368) / 38912,
+     "sha1": {"ddsg_nodal.cu": "8dbf881b99e0515bb9fe4bb8be984e9d8d943fb9", "ddsg_eval.cuh": "a190d34e3b3fe0a7095a2f5ca6734106056dd7c9", "ddsg_internal.h": "103a72ef0530989e3daa14bf03b10b6c7a671e96", "ddsg_tma.cuh": "3d90c7da8651e19c5d8c36464fa0ee4bdc3e1dbd"}},
     {"workload": "d100", "schedule": (5, 32), "dram_bytes_per_query": (355433472 + 4008448) / 29184,
      "sha1": {"ddsg_nodal.cu": "c3418abccc98544024d6121b90a3260f2c5968df",
               "ddsg_eval.cuh": "a190d34e3b3fe0a7095a2f5ca6734106056dd7c9",
