@@ -166,23 +166,31 @@ __global__ void __launch_bounds__(RES_THREADS) irbc_residual_kernel(IrbcDev P, i
                      mb2 = e3[2] * cA + ((1.0 - P.delta) - hphi);
         const double db0 = e3[0] * cA * (P.alpha - 1.0), db1 = e3[1] * cA * (P.alpha - 1.0),
                      db2 = e3[2] * cA * (P.alpha - 1.0);
-        double Es = 0.0, Ms = 0.0, S1s = 0.0, SMs = 0.0, Ds = 0.0;
+        // M_q = hphi r^2 + mb_v and d/dk'_j [lambda' M_q] = (db_v - 2 hphi r^2) lambda' / k'_j with
+        // r = k''_j / k'_j and v the node's a'_j value, so every node sum follows from
+        // A1 = sum lambda' k'', A2 = sum lambda' k''^2, K2 = sum k''^2 and the sums of
+        // lambda' per value (value 1: the nodes 2j and 2N, value 2: 2j+1 and 2N+1,
+        // value 0: the others): four FP64 operations per node instead of ten.
+        double A1 = 0.0, A2 = 0.0, K2 = 0.0, Lall = 0.0, Ms = 0.0;
 #pragma unroll 4
         for (int q = 0; q < nq; ++q) {
-            const int vv = node_variant(q, j, N);
             const double kpp = ys[(int64_t)q * m + j];
             const double lamp = ys[(int64_t)q * m + L];
-            const double r = kpp * ikp;
-            const double hr = hphi * r;
-            const double Mq = fma(hr, r, vv == 0 ? mb0 : (vv == 1 ? mb1 : mb2));
-            Es = fma(lamp, Mq, Es);
+            const double t = lamp * kpp;
+            A1 += t;
+            A2 = fma(t, kpp, A2);
+            Lall += lamp;
+            if (jac) K2 = fma(kpp, kpp, K2);
             if (P.irr) Ms += ys[(int64_t)q * m + N + j];
-            if (jac) {
-                S1s = fma(lamp, r, S1s);
-                SMs += Mq;
-                Ds = fma(lamp, fma(-2.0 * hr, r, vv == 0 ? db0 : (vv == 1 ? db1 : db2)), Ds);
-            }
         }
+        const double L1 = ys[(int64_t)(2 * j) * m + L] + ys[(int64_t)(2 * N) * m + L];
+        const double L2 = ys[(int64_t)(2 * j + 1) * m + L] + ys[(int64_t)(2 * N + 1) * m + L];
+        const double L0 = Lall - L1 - L2;
+        const double ikp2 = ikp * ikp;
+        const double Es = fma(hphi * ikp2, A2, fma(mb0, L0, fma(mb1, L1, mb2 * L2)));
+        const double S1s = ikp * A1;
+        const double SMs = fma(hphi * ikp2, K2, fma(mb0, (double)(nq - 4), 2.0 * (mb1 + mb2)));
+        const double Ds = fma(-2.0 * hphi * ikp2, A2, fma(db0, L0, fma(db1, L1, db2 * L2)));
         // E = sum_q w lambda' M_q (- (1 - delta) w mu'_j when irreversible);
         // S1 = sum_q w lambda' phi (g2 + 1) / k'_j, SM = sum_q w M_q,
         // Dd = d/dk'_j of sum_q w lambda' M_q at fixed next-period policy
