@@ -146,6 +146,25 @@ __global__ void __launch_bounds__(RES_THREADS) irbc_residual_kernel(IrbcDev P, i
     const double w = 1.0 / (double)nq;
     const double *ys = y + sl * nq * (int64_t)m;
     double res = 0.0, ysum = 0.0, emax = 0.0, dlam = 0.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // sum over the nodes of lambda', shared by every country: once per state
+    // (threads over the nodes, then the warps' partials in warp order)
+    __shared__ double red[4][RES_THREADS / 32];
+    __shared__ double lsum_sh;
+    {
+        double ls = 0.0;
+        for (int q = threadIdx.x; q < nq; q += blockDim.x) ls += ys[(int64_t)q * m + L];
+        for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
+        if (lane == 0) red[0][warp] = ls;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int wq = 0; wq < (int)(blockDim.x >> 5); ++wq) t += red[0][wq];
+            lsum_sh = t;
+        }
+        __syncthreads();
+    }
+    const double Lall = lsum_sh;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         double e3[3];
         next_a3(P, a[j], e3[0], e3[1], e3[2]);
@@ -170,8 +189,9 @@ __global__ void __launch_bounds__(RES_THREADS) irbc_residual_kernel(IrbcDev P, i
         // r = k''_j / k'_j and v the node's a'_j value, so every node sum follows from
         // A1 = sum lambda' k'', A2 = sum lambda' k''^2, K2 = sum k''^2 and the sums of
         // lambda' per value (value 1: the nodes 2j and 2N, value 2: 2j+1 and 2N+1,
-        // value 0: the others): four FP64 operations per node instead of ten.
-        double A1 = 0.0, A2 = 0.0, K2 = 0.0, Lall = 0.0, Ms = 0.0;
+        // value 0: the others; their total Lall is the state's): three FP64
+        // operations per node (four with the Jacobian) instead of ten.
+        double A1 = 0.0, A2 = 0.0, K2 = 0.0, Ms = 0.0;
 #pragma unroll 4
         for (int q = 0; q < nq; ++q) {
             const double kpp = ys[(int64_t)q * m + j];
@@ -179,7 +199,6 @@ __global__ void __launch_bounds__(RES_THREADS) irbc_residual_kernel(IrbcDev P, i
             const double t = lamp * kpp;
             A1 += t;
             A2 = fma(t, kpp, A2);
-            Lall += lamp;
             if (jac) K2 = fma(kpp, kpp, K2);
             if (P.irr) Ms += ys[(int64_t)q * m + N + j];
         }
@@ -234,14 +253,12 @@ __global__ void __launch_bounds__(RES_THREADS) irbc_residual_kernel(IrbcDev P, i
     }
     // block reductions (sum / max) in a fixed order: warp butterflies, then the
     // warps' partials in warp order (any block size that is a multiple of 32)
-    __shared__ double red[4][RES_THREADS / 32];
     for (int o = 16; o > 0; o >>= 1) {
         res += __shfl_xor_sync(0xffffffffu, res, o);
         ysum += __shfl_xor_sync(0xffffffffu, ysum, o);
         emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
         dlam += __shfl_xor_sync(0xffffffffu, dlam, o);
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
         red[0][warp] = res;
         red[1][warp] = ysum;
@@ -1003,172 +1020,261 @@ __global__ void irbc_queries3_kernel(IrbcDev P, int64_t ns, const double *__rest
     if ((threadIdx.x & 31) == 0 && clamps) atomicAdd(&stats[0], clamps);
 }
 
-// acc[o] += coef * s_c(x)[m0 + o] for one component c at coordinates Xd (one per
-// component dimension), the tuples [tb, te) (interior ones in the slice-free form).
-template <int PREC, int MC>
-__device__ __forceinline__ void comp_at(const DevTables &t, const DevComp &cd, int tb, double coef,
-                                        const uint64_t *Xd, int m0, int mv,
-                                        typename DeltaT<PREC>::W (&acc)[MC]) {
-    using W = typename DeltaT<PREC>::W;
-    const W *alpha = DeltaT<PREC>::alpha(t);
-    const int mp = DeltaT<PREC>::stride(t);
-    for (int ti = tb; ti < cd.tup_end; ++ti) {
-        const DevTup tu = t.tups[ti];
-        uint32_t off = 0;
-        double w = coef;
-        bool act = true;
-        for (int j = 0; j < cd.k; ++j) {
-            Basis1D o;
-            const int l = tu.lev[j];
-            if (!basis1d(Xd[j], l, o)) { act = false; break; }
-            off = off * (j == 1 ? tu.nc1 : ncells(l)) + o.cell;
-            w *= (double)o.N * ldexp(1.0, -o.e);
+// Node shortcut (one thread per (state, country i) for the term search, then
+// one warp per 32 such pairs for the sums). The policy at the two nodes that
+// shock country i (2i: +, 2i+1: -) is the no-shock policy plus the change of
+// every component holding a_i when a'_i moves to its shocked value; the pair
+// with i = 0 also copies the two global-shock rows. Writes the 2(N+1)-node
+// policy array y in the layout the residual and Jacobian kernels read.
+// Phase 1: each thread encodes a'_i's three values (no shock, +, -) and walks
+// the tuples of its components once, keeping the active (row, weight) term of
+// every value in shared memory (at most DLT_CAP per value; a pair with more
+// is flagged). Phase 2: the warp takes its 32 pairs in turn, lanes over the
+// outputs (o, o + 32, ...), and sums weight x surplus row over each value's
+// terms in (component, tuple) order, DLT_UNR terms' rows in flight at a time;
+// every surplus row is read and every policy row written coalesced. A
+// flagged pair is summed by a warp-wide walk of its tuples (lanes over the
+// tuples, active terms broadcast in the same order). Node rows =
+// no-shock + (sum_v - sum_0), each sum in W.
+constexpr int DLT_WARPS = 4;   // warps per block
+constexpr int DLT_CAP = 16;    // terms per (pair, value) kept in shared memory
+
+template <class W>
+struct DltTerms {   // one warp's term lists, lane (pair) fastest
+    int32_t row[3][DLT_CAP][32];
+    W w[3][DLT_CAP][32];
+};
+
+template <int PREC>
+constexpr int dlt_unroll() { return PREC == DDSG_F64 ? 2 : 4; }
+
+// Coordinates of component cd at state s with a'_i in Xd[ipos] = Xi0 (the
+// other a-dimensions at their no-shock values, k-dimensions at the guess).
+__device__ __forceinline__ int delta_coords(const IrbcDev &P, const DevComp &cd, int i, int64_t s,
+                                            const double *states, const double *guess, const double *lo,
+                                            const double *span, uint64_t Xi0, uint64_t *Xd, bool &bad) {
+    const int N = P.N, d = 2 * N, m = P.m;
+    unsigned long long cl = 0;
+    int ipos = 0;
+    for (int j = 0; j < cd.k; ++j) {
+        const int dj = cd.dims[j];
+        if (dj == i) {
+            ipos = j;
+            Xd[j] = Xi0;
+        } else if (dj < N) {
+            double f0, fp, fm;
+            next_a3(P, states[s * d + dj], f0, fp, fm);
+            Xd[j] = encode_coord(f0, lo[dj], span[dj], bad, cl);
+        } else {
+            Xd[j] = encode_coord(guess[s * m + dj - N], lo[dj], span[dj], bad, cl);
         }
-        if (!act) continue;
-        const int32_t row = tuple_row_at(tu, off, t.slots, t.S, cd.row_begin, cd.row_end);
-        if (row < 0) continue;
-        const W *r = alpha + (int64_t)row * mp + m0;
-        const W ww = (W)w;
-#pragma unroll
-        for (int o = 0; o < MC; ++o)
-            if (o < mv) acc[o] += ww * r[o];
     }
+    return ipos;
 }
 
-// One thread per (state, country i): the policy at the two nodes that shock
-// country i (2i: +, 2i+1: -) is the no-shock policy plus the change of every
-// component holding a_i when a'_i moves to its shocked value; the thread with
-// i = 0 also copies the two global-shock rows. Writes the 2(N+1)-node policy
-// array y in the layout the residual and Jacobian kernels read. For each value
-// of a'_i (no shock, +, -) the thread finds the active (row, weight) terms of
-// its components once, then sweeps the outputs in chunks of MC (when there are
-// more terms than the list holds it walks the tuples again for every chunk,
-// in the same order). The no-shock pass stores -sum into both node rows; the
-// + and - passes turn that into no-shock policy + (sum - no-shock sum).
-constexpr int DLT_MC = 32;   // outputs per chunk
+// (row, weight) of tuple tu at coordinates Xd; row -1 when inactive
+__device__ __forceinline__ int32_t delta_term(const DevTables &t, const DevComp &cd, const DevTup &tu,
+                                              const uint64_t *Xd, double coef, double &w) {
+    uint32_t off = 0;
+    w = coef;
+    for (int j = 0; j < cd.k; ++j) {
+        Basis1D o;
+        const int l = tu.lev[j];
+        if (!basis1d(Xd[j], l, o)) return -1;
+        off = off * (j == 1 ? tu.nc1 : ncells(l)) + o.cell;
+        w *= (double)o.N * ldexp(1.0, -o.e);
+    }
+    return tuple_row_at(tu, off, t.slots, t.S, cd.row_begin, cd.row_end);
+}
 
-template <int PREC, int MC>
-__global__ void __launch_bounds__(128) irbc_delta_kernel(IrbcDev P, int64_t s0, int64_t nsc, DevTables t,
-                                                         int form, const int32_t *__restrict__ aoff,
-                                                         const int32_t *__restrict__ acomp,
-                                                         const double *__restrict__ states,
-                                                         const double *__restrict__ guess,
-                                                         const double *__restrict__ lo,
-                                                         const double *__restrict__ span,
-                                                         const double *__restrict__ y3, double *__restrict__ y) {
+// Warp-wide walk for one pair whose terms did not fit: acc[v][c] += the sum for
+// value v at outputs m0 + lane + 32c. Returns false on a non-finite coordinate.
+template <int PREC, int OC>
+__device__ __forceinline__ bool delta_walk_warp(const IrbcDev &P, const DevTables &t, bool paper, const int32_t *aoff,
+                                const int32_t *acomp, const double *states, const double *guess,
+                                const double *lo, const double *span, int64_t s, int i, const uint64_t (&Xi)[3],
+                                int m0, int lane, typename DeltaT<PREC>::W (&acc)[3][OC]) {
     using W = typename DeltaT<PREC>::W;
     const W *alpha = DeltaT<PREC>::alpha(t);
     const int mp = DeltaT<PREC>::stride(t);
-    const int N = P.N, d = 2 * N, m = P.m, nq = 2 * (N + 1);
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nsc * N) return;
-    const int64_t sl = idx / N;
-    const int i = (int)(idx - sl * N);
-    const int64_t s = s0 + sl;
-    const bool paper = form == DDSG_FORM_PAPER;
-    bool bad = false;
-    unsigned long long cl = 0;
-    double e3[3];
-    next_a3(P, states[s * d + i], e3[0], e3[1], e3[2]);
-    uint64_t Xi[3];
-    for (int v = 0; v < 3; ++v) Xi[v] = encode_coord(e3[v], lo[i], span[i], bad, cl);
-    const double *yb = y3 + (sl * 3) * (int64_t)m;
-    double *yp = y + (sl * nq + 2 * i) * (int64_t)m;
-    double *ym = yp + m;
-    DTerm<W> terms[DT_CAP];
-    // coordinates of component cd with a'_i = value v (false: a non-finite one)
-    auto coords = [&](const DevComp &cd, int v, uint64_t *Xd) -> bool {
-        bool bd = false;
-        for (int j = 0; j < cd.k; ++j) {
-            const int dj = cd.dims[j];
-            if (dj == i) {
-                Xd[j] = Xi[v];
-            } else if (dj < N) {
-                double f0, fp, fm;
-                next_a3(P, states[s * d + dj], f0, fp, fm);
-                Xd[j] = encode_coord(f0, lo[dj], span[dj], bd, cl);
-            } else {
-                Xd[j] = encode_coord(guess[s * m + dj - N], lo[dj], span[dj], bd, cl);
-            }
-        }
-        return !bd;
-    };
-    for (int v = 0; v < 3; ++v) {
-        // the active terms of every component holding a_i at a'_i = value v
-        int nt = 0;
-        bool over = false;
-        for (int e = aoff[i]; e < aoff[i + 1] && !bad && !over; ++e) {
-            if (!comp_ok(t, acomp[e], d)) continue;
-            const DevComp &cd = t.comps[acomp[e]];
-            const double coef = paper ? cd.b : 1.0;
-            if (coef == 0.0) continue;
-            const int tb = paper ? cd.tup_begin : cd.tup_int;
-            uint64_t Xd[KMAX];
-            if (!coords(cd, v, Xd)) { bad = true; break; }
-            for (int ti = tb; ti < cd.tup_end; ++ti) {
+    const int m = P.m, d = 2 * P.N;
+    for (int e = aoff[i]; e < aoff[i + 1]; ++e) {
+        if (!comp_ok(t, acomp[e], d)) continue;
+        const DevComp &cd = t.comps[acomp[e]];
+        const double coef = paper ? cd.b : 1.0;
+        if (coef == 0.0) continue;
+        uint64_t Xd[KMAX];
+        bool bad = false;
+        const int ipos = delta_coords(P, cd, i, s, states, guess, lo, span, Xi[0], Xd, bad);
+        if (bad) return false;
+        const int tb = paper ? cd.tup_begin : cd.tup_int;
+        for (int t0 = tb; t0 < cd.tup_end; t0 += 32) {
+            const int ti = t0 + lane;
+            int32_t row[3] = {-1, -1, -1};
+            W wv[3] = {(W)0, (W)0, (W)0};
+            if (ti < cd.tup_end) {
                 const DevTup tu = t.tups[ti];
-                uint32_t off = 0;
-                double w = coef;
-                bool act = true;
-                for (int j = 0; j < cd.k; ++j) {
-                    Basis1D o;
-                    const int l = tu.lev[j];
-                    if (!basis1d(Xd[j], l, o)) { act = false; break; }
-                    off = off * (j == 1 ? tu.nc1 : ncells(l)) + o.cell;
-                    w *= (double)o.N * ldexp(1.0, -o.e);
-                }
-                if (!act) continue;
-                const int32_t row = tuple_row_at(tu, off, t.slots, t.S, cd.row_begin, cd.row_end);
-                if (row < 0) continue;
-                if (nt == DT_CAP) { over = true; break; }   // more terms than the list holds
-                terms[nt].row = row;
-                terms[nt].w = (W)w;
-                ++nt;
-            }
-        }
-        // outputs in chunks: sum of weight x surplus over the terms, in W
-        for (int m0 = 0; m0 < m; m0 += MC) {
-            const int mv = min(MC, m - m0);
-            W acc[MC];
 #pragma unroll
-            for (int o = 0; o < MC; ++o) acc[o] = (W)0;
-            if (!over) {
-                for (int q = 0; q < nt; ++q) {
-                    const W *r = alpha + (int64_t)terms[q].row * mp + m0;
-                    const W ww = terms[q].w;
-#pragma unroll
-                    for (int o = 0; o < MC; ++o)
-                        if (o < mv) acc[o] += ww * r[o];
-                }
-            } else {
-                for (int e = aoff[i]; e < aoff[i + 1] && !bad; ++e) {
-                    if (!comp_ok(t, acomp[e], d)) continue;
-                    const DevComp &cd = t.comps[acomp[e]];
-                    const double coef = paper ? cd.b : 1.0;
-                    if (coef == 0.0) continue;
-                    uint64_t Xd[KMAX];
-                    if (!coords(cd, v, Xd)) { bad = true; break; }
-                    comp_at<PREC, MC>(t, cd, paper ? cd.tup_begin : cd.tup_int, coef, Xd, m0, mv, acc);
+                for (int v = 0; v < 3; ++v) {
+                    Xd[ipos] = Xi[v];
+                    double w;
+                    row[v] = delta_term(t, cd, tu, Xd, coef, w);
+                    wv[v] = (W)w;
                 }
             }
 #pragma unroll
-            for (int o = 0; o < MC; ++o) {
-                if (o < mv) {
-                    if (v == 0) {
-                        yp[m0 + o] = -(double)acc[o];
-                        ym[m0 + o] = -(double)acc[o];
-                    } else {
-                        double *yo = v == 1 ? yp : ym;
-                        yo[m0 + o] = bad ? NAN : yb[m0 + o] + ((double)acc[o] + yo[m0 + o]);
+            for (int v = 0; v < 3; ++v) {
+                unsigned mask = __ballot_sync(0xffffffffu, row[v] >= 0);
+                while (mask) {
+                    const int src = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const int32_t r = __shfl_sync(0xffffffffu, row[v], src);
+                    const W ww = __shfl_sync(0xffffffffu, wv[v], src);
+                    const W *a = alpha + (int64_t)r * mp;
+#pragma unroll
+                    for (int c = 0; c < OC; ++c) {
+                        const int o = m0 + lane + 32 * c;
+                        if (o < m) acc[v][c] += ww * a[o];
                     }
                 }
             }
         }
     }
-    if (i == 0) {
-        for (int o = 0; o < m; ++o) {
-            y[(sl * nq + 2 * N) * (int64_t)m + o] = y3[(sl * 3 + 1) * (int64_t)m + o];
-            y[(sl * nq + 2 * N + 1) * (int64_t)m + o] = y3[(sl * 3 + 2) * (int64_t)m + o];
+    return true;
+}
+
+template <int PREC, int OC>
+__global__ void __launch_bounds__(32 * DLT_WARPS) irbc_delta_kernel(IrbcDev P, int64_t s0, int64_t nsc, DevTables t,
+                                                                    int form, const int32_t *__restrict__ aoff,
+                                                                    const int32_t *__restrict__ acomp,
+                                                                    const double *__restrict__ states,
+                                                                    const double *__restrict__ guess,
+                                                                    const double *__restrict__ lo,
+                                                                    const double *__restrict__ span,
+                                                                    const double *__restrict__ y3, double *__restrict__ y) {
+    using W = typename DeltaT<PREC>::W;
+    constexpr int UNR = dlt_unroll<PREC>();
+    const W *alpha = DeltaT<PREC>::alpha(t);
+    const int mp = DeltaT<PREC>::stride(t);
+    const int N = P.N, d = 2 * N, m = P.m, nq = 2 * (N + 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool paper = form == DDSG_FORM_PAPER;
+    extern __shared__ float4 dlt_raw[];
+    DltTerms<W> &T = reinterpret_cast<DltTerms<W> *>(dlt_raw)[warp];
+    const int64_t npairs = nsc * N;
+    const int64_t wbase = ((int64_t)blockIdx.x * DLT_WARPS + warp) * 32;
+    if (wbase >= npairs) return;   // whole warps leave together
+    // phase 1: this lane's pair
+    const int64_t pair = wbase + lane;
+    int64_t sl = 0;
+    int i = 0;
+    bool bad = false, over = false;
+    int cnt[3] = {0, 0, 0};
+    uint64_t Xi[3] = {0, 0, 0};
+    if (pair < npairs) {
+        sl = pair / N;
+        i = (int)(pair - sl * N);
+        const int64_t s = s0 + sl;
+        unsigned long long cl = 0;
+        double e3[3];
+        next_a3(P, states[s * d + i], e3[0], e3[1], e3[2]);
+        for (int v = 0; v < 3; ++v) Xi[v] = encode_coord(e3[v], lo[i], span[i], bad, cl);
+        for (int e = aoff[i]; e < aoff[i + 1] && !bad && !over; ++e) {
+            if (!comp_ok(t, acomp[e], d)) continue;
+            const DevComp &cd = t.comps[acomp[e]];
+            const double coef = paper ? cd.b : 1.0;
+            if (coef == 0.0) continue;
+            uint64_t Xd[KMAX];
+            const int ipos = delta_coords(P, cd, i, s, states, guess, lo, span, Xi[0], Xd, bad);
+            if (bad) break;
+            const int tb = paper ? cd.tup_begin : cd.tup_int;
+            for (int ti = tb; ti < cd.tup_end && !over; ++ti) {
+                const DevTup tu = t.tups[ti];
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    Xd[ipos] = Xi[v];
+                    double w;
+                    const int32_t r = delta_term(t, cd, tu, Xd, coef, w);
+                    if (r < 0) continue;
+                    if (cnt[v] == DLT_CAP) { over = true; break; }
+                    T.row[v][cnt[v]][lane] = r;
+                    T.w[v][cnt[v]][lane] = (W)w;
+                    ++cnt[v];
+                }
+            }
+        }
+    }
+    __syncwarp();
+    // phase 2: the warp's pairs in turn
+    const int np = npairs - wbase < 32 ? (int)(npairs - wbase) : 32;
+    for (int p = 0; p < np; ++p) {
+        const int64_t slp = __shfl_sync(0xffffffffu, sl, p);
+        const int ip = __shfl_sync(0xffffffffu, i, p);
+        const bool badp = __shfl_sync(0xffffffffu, (int)bad, p) != 0;
+        const bool overp = __shfl_sync(0xffffffffu, (int)over, p) != 0;
+        int cp[3];
+        uint64_t Xp[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            cp[v] = __shfl_sync(0xffffffffu, cnt[v], p);
+            Xp[v] = __shfl_sync(0xffffffffu, Xi[v], p);
+        }
+        const double *yb = y3 + (slp * 3) * (int64_t)m;
+        double *yp = y + (slp * nq + 2 * ip) * (int64_t)m;
+        double *ym = yp + m;
+        for (int m0 = 0; m0 < m; m0 += 32 * OC) {
+            W acc[3][OC];
+#pragma unroll
+            for (int v = 0; v < 3; ++v)
+#pragma unroll
+                for (int c = 0; c < OC; ++c) acc[v][c] = (W)0;
+            bool nan = badp;
+            if (!badp && overp) {
+                nan = !delta_walk_warp<PREC, OC>(P, t, paper, aoff, acomp, states, guess, lo, span, s0 + slp, ip, Xp,
+                                                 m0, lane, acc);
+            } else if (!badp) {
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    const int n = cp[v];
+                    for (int q = 0; q < n; q += UNR) {
+                        int32_t r[UNR];
+                        W ww[UNR], x[UNR][OC];
+#pragma unroll
+                        for (int k = 0; k < UNR; ++k) {
+                            const int qq = q + k < n ? q + k : q;
+                            r[k] = T.row[v][qq][p];
+                            ww[k] = T.w[v][qq][p];
+                        }
+#pragma unroll
+                        for (int k = 0; k < UNR; ++k)
+#pragma unroll
+                            for (int c = 0; c < OC; ++c) {
+                                const int o = m0 + lane + 32 * c;
+                                x[k][c] = (q + k < n && o < m) ? alpha[(int64_t)r[k] * mp + o] : (W)0;
+                            }
+#pragma unroll
+                        for (int k = 0; k < UNR; ++k)
+#pragma unroll
+                            for (int c = 0; c < OC; ++c)
+                                if (q + k < n && m0 + lane + 32 * c < m) acc[v][c] += ww[k] * x[k][c];
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < OC; ++c) {
+                const int o = m0 + lane + 32 * c;
+                if (o < m) {
+                    const double n0 = -(double)acc[0][c];
+                    yp[o] = nan ? NAN : yb[o] + ((double)acc[1][c] + n0);
+                    ym[o] = nan ? NAN : yb[o] + ((double)acc[2][c] + n0);
+                }
+            }
+        }
+        if (ip == 0) {
+            for (int o = lane; o < m; o += 32) {
+                y[(slp * nq + 2 * N) * (int64_t)m + o] = y3[(slp * 3 + 1) * (int64_t)m + o];
+                y[(slp * nq + 2 * N + 1) * (int64_t)m + o] = y3[(slp * 3 + 2) * (int64_t)m + o];
+            }
         }
     }
 }
@@ -1287,13 +1393,30 @@ int a_components(hdmr_t *h, int N, std::vector<int32_t> &off, std::vector<int32_
     return DDSG_OK;
 }
 
+template <int PREC, int OC>
+cudaError_t launch_delta_oc(const IrbcDev &P, int64_t s0, int64_t nsc, const DevTables &t, int form,
+                            const int32_t *aoff, const int32_t *acomp, const double *states, const double *guess,
+                            const double *lo, const double *span, const double *y3, double *y, cudaStream_t st) {
+    const size_t smem = sizeof(DltTerms<typename DeltaT<PREC>::W>) * DLT_WARPS;
+    cudaError_t e = cudaFuncSetAttribute(irbc_delta_kernel<PREC, OC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t warps = (nsc * P.N + 31) / 32;
+    irbc_delta_kernel<PREC, OC><<<(unsigned)((warps + DLT_WARPS - 1) / DLT_WARPS), 32 * DLT_WARPS, smem, st>>>(
+        P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, y);
+    return cudaGetLastError();
+}
+
+// outputs per lane per pass: the fewest of 2, 4, 6, 8 that cover m in one pass
 template <int PREC>
 cudaError_t launch_delta(const IrbcDev &P, int64_t s0, int64_t nsc, const DevTables &t, int form,
                          const int32_t *aoff, const int32_t *acomp, const double *states, const double *guess,
                          const double *lo, const double *span, const double *y3, double *y, cudaStream_t st) {
-    irbc_delta_kernel<PREC, DLT_MC><<<(unsigned)((nsc * P.N + 127) / 128), 128, 0, st>>>(
-        P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, y);
-    return cudaGetLastError();
+    const int need = (P.m + 31) / 32;
+    if (need <= 2) return launch_delta_oc<PREC, 2>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, y, st);
+    if (need <= 4) return launch_delta_oc<PREC, 4>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, y, st);
+    if (need <= 6) return launch_delta_oc<PREC, 6>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, y, st);
+    return launch_delta_oc<PREC, 8>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, y, st);
 }
 
 }  // namespace

@@ -146,8 +146,8 @@ def test_delta_nodes_newton_and_nonfinite_states(G):
 def test_delta_nodes_with_more_terms_than_the_list_holds(G):
     """Every pair at level 7 (N = 3): a_i is held by 6 components with up to
     7 + 5 x 28 tuples, more active terms per a'-value than the delta kernel's
-    term list, so it walks the tuples again per output chunk. Same results as
-    the all-node path and the oracle."""
+    shared term list holds, so the warp walks those pairs' tuples itself. Same
+    results as the all-node path and the oracle."""
     N, level = 3, 7
     I = O.IRBCOracle(N, sigma=0.01)
     lam = I.steady_lambda()
@@ -176,3 +176,36 @@ def test_delta_nodes_with_more_terms_than_the_list_holds(G):
         assert np.all(np.abs(r_d - r_a) <= (1e-13 if prec == 0 else 1e-6) * sc), (prec, np.max(np.abs(r_d - r_a) / sc))
         if prec == 0:
             assert np.all(np.abs(r_d - r_ref) <= 1e-11 * sc), np.max(np.abs(r_d - r_ref) / sc)
+
+
+@pytest.mark.parametrize("N", [80, 200, 300])
+def test_delta_nodes_wide_policies(G, N):
+    """Policies of N + 1 = 81, 201 and 301 outputs: the delta kernel's lanes
+    hold 4 and 8 outputs each, and at 301 outputs it takes two passes. States
+    not a multiple of the 32 pairs a warp sums. Delta against the all-node
+    path at the bars of the N = 150 case (the all-node path is pinned to the
+    oracle there; the F32C bar is twice the oracle one)."""
+    I = O.IRBCOracle(N, sigma=0.01)
+    lam = I.steady_lambda()
+    base = np.concatenate([np.ones(N), [lam]])
+    pert = synth.irbc_policy_perturbation(synth.BASE_SEED + 416, N)
+    fn = lambda dims, X: synth.irbc_policy_values(base, pert, dims, X)
+    d = 2 * N
+    h = G.HDMR(d, N + 1, 2, lo=np.full(d, 0.8), hi=np.full(d, 1.2))
+    comps = [()] + [(i,) for i in range(d)] + [(j, N + j) for j in range(N)]
+    for u in comps:
+        h.add_regular(list(u), 4)
+    vals = np.concatenate([fn(u, h.component_points(c)[2]) for c, u in enumerate(comps)])
+    h.hierarchize(torch.from_numpy(vals).cuda())
+    M = G.IRBC(N, I.p["beta"], I.p["alpha"], I.p["delta"], I.p["sigma"], I.p["rho"], I.p["phi"],
+               I.A, I.gamma, I.tau)
+    S, g = states_and_guess(N, 3, lam, synth.BASE_SEED + 417)
+    for form in (1, 0):
+        for prec in (0, 1):
+            r_d, _, _ = run(G, M, h, S, g, prec, form, G.NODES_DELTA)
+            r_a, _, _ = run(G, M, h, S, g, prec, form, G.NODES_ALL)
+            sc = scales(I, S, g, r_a)
+            assert np.all(np.isfinite(r_d))
+            # F32C: both paths within the oracle bar, so at most twice it apart
+            tol = 1e-13 if prec == 0 else 2 * (1e-6 if form == 1 else 1e-7 * float(np.sum(np.abs(h.b_coeffs()))))
+            assert np.all(np.abs(r_d - r_a) <= tol * sc), (form, prec, np.max(np.abs(r_d - r_a) / sc))
