@@ -21,11 +21,14 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include <algorithm>
 #include <string>
 #include <vector>
 
 #include "ddsg_alloc.h"
+#include "ddsg_eval.cuh"
 #include "ddsg_internal.h"
 #include "ddsg_tables.h"
 
@@ -38,6 +41,7 @@ struct IrbcDev {
     int m;      // policy outputs: N + 1 (k', lambda) or 2N + 1 (k', mu, lambda)
     int irr;    // irreversible investment (eq. modelkink1): mu_j and a complementarity row
     double beta, alpha, delta, sigma, rho, phi, A;
+    double shk_p, shk_m;   // exp(+sigma sqrt(N + 1)), exp(-sigma sqrt(N + 1))
     const double *gamma, *tau;
 };
 
@@ -58,13 +62,12 @@ __device__ __forceinline__ uint64_t encode_coord(double v, double lo, double spa
 }
 
 // Next-period productivity of country j at the three distinct node values:
-// no shock on j (e0), +sqrt(N+1) (ep), -sqrt(N+1) (em), as exp(rho ln a + sigma (e_j + e)).
+// no shock on j (e0), +sqrt(N+1) (ep), -sqrt(N+1) (em), i.e. exp(rho ln a + sigma (e_j + e))
+// taken as a^rho times the model's constant shock factor exp(sigma (e_j + e)).
 __device__ __forceinline__ void next_a3(const IrbcDev &P, double a, double &e0, double &ep, double &em) {
-    const double h = sqrt((double)(P.N + 1));
-    const double la = log(a);
-    e0 = exp(P.rho * la + P.sigma * (0.0 + 0.0));
-    ep = exp(P.rho * la + P.sigma * (h + 0.0));
-    em = exp(P.rho * la + P.sigma * (-h + 0.0));
+    e0 = exp(P.rho * log(a));
+    ep = e0 * P.shk_p;
+    em = e0 * P.shk_m;
 }
 
 // Which of the three values node q gives to country j (nodes 2i / 2i+1 shock
@@ -302,7 +305,8 @@ __device__ __forceinline__ double dhat(uint64_t X, int l, uint32_t &cell) {
 
 // Terms of d p(x)/d x_dpos for one component at coordinates Xd (one per
 // component dimension; position dpos is the differentiated one): appends
-// (device row, weight) pairs, the weight holding coef (b or 1) and 1/span.
+// (device row, weight) pairs, the weight holding coef (b or 1) and 1/span,
+// multiplied in W.
 // Returns the number of terms, or -1 if there were more than cap.
 // Surplus table and row stride of each evaluation precision: FP64 rows, or
 // the FP32 rows that F32C multiplies in FP32.
@@ -327,12 +331,12 @@ struct DTerm { int32_t row; W w; };
 
 template <class W>
 __device__ int comp_dterms(const DevTables &t, const DevComp &cd, int tb, int dpos, const uint64_t *Xd,
-                           double scale, DTerm<W> *out, int cap) {
+                           W scale, DTerm<W> *out, int cap) {
     int n = 0;
     for (int ti = tb; ti < cd.tup_end; ++ti) {
         const DevTup tu = t.tups[ti];
         uint32_t off = 0;
-        double wt = scale;
+        W wt = scale;
         bool act = true;
         for (int j = 0; j < cd.k; ++j) {
             const int l = tu.lev[j];
@@ -340,12 +344,12 @@ __device__ int comp_dterms(const DevTables &t, const DevComp &cd, int tb, int dp
                 uint32_t cell;
                 const double sl = dhat(Xd[j], l, cell);
                 if (sl == 0.0) { act = false; break; }
-                wt *= sl;
+                wt *= (W)sl;   // +-2^(l-1): exact
                 off = off * (j == 1 ? tu.nc1 : ncells(l)) + cell;
             } else {
                 Basis1D o;
                 if (!basis1d(Xd[j], l, o)) { act = false; break; }
-                wt *= (double)o.N * ldexp(1.0, -o.e);
+                wt *= basis_val<W>(o);
                 off = off * (j == 1 ? tu.nc1 : ncells(l)) + o.cell;
             }
         }
@@ -354,7 +358,7 @@ __device__ int comp_dterms(const DevTables &t, const DevComp &cd, int tb, int dp
         if (row < 0) continue;
         if (n == cap) return -1;
         out[n].row = row;
-        out[n].w = (W)wt;
+        out[n].w = wt;
         ++n;
     }
     return n;
@@ -489,7 +493,7 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
                 DTerm<W> loc[DT_CAP];
                 for (int v = 0; v < nv && !over; ++v) {
                     if (v > 0) Xd[apos] = encode_coord(ax[(3 + v) * N + ctry], lo[ctry], span[ctry], bad, cl);
-                    const int nt = comp_dterms(t, cd, tb, dpos, Xd, coef / span[dk], loc, DT_CAP);
+                    const int nt = comp_dterms<W>(t, cd, tb, dpos, Xd, (W)(coef / span[dk]), loc, DT_CAP);
                     if (nt < 0) { over = true; break; }
                     const int off = atomicAdd(&cursor, nt);
                     if (off + nt > pool_cap) { over = true; break; }
@@ -1035,7 +1039,8 @@ __global__ void irbc_queries3_kernel(IrbcDev P, int64_t ns, const double *__rest
 // every surplus row is read and every policy row written coalesced. A
 // flagged pair is summed by a warp-wide walk of its tuples (lanes over the
 // tuples, active terms broadcast in the same order). Node rows =
-// no-shock + (sum_v - sum_0), each sum in W.
+// no-shock + (sum_v - sum_0), the sums and their difference in W (FP64 is
+// GB300's slow unit: F32C leaves one conversion and one FP64 add per output).
 constexpr int DLT_WARPS = 4;   // warps per block
 constexpr int DLT_CAP = 16;    // terms per (pair, value) kept in shared memory
 
@@ -1072,9 +1077,12 @@ __device__ __forceinline__ int delta_coords(const IrbcDev &P, const DevComp &cd,
     return ipos;
 }
 
-// (row, weight) of tuple tu at coordinates Xd; row -1 when inactive
+// (row, weight) of tuple tu at coordinates Xd; row -1 when inactive. The
+// weight is coef times the hat values, in W (the hat values built from their
+// fixed-point bits as in the evaluation kernels: no FP64 work for W = float).
+template <class W>
 __device__ __forceinline__ int32_t delta_term(const DevTables &t, const DevComp &cd, const DevTup &tu,
-                                              const uint64_t *Xd, double coef, double &w) {
+                                              const uint64_t *Xd, W coef, W &w) {
     uint32_t off = 0;
     w = coef;
     for (int j = 0; j < cd.k; ++j) {
@@ -1082,7 +1090,7 @@ __device__ __forceinline__ int32_t delta_term(const DevTables &t, const DevComp 
         const int l = tu.lev[j];
         if (!basis1d(Xd[j], l, o)) return -1;
         off = off * (j == 1 ? tu.nc1 : ncells(l)) + o.cell;
-        w *= (double)o.N * ldexp(1.0, -o.e);
+        w *= basis_val<W>(o);
     }
     return tuple_row_at(tu, off, t.slots, t.S, cd.row_begin, cd.row_end);
 }
@@ -1117,9 +1125,7 @@ __device__ __forceinline__ bool delta_walk_warp(const IrbcDev &P, const DevTable
 #pragma unroll
                 for (int v = 0; v < 3; ++v) {
                     Xd[ipos] = Xi[v];
-                    double w;
-                    row[v] = delta_term(t, cd, tu, Xd, coef, w);
-                    wv[v] = (W)w;
+                    row[v] = delta_term<W>(t, cd, tu, Xd, (W)coef, wv[v]);
                 }
             }
 #pragma unroll
@@ -1193,12 +1199,12 @@ __global__ void __launch_bounds__(32 * DLT_WARPS) irbc_delta_kernel(IrbcDev P, i
 #pragma unroll
                 for (int v = 0; v < 3; ++v) {
                     Xd[ipos] = Xi[v];
-                    double w;
-                    const int32_t r = delta_term(t, cd, tu, Xd, coef, w);
+                    W w;
+                    const int32_t r = delta_term<W>(t, cd, tu, Xd, (W)coef, w);
                     if (r < 0) continue;
                     if (cnt[v] == DLT_CAP) { over = true; break; }
                     T.row[v][cnt[v]][lane] = r;
-                    T.w[v][cnt[v]][lane] = (W)w;
+                    T.w[v][cnt[v]][lane] = w;
                     ++cnt[v];
                 }
             }
@@ -1264,9 +1270,10 @@ __global__ void __launch_bounds__(32 * DLT_WARPS) irbc_delta_kernel(IrbcDev P, i
             for (int c = 0; c < OC; ++c) {
                 const int o = m0 + lane + 32 * c;
                 if (o < m) {
-                    const double n0 = -(double)acc[0][c];
-                    yp[o] = nan ? NAN : yb[o] + ((double)acc[1][c] + n0);
-                    ym[o] = nan ? NAN : yb[o] + ((double)acc[2][c] + n0);
+                    // the changes in W (F32C: one FP32 rounding each), added in FP64
+                    const W dp = acc[1][c] - acc[0][c], dm = acc[2][c] - acc[0][c];
+                    yp[o] = nan ? NAN : yb[o] + (double)dp;
+                    ym[o] = nan ? NAN : yb[o] + (double)dm;
                 }
             }
         }
@@ -1326,6 +1333,8 @@ IrbcDev dev_params(const irbc *M) {
     P.rho = M->p.rho;
     P.phi = M->p.phi;
     P.A = M->p.A;
+    P.shk_p = std::exp(M->p.sigma * std::sqrt((double)(M->p.N + 1)));
+    P.shk_m = std::exp(-M->p.sigma * std::sqrt((double)(M->p.N + 1)));
     P.gamma = M->gamma_d;
     P.tau = M->tau_d;
     return P;
