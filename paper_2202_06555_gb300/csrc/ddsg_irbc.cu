@@ -387,6 +387,25 @@ constexpr int DT_CAP = 48;
 constexpr int JAC_THREADS = 256;
 constexpr int JAC_KJ = 6;   // outputs per lane: N <= 32 * JAC_KJ = 192
 
+// A node policy value in W. For FP32 the conversion is done on the integer
+// units from the IEEE-754 fields (sign, exponent rebiased, significand cut to
+// 23 bits: rounding toward zero, within one FP32 ulp, which the Jacobian
+// tolerates); zeros, values outside FP32's normal range, infinities and NaN
+// take the hardware conversion. GB300's FP64 units (conversions included) are
+// its slow ones.
+template <class W>
+__device__ __forceinline__ W to_w(double x);
+template <>
+__device__ __forceinline__ double to_w<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_w<float>(double x) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff) - 1023 + 127;   // FP32 biased exponent
+    if (ex < 1 || ex > 254) return (float)x;
+    const uint32_t f = (uint32_t)(b >> 32) & 0x80000000u;
+    return __uint_as_float(f | ((uint32_t)ex << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
+}
+
 struct JGroup {
     int32_t i, ctry, nv, off[3], cnt[3];
     double dPN[3];
@@ -518,13 +537,14 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
     }
     __syncthreads();
     // phase 2: a warp per column i, lane outputs j = lane + 32 k; the node
-    // factors in W (FP32 in the F32C mode, like the derivative sums)
+    // factors and the column's sum over its groups in W (FP32 in the F32C
+    // mode, like the derivative sums)
     const W beta = (W)P.beta, phi = (W)P.phi, ww = (W)w, omd = (W)(1.0 - P.delta);
     for (int i = warp; i < N; i += JAC_THREADS / 32) {
         const int cs = colstate[i];
-        double acc[JAC_KJ];
+        W acc[JAC_KJ];
 #pragma unroll
-        for (int kk = 0; kk < JAC_KJ; ++kk) acc[kk] = 0.0;
+        for (int kk = 0; kk < JAC_KJ; ++kk) acc[kk] = (W)0;
         if (cs == 0) {
             for (int g = koff[i]; g < koff[i + 1]; ++g) {
                 const JGroup &gr = grp[g];
@@ -576,10 +596,10 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
                         W s1c[2], sMc[2];
                         for (int u = 0; u < 2; ++u) {
                             const int q = 2 * ctry + u;
-                            const W kpp = (W)ys[(int64_t)q * m + j];
-                            const W lamp = (W)ys[(int64_t)q * m + L];
+                            const W kpp = to_w<W>(ys[(int64_t)q * m + j]);
+                            const W lamp = to_w<W>(ys[(int64_t)q * m + L]);
                             const W g2 = kpp * ik - (W)1;
-                            const W ap = (W)ax[(j == ctry ? 4 + u : 3) * N + j];
+                            const W ap = to_w<W>(ax[(j == ctry ? 4 + u : 3) * N + j]);
                             s1c[u] = ww * lamp * phi * (g2 + (W)1) * ik;
                             sMc[u] = ww * (ap * cA + omd + (W)0.5 * phi * g2 * (g2 + (W)2));
                         }
@@ -594,14 +614,14 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
                                                : ww * ((W)(nq - 4) * dM0[kk] + (W)2 * dM1[kk] + (W)2 * dM2[kk]);
                         v0 += beta * omd * sumw;
                     }
-                    acc[kk] += (double)v0;
+                    acc[kk] += v0;
                 }
             }
         }
 #pragma unroll
         for (int kk = 0; kk < JAC_KJ; ++kk) {
             const int j = lane + 32 * kk;
-            if (j < N) J[(int64_t)j * m + i] = cs == 2 ? NAN : (j == i ? ax[2 * N + j] : 0.0) + acc[kk];
+            if (j < N) J[(int64_t)j * m + i] = cs == 2 ? NAN : (j == i ? ax[2 * N + j] : 0.0) + (double)acc[kk];
         }
     }
 }
