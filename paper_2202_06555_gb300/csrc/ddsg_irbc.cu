@@ -128,12 +128,23 @@ __global__ void irbc_queries_kernel(IrbcDev P, int64_t ns, const double *__restr
 // aux (per state, 7 x N): S1, SM, the diagonal part of d r_j / d k'_j, the three
 // a'_j values (no shock, +, -), k'_j^(alpha-1); the Jacobian kernel reads them.
 // Block: RES_THREADS at most (N rounded up to a warp), threads over countries j.
+// The next-period policy at the nodes comes as NodePolicy<DELTA, W>: all 2(N+1)
+// node rows (y), or with the node shortcut the no-shock and global-shock rows
+// (y3) plus each country node's change from the no-shock row (dY, in W).
 constexpr int RES_THREADS = 256;
 
+template <bool DELTA, class W>
+struct NodePolicy {
+    const double *y;    // all nodes: nq rows of m per state
+    const double *y3;   // shortcut: no shock, every country +, every country -
+    const W *dY;        // shortcut: 2N rows of m per state, node 2i + u (u = 0: +, 1: -)
+};
+
+template <bool DELTA, class W>
 __global__ void __launch_bounds__(RES_THREADS) irbc_residual_kernel(IrbcDev P, int64_t s0, int64_t nsc,
                                                             const double *__restrict__ states,
                                                             const double *__restrict__ guess,
-                                                            const double *__restrict__ y,
+                                                            const NodePolicy<DELTA, W> pol,
                                                             double *__restrict__ resid,
                                                             double *__restrict__ err,
                                                             double *__restrict__ jac,
@@ -147,22 +158,36 @@ __global__ void __launch_bounds__(RES_THREADS) irbc_residual_kernel(IrbcDev P, i
     const double *kp = guess + s * m;
     const double lam = guess[s * m + L];
     const double w = 1.0 / (double)nq;
-    const double *ys = y + sl * nq * (int64_t)m;
+    const double *ys = DELTA ? nullptr : pol.y + sl * nq * (int64_t)m;
+    const double *yb = DELTA ? pol.y3 + sl * 3 * (int64_t)m : nullptr;   // no shock
+    const double *ygp = yb ? yb + m : nullptr, *ygm = yb ? yb + 2 * m : nullptr;   // global +, -
+    const W *dY = DELTA ? pol.dY + sl * 2 * N * (int64_t)m : nullptr;
     double res = 0.0, ysum = 0.0, emax = 0.0, dlam = 0.0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // sum over the nodes of lambda', shared by every country: once per state
-    // (threads over the nodes, then the warps' partials in warp order)
+    // (threads over the nodes, then the warps' partials in warp order; with the
+    // shortcut the sum of the country nodes' changes, added to the FP64 terms)
     __shared__ double red[4][RES_THREADS / 32];
-    __shared__ double lsum_sh;
+    __shared__ double lsum_sh, dl_sh;
     {
         double ls = 0.0;
-        for (int q = threadIdx.x; q < nq; q += blockDim.x) ls += ys[(int64_t)q * m + L];
+        if constexpr (DELTA) {
+            W lw = (W)0;
+            for (int c = threadIdx.x; c < 2 * N; c += blockDim.x) lw += dY[(int64_t)c * m + L];
+            ls = (double)lw;
+        } else {
+            for (int q = threadIdx.x; q < nq; q += blockDim.x) ls += ys[(int64_t)q * m + L];
+        }
         for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
         if (lane == 0) red[0][warp] = ls;
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
             for (int wq = 0; wq < (int)(blockDim.x >> 5); ++wq) t += red[0][wq];
+            if constexpr (DELTA) {
+                dl_sh = t;   // sum of the country nodes' lambda' changes
+                t += (double)(2 * N) * yb[L] + ygp[L] + ygm[L];
+            }
             lsum_sh = t;
         }
         __syncthreads();
@@ -194,19 +219,50 @@ __global__ void __launch_bounds__(RES_THREADS) irbc_residual_kernel(IrbcDev P, i
         // lambda' per value (value 1: the nodes 2j and 2N, value 2: 2j+1 and 2N+1,
         // value 0: the others; their total Lall is the state's): three FP64
         // operations per node (four with the Jacobian) instead of ten.
-        double A1 = 0.0, A2 = 0.0, K2 = 0.0, Ms = 0.0;
+        double A1 = 0.0, A2 = 0.0, K2 = 0.0, Ms = 0.0, L1, L2;
+        if constexpr (DELTA) {
+            // country node c: k'' = kb + dk_c, lambda' = lb + dl_c. The sums of the
+            // changes run in W (FP32 with F32C), the no-shock and global terms in FP64:
+            //   A1 = 2N lb kb + lb S1 + kb Dl + P1 + globals,
+            //   A2 = 2N lb kb^2 + 2 lb kb S1 + lb S2 + kb^2 Dl + 2 kb P1 + P2 + globals,
+            //   K2 = 2N kb^2 + 2 kb S1 + S2 + globals,
+            // S1 = sum dk, S2 = sum dk^2, P1 = sum dl dk, P2 = sum dl dk^2, Dl = sum dl.
+            W s1 = (W)0, s2 = (W)0, p1 = (W)0, p2 = (W)0, sm = (W)0;
 #pragma unroll 4
-        for (int q = 0; q < nq; ++q) {
-            const double kpp = ys[(int64_t)q * m + j];
-            const double lamp = ys[(int64_t)q * m + L];
-            const double t = lamp * kpp;
-            A1 += t;
-            A2 = fma(t, kpp, A2);
-            if (jac) K2 = fma(kpp, kpp, K2);
-            if (P.irr) Ms += ys[(int64_t)q * m + N + j];
+            for (int c = 0; c < 2 * N; ++c) {
+                const W dk = dY[(int64_t)c * m + j];
+                const W dl = dY[(int64_t)c * m + L];
+                const W t = dl * dk;
+                s1 += dk;
+                p1 += t;
+                s2 = fma(dk, dk, s2);
+                p2 = fma(t, dk, p2);
+                if (P.irr) sm += dY[(int64_t)c * m + N + j];
+            }
+            const double kb = yb[j], lb = yb[L], n2 = (double)(2 * N);
+            const double S1 = (double)s1, S2 = (double)s2, P1 = (double)p1, P2 = (double)p2, Dl = dl_sh;
+            const double kp_ = ygp[j], km_ = ygm[j], lp_ = ygp[L], lm_ = ygm[L];
+            A1 = n2 * lb * kb + lb * S1 + kb * Dl + P1 + (lp_ * kp_ + lm_ * km_);
+            A2 = n2 * lb * kb * kb + 2.0 * lb * kb * S1 + lb * S2 + kb * kb * Dl + 2.0 * kb * P1 + P2 +
+                 (lp_ * kp_ * kp_ + lm_ * km_ * km_);
+            if (jac) K2 = n2 * kb * kb + 2.0 * kb * S1 + S2 + (kp_ * kp_ + km_ * km_);
+            if (P.irr) Ms = n2 * yb[N + j] + (double)sm + (ygp[N + j] + ygm[N + j]);
+            L1 = (lb + (double)dY[(int64_t)(2 * j) * m + L]) + lp_;
+            L2 = (lb + (double)dY[(int64_t)(2 * j + 1) * m + L]) + lm_;
+        } else {
+#pragma unroll 4
+            for (int q = 0; q < nq; ++q) {
+                const double kpp = ys[(int64_t)q * m + j];
+                const double lamp = ys[(int64_t)q * m + L];
+                const double t = lamp * kpp;
+                A1 += t;
+                A2 = fma(t, kpp, A2);
+                if (jac) K2 = fma(kpp, kpp, K2);
+                if (P.irr) Ms += ys[(int64_t)q * m + N + j];
+            }
+            L1 = ys[(int64_t)(2 * j) * m + L] + ys[(int64_t)(2 * N) * m + L];
+            L2 = ys[(int64_t)(2 * j + 1) * m + L] + ys[(int64_t)(2 * N + 1) * m + L];
         }
-        const double L1 = ys[(int64_t)(2 * j) * m + L] + ys[(int64_t)(2 * N) * m + L];
-        const double L2 = ys[(int64_t)(2 * j + 1) * m + L] + ys[(int64_t)(2 * N + 1) * m + L];
         const double L0 = Lall - L1 - L2;
         const double ikp2 = ikp * ikp;
         const double Es = fma(hphi * ikp2, A2, fma(mb0, L0, fma(mb1, L1, mb2 * L2)));
@@ -411,7 +467,7 @@ struct JGroup {
     double dPN[3];
 };
 
-template <int PREC>
+template <int PREC, bool DELTA>
 __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, int64_t s0, int64_t nsc,
                                                                    DevTables t, int form,
                                                                    const int32_t *__restrict__ koff,
@@ -419,7 +475,7 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
                                                                    const double *__restrict__ lo,
                                                                    const double *__restrict__ span,
                                                                    const double *__restrict__ guess,
-                                                                   const double *__restrict__ y,
+                                                                   const NodePolicy<DELTA, typename DeltaT<PREC>::W> pol,
                                                                    const double *__restrict__ aux,
                                                                    double *__restrict__ jac, int pool_cap) {
     using W = typename DeltaT<PREC>::W;
@@ -430,7 +486,18 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
     const bool paper = form == DDSG_FORM_PAPER;
     const double *kp = guess + s * m;
     const double *ax = aux + sl * 7 * (int64_t)N;
-    const double *ys = y + sl * nq * (int64_t)m;
+    // node q's policy at output o: stored, or (shortcut) no-shock + change / global rows
+    const double *ys = DELTA ? nullptr : pol.y + sl * nq * (int64_t)m;
+    const double *y3s = DELTA ? pol.y3 + sl * 3 * (int64_t)m : nullptr;
+    const W *dYs = DELTA ? pol.dY + sl * 2 * N * (int64_t)m : nullptr;
+    auto node64 = [&](int q, int o) -> double {   // global nodes (q >= 2N) or all-node mode
+        if constexpr (DELTA) return y3s[(int64_t)(q - 2 * N + 1) * m + o];
+        else return ys[(int64_t)q * m + o];
+    };
+    auto nodew = [&](int q, int o) -> W {         // country nodes, in W
+        if constexpr (DELTA) return to_w<W>(y3s[o]) + dYs[(int64_t)q * m + o];
+        else return to_w<W>(ys[(int64_t)q * m + o]);
+    };
     double *J = jac + s * (int64_t)m * m;
     const double w = 1.0 / (double)nq;
     const W *alpha = DeltaT<PREC>::alpha(t);
@@ -462,7 +529,7 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
         ocA[j] = (W)cA;
         for (int u = 0; u < 2; ++u) {
             const int q = 2 * N + u;   // global node: every a' shocked, variant 1 (+) or 2 (-)
-            const double kpp = ys[(int64_t)q * m + j], lamp = ys[(int64_t)q * m + L];
+            const double kpp = node64(q, j), lamp = node64(q, L);
             const double g2 = kpp * ik - 1.0;
             const double s1 = w * lamp * P.phi * (g2 + 1.0) * ik;
             const double sM = w * (ax[(4 + u) * N + j] * cA + (1.0 - P.delta) + 0.5 * P.phi * g2 * (g2 + 2.0));
@@ -596,8 +663,8 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
                         W s1c[2], sMc[2];
                         for (int u = 0; u < 2; ++u) {
                             const int q = 2 * ctry + u;
-                            const W kpp = to_w<W>(ys[(int64_t)q * m + j]);
-                            const W lamp = to_w<W>(ys[(int64_t)q * m + L]);
+                            const W kpp = nodew(q, j);
+                            const W lamp = nodew(q, L);
                             const W g2 = kpp * ik - (W)1;
                             const W ap = to_w<W>(ax[(j == ctry ? 4 + u : 3) * N + j]);
                             s1c[u] = ww * lamp * phi * (g2 + (W)1) * ik;
@@ -632,10 +699,26 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
 // do not fit is NaN). A pool sized to the tables lets several blocks share an SM.
 constexpr size_t kJacSmem = 160 * 1024;
 
+template <int PREC, bool DELTA>
+static cudaError_t launch_jacobian_t(const IrbcDev &P, int64_t s0, int64_t nsc, const DevTables &t, int form,
+                                     const int32_t *koff, const int32_t *kids, const double *lo, const double *span,
+                                     const double *guess, const NodePolicy<DELTA, typename DeltaT<PREC>::W> &pol,
+                                     const double *aux, double *jac, size_t smem, int cap, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(irbc_jacobian_kernel<PREC, DELTA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    irbc_jacobian_kernel<PREC, DELTA><<<(unsigned)nsc, JAC_THREADS, smem, st>>>(P, s0, nsc, t, form, koff, kids, lo, span,
+                                                                             guess, pol, aux, jac, cap);
+    return cudaGetLastError();
+}
+
+// y: all node rows, or (dY != null, the node shortcut) the 3 rows per state
+// of the no-shock and global-shock queries, with dY the country nodes' changes
+// (double for FP64, float for F32C)
 static cudaError_t launch_jacobian(int precision, const IrbcDev &P, int64_t s0, int64_t nsc, const DevTables &t,
                                    int form, int G, int64_t terms, const int32_t *koff, const int32_t *kids,
                                    const double *lo, const double *span, const double *guess, const double *y,
-                                   const double *aux, double *jac, cudaStream_t st) {
+                                   const void *dY, const double *aux, double *jac, cudaStream_t st) {
     const size_t wsz = precision == DDSG_F64 ? sizeof(double) : sizeof(float);
     const size_t fixed = ((sizeof(JGroup) * G + sizeof(int32_t) * P.N + 15) & ~(size_t)15) +
                          ((wsz * 8 * P.N + 15) & ~(size_t)15);
@@ -643,20 +726,24 @@ static cudaError_t launch_jacobian(int precision, const IrbcDev &P, int64_t s0, 
     if (fixed + 64 * term > kJacSmem) return cudaErrorInvalidValue;
     const size_t cap = std::min<size_t>(std::max<int64_t>(terms, 1), (kJacSmem - fixed) / term);
     const size_t smem = fixed + cap * term;
-    cudaError_t e;
     if (precision == DDSG_F64) {
-        e = cudaFuncSetAttribute(irbc_jacobian_kernel<DDSG_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            irbc_jacobian_kernel<DDSG_F64><<<(unsigned)nsc, JAC_THREADS, smem, st>>>(
-                P, s0, nsc, t, form, koff, kids, lo, span, guess, y, aux, jac, (int)cap);
-    } else {
-        e = cudaFuncSetAttribute(irbc_jacobian_kernel<DDSG_F32C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            irbc_jacobian_kernel<DDSG_F32C><<<(unsigned)nsc, JAC_THREADS, smem, st>>>(
-                P, s0, nsc, t, form, koff, kids, lo, span, guess, y, aux, jac, (int)cap);
+        if (dY) {
+            const NodePolicy<true, double> pol{nullptr, y, static_cast<const double *>(dY)};
+            return launch_jacobian_t<DDSG_F64, true>(P, s0, nsc, t, form, koff, kids, lo, span, guess, pol, aux, jac,
+                                                     smem, (int)cap, st);
+        }
+        const NodePolicy<false, double> pol{y, nullptr, nullptr};
+        return launch_jacobian_t<DDSG_F64, false>(P, s0, nsc, t, form, koff, kids, lo, span, guess, pol, aux, jac, smem,
+                                                  (int)cap, st);
     }
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
+    if (dY) {
+        const NodePolicy<true, float> pol{nullptr, y, static_cast<const float *>(dY)};
+        return launch_jacobian_t<DDSG_F32C, true>(P, s0, nsc, t, form, koff, kids, lo, span, guess, pol, aux, jac, smem,
+                                                  (int)cap, st);
+    }
+    const NodePolicy<false, float> pol{y, nullptr, nullptr};
+    return launch_jacobian_t<DDSG_F32C, false>(P, s0, nsc, t, form, koff, kids, lo, span, guess, pol, aux, jac, smem,
+                                               (int)cap, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1047,9 +1134,9 @@ __global__ void irbc_queries3_kernel(IrbcDev P, int64_t ns, const double *__rest
 // Node shortcut (one thread per (state, country i) for the term search, then
 // one warp per 32 such pairs for the sums). The policy at the two nodes that
 // shock country i (2i: +, 2i+1: -) is the no-shock policy plus the change of
-// every component holding a_i when a'_i moves to its shocked value; the pair
-// with i = 0 also copies the two global-shock rows. Writes the 2(N+1)-node
-// policy array y in the layout the residual and Jacobian kernels read.
+// every component holding a_i when a'_i moves to its shocked value. Writes
+// those changes, dY (2N rows of m per state, in W), which the residual and
+// Jacobian kernels read beside the no-shock and global-shock rows.
 // Phase 1: each thread encodes a'_i's three values (no shock, +, -) and walks
 // the tuples of its components once, keeping the active (row, weight) term of
 // every value in shared memory (at most DLT_CAP per value; a pair with more
@@ -1058,9 +1145,8 @@ __global__ void irbc_queries3_kernel(IrbcDev P, int64_t ns, const double *__rest
 // terms in (component, tuple) order, DLT_UNR terms' rows in flight at a time;
 // every surplus row is read and every policy row written coalesced. A
 // flagged pair is summed by a warp-wide walk of its tuples (lanes over the
-// tuples, active terms broadcast in the same order). Node rows =
-// no-shock + (sum_v - sum_0), the sums and their difference in W (FP64 is
-// GB300's slow unit: F32C leaves one conversion and one FP64 add per output).
+// tuples, active terms broadcast in the same order). Changes = sum_v - sum_0,
+// the sums and their difference in W (no FP64 arithmetic per output).
 constexpr int DLT_WARPS = 4;   // warps per block
 constexpr int DLT_CAP = 16;    // terms per (pair, value) kept in shared memory
 
@@ -1177,12 +1263,13 @@ __global__ void __launch_bounds__(32 * DLT_WARPS) irbc_delta_kernel(IrbcDev P, i
                                                                     const double *__restrict__ guess,
                                                                     const double *__restrict__ lo,
                                                                     const double *__restrict__ span,
-                                                                    const double *__restrict__ y3, double *__restrict__ y) {
+                                                                    const double *__restrict__ y3,
+                                                                    typename DeltaT<PREC>::W *__restrict__ dY) {
     using W = typename DeltaT<PREC>::W;
     constexpr int UNR = dlt_unroll<PREC>();
     const W *alpha = DeltaT<PREC>::alpha(t);
     const int mp = DeltaT<PREC>::stride(t);
-    const int N = P.N, d = 2 * N, m = P.m, nq = 2 * (N + 1);
+    const int N = P.N, d = 2 * N, m = P.m;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool paper = form == DDSG_FORM_PAPER;
     extern __shared__ float4 dlt_raw[];
@@ -1245,9 +1332,8 @@ __global__ void __launch_bounds__(32 * DLT_WARPS) irbc_delta_kernel(IrbcDev P, i
             cp[v] = __shfl_sync(0xffffffffu, cnt[v], p);
             Xp[v] = __shfl_sync(0xffffffffu, Xi[v], p);
         }
-        const double *yb = y3 + (slp * 3) * (int64_t)m;
-        double *yp = y + (slp * nq + 2 * ip) * (int64_t)m;
-        double *ym = yp + m;
+        W *dp_row = dY + (slp * 2 * N + 2 * ip) * (int64_t)m;   // node 2i (+); node 2i + 1 (-) follows
+        W *dm_row = dp_row + m;
         for (int m0 = 0; m0 < m; m0 += 32 * OC) {
             W acc[3][OC];
 #pragma unroll
@@ -1290,17 +1376,9 @@ __global__ void __launch_bounds__(32 * DLT_WARPS) irbc_delta_kernel(IrbcDev P, i
             for (int c = 0; c < OC; ++c) {
                 const int o = m0 + lane + 32 * c;
                 if (o < m) {
-                    // the changes in W (F32C: one FP32 rounding each), added in FP64
-                    const W dp = acc[1][c] - acc[0][c], dm = acc[2][c] - acc[0][c];
-                    yp[o] = nan ? NAN : yb[o] + (double)dp;
-                    ym[o] = nan ? NAN : yb[o] + (double)dm;
+                    dp_row[o] = nan ? (W)NAN : acc[1][c] - acc[0][c];
+                    dm_row[o] = nan ? (W)NAN : acc[2][c] - acc[0][c];
                 }
-            }
-        }
-        if (ip == 0) {
-            for (int o = lane; o < m; o += 32) {
-                y[(slp * nq + 2 * N) * (int64_t)m + o] = y3[(slp * 3 + 1) * (int64_t)m + o];
-                y[(slp * nq + 2 * N + 1) * (int64_t)m + o] = y3[(slp * 3 + 2) * (int64_t)m + o];
             }
         }
     }
@@ -1425,14 +1503,15 @@ int a_components(hdmr_t *h, int N, std::vector<int32_t> &off, std::vector<int32_
 template <int PREC, int OC>
 cudaError_t launch_delta_oc(const IrbcDev &P, int64_t s0, int64_t nsc, const DevTables &t, int form,
                             const int32_t *aoff, const int32_t *acomp, const double *states, const double *guess,
-                            const double *lo, const double *span, const double *y3, double *y, cudaStream_t st) {
+                            const double *lo, const double *span, const double *y3,
+                            typename DeltaT<PREC>::W *dY, cudaStream_t st) {
     const size_t smem = sizeof(DltTerms<typename DeltaT<PREC>::W>) * DLT_WARPS;
     cudaError_t e = cudaFuncSetAttribute(irbc_delta_kernel<PREC, OC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t warps = (nsc * P.N + 31) / 32;
     irbc_delta_kernel<PREC, OC><<<(unsigned)((warps + DLT_WARPS - 1) / DLT_WARPS), 32 * DLT_WARPS, smem, st>>>(
-        P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, y);
+        P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, dY);
     return cudaGetLastError();
 }
 
@@ -1440,12 +1519,13 @@ cudaError_t launch_delta_oc(const IrbcDev &P, int64_t s0, int64_t nsc, const Dev
 template <int PREC>
 cudaError_t launch_delta(const IrbcDev &P, int64_t s0, int64_t nsc, const DevTables &t, int form,
                          const int32_t *aoff, const int32_t *acomp, const double *states, const double *guess,
-                         const double *lo, const double *span, const double *y3, double *y, cudaStream_t st) {
+                         const double *lo, const double *span, const double *y3, typename DeltaT<PREC>::W *dY,
+                         cudaStream_t st) {
     const int need = (P.m + 31) / 32;
-    if (need <= 2) return launch_delta_oc<PREC, 2>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, y, st);
-    if (need <= 4) return launch_delta_oc<PREC, 4>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, y, st);
-    if (need <= 6) return launch_delta_oc<PREC, 6>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, y, st);
-    return launch_delta_oc<PREC, 8>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, y, st);
+    if (need <= 2) return launch_delta_oc<PREC, 2>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, dY, st);
+    if (need <= 4) return launch_delta_oc<PREC, 4>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, dY, st);
+    if (need <= 6) return launch_delta_oc<PREC, 6>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, dY, st);
+    return launch_delta_oc<PREC, 8>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, dY, st);
 }
 
 }  // namespace
@@ -1617,7 +1697,7 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
         uint64_t *X = reinterpret_cast<uint64_t *>(base);
         int32_t *flags = reinterpret_cast<int32_t *>(X + (int64_t)d * Qe);
         double *y3 = reinterpret_cast<double *>(((uintptr_t)(flags + Qe) + 255) & ~(uintptr_t)255);
-        double *y = delta ? y3 + Qe * m : y3;
+        double *y = delta ? y3 + Qe * m : y3;   // shortcut: the country nodes' changes dY, in W
         double *aux = y + Q * m;
         cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int32_t) * Qe, st);
         if (e == cudaSuccess) {
@@ -1657,19 +1737,32 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
                                                guess_dev, v.lo, v.span, y3, y, st);
             else
                 e = launch_delta<DDSG_F32C>(P, s0, nsc, *v.tables, form, aoff_dev, acomp_dev, states_dev,
-                                                guess_dev, v.lo, v.span, y3, y, st);
+                                                guess_dev, v.lo, v.span, y3, reinterpret_cast<float *>(y), st);
         }
         if (e == cudaSuccess) {
             Tracer::Scope ts(&M->tr, 2, st);
             const int rt = std::min(RES_THREADS, (N + 31) / 32 * 32);
-            irbc_residual_kernel<<<(unsigned)nsc, rt, 0, st>>>(P, s0, nsc, states_dev, guess_dev, y, resid_dev,
-                                                               euler_err_dev, jac_dev, aux);
+            const unsigned nb = (unsigned)nsc;
+            if (!delta)
+                irbc_residual_kernel<false, double><<<nb, rt, 0, st>>>(
+                    P, s0, nsc, states_dev, guess_dev, NodePolicy<false, double>{y, nullptr, nullptr}, resid_dev,
+                    euler_err_dev, jac_dev, aux);
+            else if (precision == DDSG_F64)
+                irbc_residual_kernel<true, double><<<nb, rt, 0, st>>>(
+                    P, s0, nsc, states_dev, guess_dev, NodePolicy<true, double>{nullptr, y3, y}, resid_dev,
+                    euler_err_dev, jac_dev, aux);
+            else
+                irbc_residual_kernel<true, float><<<nb, rt, 0, st>>>(
+                    P, s0, nsc, states_dev, guess_dev,
+                    NodePolicy<true, float>{nullptr, y3, reinterpret_cast<const float *>(y)}, resid_dev,
+                    euler_err_dev, jac_dev, aux);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess && jac_dev) {
             Tracer::Scope ts(&M->tr, 3, st);
             e = launch_jacobian(precision, P, s0, nsc, *v.tables, form, (int)kids.size(), jac_terms, koff_dev,
-                                kids_dev, v.lo, v.span, guess_dev, y, aux, jac_dev, st);
+                                kids_dev, v.lo, v.span, guess_dev, delta ? y3 : y, delta ? (const void *)y : nullptr,
+                                aux, jac_dev, st);
         }
         if (e != cudaSuccess) return set_error(DDSG_ERR_CUDA, cudaGetErrorString(e));
     }
