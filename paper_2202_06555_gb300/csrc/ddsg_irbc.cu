@@ -914,6 +914,28 @@ __device__ __forceinline__ void lum_solve(const float *A, int ld, int n, float *
     }
 }
 
+// Rows c + 1 .. n - 1 of the factorization step at column c: a warp per row,
+// lane entries j = c + 1 + lane + 32 kk, kk < NK, the pivot row's in registers.
+template <int NK>
+__device__ __forceinline__ void lum_update_rows(float *A, int ld, int n, int c, float inv, int lane, int warp) {
+    float prow[NK];
+#pragma unroll
+    for (int kk = 0; kk < NK; ++kk) {
+        const int j = c + 1 + lane + 32 * kk;
+        prow[kk] = j < n ? A[c * ld + j] : 0.0f;
+    }
+    for (int r = c + 1 + warp; r < n; r += LUM_WARPS) {
+        const float l = A[r * ld + c] * inv;
+#pragma unroll
+        for (int kk = 0; kk < NK; ++kk) {
+            const int j = c + 1 + lane + 32 * kk;
+            if (j < n) A[r * ld + j] = fmaf(-l, prow[kk], A[r * ld + j]);
+        }
+        __syncwarp();   // every lane has read A[r][c] before it becomes the multiplier
+        if (lane == 0) A[r * ld + c] = l;
+    }
+}
+
 __global__ void __launch_bounds__(LUM_THREADS, 2) lu_mixed_kernel(int n, int64_t ns, const double *__restrict__ Ag,
                                                                   const double *__restrict__ bg,
                                                                   const int32_t *__restrict__ active,
@@ -976,23 +998,16 @@ __global__ void __launch_bounds__(LUM_THREADS, 2) lu_mixed_kernel(int n, int64_t
         }
         __syncthreads();
         const float inv = 1.0f / A[c * ld + c];
-        // this lane's entries of the pivot row, j = c + 1 + lane + 32 kk, held in
-        // registers for the whole column (n <= 32 * LUM_KJ)
-        float prow[LUM_KJ];
-#pragma unroll
-        for (int kk = 0; kk < LUM_KJ; ++kk) {
-            const int j = c + 1 + lane + 32 * kk;
-            prow[kk] = j < n ? A[c * ld + j] : 0.0f;
-        }
-        for (int r = c + 1 + warp; r < n; r += LUM_WARPS) {
-            const float l = A[r * ld + c] * inv;
-#pragma unroll
-            for (int kk = 0; kk < LUM_KJ; ++kk) {
-                const int j = c + 1 + lane + 32 * kk;
-                if (j < n) A[r * ld + j] = fmaf(-l, prow[kk], A[r * ld + j]);
-            }
-            __syncwarp();   // every lane has read A[r][c] before it becomes the multiplier
-            if (lane == 0) A[r * ld + c] = l;
+        // the update of rows c + 1 .. n - 1, compiled for the number of 32-column
+        // chunks left of the pivot row (the instruction stream is the limit)
+        switch ((n - c + 30) >> 5) {
+            case 1: lum_update_rows<1>(A, ld, n, c, inv, lane, warp); break;
+            case 2: lum_update_rows<2>(A, ld, n, c, inv, lane, warp); break;
+            case 3: lum_update_rows<3>(A, ld, n, c, inv, lane, warp); break;
+            case 4: lum_update_rows<4>(A, ld, n, c, inv, lane, warp); break;
+            case 5: lum_update_rows<5>(A, ld, n, c, inv, lane, warp); break;
+            case 6: lum_update_rows<6>(A, ld, n, c, inv, lane, warp); break;
+            default: break;   // c = n - 1: no rows below
         }
         __syncthreads();
     }
