@@ -881,7 +881,6 @@ __global__ void __launch_bounds__(NodShape<GR>::NT, 1) eval_nodal_f32x2_kernel(c
 constexpr int kTmQB = 256;                 // queries per block
 constexpr int kTmNT = 2 * kTmQB;           // two output windows
 constexpr uint32_t kTmCols = 256;          // tensor-memory columns per block
-constexpr int kTmFold = 4;                 // components per fold of the partials into the totals
 
 __device__ __forceinline__ void tm_ld8(uint32_t taddr, uint32_t (&r)[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -1060,7 +1059,7 @@ __global__ void __launch_bounds__(kTmNT, 1) eval_nodal_tmem_kernel(const EvalPar
                 pr = nx;
             }
         }
-        if ((i & (kTmFold - 1)) == kTmFold - 1 || i + 1 == nproc) fold();
+        if ((i & 1) || i + 1 == nproc) fold();
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[b]);
         int pf = 0;
