@@ -850,7 +850,6 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(int n, int64_t ns, const 
 
 constexpr int LUM_THREADS = 256;
 constexpr int LUM_WARPS = LUM_THREADS / 32;
-constexpr int LUM_KJ = 6;       // pivot-row entries per lane: n <= 192
 constexpr int LUM_SOLVES = 12;  // first solve + up to 11 corrections (each must halve the last)
 
 inline size_t lum_smem_bytes(int n) {
@@ -999,7 +998,7 @@ __global__ void __launch_bounds__(LUM_THREADS, 2) lu_mixed_kernel(int n, int64_t
         __syncthreads();
         const float inv = 1.0f / A[c * ld + c];
         // the update of rows c + 1 .. n - 1, compiled for the number of 32-column
-        // chunks left of the pivot row (the instruction stream is the limit)
+        // chunks left of the pivot row (the instruction stream is the limit; n <= 192)
         switch ((n - c + 30) >> 5) {
             case 1: lum_update_rows<1>(A, ld, n, c, inv, lane, warp); break;
             case 2: lum_update_rows<2>(A, ld, n, c, inv, lane, warp); break;
@@ -1085,6 +1084,24 @@ __global__ void accept_kernel(int n, int64_t ns, const int32_t *__restrict__ acc
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ns * n) return;
     if (acc[e / n]) z[e] = zt[e];
+}
+
+// dst row k = src row kidx[k] (rows of w doubles): the Newton working set compacted
+__global__ void gather_rows_kernel(int64_t nk, int w, const int32_t *__restrict__ kidx, const double *__restrict__ src,
+                                   double *__restrict__ dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nk * w) return;
+    const int64_t k = e / w;
+    dst[e] = src[(int64_t)kidx[k] * w + (e - k * w)];
+}
+
+// dst row widx[k] = src row k: the working set's solutions back to the caller's array
+__global__ void scatter_rows_kernel(int64_t nk, int w, const int64_t *__restrict__ widx, const double *__restrict__ src,
+                                    double *__restrict__ dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nk * w) return;
+    const int64_t k = e / w;
+    dst[widx[k] * w + (e - k * w)] = src[e];
 }
 
 __global__ void trial_kernel(int n, int64_t ns, const double *__restrict__ z, const double *__restrict__ dz,
@@ -1784,6 +1801,31 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
     return DDSG_OK;
 }
 
+namespace {
+
+// dx = -A^-1 r for the systems with active[s] != 0 (all when active is null):
+// FP32 factors refined in FP64, then the FP64 kernel for those it could not refine
+int lu_solve_masked(int n, int64_t ns, const double *A_dev, const double *r_dev, const int32_t *active,
+                    double *dx_dev, int32_t *status_dev, cudaStream_t st) {
+    const size_t smem = sizeof(double) * ((size_t)n * n + n);
+    const size_t smem_m = lum_smem_bytes(n);
+    cudaError_t e = cudaFuncSetAttribute(lu_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
+    if (e == cudaSuccess) {
+        lu_mixed_kernel<<<(unsigned)ns, LUM_THREADS, smem_m, st>>>(n, ns, A_dev, r_dev, active, dx_dev, status_dev);
+        e = cudaGetLastError();
+    }
+    // the systems the FP32 factors could not refine (status 3), again in FP64
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        lu_solve_kernel<<<(unsigned)ns, 256, smem, st>>>(n, ns, A_dev, r_dev, active, dx_dev, status_dev, 1);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return set_error(DDSG_ERR_CUDA, cudaGetErrorString(e));
+    return DDSG_OK;
+}
+
+}  // namespace
+
 extern "C" int irbc_lu_solve(int n, int64_t ns, const double *A_dev, const double *r_dev, double *dx_dev,
                              int32_t *status_dev, ddsg_stream_t stream) {
     if (n < 1 || ns < 0) return set_error(DDSG_ERR_ARG, "irbc_lu_solve: bad size");
@@ -1791,21 +1833,7 @@ extern "C" int irbc_lu_solve(int n, int64_t ns, const double *A_dev, const doubl
     const size_t smem = sizeof(double) * ((size_t)n * n + n);
     if (smem > 220 * 1024) return set_error(DDSG_ERR_ARG, "irbc_lu_solve: system too large for shared memory (n <= 165)");
     if (!A_dev || !r_dev || !dx_dev || !status_dev) return set_error(DDSG_ERR_ARG, "irbc_lu_solve: NULL argument");
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const size_t smem_m = lum_smem_bytes(n);
-    cudaError_t e = cudaFuncSetAttribute(lu_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
-    if (e == cudaSuccess) {
-        lu_mixed_kernel<<<(unsigned)ns, LUM_THREADS, smem_m, st>>>(n, ns, A_dev, r_dev, nullptr, dx_dev, status_dev);
-        e = cudaGetLastError();
-    }
-    // the systems the FP32 factors could not refine (status 3), again in FP64
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) {
-        lu_solve_kernel<<<(unsigned)ns, 256, smem, st>>>(n, ns, A_dev, r_dev, nullptr, dx_dev, status_dev, 1);
-        e = cudaGetLastError();
-    }
-    if (e != cudaSuccess) return set_error(DDSG_ERR_CUDA, cudaGetErrorString(e));
-    return DDSG_OK;
+    return lu_solve_masked(n, ns, A_dev, r_dev, nullptr, dx_dev, status_dev, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *states_dev, double *sol_dev,
@@ -1815,9 +1843,11 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
         return set_error(DDSG_ERR_ARG, "irbc_newton: bad argument");
     if (ns == 0) return DDSG_OK;
     if ((ns > 0) && (!states_dev || !sol_dev)) return set_error(DDSG_ERR_ARG, "irbc_newton: NULL states or solution");
-    const int N = M->p.N, n = M->irreversible ? 2 * N + 1 : N + 1;
+    const int N = M->p.N, n = M->irreversible ? 2 * N + 1 : N + 1, d = 2 * N;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // Newton buffers (separate from the residual workspace): r, J, dz, zt, rt, norms, steps, flags
+    // Newton buffers (separate from the residual workspace): r, J, dz, zt, rt, norms,
+    // steps, flags, and the compacted working set (two copies of its states and
+    // solutions, spare r and dz, slot indices)
     double *r = nullptr, *J = nullptr, *dz = nullptr, *zt = nullptr, *rt = nullptr;
     double *n2 = nullptr, *ninf = nullptr, *n2t = nullptr, *ninft = nullptr, *step = nullptr;
     int32_t *active = nullptr, *stat = nullptr;
@@ -1825,8 +1855,9 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
     auto rnd = [](size_t b) { return (b + 255) & ~(size_t)255; };
     // sub-buffer sizes, each rounded to 256 bytes; the block is exactly their sum
     const size_t szv = rnd(bytes((size_t)ns * n)), szJ = rnd(bytes((size_t)ns * n * n)),
-                 szs = rnd(bytes((size_t)ns)), szi = rnd(sizeof(int32_t) * (size_t)ns);
-    const size_t tot = 4 * szv + szJ + 5 * szs + 3 * szi;
+                 szs = rnd(bytes((size_t)ns)), szi = rnd(sizeof(int32_t) * (size_t)ns),
+                 szS = rnd(bytes((size_t)ns * d)), szl = rnd(sizeof(int64_t) * (size_t)ns);
+    const size_t tot = 4 * szv + szJ + 5 * szs + 4 * szi + 2 * szS + 4 * szv + szl;
     if (tot > M->nws_bytes) {
         cudaFree(M->nws);
         M->nws = nullptr;
@@ -1853,94 +1884,164 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
     active = (int32_t *)take(szi);
     stat = (int32_t *)take(szi);
     int32_t *accd = (int32_t *)take(szi);
+    int32_t *kidx_d = (int32_t *)take(szi);
+    double *Sw[2] = {(double *)take(szS), (double *)take(szS)};
+    double *Zw[2] = {(double *)take(szv), (double *)take(szv)};
+    double *r2 = (double *)take(szv), *dz2 = (double *)take(szv);
+    int64_t *widx_d = (int64_t *)take(szl);
     if ((size_t)(p - static_cast<unsigned char *>(blk)) != tot)
         return set_error(DDSG_ERR_STATE, "irbc_newton: internal buffer layout mismatch");
-    std::vector<double> h_n2(ns), h_ninf(ns), h_n2t(ns), h_step(ns);
+    std::vector<double> h_n2(ns), h_ninf(ns), h_n2t(ns), h_step(ns), h_res(ns, 0.0);
     std::vector<int32_t> h_active(ns, 1), h_iters(ns, 0), h_stat(ns, 1);   // 1 = max-iter until converged
     int rc = DDSG_OK;
     auto fail_cuda = [&](cudaError_t e) { rc = set_error(DDSG_ERR_CUDA, cudaGetErrorString(e)); };
-    const unsigned nb = (unsigned)((ns + 255) / 256);
+    // The working set: slot k holds state widx[k]. It starts as the caller's
+    // arrays; once at most 3/4 of its slots are still iterating, the live ones
+    // are gathered into contiguous slots (states, solution, residual, step), so
+    // converged states cost nothing in later iterations. Per-state arithmetic
+    // does not depend on the slot, so the results are those of the full batch.
+    std::vector<int64_t> widx(ns);
+    for (int64_t s = 0; s < ns; ++s) widx[s] = s;
+    int64_t nw = ns;
+    const double *S = states_dev;
+    double *Z = sol_dev;
+    int wb = 0;
+    bool own = false;   // Z is a working copy (scattered back at the end)
     for (int it = 0; it <= max_it && rc == DDSG_OK; ++it) {
-        rc = euler_residual(M, policy, ns, states_dev, sol_dev, r, it < max_it ? J : nullptr, nullptr,
-                            precision, form, stream);
+        const unsigned nb = (unsigned)((nw + 255) / 256);
+        rc = euler_residual(M, policy, nw, S, Z, r, it < max_it ? J : nullptr, nullptr, precision, form, stream);
         if (rc) break;
         {
             Tracer::Scope ts(&M->tr, 5, st);
-            norms_kernel<<<nb, 256, 0, st>>>(n, ns, r, n2, ninf);
+            norms_kernel<<<nb, 256, 0, st>>>(n, nw, r, n2, ninf);
         }
-        cudaError_t e = cudaMemcpyAsync(h_n2.data(), n2, bytes(ns), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h_ninf.data(), ninf, bytes(ns), cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaMemcpyAsync(h_n2.data(), n2, bytes(nw), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_ninf.data(), ninf, bytes(nw), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { fail_cuda(e); break; }
         int64_t live = 0;
-        for (int64_t s = 0; s < ns; ++s) {
-            if (h_active[s] && h_ninf[s] <= tol) {
+        std::vector<int32_t> act(nw);
+        for (int64_t k = 0; k < nw; ++k) {
+            const int64_t s = widx[k];
+            h_res[s] = h_ninf[k];
+            if (h_active[s] && h_ninf[k] <= tol) {
                 h_active[s] = 0;
                 h_stat[s] = 0;
             }
-            live += h_active[s];
+            act[k] = h_active[s];
+            live += act[k];
         }
         if (live == 0 || it == max_it) break;
-        // Newton step dz = -J^-1 r (all states; converged ones are not applied)
-        e = cudaMemsetAsync(stat, 0, sizeof(int32_t) * ns, st);
+        // Newton step dz = -J^-1 r for the live slots
+        e = cudaMemsetAsync(stat, 0, sizeof(int32_t) * nw, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) { fail_cuda(e); break; }
         {
             Tracer::Scope ts(&M->tr, 4, st);
-            rc = irbc_lu_solve(n, ns, J, r, dz, stat, stream);
+            rc = lu_solve_masked(n, nw, J, r, active, dz, stat, st);
         }
         if (rc) break;
-        std::vector<int32_t> h_lu(ns);
-        e = cudaMemcpyAsync(h_lu.data(), stat, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, st);
+        std::vector<int32_t> h_lu(nw);
+        e = cudaMemcpyAsync(h_lu.data(), stat, sizeof(int32_t) * nw, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { fail_cuda(e); break; }
-        for (int64_t s = 0; s < ns; ++s) {
-            if (h_active[s] && h_lu[s] == 2) {
+        for (int64_t k = 0; k < nw; ++k) {
+            const int64_t s = widx[k];
+            if (h_active[s] && h_lu[k] == 2) {
                 h_active[s] = 0;
                 h_stat[s] = 2;   // singular Jacobian
+                --live;
             }
-            h_step[s] = 1.0;
         }
+        if (live > 0 && live * 4 <= nw * 3) {
+            // compact: the live slots, in order, into the other working buffers
+            std::vector<int32_t> kidx;
+            std::vector<int64_t> nidx;
+            std::vector<double> n2c;
+            kidx.reserve(live);
+            nidx.reserve(live);
+            n2c.reserve(live);
+            for (int64_t k = 0; k < nw; ++k)
+                if (h_active[widx[k]]) {
+                    kidx.push_back((int32_t)k);
+                    nidx.push_back(widx[k]);
+                    n2c.push_back(h_n2[k]);
+                }
+            Tracer::Scope ts(&M->tr, 5, st);
+            if (own) {   // the leaving slots' solutions go back first
+                e = cudaMemcpyAsync(widx_d, widx.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st);
+                if (e == cudaSuccess) {
+                    scatter_rows_kernel<<<(unsigned)((nw * n + 255) / 256), 256, 0, st>>>(nw, n, widx_d, Z, sol_dev);
+                    e = cudaGetLastError();
+                }
+            }
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(kidx_d, kidx.data(), sizeof(int32_t) * live, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) {
+                const unsigned gs = (unsigned)((live * d + 255) / 256), gv = (unsigned)((live * n + 255) / 256);
+                double *Sn = Sw[wb ^ 1], *Zn = Zw[wb ^ 1];
+                gather_rows_kernel<<<gs, 256, 0, st>>>(live, d, kidx_d, S, Sn);
+                gather_rows_kernel<<<gv, 256, 0, st>>>(live, n, kidx_d, Z, Zn);
+                gather_rows_kernel<<<gv, 256, 0, st>>>(live, n, kidx_d, r, r2);
+                gather_rows_kernel<<<gv, 256, 0, st>>>(live, n, kidx_d, dz, dz2);
+                e = cudaGetLastError();
+                S = Sn;
+                Z = Zn;
+                std::swap(r, r2);
+                std::swap(dz, dz2);
+                wb ^= 1;
+                own = true;
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // kidx outlives its copy
+            if (e != cudaSuccess) { fail_cuda(e); break; }
+            widx.swap(nidx);
+            nw = live;
+            std::copy(n2c.begin(), n2c.end(), h_n2.begin());
+        }
+        for (int64_t k = 0; k < nw; ++k) h_step[k] = 1.0;
         // backtracking on ||r||_2: halve per state until the norm decreases
-        std::vector<int32_t> pending = h_active;
+        std::vector<int32_t> pending(nw);
+        for (int64_t k = 0; k < nw; ++k) pending[k] = h_active[widx[k]];
+        const unsigned nbw = (unsigned)((nw + 255) / 256);
         for (int ls = 0; ls < 12; ++ls) {
             int64_t np = 0;
-            for (int64_t s = 0; s < ns; ++s) np += pending[s];
+            for (int64_t k = 0; k < nw; ++k) np += pending[k];
             if (np == 0) break;
-            e = cudaMemcpyAsync(active, pending.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(step, h_step.data(), bytes(ns), cudaMemcpyHostToDevice, st);
+            e = cudaMemcpyAsync(active, pending.data(), sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(step, h_step.data(), bytes(nw), cudaMemcpyHostToDevice, st);
             if (e != cudaSuccess) { fail_cuda(e); break; }
             {
                 Tracer::Scope ts(&M->tr, 5, st);
-                trial_kernel<<<(unsigned)((ns * n + 255) / 256), 256, 0, st>>>(n, ns, sol_dev, dz, step, active, zt);
+                trial_kernel<<<(unsigned)((nw * n + 255) / 256), 256, 0, st>>>(n, nw, Z, dz, step, active, zt);
             }
-            rc = euler_residual(M, policy, ns, states_dev, zt, rt, nullptr, nullptr, precision, form, stream);
+            rc = euler_residual(M, policy, nw, S, zt, rt, nullptr, nullptr, precision, form, stream);
             if (rc) break;
             {
                 Tracer::Scope ts(&M->tr, 5, st);
-                norms_kernel<<<nb, 256, 0, st>>>(n, ns, rt, n2t, ninft);
+                norms_kernel<<<nbw, 256, 0, st>>>(n, nw, rt, n2t, ninft);
             }
-            e = cudaMemcpyAsync(h_n2t.data(), n2t, bytes(ns), cudaMemcpyDeviceToHost, st);
+            e = cudaMemcpyAsync(h_n2t.data(), n2t, bytes(nw), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) { fail_cuda(e); break; }
-            std::vector<int32_t> acc(ns, 0);
+            std::vector<int32_t> acc(nw, 0);
             int64_t na = 0;
-            for (int64_t s = 0; s < ns; ++s) {
-                if (!pending[s]) continue;
-                if (h_n2t[s] < h_n2[s] || ls == 11) {
-                    acc[s] = 1;
-                    pending[s] = 0;
+            for (int64_t k = 0; k < nw; ++k) {
+                if (!pending[k]) continue;
+                if (h_n2t[k] < h_n2[k] || ls == 11) {
+                    acc[k] = 1;
+                    pending[k] = 0;
                     ++na;
                 } else {
-                    h_step[s] *= 0.5;
+                    h_step[k] *= 0.5;
                 }
             }
             if (na) {
                 // copy accepted trial points into the solution (acc is read before the
                 // stream reaches the next host synchronization, so it must outlive the copy)
-                e = cudaMemcpyAsync(accd, acc.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st);
+                e = cudaMemcpyAsync(accd, acc.data(), sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st);
                 if (e == cudaSuccess) {
                     Tracer::Scope ts(&M->tr, 5, st);
-                    accept_kernel<<<(unsigned)((ns * n + 255) / 256), 256, 0, st>>>(n, ns, accd, zt, sol_dev);
+                    accept_kernel<<<(unsigned)((nw * n + 255) / 256), 256, 0, st>>>(n, nw, accd, zt, Z);
                     e = cudaGetLastError();
                 }
                 if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1950,13 +2051,22 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
         for (int64_t s = 0; s < ns; ++s)
             if (h_active[s]) h_iters[s] = it + 1;
     }
+    if (rc == DDSG_OK && own) {   // the working copies' solutions back to the caller's array
+        cudaError_t e = cudaMemcpyAsync(widx_d, widx.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            scatter_rows_kernel<<<(unsigned)((nw * n + 255) / 256), 256, 0, st>>>(nw, n, widx_d, Z, sol_dev);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) fail_cuda(e);
+    }
     if (rc == DDSG_OK) {
         cudaError_t e = cudaSuccess;
         if (iters_dev) e = cudaMemcpyAsync(iters_dev, h_iters.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess && status_dev)
             e = cudaMemcpyAsync(status_dev, h_stat.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess && resnorm_dev)
-            e = cudaMemcpyAsync(resnorm_dev, ninf, bytes(ns), cudaMemcpyDeviceToDevice, st);
+            e = cudaMemcpyAsync(resnorm_dev, h_res.data(), bytes(ns), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) fail_cuda(e);
     }

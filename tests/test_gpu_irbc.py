@@ -193,3 +193,44 @@ def test_newton_matches_oracle(G, prec):
     assert np.all(stt.cpu().numpy() == 0) and np.all(nr.cpu().numpy() <= tol)
     assert np.all(it.cpu().numpy() <= 10)
     assert np.allclose(z.cpu().numpy(), sol_ref, atol=1e-7 if prec == 0 else 1e-5)
+
+
+@pytest.mark.parametrize("mode", ["all", "delta"])
+def test_newton_batch_equals_states_solved_apart(G, mode):
+    """States that converge after different numbers of iterations leave the
+    Newton working set as they converge (the live ones are gathered into
+    contiguous slots). Per-state arithmetic does not depend on the slot, so
+    the batch must give, bit for bit, the solution, iteration count, status
+    and residual norm of each state solved in a batch of its own. Guesses
+    from 1x to 8x the base perturbation spread the iteration counts; one state
+    gets a non-finite guess (status 1 after the iteration cap, or the
+    residual stays NaN)."""
+    N = 10
+    I, E, h, M, lam = make_model(G, N)
+    M.set_node_mode(G.NODES_DELTA if mode == "delta" else G.NODES_ALL)
+    S, g = states_and_guess(N, 24, lam, synth.BASE_SEED + 405)
+    scale = np.repeat([1.0, 2.0, 4.0, 8.0], 6)[:, None]
+    base = np.concatenate([S[:, N:], np.full((24, 1), lam)], 1)
+    g = np.ascontiguousarray(base + scale * (g - base))
+    g[5, 0] = np.nan
+
+    def solve(idx):
+        sd = torch.from_numpy(np.ascontiguousarray(S[idx])).cuda()
+        z = torch.from_numpy(np.ascontiguousarray(g[idx])).cuda()
+        it = torch.zeros(len(idx), dtype=torch.int32, device="cuda")
+        stt = torch.zeros(len(idx), dtype=torch.int32, device="cuda")
+        nr = torch.zeros(len(idx), dtype=torch.float64, device="cuda")
+        M.newton(h, sd, z, 12, 1e-10, it, stt, nr, 0, 1)
+        torch.cuda.synchronize()
+        return z.cpu().numpy(), it.cpu().numpy(), stt.cpu().numpy(), nr.cpu().numpy()
+
+    try:
+        zb, itb, stb, nrb = solve(np.arange(24))
+        assert len(set(itb[stb == 0].tolist())) >= 2, itb   # the working set did shrink
+        for s in range(24):
+            z1, it1, st1, nr1 = solve(np.array([s]))
+            assert it1[0] == itb[s] and st1[0] == stb[s], (s, it1, itb[s], st1, stb[s])
+            assert np.array_equal(z1[0], zb[s], equal_nan=True), s
+            assert np.array_equal(nr1[0], nrb[s], equal_nan=True), s
+    finally:
+        M.set_node_mode(G.NODES_ALL)
