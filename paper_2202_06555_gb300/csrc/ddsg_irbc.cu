@@ -1907,14 +1907,23 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
     double *Z = sol_dev;
     int wb = 0;
     bool own = false;   // Z is a working copy (scattered back at the end)
+    // The residual, its norms and the Jacobian at the accepted points come out
+    // of the last line-search evaluation (it is evaluated with the Jacobian), so
+    // an iteration after a step reuses them instead of evaluating again.
+    bool have_next = false;
     for (int it = 0; it <= max_it && rc == DDSG_OK; ++it) {
         const unsigned nb = (unsigned)((nw + 255) / 256);
-        rc = euler_residual(M, policy, nw, S, Z, r, it < max_it ? J : nullptr, nullptr, precision, form, stream);
-        if (rc) break;
-        {
+        if (have_next) {
+            std::swap(r, rt);
+            std::swap(n2, n2t);
+            std::swap(ninf, ninft);
+        } else {
+            rc = euler_residual(M, policy, nw, S, Z, r, it < max_it ? J : nullptr, nullptr, precision, form, stream);
+            if (rc) break;
             Tracer::Scope ts(&M->tr, 5, st);
             norms_kernel<<<nb, 256, 0, st>>>(n, nw, r, n2, ninf);
         }
+        have_next = false;
         cudaError_t e = cudaMemcpyAsync(h_n2.data(), n2, bytes(nw), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_ninf.data(), ninf, bytes(nw), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -2014,8 +2023,12 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
                 Tracer::Scope ts(&M->tr, 5, st);
                 trial_kernel<<<(unsigned)((nw * n + 255) / 256), 256, 0, st>>>(n, nw, Z, dz, step, active, zt);
             }
-            rc = euler_residual(M, policy, nw, S, zt, rt, nullptr, nullptr, precision, form, stream);
+            // with the Jacobian when the next iteration may take a step: after the
+            // last round every slot's trial point is its accepted point
+            rc = euler_residual(M, policy, nw, S, zt, rt, it + 1 < max_it ? J : nullptr, nullptr, precision, form,
+                                stream);
             if (rc) break;
+            have_next = true;
             {
                 Tracer::Scope ts(&M->tr, 5, st);
                 norms_kernel<<<nbw, 256, 0, st>>>(n, nw, rt, n2t, ninft);
