@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(int n, int64_t ns, const 
 // b - A x in FP64 from the original matrix, solve for the correction, repeat).
 // On GB300 FP32 arithmetic is far faster than FP64 and the FP32 factors take
 // half the shared memory (two systems per SM). Each system's refinement stops
-// once the correction is below 2^-46 of the solution (FP64 accuracy). The
+// once the correction is below rtol of the solution (2^-46: FP64 accuracy). The
 // corrections shrink by about cond(A) u_32 per step; a system whose
 // correction stops halving, or that needs more than LUM_SOLVES solves
 // (condition number near 1/u_32 or worse), gets status 3 and is solved again
@@ -939,7 +939,7 @@ __global__ void __launch_bounds__(LUM_THREADS, 2) lu_mixed_kernel(int n, int64_t
                                                                   const double *__restrict__ bg,
                                                                   const int32_t *__restrict__ active,
                                                                   double *__restrict__ xg,
-                                                                  int32_t *__restrict__ status) {
+                                                                  int32_t *__restrict__ status, double rtol) {
     extern __shared__ float4 lum_raw[];
     const int ld = n | 1;   // odd row stride: column reads hit distinct banks
     float *A = reinterpret_cast<float *>(lum_raw);
@@ -1043,7 +1043,7 @@ __global__ void __launch_bounds__(LUM_THREADS, 2) lu_mixed_kernel(int n, int64_t
         dmax = lum_block_max(dmax, red);
         xmax = lum_block_max(xmax, red);
         if (!(xmax < HUGE_VAL)) break;
-        if (dmax <= xmax * 0x1p-46) { done = true; break; }
+        if (dmax <= xmax * rtol) { done = true; break; }
         if (it > 0 && !(dmax <= 0.5 * dprev)) break;   // not converging: left to FP64
         dprev = dmax;
         // residual -r - A x in FP64 (a warp per row, lanes along the row)
@@ -1804,14 +1804,16 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
 namespace {
 
 // dx = -A^-1 r for the systems with active[s] != 0 (all when active is null):
-// FP32 factors refined in FP64, then the FP64 kernel for those it could not refine
+// FP32 factors refined in FP64 until the correction is below rtol of the
+// solution, then the FP64 kernel for those it could not refine
 int lu_solve_masked(int n, int64_t ns, const double *A_dev, const double *r_dev, const int32_t *active,
-                    double *dx_dev, int32_t *status_dev, cudaStream_t st) {
+                    double *dx_dev, int32_t *status_dev, double rtol, cudaStream_t st) {
     const size_t smem = sizeof(double) * ((size_t)n * n + n);
     const size_t smem_m = lum_smem_bytes(n);
     cudaError_t e = cudaFuncSetAttribute(lu_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
     if (e == cudaSuccess) {
-        lu_mixed_kernel<<<(unsigned)ns, LUM_THREADS, smem_m, st>>>(n, ns, A_dev, r_dev, active, dx_dev, status_dev);
+        lu_mixed_kernel<<<(unsigned)ns, LUM_THREADS, smem_m, st>>>(n, ns, A_dev, r_dev, active, dx_dev, status_dev,
+                                                                   rtol);
         e = cudaGetLastError();
     }
     // the systems the FP32 factors could not refine (status 3), again in FP64
@@ -1833,7 +1835,8 @@ extern "C" int irbc_lu_solve(int n, int64_t ns, const double *A_dev, const doubl
     const size_t smem = sizeof(double) * ((size_t)n * n + n);
     if (smem > 220 * 1024) return set_error(DDSG_ERR_ARG, "irbc_lu_solve: system too large for shared memory (n <= 165)");
     if (!A_dev || !r_dev || !dx_dev || !status_dev) return set_error(DDSG_ERR_ARG, "irbc_lu_solve: NULL argument");
-    return lu_solve_masked(n, ns, A_dev, r_dev, nullptr, dx_dev, status_dev, reinterpret_cast<cudaStream_t>(stream));
+    return lu_solve_masked(n, ns, A_dev, r_dev, nullptr, dx_dev, status_dev, 0x1p-46,
+                           reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *states_dev, double *sol_dev,
@@ -1947,7 +1950,9 @@ extern "C" int irbc_newton(irbc_t *M, hdmr_t *policy, int64_t ns, const double *
         if (e != cudaSuccess) { fail_cuda(e); break; }
         {
             Tracer::Scope ts(&M->tr, 4, st);
-            rc = lu_solve_masked(n, nw, J, r, active, dz, stat, st);
+            // F32C: the Jacobian's derivative sums are FP32, so the step is refined
+            // to 2^-30 of its size; FP64: to FP64 accuracy
+            rc = lu_solve_masked(n, nw, J, r, active, dz, stat, precision == DDSG_F32C ? 0x1p-30 : 0x1p-46, st);
         }
         if (rc) break;
         std::vector<int32_t> h_lu(nw);
