@@ -512,8 +512,11 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
                                   ((sizeof(JGroup) * G + sizeof(int32_t) * N + 15) & ~(size_t)15));
     W *oS1 = oj, *oSM = oj + N, *oik = oj + 2 * N, *ocA = oj + 3 * N;
     W *os1p = oj + 4 * N, *osMp = oj + 5 * N, *os1m = oj + 6 * N, *osMm = oj + 7 * N;
-    DTerm<W> *pool = reinterpret_cast<DTerm<W> *>(
-        reinterpret_cast<unsigned char *>(oj) + ((sizeof(W) * 8 * N + 15) & ~(size_t)15));
+    // per country j: k'_j and the three a'_j values (no shock, +, -) encoded once
+    uint64_t *Xk = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(oj) +
+                                                ((sizeof(W) * 8 * N + 15) & ~(size_t)15));
+    uint64_t *Xa = Xk + N;   // Xa[3 j + v]
+    DTerm<W> *pool = reinterpret_cast<DTerm<W> *>(Xk + 4 * N);
     __shared__ int cursor;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) cursor = 0;
@@ -527,6 +530,12 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
         oSM[j] = (W)ax[1 * N + j];
         oik[j] = (W)ik;
         ocA[j] = (W)cA;
+        {
+            bool bd = false;
+            unsigned long long cl = 0;
+            Xk[j] = encode_coord(kp[j], lo[N + j], span[N + j], bd, cl);
+            for (int v = 0; v < 3; ++v) Xa[3 * j + v] = encode_coord(ax[(3 + v) * N + j], lo[j], span[j], bd, cl);
+        }
         for (int u = 0; u < 2; ++u) {
             const int q = 2 * N + u;   // global node: every a' shocked, variant 1 (+) or 2 (-)
             const double kpp = node64(q, j), lamp = node64(q, L);
@@ -555,8 +564,6 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
             const DevComp &cd = t.comps[kids[g]];
             const double coef = paper ? cd.b : 1.0;
             if (coef != 0.0) {
-                bool bad = false;
-                unsigned long long cl = 0;
                 const int tb = paper ? cd.tup_begin : cd.tup_int;
                 uint64_t Xd[KMAX];
                 int dpos = 0, apos = -1, ctry = -1, na = 0;
@@ -564,22 +571,23 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
                     const int dim = cd.dims[j];
                     if (dim == dk) {
                         dpos = j;
-                        Xd[j] = encode_coord(kp[i], lo[dk], span[dk], bad, cl);
+                        Xd[j] = Xk[i];
                     } else if (dim < N) {
                         apos = j;
                         ctry = dim;
                         ++na;
-                        Xd[j] = encode_coord(ax[3 * N + dim], lo[dim], span[dim], bad, cl);
+                        Xd[j] = Xa[3 * dim];
                     } else {
-                        Xd[j] = encode_coord(kp[dim - N], lo[dim], span[dim], bad, cl);
+                        Xd[j] = Xk[dim - N];
                     }
                 }
                 const int nv = na == 0 ? 1 : 3;
                 bool over = na > 1;
                 DTerm<W> loc[DT_CAP];
+                const W dscale = (W)(coef / span[dk]);
                 for (int v = 0; v < nv && !over; ++v) {
-                    if (v > 0) Xd[apos] = encode_coord(ax[(3 + v) * N + ctry], lo[ctry], span[ctry], bad, cl);
-                    const int nt = comp_dterms<W>(t, cd, tb, dpos, Xd, (W)(coef / span[dk]), loc, DT_CAP);
+                    if (v > 0) Xd[apos] = Xa[3 * ctry + v];
+                    const int nt = comp_dterms<W>(t, cd, tb, dpos, Xd, dscale, loc, DT_CAP);
                     if (nt < 0) { over = true; break; }
                     const int off = atomicAdd(&cursor, nt);
                     if (off + nt > pool_cap) { over = true; break; }
@@ -693,7 +701,8 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
     }
 }
 
-// Shared memory of the Jacobian kernel: the groups, the column states and a
+// Shared memory of the Jacobian kernel: the groups, the column states, the
+// per-country node factors and encoded coordinates, and a
 // term pool sized for the most terms one state can collect (`terms`, from the
 // tables' tuple counts), within kJacSmem bytes in all (a column whose terms
 // do not fit is NaN). A pool sized to the tables lets several blocks share an SM.
@@ -721,7 +730,7 @@ static cudaError_t launch_jacobian(int precision, const IrbcDev &P, int64_t s0, 
                                    const void *dY, const double *aux, double *jac, cudaStream_t st) {
     const size_t wsz = precision == DDSG_F64 ? sizeof(double) : sizeof(float);
     const size_t fixed = ((sizeof(JGroup) * G + sizeof(int32_t) * P.N + 15) & ~(size_t)15) +
-                         ((wsz * 8 * P.N + 15) & ~(size_t)15);
+                         ((wsz * 8 * P.N + 15) & ~(size_t)15) + sizeof(uint64_t) * 4 * P.N;
     const size_t term = precision == DDSG_F64 ? sizeof(DTerm<double>) : sizeof(DTerm<float>);
     if (fixed + 64 * term > kJacSmem) return cudaErrorInvalidValue;
     const size_t cap = std::min<size_t>(std::max<int64_t>(terms, 1), (kJacSmem - fixed) / term);
@@ -1680,7 +1689,8 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
         if (N > 32 * JAC_KJ)
             return set_error(DDSG_ERR_ARG, "euler_residual: the Jacobian supports N <= 192");
         if (((sizeof(JGroup) * kids.size() + sizeof(int32_t) * N + 15) & ~(size_t)15) +
-                ((sizeof(double) * 8 * N + 15) & ~(size_t)15) + 64 * sizeof(DTerm<double>) > kJacSmem)
+                ((sizeof(double) * 8 * N + 15) & ~(size_t)15) + sizeof(uint64_t) * 4 * N +
+                64 * sizeof(DTerm<double>) > kJacSmem)
             return set_error(DDSG_ERR_ARG, "euler_residual: too many components hold a k dimension for the Jacobian");
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
