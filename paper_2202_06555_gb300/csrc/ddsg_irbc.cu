@@ -462,6 +462,19 @@ __device__ __forceinline__ float to_w<float>(double x) {
     return __uint_as_float(f | ((uint32_t)ex << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
 }
 
+// FP32 -> FP64 on the integer units (exact for every value: normal FP32 values
+// from their fields, the others through the hardware conversion). GB300's FP64
+// pipe runs conversions too, at 16 cycles per warp instruction.
+__device__ __forceinline__ double widen_f32(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t ex = (b >> 23) & 0xffu;
+    if (ex == 0u || ex == 0xffu) return (double)x;
+    return __longlong_as_double((long long)(((uint64_t)(b & 0x80000000u) << 32) | ((uint64_t)(ex + 896u) << 52) |
+                                            ((uint64_t)(b & 0x7fffffu) << 29)));
+}
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return widen_f32(x); }
+
 struct JGroup {
     int32_t i, ctry, nv, off[3], cnt[3];
     double dPN[3];
@@ -512,9 +525,11 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
                                   ((sizeof(JGroup) * G + sizeof(int32_t) * N + 15) & ~(size_t)15));
     W *oS1 = oj, *oSM = oj + N, *oik = oj + 2 * N, *ocA = oj + 3 * N;
     W *os1p = oj + 4 * N, *osMp = oj + 5 * N, *os1m = oj + 6 * N, *osMm = oj + 7 * N;
+    // a'_j at no shock / + / -, and (node shortcut) the no-shock k''_j, in W
+    W *oa0 = oj + 8 * N, *oap = oj + 9 * N, *oam = oj + 10 * N, *okb = oj + 11 * N;
     // per country j: k'_j and the three a'_j values (no shock, +, -) encoded once
     uint64_t *Xk = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(oj) +
-                                                ((sizeof(W) * 8 * N + 15) & ~(size_t)15));
+                                                ((sizeof(W) * 12 * N + 15) & ~(size_t)15));
     uint64_t *Xa = Xk + N;   // Xa[3 j + v]
     DTerm<W> *pool = reinterpret_cast<DTerm<W> *>(Xk + 4 * N);
     __shared__ int cursor;
@@ -530,6 +545,10 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
         oSM[j] = (W)ax[1 * N + j];
         oik[j] = (W)ik;
         ocA[j] = (W)cA;
+        oa0[j] = (W)ax[3 * N + j];
+        oap[j] = (W)ax[4 * N + j];
+        oam[j] = (W)ax[5 * N + j];
+        okb[j] = DELTA ? (W)y3s[j] : (W)0;
         {
             bool bd = false;
             unsigned long long cl = 0;
@@ -657,6 +676,10 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
                 }
                 const int ctry = gr.ctry;
                 const W dPN0 = (W)gr.dPN[0], dPN1 = (W)gr.dPN[1], dPN2 = (W)gr.dPN[2];
+                // lambda' at the country's two nodes (the same for every output)
+                W lamq[2] = {(W)0, (W)0};
+                if (nv == 3)
+                    for (int u = 0; u < 2; ++u) lamq[u] = nodew(2 * ctry + u, L);
 #pragma unroll
                 for (int kk = 0; kk < JAC_KJ; ++kk) {
                     const int j = lane + 32 * kk;
@@ -671,10 +694,10 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
                         W s1c[2], sMc[2];
                         for (int u = 0; u < 2; ++u) {
                             const int q = 2 * ctry + u;
-                            const W kpp = nodew(q, j);
-                            const W lamp = nodew(q, L);
+                            const W kpp = DELTA ? okb[j] + dYs[(int64_t)q * m + j] : nodew(q, j);
+                            const W lamp = lamq[u];
                             const W g2 = kpp * ik - (W)1;
-                            const W ap = to_w<W>(ax[(j == ctry ? 4 + u : 3) * N + j]);
+                            const W ap = j == ctry ? (u == 0 ? oap[j] : oam[j]) : oa0[j];
                             s1c[u] = ww * lamp * phi * (g2 + (W)1) * ik;
                             sMc[u] = ww * (ap * cA + omd + (W)0.5 * phi * g2 * (g2 + (W)2));
                         }
@@ -696,7 +719,8 @@ __global__ void __launch_bounds__(JAC_THREADS) irbc_jacobian_kernel(IrbcDev P, i
 #pragma unroll
         for (int kk = 0; kk < JAC_KJ; ++kk) {
             const int j = lane + 32 * kk;
-            if (j < N) J[(int64_t)j * m + i] = cs == 2 ? NAN : (j == i ? ax[2 * N + j] : 0.0) + (double)acc[kk];
+            if (j < N)
+                J[(int64_t)j * m + i] = cs == 2 ? NAN : (j == i ? ax[2 * N + j] + to_f64(acc[kk]) : to_f64(acc[kk]));
         }
     }
 }
@@ -730,7 +754,7 @@ static cudaError_t launch_jacobian(int precision, const IrbcDev &P, int64_t s0, 
                                    const void *dY, const double *aux, double *jac, cudaStream_t st) {
     const size_t wsz = precision == DDSG_F64 ? sizeof(double) : sizeof(float);
     const size_t fixed = ((sizeof(JGroup) * G + sizeof(int32_t) * P.N + 15) & ~(size_t)15) +
-                         ((wsz * 8 * P.N + 15) & ~(size_t)15) + sizeof(uint64_t) * 4 * P.N;
+                         ((wsz * 12 * P.N + 15) & ~(size_t)15) + sizeof(uint64_t) * 4 * P.N;
     const size_t term = precision == DDSG_F64 ? sizeof(DTerm<double>) : sizeof(DTerm<float>);
     if (fixed + 64 * term > kJacSmem) return cudaErrorInvalidValue;
     const size_t cap = std::min<size_t>(std::max<int64_t>(terms, 1), (kJacSmem - fixed) / term);
@@ -1689,7 +1713,7 @@ extern "C" int euler_residual(irbc_t *M, hdmr_t *policy, int64_t ns, const doubl
         if (N > 32 * JAC_KJ)
             return set_error(DDSG_ERR_ARG, "euler_residual: the Jacobian supports N <= 192");
         if (((sizeof(JGroup) * kids.size() + sizeof(int32_t) * N + 15) & ~(size_t)15) +
-                ((sizeof(double) * 8 * N + 15) & ~(size_t)15) + sizeof(uint64_t) * 4 * N +
+                ((sizeof(double) * 12 * N + 15) & ~(size_t)15) + sizeof(uint64_t) * 4 * N +
                 64 * sizeof(DTerm<double>) > kJacSmem)
             return set_error(DDSG_ERR_ARG, "euler_residual: too many components hold a k dimension for the Jacobian");
     }
