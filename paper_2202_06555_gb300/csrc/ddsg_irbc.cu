@@ -1410,30 +1410,37 @@ __global__ void __launch_bounds__(32 * DLT_WARPS) irbc_delta_kernel(IrbcDev P, i
                 nan = !delta_walk_warp<PREC, OC>(P, t, paper, aoff, acomp, states, guess, lo, span, s0 + slp, ip, Xp,
                                                  m0, lane, acc);
             } else if (!badp) {
+                bool ok[OC];   // this lane's outputs in range
+#pragma unroll
+                for (int c = 0; c < OC; ++c) ok[c] = m0 + lane + 32 * c < m;
+                const W *al = alpha + m0 + lane;
 #pragma unroll
                 for (int v = 0; v < 3; ++v) {
                     const int n = cp[v];
-                    for (int q = 0; q < n; q += UNR) {
+                    int q = 0;
+                    for (; q + UNR <= n; q += UNR) {   // UNR terms' rows in flight
                         int32_t r[UNR];
                         W ww[UNR], x[UNR][OC];
 #pragma unroll
                         for (int k = 0; k < UNR; ++k) {
-                            const int qq = q + k < n ? q + k : q;
-                            r[k] = T.row[v][qq][p];
-                            ww[k] = T.w[v][qq][p];
+                            r[k] = T.row[v][q + k][p];
+                            ww[k] = T.w[v][q + k][p];
                         }
 #pragma unroll
                         for (int k = 0; k < UNR; ++k)
 #pragma unroll
-                            for (int c = 0; c < OC; ++c) {
-                                const int o = m0 + lane + 32 * c;
-                                x[k][c] = (q + k < n && o < m) ? alpha[(int64_t)r[k] * mp + o] : (W)0;
-                            }
+                            for (int c = 0; c < OC; ++c) x[k][c] = ok[c] ? al[(int64_t)r[k] * mp + 32 * c] : (W)0;
 #pragma unroll
                         for (int k = 0; k < UNR; ++k)
 #pragma unroll
-                            for (int c = 0; c < OC; ++c)
-                                if (q + k < n && m0 + lane + 32 * c < m) acc[v][c] += ww[k] * x[k][c];
+                            for (int c = 0; c < OC; ++c) acc[v][c] += ww[k] * x[k][c];
+                    }
+                    for (; q < n; ++q) {   // the rest, one term at a time (same order)
+                        const int32_t r = T.row[v][q][p];
+                        const W ww = T.w[v][q][p];
+#pragma unroll
+                        for (int c = 0; c < OC; ++c)
+                            if (ok[c]) acc[v][c] += ww * al[(int64_t)r * mp + 32 * c];
                     }
                 }
             }
@@ -1580,7 +1587,7 @@ cudaError_t launch_delta_oc(const IrbcDev &P, int64_t s0, int64_t nsc, const Dev
     return cudaGetLastError();
 }
 
-// outputs per lane per pass: the fewest of 2, 4, 6, 8 that cover m in one pass
+// outputs per lane per pass: the fewest of 2, 4, 5, 6, 8 that cover m in one pass
 template <int PREC>
 cudaError_t launch_delta(const IrbcDev &P, int64_t s0, int64_t nsc, const DevTables &t, int form,
                          const int32_t *aoff, const int32_t *acomp, const double *states, const double *guess,
@@ -1589,6 +1596,7 @@ cudaError_t launch_delta(const IrbcDev &P, int64_t s0, int64_t nsc, const DevTab
     const int need = (P.m + 31) / 32;
     if (need <= 2) return launch_delta_oc<PREC, 2>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, dY, st);
     if (need <= 4) return launch_delta_oc<PREC, 4>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, dY, st);
+    if (need <= 5) return launch_delta_oc<PREC, 5>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, dY, st);
     if (need <= 6) return launch_delta_oc<PREC, 6>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, dY, st);
     return launch_delta_oc<PREC, 8>(P, s0, nsc, t, form, aoff, acomp, states, guess, lo, span, y3, dY, st);
 }

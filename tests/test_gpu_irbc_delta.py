@@ -178,10 +178,11 @@ def test_delta_nodes_with_more_terms_than_the_list_holds(G):
             assert np.all(np.abs(r_d - r_ref) <= 1e-11 * sc), np.max(np.abs(r_d - r_ref) / sc)
 
 
-@pytest.mark.parametrize("N", [80, 200, 300])
+@pytest.mark.parametrize("N", [80, 170, 200, 300])
 def test_delta_nodes_wide_policies(G, N):
-    """Policies of N + 1 = 81, 201 and 301 outputs: the delta kernel's lanes
-    hold 4 and 8 outputs each, and at 301 outputs it takes two passes. States
+    """Policies of N + 1 = 81, 171, 201 and 301 outputs: the delta kernel's
+    lanes hold 4, 6 and 8 outputs each (N = 150 takes 5), and at 301 outputs
+    it takes two passes. States
     not a multiple of the 32 pairs a warp sums. Delta against the all-node
     path at the bars of the N = 150 case (the all-node path is pinned to the
     oracle there; the F32C bar is twice the oracle one)."""
