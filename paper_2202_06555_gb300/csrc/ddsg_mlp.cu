@@ -3,7 +3,7 @@
 // tiles, FP32 accumulators in tensor memory, fused epilogues).
 //
 // The network proposes Newton initial guesses for the IRBC step; the paper
-// has no network -- the interpolant and the Newton solve stay the judges.
+// has no network -- the interpolant and the Newton solve decide the result.
 //
 // Layout: every width is padded to a multiple of 64 with zeros (weights,
 // biases, activations); batches are padded to a multiple of 128 rows whose
