@@ -381,6 +381,49 @@ def irbc_workload(w, G=None):
     return t1, lam, fn, comps, S, g
 
 
+def irbc_sweep_flops(G, h, w, t1, comps, fn, S, g, prec, form, sample=1000):
+    """Algorithmic flops of one all-node sweep's interpolation: the active points
+    of the next-period states at the 2(N+1) monomial nodes of a sample of the
+    states (counted by the library's count pass), scaled to all states, each
+    point costing 2m + k + 1 (k its component's order). The node queries are
+    formed here from the law of motion only to count points."""
+    import torch
+    N, m, d = w["N"], w["m"], w["d"]
+    ns = min(sample, S.shape[0])
+    hs = np.sqrt(N + 1.0)
+    la = np.log(S[:ns, :N])
+    X = np.empty((ns, 2 * (N + 1), d))
+    for q in range(2 * (N + 1)):
+        e = np.zeros(N)
+        if q < 2 * N:
+            e[q // 2] = hs if q % 2 == 0 else -hs
+        else:
+            e[:] = hs if q == 2 * N else -hs
+        X[:, q, :N] = np.exp(t1["rho"] * la + t1["sigma"] * e[None, :])
+        X[:, q, N:] = g[:ns, :N]
+    X = X.reshape(-1, d)
+    n = X.shape[0]
+    x = torch.from_numpy(X).cuda()
+    y = torch.empty((n, m), dtype=torch.float64, device="cuda")
+    cnt = torch.empty(n, dtype=torch.int32, device="cuda")
+    h.eval(x, y, prec, form, None, cnt)
+    torch.cuda.synchronize()
+    A = float(cnt.double().sum().item())
+    # the order <= 1 part of the same policy, for the k of each point
+    h1 = G.HDMR(d, m, 2, lo=np.full(d, 0.8), hi=np.full(d, 1.2))
+    c1 = [u for u in comps if len(u) <= 1]
+    for u in c1:
+        h1.add_regular(list(u), w["level"])
+    h1.hierarchize(torch.from_numpy(np.concatenate([fn(u, h1.component_points(c)[2]) for c, u in enumerate(c1)])).cuda())
+    h1.eval(x, y, prec, form, None, cnt)
+    torch.cuda.synchronize()
+    A1 = float(cnt.double().sum().item())
+    h1.close()
+    scale = S.shape[0] / ns
+    flops = ((2.0 * m + 1.0) * A + 2.0 * (A - A1) + (A1 - n)) * scale
+    return flops, A / n
+
+
 def run_irbc(args, w):
     N, m, d = w["N"], w["m"], w["d"]
     nq = 2 * (N + 1)
@@ -413,8 +456,10 @@ def run_irbc(args, w):
                                   "d2h_bytes_per_step": 0}}), flush=True)
         return 0
     import torch
+    import paper_2202_06555_gb300 as G
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    out = measure_irbc(w, args.steps, args.warmup)
+    G.load()
+    out = measure_irbc(w, args.steps, args.warmup, fma=measure_fma_peaks(G, None))
     print(json.dumps(out), flush=True)
     return 0
 
@@ -426,7 +471,7 @@ IRBC_NEWTON_ALL = (("f64", "F64", 1e-6, "NODES_ALL"), ("f32c", "F32C", 1e-6, "NO
                    ("f64_tight_node_shortcut", "F64", 1e-10, "NODES_DELTA"))
 
 
-def measure_irbc(w, steps, warmup, newton_variants=IRBC_NEWTON_ALL):
+def measure_irbc(w, steps, warmup, newton_variants=IRBC_NEWTON_ALL, fma=None):
     """Euler-residual sweep of the N = 150 model on the GPU (all nodes, then the
     node shortcut) and Newton solves per variant; returns the JSON record."""
     import torch
@@ -523,6 +568,25 @@ def measure_irbc(w, steps, warmup, newton_variants=IRBC_NEWTON_ALL):
                         "euler_error_log10_max": float(np.log10(np.max(ee[:, 0]))),
                         "kernels_ms_total": {kk: vv[0] for kk, vv in prof_n.items()},
                         "launches": sum(vv[1] for vv in prof_n.values())}
+    roof = None
+    if fma is not None:
+        # the sweep's interpolation (all nodes) against the measured FMA peak
+        flops, apq = irbc_sweep_flops(G, h, w, t1, comps, fn, S, g, prec, form)
+        ev_tot, ev_n = prof.get("eval", (0.0, 1))
+        ev_n = max(1, ev_n) // max(1, steps)   # launches per sweep (chunks of states)
+        ev_ms = ev_tot / max(1, steps)        # eval time per sweep
+        peak = fma["fp32"] if prec == G.F32C else fma["fp64_fma"]
+        achieved = flops / (ev_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "eval (the sweep's interpolation of all 2(N+1) nodes)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel_ms_per_sweep": ev_ms, "launches_per_sweep": ev_n,
+                "flops_per_sweep": flops,
+                "active_points_per_query": apq,
+                "flop_count": "sum over active points of 2m + k + 1, counted on the node queries of "
+                              "1,000 of the states and scaled to all",
+                "peak_source": "measured (of measured): ddsg_probe_fma %s chains" %
+                               ("FP32" if prec == G.F32C else "FP64"),
+                "note": "the residual, Jacobian, LU and delta kernels: profiles/irbc150_newton_kernels.md"}
     out = {"metric": metric, "value": value, "unit": "evals/s", "n_gpus": 1, "steps": steps,
            "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32" if prec == G.F32C else "f64", "data": "synthetic",
@@ -534,6 +598,8 @@ def measure_irbc(w, steps, warmup, newton_variants=IRBC_NEWTON_ALL):
            "kernels_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
            "gpu_launches": sum(v[1] for v in prof.values()),
            "node_shortcut": shortcut, "newton": newton, "clocks": clk.summary()}
+    if roof is not None:
+        out["roofline"] = roof
     h.close()
     M.close()
     return out
@@ -944,11 +1010,7 @@ def run_extra_configs(uuid, fma):
     rec = measure_irbc(dict(WORKLOADS["irbc150"]), 5, 3,
                        newton_variants=(("f32c_node_shortcut", "F32C", 1e-6, "NODES_DELTA"),
                                         ("f64_tight_node_shortcut", "F64", 1e-10, "NODES_DELTA"),
-                                        ("f32c", "F32C", 1e-6, "NODES_ALL")))
-    ev = rec["kernels_ms"]
-    rec["roofline"] = {"bound": "latency", "kernel": "irbc residual sweep (eval dominates)",
-                       "kernel_ms": ev, "traffic": None,
-                       "note": "per-kernel split in kernels_ms; profiles/irbc150_newton_kernels.md gives each limiter"}
+                                        ("f32c", "F32C", 1e-6, "NODES_ALL")), fma=fma)
     rec["wall_s"] = time.perf_counter() - t0
     out["c4_irbc150"] = rec
     torch.cuda.synchronize()

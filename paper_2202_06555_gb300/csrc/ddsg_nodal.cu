@@ -913,15 +913,22 @@ __global__ void __launch_bounds__(kTmNT, 1) eval_nodal_tmem_kernel(const EvalPar
     const int grp = warp / QW;
     const int qw = warp - grp * QW;
     const int qi = qw * 32 + lane;
-    const int64_t q = (int64_t)blockIdx.x * kTmQB + qi;
+    // work items (query tile of kTmQB, output window of 32), window fastest; the
+    // block's two warp groups take two consecutive items, so an odd number of
+    // windows leaves no group idle
+    const int nwin = N.rs32 >> 5;
+    const int64_t ntile = (p.n + kTmQB - 1) / kTmQB;
+    const int64_t item = (int64_t)blockIdx.x * 2 + grp;
+    const int64_t tile = item / nwin;
+    const int64_t q = tile * kTmQB + qi;
     const int64_t qc = q < p.n ? q : p.n - 1;
     const bool valid = q < p.n;
     const bool bad = !valid || p.flags[q] != 0;
     const bool paper = p.form == DDSG_FORM_PAPER;
     const int m = p.m;
     const int rs = N.rs32;
-    const int m0 = (blockIdx.y * 2 + grp) * 32;
-    const bool wact = m0 < rs;
+    const int m0 = (int)(item - tile * nwin) * 32;
+    const bool wact = item < ntile * nwin;
     const int nproc = N.n;
     const int meta_bytes = N.meta_bytes;
     const int l8 = lane & 7;
@@ -1121,7 +1128,8 @@ static cudaError_t launch_nodal_tmem(const EvalParams &p, cudaStream_t st) {
     const int buf = (int)((N.stage_bytes[DDSG_F32C] + 127) & ~127ll);
     const int nbuf = 128 + 3 * (int64_t)buf <= kSmemLimit ? 3 : 2;
     const int smem = 128 + nbuf * buf;
-    dim3 grid((unsigned)((p.n + kTmQB - 1) / kTmQB), (unsigned)((N.rs32 + 63) / 64));
+    const int64_t items = (p.n + kTmQB - 1) / kTmQB * (N.rs32 >> 5);   // (query tile, 32-output window)
+    dim3 grid((unsigned)((items + 1) / 2));
     cudaError_t e = cudaFuncSetAttribute(eval_nodal_tmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     eval_nodal_tmem_kernel<<<grid, kTmNT, smem, st>>>(p, buf, nbuf);

@@ -301,17 +301,21 @@ def test_every_kernel_config_matches_oracle(G):
     assert h.stats()["wait_timeouts"] == 0
 
 
-@pytest.mark.parametrize("m", [20, 33, 64])
+@pytest.mark.parametrize("m", [20, 33, 64, 96, 151])
 def test_nodal_kernels_wide_outputs(G, m):
     """The nodal-slab kernels at output counts that fill one window (20, 32 padded),
-    spill into a second (33 -> 64) or fill two (64), on an adaptive d = 5 order-2
-    expansion, at uniform queries and the edge cases (nodes, faces, corners,
-    clamped and non-finite rows), against the oracle; kernel 6 keeps its totals
-    in tensor memory."""
+    spill into a second (33 -> 64), fill two (64), or take 3 and 5 windows (96,
+    151 -> 160), on an adaptive d = 5 order-2 expansion, at uniform queries and
+    the edge cases (nodes, faces, corners, clamped and non-finite rows), against
+    the oracle. Kernel 6 keeps its totals in tensor memory and gives each warp
+    group of a block one (query tile, window) item: with 1, 3 or 5 windows a
+    block's two groups take different tiles, or one group finds no item. At 151
+    outputs the grid stops at level 5 so that a component's node rows fit the
+    shared staging buffer."""
     d = 5
     c = synth.family_coeffs(synth.BASE_SEED + 63 + m, m, d)
     fn = lambda dims, X: synth.family_cut(c, dims, X)
-    ref, h = build_pair(G, d, m, O.full_order_components(d, 2), fn, eps=1e-3, level=8)
+    ref, h = build_pair(G, d, m, O.full_order_components(d, 2), fn, eps=1e-3, level=8 if m <= 96 else 5)
     pts = [np.zeros(d), np.ones(d), np.full(d, 0.5), np.array([0.25, 0.75, 0.125, 0.375, 0.625]),
            np.array([-0.2, 1.4, 0.5, 0.5, 2.0]), np.array([np.nan, 0.2, 0.3, 0.4, 0.5])]
     X = np.concatenate([np.array(pts), ref.node_coords(d + 3)[:, [0, 0, 0, 0, 0]][:60],
