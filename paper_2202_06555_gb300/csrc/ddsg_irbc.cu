@@ -1,22 +1,30 @@
-// ddsg_irbc.cu -- smooth IRBC model step on the GPU (Sec. 2.1 of the paper):
-// Euler-equation residuals (eq. model1) and the aggregate resource constraint
-// (eq. model2) at a batch of states, with the expectation taken by a degree-3
-// monomial rule over the 2(N+1) shocks; an analytic Jacobian; and a batched
-// FP64 Newton solve with dense LU and backtracking.
+// ddsg_irbc.cu -- smooth and non-smooth IRBC model step on the GPU (Sec. 2.1 of
+// the paper): Euler-equation residuals (eq. model1; eq. modelkink1 with
+// irreversible investment) and the aggregate resource constraint (eq. model2)
+// at a batch of states, with the expectation taken by a degree-3 monomial rule
+// over the 2(N+1) shocks; an analytic Jacobian; a batched mixed-precision LU;
+// and a damped Newton solve.
 //
 // Pipeline of one residual sweep (states processed in chunks that fit the
 // model's workspace):
 //   irbc_queries_kernel   next state x' = (a', k') at every (state, node)
 //                         (eq. law_of_motion), encoded into the evaluation
 //                         kernels' dimension-major fixed-point layout;
-//   launch_eval           the policy interpolant at all x' (FP64 or F32C);
-//   irbc_residual_kernel  one block per state: node sums in FP64, residuals,
-//                         Euler errors and the Jacobian's border and diagonal
-//                         pieces;
-//   irbc_jacobian_kernel  one thread per column i < N: the policy's derivative
-//                         in k'_i enters through the components holding dim N+i,
-//                         whose a-coordinate (if any) takes only three values
-//                         over the nodes (no shock, +shock, -shock).
+//                         node shortcut: irbc_queries3_kernel, only the
+//                         no-shock state and the two global-shock nodes;
+//   launch_eval           the policy interpolant at those queries (FP64 or F32C);
+//   irbc_delta_kernel     node shortcut: each country node's policy change from
+//                         the no-shock policy, from the components holding a_i;
+//   irbc_residual_kernel  one block per state: node sums (FP64; with the node
+//                         shortcut FP64 no-shock terms plus sums of the changes),
+//                         residuals, Euler errors and the Jacobian's border and
+//                         diagonal pieces;
+//   irbc_jacobian_kernel  one block per state: d r_j / d k'_i through the
+//                         components holding dim N+i, whose a-coordinate (if
+//                         any) takes only three values over the nodes.
+// irbc_newton iterates residual, LU (lu_mixed_kernel: FP32 factors refined in
+// FP64, lu_solve_kernel in FP64 for the rest) and a backtracking line search
+// over a working set from which converged states leave.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
