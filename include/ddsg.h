@@ -477,7 +477,10 @@ int euler_residual(irbc_t *model, hdmr_t *policy, int64_t ns, const double *stat
  *     policy plus, for each component holding a_i, that component at the
  *     shocked a'_i minus it at the no-shock a'_i (exact by the additive cut-HDMR
  *     form; differences are rounding only). Needs no assumption on the
- *     component set. About N times less interpolation work.
+ *     component set. About N times less interpolation work. The changes are
+ *     kept in the evaluation precision and the residual's node sums expand
+ *     around the no-shock policy: FP64 no-shock and global-node terms plus
+ *     sums of the changes (FP32 with DDSG_F32C).
  */
 enum { DDSG_IRBC_NODES_ALL = 0, DDSG_IRBC_NODES_DELTA = 1 };
 
@@ -512,9 +515,14 @@ int irbc_lu_solve(int n, int64_t ns, const double *A_dev, const double *r_dev, d
  * holds the initial guess and receives the solution. Stops a state when
  * ||r||_inf <= tol. Outputs (nullable): iters_dev, status_dev (0 converged,
  * 1 max_it reached, 2 singular Jacobian), resnorm_dev (final ||r||_inf).
- * Synchronizes `stream` between iterations. Its device buffers (about
- * ns * m^2 * 8 bytes for the Jacobians) stay on the model for later calls and
- * are freed by irbc_destroy.
+ * Each step is solved as irbc_lu_solve does, refined to FP64 accuracy with
+ * precision DDSG_F64 and to 2^-30 of the step with DDSG_F32C (whose
+ * Jacobian carries FP32 derivative sums). The line search evaluates its trial
+ * points with the Jacobian, which the next iteration reuses; converged states
+ * leave the working set. A state's iterates do not depend on the other
+ * states of the batch. Synchronizes `stream` between iterations. Its device
+ * buffers (about ns * m^2 * 8 bytes for the Jacobians) stay on the model for
+ * later calls and are freed by irbc_destroy.
  */
 int irbc_newton(irbc_t *model, hdmr_t *policy, int64_t ns, const double *states_dev,
                 double *sol_dev, int max_it, double tol, int32_t *iters_dev, int32_t *status_dev,
@@ -534,8 +542,8 @@ int irbc_profile_read(irbc_t *model, double *ms_host, int64_t *launches_host, in
  * inputs are normalized as (x - in_shift) * in_scale and the network is
  * trained (mean squared error) on targets normalized as
  * (y - out_shift) * out_scale. GEMMs are hand-written BF16 tensor-core
- * kernels (mma.sync m16n8k16, FP32 accumulate); master weights and Adam
- * (beta 0.9/0.999, eps 1e-8) are FP32.
+ * kernels (tcgen05.mma with TMA operand tiles and FP32 accumulators in tensor
+ * memory); master weights and Adam (beta 0.9/0.999, eps 1e-8) are FP32.
  * ------------------------------------------------------------------------ */
 typedef struct mlp mlp_t;
 
