@@ -195,8 +195,8 @@ def test_newton_matches_oracle(G, prec):
     assert np.allclose(z.cpu().numpy(), sol_ref, atol=1e-7 if prec == 0 else 1e-5)
 
 
-@pytest.mark.parametrize("mode", ["all", "delta"])
-def test_newton_batch_equals_states_solved_apart(G, mode):
+@pytest.mark.parametrize("mode,prec", [("all", 0), ("delta", 0), ("delta", 1)])
+def test_newton_batch_equals_states_solved_apart(G, mode, prec):
     """States that converge after different numbers of iterations leave the
     Newton working set as they converge (the live ones are gathered into
     contiguous slots). Per-state arithmetic does not depend on the slot, so
@@ -220,13 +220,14 @@ def test_newton_batch_equals_states_solved_apart(G, mode):
         it = torch.zeros(len(idx), dtype=torch.int32, device="cuda")
         stt = torch.zeros(len(idx), dtype=torch.int32, device="cuda")
         nr = torch.zeros(len(idx), dtype=torch.float64, device="cuda")
-        M.newton(h, sd, z, 12, 1e-10, it, stt, nr, 0, 1)
+        M.newton(h, sd, z, 12, 1e-10 if prec == 0 else 1e-6, it, stt, nr, prec, 1)
         torch.cuda.synchronize()
         return z.cpu().numpy(), it.cpu().numpy(), stt.cpu().numpy(), nr.cpu().numpy()
 
     try:
         zb, itb, stb, nrb = solve(np.arange(24))
-        assert len(set(itb[stb == 0].tolist())) >= 2, itb   # the working set did shrink
+        if prec == 0:
+            assert len(set(itb[stb == 0].tolist())) >= 2, itb   # the working set did shrink
         for s in range(24):
             z1, it1, st1, nr1 = solve(np.array([s]))
             assert it1[0] == itb[s] and st1[0] == stb[s], (s, it1, itb[s], st1, stb[s])
