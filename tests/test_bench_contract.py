@@ -41,3 +41,35 @@ def test_headline_metric_is_verbatim_at_d100():
 def test_time_iteration_reference_arm_says_unavailable():
     d = _line("--impl", "reference", "--workload", "ti10", "--steps", "1", "--warmup", "0")
     assert d["impl"] == "reference" and "unavailable" in d
+
+
+def test_flop_count_from_two_count_passes():
+    """The rooflines count Σ over active points of (2m + k + 1), k the point's
+    component order, from two count passes: A over the whole expansion and A1
+    over its order <= 1 part, as (2m + 1) A + 2 (A - A1) + (A1 - n). That holds
+    when the constant component contributes exactly one active point per query,
+    in both forms; the per-order counts of the oracle (expansions cut at order
+    0, 1 and 2) give the direct sum to compare with."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import oracle as O
+    import synth
+    O.build()
+    d, m = 4, 3
+    c = synth.family_coeffs(synth.BASE_SEED + 71, m, d)
+    fn = lambda dims, X: synth.family_cut(c, dims, X)
+    X = synth.uniform_queries(synth.BASE_SEED + 71, 300, d)
+    n = X.shape[0]
+    for form in (0, 1):
+        counts = []
+        for order in (0, 1, 2):
+            E = O.OracleDDSG(d, m)
+            for u in O.full_order_components(d, order):
+                E.add_regular(u, 3)
+            E.fill_values(fn)
+            E.hierarchize()
+            counts.append(float(E.eval(X, form=form, want=("count",))["count"].astype(np.float64).sum()))
+        assert counts[0] == n, (form, counts[0])            # one constant point per query
+        A1, A = counts[1], counts[2]
+        direct = (2 * m + 1) * counts[0] + (2 * m + 2) * (counts[1] - counts[0]) + (2 * m + 3) * (counts[2] - counts[1])
+        assert (2.0 * m + 1.0) * A + 2.0 * (A - A1) + (A1 - n) == direct
